@@ -1,0 +1,252 @@
+/*
+ * nks.h -- C ABI of the GB300 Newton-Krylov-Schwarz solver for the
+ * semi-implicit discrete-variational-derivative (DVD) scheme NSOA-1 of
+ * Huang & Yang, "Parallel energy stable phase field simulations of Ni-based
+ * alloys system" (arXiv 2209.08001).
+ *
+ * The solver advances the coupled Cahn-Hilliard / Allen-Cahn (Ginzburg-Landau)
+ * system for the Al composition c, one long-range order parameter eta and the
+ * elastic displacement u on a periodic, cell-centred, uniform grid (Sec. 2-3).
+ * Every time step solves the nonlinear system F(X) = 0 of Eq. NSOA-1 by an
+ * inexact Newton method with line search (Sec. 4), whose Jacobian systems are
+ * solved by restarted GMRES preconditioned with restricted additive Schwarz
+ * and ILU(0) subdomain solves (Sec. 4, Sec. 5.4).  The step size is adaptive
+ * (Sec. 4, Eq. sencondt) with divergence retries.
+ *
+ * Conventions for every entry point:
+ *   - Grids are x-fastest: point p = x + nx*(y + ny*z).  A "field" array holds
+ *     N = nx*ny*nz doubles in that order.
+ *   - A "state" array (X) holds the fields one after another (SoA): c, eta and,
+ *     when elasticity is on (any of C11, C12, C44 non-zero), u_1..u_d.  Its
+ *     length is nf*N with nf = 2 + d (elastic) or 2.
+ *   - Pointers marked HOST are read or written with synchronous copies before
+ *     the call returns; the caller keeps ownership.  Pointers marked DEVICE
+ *     must be device memory on the problem's device.
+ *   - Every int-returning function returns NKS_OK (0) or a negative-free
+ *     error code below; nks_last_error() then describes the failure.
+ *   - A problem is bound to the CUDA device and stream given at creation and
+ *     is not thread safe; distinct problems may be used from distinct threads.
+ */
+#ifndef NKS_H
+#define NKS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define NKS_OK 0
+#define NKS_EINVAL 1     /* invalid argument or unsupported configuration        */
+#define NKS_EDOMAIN 2    /* c, c*eta or c*(4-3*eta) outside (0, 1)               */
+#define NKS_ENOMEM 3     /* device allocation failed                              */
+#define NKS_EDIVERGED 4  /* Newton failed and the retry budget is spent (Sec. 4)  */
+#define NKS_ETIMEOUT 5   /* an iteration cap was reached                          */
+#define NKS_ECUDA 6      /* CUDA runtime error                                    */
+#define NKS_EPIVOT 7     /* zero pivot in an ILU(0) subdomain factorisation       */
+
+/* precision modes */
+#define NKS_FP64 0       /* everything in FP64                                     */
+#define NKS_MIXED 1      /* FP32 Schwarz factors/sub-solves and Krylov basis;
+                            FP64 residual, update, log terms, energy and mass      */
+
+/* step-size drivers (Sec. 4, Eq. sencondt) */
+#define NKS_DT_FIXED 0
+#define NKS_DT_SOLUTION 1 /* X'_d = ||X^n - X^{n-1}||_2 / dt_{n-1}                */
+#define NKS_DT_ENERGY 2   /* X'_d = |E^n - E^{n-1}| / dt_{n-1}                    */
+
+/* Periodic cell-centred grid x_i = (i - 1/2) h on each axis (Sec. 3). */
+typedef struct {
+    int dim;     /* 1, 2 or 3                                        */
+    int n[3];    /* cells per axis; entries >= dim are ignored        */
+    double h;    /* mesh size (the same on every axis)                */
+} nks_grid;
+
+/*
+ * Dimensionless coefficients (App. A scaling by V_m*dE and the length 1.5 nm).
+ *   kappa       mobility parameter, M = kappa c (1 - c)            (Eq. CHGL)
+ *   gamma_c     gradient coefficient of c                          (Eq. simple free energy-1)
+ *   gamma_eta   gradient coefficient of eta; enters as 3*gamma_eta
+ *   theta       R T / (V_m dE), weight of the entropy terms        (Eq. neq:01)
+ *   w_psi       weight of theta*Psi(c) inside E_2 (1 in Sec. 2-3; App. A cancels it)
+ *   dE0         (E0_Al - E0_Ni)/(V_m dE)                           (App. A)
+ *   L[4], U1, U4  excess and ordering parameters / (V_m dE)        (App. A)
+ *   eps0        composition expansion coefficient of the lattice   (App. A)
+ *   C11, C12, C44  cubic Hooke constants / dE; multiplied by Lscale (Sec. 5.1).
+ *               All three zero switches elasticity (and the u fields) off.
+ *   S           Taylor order of Psi_S (Sec. 3, S = 10 in Sec. 5); must be >= 1
+ */
+typedef struct {
+    double kappa, gamma_c, gamma_eta, theta, w_psi, dE0;
+    double L[4];
+    double U1, U4, eps0;
+    double C11, C12, C44, Lscale;
+    int S;
+} nks_coeffs;
+
+/*
+ * Solver options (Sec. 4; Sec. 5.4 for the Schwarz settings).
+ *   newton_rtol/atol   eps_r, eps_a: stop when ||F|| <= max(eps_r ||F(X_0)||, eps_a)
+ *   newton_maxit       Newton iterations before the step counts as diverged
+ *   ls_alpha, ls_lambda_min  backtracking: halve lambda while
+ *                      ||F(X + lambda S)||^2 > (1 - 2 alpha lambda) ||F||^2 or the
+ *                      trial leaves the domain; fail below lambda_min
+ *   gmres_restart, gmres_maxit  GMRES(m) and the total iteration cap per solve
+ *   gmres_rtol/atol    xi_r, xi_a: ||J S + F|| <= max(xi_r ||F||, xi_a)
+ *   sub[3], overlap    box decomposition (subdomains per axis) and delta (layers
+ *                      per side); each overlapped box must be at least 2 cells
+ *                      shorter than the grid along every axis
+ *   ilu_reuse          1: factor once per time step (ILU(0)-reuse, Table 1)
+ *   precision          NKS_FP64 or NKS_MIXED
+ *   dt_init            dt of the first step (Sec. 5.1: 0.01)
+ *   dt_min, dt_max, zeta  predictor parameters (Eq. sencondt)
+ *   dt_mode            NKS_DT_FIXED / NKS_DT_SOLUTION / NKS_DT_ENERGY
+ *   zeta_persist       0: a doubled zeta is used for the next prediction only
+ *   max_retries        divergence retries (dt /= sqrt 2, zeta *= 2) per step
+ *   u0_rtol/atol/maxit initial mechanical equilibrium solve
+ *   timing             1: record per-kernel CUDA-event times (nks_get_stats)
+ */
+typedef struct {
+    double newton_rtol, newton_atol;
+    int newton_maxit;
+    double ls_alpha, ls_lambda_min;
+    int gmres_restart, gmres_maxit;
+    double gmres_rtol, gmres_atol;
+    int sub[3];
+    int overlap;
+    int ilu_reuse;
+    int precision;
+    double dt_init, dt_min, dt_max, zeta;
+    int dt_mode;
+    int zeta_persist;
+    int max_retries;
+    double u0_rtol, u0_atol;
+    int u0_maxit;
+    int timing;
+} nks_opts;
+
+/* Optional device allocator (for example a framework's caching allocator).
+ * alloc returns device memory of at least `bytes` bytes (NULL on failure);
+ * free releases it.  Both are called on the creating thread. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *ctx);
+    void (*free)(void *ptr, void *ctx);
+    void *ctx;
+} nks_allocator;
+
+typedef struct nks_problem nks_problem; /* opaque, owned by the library */
+
+/* Outcome of one accepted (or failed) time step. */
+typedef struct {
+    double dt;         /* accepted step size                                   */
+    double t;          /* time after the step                                  */
+    double energy;     /* discrete energy E^{n+1} (Eq. freeenergy)             */
+    double mass;       /* <c^{n+1}> = h^d sum c                                */
+    double fnorm0;     /* ||F(X_0)|| of the accepted attempt                   */
+    double fnorm;      /* final ||F||                                          */
+    int retries;       /* divergence retries taken                             */
+    int newton_its;    /* Newton iterations of the accepted attempt            */
+    int gmres_its;     /* GMRES iterations of the accepted attempt             */
+    int status;        /* NKS_OK or the failure code                           */
+} nks_step_info;
+
+/* Per-kernel-class counters (launches and, with opts.timing, device time). */
+#define NKS_NCLASS 10
+typedef struct {
+    long long launches[NKS_NCLASS];
+    double ms[NKS_NCLASS];          /* summed CUDA-event durations (timing = 1) */
+    long long newton_its, gmres_its, steps, retries;
+    long long factor_bytes;         /* bytes of stored Schwarz factors          */
+} nks_stats;
+/* kernel classes: 0 residual, 1 Jacobian action, 2 Schwarz apply,
+ * 3 assembly + ILU(0), 4 Gram-Schmidt dots, 5 Gram-Schmidt update,
+ * 6 projection, 7 energy/mass, 8 vector ops, 9 small dense (Hessenberg) */
+
+/* Fill *g, *k, *o with the defaults: 2-D 64x64 grid, h = 0.25, the paper's
+ * printed constants, and the solver settings of Sec. 4-5. */
+void nks_default_opts(nks_opts *o);
+
+/*
+ * Create a problem from the initial fields and solve the initial mechanical
+ * equilibrium for u (reading: the energy law of Theorem 3.1 assumes u in
+ * equilibrium at level n).  The mean composition cbar0 of Sec. 3 is taken from c.
+ *   c, eta   HOST, N doubles each (x-fastest)
+ *   alloc    NULL: cudaMalloc / cudaFree
+ *   stream   a cudaStream_t, or NULL for a stream the library creates and owns
+ * Fails with NKS_EDOMAIN when an initial value leaves the domain of the
+ * logarithms, NKS_EINVAL for an unsupported grid or decomposition.
+ */
+int nks_create_problem(const nks_grid *grid, const double *c, const double *eta, const nks_coeffs *coeffs,
+                       const nks_opts *opts, const nks_allocator *alloc, void *stream, nks_problem **out);
+
+/*
+ * Advance one time step of NSOA-1.  dt > 0: that step size (no retries);
+ * dt <= 0: step size from opts (dt_init for the first step, then the
+ * predictor of Eq. sencondt) with divergence retries.  On failure the state
+ * stays at X^n and info->status holds the code.  info may be NULL.
+ */
+int nks_step(nks_problem *p, double dt, nks_step_info *info);
+
+/* Discrete energy E^n of Eq. freeenergy (Sec. 3). */
+int nks_energy(const nks_problem *p, double *out);
+
+/* Mass <c^n> = h^d sum_i c_i (Theorem 3.1). */
+int nks_mass(const nks_problem *p, double *out);
+
+/* Copy the current fields to HOST arrays (N doubles each; u: d*N doubles,
+ * component-major, or NULL; ignored without elasticity). */
+int nks_get_fields(const nks_problem *p, double *c, double *eta, double *u);
+
+/* Checkpoint: bytes needed, then save / restore X^n, X^{n-1}, t, step count,
+ * dt_{n-1}, zeta and the two last energies (HOST buffer). Restoring gives a
+ * bitwise-identical continuation. */
+size_t nks_state_size(const nks_problem *p);
+int nks_get_state(const nks_problem *p, void *buf, size_t bytes);
+int nks_set_state(nks_problem *p, const void *buf, size_t bytes);
+
+/* Counters since creation or the last reset. */
+int nks_get_stats(const nks_problem *p, nks_stats *out);
+int nks_reset_stats(nks_problem *p);
+
+void nks_destroy(nks_problem *p);
+
+/* Message of the last failure on this problem ("" if none); p may be NULL for
+ * failures of nks_create_problem on the calling thread. */
+const char *nks_last_error(const nks_problem *p);
+
+/* ------------------------------------------------------------------------ */
+/* Operator-level entry points (the stages of one Newton iteration).         */
+/* They use the problem's grid, coefficients and decomposition and leave its */
+/* state untouched.  All arrays are HOST state arrays of length nf*N.        */
+/* ------------------------------------------------------------------------ */
+
+/* F(X1; X0, dt) of Eq. NSOA-1 (mode 0), or the displacement-only residual
+ * (mode 1: F_c = F_eta = 0) used for the initial equilibrium. */
+int nks_eval_residual(nks_problem *p, const double *X1, const double *X0, double dt, int mode, double *F);
+
+/* Jv = J(X1; X0, dt) v with J = dF/dX1 (Sec. 4, J_m = grad F(X_m)). */
+int nks_apply_jacobian(nks_problem *p, const double *X1, const double *X0, double dt, int mode, const double *v,
+                       double *Jv);
+
+/* z = P sum_i R_i^0T (L_i U_i)^-1 R_i^delta r: restricted additive Schwarz
+ * (Sec. 4, left-RAS) with ILU(0) factors of J(X1; X0, dt) restricted to each
+ * overlapped box, followed by the projection P (mean of z_c removed; the
+ * null modes of the centred-difference strain removed from z_u). */
+int nks_apply_preconditioner(nks_problem *p, const double *X1, const double *X0, double dt, const double *r,
+                             double *z);
+
+/* Solve J(X1; X0, dt) x = b from x = 0 by right-preconditioned GMRES(m)
+ * (Sec. 4) to ||b - J x|| <= tol; its/res receive the iteration count and the
+ * final true residual norm. */
+int nks_linear_solve(nks_problem *p, const double *X1, const double *X0, double dt, int mode, const double *b,
+                     double *x, double tol, int *its, double *res);
+
+/* Energy parts of X (Eq. relations: E1, E2, E3, E4 summed times h^d), their
+ * total, and the mass; parts has 5 entries. */
+int nks_eval_energy(nks_problem *p, const double *X, double *parts, double *mass);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NKS_H */

@@ -1,0 +1,330 @@
+"""GB300 Newton-Krylov-Schwarz solver for the DVD scheme of arXiv 2209.08001.
+
+Thin ctypes binding over ``libnks.so`` (the C ABI of ``include/nks.h``): every
+function here only marshals arguments; all arithmetic of the time step runs in
+the library's CUDA kernels.  There is no CPU fallback: importing works without
+a GPU (so the build can be checked), but any call raises if the library or a
+CUDA device is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libnks.so")
+
+NKS_OK, NKS_EINVAL, NKS_EDOMAIN, NKS_ENOMEM, NKS_EDIVERGED, NKS_ETIMEOUT, NKS_ECUDA, NKS_EPIVOT = range(8)
+NKS_FP64, NKS_MIXED = 0, 1
+DT_MODES = {"fixed": 0, "solution": 1, "energy": 2}
+KERNEL_CLASSES = ["residual", "jacobian_action", "schwarz_apply", "assembly_ilu0", "gs_dots", "gs_update",
+                  "projection", "energy_mass", "vector_ops", "hessenberg"]
+
+
+class NksError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("nks error %d: %s" % (code, msg))
+        self.code = code
+
+
+class nks_grid(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("h", ctypes.c_double)]
+
+
+class nks_coeffs(ctypes.Structure):
+    _fields_ = [("kappa", ctypes.c_double), ("gamma_c", ctypes.c_double), ("gamma_eta", ctypes.c_double),
+                ("theta", ctypes.c_double), ("w_psi", ctypes.c_double), ("dE0", ctypes.c_double),
+                ("L", ctypes.c_double * 4), ("U1", ctypes.c_double), ("U4", ctypes.c_double),
+                ("eps0", ctypes.c_double), ("C11", ctypes.c_double), ("C12", ctypes.c_double),
+                ("C44", ctypes.c_double), ("Lscale", ctypes.c_double), ("S", ctypes.c_int)]
+
+
+class nks_opts(ctypes.Structure):
+    _fields_ = [("newton_rtol", ctypes.c_double), ("newton_atol", ctypes.c_double), ("newton_maxit", ctypes.c_int),
+                ("ls_alpha", ctypes.c_double), ("ls_lambda_min", ctypes.c_double),
+                ("gmres_restart", ctypes.c_int), ("gmres_maxit", ctypes.c_int),
+                ("gmres_rtol", ctypes.c_double), ("gmres_atol", ctypes.c_double),
+                ("sub", ctypes.c_int * 3), ("overlap", ctypes.c_int), ("ilu_reuse", ctypes.c_int),
+                ("precision", ctypes.c_int),
+                ("dt_init", ctypes.c_double), ("dt_min", ctypes.c_double), ("dt_max", ctypes.c_double),
+                ("zeta", ctypes.c_double), ("dt_mode", ctypes.c_int), ("zeta_persist", ctypes.c_int),
+                ("max_retries", ctypes.c_int), ("u0_rtol", ctypes.c_double), ("u0_atol", ctypes.c_double),
+                ("u0_maxit", ctypes.c_int), ("timing", ctypes.c_int)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class nks_allocator(ctypes.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", ctypes.c_void_p)]
+
+
+class nks_step_info(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("t", ctypes.c_double), ("energy", ctypes.c_double),
+                ("mass", ctypes.c_double), ("fnorm0", ctypes.c_double), ("fnorm", ctypes.c_double),
+                ("retries", ctypes.c_int), ("newton_its", ctypes.c_int), ("gmres_its", ctypes.c_int),
+                ("status", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+NCLASS = 10
+
+
+class nks_stats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_longlong * NCLASS), ("ms", ctypes.c_double * NCLASS),
+                ("newton_its", ctypes.c_longlong), ("gmres_its", ctypes.c_longlong),
+                ("steps", ctypes.c_longlong), ("retries", ctypes.c_longlong),
+                ("factor_bytes", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {"launches": {KERNEL_CLASSES[i]: self.launches[i] for i in range(NCLASS)},
+                "ms": {KERNEL_CLASSES[i]: self.ms[i] for i in range(NCLASS)},
+                "newton_its": self.newton_its, "gmres_its": self.gmres_its, "steps": self.steps,
+                "retries": self.retries, "factor_bytes": self.factor_bytes}
+
+
+_lib = None
+_D = ctypes.POINTER(ctypes.c_double)
+_P = ctypes.c_void_p
+
+
+def load():
+    """Load libnks.so (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libnks.so is missing: run `python -c 'import __graft_entry__ as g; g.build()'` "
+                           "(there is no CPU fallback)")
+    L = ctypes.CDLL(LIB_PATH)
+    pp = ctypes.POINTER(ctypes.c_void_p)
+    sig = {
+        "nks_default_opts": (None, [ctypes.POINTER(nks_opts)]),
+        "nks_create_problem": (ctypes.c_int, [ctypes.POINTER(nks_grid), _D, _D, ctypes.POINTER(nks_coeffs),
+                                              ctypes.POINTER(nks_opts), ctypes.POINTER(nks_allocator), _P, pp]),
+        "nks_step": (ctypes.c_int, [_P, ctypes.c_double, ctypes.POINTER(nks_step_info)]),
+        "nks_energy": (ctypes.c_int, [_P, _D]),
+        "nks_mass": (ctypes.c_int, [_P, _D]),
+        "nks_get_fields": (ctypes.c_int, [_P, _D, _D, _D]),
+        "nks_state_size": (ctypes.c_size_t, [_P]),
+        "nks_get_state": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
+        "nks_set_state": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
+        "nks_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(nks_stats)]),
+        "nks_reset_stats": (ctypes.c_int, [_P]),
+        "nks_destroy": (None, [_P]),
+        "nks_last_error": (ctypes.c_char_p, [_P]),
+        "nks_eval_residual": (ctypes.c_int, [_P, _D, _D, ctypes.c_double, ctypes.c_int, _D]),
+        "nks_apply_jacobian": (ctypes.c_int, [_P, _D, _D, ctypes.c_double, ctypes.c_int, _D, _D]),
+        "nks_apply_preconditioner": (ctypes.c_int, [_P, _D, _D, ctypes.c_double, _D, _D]),
+        "nks_linear_solve": (ctypes.c_int, [_P, _D, _D, ctypes.c_double, ctypes.c_int, _D, _D, ctypes.c_double,
+                                            ctypes.POINTER(ctypes.c_int), _D]),
+        "nks_eval_energy": (ctypes.c_int, [_P, _D, _D, _D]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def exported_symbols():
+    """Names the binding expects libnks.so to export (all of include/nks.h)."""
+    return ["nks_default_opts", "nks_create_problem", "nks_step", "nks_energy", "nks_mass", "nks_get_fields",
+            "nks_state_size", "nks_get_state", "nks_set_state", "nks_get_stats", "nks_reset_stats", "nks_destroy",
+            "nks_last_error", "nks_eval_residual", "nks_apply_jacobian", "nks_apply_preconditioner",
+            "nks_linear_solve", "nks_eval_energy"]
+
+
+def _ptr(a):
+    return a.ctypes.data_as(_D)
+
+
+def _c64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def make_grid(dim, n, h):
+    g = nks_grid()
+    g.dim = dim
+    nn = list(n) + [1] * (3 - len(n))
+    for J in range(3):
+        g.n[J] = int(nn[J]) if J < dim else 1
+    g.h = float(h)
+    return g
+
+
+def make_coeffs(cf: dict):
+    k = nks_coeffs()
+    for name in ("kappa", "gamma_c", "gamma_eta", "theta", "w_psi", "dE0", "U1", "U4", "eps0", "C11", "C12", "C44"):
+        setattr(k, name, float(cf[name]))
+    for i in range(4):
+        k.L[i] = float(cf["L"][i])
+    k.Lscale = float(cf.get("Lscale", 1.0))
+    k.S = int(cf["S"])
+    return k
+
+
+def make_opts(op: dict, timing=False):
+    o = nks_opts()
+    load().nks_default_opts(ctypes.byref(o))
+    for name in ("newton_rtol", "newton_atol", "ls_alpha", "ls_lambda_min", "gmres_rtol", "gmres_atol", "dt_init",
+                 "dt_min", "dt_max", "zeta", "u0_rtol", "u0_atol"):
+        if name in op:
+            setattr(o, name, float(op[name]))
+    for name in ("newton_maxit", "gmres_restart", "gmres_maxit", "overlap", "ilu_reuse", "zeta_persist",
+                 "max_retries", "u0_maxit"):
+        if name in op:
+            setattr(o, name, int(op[name]))
+    if "sub" in op:
+        sub = list(op["sub"]) + [1] * (3 - len(op["sub"]))
+        for J in range(3):
+            o.sub[J] = int(sub[J])
+    if "dt_mode" in op:
+        o.dt_mode = DT_MODES[op["dt_mode"]] if isinstance(op["dt_mode"], str) else int(op["dt_mode"])
+    if "precision" in op:
+        o.precision = {"fp64": NKS_FP64, "mixed": NKS_MIXED}.get(op["precision"], op["precision"])
+    o.timing = 1 if timing else 0
+    return o
+
+
+def last_error(p=None):
+    m = load().nks_last_error(p)
+    return m.decode() if m else ""
+
+
+def _check(rc, p=None):
+    if rc != NKS_OK:
+        raise NksError(rc, last_error(p))
+    return rc
+
+
+class Problem:
+    """One simulation resident on the current CUDA device (``nks_problem``)."""
+
+    def __init__(self, dim, n, h, c, eta, coeffs: dict, opts: dict, stream=None, allocator=None, timing=False):
+        L = load()
+        self.dim, self.n = dim, tuple(n[:dim])
+        self.N = int(np.prod(self.n))
+        self._grid = make_grid(dim, n, h)
+        self._coeffs = make_coeffs(coeffs)
+        self._opts = make_opts(opts, timing)
+        elastic = any(coeffs[k] != 0.0 for k in ("C11", "C12", "C44")) and coeffs.get("Lscale", 1.0) != 0.0
+        self.nf = 2 + (dim if elastic else 0)
+        c, eta = _c64(c), _c64(eta)
+        assert c.size == self.N and eta.size == self.N
+        self._alloc = allocator
+        handle = ctypes.c_void_p()
+        rc = L.nks_create_problem(ctypes.byref(self._grid), _ptr(c), _ptr(eta), ctypes.byref(self._coeffs),
+                                  ctypes.byref(self._opts), ctypes.byref(allocator) if allocator else None,
+                                  ctypes.c_void_p(stream) if stream else None, ctypes.byref(handle))
+        _check(rc, None)
+        self._h = handle
+
+    def __del__(self):
+        self.destroy()
+
+    def destroy(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            load().nks_destroy(h)
+            self._h = None
+
+    # -- the time step
+    def step(self, dt=0.0):
+        info = nks_step_info()
+        rc = load().nks_step(self._h, float(dt), ctypes.byref(info))
+        _check(rc, self._h)
+        return info.as_dict()
+
+    def energy(self):
+        v = ctypes.c_double()
+        _check(load().nks_energy(self._h, ctypes.byref(v)), self._h)
+        return v.value
+
+    def mass(self):
+        v = ctypes.c_double()
+        _check(load().nks_mass(self._h, ctypes.byref(v)), self._h)
+        return v.value
+
+    def get_fields(self):
+        c, eta = np.empty(self.N), np.empty(self.N)
+        u = np.empty((self.nf - 2, self.N)) if self.nf > 2 else None
+        _check(load().nks_get_fields(self._h, _ptr(c), _ptr(eta), _ptr(u) if u is not None else None), self._h)
+        return c, eta, u
+
+    def get_state(self) -> bytes:
+        L = load()
+        n = L.nks_state_size(self._h)
+        buf = ctypes.create_string_buffer(n)
+        _check(L.nks_get_state(self._h, buf, n), self._h)
+        return buf.raw
+
+    def set_state(self, blob: bytes):
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        _check(load().nks_set_state(self._h, buf, len(blob)), self._h)
+
+    def get_stats(self):
+        s = nks_stats()
+        _check(load().nks_get_stats(self._h, ctypes.byref(s)), self._h)
+        return s.as_dict()
+
+    def reset_stats(self):
+        _check(load().nks_reset_stats(self._h), self._h)
+
+    # -- operator-level entry points (state arrays: fields one after another)
+    def eval_residual(self, X1, X0, dt, mode=0):
+        X1, X0 = _c64(X1), _c64(X0)
+        F = np.empty(self.nf * self.N)
+        _check(load().nks_eval_residual(self._h, _ptr(X1), _ptr(X0), float(dt), int(mode), _ptr(F)), self._h)
+        return F
+
+    def apply_jacobian(self, X1, X0, dt, v, mode=0):
+        X1, X0, v = _c64(X1), _c64(X0), _c64(v)
+        out = np.empty(self.nf * self.N)
+        _check(load().nks_apply_jacobian(self._h, _ptr(X1), _ptr(X0), float(dt), int(mode), _ptr(v), _ptr(out)),
+               self._h)
+        return out
+
+    def apply_preconditioner(self, X1, X0, dt, r):
+        X1, X0, r = _c64(X1), _c64(X0), _c64(r)
+        z = np.empty(self.nf * self.N)
+        _check(load().nks_apply_preconditioner(self._h, _ptr(X1), _ptr(X0), float(dt), _ptr(r), _ptr(z)), self._h)
+        return z
+
+    def linear_solve(self, X1, X0, dt, b, tol, mode=0):
+        X1, X0, b = _c64(X1), _c64(X0), _c64(b)
+        x = np.empty(self.nf * self.N)
+        its, res = ctypes.c_int(), ctypes.c_double()
+        _check(load().nks_linear_solve(self._h, _ptr(X1), _ptr(X0), float(dt), int(mode), _ptr(b), _ptr(x),
+                                       float(tol), ctypes.byref(its), ctypes.byref(res)), self._h)
+        return x, its.value, res.value
+
+    def eval_energy(self, X):
+        X = _c64(X)
+        parts, mass = np.empty(5), ctypes.c_double()
+        _check(load().nks_eval_energy(self._h, _ptr(X), _ptr(parts), ctypes.byref(mass)), self._h)
+        return parts, mass.value
+
+
+def torch_allocator():
+    """An nks_allocator backed by PyTorch's caching allocator on the current device."""
+    import torch
+
+    def _alloc(nbytes, ctx):
+        return torch.cuda.caching_allocator_alloc(int(nbytes))
+
+    def _free(ptr, ctx):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    a = nks_allocator()
+    a.alloc = ALLOC_FN(_alloc)
+    a.free = FREE_FN(_free)
+    a.ctx = None
+    a._keep = (a.alloc, a.free)
+    return a

@@ -1,0 +1,204 @@
+// nks_internal.cuh -- shared declarations of the GB300 NKS solver.
+//
+// Layout in HBM: every state vector is structure-of-arrays, field-major:
+//   X[f * N + p],  f = 0 (c), 1 (eta), 2.. (u_1..u_d),  p = x + nx (y + ny z).
+// One Newton iterate therefore streams nf contiguous, coalesced planes.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "nks.h"
+
+namespace nks {
+
+constexpr int kRedBlocks = 304;    // 2 x 152 SMs: fixed reduction grid (deterministic sums)
+constexpr int kRedThreads = 256;
+constexpr int kMaxNf = 5;          // c, eta, u_1..u_3
+constexpr int kMaxRow = 72;        // longest Jacobian row: 71 entries (3-D c-row)
+constexpr int kMaxRestart = 64;
+
+// Grid as seen by the kernels.
+struct DGrid {
+    int dim;
+    int n[3];
+    long long N;
+    double h;
+};
+
+// Coefficients after the App. B reduction to the polynomial coefficients M_k.
+struct DCoef {
+    double kappa, gamma_c, gamma_eta, theta, w_psi;
+    double M0, m1a, m1b, m2a, m2b, m2c, M3, M4;  // M1 = m1a + m1b phi^2, M2 = m2a + m2b phi^2 + m2c phi^3
+    double U1, U4;                               // M5(c), M6(c)
+    double eps0, C11, C12, C44, lam;             // lam = C11 + (d - 1) C12
+    double L[4], dE0;                            // App. A, for the energy E1
+    double cbar0;                                // initial mean composition (Sec. 3)
+    double ser_c[16];                            // 1/(2k(2k+1)), k = 1..S-1  (Psi_S series)
+    double ser_e[16];                            // 1/(2k+1)
+    int S;
+    int elastic;
+    int nf;
+};
+
+// ---------------------------------------------------------------------------
+// index helpers
+// ---------------------------------------------------------------------------
+
+__host__ __device__ inline int wrapi(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+
+__host__ __device__ inline void coords_of(const DGrid &g, long long p, int &x, int &y, int &z)
+{
+    x = (int)(p % g.n[0]);
+    long long q = p / g.n[0];
+    y = (int)(q % g.n[1]);
+    z = (int)(q / g.n[1]);
+}
+
+__host__ __device__ inline long long index_of(const DGrid &g, int x, int y, int z)
+{
+    return (long long)x + (long long)g.n[0] * ((long long)y + (long long)g.n[1] * z);
+}
+
+// neighbour of (x, y, z) shifted by (dx, dy, dz), periodic (|shift| < n)
+__host__ __device__ inline long long nbr_of(const DGrid &g, int x, int y, int z, int dx, int dy, int dz)
+{
+    return index_of(g, wrapi(x + dx, g.n[0]), wrapi(y + dy, g.n[1]), wrapi(z + dz, g.n[2]));
+}
+
+__device__ inline long long nbrJ(const DGrid &g, int x, int y, int z, int J, int s)
+{
+    return nbr_of(g, x, y, z, J == 0 ? s : 0, J == 1 ? s : 0, J == 2 ? s : 0);
+}
+
+// ---------------------------------------------------------------------------
+// deterministic block reduction of K values (fixed tree, fixed grid)
+// ---------------------------------------------------------------------------
+
+template <int K>
+__device__ inline void block_reduce_store(double (&v)[K], double *partials /* [gridDim.x][K] */)
+{
+    __shared__ double red[K][kRedThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        double a = v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        if (lane == 0) red[k][warp] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x < K) {
+        double a = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) a += red[threadIdx.x][w];
+        partials[(size_t)blockIdx.x * K + threadIdx.x] = a;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// stencil / reduction kernels (nks_stencil.cu)
+// ---------------------------------------------------------------------------
+
+void launch_mobility(const DGrid &g, const DCoef &k, const double *c0, double *mob, cudaStream_t st);
+void launch_trace0(const DGrid &g, const DCoef &k, const double *X0, double *tr0, cudaStream_t st);
+void launch_residual(const DGrid &g, const DCoef &k, double dt, int mode, const double *X1, const double *X0,
+                     const double *tr0, const double *mob, double *Gc, double *sig, double *part, double *F,
+                     int *flag, double *partials, cudaStream_t st);
+void launch_jv(const DGrid &g, const DCoef &k, double dt, int mode, const double *part, const double *mob,
+               const double *v, double *dG, double *sig, double *Jv, cudaStream_t st);
+void launch_energy(const DGrid &g, const DCoef &k, const double *X, double *partials, cudaStream_t st);
+void launch_finalize(const double *partials, int nblocks, int K, double *out, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// vector kernels (nks_krylov.cu)
+// ---------------------------------------------------------------------------
+
+void launch_axpby(long long n, double a, const double *x, double b, double *y, cudaStream_t st);   // y = a x + b y
+void launch_waxpy(long long n, const double *x, double a, const double *y, double *w, cudaStream_t st); // w = x + a y
+void launch_scale_dev(long long n, const double *src, const double *inv_norm, double *dst, cudaStream_t st);
+void launch_dot2(long long n, const double *x, const double *y, double *partials, cudaStream_t st); // x.y, y.y
+
+// GMRES(m) with right preconditioning; see nks_krylov.cu.
+struct Problem;
+int gmres_solve(Problem *P, int mode, const double *b, double *x, double tol, int *its, double *res);
+
+// ---------------------------------------------------------------------------
+// restricted additive Schwarz (nks_ras.cu)
+// ---------------------------------------------------------------------------
+
+struct RasPlan;
+int ras_plan_create(Problem *P, std::string &err);
+void ras_plan_destroy(Problem *P);
+int ras_factor(Problem *P, int mode);                              // assemble J restricted + ILU(0)
+void ras_apply(Problem *P, const double *r, double *z);           // z = P RAS^-1 r
+void project(Problem *P, double *z);
+
+// ---------------------------------------------------------------------------
+// problem object (nks_api.cu)
+// ---------------------------------------------------------------------------
+
+struct Timer {
+    cudaEvent_t a = nullptr, b = nullptr;
+};
+
+struct Problem {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    nks_allocator alloc{};
+    bool have_alloc = false;
+    std::vector<void *> allocations;
+
+    nks_grid grid{};
+    nks_coeffs coeffs{};
+    nks_opts opts{};
+    DGrid g{};
+    DCoef k{};
+    int nf = 2;
+    long long N = 0, nvec = 0;
+
+    // state
+    double *Xn = nullptr, *Xprev = nullptr, *X = nullptr, *Xt = nullptr;
+    double *F = nullptr, *Ft = nullptr, *S = nullptr, *B = nullptr;
+    double *part = nullptr, *part_t = nullptr;  // 4 N: pointwise derivatives of G^1 + G^2 at X / Xt
+    double *mob = nullptr;                      // d N edge mobilities at level n
+    double *tr0 = nullptr;                      // N: trace of eps^el at level n
+    double *Gc = nullptr, *sig = nullptr;       // residual / Jv temporaries
+    double *partials = nullptr;                 // kRedBlocks * 64
+    double *dscal = nullptr;                    // small device scalars
+    double *hscal = nullptr;                    // pinned host mirror
+    int *dflag = nullptr;
+
+    // Krylov workspace
+    double *V = nullptr;                        // (m + 1) nvec
+    double *W = nullptr, *Z = nullptr, *R = nullptr;
+    double *gm = nullptr;                       // device GMRES small state
+
+    RasPlan *ras = nullptr;
+    bool factored = false;
+
+    double cur_dt = 1.0;                        // dt of the system being solved
+    int cur_mode = 0;                           // 0 full system, 1 displacement only
+
+    // time stepping
+    double t = 0.0, dt_prev = 0.0, zeta = 0.0, E = 0.0, Eprev = 0.0;
+    long long nstep = 0;
+    double cbar0 = 0.0;
+
+    nks_stats stats{};
+    std::vector<Timer> timers[NKS_NCLASS];
+    std::string err;
+
+    void *dalloc(size_t bytes);
+    void dfree_all();
+    void tick(int cls);                         // count a launch of class cls (and start a timer)
+    void tock(int cls);                         // stop its timer
+    int sync_check(const char *where);
+};
+
+int cuda_fail(Problem *P, cudaError_t e, const char *where);
+
+}  // namespace nks

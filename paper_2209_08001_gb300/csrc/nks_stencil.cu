@@ -1,0 +1,454 @@
+// nks_stencil.cu -- DVD residual, Jacobian action and energy/mass reductions.
+//
+// The residual of the scheme NSOA-1 (Sec. 3) is evaluated in two passes so
+// that the expensive pointwise part (three Psi_S series with logarithms,
+// App. B polynomials, FP64) runs once per point:
+//   pass A: G_c = G^1_c + G^{2,S}_c + G^3_c + G^4_c and G_eta at each point,
+//           F_eta = (eta1 - eta0)/dt + G_eta, the four pointwise derivatives
+//           of G^1 + G^{2,S} (reused by the Jacobian action), and the stress
+//           sigma(eps^el(u1, c1)) at each point;
+//   pass B: F_c = (c1 - c0)/dt - D M D G_c (flux form with level-n edge
+//           mobilities) and F_u = sum_J Dhat_J sigma_IJ, plus ||F||^2 partials.
+// The Jacobian action J v uses the same two passes on the linearisation.
+#include <math.h>
+
+#include "nks_internal.cuh"
+
+namespace nks {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline int blocks_for(long long n, int threads = kThreads)
+{
+    long long b = (n + threads - 1) / threads;
+    return (int)(b < 1 ? 1 : b);
+}
+
+// index of the stress component (I, J), I <= J, in the packed array
+__host__ __device__ inline int scomp(int d, int I, int J)
+{
+    if (I > J) {
+        int t = I;
+        I = J;
+        J = t;
+    }
+    if (I == J) return I;
+    // off-diagonals after the d diagonal entries: (0,1), (0,2), (1,2)
+    return d + (I == 0 ? J - 1 : 2);
+}
+
+// Psi_S[y1, y0] of Sec. 3 and its derivative in y1.  With ybar = (y1 + y0)/2,
+// delta = (y0 - y1)/2, a = delta/(1 - ybar), b = delta/ybar:
+//   Psi_S = ln(ybar/(1 - ybar)) + sum_{k=1}^{S-1} (a^2k - b^2k) / (2k(2k+1))
+//   dPsi_S/dy1 = 1/2 [1/ybar + 1/(1-ybar) + sum_k (a^2k/(1-ybar) + b^2k/ybar)/(2k+1)]
+//              - 1/2 [sum_k (a^(2k-1)/(1-ybar) - b^(2k-1)/ybar)/(2k+1)]
+// Series by Horner in a^2, b^2 with the coefficient tables of DCoef.
+__device__ inline void psiS_d1(const DCoef &k, double y1, double y0, double &q, double &d1)
+{
+    const double yb = 0.5 * (y1 + y0), de = 0.5 * (y0 - y1);
+    const double iy = 1.0 / yb, iz = 1.0 / (1.0 - yb);
+    const double a = de * iz, b = de * iy;
+    const double A = a * a, B = b * b;
+    double sAc = 0.0, sBc = 0.0, tAe = 0.0, tBe = 0.0;
+    for (int kk = k.S - 1; kk >= 1; kk--) {
+        sAc = (sAc + k.ser_c[kk]) * A;
+        sBc = (sBc + k.ser_c[kk]) * B;
+        tAe = tAe * A + k.ser_e[kk];
+        tBe = tBe * B + k.ser_e[kk];
+    }
+    q = log(yb * iz) + (sAc - sBc);
+    d1 = 0.5 * (iy + iz + iz * A * tAe + iy * B * tBe) - 0.5 * (iz * a * tAe - iy * b * tBe);
+}
+
+struct PointG {
+    double gc, ge;              // G^1 + G^{2,S}
+    double dcc, dce, dec, dee;  // d(G_c, G_eta)/d(c1, eta1)
+};
+
+// G^1 (App. B, polynomial part) + G^{2,S} (Eq. D2-1) at one point, with derivatives.
+__device__ inline PointG pointG(const DCoef &k, double c1, double e1, double c0, double e0)
+{
+    PointG r;
+    const double f1 = 1.0 - e1, f0 = 1.0 - e0;
+    const double ch = 0.5 * (c1 + c0), fh = 0.5 * (f1 + f0), eh = 0.5 * (e1 + e0);
+    // App. B: M1(phi) = m1a + m1b phi^2, M2(phi) = m2a + m2b phi^2 + m2c phi^3
+    const double M1_0 = k.m1a + k.m1b * f0 * f0, M1_1 = k.m1a + k.m1b * f1 * f1;
+    const double M2_0 = k.m2a + f0 * f0 * (k.m2b + k.m2c * f0), M2_1 = k.m2a + f1 * f1 * (k.m2b + k.m2c * f1);
+    const double c1s = c1 * c1, c0s = c0 * c0, c10 = c1 * c0;
+    const double Q3 = c1s + c10 + c0s;
+    const double Q4 = (c1 + c0) * (c1s + c0s);
+    const double Q5 = c1s * c1s + c1s * c10 + c10 * c10 + c10 * c0s + c0s * c0s;
+    const double gc1 = 0.5 * (M1_0 + M1_1) * ch + (M2_0 + M2_1) * (1.0 / 6.0) * Q3 + 0.25 * k.M3 * Q4 +
+                       0.2 * k.M4 * Q5 + k.M0;
+    // M5(c) = -(24 U1 c^2 + 72 U4 (1 - 2c) c^2), M6(c) = 144 U4 c^3
+    const double M5_0 = -c0s * (24.0 * k.U1 + 72.0 * k.U4 * (1.0 - 2.0 * c0));
+    const double M5_1 = -c1s * (24.0 * k.U1 + 72.0 * k.U4 * (1.0 - 2.0 * c1));
+    const double M6_0 = 144.0 * k.U4 * c0s * c0, M6_1 = 144.0 * k.U4 * c1s * c1;
+    const double P3 = f1 * f1 + f1 * f0 + f0 * f0;
+    const double ge1 = 0.5 * (M5_0 + M5_1) * fh + (M6_0 + M6_1) * (1.0 / 6.0) * P3;
+    // derivatives of G^1
+    const double g1c_c = 0.25 * (M1_0 + M1_1) + (M2_0 + M2_1) * (1.0 / 6.0) * (2.0 * c1 + c0) +
+                         0.25 * k.M3 * (3.0 * c1s + 2.0 * c10 + c0s) +
+                         0.2 * k.M4 * (4.0 * c1s * c1 + 3.0 * c1s * c0 + 2.0 * c1 * c0s + c0s * c0);
+    const double g1c_e = -(k.m1b * f1 * ch + (2.0 * k.m2b * f1 + 3.0 * k.m2c * f1 * f1) * (1.0 / 6.0) * Q3);
+    const double dM5 = -(48.0 * k.U1 * c1 + 72.0 * k.U4 * (2.0 * c1 - 6.0 * c1s));
+    const double dM6 = 432.0 * k.U4 * c1s;
+    const double g1e_c = 0.5 * dM5 * fh + dM6 * (1.0 / 6.0) * P3;
+    const double g1e_e = -(0.25 * (M5_0 + M5_1) + (M6_0 + M6_1) * (1.0 / 6.0) * (2.0 * f1 + f0));
+    // G^{2,S}: p = c eta, q = c (4 - 3 eta)
+    const double p1 = c1 * e1, p0 = c0 * e0;
+    const double q1 = c1 * (4.0 - 3.0 * e1), q0 = c0 * (4.0 - 3.0 * e0);
+    double Qc = 0.0, Dc = 0.0, Qp, Dp, Qq, Dq;
+    if (k.w_psi != 0.0) psiS_d1(k, c1, c0, Qc, Dc);
+    psiS_d1(k, p1, p0, Qp, Dp);
+    psiS_d1(k, q1, q0, Qq, Dq);
+    const double t4 = 0.25 * k.theta;
+    const double eph = 4.0 - 3.0 * eh;
+    const double gc2 = t4 * (4.0 * k.w_psi * Qc + 3.0 * eh * Qp + eph * Qq);
+    const double ge2 = t4 * 3.0 * ch * (Qp - Qq);
+    const double g2c_c = t4 * (4.0 * k.w_psi * Dc + 3.0 * eh * e1 * Dp + eph * (4.0 - 3.0 * e1) * Dq);
+    const double g2c_e = t4 * (1.5 * (Qp - Qq) + 3.0 * c1 * (eh * Dp - eph * Dq));
+    const double g2e_c = t4 * 3.0 * (0.5 * (Qp - Qq) + ch * (e1 * Dp - (4.0 - 3.0 * e1) * Dq));
+    const double g2e_e = t4 * 3.0 * ch * c1 * (Dp + 3.0 * Dq);
+    r.gc = gc1 + gc2;
+    r.ge = ge1 + ge2;
+    r.dcc = g1c_c + g2c_c;
+    r.dce = g1c_e + g2c_e;
+    r.dec = g1e_c + g2e_c;
+    r.dee = g1e_e + g2e_e;
+    return r;
+}
+
+__device__ inline bool in_domain(double c, double e)
+{
+    const double p = c * e, q = c * (4.0 - 3.0 * e);
+    return c > 0.0 && c < 1.0 && p > 0.0 && p < 1.0 && q > 0.0 && q < 1.0;
+}
+
+// symmetric gradient of the displacement at (x, y, z): Du[I][J] = Dhat_J u_I
+__device__ inline void grad_u(const DGrid &g, const double *U /* field 2 plane */, int x, int y, int z,
+                              double (&Du)[3][3])
+{
+    const double i2h = 0.5 / g.h;
+    for (int I = 0; I < g.dim; I++)
+        for (int J = 0; J < g.dim; J++)
+            Du[I][J] = (U[I * g.N + nbrJ(g, x, y, z, J, +1)] - U[I * g.N + nbrJ(g, x, y, z, J, -1)]) * i2h;
+}
+
+// sigma = C : (sym(Du) - s I) for the cubic Hooke law, packed by scomp()
+__device__ inline void hooke_packed(const DGrid &g, const DCoef &k, const double (&Du)[3][3], double s,
+                                    double *sig, long long p)
+{
+    const int d = g.dim;
+    double tr = 0.0;
+    for (int I = 0; I < d; I++) tr += Du[I][I] - s;
+    for (int I = 0; I < d; I++) {
+        const double eII = Du[I][I] - s;
+        sig[(long long)I * g.N + p] = k.C11 * eII + k.C12 * (tr - eII);
+        for (int J = I + 1; J < d; J++)
+            sig[(long long)scomp(d, I, J) * g.N + p] = k.C44 * (Du[I][J] + Du[J][I]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+
+__global__ void k_mobility(DGrid g, DCoef k, const double *__restrict__ c0, double *__restrict__ mob)
+{
+    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= g.N) return;
+    int x, y, z;
+    coords_of(g, p, x, y, z);
+    const double a = c0[p] * (1.0 - c0[p]);
+    for (int J = 0; J < g.dim; J++) {
+        const double cb = c0[nbrJ(g, x, y, z, J, +1)];
+        mob[J * g.N + p] = k.kappa * 0.5 * (a + cb * (1.0 - cb));  // M_{p + e_J/2} (Sec. 3)
+    }
+}
+
+// tr eps^el of the level-n state (used by G^3 at n + 1/2)
+__global__ void k_trace0(DGrid g, DCoef k, const double *__restrict__ X0, double *__restrict__ tr0)
+{
+    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= g.N) return;
+    int x, y, z;
+    coords_of(g, p, x, y, z);
+    const double *U = X0 + 2 * g.N;
+    double tr = 0.0;
+    for (int K = 0; K < g.dim; K++)
+        tr += (U[K * g.N + nbrJ(g, x, y, z, K, +1)] - U[K * g.N + nbrJ(g, x, y, z, K, -1)]) * (0.5 / g.h);
+    tr0[p] = tr - g.dim * k.eps0 * (X0[p] - k.cbar0);
+}
+
+__global__ void k_res_a(DGrid g, DCoef k, double dt, int mode, const double *__restrict__ X1,
+                        const double *__restrict__ X0, const double *__restrict__ tr0, double *__restrict__ Gc,
+                        double *__restrict__ sig, double *__restrict__ part, double *__restrict__ F,
+                        int *__restrict__ flag)
+{
+    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= g.N) return;
+    int x, y, z;
+    coords_of(g, p, x, y, z);
+    const long long N = g.N;
+    const double c1 = X1[p], e1 = X1[N + p];
+    if (!in_domain(c1, e1)) atomicOr(flag, 1);
+    double Du[3][3];
+    if (k.elastic) {
+        grad_u(g, X1 + 2 * N, x, y, z, Du);
+        hooke_packed(g, k, Du, k.eps0 * (c1 - k.cbar0), sig, p);
+    }
+    if (mode != 0) {
+        F[N + p] = 0.0;
+        return;
+    }
+    const double c0 = X0[p], e0 = X0[N + p];
+    PointG G = pointG(k, c1, e1, c0, e0);
+    double gc = G.gc, ge = G.ge;
+    if (k.elastic) {
+        // G^3_c = -eps0 sum_I sigma_II(eps^el_{n+1/2}) = -eps0 lam (tr1 + tr0)/2
+        double tr1 = -g.dim * k.eps0 * (c1 - k.cbar0);
+        for (int K = 0; K < g.dim; K++) tr1 += Du[K][K];
+        gc += -k.eps0 * k.lam * 0.5 * (tr1 + tr0[p]);
+    }
+    // G^4 = (-gamma_c D^2 c_h, -3 gamma_eta D^2 eta_h), D^2 = sum_J D+_J D-_J
+    const double ih2 = 1.0 / (g.h * g.h);
+    double lc = 0.0, le = 0.0;
+    const double chp = c1 + c0, ehp = e1 + e0;
+    for (int J = 0; J < g.dim; J++) {
+        const long long pp = nbrJ(g, x, y, z, J, +1), pm = nbrJ(g, x, y, z, J, -1);
+        lc += (X1[pp] + X0[pp]) + (X1[pm] + X0[pm]) - 2.0 * chp;
+        le += (X1[N + pp] + X0[N + pp]) + (X1[N + pm] + X0[N + pm]) - 2.0 * ehp;
+    }
+    gc += -k.gamma_c * 0.5 * lc * ih2;
+    ge += -3.0 * k.gamma_eta * 0.5 * le * ih2;
+    Gc[p] = gc;
+    F[N + p] = (e1 - e0) / dt + ge;
+    part[p] = G.dcc;
+    part[N + p] = G.dce;
+    part[2 * N + p] = G.dec;
+    part[3 * N + p] = G.dee;
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_res_b(DGrid g, DCoef k, double dt, int mode,
+                                                       const double *__restrict__ X1, const double *__restrict__ X0,
+                                                       const double *__restrict__ Gc, const double *__restrict__ mob,
+                                                       const double *__restrict__ sig, double *__restrict__ F,
+                                                       double *__restrict__ partials)
+{
+    const long long N = g.N;
+    const double ih2 = 1.0 / (g.h * g.h), i2h = 0.5 / g.h;
+    double acc[1] = {0.0};
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
+         p += (long long)gridDim.x * blockDim.x) {
+        int x, y, z;
+        coords_of(g, p, x, y, z);
+        double fc = 0.0;
+        if (mode == 0) {
+            double flux = 0.0;
+            const double G0 = Gc[p];
+            for (int J = 0; J < g.dim; J++) {
+                const long long pp = nbrJ(g, x, y, z, J, +1), pm = nbrJ(g, x, y, z, J, -1);
+                flux += mob[J * N + p] * (Gc[pp] - G0) - mob[J * N + pm] * (G0 - Gc[pm]);
+            }
+            fc = (X1[p] - X0[p]) / dt - flux * ih2;
+        }
+        F[p] = fc;
+        const double fe = F[N + p];
+        double s = fc * fc + fe * fe;
+        if (k.elastic) {
+            for (int I = 0; I < g.dim; I++) {
+                double div = 0.0;
+                for (int J = 0; J < g.dim; J++) {
+                    const int cmp = scomp(g.dim, I, J);
+                    div += (sig[cmp * N + nbrJ(g, x, y, z, J, +1)] - sig[cmp * N + nbrJ(g, x, y, z, J, -1)]) * i2h;
+                }
+                F[(2 + I) * N + p] = div;
+                s += div * div;
+            }
+        }
+        acc[0] += s;
+    }
+    block_reduce_store<1>(acc, partials);
+}
+
+// Jacobian action, pass A: dG_c (linearised G_c), (J v)_eta, sigma(eps(v_u) - eps0 v_c I)
+__global__ void k_jv_a(DGrid g, DCoef k, double dt, int mode, const double *__restrict__ part,
+                       const double *__restrict__ v, double *__restrict__ dG, double *__restrict__ sig,
+                       double *__restrict__ Jv)
+{
+    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= g.N) return;
+    int x, y, z;
+    coords_of(g, p, x, y, z);
+    const long long N = g.N;
+    const double vc = v[p], ve = v[N + p];
+    double Du[3][3];
+    double trv = 0.0;
+    if (k.elastic) {
+        grad_u(g, v + 2 * N, x, y, z, Du);
+        hooke_packed(g, k, Du, k.eps0 * vc, sig, p);
+        for (int K = 0; K < g.dim; K++) trv += Du[K][K];
+    }
+    if (mode != 0) {
+        Jv[N + p] = ve;
+        return;
+    }
+    const double ih2 = 1.0 / (g.h * g.h);
+    double lc = 0.0, le = 0.0;
+    for (int J = 0; J < g.dim; J++) {
+        const long long pp = nbrJ(g, x, y, z, J, +1), pm = nbrJ(g, x, y, z, J, -1);
+        lc += v[pp] + v[pm] - 2.0 * vc;
+        le += v[N + pp] + v[N + pm] - 2.0 * ve;
+    }
+    double dg = part[p] * vc + part[N + p] * ve - 0.5 * k.gamma_c * lc * ih2;
+    if (k.elastic) dg += -0.5 * k.eps0 * k.lam * (trv - g.dim * k.eps0 * vc);
+    dG[p] = dg;
+    Jv[N + p] = ve / dt + part[2 * N + p] * vc + part[3 * N + p] * ve - 1.5 * k.gamma_eta * le * ih2;
+}
+
+// Jacobian action, pass B: (J v)_c = v_c/dt - D M D dG_c, (J v)_u = sum_J Dhat_J sigma(v)_IJ
+__global__ void k_jv_b(DGrid g, DCoef k, double dt, int mode, const double *__restrict__ mob,
+                       const double *__restrict__ v, const double *__restrict__ dG, const double *__restrict__ sig,
+                       double *__restrict__ Jv)
+{
+    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= g.N) return;
+    int x, y, z;
+    coords_of(g, p, x, y, z);
+    const long long N = g.N;
+    if (mode == 0) {
+        const double ih2 = 1.0 / (g.h * g.h);
+        double flux = 0.0;
+        const double G0 = dG[p];
+        for (int J = 0; J < g.dim; J++) {
+            const long long pp = nbrJ(g, x, y, z, J, +1), pm = nbrJ(g, x, y, z, J, -1);
+            flux += mob[J * N + p] * (dG[pp] - G0) - mob[J * N + pm] * (G0 - dG[pm]);
+        }
+        Jv[p] = v[p] / dt - flux * ih2;
+    } else {
+        Jv[p] = v[p];
+    }
+    if (k.elastic) {
+        const double i2h = 0.5 / g.h;
+        for (int I = 0; I < g.dim; I++) {
+            double div = 0.0;
+            for (int J = 0; J < g.dim; J++) {
+                const int cmp = scomp(g.dim, I, J);
+                div += (sig[cmp * N + nbrJ(g, x, y, z, J, +1)] - sig[cmp * N + nbrJ(g, x, y, z, J, -1)]) * i2h;
+            }
+            Jv[(2 + I) * N + p] = div;
+        }
+    }
+}
+
+__device__ inline double Psi(double z) { return z * log(z) + (1.0 - z) * log1p(-z); }
+
+// energy parts e1..e4 (Eq. relations) and mass, per-block partial sums
+__global__ void __launch_bounds__(kRedThreads) k_energy(DGrid g, DCoef k, const double *__restrict__ X,
+                                                        double *__restrict__ partials)
+{
+    const long long N = g.N;
+    const double ih = 1.0 / g.h;
+    double acc[5] = {0, 0, 0, 0, 0};
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
+         p += (long long)gridDim.x * blockDim.x) {
+        int x, y, z;
+        coords_of(g, p, x, y, z);
+        const double c = X[p], e = X[N + p], f = 1.0 - e;
+        // E1 = Phi(c, phi): App. A with one order parameter
+        const double s = 2.0 * c - 1.0;
+        const double ex = c * (1.0 - c) * (k.L[0] + s * (k.L[1] + s * (k.L[2] + s * k.L[3])));
+        const double e1 = k.dE0 * c + ex + 12.0 * k.U1 * c * c * f * f + 36.0 * k.U4 * (1.0 - 2.0 * c) * c * c * f * f -
+                          48.0 * k.U4 * c * c * c * f * f * f;
+        const double e2 = k.theta * (k.w_psi * Psi(c) + 0.75 * Psi(c * e) + 0.25 * Psi(c * (4.0 - 3.0 * e)));
+        double e3 = 0.0;
+        if (k.elastic) {
+            double Du[3][3];
+            grad_u(g, X + 2 * N, x, y, z, Du);
+            const double s0 = k.eps0 * (c - k.cbar0);
+            double tr = 0.0, sq = 0.0, off = 0.0;
+            for (int I = 0; I < g.dim; I++) {
+                const double eII = Du[I][I] - s0;
+                tr += eII;
+                sq += eII * eII;
+                for (int J = I + 1; J < g.dim; J++) {
+                    const double eIJ = 0.5 * (Du[I][J] + Du[J][I]);
+                    off += eIJ * eIJ;
+                }
+            }
+            e3 = 0.5 * (k.C12 * tr * tr + (k.C11 - k.C12) * sq + 4.0 * k.C44 * off);
+        }
+        double gc = 0.0, ge = 0.0;
+        for (int J = 0; J < g.dim; J++) {
+            const long long pp = nbrJ(g, x, y, z, J, +1), pm = nbrJ(g, x, y, z, J, -1);
+            const double dpc = (X[pp] - c) * ih, dmc = (c - X[pm]) * ih;
+            const double dpe = (X[N + pp] - e) * ih, dme = (e - X[N + pm]) * ih;
+            gc += 0.5 * (dpc * dpc + dmc * dmc);
+            ge += 0.5 * (dpe * dpe + dme * dme);
+        }
+        acc[0] += e1;
+        acc[1] += e2;
+        acc[2] += e3;
+        acc[3] += 0.5 * k.gamma_c * gc + 1.5 * k.gamma_eta * ge;
+        acc[4] += c;
+    }
+    block_reduce_store<5>(acc, partials);
+}
+
+// sums K columns of nblocks partial rows in a fixed order (one block)
+__global__ void k_finalize(const double *__restrict__ partials, int nblocks, int K, double *__restrict__ out)
+{
+    __shared__ double red[kRedThreads];
+    for (int kk = 0; kk < K; kk++) {
+        double a = 0.0;
+        for (int b = threadIdx.x; b < nblocks; b += blockDim.x) a += partials[(size_t)b * K + kk];
+        red[threadIdx.x] = a;
+        __syncthreads();
+        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+            if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[kk] = red[0];
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+void launch_mobility(const DGrid &g, const DCoef &k, const double *c0, double *mob, cudaStream_t st)
+{
+    k_mobility<<<blocks_for(g.N), kThreads, 0, st>>>(g, k, c0, mob);
+}
+
+void launch_trace0(const DGrid &g, const DCoef &k, const double *X0, double *tr0, cudaStream_t st)
+{
+    k_trace0<<<blocks_for(g.N), kThreads, 0, st>>>(g, k, X0, tr0);
+}
+
+void launch_residual(const DGrid &g, const DCoef &k, double dt, int mode, const double *X1, const double *X0,
+                     const double *tr0, const double *mob, double *Gc, double *sig, double *part, double *F, int *flag,
+                     double *partials, cudaStream_t st)
+{
+    k_res_a<<<blocks_for(g.N), kThreads, 0, st>>>(g, k, dt, mode, X1, X0, tr0, Gc, sig, part, F, flag);
+    k_res_b<<<kRedBlocks, kRedThreads, 0, st>>>(g, k, dt, mode, X1, X0, Gc, mob, sig, F, partials);
+}
+
+void launch_jv(const DGrid &g, const DCoef &k, double dt, int mode, const double *part, const double *mob,
+               const double *v, double *dG, double *sig, double *Jv, cudaStream_t st)
+{
+    k_jv_a<<<blocks_for(g.N), kThreads, 0, st>>>(g, k, dt, mode, part, v, dG, sig, Jv);
+    k_jv_b<<<blocks_for(g.N), kThreads, 0, st>>>(g, k, dt, mode, mob, v, dG, sig, Jv);
+}
+
+void launch_energy(const DGrid &g, const DCoef &k, const double *X, double *partials, cudaStream_t st)
+{
+    k_energy<<<kRedBlocks, kRedThreads, 0, st>>>(g, k, X, partials);
+}
+
+void launch_finalize(const double *partials, int nblocks, int K, double *out, cudaStream_t st)
+{
+    k_finalize<<<1, kRedThreads, 0, st>>>(partials, nblocks, K, out);
+}
+
+}  // namespace nks

@@ -1,0 +1,226 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Operator level: energy/mass, the residual F, the Jacobian action, the Schwarz
+preconditioner and the GMRES solve, element by element on seeded inputs whose
+grids span several subdomains with ragged sizes.  Time-step level: the fields
+after whole NKS steps, relative L2 per field <= 1e-8 (the tolerance of the
+FP64 method), mass to 1e-12 and a non-increasing energy.  Full size: one step
+of the 1024^2 workload checked by the oracle's own residual on the GPU result.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nks():
+    import torch
+    assert torch.cuda.is_available()
+    import __graft_entry__ as g
+    g.build()
+    import paper_2209_08001_gb300 as m
+    return m
+
+
+def soa(c, e, u=None):
+    parts = [c, e] + ([] if u is None else list(np.asarray(u)))
+    return np.concatenate(parts)
+
+
+def split_soa(X, N, nf):
+    Y = X.reshape(nf, N)
+    return Y[0], Y[1], (Y[2:] if nf > 2 else None)
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _pair(dim, n, seed, du=0.01):
+    c0, e0, u0 = S.random_fields(dim, n, seed, u_amp=du)
+    rng = np.random.default_rng(seed + 1)
+    c1 = c0 * (1 + 0.04 * rng.uniform(-1, 1, c0.shape))
+    e1 = e0 * (1 + 0.04 * rng.uniform(-1, 1, e0.shape))
+    u1 = u0 * (1 + 0.04 * rng.uniform(-1, 1, u0.shape))
+    return (c1, e1, u1), (c0, e0, u0)
+
+
+CASES = [(2, (37, 29), (3, 2), 1), (2, (40, 36), (2, 3), 2), (3, (11, 10, 9), (2, 2, 1), 1)]
+
+
+@pytest.mark.parametrize("dim,n,sub,ov", CASES)
+def test_operators_match_oracle(nks, dim, n, sub, ov):
+    cf = S.coefficients()
+    op = S.options(sub=sub, overlap=ov)
+    (c1, e1, u1), (c0, e0, u0) = _pair(dim, n, 100 + dim)
+    P = nks.Problem(dim, n, 0.25, c0, e0, cf, op)
+    O = oracle.Problem(dim, n, 0.25, cf, op)
+    N, nf = P.N, P.nf
+    cb = float(np.sum(c0) / N)
+    X1g, X0g = soa(c1, e1, u1), soa(c0, e0, u0)
+    X1o, X0o = O.interleave(c1, e1, u1), O.interleave(c0, e0, u0)
+    to_soa = lambda Xo: soa(*O.split(Xo)) if nf > 2 else soa(*O.split(Xo)[:2])
+    dt = 0.07
+    # energy and mass
+    parts, mass = P.eval_energy(X1g)
+    e_o, parts_o = O.energy(X1o, cb, parts=True)
+    assert parts[4] == pytest.approx(e_o, rel=1e-13, abs=1e-11)
+    assert np.allclose(parts[:4], parts_o, rtol=1e-12, atol=1e-11)
+    assert mass == pytest.approx(O.mass(X1o), rel=1e-14)
+    # residual (full and displacement-only systems)
+    for mode in (0, 1):
+        Fg = P.eval_residual(X1g, X0g, dt, mode)
+        Fo = to_soa(O.residual(X1o, X0o, cb, dt, mode))
+        for f in range(nf):
+            a, b = Fg[f * N:(f + 1) * N], Fo[f * N:(f + 1) * N]
+            assert np.max(np.abs(a - b)) <= 1e-12 * max(np.max(np.abs(b)), 1e-30) + 1e-300, (mode, f)
+    # Jacobian action against the oracle's assembled Jacobian
+    v = np.random.default_rng(5).standard_normal(nf * N)
+    vo = O.interleave(*split_soa(v, N, nf))
+    for mode in (0, 1):
+        Jv = P.apply_jacobian(X1g, X0g, dt, v, mode)
+        Jo = to_soa(O.jacobian_scipy(X1o, X0o, cb, dt, mode) @ vo)
+        for f in range(nf):
+            a, b = Jv[f * N:(f + 1) * N], Jo[f * N:(f + 1) * N]
+            assert np.max(np.abs(a - b)) <= 1e-12 * np.max(np.abs(b)), (mode, f)
+    # Schwarz preconditioner with the projection
+    r = np.random.default_rng(6).standard_normal(nf * N)
+    z = P.apply_preconditioner(X1g, X0g, dt, r)
+    rc, zo = O.precond_apply(X1o, X0o, cb, dt, O.interleave(*split_soa(r, N, nf)))
+    assert rc == 0
+    assert rel(z, to_soa(zo)) <= 1e-9
+    assert abs(z[:N].sum()) <= 1e-11 * np.abs(z[:N]).sum()
+    # GMRES solve
+    b = -P.eval_residual(X1g, X0g, dt, 0)
+    tol = 1e-11 * np.linalg.norm(b)
+    x, its, res = P.linear_solve(X1g, X0g, dt, b, tol)
+    assert res <= tol
+    rc, xo, its_o, res_o = O.linear_solve(X1o, X0o, cb, dt, O.interleave(*split_soa(b, N, nf)), tol)
+    assert rel(x, to_soa(xo)) <= 1e-8
+    assert abs(its - its_o) <= max(2, its_o // 5)
+    P.destroy()
+
+
+def _run_both(nks, dim, n, cbar, seed, steps, op, cf=None, dt=0.01):
+    cf = cf or S.coefficients()
+    c, e = S.initial_fields(dim, n, cbar, seed)
+    P = nks.Problem(dim, n, 0.25, c, e, cf, op)
+    infos = [P.step(dt) for _ in range(steps)]
+    cg, eg, ug = P.get_fields()
+    O = oracle.Problem(dim, n, 0.25, cf, dict(op, newton_rtol=1e-12))
+    rc, X, oinf, e0 = O.simulate(c, e, steps, dt_replay=[i["dt"] for i in infos])
+    assert rc == 0
+    co, eo, uo = O.split(X)
+    return P, (c, e), (cg, eg, ug), (co, eo, uo), infos, oinf, e0
+
+
+def test_config_2d64_ten_steps(nks):
+    cfg = S.CONFIGS["2d64"]
+    op = S.options(**cfg["opts"])
+    P, (c, e), (cg, eg, ug), (co, eo, uo), infos, oinf, e0 = _run_both(nks, 2, cfg["n"], cfg["cbar"], cfg["seed"],
+                                                                        cfg["steps"], op)
+    assert rel(cg, co) <= 1e-8 and rel(eg, eo) <= 1e-8
+    assert rel(ug, uo) <= 1e-8
+    m0 = c.sum() * 0.25 ** 2
+    E = [e0] + [i["energy"] for i in infos]
+    for i in infos:
+        assert abs(i["mass"] - m0) <= 1e-12 * m0
+        assert i["newton_its"] >= 1
+    for a, b in zip(E[:-1], E[1:]):
+        assert b <= a + 1e-12 * abs(a)
+    for gi, oi in zip(infos, oinf):
+        assert gi["energy"] == pytest.approx(oi["energy"], rel=1e-10)
+        assert abs(gi["gmres_its"] - oi["gmres_its"]) <= max(3, oi["gmres_its"] // 5)
+    P.destroy()
+
+
+def test_3d_small_three_steps(nks):
+    op = S.options(sub=(2, 2, 2), overlap=1)
+    P, _, (cg, eg, ug), (co, eo, uo), infos, oinf, _ = _run_both(nks, 3, (16, 14, 12), 0.18, 9, 3, op)
+    assert rel(cg, co) <= 1e-8 and rel(eg, eo) <= 1e-8 and rel(ug, uo) <= 1e-8
+    P.destroy()
+
+
+def test_adaptive_steps_replayed_by_oracle(nks):
+    cf = S.coefficients()
+    op = S.options(sub=(2, 2), overlap=1, dt_mode="energy")
+    c, e = S.initial_fields(2, (32, 32), 0.2, 4)
+    P = nks.Problem(2, (32, 32), 0.25, c, e, cf, op)
+    infos = [P.step() for _ in range(6)]
+    assert infos[0]["dt"] == 0.01
+    assert all(i["dt"] >= 0.01 - 1e-15 for i in infos)
+    cg, eg, ug = P.get_fields()
+    O = oracle.Problem(2, (32, 32), 0.25, cf, dict(op, newton_rtol=1e-12))
+    rc, X, oinf, _ = O.simulate(c, e, 6, dt_replay=[i["dt"] for i in infos])
+    co, eo, uo = O.split(X)
+    assert rc == 0 and rel(cg, co) <= 1e-8 and rel(eg, eo) <= 1e-8
+    P.destroy()
+
+
+def test_checkpoint_resume_is_bitwise(nks):
+    cf = S.coefficients()
+    op = S.options(sub=(2, 2), overlap=1, dt_mode="solution")
+    c, e = S.initial_fields(2, (24, 24), 0.18, 3)
+    A = nks.Problem(2, (24, 24), 0.25, c, e, cf, op)
+    for _ in range(2):
+        A.step()
+    blob = A.get_state()
+    ref = [A.step() for _ in range(2)]
+    ca, ea, ua = A.get_fields()
+    B = nks.Problem(2, (24, 24), 0.25, c, e, cf, op)
+    B.set_state(blob)
+    got = [B.step() for _ in range(2)]
+    cb_, eb_, ub_ = B.get_fields()
+    assert np.array_equal(ca, cb_) and np.array_equal(ea, eb_) and np.array_equal(ua, ub_)
+    assert [r["dt"] for r in ref] == [g["dt"] for g in got]
+    A.destroy()
+    B.destroy()
+
+
+def test_steady_state_and_invalid_inputs(nks):
+    cf = S.coefficients()
+    op = S.options(sub=(2, 2), overlap=1)
+    N = 16 * 16
+    P = nks.Problem(2, (16, 16), 0.25, np.full(N, 0.17), np.full(N, 1.0), cf, op)
+    info = P.step(0.5)
+    assert info["newton_its"] == 0
+    c, e, u = P.get_fields()
+    assert np.all(c == 0.17) and np.all(e == 1.0)
+    P.destroy()
+    with pytest.raises(nks.NksError) as ei:
+        nks.Problem(2, (16, 16), 0.25, np.full(N, 0.3), np.full(N, 0.0), cf, op)
+    assert ei.value.code == nks.NKS_EDOMAIN
+    with pytest.raises(nks.NksError) as ei:
+        nks.Problem(2, (16, 16), 0.25, np.full(N, 0.17), np.full(N, 0.5), cf, S.options(sub=(1, 1), overlap=1))
+    assert ei.value.code == nks.NKS_EINVAL
+
+
+def test_full_size_2d1024_step_checked_by_oracle_residual(nks):
+    cfg = S.CONFIGS["2d1024"]
+    cf = S.coefficients()
+    op = S.options(**cfg["opts"])
+    n = cfg["n"]
+    c, e = S.initial_fields(2, n, cfg["cbar"], cfg["seed"])
+    P = nks.Problem(2, n, 0.25, c, e, cf, op)
+    _, _, u0 = P.get_fields()
+    info = P.step()
+    assert info["status"] == 0 and info["dt"] == 0.01
+    cg, eg, ug = P.get_fields()
+    O = oracle.Problem(2, n, 0.25, cf, op)
+    cb = float(np.sum(c) / c.size)
+    X0 = O.interleave(c, e, u0)
+    X1 = O.interleave(cg, eg, ug)
+    # u0 is the oracle's equilibrium too: its displacement residual vanishes
+    Fu0 = O.residual(X0, X0, cb, 1.0, mode=1)
+    assert np.linalg.norm(Fu0) <= 1e-9 * np.linalg.norm(O.residual(O.interleave(c, e), O.interleave(c, e), cb, 1.0, 1))
+    F = O.residual(X1, X0, cb, info["dt"])
+    F0 = O.residual(X0, X0, cb, info["dt"])
+    assert np.linalg.norm(F) <= 1e-9 * np.linalg.norm(F0)
+    m0 = O.mass(X0)
+    assert abs(info["mass"] - m0) <= 1e-12 * m0
+    assert info["energy"] <= O.energy(X0, cb)
+    P.destroy()
