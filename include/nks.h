@@ -158,13 +158,20 @@ typedef struct {
     double ms[NKS_NCLASS];          /* summed CUDA-event durations (timing = 1) */
     long long newton_its, gmres_its, steps, retries;
     long long factor_bytes;         /* bytes of stored Schwarz factors          */
+    double schwarz_points;          /* overlapped points of all subdomains      */
+    double schwarz_bytes;           /* algorithmic bytes of one Schwarz sweep:
+                                       factors of every overlapped point, the
+                                       gathered sub-vectors and the owned output */
+    double schwarz_flops;           /* algorithmic FLOPs of one Schwarz sweep   */
+    long long kernel_launches;      /* CUDA kernels this problem launched       */
 } nks_stats;
 /* kernel classes: 0 residual, 1 Jacobian action, 2 Schwarz apply,
  * 3 assembly + ILU(0), 4 Gram-Schmidt dots, 5 Gram-Schmidt update,
  * 6 projection, 7 energy/mass, 8 vector ops, 9 small dense (Hessenberg) */
 
-/* Fill *g, *k, *o with the defaults: 2-D 64x64 grid, h = 0.25, the paper's
- * printed constants, and the solver settings of Sec. 4-5. */
+/* Fill *o with the default solver settings (Sec. 4-5): eps_r = 1e-10,
+ * GMRES(30), 4x4 subdomains with overlap 1, ILU(0)-reuse, dt_1 = dt_min =
+ * 0.01, dt_max = 2, zeta = 100, fixed dt. */
 void nks_default_opts(nks_opts *o);
 
 /*

@@ -79,13 +79,17 @@ class nks_stats(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_longlong * NCLASS), ("ms", ctypes.c_double * NCLASS),
                 ("newton_its", ctypes.c_longlong), ("gmres_its", ctypes.c_longlong),
                 ("steps", ctypes.c_longlong), ("retries", ctypes.c_longlong),
-                ("factor_bytes", ctypes.c_longlong)]
+                ("factor_bytes", ctypes.c_longlong), ("schwarz_points", ctypes.c_double),
+                ("schwarz_bytes", ctypes.c_double), ("schwarz_flops", ctypes.c_double),
+                ("kernel_launches", ctypes.c_longlong)]
 
     def as_dict(self):
         return {"launches": {KERNEL_CLASSES[i]: self.launches[i] for i in range(NCLASS)},
                 "ms": {KERNEL_CLASSES[i]: self.ms[i] for i in range(NCLASS)},
                 "newton_its": self.newton_its, "gmres_its": self.gmres_its, "steps": self.steps,
-                "retries": self.retries, "factor_bytes": self.factor_bytes}
+                "retries": self.retries, "factor_bytes": self.factor_bytes,
+                "schwarz_points": self.schwarz_points, "schwarz_bytes": self.schwarz_bytes,
+                "schwarz_flops": self.schwarz_flops, "kernel_launches": self.kernel_launches}
 
 
 _lib = None

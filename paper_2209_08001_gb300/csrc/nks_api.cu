@@ -48,33 +48,49 @@ void Problem::tick(int cls)
 {
     stats.launches[cls]++;
     if (!opts.timing) return;
-    Timer t;
-    cudaEventCreate(&t.a);
-    cudaEventCreate(&t.b);
-    cudaEventRecord(t.a, stream);
-    timers[cls].push_back(t);
+    TimerPool &tp = timers[cls];
+    if (tp.used == tp.ev.size()) {
+        Timer t;
+        cudaEventCreate(&t.a);
+        cudaEventCreate(&t.b);
+        tp.ev.push_back(t);
+    }
+    cudaEventRecord(tp.ev[tp.used].a, stream);
 }
 
 void Problem::tock(int cls)
 {
-    if (!opts.timing || timers[cls].empty()) return;
-    cudaEventRecord(timers[cls].back().b, stream);
+    if (!opts.timing) return;
+    TimerPool &tp = timers[cls];
+    if (tp.used < tp.ev.size()) cudaEventRecord(tp.ev[tp.used++].b, stream);
 }
 
+// accumulate the recorded intervals (synchronises) and recycle the events
 static void harvest_timers(Problem *P)
 {
     if (!P->opts.timing) return;
     cudaStreamSynchronize(P->stream);
     for (int c = 0; c < NKS_NCLASS; c++) {
-        for (Timer &t : P->timers[c]) {
+        TimerPool &tp = P->timers[c];
+        for (size_t i = 0; i < tp.used; i++) {
             float ms = 0.f;
-            if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) P->stats.ms[c] += ms;
+            if (cudaEventElapsedTime(&ms, tp.ev[i].a, tp.ev[i].b) == cudaSuccess) P->stats.ms[c] += ms;
+        }
+        tp.used = 0;
+    }
+    cudaGetLastError();
+}
+
+static void destroy_timers(Problem *P)
+{
+    for (int c = 0; c < NKS_NCLASS; c++) {
+        for (Timer &t : P->timers[c].ev) {
             cudaEventDestroy(t.a);
             cudaEventDestroy(t.b);
         }
-        P->timers[c].clear();
+        P->timers[c].ev.clear();
+        P->timers[c].used = 0;
     }
-    cudaGetLastError();
 }
 
 int Problem::sync_check(const char *where)
@@ -131,9 +147,9 @@ static int residual(Problem *P, double dt, int mode, const double *X1, const dou
 {
     cudaMemsetAsync(P->dflag, 0, sizeof(int), P->stream);
     P->tick(0);
-    launch_residual(P->g, P->k, dt, mode, X1, X0, P->tr0, P->mob, P->Gc, P->sig, part, F, P->dflag, P->partials,
-                    P->stream);
-    launch_finalize(P->partials, kRedBlocks, 1, P->dscal, P->stream);
+    P->count(launch_residual(P->g, P->k, dt, mode, X1, X0, P->tr0, P->mob, P->Gc, P->sig, part, F, P->dflag,
+                             P->partials, P->stream));
+    P->count(launch_finalize(P->partials, kRedBlocks, 1, P->dscal, P->stream));
     P->tock(0);
     cudaMemcpyAsync(P->hscal, P->dscal, sizeof(double), cudaMemcpyDeviceToHost, P->stream);
     cudaMemcpyAsync(P->hscal + 1, P->dflag, sizeof(int), cudaMemcpyDeviceToHost, P->stream);
@@ -150,8 +166,8 @@ static int residual(Problem *P, double dt, int mode, const double *X1, const dou
 static void prepare_level(Problem *P, const double *X0)
 {
     P->tick(8);
-    launch_mobility(P->g, P->k, X0, P->mob, P->stream);
-    if (P->k.elastic) launch_trace0(P->g, P->k, X0, P->tr0, P->stream);
+    P->count(launch_mobility(P->g, P->k, X0, P->mob, P->stream));
+    if (P->k.elastic) P->count(launch_trace0(P->g, P->k, X0, P->tr0, P->stream));
     P->tock(8);
 }
 
@@ -188,7 +204,7 @@ static int newton(Problem *P, double dt, int mode, double rtol, double atol, int
             if (rc) return rc;
         }
         P->tick(8);
-        launch_axpby(n, -1.0, P->F, 0.0, P->B, P->stream);
+        P->count(launch_axpby(n, -1.0, P->F, 0.0, P->B, P->stream));
         P->tock(8);
         int gits = 0;
         double gres = 0.0;
@@ -200,7 +216,7 @@ static int newton(Problem *P, double dt, int mode, double rtol, double atol, int
         bool accepted = false;
         while (lam >= P->opts.ls_lambda_min) {
             P->tick(8);
-            launch_waxpy(n, P->X, lam, P->S, P->Xt, P->stream);
+            P->count(launch_waxpy(n, P->X, lam, P->S, P->Xt, P->stream));
             P->tock(8);
             bool dok;
             rc = residual(P, dt, mode, P->Xt, P->Xn, P->Ft, P->part_t, &ftn, &dok);
@@ -231,8 +247,8 @@ static int newton(Problem *P, double dt, int mode, double rtol, double atol, int
 static int energy_mass(Problem *P, const double *X, double *parts5, double *mass)
 {
     P->tick(7);
-    launch_energy(P->g, P->k, X, P->partials, P->stream);
-    launch_finalize(P->partials, kRedBlocks, 5, P->dscal, P->stream);
+    P->count(launch_energy(P->g, P->k, X, P->partials, P->stream));
+    P->count(launch_finalize(P->partials, kRedBlocks, 5, P->dscal, P->stream));
     P->tock(7);
     cudaMemcpyAsync(P->hscal, P->dscal, 5 * sizeof(double), cudaMemcpyDeviceToHost, P->stream);
     int rc = P->sync_check("energy");
@@ -435,9 +451,9 @@ int nks_step(nks_problem *H, double dt_arg, nks_step_info *info_out)
     } else {
         double Xd;
         if (P->opts.dt_mode == NKS_DT_SOLUTION) {
-            launch_waxpy(n, P->Xn, -1.0, P->Xprev, P->W, P->stream);
-            launch_dot2(n, P->W, P->W, P->partials, P->stream);
-            launch_finalize(P->partials, kRedBlocks, 2, P->dscal, P->stream);
+            P->count(launch_waxpy(n, P->Xn, -1.0, P->Xprev, P->W, P->stream));
+            P->count(launch_dot2(n, P->W, P->W, P->partials, P->stream));
+            P->count(launch_finalize(P->partials, kRedBlocks, 2, P->dscal, P->stream));
             cudaMemcpyAsync(P->hscal, P->dscal + 1, sizeof(double), cudaMemcpyDeviceToHost, P->stream);
             int rc = P->sync_check("dt");
             if (rc) return rc;
@@ -581,9 +597,12 @@ int nks_get_stats(const nks_problem *H, nks_stats *out)
 
 int nks_reset_stats(nks_problem *H)
 {
-    long long fb = H->P.stats.factor_bytes;
+    nks_stats keep = H->P.stats;  // plan figures survive a reset
     memset(&H->P.stats, 0, sizeof(nks_stats));
-    H->P.stats.factor_bytes = fb;
+    H->P.stats.factor_bytes = keep.factor_bytes;
+    H->P.stats.schwarz_points = keep.schwarz_points;
+    H->P.stats.schwarz_bytes = keep.schwarz_bytes;
+    H->P.stats.schwarz_flops = keep.schwarz_flops;
     return NKS_OK;
 }
 
@@ -593,6 +612,7 @@ void nks_destroy(nks_problem *H)
     Problem *P = &H->P;
     if (P->stream) cudaStreamSynchronize(P->stream);
     harvest_timers(P);
+    destroy_timers(P);
     ras_plan_destroy(P);
     P->dfree_all();
     if (P->hscal) cudaFreeHost(P->hscal);
@@ -618,8 +638,8 @@ static int op_setup(Problem *P, const double *X1, const double *X0, double dt, i
     P->cur_dt = dt;
     P->cur_mode = mode;
     P->tick(8);
-    launch_mobility(P->g, P->k, P->Xt, P->mob, P->stream);
-    if (P->k.elastic) launch_trace0(P->g, P->k, P->Xt, P->tr0, P->stream);
+    P->count(launch_mobility(P->g, P->k, P->Xt, P->mob, P->stream));
+    if (P->k.elastic) P->count(launch_trace0(P->g, P->k, P->Xt, P->tr0, P->stream));
     P->tock(8);
     double fn;
     bool ok;
@@ -656,7 +676,7 @@ int nks_apply_jacobian(nks_problem *H, const double *X1, const double *X0, doubl
         const size_t vb = sizeof(double) * (size_t)P->nvec;
         cudaMemcpyAsync(P->B, v, vb, cudaMemcpyHostToDevice, P->stream);
         P->tick(1);
-        launch_jv(P->g, P->k, dt, mode, P->part, P->mob, P->B, P->Gc, P->sig, P->W, P->stream);
+        P->count(launch_jv(P->g, P->k, dt, mode, P->part, P->mob, P->B, P->Gc, P->sig, P->W, P->stream));
         P->tock(1);
         cudaMemcpyAsync(Jv, P->W, vb, cudaMemcpyDeviceToHost, P->stream);
         rc = P->sync_check("apply_jacobian");
@@ -672,9 +692,7 @@ int nks_apply_preconditioner(nks_problem *H, const double *X1, const double *X0,
     if (!rc) {
         const size_t vb = sizeof(double) * (size_t)P->nvec;
         cudaMemcpyAsync(P->B, r, vb, cudaMemcpyHostToDevice, P->stream);
-        P->tick(2);
         ras_apply(P, P->B, P->Z);
-        P->tock(2);
         cudaMemcpyAsync(z, P->Z, vb, cudaMemcpyDeviceToHost, P->stream);
         rc = P->sync_check("apply_preconditioner");
     }

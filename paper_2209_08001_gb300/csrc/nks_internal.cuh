@@ -102,24 +102,24 @@ __device__ inline void block_reduce_store(double (&v)[K], double *partials /* [g
 // stencil / reduction kernels (nks_stencil.cu)
 // ---------------------------------------------------------------------------
 
-void launch_mobility(const DGrid &g, const DCoef &k, const double *c0, double *mob, cudaStream_t st);
-void launch_trace0(const DGrid &g, const DCoef &k, const double *X0, double *tr0, cudaStream_t st);
-void launch_residual(const DGrid &g, const DCoef &k, double dt, int mode, const double *X1, const double *X0,
+int launch_mobility(const DGrid &g, const DCoef &k, const double *c0, double *mob, cudaStream_t st);
+int launch_trace0(const DGrid &g, const DCoef &k, const double *X0, double *tr0, cudaStream_t st);
+int launch_residual(const DGrid &g, const DCoef &k, double dt, int mode, const double *X1, const double *X0,
                      const double *tr0, const double *mob, double *Gc, double *sig, double *part, double *F,
                      int *flag, double *partials, cudaStream_t st);
-void launch_jv(const DGrid &g, const DCoef &k, double dt, int mode, const double *part, const double *mob,
+int launch_jv(const DGrid &g, const DCoef &k, double dt, int mode, const double *part, const double *mob,
                const double *v, double *dG, double *sig, double *Jv, cudaStream_t st);
-void launch_energy(const DGrid &g, const DCoef &k, const double *X, double *partials, cudaStream_t st);
-void launch_finalize(const double *partials, int nblocks, int K, double *out, cudaStream_t st);
+int launch_energy(const DGrid &g, const DCoef &k, const double *X, double *partials, cudaStream_t st);
+int launch_finalize(const double *partials, int nblocks, int K, double *out, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // vector kernels (nks_krylov.cu)
 // ---------------------------------------------------------------------------
 
-void launch_axpby(long long n, double a, const double *x, double b, double *y, cudaStream_t st);   // y = a x + b y
-void launch_waxpy(long long n, const double *x, double a, const double *y, double *w, cudaStream_t st); // w = x + a y
-void launch_scale_dev(long long n, const double *src, const double *inv_norm, double *dst, cudaStream_t st);
-void launch_dot2(long long n, const double *x, const double *y, double *partials, cudaStream_t st); // x.y, y.y
+int launch_axpby(long long n, double a, const double *x, double b, double *y, cudaStream_t st);   // y = a x + b y
+int launch_waxpy(long long n, const double *x, double a, const double *y, double *w, cudaStream_t st); // w = x + a y
+int launch_scale_dev(long long n, const double *src, const double *inv_norm, double *dst, cudaStream_t st);
+int launch_dot2(long long n, const double *x, const double *y, double *partials, cudaStream_t st); // x.y, y.y
 
 // GMRES(m) with right preconditioning; see nks_krylov.cu.
 struct Problem;
@@ -135,6 +135,7 @@ void ras_plan_destroy(Problem *P);
 int ras_factor(Problem *P, int mode);                              // assemble J restricted + ILU(0)
 void ras_apply(Problem *P, const double *r, double *z);           // z = P RAS^-1 r
 void project(Problem *P, double *z);
+void ras_work(const Problem *P, double *bytes, double *flops);  // algorithmic work of one sweep
 
 // ---------------------------------------------------------------------------
 // problem object (nks_api.cu)
@@ -142,6 +143,12 @@ void project(Problem *P, double *z);
 
 struct Timer {
     cudaEvent_t a = nullptr, b = nullptr;
+};
+
+// per-class pool of event pairs, reused across steps
+struct TimerPool {
+    std::vector<Timer> ev;
+    size_t used = 0;
 };
 
 struct Problem {
@@ -189,11 +196,12 @@ struct Problem {
     double cbar0 = 0.0;
 
     nks_stats stats{};
-    std::vector<Timer> timers[NKS_NCLASS];
+    TimerPool timers[NKS_NCLASS];
     std::string err;
 
     void *dalloc(size_t bytes);
     void dfree_all();
+    void count(int n) { stats.kernel_launches += n; }  // kernels launched on this problem
     void tick(int cls);                         // count a launch of class cls (and start a timer)
     void tock(int cls);                         // stop its timer
     int sync_check(const char *where);

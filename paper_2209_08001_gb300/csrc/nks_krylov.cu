@@ -13,6 +13,9 @@
 // depend on timing.
 #include <math.h>
 
+#include <array>
+#include <utility>
+
 #include "nks_internal.cuh"
 
 namespace nks {
@@ -77,69 +80,74 @@ __global__ void __launch_bounds__(kRedThreads) k_dot2(long long n, const double 
     block_reduce_store<2>(acc, partials);
 }
 
-// runtime-K block reduction (K <= kMaxDots + 1)
-__device__ inline void block_reduce_dyn(const double *v, int K, double *partials)
-{
-    __shared__ double red[kMaxDots + 1][kRedThreads / 32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < kMaxDots + 1; k++) {
-        if (k < K) {
-            double a = v[k];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-            if (lane == 0) red[k][warp] = a;
-        }
-    }
-    __syncthreads();
-    if ((int)threadIdx.x < K) {
-        double a = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); w++) a += red[threadIdx.x][w];
-        partials[(size_t)blockIdx.x * K + threadIdx.x] = a;
-    }
-}
-
-// CGS pass 1: h_i = v_i . w (i < nv) and w . w, one read of V and w.
+// CGS pass 1: h_i = v_i . w (i < NV) and w . w, one read of V and w.
 // gate (optional): skip unless gate[0] != 0.
+template <int NV>
 __global__ void __launch_bounds__(kRedThreads) k_multidot(long long n, const double *__restrict__ V, long long ldv,
-                                                          int nv, const double *__restrict__ w,
-                                                          double *__restrict__ partials, const double *gate)
+                                                          const double *__restrict__ w, double *__restrict__ partials,
+                                                          const double *gate)
 {
     if (gate && gate[0] == 0.0) return;
-    double acc[kMaxDots + 1];
+    double acc[NV + 1];
 #pragma unroll
-    for (int k = 0; k < kMaxDots + 1; k++) acc[k] = 0.0;
+    for (int k = 0; k <= NV; k++) acc[k] = 0.0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const double wi = w[i];
 #pragma unroll
-        for (int k = 0; k < kMaxDots; k++)
-            if (k < nv) acc[k] += V[k * ldv + i] * wi;
-        acc[kMaxDots] += wi * wi;
+        for (int k = 0; k < NV; k++) acc[k] += V[k * ldv + i] * wi;
+        acc[NV] += wi * wi;
     }
-    acc[nv] = acc[kMaxDots];
-    block_reduce_dyn(acc, nv + 1, partials);
+    block_reduce_store<NV + 1>(acc, partials);
 }
 
 // CGS pass 2: w -= sum_i h_i v_i, accumulating ||w||^2.
+template <int NV>
 __global__ void __launch_bounds__(kRedThreads) k_cgs_update(long long n, const double *__restrict__ V, long long ldv,
-                                                            int nv, const double *__restrict__ h,
-                                                            double *__restrict__ w, double *__restrict__ partials,
-                                                            const double *gate)
+                                                            const double *__restrict__ h, double *__restrict__ w,
+                                                            double *__restrict__ partials, const double *gate)
 {
     if (gate && gate[0] == 0.0) return;
-    __shared__ double hs[kMaxDots];
-    if ((int)threadIdx.x < nv) hs[threadIdx.x] = h[threadIdx.x];
-    __syncthreads();
+    double hk[NV];
+#pragma unroll
+    for (int k = 0; k < NV; k++) hk[k] = h[k];
     double acc[1] = {0.0};
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         double s = w[i];
 #pragma unroll
-        for (int k = 0; k < kMaxDots; k++)
-            if (k < nv) s -= hs[k] * V[k * ldv + i];
+        for (int k = 0; k < NV; k++) s -= hk[k] * V[k * ldv + i];
         w[i] = s;
         acc[0] += s * s;
     }
     block_reduce_store<1>(acc, partials);
+}
+
+using MultidotFn = void (*)(long long, const double *, long long, const double *, double *, const double *);
+using UpdateFn = void (*)(long long, const double *, long long, const double *, double *, double *, const double *);
+
+template <int... I>
+constexpr auto multidot_table(std::integer_sequence<int, I...>)
+{
+    return std::array<MultidotFn, sizeof...(I)>{{&k_multidot<I + 1>...}};
+}
+template <int... I>
+constexpr auto update_table(std::integer_sequence<int, I...>)
+{
+    return std::array<UpdateFn, sizeof...(I)>{{&k_cgs_update<I + 1>...}};
+}
+constexpr int kMaxNv = 31;
+const auto g_multidot = multidot_table(std::make_integer_sequence<int, kMaxNv>{});
+const auto g_update = update_table(std::make_integer_sequence<int, kMaxNv>{});
+
+void launch_multidot(int nv, long long n, const double *V, const double *w, double *partials, const double *gate,
+                     cudaStream_t st)
+{
+    g_multidot[nv - 1]<<<kRedBlocks, kRedThreads, 0, st>>>(n, V, n, w, partials, gate);
+}
+
+void launch_update(int nv, long long n, const double *V, const double *h, double *w, double *partials,
+                   const double *gate, cudaStream_t st)
+{
+    g_update[nv - 1]<<<kRedBlocks, kRedThreads, 0, st>>>(n, V, n, h, w, partials, gate);
 }
 
 __global__ void k_finalize_g(const double *__restrict__ partials, int nblocks, int K, double *__restrict__ out,
@@ -239,24 +247,28 @@ __global__ void k_lincomb(long long n, const double *__restrict__ V, long long l
 
 }  // namespace
 
-void launch_axpby(long long n, double a, const double *x, double b, double *y, cudaStream_t st)
+int launch_axpby(long long n, double a, const double *x, double b, double *y, cudaStream_t st)
 {
     k_axpby<<<nb(n), kT, 0, st>>>(n, a, x, b, y);
+    return 1;
 }
 
-void launch_waxpy(long long n, const double *x, double a, const double *y, double *w, cudaStream_t st)
+int launch_waxpy(long long n, const double *x, double a, const double *y, double *w, cudaStream_t st)
 {
     k_waxpy<<<nb(n), kT, 0, st>>>(n, x, a, y, w);
+    return 1;
 }
 
-void launch_scale_dev(long long n, const double *src, const double *inv, double *dst, cudaStream_t st)
+int launch_scale_dev(long long n, const double *src, const double *inv, double *dst, cudaStream_t st)
 {
     k_scale_dev<<<nb(n), kT, 0, st>>>(n, src, inv, dst);
+    return 1;
 }
 
-void launch_dot2(long long n, const double *x, const double *y, double *partials, cudaStream_t st)
+int launch_dot2(long long n, const double *x, const double *y, double *partials, cudaStream_t st)
 {
     k_dot2<<<kRedBlocks, kRedThreads, 0, st>>>(n, x, y, partials);
+    return 1;
 }
 
 size_t gmres_state_doubles(int m) { return (size_t)GmLayout(m).total; }
@@ -265,8 +277,8 @@ size_t gmres_state_doubles(int m) { return (size_t)GmLayout(m).total; }
 static double norm2_host(Problem *P, const double *x)
 {
     P->tick(8);
-    launch_dot2(P->nvec, x, x, P->partials, P->stream);
-    launch_finalize(P->partials, kRedBlocks, 2, P->dscal, P->stream);
+    P->count(launch_dot2(P->nvec, x, x, P->partials, P->stream));
+    P->count(launch_finalize(P->partials, kRedBlocks, 2, P->dscal, P->stream));
     P->tock(8);
     cudaMemcpyAsync(P->hscal, P->dscal + 1, sizeof(double), cudaMemcpyDeviceToHost, P->stream);
     cudaStreamSynchronize(P->stream);
@@ -276,7 +288,7 @@ static double norm2_host(Problem *P, const double *x)
 static void apply_J(Problem *P, int mode, const double *v, double *out)
 {
     P->tick(1);
-    launch_jv(P->g, P->k, P->cur_dt, mode, P->part, P->mob, v, P->Gc, P->sig, out, P->stream);
+    P->count(launch_jv(P->g, P->k, P->cur_dt, mode, P->part, P->mob, v, P->Gc, P->sig, out, P->stream));
     P->tock(1);
 }
 
@@ -294,32 +306,30 @@ int gmres_solve(Problem *P, int mode, const double *b, double *x, double tol, in
     const int maxit = P->opts.gmres_maxit;
     while (beta > tol && its < maxit) {
         k_gm_start<<<1, 1, 0, st>>>(gm, L, beta);
-        launch_scale_dev(n, R, gm + L.scal + S_INV, V, st);
+        P->count(1 + launch_scale_dev(n, R, gm + L.scal + S_INV, V, st));
         int kdim = 0;
         for (int j = 0; j < m; j++) {
             double *vj = V + (size_t)j * n, *vn = V + (size_t)(j + 1) * n;
-            P->tick(2);
             ras_apply(P, vj, Z);
-            P->tock(2);
             apply_J(P, mode, Z, W);
             // CGS pass 1 and 2
             P->tick(4);
-            k_multidot<<<kRedBlocks, kRedThreads, 0, st>>>(n, V, n, j + 1, W, P->partials, nullptr);
+            launch_multidot(j + 1, n, V, W, P->partials, nullptr, st);
             k_finalize_g<<<1, kRedThreads, 0, st>>>(P->partials, kRedBlocks, j + 2, gm + L.hcol, nullptr);
             P->tock(4);
             P->tick(5);
-            k_cgs_update<<<kRedBlocks, kRedThreads, 0, st>>>(n, V, n, j + 1, gm + L.hcol, W, P->partials, nullptr);
+            launch_update(j + 1, n, V, gm + L.hcol, W, P->partials, nullptr, st);
             k_finalize_g<<<1, kRedThreads, 0, st>>>(P->partials, kRedBlocks, 1, gm + L.scal + S_WN, nullptr);
             P->tock(5);
             // optional second pass (CGS2), gated on the device
             k_cgs_decide<<<1, 1, 0, st>>>(gm, L, j);
             const double *gate = gm + L.scal + S_FLAG;
             P->tick(4);
-            k_multidot<<<kRedBlocks, kRedThreads, 0, st>>>(n, V, n, j + 1, W, P->partials, gate);
+            launch_multidot(j + 1, n, V, W, P->partials, gate, st);
             k_finalize_g<<<1, kRedThreads, 0, st>>>(P->partials, kRedBlocks, j + 2, gm + L.h2, gate);
             P->tock(4);
             P->tick(5);
-            k_cgs_update<<<kRedBlocks, kRedThreads, 0, st>>>(n, V, n, j + 1, gm + L.h2, W, P->partials, gate);
+            launch_update(j + 1, n, V, gm + L.h2, W, P->partials, gate, st);
             k_finalize_g<<<1, kRedThreads, 0, st>>>(P->partials, kRedBlocks, 1, gm + L.scal + S_WN, gate);
             P->tock(5);
             k_cgs_accum<<<1, 1, 0, st>>>(gm, L, j);
@@ -327,6 +337,7 @@ int gmres_solve(Problem *P, int mode, const double *b, double *x, double tol, in
             k_arnoldi<<<1, 1, 0, st>>>(gm, L, j);
             P->tock(9);
             launch_scale_dev(n, W, gm + L.scal + S_INV, vn, st);
+            P->count(12);  // 2 multidot + 4 finalize + 2 update + decide + accum + arnoldi + scale
             its++;
             kdim = j + 1;
             cudaMemcpyAsync(P->hscal, gm + L.scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, st);
@@ -338,12 +349,11 @@ int gmres_solve(Problem *P, int mode, const double *b, double *x, double tol, in
         }
         k_hsolve<<<1, 1, 0, st>>>(gm, L, kdim);
         k_lincomb<<<nb(n), kT, 0, st>>>(n, V, n, kdim, gm + L.y, W);
-        P->tick(2);
+        P->count(2);
         ras_apply(P, W, Z);
-        P->tock(2);
-        launch_axpby(n, 1.0, Z, 1.0, x, st);
+        P->count(launch_axpby(n, 1.0, Z, 1.0, x, st));
         apply_J(P, mode, x, W);
-        launch_waxpy(n, b, -1.0, W, R, st);
+        P->count(launch_waxpy(n, b, -1.0, W, R, st));
         beta = sqrt(norm2_host(P, R));
         if (!(beta == beta)) break;
     }

@@ -1,0 +1,217 @@
+// nks_pattern.cuh -- one row of the Jacobian dF/dX1 of NSOA-1 and its
+// compile-time sparsity pattern.
+//
+// jac_row() lists the entries of row f at a point as (offset, field, value)
+// contributions.  The assembly kernel evaluates it numerically; the same
+// function, run at compile time with a structural accumulator, yields the
+// exact pattern (and its column order) that the Schwarz sweeps unroll over.
+#pragma once
+
+#include "nks_internal.cuh"
+
+namespace nks {
+
+// ---------------------------------------------------------------------------
+// one row of the Jacobian dF/dX1 as a list of (offset, field, value)
+// ---------------------------------------------------------------------------
+
+struct RowCtx {
+    double a0[7], a1[7];  // dGc/dc1, dGc/deta1 at p (0) and p + e_J (1 + 2J), p - e_J (2 + 2J)
+    double a2, a3;        // dGeta/dc1, dGeta/deta1 at p
+    double Mp[3], Mm[3];  // edge mobilities M_{p + e_J/2}, M_{p - e_J/2}
+};
+
+// contributions of the linearised G_c at q = p + o (o = 0 or +-e_J) with weight w
+template <class Acc>
+__host__ __device__ constexpr void add_grow(Acc &acc, const DCoef &k, int d, double h, int ox, int oy, int oz, double w,
+                                         double a0, double a1)
+{
+    const double ih2 = 1.0 / (h * h);
+    double diag = a0 + k.gamma_c * d * ih2;
+    if (k.elastic) diag += 0.5 * d * k.eps0 * k.eps0 * k.lam;
+    acc(ox, oy, oz, 0, w * diag);
+    for (int J = 0; J < d; J++) {
+        const int ex = J == 0, ey = J == 1, ez = J == 2;
+        acc(ox + ex, oy + ey, oz + ez, 0, -w * 0.5 * k.gamma_c * ih2);
+        acc(ox - ex, oy - ey, oz - ez, 0, -w * 0.5 * k.gamma_c * ih2);
+    }
+    acc(ox, oy, oz, 1, w * a1);
+    if (k.elastic) {
+        const double t = w * k.eps0 * k.lam * 0.25 / h;  // G^3_c = -eps0 lam (sum_K Dhat_K u_K - d eps0 c ...)/2
+        for (int K = 0; K < d; K++) {
+            const int ex = K == 0, ey = K == 1, ez = K == 2;
+            acc(ox + ex, oy + ey, oz + ez, 2 + K, -t);
+            acc(ox - ex, oy - ey, oz - ez, 2 + K, +t);
+        }
+    }
+}
+
+// sigma_IJ(q) row, q = p + o, weight w (stress of eps(u) - eps0 (c - cbar) I)
+template <class Acc>
+__host__ __device__ constexpr void add_sigrow(Acc &acc, const DCoef &k, int d, double h, int ox, int oy, int oz, int I,
+                                           int J, double w)
+{
+    const double i2h = 0.5 / h;
+    if (I == J) {
+        for (int K = 0; K < d; K++) {
+            const int ex = K == 0, ey = K == 1, ez = K == 2;
+            const double cf = (K == I) ? k.C11 : k.C12;
+            acc(ox + ex, oy + ey, oz + ez, 2 + K, w * cf * i2h);
+            acc(ox - ex, oy - ey, oz - ez, 2 + K, -w * cf * i2h);
+        }
+        acc(ox, oy, oz, 0, -w * k.eps0 * k.lam);
+    } else {
+        const int jx = J == 0, jy = J == 1, jz = J == 2;
+        const int ix = I == 0, iy = I == 1, iz = I == 2;
+        acc(ox + jx, oy + jy, oz + jz, 2 + I, w * k.C44 * i2h);
+        acc(ox - jx, oy - jy, oz - jz, 2 + I, -w * k.C44 * i2h);
+        acc(ox + ix, oy + iy, oz + iz, 2 + J, w * k.C44 * i2h);
+        acc(ox - ix, oy - iy, oz - iz, 2 + J, -w * k.C44 * i2h);
+    }
+}
+
+// Row f of J at a point: c-row from F_c = (c1-c0)/dt - D M D G_c, eta-row from
+// F_eta = (eta1-eta0)/dt + G_eta, u_I-row from F_uI = sum_J Dhat_J sigma_IJ.
+// mode 1 (displacement-only system): c and eta rows are identity rows.
+template <class Acc>
+__host__ __device__ constexpr void jac_row(Acc &acc, int f, const DCoef &k, int d, double h, double dt, int mode,
+                                        const RowCtx &r)
+{
+    const double ih2 = 1.0 / (h * h);
+    if (f == 0) {
+        if (mode != 0) {
+            acc(0, 0, 0, 0, 1.0);
+            return;
+        }
+        acc(0, 0, 0, 0, 1.0 / dt);
+        double wc = 0.0;
+        for (int J = 0; J < d; J++) wc += (r.Mp[J] + r.Mm[J]) * ih2;
+        add_grow(acc, k, d, h, 0, 0, 0, wc, r.a0[0], r.a1[0]);
+        for (int J = 0; J < d; J++) {
+            const int ex = J == 0, ey = J == 1, ez = J == 2;
+            add_grow(acc, k, d, h, ex, ey, ez, -r.Mp[J] * ih2, r.a0[1 + 2 * J], r.a1[1 + 2 * J]);
+            add_grow(acc, k, d, h, -ex, -ey, -ez, -r.Mm[J] * ih2, r.a0[2 + 2 * J], r.a1[2 + 2 * J]);
+        }
+    } else if (f == 1) {
+        if (mode != 0) {
+            acc(0, 0, 0, 1, 1.0);
+            return;
+        }
+        acc(0, 0, 0, 1, 1.0 / dt + r.a3 + 3.0 * k.gamma_eta * d * ih2);
+        acc(0, 0, 0, 0, r.a2);
+        for (int J = 0; J < d; J++) {
+            const int ex = J == 0, ey = J == 1, ez = J == 2;
+            acc(ex, ey, ez, 1, -1.5 * k.gamma_eta * ih2);
+            acc(-ex, -ey, -ez, 1, -1.5 * k.gamma_eta * ih2);
+        }
+    } else {
+        const int I = f - 2;
+        const double i2h = 0.5 / h;
+        for (int J = 0; J < d; J++) {
+            const int ex = J == 0, ey = J == 1, ez = J == 2;
+            add_sigrow(acc, k, d, h, ex, ey, ez, I, J, i2h);
+            add_sigrow(acc, k, d, h, -ex, -ey, -ez, I, J, -i2h);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// compile-time pattern
+// ---------------------------------------------------------------------------
+
+constexpr int kMaxSlots = 132;
+
+struct Pattern {
+    int nf;
+    int len[kMaxNf];
+    int diag[kMaxNf];
+    int rowoff[kMaxNf + 1];
+    signed char dx[kMaxSlots], dy[kMaxSlots], dz[kMaxSlots], fc[kMaxSlots];
+    // storage of a point's factors: the strictly lower entries of all rows form
+    // the forward part (nlow rows), the strictly upper entries then the inverse
+    // pivots form the backward part (nup + nf rows); st[a] is the row of slot a
+    // inside its part (the pivot slot itself is stored as its inverse, st = nup + f)
+    int nlow, nup;
+    short st[kMaxSlots];
+};
+
+// structural accumulator: records each (offset, field) once
+struct CxAcc {
+    int n = 0;
+    signed char dx[kMaxRow] = {}, dy[kMaxRow] = {}, dz[kMaxRow] = {}, fc[kMaxRow] = {};
+    __host__ __device__ constexpr void operator()(int x, int y, int z, int f, double)
+    {
+        for (int i = 0; i < n; i++)
+            if (dx[i] == x && dy[i] == y && dz[i] == z && fc[i] == f) return;
+        dx[n] = (signed char)x;
+        dy[n] = (signed char)y;
+        dz[n] = (signed char)z;
+        fc[n] = (signed char)f;
+        n++;
+    }
+};
+
+// column order of a box-local row: lexicographic in (dz, dy, dx, field)
+__host__ __device__ constexpr bool col_less(int z1, int y1, int x1, int f1, int z2, int y2, int x2, int f2)
+{
+    if (z1 != z2) return z1 < z2;
+    if (y1 != y2) return y1 < y2;
+    if (x1 != x2) return x1 < x2;
+    return f1 < f2;
+}
+
+template <int DIM, int NF>
+__host__ __device__ constexpr Pattern make_pattern()
+{
+    Pattern P{};
+    P.nf = NF;
+    DCoef k{};
+    k.gamma_c = k.gamma_eta = k.eps0 = k.lam = k.C11 = k.C12 = k.C44 = 1.0;
+    k.elastic = NF > 2 ? 1 : 0;
+    RowCtx r{};
+    for (int i = 0; i < 7; i++) r.a0[i] = r.a1[i] = 1.0;
+    r.a2 = r.a3 = 1.0;
+    for (int J = 0; J < 3; J++) r.Mp[J] = r.Mm[J] = 1.0;
+    int off = 0;
+    for (int f = 0; f < NF; f++) {
+        CxAcc a{};
+        jac_row(a, f, k, DIM, 1.0, 1.0, 0, r);
+        for (int i = 1; i < a.n; i++) {  // insertion sort into column order
+            int j = i;
+            while (j > 0 && col_less(a.dz[j], a.dy[j], a.dx[j], a.fc[j], a.dz[j - 1], a.dy[j - 1], a.dx[j - 1],
+                                     a.fc[j - 1])) {
+                signed char t = 0;
+                t = a.dx[j]; a.dx[j] = a.dx[j - 1]; a.dx[j - 1] = t;
+                t = a.dy[j]; a.dy[j] = a.dy[j - 1]; a.dy[j - 1] = t;
+                t = a.dz[j]; a.dz[j] = a.dz[j - 1]; a.dz[j - 1] = t;
+                t = a.fc[j]; a.fc[j] = a.fc[j - 1]; a.fc[j - 1] = t;
+                j--;
+            }
+        }
+        P.rowoff[f] = off;
+        P.len[f] = a.n;
+        P.diag[f] = -1;
+        for (int i = 0; i < a.n; i++) {
+            P.dx[off + i] = a.dx[i];
+            P.dy[off + i] = a.dy[i];
+            P.dz[off + i] = a.dz[i];
+            P.fc[off + i] = a.fc[i];
+            if (a.dx[i] == 0 && a.dy[i] == 0 && a.dz[i] == 0 && a.fc[i] == f) P.diag[f] = i;
+        }
+        off += a.n;
+    }
+    P.rowoff[NF] = off;
+    int lo = 0, up = 0;
+    for (int f = 0; f < NF; f++)
+        for (int i = 0; i < P.len[f]; i++) {
+            const int a = P.rowoff[f] + i;
+            if (i < P.diag[f]) P.st[a] = (short)lo++;
+            else if (i > P.diag[f]) P.st[a] = (short)up++;
+        }
+    P.nlow = lo;
+    P.nup = up;
+    for (int f = 0; f < NF; f++) P.st[P.rowoff[f] + P.diag[f]] = (short)(up + f);
+    return P;
+}
+
+}  // namespace nks

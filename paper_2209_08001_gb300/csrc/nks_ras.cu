@@ -4,258 +4,170 @@
 // (one subdomain per core in the paper); Sec. 5.4 selects ILU(0) reused for
 // the whole time step.  Here one overlapping subdomain is one thread block:
 //
-//   * plan (host, once): the exact nonzero pattern of a Jacobian row per
-//     field, derived structurally from the same row function the assembly
-//     kernel evaluates; the ILU(0) update lists (which entries of row k
-//     update which entries of row i); per subdomain the overlapped box,
-//     its owned part and its wavefront levels lv = x + 2y + 4z, which order
-//     every lower neighbour of a point before the point itself;
+//   * plan (host, once): per subdomain the overlapped box, its owned part and
+//     its wavefront levels lv = x + 2y + 4z, which order every lower
+//     neighbour of a point (every column left of the diagonal in the exact
+//     Jacobian pattern, x-fastest point-interleaved numbering) before the
+//     point itself;
 //   * factor (device, once per time step): assemble J restricted to the box
-//     (columns outside the box dropped) and run ILU(0) row by row, level by
-//     level, all rows of one level in parallel.  Factors are stored
-//     slot-major and level-ordered, so one level's threads read
-//     consecutive addresses;
+//     (columns outside it dropped) and run ILU(0) row by row, all points of a
+//     level in parallel, level after level;
 //   * apply (device, every GMRES iteration): gather r on the box into shared
 //     memory, forward and backward sweeps level by level, write the owned
 //     points (restricted prolongation, no atomics), then the projection P.
+//
+// Factor layout (level-major).  For each level the factors of its points form
+// one block: a forward part with the strictly lower entries (rows of the
+// pattern's lower slots, points contiguous within a row) and a backward part
+// with the strictly upper entries and the inverse pivots.  Each part of a
+// level is one contiguous, 16-byte aligned run, so one TMA bulk copy
+// (cp.async.bulk + mbarrier) brings it into shared memory while the previous
+// level is being computed; the dependent path touches shared memory only.
 #include <math.h>
 
 #include <algorithm>
-#include <map>
 #include <set>
 #include <tuple>
+#include <utility>
 
 #include "nks_internal.cuh"
+#include "nks_pattern.cuh"
 
 namespace nks {
-
-// ---------------------------------------------------------------------------
-// one row of the Jacobian dF/dX1 as a list of (offset, field, value)
-// ---------------------------------------------------------------------------
-
-struct RowCtx {
-    double a0[7], a1[7];  // dGc/dc1, dGc/deta1 at p (0) and p + e_J (1 + 2J), p - e_J (2 + 2J)
-    double a2, a3;        // dGeta/dc1, dGeta/deta1 at p
-    double Mp[3], Mm[3];  // edge mobilities M_{p + e_J/2}, M_{p - e_J/2}
-};
-
-// contributions of the linearised G_c at q = p + o (o = 0 or +-e_J) with weight w
-template <class Acc>
-__host__ __device__ inline void add_grow(Acc &acc, const DCoef &k, int d, double h, int ox, int oy, int oz, double w,
-                                         double a0, double a1)
-{
-    const double ih2 = 1.0 / (h * h);
-    double diag = a0 + k.gamma_c * d * ih2;
-    if (k.elastic) diag += 0.5 * d * k.eps0 * k.eps0 * k.lam;
-    acc(ox, oy, oz, 0, w * diag);
-    for (int J = 0; J < d; J++) {
-        const int ex = J == 0, ey = J == 1, ez = J == 2;
-        acc(ox + ex, oy + ey, oz + ez, 0, -w * 0.5 * k.gamma_c * ih2);
-        acc(ox - ex, oy - ey, oz - ez, 0, -w * 0.5 * k.gamma_c * ih2);
-    }
-    acc(ox, oy, oz, 1, w * a1);
-    if (k.elastic) {
-        const double t = w * k.eps0 * k.lam * 0.25 / h;  // G^3_c = -eps0 lam (sum_K Dhat_K u_K - d eps0 c ...)/2
-        for (int K = 0; K < d; K++) {
-            const int ex = K == 0, ey = K == 1, ez = K == 2;
-            acc(ox + ex, oy + ey, oz + ez, 2 + K, -t);
-            acc(ox - ex, oy - ey, oz - ez, 2 + K, +t);
-        }
-    }
-}
-
-// sigma_IJ(q) row, q = p + o, weight w (stress of eps(u) - eps0 (c - cbar) I)
-template <class Acc>
-__host__ __device__ inline void add_sigrow(Acc &acc, const DCoef &k, int d, double h, int ox, int oy, int oz, int I,
-                                           int J, double w)
-{
-    const double i2h = 0.5 / h;
-    if (I == J) {
-        for (int K = 0; K < d; K++) {
-            const int ex = K == 0, ey = K == 1, ez = K == 2;
-            const double cf = (K == I) ? k.C11 : k.C12;
-            acc(ox + ex, oy + ey, oz + ez, 2 + K, w * cf * i2h);
-            acc(ox - ex, oy - ey, oz - ez, 2 + K, -w * cf * i2h);
-        }
-        acc(ox, oy, oz, 0, -w * k.eps0 * k.lam);
-    } else {
-        const int jx = J == 0, jy = J == 1, jz = J == 2;
-        const int ix = I == 0, iy = I == 1, iz = I == 2;
-        acc(ox + jx, oy + jy, oz + jz, 2 + I, w * k.C44 * i2h);
-        acc(ox - jx, oy - jy, oz - jz, 2 + I, -w * k.C44 * i2h);
-        acc(ox + ix, oy + iy, oz + iz, 2 + J, w * k.C44 * i2h);
-        acc(ox - ix, oy - iy, oz - iz, 2 + J, -w * k.C44 * i2h);
-    }
-}
-
-// Row f of J at a point: c-row from F_c = (c1-c0)/dt - D M D G_c, eta-row from
-// F_eta = (eta1-eta0)/dt + G_eta, u_I-row from F_uI = sum_J Dhat_J sigma_IJ.
-// mode 1 (displacement-only system): c and eta rows are identity rows.
-template <class Acc>
-__host__ __device__ inline void jac_row(Acc &acc, int f, const DCoef &k, int d, double h, double dt, int mode,
-                                        const RowCtx &r)
-{
-    const double ih2 = 1.0 / (h * h);
-    if (f == 0) {
-        if (mode != 0) {
-            acc(0, 0, 0, 0, 1.0);
-            return;
-        }
-        acc(0, 0, 0, 0, 1.0 / dt);
-        double wc = 0.0;
-        for (int J = 0; J < d; J++) wc += (r.Mp[J] + r.Mm[J]) * ih2;
-        add_grow(acc, k, d, h, 0, 0, 0, wc, r.a0[0], r.a1[0]);
-        for (int J = 0; J < d; J++) {
-            const int ex = J == 0, ey = J == 1, ez = J == 2;
-            add_grow(acc, k, d, h, ex, ey, ez, -r.Mp[J] * ih2, r.a0[1 + 2 * J], r.a1[1 + 2 * J]);
-            add_grow(acc, k, d, h, -ex, -ey, -ez, -r.Mm[J] * ih2, r.a0[2 + 2 * J], r.a1[2 + 2 * J]);
-        }
-    } else if (f == 1) {
-        if (mode != 0) {
-            acc(0, 0, 0, 1, 1.0);
-            return;
-        }
-        acc(0, 0, 0, 1, 1.0 / dt + r.a3 + 3.0 * k.gamma_eta * d * ih2);
-        acc(0, 0, 0, 0, r.a2);
-        for (int J = 0; J < d; J++) {
-            const int ex = J == 0, ey = J == 1, ez = J == 2;
-            acc(ex, ey, ez, 1, -1.5 * k.gamma_eta * ih2);
-            acc(-ex, -ey, -ez, 1, -1.5 * k.gamma_eta * ih2);
-        }
-    } else {
-        const int I = f - 2;
-        const double i2h = 0.5 / h;
-        for (int J = 0; J < d; J++) {
-            const int ex = J == 0, ey = J == 1, ez = J == 2;
-            add_sigrow(acc, k, d, h, ex, ey, ez, I, J, i2h);
-            add_sigrow(acc, k, d, h, -ex, -ey, -ez, I, J, -i2h);
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// plan
-// ---------------------------------------------------------------------------
 
 struct SubInfo {
     int org[3];               // global coordinates of local (0,0,0) (may be negative: periodic)
     int L[3];                 // box extent
     int own0[3], own1[3];     // owned local range [own0, own1)
     int np, nlev;
-    long long lvl_off;        // into lvl_ptr (nlev + 1 entries)
-    long long pos_off;        // into lvl_lp / pos_of_lp (np entries)
-    long long fac_off;        // into the factor array (nslot * np)
+    long long lvl_off;        // into lvl_ptr / lvl_blk (nlev + 1 entries)
+    long long pos_off;        // into lvl_lp (np entries)
+    long long fac_off;        // into the factor array (elements)
     long long scr_off;        // into the global scratch vector (nf * np), when not in shared memory
 };
 
 struct RasPlan {
-    int nsub = 0, nslot = 0, threads = 128;
+    int nsub = 0, nslot = 0, nlow = 0, nup = 0;
+    int threads = 64;
     int maxnp = 0;
-    bool smem = true;
-    size_t smem_bytes = 0;
-    // device tables
-    char4 *tmpl = nullptr;          // (dx, dy, dz, fc) per slot, rows concatenated
-    short *slotmap = nullptr;       // [f][(dz+2)*25 + (dy+2)*5 + (dx+2)][fc]
-    int *upd_ptr = nullptr;         // [rowoff[f] + a] -> start in upd (size nslot + 1)
-    short2 *upd = nullptr;          // (b, c) pairs
+    long long maxblk = 0;           // largest forward or backward part of a level (elements)
+    long long fac_elems = 0;
+    long long total_np = 0;         // overlapped points of all subdomains
+    bool x_smem = true;
+    size_t smem_bytes = 0;          // dynamic shared memory of the apply kernel (FP64 factors)
     SubInfo *sub = nullptr;
-    int *lvl_ptr = nullptr, *lvl_lp = nullptr, *pos_of_lp = nullptr;
+    // runtime copies of the pattern for the assembly kernel
+    char4 *tmpl = nullptr;          // (dx, dy, dz, field) per slot
+    short *st = nullptr;            // storage row per slot
+    short *slotmap = nullptr;       // [f][(dz+2)*25 + (dy+2)*5 + (dx+2)][field] -> slot in row f, or -1
+    int *upd_ptr = nullptr;         // ILU(0) update pairs of each lower slot
+    short2 *upd = nullptr;          // (later slot b of row i, slot c of the same column in row k)
+    int *lvl_ptr = nullptr, *lvl_lp = nullptr;
+    long long *lvl_blk = nullptr;
     double *fac = nullptr;
     double *scratch = nullptr;
-    double *proj = nullptr;         // projection coefficients
-    int rowoff[kMaxNf + 1];
-    int diag[kMaxNf];
+    double *proj = nullptr;         // projection sums
     int nmodes = 1;                 // null modes per displacement component
     int evenmask = 0;
     bool attr_set = false;
 };
 
-namespace {
-
-struct StructAcc {
-    std::set<std::tuple<int, int, int, int>> *s;
-    void operator()(int dx, int dy, int dz, int fc, double) { s->insert(std::make_tuple(dz, dy, dx, fc)); }
+template <int D, int NF>
+struct Pat {
+    static constexpr Pattern v = make_pattern<D, NF>();
 };
 
-}  // namespace
+static Pattern compile_time_pattern(int d, int nf)
+{
+    switch (d * 10 + nf) {
+    case 12: return Pat<1, 2>::v;
+    case 13: return Pat<1, 3>::v;
+    case 22: return Pat<2, 2>::v;
+    case 24: return Pat<2, 4>::v;
+    case 32: return Pat<3, 2>::v;
+    case 35: return Pat<3, 5>::v;
+    }
+    return Pattern{};
+}
+
+__host__ __device__ static inline long long pad4(long long n) { return (n + 3) & ~3LL; }
+__host__ __device__ static inline size_t pad16(size_t n) { return (n + 15) & ~(size_t)15; }
+
+// dynamic shared memory of the apply kernel: barriers, point table, two level
+// buffers and (when it fits) the sub-vector
+static size_t apply_smem(const RasPlan *R, int nf, size_t tsize, bool with_x)
+{
+    size_t b = 16 + pad16((size_t)R->maxnp * sizeof(int)) + 2 * pad16((size_t)R->maxblk * tsize);
+    if (with_x) b += pad16((size_t)R->maxnp * nf * tsize);
+    return b;
+}
 
 int ras_plan_create(Problem *P, std::string &err)
 {
     RasPlan *R = new RasPlan();
     P->ras = R;
     const int d = P->g.dim, nf = P->nf;
-    // ---- templates (structural pattern of each row field)
-    DCoef kk = P->k;
-    kk.C11 = kk.C12 = kk.C44 = kk.lam = 1.0;  // structural pass: every coefficient non-zero
-    kk.gamma_c = kk.gamma_eta = kk.eps0 = 1.0;
-    RowCtx rc;
-    for (int i = 0; i < 7; i++) rc.a0[i] = rc.a1[i] = 1.0;
-    rc.a2 = rc.a3 = 1.0;
-    for (int J = 0; J < 3; J++) rc.Mp[J] = rc.Mm[J] = 1.0;
-    std::vector<std::vector<std::tuple<int, int, int, int>>> rows(nf);
-    int total = 0;
-    for (int f = 0; f < nf; f++) {
-        std::set<std::tuple<int, int, int, int>> s;
-        StructAcc acc{&s};
-        jac_row(acc, f, kk, d, 1.0, 1.0, 0, rc);
-        rows[f].assign(s.begin(), s.end());  // lexicographic (dz, dy, dx, fc) = column order
-        R->rowoff[f] = total;
-        total += (int)rows[f].size();
-        R->diag[f] = -1;
-        for (size_t a = 0; a < rows[f].size(); a++) {
-            auto [dz, dy, dx, fc] = rows[f][a];
-            if (dz == 0 && dy == 0 && dx == 0 && fc == f) R->diag[f] = (int)a;
-        }
-        if (R->diag[f] < 0 || rows[f].size() > (size_t)kMaxRow) {
-            err = "internal: Jacobian row template";
-            return NKS_EINVAL;
-        }
-        // every column before the diagonal must lie on an earlier wavefront level (or the same point)
-        for (int a = 0; a < R->diag[f]; a++) {
-            auto [dz, dy, dx, fc] = rows[f][a];
-            const int lv = dx + 2 * dy + 4 * dz;
-            if (!((dx == 0 && dy == 0 && dz == 0) || lv < 0)) {
+    const Pattern CP = compile_time_pattern(d, nf);
+    if (CP.nf != nf) {
+        err = "internal: no Jacobian pattern for this dimension";
+        return NKS_EINVAL;
+    }
+    // every column left of the diagonal lies on an earlier wavefront level or at the same point
+    for (int f = 0; f < nf; f++)
+        for (int a = 0; a < CP.diag[f]; a++) {
+            const int i = CP.rowoff[f] + a;
+            const int lv = CP.dx[i] + 2 * CP.dy[i] + 4 * CP.dz[i];
+            if (!((CP.dx[i] == 0 && CP.dy[i] == 0 && CP.dz[i] == 0) || lv < 0)) {
                 err = "internal: wavefront ordering";
                 return NKS_EINVAL;
             }
         }
-    }
-    R->rowoff[nf] = total;
-    R->nslot = total;
-    std::vector<char4> tmpl(total);
-    std::vector<short> slotmap((size_t)nf * 125 * nf, -1);
+    R->nslot = CP.rowoff[nf];
+    R->nlow = CP.nlow;
+    R->nup = CP.nup;
+    const int per_pt = CP.nlow + CP.nup + nf;
+    // runtime tables for the assembly kernel
+    std::vector<char4> tmpl(R->nslot);
+    std::vector<short> st(R->nslot), slotmap((size_t)nf * 125 * nf, -1);
     for (int f = 0; f < nf; f++)
-        for (size_t a = 0; a < rows[f].size(); a++) {
-            auto [dz, dy, dx, fc] = rows[f][a];
-            tmpl[R->rowoff[f] + a] = make_char4((signed char)dx, (signed char)dy, (signed char)dz, (signed char)fc);
-            slotmap[((size_t)f * 125 + (dz + 2) * 25 + (dy + 2) * 5 + (dx + 2)) * nf + fc] = (short)a;
+        for (int a = 0; a < CP.len[f]; a++) {
+            const int i = CP.rowoff[f] + a;
+            tmpl[i] = make_char4(CP.dx[i], CP.dy[i], CP.dz[i], CP.fc[i]);
+            st[i] = CP.st[i];
+            slotmap[((size_t)f * 125 + (CP.dz[i] + 2) * 25 + (CP.dy[i] + 2) * 5 + (CP.dx[i] + 2)) * nf + CP.fc[i]] =
+                (short)a;
         }
-    // ---- ILU(0) update lists: for row f, lower slot a (row k = p + o_a, field f_a), every later
-    // slot b of row f whose column also appears in row k gives (b, slot c of that column in row k)
-    std::vector<int> upd_ptr(total + 1, 0);
+    // ILU(0) update lists: for row f and lower slot a (row k = p + o_a, field f_a), every
+    // later slot b of row f whose column also appears among the upper entries of row k
+    std::vector<int> upd_ptr(R->nslot + 1, 0);
     std::vector<short2> upd;
     for (int f = 0; f < nf; f++)
-        for (int a = 0; a < (int)rows[f].size(); a++) {
-            upd_ptr[R->rowoff[f] + a] = (int)upd.size();
-            if (a >= R->diag[f]) continue;
-            auto [az, ay, ax, afc] = rows[f][a];
-            for (int b = a + 1; b < (int)rows[f].size(); b++) {
-                auto [bz, by, bx, bfc] = rows[f][b];
-                const int rx = bx - ax, ry = by - ay, rz = bz - az;
-                if (abs(rx) > 2 || abs(ry) > 2 || abs(rz) > 2) continue;
-                const short c = slotmap[((size_t)afc * 125 + (rz + 2) * 25 + (ry + 2) * 5 + (rx + 2)) * nf + bfc];
-                if (c >= 0) upd.push_back(make_short2((short)b, c));
+        for (int a = 0; a < CP.len[f]; a++) {
+            const int ia = CP.rowoff[f] + a;
+            upd_ptr[ia] = (int)upd.size();
+            if (a >= CP.diag[f]) continue;
+            const int fk = CP.fc[ia];
+            for (int b = a + 1; b < CP.len[f]; b++) {
+                const int ib = CP.rowoff[f] + b;
+                const int rx = CP.dx[ib] - CP.dx[ia], ry = CP.dy[ib] - CP.dy[ia], rz = CP.dz[ib] - CP.dz[ia];
+                for (int c = CP.diag[fk] + 1; c < CP.len[fk]; c++) {
+                    const int ic = CP.rowoff[fk] + c;
+                    if (CP.dx[ic] == rx && CP.dy[ic] == ry && CP.dz[ic] == rz && CP.fc[ic] == CP.fc[ib]) {
+                        upd.push_back(make_short2((short)b, (short)c));
+                        break;
+                    }
+                }
             }
         }
-    upd_ptr[total] = (int)upd.size();
+    upd_ptr[R->nslot] = (int)upd.size();
 
-    // ---- subdomains
     int sub[3] = {1, 1, 1};
     for (int J = 0; J < d; J++) sub[J] = std::max(1, P->opts.sub[J]);
     const int delta = P->opts.overlap;
     R->nsub = sub[0] * sub[1] * sub[2];
     std::vector<SubInfo> infos(R->nsub);
-    std::vector<int> lvl_ptr, lvl_lp, pos_of_lp;
+    std::vector<int> lvl_ptr, lvl_lp;
+    std::vector<long long> lvl_blk;
     long long fac_off = 0, scr_off = 0;
     for (int s2 = 0; s2 < sub[2]; s2++)
         for (int s1 = 0; s1 < sub[1]; s1++)
@@ -286,43 +198,51 @@ int ras_plan_create(Problem *P, std::string &err)
                 }
                 si.np = si.L[0] * si.L[1] * si.L[2];
                 R->maxnp = std::max(R->maxnp, si.np);
-                // wavefront levels
+                R->total_np += si.np;
                 const int nlev = (si.L[0] - 1) + 2 * (si.L[1] - 1) + 4 * (si.L[2] - 1) + 1;
                 si.nlev = nlev;
                 si.lvl_off = (long long)lvl_ptr.size();
                 si.pos_off = (long long)lvl_lp.size();
+                si.fac_off = fac_off;
                 std::vector<std::vector<int>> bylev(nlev);
                 for (int lz = 0; lz < si.L[2]; lz++)
                     for (int ly = 0; ly < si.L[1]; ly++)
                         for (int lx = 0; lx < si.L[0]; lx++)
                             bylev[lx + 2 * ly + 4 * lz].push_back(lx + si.L[0] * (ly + si.L[1] * lz));
-                std::vector<int> pos(si.np);
                 int cnt = 0;
+                long long blk = 0;
                 for (int l = 0; l < nlev; l++) {
                     lvl_ptr.push_back(cnt);
+                    lvl_blk.push_back(blk);
                     for (int lp : bylev[l]) {
-                        pos[lp] = cnt;
                         lvl_lp.push_back(lp);
                         cnt++;
                     }
+                    const long long cp = pad4((long long)bylev[l].size());
+                    R->maxblk = std::max(R->maxblk, std::max<long long>(CP.nlow, CP.nup + nf) * cp);
+                    R->threads = std::max(R->threads, (int)((bylev[l].size() + 31) / 32 * 32));
+                    blk += (long long)per_pt * cp;
                 }
                 lvl_ptr.push_back(cnt);
-                for (int lp = 0; lp < si.np; lp++) pos_of_lp.push_back(pos[lp]);
-                si.fac_off = fac_off;
-                fac_off += (long long)R->nslot * si.np;
+                lvl_blk.push_back(blk);
+                fac_off += blk;
                 si.scr_off = scr_off;
                 scr_off += (long long)nf * si.np;
             }
-    // shared memory for the sub-vector when it fits
-    R->smem_bytes = (size_t)R->maxnp * nf * sizeof(double);
-    R->smem = R->smem_bytes <= 200 * 1024;
+    R->threads = std::min(R->threads, 256);
+    R->fac_elems = fac_off;
+    R->x_smem = apply_smem(R, nf, sizeof(double), true) <= 227 * 1024;
+    R->smem_bytes = apply_smem(R, nf, sizeof(double), R->x_smem);
+    if (R->smem_bytes > 227 * 1024) {
+        err = "decomposition: subdomain boxes too large for the Schwarz kernel (use more subdomains)";
+        return NKS_EINVAL;
+    }
     // null modes of the centred-difference strain: sign patterns over the even axes
     R->evenmask = 0;
     for (int J = 0; J < d; J++)
         if (P->g.n[J] % 2 == 0) R->evenmask |= 1 << J;
     R->nmodes = 1 << __builtin_popcount(R->evenmask);
 
-    // ---- upload
     auto up = [&](void **dst, const void *src, size_t bytes) -> bool {
         *dst = P->dalloc(bytes);
         if (!*dst) return false;
@@ -330,25 +250,29 @@ int ras_plan_create(Problem *P, std::string &err)
         return true;
     };
     bool ok = up((void **)&R->tmpl, tmpl.data(), tmpl.size() * sizeof(char4)) &&
+              up((void **)&R->st, st.data(), st.size() * sizeof(short)) &&
               up((void **)&R->slotmap, slotmap.data(), slotmap.size() * sizeof(short)) &&
               up((void **)&R->upd_ptr, upd_ptr.data(), upd_ptr.size() * sizeof(int)) &&
               up((void **)&R->upd, upd.data(), std::max<size_t>(1, upd.size()) * sizeof(short2)) &&
               up((void **)&R->sub, infos.data(), infos.size() * sizeof(SubInfo)) &&
               up((void **)&R->lvl_ptr, lvl_ptr.data(), lvl_ptr.size() * sizeof(int)) &&
-              up((void **)&R->lvl_lp, lvl_lp.data(), lvl_lp.size() * sizeof(int)) &&
-              up((void **)&R->pos_of_lp, pos_of_lp.data(), pos_of_lp.size() * sizeof(int));
+              up((void **)&R->lvl_blk, lvl_blk.data(), lvl_blk.size() * sizeof(long long)) &&
+              up((void **)&R->lvl_lp, lvl_lp.data(), lvl_lp.size() * sizeof(int));
     if (!ok) {
         err = "out of device memory (Schwarz tables)";
         return NKS_ENOMEM;
     }
     R->fac = (double *)P->dalloc(sizeof(double) * (size_t)fac_off);
     R->proj = (double *)P->dalloc(sizeof(double) * 64);
-    if (!R->smem) R->scratch = (double *)P->dalloc(sizeof(double) * (size_t)scr_off);
-    if (!R->fac || !R->proj || (!R->smem && !R->scratch)) {
+    if (!R->x_smem) R->scratch = (double *)P->dalloc(sizeof(double) * (size_t)scr_off);
+    if (!R->fac || !R->proj || (!R->x_smem && !R->scratch)) {
         err = "out of device memory (Schwarz factors)";
         return NKS_ENOMEM;
     }
+    cudaMemset(R->fac, 0, sizeof(double) * (size_t)fac_off);  // padding entries stay 0
     P->stats.factor_bytes = (long long)(sizeof(double) * (size_t)fac_off);
+    P->stats.schwarz_points = (double)R->total_np;
+    ras_work(P, &P->stats.schwarz_bytes, &P->stats.schwarz_flops);
     return NKS_OK;
 }
 
@@ -364,60 +288,75 @@ void ras_plan_destroy(Problem *P)
 
 namespace {
 
-struct Tables {
-    int rowoff[kMaxNf + 1];
-    int diag[kMaxNf];
-    int nf;
-};
+template <int B, int E, class Fn>
+__device__ __forceinline__ void static_for(Fn &&fn)
+{
+    if constexpr (B < E) {
+        fn(std::integral_constant<int, B>{});
+        static_for<B + 1, E>(fn);
+    }
+}
 
-__device__ inline bool inbox(const SubInfo &si, int lx, int ly, int lz)
+__host__ __device__ inline bool inbox(const SubInfo &si, int lx, int ly, int lz)
 {
     return lx >= 0 && lx < si.L[0] && ly >= 0 && ly < si.L[1] && lz >= 0 && lz < si.L[2];
 }
 
+struct FacTables {
+    int rowoff[kMaxNf + 1], len[kMaxNf], diag[kMaxNf];
+    int nlow, nup, nf;
+};
+
+// adds the contributions of one Jacobian row into a slot-indexed row (columns
+// outside the box dropped)
 struct DevAcc {
     double *vals;
-    const short *slotmap;  // row f block
+    const short *slotmap;  // block of row f
     int nf, lx, ly, lz;
     const SubInfo *si;
-    __device__ void operator()(int dx, int dy, int dz, int fc, double v)
+    __host__ __device__ void operator()(int dx, int dy, int dz, int fc, double v)
     {
-        if (!inbox(*si, lx + dx, ly + dy, lz + dz)) return;  // column outside the overlapped box: dropped
+        if (!inbox(*si, lx + dx, ly + dy, lz + dz)) return;
         const int s = slotmap[((dz + 2) * 25 + (dy + 2) * 5 + (dx + 2)) * nf + fc];
         if (s >= 0) vals[s] += v;
     }
 };
 
-__global__ void k_ras_factor(DGrid g, DCoef k, double dt, int mode, Tables T, const SubInfo *__restrict__ subs,
-                             const int *__restrict__ lvl_ptr, const int *__restrict__ lvl_lp,
-                             const int *__restrict__ pos_of_lp, const char4 *__restrict__ tmpl,
-                             const short *__restrict__ slotmap, const int *__restrict__ upd_ptr,
-                             const short2 *__restrict__ upd, const double *__restrict__ part,
-                             const double *__restrict__ mob, double *__restrict__ fac, int *__restrict__ flag)
+// Fused assembly + ILU(0) (textbook IKJ order within a row) of J restricted to
+// each overlapped box.  Rows of earlier points are final when a level starts.
+__global__ void k_ras_factor(DGrid g, DCoef k, double dt, int mode, FacTables T, const SubInfo *__restrict__ subs,
+                             const int *__restrict__ lvl_ptr, const long long *__restrict__ lvl_blk,
+                             const int *__restrict__ lvl_lp, const char4 *__restrict__ tmpl,
+                             const short *__restrict__ st, const short *__restrict__ slotmap,
+                             const int *__restrict__ upd_ptr, const short2 *__restrict__ upd,
+                             const double *__restrict__ part, const double *__restrict__ mob,
+                             double *__restrict__ fac, int *__restrict__ flag)
 {
     const SubInfo si = subs[blockIdx.x];
-    const int nf = T.nf, d = g.dim;
-    const int np = si.np;
-    double *F = fac + si.fac_off;
-    const int *lp_of = lvl_lp + si.pos_off;
-    const int *posof = pos_of_lp + si.pos_off;
+    const int nf = T.nf, D = g.dim;
     const int *lptr = lvl_ptr + si.lvl_off;
+    const long long *lblk = lvl_blk + si.lvl_off;
+    const int *lp_of = lvl_lp + si.pos_off;
+    double *F = fac + si.fac_off;
     const long long N = g.N;
     double vals[kMaxRow];
     for (int lev = 0; lev < si.nlev; lev++) {
+        const long long cp = pad4((long long)(lptr[lev + 1] - lptr[lev]));
+        double *blk = F + lblk[lev];
         for (int i = lptr[lev] + threadIdx.x; i < lptr[lev + 1]; i += blockDim.x) {
+            const int kk = i - lptr[lev];
             const int lp = lp_of[i];
             const int lx = lp % si.L[0], ly = (lp / si.L[0]) % si.L[1], lz = lp / (si.L[0] * si.L[1]);
             const int gx = wrapi(si.org[0] + lx, g.n[0]), gy = wrapi(si.org[1] + ly, g.n[1]),
                       gz = wrapi(si.org[2] + lz, g.n[2]);
             const long long gp = index_of(g, gx, gy, gz);
-            RowCtx rc;
+            RowCtx rc{};
             if (mode == 0) {
                 rc.a0[0] = part[gp];
                 rc.a1[0] = part[N + gp];
                 rc.a2 = part[2 * N + gp];
                 rc.a3 = part[3 * N + gp];
-                for (int J = 0; J < d; J++) {
+                for (int J = 0; J < D; J++) {
                     const long long pp = nbrJ(g, gx, gy, gz, J, +1), pm = nbrJ(g, gx, gy, gz, J, -1);
                     rc.a0[1 + 2 * J] = part[pp];
                     rc.a1[1 + 2 * J] = part[N + pp];
@@ -428,101 +367,236 @@ __global__ void k_ras_factor(DGrid g, DCoef k, double dt, int mode, Tables T, co
                 }
             }
             for (int f = 0; f < nf; f++) {
-                const int len = T.rowoff[f + 1] - T.rowoff[f];
+                const int len = T.len[f], r0 = T.rowoff[f];
                 for (int a = 0; a < len; a++) vals[a] = 0.0;
                 DevAcc acc{vals, slotmap + (size_t)f * 125 * nf, nf, lx, ly, lz, &si};
-                jac_row(acc, f, k, d, g.h, dt, mode, rc);
-                // ILU(0) elimination of row (p, f) with the finished rows of earlier points / fields
+                jac_row(acc, f, k, D, g.h, dt, mode, rc);
                 for (int a = 0; a < T.diag[f]; a++) {
-                    const char4 o = tmpl[T.rowoff[f] + a];
-                    if (!inbox(si, lx + o.x, ly + o.y, lz + o.z)) continue;
-                    const int lpk = lp + o.x + si.L[0] * (o.y + si.L[1] * o.z);
-                    const int posk = posof[lpk];
+                    const char4 o = tmpl[r0 + a];
+                    const int nx = lx + o.x, ny = ly + o.y, nz = lz + o.z;
+                    if (!inbox(si, nx, ny, nz)) continue;  // stays exactly 0
                     const int fk = o.w;
-                    const double dk = F[(size_t)(T.rowoff[fk] + T.diag[fk]) * np + posk];
-                    const double l = vals[a] / dk;
+                    // level-major position of the earlier point (points of a level are stored in lp order)
+                    const int lv = nx + 2 * ny + 4 * nz;
+                    const int lpk = nx + si.L[0] * (ny + si.L[1] * nz);
+                    int lo = lptr[lv], hi = lptr[lv + 1] - 1;
+                    while (lo < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        if (lp_of[mid] < lpk) lo = mid + 1;
+                        else hi = mid;
+                    }
+                    const int qk = lo - lptr[lv];
+                    const long long qcp = pad4((long long)(lptr[lv + 1] - lptr[lv]));
+                    const double *U = F + lblk[lv] + (long long)T.nlow * qcp;  // backward part of that level
+                    const int rk = T.rowoff[fk];
+                    const double l = vals[a] * U[(long long)st[rk + T.diag[fk]] * qcp + qk];  // times 1/u_kk
                     vals[a] = l;
-                    for (int u = upd_ptr[T.rowoff[f] + a]; u < upd_ptr[T.rowoff[f] + a + 1]; u++) {
+                    // a_ib -= l * u_kb for every later column b of row i present in row k
+                    for (int u = upd_ptr[r0 + a]; u < upd_ptr[r0 + a + 1]; u++) {
                         const short2 bc = upd[u];
-                        vals[bc.x] -= l * F[(size_t)(T.rowoff[fk] + bc.y) * np + posk];
+                        vals[bc.x] -= l * U[(long long)st[rk + bc.y] * qcp + qk];
                     }
                 }
-                if (vals[T.diag[f]] == 0.0 || !isfinite(vals[T.diag[f]])) atomicOr(flag, 2);
-                for (int a = 0; a < len; a++) F[(size_t)(T.rowoff[f] + a) * np + i] = vals[a];
+                const double piv = vals[T.diag[f]];
+                if (piv == 0.0 || !isfinite(piv)) atomicOr(flag, 2);
+                for (int a = 0; a < len; a++) {
+                    const int ia = r0 + a;
+                    if (a < T.diag[f]) blk[(long long)st[ia] * cp + kk] = vals[a];
+                    else if (a > T.diag[f]) blk[((long long)T.nlow + st[ia]) * cp + kk] = vals[a];
+                    else blk[((long long)T.nlow + st[ia]) * cp + kk] = 1.0 / piv;
+                }
             }
         }
         __syncthreads();
     }
 }
 
-__global__ void k_ras_apply(DGrid g, Tables T, const SubInfo *__restrict__ subs, const int *__restrict__ lvl_ptr,
-                            const int *__restrict__ lvl_lp, const char4 *__restrict__ tmpl,
-                            const double *__restrict__ fac, const double *__restrict__ r, double *__restrict__ z,
-                            double *__restrict__ scratch, int use_smem)
+// ---- TMA bulk copies and mbarriers (inline PTX) ---------------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
 {
-    extern __shared__ double xs[];
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait: gives up after ~2^31 clocks (about a second) and reports it
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+{
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > (1LL << 31)) return false;
+    return true;
+}
+
+// is the neighbour at the compile-time offset (DX, DY, DZ) inside the box?
+template <int DX, int DY, int DZ>
+__device__ __forceinline__ bool nb_inbox(int lx, int ly, int lz, const SubInfo &si)
+{
+    bool ok = true;
+    if constexpr (DX < 0) ok = ok && lx >= -DX;
+    if constexpr (DX > 0) ok = ok && lx < si.L[0] - DX;
+    if constexpr (DY < 0) ok = ok && ly >= -DY;
+    if constexpr (DY > 0) ok = ok && ly < si.L[1] - DY;
+    if constexpr (DZ < 0) ok = ok && lz >= -DZ;
+    if constexpr (DZ > 0) ok = ok && lz < si.L[2] - DZ;
+    return ok;
+}
+
+// s -= sum over pattern slots [B, E) of the stored entries times x at their
+// columns.  A column outside the box has a stored entry of exactly 0 (dropped
+// at assembly; no ILU(0) update reaches it), so its product is read at the
+// point itself and contributes nothing: no branch, no load depends on x.
+template <int D, int NF, int B, int E, typename T>
+__device__ __forceinline__ T row_dot(T s, const T *__restrict__ part, long long cp, int k, const T *x, int np, int lp,
+                                     int lx, int ly, int lz, const SubInfo &si, int sy, int sz)
+{
+    static_for<B, E>([&](auto ic) {
+        constexpr int a = decltype(ic)::value;
+        constexpr int dx = Pat<D, NF>::v.dx[a], dy = Pat<D, NF>::v.dy[a], dz = Pat<D, NF>::v.dz[a];
+        constexpr int fc = Pat<D, NF>::v.fc[a];
+        constexpr int row = Pat<D, NF>::v.st[a];
+        const bool ok = nb_inbox<dx, dy, dz>(lx, ly, lz, si);
+        const int idx = ok ? lp + dx + sy * dy + sz * dz : lp;
+        s -= part[row * cp + k] * x[fc * np + idx];
+    });
+    return s;
+}
+
+template <int D, int NF, typename T, typename TV>
+__global__ void k_ras_apply(DGrid g, const SubInfo *__restrict__ subs, const int *__restrict__ lvl_ptr,
+                            const long long *__restrict__ lvl_blk, const int *__restrict__ lvl_lp,
+                            const T *__restrict__ fac, const TV *__restrict__ r, TV *__restrict__ z,
+                            T *__restrict__ scratch, int x_in_smem, int maxnp, long long maxblk, int *flag)
+{
+    constexpr Pattern PT = Pat<D, NF>::v;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    int *lps = reinterpret_cast<int *>(smem + 16);
+    T *buf0 = reinterpret_cast<T *>(smem + 16 + pad16((size_t)maxnp * sizeof(int)));
+    T *buf1 = reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(buf0) + pad16((size_t)maxblk * sizeof(T)));
     const SubInfo si = subs[blockIdx.x];
-    const int nf = T.nf;
-    const int np = si.np;
-    const double *F = fac + si.fac_off;
-    const int *lp_of = lvl_lp + si.pos_off;
+    T *x = x_in_smem ? reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(buf1) + pad16((size_t)maxblk * sizeof(T)))
+                     : scratch + si.scr_off;
+    const int np = si.np, nlev = si.nlev;
     const int *lptr = lvl_ptr + si.lvl_off;
-    double *x = use_smem ? xs : scratch + si.scr_off;
+    const long long *lblk = lvl_blk + si.lvl_off;
+    const T *F = fac + si.fac_off;
     const long long N = g.N;
-    // gather R_i^delta r
-    for (int lp = threadIdx.x; lp < np; lp += blockDim.x) {
-        const int lx = lp % si.L[0], ly = (lp / si.L[0]) % si.L[1], lz = lp / (si.L[0] * si.L[1]);
-        const long long gp = index_of(g, wrapi(si.org[0] + lx, g.n[0]), wrapi(si.org[1] + ly, g.n[1]),
-                                      wrapi(si.org[2] + lz, g.n[2]));
-        for (int f = 0; f < nf; f++) x[f * np + lp] = r[f * N + gp];
+    const int sy = si.L[0], sz = si.L[0] * si.L[1];
+    const int tid = threadIdx.x;
+    const int nuse = 2 * nlev;  // forward parts of levels 0..nlev-1, then backward parts of nlev-1..0
+
+    // the copy of use `it` into buffer it & 1
+    auto issue = [&](int it) {
+        const int lev = it < nlev ? it : 2 * nlev - 1 - it;
+        const long long cp = pad4((long long)(lptr[lev + 1] - lptr[lev]));
+        const T *src = F + lblk[lev] + (it < nlev ? 0 : (long long)PT.nlow * cp);
+        const uint32_t bytes = (uint32_t)((it < nlev ? PT.nlow : PT.nup + NF) * cp * (long long)sizeof(T));
+        uint64_t *b = &bar[it & 1];
+        fence_proxy_async();
+        mbar_expect_tx(b, bytes);
+        bulk_g2s((it & 1) ? buf1 : buf0, src, bytes, b);
+    };
+
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
     }
     __syncthreads();
-    // forward sweep: L y = b (unit lower)
-    for (int lev = 0; lev < si.nlev; lev++) {
-        for (int i = lptr[lev] + threadIdx.x; i < lptr[lev + 1]; i += blockDim.x) {
-            const int lp = lp_of[i];
-            const int lx = lp % si.L[0], ly = (lp / si.L[0]) % si.L[1], lz = lp / (si.L[0] * si.L[1]);
-            for (int f = 0; f < nf; f++) {
-                double s = x[f * np + lp];
-                for (int a = 0; a < T.diag[f]; a++) {
-                    const char4 o = tmpl[T.rowoff[f] + a];
-                    if (!inbox(si, lx + o.x, ly + o.y, lz + o.z)) continue;
-                    const int lpk = lp + o.x + si.L[0] * (o.y + si.L[1] * o.z);
-                    s -= F[(size_t)(T.rowoff[f] + a) * np + i] * x[o.w * np + lpk];
-                }
-                x[f * np + lp] = s;
-            }
-        }
-        __syncthreads();
+    if (tid == 0) issue(0);
+    for (int i = tid; i < np; i += blockDim.x) lps[i] = lvl_lp[si.pos_off + i];
+    // gather R_i^delta r
+    for (int lp = tid; lp < np; lp += blockDim.x) {
+        const int lx = lp % si.L[0], ly = (lp / si.L[0]) % si.L[1], lz = lp / sz;
+        const long long gp = index_of(g, wrapi(si.org[0] + lx, g.n[0]), wrapi(si.org[1] + ly, g.n[1]),
+                                      wrapi(si.org[2] + lz, g.n[2]));
+#pragma unroll
+        for (int f = 0; f < NF; f++) x[f * np + lp] = (T)r[f * N + gp];
     }
-    // backward sweep: U x = y
-    for (int lev = si.nlev - 1; lev >= 0; lev--) {
-        for (int i = lptr[lev] + threadIdx.x; i < lptr[lev + 1]; i += blockDim.x) {
-            const int lp = lp_of[i];
-            const int lx = lp % si.L[0], ly = (lp / si.L[0]) % si.L[1], lz = lp / (si.L[0] * si.L[1]);
-            for (int f = nf - 1; f >= 0; f--) {
-                const int len = T.rowoff[f + 1] - T.rowoff[f];
-                double s = x[f * np + lp];
-                for (int a = T.diag[f] + 1; a < len; a++) {
-                    const char4 o = tmpl[T.rowoff[f] + a];
-                    if (!inbox(si, lx + o.x, ly + o.y, lz + o.z)) continue;
-                    const int lpk = lp + o.x + si.L[0] * (o.y + si.L[1] * o.z);
-                    s -= F[(size_t)(T.rowoff[f] + a) * np + i] * x[o.w * np + lpk];
+    __syncthreads();
+    bool failed = false;
+    for (int it = 0; it < nuse; it++) {
+        if (tid == 0 && it + 1 < nuse) issue(it + 1);
+        const bool ok = mbar_wait_bounded(&bar[it & 1], (uint32_t)((it >> 1) & 1));
+        const int lev = it < nlev ? it : 2 * nlev - 1 - it;
+        const int base = lptr[lev], cnt = lptr[lev + 1] - base;
+        const long long cp = pad4((long long)cnt);
+        const T *B = (it & 1) ? buf1 : buf0;
+        if (ok) {
+            for (int kk = tid; kk < cnt; kk += blockDim.x) {
+                const int lp = lps[base + kk];
+                const int lx = lp % si.L[0], ly = (lp / si.L[0]) % si.L[1], lz = lp / sz;
+                if (it < nlev) {  // forward: L y = b (unit lower triangular)
+                    static_for<0, NF>([&](auto fi) {
+                        constexpr int f = decltype(fi)::value;
+                        constexpr int b0 = PT.rowoff[f], e0 = PT.rowoff[f] + PT.diag[f];
+                        x[f * np + lp] = row_dot<D, NF, b0, e0, T>(x[f * np + lp], B, cp, kk, x, np, lp, lx, ly, lz,
+                                                                   si, sy, sz);
+                    });
+                } else {  // backward: U x = y
+                    static_for<0, NF>([&](auto fi) {
+                        constexpr int f = NF - 1 - decltype(fi)::value;
+                        constexpr int b0 = PT.rowoff[f] + PT.diag[f] + 1, e0 = PT.rowoff[f] + PT.len[f];
+                        const T s = row_dot<D, NF, b0, e0, T>(x[f * np + lp], B, cp, kk, x, np, lp, lx, ly, lz, si,
+                                                              sy, sz);
+                        x[f * np + lp] = s * B[(long long)(PT.nup + f) * cp + kk];
+                    });
                 }
-                x[f * np + lp] = s / F[(size_t)(T.rowoff[f] + T.diag[f]) * np + i];
             }
         }
-        __syncthreads();
+        failed = __syncthreads_or(!ok);
+        if (failed) break;
+    }
+    if (failed) {
+        // a copy never completed: report it, let outstanding copies land (bounded), leave
+        if (tid == 0) {
+            atomicOr(flag, 4);
+            mbar_wait_bounded(&bar[0], 0);
+            mbar_wait_bounded(&bar[1], 0);
+        }
+        return;
     }
     // restricted prolongation: owned points only
-    for (int lp = threadIdx.x; lp < np; lp += blockDim.x) {
-        const int lx = lp % si.L[0], ly = (lp / si.L[0]) % si.L[1], lz = lp / (si.L[0] * si.L[1]);
+    for (int lp = tid; lp < np; lp += blockDim.x) {
+        const int lx = lp % si.L[0], ly = (lp / si.L[0]) % si.L[1], lz = lp / sz;
         if (lx < si.own0[0] || lx >= si.own1[0] || ly < si.own0[1] || ly >= si.own1[1] || lz < si.own0[2] ||
             lz >= si.own1[2])
             continue;
         const long long gp = index_of(g, wrapi(si.org[0] + lx, g.n[0]), wrapi(si.org[1] + ly, g.n[1]),
                                       wrapi(si.org[2] + lz, g.n[2]));
-        for (int f = 0; f < nf; f++) z[f * N + gp] = x[f * np + lp];
+#pragma unroll
+        for (int f = 0; f < NF; f++) z[f * N + gp] = (TV)x[f * np + lp];
     }
 }
 
@@ -592,25 +666,56 @@ __global__ void k_proj_sub(DGrid g, int nf, int evenmask, int nmodes, const doub
     }
 }
 
-Tables tables_of(const Problem *P)
+void launch_factor(Problem *P, int mode)
 {
-    Tables T;
-    for (int f = 0; f <= P->nf; f++) T.rowoff[f] = P->ras->rowoff[f];
-    for (int f = 0; f < P->nf; f++) T.diag[f] = P->ras->diag[f];
+    RasPlan *R = P->ras;
+    const Pattern CP = compile_time_pattern(P->g.dim, P->nf);
+    FacTables T{};
+    for (int f = 0; f <= P->nf; f++) T.rowoff[f] = CP.rowoff[f];
+    for (int f = 0; f < P->nf; f++) {
+        T.len[f] = CP.len[f];
+        T.diag[f] = CP.diag[f];
+    }
+    T.nlow = CP.nlow;
+    T.nup = CP.nup;
     T.nf = P->nf;
-    return T;
+    k_ras_factor<<<R->nsub, 64, 0, P->stream>>>(P->g, P->k, P->cur_dt, mode, T, R->sub, R->lvl_ptr, R->lvl_blk,
+                                                R->lvl_lp, R->tmpl, R->st, R->slotmap, R->upd_ptr, R->upd, P->part,
+                                                P->mob, R->fac, P->dflag);
+}
+
+template <int D, int NF>
+void launch_apply_t(Problem *P, const double *r, double *z)
+{
+    RasPlan *R = P->ras;
+    if (R->smem_bytes > 48 * 1024 && !R->attr_set) {
+        cudaFuncSetAttribute(k_ras_apply<D, NF, double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)R->smem_bytes);
+        R->attr_set = true;
+    }
+    k_ras_apply<D, NF, double, double><<<R->nsub, R->threads, R->smem_bytes, P->stream>>>(
+        P->g, R->sub, R->lvl_ptr, R->lvl_blk, R->lvl_lp, R->fac, r, z, R->scratch, R->x_smem ? 1 : 0, R->maxnp,
+        R->maxblk, P->dflag);
 }
 
 }  // namespace
 
+#define NKS_DISPATCH(FN, ...)              \
+    switch (P->g.dim * 10 + P->nf) {       \
+    case 12: FN<1, 2>(__VA_ARGS__); break; \
+    case 13: FN<1, 3>(__VA_ARGS__); break; \
+    case 22: FN<2, 2>(__VA_ARGS__); break; \
+    case 24: FN<2, 4>(__VA_ARGS__); break; \
+    case 32: FN<3, 2>(__VA_ARGS__); break; \
+    case 35: FN<3, 5>(__VA_ARGS__); break; \
+    }
+
 int ras_factor(Problem *P, int mode)
 {
-    RasPlan *R = P->ras;
     cudaMemsetAsync(P->dflag, 0, sizeof(int), P->stream);
     P->tick(3);
-    k_ras_factor<<<R->nsub, R->threads, 0, P->stream>>>(P->g, P->k, P->cur_dt, mode, tables_of(P), R->sub, R->lvl_ptr,
-                                                        R->lvl_lp, R->pos_of_lp, R->tmpl, R->slotmap, R->upd_ptr,
-                                                        R->upd, P->part, P->mob, R->fac, P->dflag);
+    launch_factor(P, mode);
+    P->count(1);
     P->tock(3);
     int hflag = 0;
     cudaMemcpyAsync(&hflag, P->dflag, sizeof(int), cudaMemcpyDeviceToHost, P->stream);
@@ -632,19 +737,30 @@ void project(Problem *P, double *z)
     k_proj_dots<<<kRedBlocks, kRedThreads, 0, P->stream>>>(P->g, P->nf, R->evenmask, R->nmodes, z, P->partials);
     launch_finalize(P->partials, kRedBlocks, K, R->proj, P->stream);
     k_proj_sub<<<(int)((P->N + 255) / 256), 256, 0, P->stream>>>(P->g, P->nf, R->evenmask, R->nmodes, R->proj, z);
+    P->count(3);
     P->tock(6);
 }
 
 void ras_apply(Problem *P, const double *r, double *z)
 {
-    RasPlan *R = P->ras;
-    if (R->smem && R->smem_bytes > 48 * 1024 && !R->attr_set) {
-        cudaFuncSetAttribute(k_ras_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)R->smem_bytes);
-        R->attr_set = true;
-    }
-    k_ras_apply<<<R->nsub, R->threads, R->smem ? R->smem_bytes : 0, P->stream>>>(
-        P->g, tables_of(P), R->sub, R->lvl_ptr, R->lvl_lp, R->tmpl, R->fac, r, z, R->scratch, R->smem ? 1 : 0);
+    P->tick(2);
+    NKS_DISPATCH(launch_apply_t, P, r, z);
+    P->count(1);
+    P->tock(2);
     project(P, z);
+}
+
+// algorithmic work of one Schwarz sweep (both triangular solves over every
+// overlapped point): bytes of factors + gathered and written vectors, FLOPs
+void ras_work(const Problem *P, double *bytes, double *flops)
+{
+    const RasPlan *R = P->ras;
+    const double pts = (double)R->total_np, owned = (double)P->N;
+    // factors (lower + upper entries + inverse pivots) of every overlapped point, the
+    // gathered sub-vectors and the owned output, each moved once
+    *bytes = pts * (R->nlow + R->nup + P->nf) * sizeof(double) + pts * P->nf * sizeof(double) +
+             owned * P->nf * sizeof(double);
+    *flops = pts * (2.0 * (R->nlow + R->nup) + P->nf);
 }
 
 }  // namespace nks

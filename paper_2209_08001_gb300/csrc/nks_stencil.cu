@@ -416,39 +416,45 @@ __global__ void k_finalize(const double *__restrict__ partials, int nblocks, int
 
 }  // namespace
 
-void launch_mobility(const DGrid &g, const DCoef &k, const double *c0, double *mob, cudaStream_t st)
+int launch_mobility(const DGrid &g, const DCoef &k, const double *c0, double *mob, cudaStream_t st)
 {
     k_mobility<<<blocks_for(g.N), kThreads, 0, st>>>(g, k, c0, mob);
+    return 1;
 }
 
-void launch_trace0(const DGrid &g, const DCoef &k, const double *X0, double *tr0, cudaStream_t st)
+int launch_trace0(const DGrid &g, const DCoef &k, const double *X0, double *tr0, cudaStream_t st)
 {
     k_trace0<<<blocks_for(g.N), kThreads, 0, st>>>(g, k, X0, tr0);
+    return 1;
 }
 
-void launch_residual(const DGrid &g, const DCoef &k, double dt, int mode, const double *X1, const double *X0,
+int launch_residual(const DGrid &g, const DCoef &k, double dt, int mode, const double *X1, const double *X0,
                      const double *tr0, const double *mob, double *Gc, double *sig, double *part, double *F, int *flag,
                      double *partials, cudaStream_t st)
 {
     k_res_a<<<blocks_for(g.N), kThreads, 0, st>>>(g, k, dt, mode, X1, X0, tr0, Gc, sig, part, F, flag);
     k_res_b<<<kRedBlocks, kRedThreads, 0, st>>>(g, k, dt, mode, X1, X0, Gc, mob, sig, F, partials);
+    return 2;
 }
 
-void launch_jv(const DGrid &g, const DCoef &k, double dt, int mode, const double *part, const double *mob,
+int launch_jv(const DGrid &g, const DCoef &k, double dt, int mode, const double *part, const double *mob,
                const double *v, double *dG, double *sig, double *Jv, cudaStream_t st)
 {
     k_jv_a<<<blocks_for(g.N), kThreads, 0, st>>>(g, k, dt, mode, part, v, dG, sig, Jv);
     k_jv_b<<<blocks_for(g.N), kThreads, 0, st>>>(g, k, dt, mode, mob, v, dG, sig, Jv);
+    return 2;
 }
 
-void launch_energy(const DGrid &g, const DCoef &k, const double *X, double *partials, cudaStream_t st)
+int launch_energy(const DGrid &g, const DCoef &k, const double *X, double *partials, cudaStream_t st)
 {
     k_energy<<<kRedBlocks, kRedThreads, 0, st>>>(g, k, X, partials);
+    return 1;
 }
 
-void launch_finalize(const double *partials, int nblocks, int K, double *out, cudaStream_t st)
+int launch_finalize(const double *partials, int nblocks, int K, double *out, cudaStream_t st)
 {
     k_finalize<<<1, kRedThreads, 0, st>>>(partials, nblocks, K, out);
+    return 1;
 }
 
 }  // namespace nks
