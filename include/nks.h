@@ -253,6 +253,44 @@ int nks_linear_solve(nks_problem *p, const double *X1, const double *X0, double 
  * total, and the mass; parts has 5 entries. */
 int nks_eval_energy(nks_problem *p, const double *X, double *parts, double *mass);
 
+/* ------------------------------------------------------------------------ */
+/* Residual evaluation that allocates no device memory.                      */
+/* ------------------------------------------------------------------------ */
+
+/* Largest grid (points) nks_residual_noalloc accepts. */
+#define NKS_NOALLOC_MAX_POINTS 65536
+
+/*
+ * F(X1; X0, dt) as nks_eval_residual computes it, but on DEVICE arrays and
+ * without allocating: no cudaMalloc, cudaFree or allocating library call is
+ * made.  The paper has no counterpart; this entry point serves callers that
+ * cannot allocate device memory when they evaluate the residual, for example
+ * a host application whose memory manager owns the whole device, or a
+ * latency-critical loop that must not allocate because allocation can
+ * synchronise the device.
+ *
+ *   grid, coeffs   as for nks_create_problem; grid->n[0]*n[1]*n[2] must not
+ *                  exceed NKS_NOALLOC_MAX_POINTS (NKS_EINVAL otherwise)
+ *   cbar0          mean composition of the initial state (Sec. 3)
+ *   dt, mode       as for nks_eval_residual (mode 1: displacement-only system)
+ *   X1, X0, F      DEVICE state arrays of nf*N doubles (layout of this header)
+ *   fnorm2         DEVICE pointer receiving ||F||^2, or NULL
+ *   stream         cudaStream_t to run on (NULL: the legacy default stream)
+ * Returns NKS_OK, NKS_EINVAL, NKS_EDOMAIN (X1 outside the domain of the
+ * logarithms; F is still written) or NKS_ECUDA; nks_last_error(NULL) gives
+ * the message.  The call synchronises the stream before it returns.
+ *
+ * Scratch: a fixed array of 15 * NKS_NOALLOC_MAX_POINTS doubles (7.5 MiB) plus
+ * reduction space, held in device memory by every GPU that loads the library
+ * until the process exits.  The first call on a device looks up the array's
+ * device address (once per device, with that device current); make that first
+ * call before any stream capture.  All calls share the array and it keeps the
+ * previous call's contents, so calls that overlap on the GPU (from several
+ * threads or streams) race: serialise them.
+ */
+int nks_residual_noalloc(const nks_grid *grid, const nks_coeffs *coeffs, double cbar0, double dt, int mode,
+                         const double *X1, const double *X0, double *F, double *fnorm2, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

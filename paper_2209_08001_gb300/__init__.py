@@ -128,6 +128,8 @@ def load():
         "nks_linear_solve": (ctypes.c_int, [_P, _D, _D, ctypes.c_double, ctypes.c_int, _D, _D, ctypes.c_double,
                                             ctypes.POINTER(ctypes.c_int), _D]),
         "nks_eval_energy": (ctypes.c_int, [_P, _D, _D, _D]),
+        "nks_residual_noalloc": (ctypes.c_int, [ctypes.POINTER(nks_grid), ctypes.POINTER(nks_coeffs),
+                                                ctypes.c_double, ctypes.c_double, ctypes.c_int, _P, _P, _P, _P, _P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -142,7 +144,7 @@ def exported_symbols():
     return ["nks_default_opts", "nks_create_problem", "nks_step", "nks_energy", "nks_mass", "nks_get_fields",
             "nks_state_size", "nks_get_state", "nks_set_state", "nks_get_stats", "nks_reset_stats", "nks_destroy",
             "nks_last_error", "nks_eval_residual", "nks_apply_jacobian", "nks_apply_preconditioner",
-            "nks_linear_solve", "nks_eval_energy"]
+            "nks_linear_solve", "nks_eval_energy", "nks_residual_noalloc"]
 
 
 def _ptr(a):
@@ -314,6 +316,18 @@ class Problem:
         parts, mass = np.empty(5), ctypes.c_double()
         _check(load().nks_eval_energy(self._h, _ptr(X), _ptr(parts), ctypes.byref(mass)), self._h)
         return parts, mass.value
+
+
+NOALLOC_MAX_POINTS = 65536
+
+
+def residual_noalloc(dim, n, h, coeffs: dict, cbar0, dt, X1_ptr, X0_ptr, F_ptr, fnorm2_ptr=None, stream=None,
+                     mode=0):
+    """F(X1; X0, dt) on caller-owned device arrays (raw pointers) without any
+    device allocation (nks_residual_noalloc).  Returns the status code."""
+    g, k = make_grid(dim, n, h), make_coeffs(coeffs)
+    return load().nks_residual_noalloc(ctypes.byref(g), ctypes.byref(k), float(cbar0), float(dt), int(mode),
+                                       X1_ptr, X0_ptr, F_ptr, fnorm2_ptr, stream)
 
 
 def torch_allocator():

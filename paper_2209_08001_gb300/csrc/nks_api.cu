@@ -14,6 +14,9 @@ size_t gmres_state_doubles(int m);
 
 static thread_local std::string g_create_error;
 
+// message returned by nks_last_error(NULL) on this thread
+void set_thread_error(const char *msg) { g_create_error = msg ? msg : ""; }
+
 int cuda_fail(Problem *P, cudaError_t e, const char *where)
 {
     P->err = std::string("CUDA error in ") + where + ": " + cudaGetErrorString(e);
@@ -103,7 +106,7 @@ int Problem::sync_check(const char *where)
 
 // App. B: dE_G/dc = M0 + M1(phi) c + M2(phi) c^2 + M3 c^3 + M4 c^4 + ..., with the
 // coefficients expressed through the App. A parameters (all divided by V_m dE).
-static DCoef derive_coefficients(const nks_coeffs &c, int dim, double cbar0)
+DCoef derive_coefficients(const nks_coeffs &c, int dim, double cbar0)
 {
     DCoef k;
     memset(&k, 0, sizeof(k));

@@ -208,5 +208,7 @@ struct Problem {
 };
 
 int cuda_fail(Problem *P, cudaError_t e, const char *where);
+DCoef derive_coefficients(const nks_coeffs &c, int dim, double cbar0);  // App. B reduction
+void set_thread_error(const char *msg);                                 // for nks_last_error(NULL)
 
 }  // namespace nks
