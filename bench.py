@@ -185,6 +185,8 @@ def run_ours(args):
 
     cfg = S.CONFIGS[args.config]
     op = S.options(**cfg["opts"])
+    if args.precision:
+        op["precision"] = args.precision
     seed = cfg["seed"] + 1000 * rank  # independent replica per rank
     c, e = S.initial_fields(cfg["dim"], cfg["n"], cfg["cbar"], seed)
     N = c.size
@@ -269,8 +271,10 @@ def run_ours(args):
     out = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded SplitMix64 initial fields)",
-        "config": {"workload": cfg["desc"], "grid": list(cfg["n"]), "points": N, "steps_in_workload": cfg["steps"],
+        "vs_baseline": None, "dtype": "f64" if op["precision"] == "fp64" else "f64+f32",
+        "data": "synthetic (seeded SplitMix64 initial fields)",
+        "config": {"workload": cfg["desc"], "precision": op["precision"], "grid": list(cfg["n"]), "points": N,
+                   "steps_in_workload": cfg["steps"],
                    "timed_steps": "steps 1..K of the workload from its initial state",
                    "l2": "working set (state, Krylov basis, ~0.65 GB of Schwarz factors) far above the 129 MB L2",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
@@ -343,6 +347,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="2d1024", choices=sorted(S.CONFIGS))
+    ap.add_argument("--precision", default=None, choices=["fp64", "mixed"],
+                    help="override the workload's precision mode (default: the workload's own)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     # iteration counts used to scale the oracle sample in the reference arm (measured on the GPU arm)

@@ -239,7 +239,9 @@ int nks_apply_jacobian(nks_problem *p, const double *X1, const double *X0, doubl
 /* z = P sum_i R_i^0T (L_i U_i)^-1 R_i^delta r: restricted additive Schwarz
  * (Sec. 4, left-RAS) with ILU(0) factors of J(X1; X0, dt) restricted to each
  * overlapped box, followed by the projection P (mean of z_c removed; the
- * null modes of the centred-difference strain removed from z_u). */
+ * null modes of the centred-difference strain removed from z_u).  In the
+ * NKS_MIXED mode the sweeps run as the solver runs them: FP32 factors and
+ * vectors (r rounded to FP32 on input). */
 int nks_apply_preconditioner(nks_problem *p, const double *X1, const double *X0, double dt, const double *r,
                              double *z);
 

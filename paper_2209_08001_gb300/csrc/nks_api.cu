@@ -354,8 +354,8 @@ int nks_create_problem(const nks_grid *grid, const double *c, const double *eta,
         g_create_error = "opts: gmres_restart must be in 1..31";
         return NKS_EINVAL;
     }
-    if (opts->precision != NKS_FP64) {
-        g_create_error = "opts: precision mode not available in this build";
+    if (opts->precision != NKS_FP64 && opts->precision != NKS_MIXED) {
+        g_create_error = "opts: precision must be NKS_FP64 or NKS_MIXED";
         return NKS_EINVAL;
     }
     nks_problem *H = new nks_problem();
@@ -391,7 +391,10 @@ int nks_create_problem(const nks_grid *grid, const double *c, const double *eta,
     P->k = derive_coefficients(*coeffs, g.dim, P->cbar0);
     P->nf = P->k.nf;
     P->nvec = P->nf * g.N;
-    const size_t vb = sizeof(double) * (size_t)P->nvec, fb = sizeof(double) * (size_t)g.N;
+    P->ldv = (P->nvec + 1) & ~1LL;
+    P->ldvf = (P->nvec + 3) & ~3LL;
+    // every work vector holds ldv entries; the entry past nvec stays zero (16-byte pair loads)
+    const size_t vb = sizeof(double) * (size_t)P->ldv, fb = sizeof(double) * (size_t)g.N;
     const int m = opts->gmres_restart;
     double **vecs[] = {&P->Xn, &P->Xprev, &P->X, &P->Xt, &P->F, &P->Ft, &P->S, &P->B, &P->W, &P->Z, &P->R};
     bool ok = true;
@@ -401,18 +404,33 @@ int nks_create_problem(const nks_grid *grid, const double *c, const double *eta,
          (P->Gc = (double *)P->dalloc(fb)) && (P->sig = (double *)P->dalloc(6 * fb)) &&
          (P->partials = (double *)P->dalloc(sizeof(double) * kRedBlocks * 64)) &&
          (P->dscal = (double *)P->dalloc(sizeof(double) * 64)) && (P->dflag = (int *)P->dalloc(sizeof(int) * 4)) &&
-         (P->V = (double *)P->dalloc(vb * (m + 1))) &&
+         (P->tickets = (unsigned int *)P->dalloc(sizeof(unsigned int) * 16)) &&
+         (P->V = (double *)P->dalloc(vb * (opts->precision == NKS_MIXED ? 1 : m + 1))) &&
+         (P->T64 = (double *)P->dalloc(vb)) &&
          (P->gm = (double *)P->dalloc(sizeof(double) * gmres_state_doubles(m)));
+    if (ok && opts->precision == NKS_MIXED) {
+        const size_t fvb = sizeof(float) * (size_t)P->ldvf;
+        ok = (P->Vf = (float *)P->dalloc(fvb * (m + 1))) && (P->Wf = (float *)P->dalloc(fvb)) &&
+             (P->Zf = (float *)P->dalloc(fvb));
+        if (ok) {
+            cudaMemsetAsync(P->Vf, 0, fvb * (m + 1), P->stream);
+            cudaMemsetAsync(P->Wf, 0, fvb, P->stream);
+            cudaMemsetAsync(P->Zf, 0, fvb, P->stream);
+        }
+    }
     if (ok && cudaMallocHost((void **)&P->hscal, 64 * sizeof(double)) != cudaSuccess) ok = false;
     if (!ok) {
         g_create_error = "out of device memory";
         nks_destroy(H);
         return NKS_ENOMEM;
     }
-    cudaMemsetAsync(P->Xn, 0, vb, P->stream);
+    for (double **v : vecs) cudaMemsetAsync(*v, 0, vb, P->stream);
+    cudaMemsetAsync(P->V, 0, vb * (opts->precision == NKS_MIXED ? 1 : m + 1), P->stream);
+    cudaMemsetAsync(P->T64, 0, vb, P->stream);
     cudaMemcpyAsync(P->Xn, c, fb, cudaMemcpyHostToDevice, P->stream);
     cudaMemcpyAsync(P->Xn + g.N, eta, fb, cudaMemcpyHostToDevice, P->stream);
     cudaMemsetAsync(P->tr0, 0, fb, P->stream);
+    cudaMemsetAsync(P->tickets, 0, sizeof(unsigned int) * 16, P->stream);
     std::string err;
     int rc = ras_plan_create(P, err);
     if (rc) {
@@ -695,7 +713,14 @@ int nks_apply_preconditioner(nks_problem *H, const double *X1, const double *X0,
     if (!rc) {
         const size_t vb = sizeof(double) * (size_t)P->nvec;
         cudaMemcpyAsync(P->B, r, vb, cudaMemcpyHostToDevice, P->stream);
-        ras_apply(P, P->B, P->Z);
+        if (P->opts.precision == NKS_MIXED) {
+            // as the solver applies it: FP32 vectors and factors
+            P->count(launch_convert(P->nvec, P->B, P->Wf, P->stream));
+            ras_apply_t<float>(P, P->Wf, P->Zf);
+            P->count(launch_convert(P->nvec, P->Zf, P->Z, P->stream));
+        } else {
+            ras_apply(P, P->B, P->Z);
+        }
         cudaMemcpyAsync(z, P->Z, vb, cudaMemcpyDeviceToHost, P->stream);
         rc = P->sync_check("apply_preconditioner");
     }

@@ -15,7 +15,7 @@
 
 namespace nks {
 
-constexpr int kRedBlocks = 304;    // 2 x 152 SMs: fixed reduction grid (deterministic sums)
+constexpr int kRedBlocks = 608;    // 4 x 152 SMs: fixed reduction grid (deterministic sums)
 constexpr int kRedThreads = 256;
 constexpr int kMaxNf = 5;          // c, eta, u_1..u_3
 constexpr int kMaxRow = 72;        // longest Jacobian row: 71 entries (3-D c-row)
@@ -98,6 +98,31 @@ __device__ inline void block_reduce_store(double (&v)[K], double *partials /* [g
     }
 }
 
+// Last-block finalisation: after every block stored its K partial sums, the
+// block that finishes last adds the columns of all blocks' partials in a fixed
+// order (lanes stride over blocks, then a fixed shuffle tree) and writes out[K];
+// counter returns to zero.  The result does not depend on which block is last.
+__device__ inline void grid_finalize(const double *partials, int K, double *out, unsigned int *counter)
+{
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const volatile double *vp = partials;
+    for (int k = warp; k < K; k += nw) {
+        double a = 0.0;
+        for (int b = lane; b < (int)gridDim.x; b += 32) a += vp[(size_t)b * K + k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        if (lane == 0) out[k] = a;
+    }
+    if (threadIdx.x == 0) *counter = 0u;
+}
+
 // ---------------------------------------------------------------------------
 // stencil / reduction kernels (nks_stencil.cu)
 // ---------------------------------------------------------------------------
@@ -109,6 +134,9 @@ int launch_residual(const DGrid &g, const DCoef &k, double dt, int mode, const d
                      int *flag, double *partials, cudaStream_t st);
 int launch_jv(const DGrid &g, const DCoef &k, double dt, int mode, const double *part, const double *mob,
                const double *v, double *dG, double *sig, double *Jv, cudaStream_t st);
+template <typename TV>
+int launch_jv_t(const DGrid &g, const DCoef &k, double dt, int mode, const double *part, const double *mob,
+                const TV *v, double *dG, double *sig, TV *Jv, cudaStream_t st);
 int launch_energy(const DGrid &g, const DCoef &k, const double *X, double *partials, cudaStream_t st);
 int launch_finalize(const double *partials, int nblocks, int K, double *out, cudaStream_t st);
 
@@ -120,6 +148,8 @@ int launch_axpby(long long n, double a, const double *x, double b, double *y, cu
 int launch_waxpy(long long n, const double *x, double a, const double *y, double *w, cudaStream_t st); // w = x + a y
 int launch_scale_dev(long long n, const double *src, const double *inv_norm, double *dst, cudaStream_t st);
 int launch_dot2(long long n, const double *x, const double *y, double *partials, cudaStream_t st); // x.y, y.y
+int launch_convert(long long n, const double *a, float *b, cudaStream_t st);
+int launch_convert(long long n, const float *a, double *b, cudaStream_t st);
 
 // GMRES(m) with right preconditioning; see nks_krylov.cu.
 struct Problem;
@@ -134,6 +164,8 @@ int ras_plan_create(Problem *P, std::string &err);
 void ras_plan_destroy(Problem *P);
 int ras_factor(Problem *P, int mode);                              // assemble J restricted + ILU(0)
 void ras_apply(Problem *P, const double *r, double *z);           // z = P RAS^-1 r
+template <typename TV>
+void ras_apply_t(Problem *P, const TV *r, TV *z);                  // FP64 or FP32 (mixed) vectors
 void project(Problem *P, double *z);
 void ras_work(const Problem *P, double *bytes, double *flops);  // algorithmic work of one sweep
 
@@ -166,6 +198,7 @@ struct Problem {
     DCoef k{};
     int nf = 2;
     long long N = 0, nvec = 0;
+    long long ldv = 0;                          // stride of the Krylov basis: nvec rounded up to even
 
     // state
     double *Xn = nullptr, *Xprev = nullptr, *X = nullptr, *Xt = nullptr;
@@ -178,10 +211,14 @@ struct Problem {
     double *dscal = nullptr;                    // small device scalars
     double *hscal = nullptr;                    // pinned host mirror
     int *dflag = nullptr;
+    unsigned int *tickets = nullptr;            // last-block counters of the fused reductions (start at 0)
 
     // Krylov workspace
-    double *V = nullptr;                        // (m + 1) nvec
+    double *V = nullptr;                        // (m + 1) ldv, FP64 basis
     double *W = nullptr, *Z = nullptr, *R = nullptr;
+    double *T64 = nullptr;                      // FP64 J x of the true residual
+    float *Vf = nullptr, *Wf = nullptr, *Zf = nullptr;  // FP32 basis and Arnoldi vectors (mixed precision)
+    long long ldvf = 0;                         // FP32 basis stride: nvec rounded up to a multiple of 4
     double *gm = nullptr;                       // device GMRES small state
 
     RasPlan *ras = nullptr;

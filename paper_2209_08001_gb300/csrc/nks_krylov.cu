@@ -11,6 +11,12 @@
 //     as x += M^-1 (V y) and the true residual b - J x decides termination.
 // Every reduction uses a fixed grid and a fixed tree, so results do not
 // depend on timing.
+//
+// The basis type TV is FP64, or FP32 in the mixed-precision mode: there the
+// basis, the Arnoldi vectors, the Schwarz sweeps and the Jacobian action's
+// inputs/outputs are FP32 (per-thread dot products accumulate in FP32, block
+// and grid sums in FP64), while the Hessenberg/Givens state, the solution x,
+// the true residual b - J x and the Jacobian arithmetic stay FP64.
 #include <math.h>
 
 #include <array>
@@ -61,11 +67,20 @@ __global__ void k_waxpy(long long n, const double *__restrict__ x, double a, con
     if (i < n) w[i] = x[i] + a * y[i];
 }
 
-__global__ void k_scale_dev(long long n, const double *__restrict__ src, const double *__restrict__ s,
-                            double *__restrict__ dst)
+template <typename TS, typename TD>
+__global__ void k_scale_dev(long long n, const TS *__restrict__ src, const double *__restrict__ s,
+                            TD *__restrict__ dst)
 {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i < n) dst[i] = src[i] * (*s);
+    if (i < n) dst[i] = (TD)((double)src[i] * (*s));
+}
+
+// y += x (x stored as TV)
+template <typename TV>
+__global__ void k_add(long long n, const TV *__restrict__ x, double *__restrict__ y)
+{
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) y[i] += (double)x[i];
 }
 
 __global__ void __launch_bounds__(kRedThreads) k_dot2(long long n, const double *__restrict__ x,
@@ -80,93 +95,156 @@ __global__ void __launch_bounds__(kRedThreads) k_dot2(long long n, const double 
     block_reduce_store<2>(acc, partials);
 }
 
+template <typename TV>
+struct Vec;
+template <>
+struct Vec<double> {
+    using type = double2;
+    static constexpr int W = 2;
+};
+template <>
+struct Vec<float> {
+    using type = float4;
+    static constexpr int W = 4;
+};
+
+template <typename TV>
+__device__ __forceinline__ void unpack(const typename Vec<TV>::type &t, TV (&a)[Vec<TV>::W])
+{
+    a[0] = t.x;
+    a[1] = t.y;
+    if constexpr (Vec<TV>::W == 4) {
+        a[2] = t.z;
+        a[3] = t.w;
+    }
+}
+
+template <typename TV>
+__device__ __forceinline__ typename Vec<TV>::type pack(const TV (&a)[Vec<TV>::W])
+{
+    typename Vec<TV>::type t;
+    t.x = a[0];
+    t.y = a[1];
+    if constexpr (Vec<TV>::W == 4) {
+        t.z = a[2];
+        t.w = a[3];
+    }
+    return t;
+}
+
 // CGS pass 1: h_i = v_i . w (i < NV) and w . w, one read of V and w.
-// gate (optional): skip unless gate[0] != 0.
-template <int NV>
-__global__ void __launch_bounds__(kRedThreads) k_multidot(long long n, const double *__restrict__ V, long long ldv,
-                                                          const double *__restrict__ w, double *__restrict__ partials,
-                                                          const double *gate)
+// Vectors are read as 16-byte packs (nq packs each): ldv is a multiple of the
+// pack and entries past the vector length are zero.  gate (optional): skip
+// unless gate[0] != 0.
+template <int NV, typename TV>
+__global__ void __launch_bounds__(kRedThreads, 4) k_multidot(long long nq, const TV *__restrict__ V, long long ldv,
+                                                             const TV *__restrict__ w, double *__restrict__ partials,
+                                                             const double *gate, double *out, unsigned int *ticket)
 {
     if (gate && gate[0] == 0.0) return;
-    double acc[NV + 1];
+    using VT = typename Vec<TV>::type;
+    constexpr int WD = Vec<TV>::W;
+    TV acc[NV + 1];
 #pragma unroll
-    for (int k = 0; k <= NV; k++) acc[k] = 0.0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const double wi = w[i];
+    for (int k = 0; k <= NV; k++) acc[k] = (TV)0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nq; i += (long long)gridDim.x * blockDim.x) {
+        TV wa[WD];
+        unpack<TV>(reinterpret_cast<const VT *>(w)[i], wa);
 #pragma unroll
-        for (int k = 0; k < NV; k++) acc[k] += V[k * ldv + i] * wi;
-        acc[NV] += wi * wi;
+        for (int k = 0; k < NV; k++) {
+            TV va[WD];
+            unpack<TV>(reinterpret_cast<const VT *>(V + k * ldv)[i], va);
+#pragma unroll
+            for (int e = 0; e < WD; e++) acc[k] += va[e] * wa[e];
+        }
+#pragma unroll
+        for (int e = 0; e < WD; e++) acc[NV] += wa[e] * wa[e];
     }
-    block_reduce_store<NV + 1>(acc, partials);
+    double accd[NV + 1];
+#pragma unroll
+    for (int k = 0; k <= NV; k++) accd[k] = (double)acc[k];
+    block_reduce_store<NV + 1>(accd, partials);
+    grid_finalize(partials, NV + 1, out, ticket);
 }
 
 // CGS pass 2: w -= sum_i h_i v_i, accumulating ||w||^2.
-template <int NV>
-__global__ void __launch_bounds__(kRedThreads) k_cgs_update(long long n, const double *__restrict__ V, long long ldv,
-                                                            const double *__restrict__ h, double *__restrict__ w,
-                                                            double *__restrict__ partials, const double *gate)
+template <int NV, typename TV>
+__global__ void __launch_bounds__(kRedThreads, 4) k_cgs_update(long long nq, const TV *__restrict__ V, long long ldv,
+                                                               const double *__restrict__ h, TV *__restrict__ w,
+                                                               double *__restrict__ partials, const double *gate,
+                                                               double *out, unsigned int *ticket)
 {
     if (gate && gate[0] == 0.0) return;
-    double hk[NV];
+    using VT = typename Vec<TV>::type;
+    constexpr int WD = Vec<TV>::W;
+    TV hk[NV];
 #pragma unroll
-    for (int k = 0; k < NV; k++) hk[k] = h[k];
-    double acc[1] = {0.0};
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        double s = w[i];
+    for (int k = 0; k < NV; k++) hk[k] = (TV)h[k];
+    TV acc = (TV)0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nq; i += (long long)gridDim.x * blockDim.x) {
+        TV sa[WD];
+        unpack<TV>(reinterpret_cast<const VT *>(w)[i], sa);
 #pragma unroll
-        for (int k = 0; k < NV; k++) s -= hk[k] * V[k * ldv + i];
-        w[i] = s;
-        acc[0] += s * s;
+        for (int k = 0; k < NV; k++) {
+            TV va[WD];
+            unpack<TV>(reinterpret_cast<const VT *>(V + k * ldv)[i], va);
+#pragma unroll
+            for (int e = 0; e < WD; e++) sa[e] -= hk[k] * va[e];
+        }
+        reinterpret_cast<VT *>(w)[i] = pack<TV>(sa);
+#pragma unroll
+        for (int e = 0; e < WD; e++) acc += sa[e] * sa[e];
     }
-    block_reduce_store<1>(acc, partials);
+    double accd[1] = {(double)acc};
+    block_reduce_store<1>(accd, partials);
+    grid_finalize(partials, 1, out, ticket);
 }
 
-using MultidotFn = void (*)(long long, const double *, long long, const double *, double *, const double *);
-using UpdateFn = void (*)(long long, const double *, long long, const double *, double *, double *, const double *);
+template <typename TV>
+using MultidotFn = void (*)(long long, const TV *, long long, const TV *, double *, const double *, double *,
+                            unsigned int *);
+template <typename TV>
+using UpdateFn = void (*)(long long, const TV *, long long, const double *, TV *, double *, const double *, double *,
+                          unsigned int *);
 
-template <int... I>
+template <typename TV, int... I>
 constexpr auto multidot_table(std::integer_sequence<int, I...>)
 {
-    return std::array<MultidotFn, sizeof...(I)>{{&k_multidot<I + 1>...}};
+    return std::array<MultidotFn<TV>, sizeof...(I)>{{&k_multidot<I + 1, TV>...}};
 }
-template <int... I>
+template <typename TV, int... I>
 constexpr auto update_table(std::integer_sequence<int, I...>)
 {
-    return std::array<UpdateFn, sizeof...(I)>{{&k_cgs_update<I + 1>...}};
+    return std::array<UpdateFn<TV>, sizeof...(I)>{{&k_cgs_update<I + 1, TV>...}};
 }
 constexpr int kMaxNv = 31;
-const auto g_multidot = multidot_table(std::make_integer_sequence<int, kMaxNv>{});
-const auto g_update = update_table(std::make_integer_sequence<int, kMaxNv>{});
+const auto g_multidot64 = multidot_table<double>(std::make_integer_sequence<int, kMaxNv>{});
+const auto g_update64 = update_table<double>(std::make_integer_sequence<int, kMaxNv>{});
+const auto g_multidot32 = multidot_table<float>(std::make_integer_sequence<int, kMaxNv>{});
+const auto g_update32 = update_table<float>(std::make_integer_sequence<int, kMaxNv>{});
 
-void launch_multidot(int nv, long long n, const double *V, const double *w, double *partials, const double *gate,
-                     cudaStream_t st)
+// h_i = v_i . w (i < nv) and w . w into out[0..nv]; ldv a multiple of the 16-byte pack
+template <typename TV>
+void launch_multidot(int nv, long long ldv, const TV *V, const TV *w, double *partials, const double *gate,
+                     double *out, unsigned int *ticket, cudaStream_t st)
 {
-    g_multidot[nv - 1]<<<kRedBlocks, kRedThreads, 0, st>>>(n, V, n, w, partials, gate);
+    constexpr int WD = Vec<TV>::W;
+    if constexpr (sizeof(TV) == 8)
+        g_multidot64[nv - 1]<<<kRedBlocks, kRedThreads, 0, st>>>(ldv / WD, V, ldv, w, partials, gate, out, ticket);
+    else
+        g_multidot32[nv - 1]<<<kRedBlocks, kRedThreads, 0, st>>>(ldv / WD, V, ldv, w, partials, gate, out, ticket);
 }
 
-void launch_update(int nv, long long n, const double *V, const double *h, double *w, double *partials,
-                   const double *gate, cudaStream_t st)
+// w -= V h, ||w||^2 into out[0]
+template <typename TV>
+void launch_update(int nv, long long ldv, const TV *V, const double *h, TV *w, double *partials, const double *gate,
+                   double *out, unsigned int *ticket, cudaStream_t st)
 {
-    g_update[nv - 1]<<<kRedBlocks, kRedThreads, 0, st>>>(n, V, n, h, w, partials, gate);
-}
-
-__global__ void k_finalize_g(const double *__restrict__ partials, int nblocks, int K, double *__restrict__ out,
-                             const double *gate)
-{
-    if (gate && gate[0] == 0.0) return;
-    __shared__ double red[kRedThreads];
-    for (int kk = 0; kk < K; kk++) {
-        double a = 0.0;
-        for (int b = threadIdx.x; b < nblocks; b += blockDim.x) a += partials[(size_t)b * K + kk];
-        red[threadIdx.x] = a;
-        __syncthreads();
-        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-            if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) out[kk] = red[0];
-        __syncthreads();
-    }
+    constexpr int WD = Vec<TV>::W;
+    if constexpr (sizeof(TV) == 8)
+        g_update64[nv - 1]<<<kRedBlocks, kRedThreads, 0, st>>>(ldv / WD, V, ldv, h, w, partials, gate, out, ticket);
+    else
+        g_update32[nv - 1]<<<kRedBlocks, kRedThreads, 0, st>>>(ldv / WD, V, ldv, h, w, partials, gate, out, ticket);
 }
 
 // after pass 2: remember ||w||^2 before orthogonalisation, decide on a second pass
@@ -229,9 +307,10 @@ __global__ void k_hsolve(double *gm, GmLayout L, int kdim)
     }
 }
 
-// out = sum_{i < kdim} y_i v_i
-__global__ void k_lincomb(long long n, const double *__restrict__ V, long long ldv, int kdim,
-                          const double *__restrict__ y, double *__restrict__ out)
+// out = sum_{i < kdim} y_i v_i (FP64 sums)
+template <typename TV>
+__global__ void k_lincomb(long long n, const TV *__restrict__ V, long long ldv, int kdim,
+                          const double *__restrict__ y, TV *__restrict__ out)
 {
     __shared__ double ys[kMaxDots];
     if ((int)threadIdx.x < kdim) ys[threadIdx.x] = y[threadIdx.x];
@@ -241,8 +320,8 @@ __global__ void k_lincomb(long long n, const double *__restrict__ V, long long l
     double s = 0.0;
 #pragma unroll
     for (int k = 0; k < kMaxDots; k++)
-        if (k < kdim) s += ys[k] * V[k * ldv + i];
-    out[i] = s;
+        if (k < kdim) s += ys[k] * (double)V[k * ldv + i];
+    out[i] = (TV)s;
 }
 
 }  // namespace
@@ -259,9 +338,28 @@ int launch_waxpy(long long n, const double *x, double a, const double *y, double
     return 1;
 }
 
+template <typename TS, typename TD>
+__global__ void k_convert(long long n, const TS *__restrict__ a, TD *__restrict__ b)
+{
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (TD)a[i];
+}
+
+int launch_convert(long long n, const double *a, float *b, cudaStream_t st)
+{
+    k_convert<double, float><<<nb(n), kT, 0, st>>>(n, a, b);
+    return 1;
+}
+
+int launch_convert(long long n, const float *a, double *b, cudaStream_t st)
+{
+    k_convert<float, double><<<nb(n), kT, 0, st>>>(n, a, b);
+    return 1;
+}
+
 int launch_scale_dev(long long n, const double *src, const double *inv, double *dst, cudaStream_t st)
 {
-    k_scale_dev<<<nb(n), kT, 0, st>>>(n, src, inv, dst);
+    k_scale_dev<double, double><<<nb(n), kT, 0, st>>>(n, src, inv, dst);
     return 1;
 }
 
@@ -285,20 +383,33 @@ static double norm2_host(Problem *P, const double *x)
     return P->hscal[0];
 }
 
-static void apply_J(Problem *P, int mode, const double *v, double *out)
+template <typename TV>
+static void apply_J(Problem *P, int mode, const TV *v, TV *out)
 {
     P->tick(1);
-    P->count(launch_jv(P->g, P->k, P->cur_dt, mode, P->part, P->mob, v, P->Gc, P->sig, out, P->stream));
+    P->count(launch_jv_t<TV>(P->g, P->k, P->cur_dt, mode, P->part, P->mob, v, P->Gc, P->sig, out, P->stream));
     P->tock(1);
 }
 
-int gmres_solve(Problem *P, int mode, const double *b, double *x, double tol, int *its_out, double *res_out)
+// Krylov work vectors of the basis type
+template <typename TV>
+struct Basis {
+    TV *V, *W, *Z;
+    long long ldv;
+};
+static Basis<double> basis64(Problem *P) { return {P->V, P->W, P->Z, P->ldv}; }
+static Basis<float> basis32(Problem *P) { return {P->Vf, P->Wf, P->Zf, P->ldvf}; }
+
+template <typename TV>
+static int gmres_t(Problem *P, Basis<TV> K, int mode, const double *b, double *x, double tol, int *its_out,
+                   double *res_out)
 {
     const int m = P->opts.gmres_restart;
     const GmLayout L(m);
-    const long long n = P->nvec;
+    const long long n = P->nvec, ldv = K.ldv;
     cudaStream_t st = P->stream;
-    double *V = P->V, *W = P->W, *Z = P->Z, *R = P->R, *gm = P->gm;
+    TV *V = K.V, *W = K.W, *Z = K.Z;
+    double *R = P->R, *gm = P->gm, *Jx = P->T64;
     cudaMemsetAsync(x, 0, sizeof(double) * n, st);
     cudaMemcpyAsync(R, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
     double beta = sqrt(norm2_host(P, R));
@@ -306,38 +417,37 @@ int gmres_solve(Problem *P, int mode, const double *b, double *x, double tol, in
     const int maxit = P->opts.gmres_maxit;
     while (beta > tol && its < maxit) {
         k_gm_start<<<1, 1, 0, st>>>(gm, L, beta);
-        P->count(1 + launch_scale_dev(n, R, gm + L.scal + S_INV, V, st));
+        k_scale_dev<double, TV><<<nb(n), kT, 0, st>>>(n, R, gm + L.scal + S_INV, V);
+        P->count(2);
         int kdim = 0;
         for (int j = 0; j < m; j++) {
-            double *vj = V + (size_t)j * n, *vn = V + (size_t)(j + 1) * n;
-            ras_apply(P, vj, Z);
-            apply_J(P, mode, Z, W);
+            TV *vj = V + (size_t)j * ldv, *vn = V + (size_t)(j + 1) * ldv;
+            ras_apply_t<TV>(P, vj, Z);
+            apply_J<TV>(P, mode, Z, W);
             // CGS pass 1 and 2
             P->tick(4);
-            launch_multidot(j + 1, n, V, W, P->partials, nullptr, st);
-            k_finalize_g<<<1, kRedThreads, 0, st>>>(P->partials, kRedBlocks, j + 2, gm + L.hcol, nullptr);
+            launch_multidot<TV>(j + 1, ldv, V, W, P->partials, nullptr, gm + L.hcol, P->tickets, st);
             P->tock(4);
             P->tick(5);
-            launch_update(j + 1, n, V, gm + L.hcol, W, P->partials, nullptr, st);
-            k_finalize_g<<<1, kRedThreads, 0, st>>>(P->partials, kRedBlocks, 1, gm + L.scal + S_WN, nullptr);
+            launch_update<TV>(j + 1, ldv, V, gm + L.hcol, W, P->partials, nullptr, gm + L.scal + S_WN,
+                              P->tickets + 1, st);
             P->tock(5);
             // optional second pass (CGS2), gated on the device
             k_cgs_decide<<<1, 1, 0, st>>>(gm, L, j);
             const double *gate = gm + L.scal + S_FLAG;
             P->tick(4);
-            launch_multidot(j + 1, n, V, W, P->partials, gate, st);
-            k_finalize_g<<<1, kRedThreads, 0, st>>>(P->partials, kRedBlocks, j + 2, gm + L.h2, gate);
+            launch_multidot<TV>(j + 1, ldv, V, W, P->partials, gate, gm + L.h2, P->tickets, st);
             P->tock(4);
             P->tick(5);
-            launch_update(j + 1, n, V, gm + L.h2, W, P->partials, gate, st);
-            k_finalize_g<<<1, kRedThreads, 0, st>>>(P->partials, kRedBlocks, 1, gm + L.scal + S_WN, gate);
+            launch_update<TV>(j + 1, ldv, V, gm + L.h2, W, P->partials, gate, gm + L.scal + S_WN, P->tickets + 1,
+                              st);
             P->tock(5);
             k_cgs_accum<<<1, 1, 0, st>>>(gm, L, j);
             P->tick(9);
             k_arnoldi<<<1, 1, 0, st>>>(gm, L, j);
             P->tock(9);
-            launch_scale_dev(n, W, gm + L.scal + S_INV, vn, st);
-            P->count(12);  // 2 multidot + 4 finalize + 2 update + decide + accum + arnoldi + scale
+            k_scale_dev<TV, TV><<<nb(n), kT, 0, st>>>(n, W, gm + L.scal + S_INV, vn);
+            P->count(8);  // 2 multidot + 2 update + decide + accum + arnoldi + scale
             its++;
             kdim = j + 1;
             cudaMemcpyAsync(P->hscal, gm + L.scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, st);
@@ -347,19 +457,31 @@ int gmres_solve(Problem *P, int mode, const double *b, double *x, double tol, in
             if (!(res == res)) break;  // NaN: leave the cycle, the true residual decides
             if (res <= tol || its >= maxit || wn == 0.0) break;
         }
+        // x += M^-1 (V y), then the true residual in FP64
         k_hsolve<<<1, 1, 0, st>>>(gm, L, kdim);
-        k_lincomb<<<nb(n), kT, 0, st>>>(n, V, n, kdim, gm + L.y, W);
+        k_lincomb<TV><<<nb(n), kT, 0, st>>>(n, V, ldv, kdim, gm + L.y, W);
         P->count(2);
-        ras_apply(P, W, Z);
-        P->count(launch_axpby(n, 1.0, Z, 1.0, x, st));
-        apply_J(P, mode, x, W);
-        P->count(launch_waxpy(n, b, -1.0, W, R, st));
+        ras_apply_t<TV>(P, W, Z);
+        k_add<TV><<<nb(n), kT, 0, st>>>(n, Z, x);
+        P->count(1);
+        // FP32 corrections are mass-neutral only to FP32 rounding: apply P to the FP64
+        // sum once more (P is linear and idempotent), so every Newton correction keeps
+        // sum s_c = 0 and the gauge of u to FP64 rounding
+        if constexpr (sizeof(TV) == sizeof(float)) project(P, x);
+        apply_J<double>(P, mode, x, Jx);
+        P->count(launch_waxpy(n, b, -1.0, Jx, R, st));
         beta = sqrt(norm2_host(P, R));
         if (!(beta == beta)) break;
     }
     *its_out = its;
     *res_out = beta;
     return NKS_OK;
+}
+
+int gmres_solve(Problem *P, int mode, const double *b, double *x, double tol, int *its_out, double *res_out)
+{
+    if (P->opts.precision == NKS_MIXED) return gmres_t<float>(P, basis32(P), mode, b, x, tol, its_out, res_out);
+    return gmres_t<double>(P, basis64(P), mode, b, x, tol, its_out, res_out);
 }
 
 }  // namespace nks

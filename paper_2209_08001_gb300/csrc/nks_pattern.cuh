@@ -215,3 +215,93 @@ __host__ __device__ constexpr Pattern make_pattern()
 }
 
 }  // namespace nks
+
+namespace nks {
+
+// ---------------------------------------------------------------------------
+// two-stage schedule of one triangular sweep over a wavefront level
+// ---------------------------------------------------------------------------
+//
+// Forward sweep (L y = b) row f of a point uses its strictly lower entries;
+// backward sweep (U x = y) its strictly upper entries.  Entries at other
+// points refer to earlier (forward) or later (backward) levels, which are
+// final when the level starts; entries at the same point refer to rows of
+// the same point.  Stage A runs, for every point of the level in parallel,
+// warp-uniform tasks over chunks of the other-point entries (at most kChunk
+// entries each): a row with one chunk and no same-point entry is finished in
+// stage A, otherwise the chunk sum goes to a partial.  Stage B, one thread
+// per point, finishes the remaining rows in sweep order from their partials
+// and same-point entries.
+
+constexpr int kChunk = 5;
+constexpr int kMaxTasks = 24;
+constexpr int kMaxPartials = 24;
+
+struct SweepPlan {
+    int ntask;
+    int t_row[kMaxTasks], t_b[kMaxTasks], t_e[kMaxTasks], t_part[kMaxTasks];  // t_part < 0: finishes the row
+    int npart;
+    int row_stage_b[kMaxNf];           // 1: the row is finished in stage B
+    int row_pb[kMaxNf], row_pe[kMaxNf];  // its partials [pb, pe)
+    int same_b[kMaxNf], same_e[kMaxNf];  // its same-point slot range (contiguous in column order)
+};
+
+template <int D, int NF, bool FWD>
+__host__ __device__ constexpr SweepPlan make_sweep_plan()
+{
+    constexpr Pattern P = make_pattern<D, NF>();
+    SweepPlan S{};
+    for (int f = 0; f < NF; f++) {
+        const int b = FWD ? P.rowoff[f] : P.rowoff[f] + P.diag[f] + 1;
+        const int e = FWD ? P.rowoff[f] + P.diag[f] : P.rowoff[f] + P.len[f];
+        // same-point entries form a contiguous run at offset (0,0,0) in column order
+        int sb = e, se = e;
+        for (int a = b; a < e; a++)
+            if (P.dx[a] == 0 && P.dy[a] == 0 && P.dz[a] == 0) {
+                if (sb == e) sb = a;
+                se = a + 1;
+            }
+        S.same_b[f] = sb;
+        S.same_e[f] = se;
+        // other-point entries: [b, sb) and [se, e)
+        const int n_other = (sb - b) + (e - se);
+        const int nch = (n_other + kChunk - 1) / kChunk;
+        const bool finish_in_a = (nch <= 1) && (se == sb);
+        S.row_stage_b[f] = finish_in_a ? 0 : 1;
+        S.row_pb[f] = S.npart;
+        // split [b, sb) then [se, e) into nch balanced chunks
+        int taken = 0;
+        for (int c = 0; c < nch; c++) {
+            const int want = (n_other * (c + 1)) / nch - (n_other * c) / nch;
+            // a chunk never straddles the same-point run: take from the first range, then the second
+            const int lo_idx = taken, hi_idx = taken + want;
+            const int first_len = sb - b;
+            int cb = 0, ce = 0;
+            if (hi_idx <= first_len) {
+                cb = b + lo_idx;
+                ce = b + hi_idx;
+            } else if (lo_idx >= first_len) {
+                cb = se + (lo_idx - first_len);
+                ce = se + (hi_idx - first_len);
+            } else {  // split at the run: two tasks
+                S.t_row[S.ntask] = f;
+                S.t_b[S.ntask] = b + lo_idx;
+                S.t_e[S.ntask] = sb;
+                S.t_part[S.ntask] = finish_in_a ? -1 : S.npart++;
+                S.ntask++;
+                cb = se;
+                ce = se + (hi_idx - first_len);
+            }
+            S.t_row[S.ntask] = f;
+            S.t_b[S.ntask] = cb;
+            S.t_e[S.ntask] = ce;
+            S.t_part[S.ntask] = finish_in_a ? -1 : S.npart++;
+            S.ntask++;
+            taken = hi_idx;
+        }
+        S.row_pe[f] = S.npart;
+    }
+    return S;
+}
+
+}  // namespace nks

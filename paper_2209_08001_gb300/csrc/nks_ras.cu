@@ -40,8 +40,9 @@ struct SubInfo {
     int L[3];                 // box extent
     int own0[3], own1[3];     // owned local range [own0, own1)
     int np, nlev;
+    int px, py, npx;          // odd row pitches of the box vector and its padded size (bank-conflict free levels)
     long long lvl_off;        // into lvl_ptr / lvl_blk (nlev + 1 entries)
-    long long pos_off;        // into lvl_lp (np entries)
+    long long pos_off;        // into lvl_lp (np entries): packed coordinates x | y << 10 | z << 20
     long long fac_off;        // into the factor array (elements)
     long long scr_off;        // into the global scratch vector (nf * np), when not in shared memory
 };
@@ -50,11 +51,16 @@ struct RasPlan {
     int nsub = 0, nslot = 0, nlow = 0, nup = 0;
     int threads = 64;
     int maxnp = 0;
+    int maxnpx = 0;                 // largest padded box vector
+    int maxcnt = 0;                 // most points in one wavefront level
+    int npart = 0;                  // stage-A partial sums per point (largest of the two sweeps)
     long long maxblk = 0;           // largest forward or backward part of a level (elements)
     long long fac_elems = 0;
     long long total_np = 0;         // overlapped points of all subdomains
     bool x_smem = true;
     size_t smem_bytes = 0;          // dynamic shared memory of the apply kernel (FP64 factors)
+    bool x_smem32 = true;
+    size_t smem_bytes32 = 0;        // same for the FP32 factors of the mixed-precision mode
     SubInfo *sub = nullptr;
     // runtime copies of the pattern for the assembly kernel
     char4 *tmpl = nullptr;          // (dx, dy, dz, field) per slot
@@ -65,17 +71,33 @@ struct RasPlan {
     int *lvl_ptr = nullptr, *lvl_lp = nullptr;
     long long *lvl_blk = nullptr;
     double *fac = nullptr;
+    float *fac32 = nullptr;         // FP32 copy of the factors (mixed precision)
     double *scratch = nullptr;
+    float *scratch32 = nullptr;
     double *proj = nullptr;         // projection sums
     int nmodes = 1;                 // null modes per displacement component
     int evenmask = 0;
-    bool attr_set = false;
+    bool attr_set = false, attr_set32 = false;
 };
 
 template <int D, int NF>
 struct Pat {
     static constexpr Pattern v = make_pattern<D, NF>();
 };
+
+template <int D, int NF, bool FWD>
+struct SPlan {
+    static constexpr SweepPlan v = make_sweep_plan<D, NF, FWD>();
+};
+
+template <int D, int NF>
+struct Sched {
+    static constexpr SweepPlan fwd = SPlan<D, NF, true>::v;
+    static constexpr SweepPlan bwd = SPlan<D, NF, false>::v;
+    static constexpr int ntask = fwd.ntask > bwd.ntask ? fwd.ntask : bwd.ntask;
+    static constexpr int npart = fwd.npart > bwd.npart ? fwd.npart : bwd.npart;
+};
+
 
 static Pattern compile_time_pattern(int d, int nf)
 {
@@ -94,12 +116,27 @@ __host__ __device__ static inline long long pad4(long long n) { return (n + 3) &
 __host__ __device__ static inline size_t pad16(size_t n) { return (n + 15) & ~(size_t)15; }
 
 // dynamic shared memory of the apply kernel: barriers, point table, two level
-// buffers and (when it fits) the sub-vector
+// buffers, stage-A partial sums and (when it fits) the sub-vector
 static size_t apply_smem(const RasPlan *R, int nf, size_t tsize, bool with_x)
 {
-    size_t b = 16 + pad16((size_t)R->maxnp * sizeof(int)) + 2 * pad16((size_t)R->maxblk * tsize);
-    if (with_x) b += pad16((size_t)R->maxnp * nf * tsize);
+    const int pstride = (R->maxcnt + 31) / 32 * 32;
+    size_t b = 16 + pad16((size_t)R->maxnp * sizeof(int)) + 2 * pad16((size_t)R->maxblk * tsize) +
+               pad16((size_t)R->npart * pstride * tsize);
+    if (with_x) b += pad16((size_t)R->maxnpx * nf * tsize);
     return b;
+}
+
+static int sweep_partials(int d, int nf)
+{
+    switch (d * 10 + nf) {
+    case 12: return Sched<1, 2>::npart;
+    case 13: return Sched<1, 3>::npart;
+    case 22: return Sched<2, 2>::npart;
+    case 24: return Sched<2, 4>::npart;
+    case 32: return Sched<3, 2>::npart;
+    case 35: return Sched<3, 5>::npart;
+    }
+    return 0;
 }
 
 int ras_plan_create(Problem *P, std::string &err)
@@ -198,6 +235,12 @@ int ras_plan_create(Problem *P, std::string &err)
                 }
                 si.np = si.L[0] * si.L[1] * si.L[2];
                 R->maxnp = std::max(R->maxnp, si.np);
+                // odd pitches: points of one wavefront level are (pitch - 2), (pitch_xy - 4), ... apart,
+                // all odd, so their 8-byte accesses spread over the shared-memory banks
+                si.px = si.L[0] | 1;
+                si.py = d >= 2 ? (si.L[1] | 1) : 1;
+                si.npx = si.px * si.py * si.L[2];
+                R->maxnpx = std::max(R->maxnpx, si.npx);
                 R->total_np += si.np;
                 const int nlev = (si.L[0] - 1) + 2 * (si.L[1] - 1) + 4 * (si.L[2] - 1) + 1;
                 si.nlev = nlev;
@@ -208,7 +251,7 @@ int ras_plan_create(Problem *P, std::string &err)
                 for (int lz = 0; lz < si.L[2]; lz++)
                     for (int ly = 0; ly < si.L[1]; ly++)
                         for (int lx = 0; lx < si.L[0]; lx++)
-                            bylev[lx + 2 * ly + 4 * lz].push_back(lx + si.L[0] * (ly + si.L[1] * lz));
+                            bylev[lx + 2 * ly + 4 * lz].push_back(lx | (ly << 10) | (lz << 20));
                 int cnt = 0;
                 long long blk = 0;
                 for (int l = 0; l < nlev; l++) {
@@ -220,19 +263,21 @@ int ras_plan_create(Problem *P, std::string &err)
                     }
                     const long long cp = pad4((long long)bylev[l].size());
                     R->maxblk = std::max(R->maxblk, std::max<long long>(CP.nlow, CP.nup + nf) * cp);
-                    R->threads = std::max(R->threads, (int)((bylev[l].size() + 31) / 32 * 32));
+                    R->maxcnt = std::max(R->maxcnt, (int)bylev[l].size());
                     blk += (long long)per_pt * cp;
                 }
                 lvl_ptr.push_back(cnt);
                 lvl_blk.push_back(blk);
                 fac_off += blk;
                 si.scr_off = scr_off;
-                scr_off += (long long)nf * si.np;
+                scr_off += (long long)nf * si.npx;
             }
-    R->threads = std::min(R->threads, 256);
+    R->npart = sweep_partials(d, nf);
     R->fac_elems = fac_off;
     R->x_smem = apply_smem(R, nf, sizeof(double), true) <= 227 * 1024;
     R->smem_bytes = apply_smem(R, nf, sizeof(double), R->x_smem);
+    R->x_smem32 = apply_smem(R, nf, sizeof(float), true) <= 227 * 1024;
+    R->smem_bytes32 = apply_smem(R, nf, sizeof(float), R->x_smem32);
     if (R->smem_bytes > 227 * 1024) {
         err = "decomposition: subdomain boxes too large for the Schwarz kernel (use more subdomains)";
         return NKS_EINVAL;
@@ -264,8 +309,14 @@ int ras_plan_create(Problem *P, std::string &err)
     }
     R->fac = (double *)P->dalloc(sizeof(double) * (size_t)fac_off);
     R->proj = (double *)P->dalloc(sizeof(double) * 64);
-    if (!R->x_smem) R->scratch = (double *)P->dalloc(sizeof(double) * (size_t)scr_off);
-    if (!R->fac || !R->proj || (!R->x_smem && !R->scratch)) {
+    const bool mixed = P->opts.precision == NKS_MIXED;
+    if (!R->x_smem && !mixed) R->scratch = (double *)P->dalloc(sizeof(double) * (size_t)scr_off);
+    if (mixed) {
+        R->fac32 = (float *)P->dalloc(sizeof(float) * (size_t)fac_off);
+        if (!R->x_smem32) R->scratch32 = (float *)P->dalloc(sizeof(float) * (size_t)scr_off);
+    }
+    if (!R->fac || !R->proj || (!R->x_smem && !mixed && !R->scratch) || (mixed && !R->fac32) ||
+        (mixed && !R->x_smem32 && !R->scratch32)) {
         err = "out of device memory (Schwarz factors)";
         return NKS_ENOMEM;
     }
@@ -345,8 +396,8 @@ __global__ void k_ras_factor(DGrid g, DCoef k, double dt, int mode, FacTables T,
         double *blk = F + lblk[lev];
         for (int i = lptr[lev] + threadIdx.x; i < lptr[lev + 1]; i += blockDim.x) {
             const int kk = i - lptr[lev];
-            const int lp = lp_of[i];
-            const int lx = lp % si.L[0], ly = (lp / si.L[0]) % si.L[1], lz = lp / (si.L[0] * si.L[1]);
+            const int pk = lp_of[i];
+            const int lx = pk & 1023, ly = (pk >> 10) & 1023, lz = pk >> 20;
             const int gx = wrapi(si.org[0] + lx, g.n[0]), gy = wrapi(si.org[1] + ly, g.n[1]),
                       gz = wrapi(si.org[2] + lz, g.n[2]);
             const long long gp = index_of(g, gx, gy, gz);
@@ -378,7 +429,7 @@ __global__ void k_ras_factor(DGrid g, DCoef k, double dt, int mode, FacTables T,
                     const int fk = o.w;
                     // level-major position of the earlier point (points of a level are stored in lp order)
                     const int lv = nx + 2 * ny + 4 * nz;
-                    const int lpk = nx + si.L[0] * (ny + si.L[1] * nz);
+                    const int lpk = nx | (ny << 10) | (nz << 20);  // points of a level are stored in this key's order
                     int lo = lptr[lv], hi = lptr[lv + 1] - 1;
                     while (lo < hi) {
                         const int mid = (lo + hi) >> 1;
@@ -472,14 +523,12 @@ __device__ __forceinline__ bool nb_inbox(int lx, int ly, int lz, const SubInfo &
     return ok;
 }
 
-// s -= sum over pattern slots [B, E) of the stored entries times x at their
-// columns.  A column outside the box has a stored entry of exactly 0 (dropped
-// at assembly; no ILU(0) update reaches it), so its product is read at the
-// point itself and contributes nothing: no branch, no load depends on x.
+// sum over pattern slots [B, E) of stored entries times x at their columns (see row_dot)
 template <int D, int NF, int B, int E, typename T>
-__device__ __forceinline__ T row_dot(T s, const T *__restrict__ part, long long cp, int k, const T *x, int np, int lp,
-                                     int lx, int ly, int lz, const SubInfo &si, int sy, int sz)
+__device__ __forceinline__ T slot_sum(const T *__restrict__ part, long long cp, int k, const T *x, int np, int lp,
+                                      int lx, int ly, int lz, const SubInfo &si, int sy, int sz)
 {
+    T s = (T)0;
     static_for<B, E>([&](auto ic) {
         constexpr int a = decltype(ic)::value;
         constexpr int dx = Pat<D, NF>::v.dx[a], dy = Pat<D, NF>::v.dy[a], dz = Pat<D, NF>::v.dz[a];
@@ -487,16 +536,67 @@ __device__ __forceinline__ T row_dot(T s, const T *__restrict__ part, long long 
         constexpr int row = Pat<D, NF>::v.st[a];
         const bool ok = nb_inbox<dx, dy, dz>(lx, ly, lz, si);
         const int idx = ok ? lp + dx + sy * dy + sz * dz : lp;
-        s -= part[row * cp + k] * x[fc * np + idx];
+        s += part[row * cp + k] * x[fc * np + idx];
     });
     return s;
 }
 
+// Stage A of one sweep over a level: task t of the compile-time schedule for point k.
+template <int D, int NF, bool FWD, typename T>
+__device__ __forceinline__ void stage_a(int task, int kk, int lp, int lx, int ly, int lz, const T *B, long long cp,
+                                        T *x, int np, T *pt, int pstride, const SubInfo &si, int sy, int sz)
+{
+    using SP = SPlan<D, NF, FWD>;
+    static_for<0, SP::v.ntask>([&](auto ti) {
+        constexpr int t = decltype(ti)::value;
+        if (task != t) return;
+        constexpr int f = SP::v.t_row[t];
+        constexpr int tb = SP::v.t_b[t], te = SP::v.t_e[t], tp = SP::v.t_part[t];
+        constexpr int drow = Pat<D, NF>::v.nup + f;  // inverse pivot row in the backward part
+        const T s = slot_sum<D, NF, tb, te, T>(B, cp, kk, x, np, lp, lx, ly, lz, si, sy, sz);
+        if constexpr (tp >= 0) {
+            pt[tp * pstride + kk] = s;
+        } else if constexpr (FWD) {
+            x[f * np + lp] -= s;
+        } else {
+            x[f * np + lp] = (x[f * np + lp] - s) * B[(long long)drow * cp + kk];
+        }
+    });
+}
+
+// Stage B: rows of one point finished from their partials and same-point entries, in sweep order.
+template <int D, int NF, bool FWD, typename T>
+__device__ __forceinline__ void stage_b(int kk, int lp, int lx, int ly, int lz, const T *B, long long cp, T *x,
+                                        int np, const T *pt, int pstride, const SubInfo &si, int sy, int sz)
+{
+    using SP = SPlan<D, NF, FWD>;
+    static_for<0, NF>([&](auto fi) {
+        constexpr int f = FWD ? decltype(fi)::value : NF - 1 - decltype(fi)::value;
+        constexpr int stb = SP::v.row_stage_b[f];
+        if constexpr (stb) {
+            constexpr int sb = SP::v.same_b[f], se = SP::v.same_e[f], pb = SP::v.row_pb[f], pe = SP::v.row_pe[f];
+            constexpr int drow = Pat<D, NF>::v.nup + f;
+            T s = slot_sum<D, NF, sb, se, T>(B, cp, kk, x, np, lp, lx, ly, lz, si, sy, sz);
+            static_for<pb, pe>([&](auto pi) {
+                constexpr int q = decltype(pi)::value;
+                s += pt[q * pstride + kk];
+            });
+            if constexpr (FWD) x[f * np + lp] -= s;
+            else x[f * np + lp] = (x[f * np + lp] - s) * B[(long long)drow * cp + kk];
+        }
+    });
+}
+
+// One Schwarz subdomain per block: gather, forward and backward ILU(0) sweeps
+// level by level (factor parts streamed by TMA one level ahead, two-stage
+// schedule inside a level), restricted prolongation.  Threads are grouped in
+// warps per stage-A task: warp w serves task w / wpt, points (w % wpt) * 32 + lane.
 template <int D, int NF, typename T, typename TV>
-__global__ void k_ras_apply(DGrid g, const SubInfo *__restrict__ subs, const int *__restrict__ lvl_ptr,
+__global__ void __launch_bounds__(1024) k_ras_apply(DGrid g, const SubInfo *__restrict__ subs, const int *__restrict__ lvl_ptr,
                             const long long *__restrict__ lvl_blk, const int *__restrict__ lvl_lp,
                             const T *__restrict__ fac, const TV *__restrict__ r, TV *__restrict__ z,
-                            T *__restrict__ scratch, int x_in_smem, int maxnp, long long maxblk, int *flag)
+                            T *__restrict__ scratch, int x_in_smem, int maxnp, long long maxblk, int wpt,
+                            int pstride, int *flag)
 {
     constexpr Pattern PT = Pat<D, NF>::v;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -504,16 +604,21 @@ __global__ void k_ras_apply(DGrid g, const SubInfo *__restrict__ subs, const int
     int *lps = reinterpret_cast<int *>(smem + 16);
     T *buf0 = reinterpret_cast<T *>(smem + 16 + pad16((size_t)maxnp * sizeof(int)));
     T *buf1 = reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(buf0) + pad16((size_t)maxblk * sizeof(T)));
+    T *pt = reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(buf1) + pad16((size_t)maxblk * sizeof(T)));
     const SubInfo si = subs[blockIdx.x];
-    T *x = x_in_smem ? reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(buf1) + pad16((size_t)maxblk * sizeof(T)))
+    T *x = x_in_smem ? reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(pt) +
+                                             pad16((size_t)Sched<D, NF>::npart * pstride * sizeof(T)))
                      : scratch + si.scr_off;
-    const int np = si.np, nlev = si.nlev;
+    const int np = si.np, nlev = si.nlev;  // x holds NF planes of si.npx (padded) entries
     const int *lptr = lvl_ptr + si.lvl_off;
     const long long *lblk = lvl_blk + si.lvl_off;
     const T *F = fac + si.fac_off;
     const long long N = g.N;
-    const int sy = si.L[0], sz = si.L[0] * si.L[1];
+    const int sy = si.px, sz = si.px * si.py;
+    const int npx = si.npx;
     const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int task = warp / wpt, kq0 = (warp % wpt) * 32 + lane;
     const int nuse = 2 * nlev;  // forward parts of levels 0..nlev-1, then backward parts of nlev-1..0
 
     // the copy of use `it` into buffer it & 1
@@ -537,12 +642,13 @@ __global__ void k_ras_apply(DGrid g, const SubInfo *__restrict__ subs, const int
     if (tid == 0) issue(0);
     for (int i = tid; i < np; i += blockDim.x) lps[i] = lvl_lp[si.pos_off + i];
     // gather R_i^delta r
-    for (int lp = tid; lp < np; lp += blockDim.x) {
-        const int lx = lp % si.L[0], ly = (lp / si.L[0]) % si.L[1], lz = lp / sz;
+    for (int q = tid; q < np; q += blockDim.x) {
+        const int lx = q % si.L[0], ly = (q / si.L[0]) % si.L[1], lz = q / (si.L[0] * si.L[1]);
+        const int lp = lx + sy * ly + sz * lz;
         const long long gp = index_of(g, wrapi(si.org[0] + lx, g.n[0]), wrapi(si.org[1] + ly, g.n[1]),
                                       wrapi(si.org[2] + lz, g.n[2]));
 #pragma unroll
-        for (int f = 0; f < NF; f++) x[f * np + lp] = (T)r[f * N + gp];
+        for (int f = 0; f < NF; f++) x[f * npx + lp] = (T)r[f * N + gp];
     }
     __syncthreads();
     bool failed = false;
@@ -553,28 +659,26 @@ __global__ void k_ras_apply(DGrid g, const SubInfo *__restrict__ subs, const int
         const int base = lptr[lev], cnt = lptr[lev + 1] - base;
         const long long cp = pad4((long long)cnt);
         const T *B = (it & 1) ? buf1 : buf0;
-        if (ok) {
-            for (int kk = tid; kk < cnt; kk += blockDim.x) {
-                const int lp = lps[base + kk];
-                const int lx = lp % si.L[0], ly = (lp / si.L[0]) % si.L[1], lz = lp / sz;
-                if (it < nlev) {  // forward: L y = b (unit lower triangular)
-                    static_for<0, NF>([&](auto fi) {
-                        constexpr int f = decltype(fi)::value;
-                        constexpr int b0 = PT.rowoff[f], e0 = PT.rowoff[f] + PT.diag[f];
-                        x[f * np + lp] = row_dot<D, NF, b0, e0, T>(x[f * np + lp], B, cp, kk, x, np, lp, lx, ly, lz,
-                                                                   si, sy, sz);
-                    });
-                } else {  // backward: U x = y
-                    static_for<0, NF>([&](auto fi) {
-                        constexpr int f = NF - 1 - decltype(fi)::value;
-                        constexpr int b0 = PT.rowoff[f] + PT.diag[f] + 1, e0 = PT.rowoff[f] + PT.len[f];
-                        const T s = row_dot<D, NF, b0, e0, T>(x[f * np + lp], B, cp, kk, x, np, lp, lx, ly, lz, si,
-                                                              sy, sz);
-                        x[f * np + lp] = s * B[(long long)(PT.nup + f) * cp + kk];
-                    });
-                }
+        const bool fwd = it < nlev;
+        // stage A: chunks of other-point entries, warp-uniform tasks
+        if (ok)
+            for (int kq = kq0; kq < cnt; kq += wpt * 32) {
+                const int pk = lps[base + kq];
+                const int lx = pk & 1023, ly = (pk >> 10) & 1023, lz = pk >> 20;
+                const int lp = lx + sy * ly + sz * lz;
+                if (fwd) stage_a<D, NF, true, T>(task, kq, lp, lx, ly, lz, B, cp, x, npx, pt, pstride, si, sy, sz);
+                else stage_a<D, NF, false, T>(task, kq, lp, lx, ly, lz, B, cp, x, npx, pt, pstride, si, sy, sz);
             }
-        }
+        __syncthreads();
+        // stage B: one thread per point
+        if (ok)
+            for (int k = tid; k < cnt; k += blockDim.x) {
+                const int pk = lps[base + k];
+                const int lx = pk & 1023, ly = (pk >> 10) & 1023, lz = pk >> 20;
+                const int lp = lx + sy * ly + sz * lz;
+                if (fwd) stage_b<D, NF, true, T>(k, lp, lx, ly, lz, B, cp, x, npx, pt, pstride, si, sy, sz);
+                else stage_b<D, NF, false, T>(k, lp, lx, ly, lz, B, cp, x, npx, pt, pstride, si, sy, sz);
+            }
         failed = __syncthreads_or(!ok);
         if (failed) break;
     }
@@ -588,82 +692,95 @@ __global__ void k_ras_apply(DGrid g, const SubInfo *__restrict__ subs, const int
         return;
     }
     // restricted prolongation: owned points only
-    for (int lp = tid; lp < np; lp += blockDim.x) {
-        const int lx = lp % si.L[0], ly = (lp / si.L[0]) % si.L[1], lz = lp / sz;
+    for (int q = tid; q < np; q += blockDim.x) {
+        const int lx = q % si.L[0], ly = (q / si.L[0]) % si.L[1], lz = q / (si.L[0] * si.L[1]);
         if (lx < si.own0[0] || lx >= si.own1[0] || ly < si.own0[1] || ly >= si.own1[1] || lz < si.own0[2] ||
             lz >= si.own1[2])
             continue;
+        const int lp = lx + sy * ly + sz * lz;
         const long long gp = index_of(g, wrapi(si.org[0] + lx, g.n[0]), wrapi(si.org[1] + ly, g.n[1]),
                                       wrapi(si.org[2] + lz, g.n[2]));
 #pragma unroll
-        for (int f = 0; f < NF; f++) z[f * N + gp] = (TV)x[f * np + lp];
+        for (int f = 0; f < NF; f++) z[f * N + gp] = (TV)x[f * npx + lp];
     }
 }
 
-// projection P: sums of z_c and of sign_m(p) z_uI for every null mode m
-__global__ void __launch_bounds__(kRedThreads) k_proj_dots(DGrid g, int nf, int evenmask, int nmodes,
-                                                           const double *__restrict__ z, double *__restrict__ partials)
+// projection P: sums of z_c and of sign_m(p) z_uI for every null mode m.
+// Mode mi is the sign pattern prod over the axes J in mask[mi] of (-1)^x_J.
+struct ModeMasks {
+    int m[8];
+};
+
+template <int NF, int NM, typename TV>
+__global__ void __launch_bounds__(kRedThreads, 4) k_proj_dots(DGrid g, ModeMasks mm, const TV *__restrict__ z,
+                                                              double *__restrict__ partials, double *__restrict__ out,
+                                                              unsigned int *ticket)
 {
+    constexpr int K = 1 + (NF - 2) * NM;
     const long long N = g.N;
-    const int K = 1 + (nf - 2) * nmodes;
-    double acc[25];
-    for (int i = 0; i < 25; i++) acc[i] = 0.0;
+    double acc[K];
+#pragma unroll
+    for (int i = 0; i < K; i++) acc[i] = 0.0;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
-        acc[0] += z[p];
-        if (nf > 2) {
+        acc[0] += (double)z[p];
+        if constexpr (NF > 2) {
             int x, y, zz;
             coords_of(g, p, x, y, zz);
-            const int par[3] = {x & 1, y & 1, zz & 1};
-            int mi = 0;
-            for (int m = 0; m < 8; m++) {
-                if ((m & ~evenmask) != 0 || m >= (1 << g.dim)) continue;
-                int s = 0;
-                for (int J = 0; J < g.dim; J++)
-                    if (m & (1 << J)) s += par[J];
-                const double sg = (s & 1) ? -1.0 : 1.0;
-                for (int I = 0; I < nf - 2; I++) acc[1 + I * nmodes + mi] += sg * z[(2 + I) * N + p];
-                mi++;
+            const int par = (x & 1) | ((y & 1) << 1) | ((zz & 1) << 2);
+#pragma unroll
+            for (int mi = 0; mi < NM; mi++) {
+                const double sg = (__popc(mm.m[mi] & par) & 1) ? -1.0 : 1.0;
+#pragma unroll
+                for (int I = 0; I < NF - 2; I++) acc[1 + I * NM + mi] += sg * (double)z[(2 + I) * N + p];
             }
         }
     }
-    __shared__ double red[25][kRedThreads / 32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int k = 0; k < K; k++) {
-        double a = acc[k];
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-        if (lane == 0) red[k][warp] = a;
-    }
-    __syncthreads();
-    if ((int)threadIdx.x < K) {
-        double a = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); w++) a += red[threadIdx.x][w];
-        partials[(size_t)blockIdx.x * K + threadIdx.x] = a;
-    }
+    block_reduce_store<K>(acc, partials);
+    grid_finalize(partials, K, out, ticket);
 }
 
-__global__ void k_proj_sub(DGrid g, int nf, int evenmask, int nmodes, const double *__restrict__ sums,
-                           double *__restrict__ z)
+template <int NF, int NM, typename TV>
+__global__ void k_proj_sub(DGrid g, ModeMasks mm, const double *__restrict__ sums, TV *__restrict__ z)
 {
     long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long N = g.N;
     if (p >= N) return;
     const double invN = 1.0 / (double)N;
-    z[p] -= sums[0] * invN;
-    if (nf > 2) {
+    z[p] = (TV)((double)z[p] - sums[0] * invN);
+    if constexpr (NF > 2) {
         int x, y, zz;
         coords_of(g, p, x, y, zz);
-        const int par[3] = {x & 1, y & 1, zz & 1};
-        int mi = 0;
-        for (int m = 0; m < 8; m++) {
-            if ((m & ~evenmask) != 0 || m >= (1 << g.dim)) continue;
-            int s = 0;
-            for (int J = 0; J < g.dim; J++)
-                if (m & (1 << J)) s += par[J];
-            const double sg = (s & 1) ? -1.0 : 1.0;
-            for (int I = 0; I < nf - 2; I++) z[(2 + I) * N + p] -= sums[1 + I * nmodes + mi] * invN * sg;
-            mi++;
+        const int par = (x & 1) | ((y & 1) << 1) | ((zz & 1) << 2);
+#pragma unroll
+        for (int I = 0; I < NF - 2; I++) {
+            double s = 0.0;
+#pragma unroll
+            for (int mi = 0; mi < NM; mi++) {
+                const double sg = (__popc(mm.m[mi] & par) & 1) ? -1.0 : 1.0;
+                s += sums[1 + I * NM + mi] * sg;
+            }
+            z[(2 + I) * N + p] = (TV)((double)z[(2 + I) * N + p] - s * invN);
         }
     }
+}
+
+template <int NF, int NM, typename TV>
+void launch_project_t(Problem *P, TV *z)
+{
+    RasPlan *R = P->ras;
+    ModeMasks mm{};
+    int mi = 0;
+    for (int m = 0; m < (1 << P->g.dim); m++)
+        if ((m & ~R->evenmask) == 0) mm.m[mi++] = m;
+    k_proj_dots<NF, NM, TV><<<kRedBlocks, kRedThreads, 0, P->stream>>>(P->g, mm, z, P->partials, R->proj,
+                                                                         P->tickets + 2);
+    k_proj_sub<NF, NM, TV><<<(int)((P->N + 255) / 256), 256, 0, P->stream>>>(P->g, mm, R->proj, z);
+}
+
+__global__ void k_to_float(long long n, const double *__restrict__ a, float *__restrict__ b)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        b[i] = (float)a[i];
 }
 
 void launch_factor(Problem *P, int mode)
@@ -684,18 +801,29 @@ void launch_factor(Problem *P, int mode)
                                                 P->mob, R->fac, P->dflag);
 }
 
-template <int D, int NF>
-void launch_apply_t(Problem *P, const double *r, double *z)
+// FP64 vectors use the FP64 factors; FP32 vectors (mixed precision) the FP32 copy
+template <int D, int NF, typename TV>
+void launch_apply_t(Problem *P, const TV *r, TV *z)
 {
     RasPlan *R = P->ras;
-    if (R->smem_bytes > 48 * 1024 && !R->attr_set) {
-        cudaFuncSetAttribute(k_ras_apply<D, NF, double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)R->smem_bytes);
-        R->attr_set = true;
+    const int ntask = Sched<D, NF>::ntask;
+    const int wpt = std::max(1, std::min((R->maxcnt + 31) / 32, 32 / ntask));  // warps per stage-A task
+    const int threads = ntask * wpt * 32;
+    const int pstride = (R->maxcnt + 31) / 32 * 32;
+    constexpr bool f32 = sizeof(TV) == sizeof(float);
+    using T = TV;
+    const size_t smem = f32 ? R->smem_bytes32 : R->smem_bytes;
+    bool &attr = f32 ? R->attr_set32 : R->attr_set;
+    if (smem > 48 * 1024 && !attr) {
+        cudaFuncSetAttribute(k_ras_apply<D, NF, T, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
     }
-    k_ras_apply<D, NF, double, double><<<R->nsub, R->threads, R->smem_bytes, P->stream>>>(
-        P->g, R->sub, R->lvl_ptr, R->lvl_blk, R->lvl_lp, R->fac, r, z, R->scratch, R->x_smem ? 1 : 0, R->maxnp,
-        R->maxblk, P->dflag);
+    const T *fac = f32 ? reinterpret_cast<const T *>(R->fac32) : reinterpret_cast<const T *>(R->fac);
+    T *scr = f32 ? reinterpret_cast<T *>(R->scratch32) : reinterpret_cast<T *>(R->scratch);
+    const int xs = f32 ? R->x_smem32 : R->x_smem;
+    k_ras_apply<D, NF, T, TV><<<R->nsub, threads, smem, P->stream>>>(P->g, R->sub, R->lvl_ptr, R->lvl_blk, R->lvl_lp,
+                                                                    fac, r, z, scr, xs ? 1 : 0, R->maxnp, R->maxblk,
+                                                                    wpt, pstride, P->dflag);
 }
 
 }  // namespace
@@ -725,30 +853,60 @@ int ras_factor(Problem *P, int mode)
         P->err = "zero pivot in an ILU(0) subdomain factorisation";
         return NKS_EPIVOT;
     }
+    if (P->opts.precision == NKS_MIXED) {
+        k_to_float<<<4 * 152, 256, 0, P->stream>>>(P->ras->fac_elems, P->ras->fac, P->ras->fac32);
+        P->count(1);
+    }
     P->factored = true;
     return NKS_OK;
 }
 
-void project(Problem *P, double *z)
+template <typename TV>
+void project_t(Problem *P, TV *z)
 {
     RasPlan *R = P->ras;
-    const int K = 1 + (P->nf - 2) * R->nmodes;
     P->tick(6);
-    k_proj_dots<<<kRedBlocks, kRedThreads, 0, P->stream>>>(P->g, P->nf, R->evenmask, R->nmodes, z, P->partials);
-    launch_finalize(P->partials, kRedBlocks, K, R->proj, P->stream);
-    k_proj_sub<<<(int)((P->N + 255) / 256), 256, 0, P->stream>>>(P->g, P->nf, R->evenmask, R->nmodes, R->proj, z);
-    P->count(3);
+    if (P->nf == 2) launch_project_t<2, 1, TV>(P, z);
+    else {
+        const int code = P->nf * 10 + R->nmodes;
+        switch (code) {
+        case 31: launch_project_t<3, 1, TV>(P, z); break;
+        case 32: launch_project_t<3, 2, TV>(P, z); break;
+        case 41: launch_project_t<4, 1, TV>(P, z); break;
+        case 42: launch_project_t<4, 2, TV>(P, z); break;
+        case 44: launch_project_t<4, 4, TV>(P, z); break;
+        case 51: launch_project_t<5, 1, TV>(P, z); break;
+        case 52: launch_project_t<5, 2, TV>(P, z); break;
+        case 54: launch_project_t<5, 4, TV>(P, z); break;
+        case 58: launch_project_t<5, 8, TV>(P, z); break;
+        }
+    }
+    P->count(2);
     P->tock(6);
 }
 
-void ras_apply(Problem *P, const double *r, double *z)
+void project(Problem *P, double *z) { project_t<double>(P, z); }
+
+template <typename TV>
+void ras_apply_t(Problem *P, const TV *r, TV *z)
 {
     P->tick(2);
-    NKS_DISPATCH(launch_apply_t, P, r, z);
+    switch (P->g.dim * 10 + P->nf) {
+    case 12: launch_apply_t<1, 2, TV>(P, r, z); break;
+    case 13: launch_apply_t<1, 3, TV>(P, r, z); break;
+    case 22: launch_apply_t<2, 2, TV>(P, r, z); break;
+    case 24: launch_apply_t<2, 4, TV>(P, r, z); break;
+    case 32: launch_apply_t<3, 2, TV>(P, r, z); break;
+    case 35: launch_apply_t<3, 5, TV>(P, r, z); break;
+    }
     P->count(1);
     P->tock(2);
-    project(P, z);
+    project_t<TV>(P, z);
 }
+template void ras_apply_t<double>(Problem *, const double *, double *);
+template void ras_apply_t<float>(Problem *, const float *, float *);
+
+void ras_apply(Problem *P, const double *r, double *z) { ras_apply_t<double>(P, r, z); }
 
 // algorithmic work of one Schwarz sweep (both triangular solves over every
 // overlapped point): bytes of factors + gathered and written vectors, FLOPs

@@ -128,13 +128,14 @@ __device__ inline bool in_domain(double c, double e)
 }
 
 // symmetric gradient of the displacement at (x, y, z): Du[I][J] = Dhat_J u_I
-__device__ inline void grad_u(const DGrid &g, const double *U /* field 2 plane */, int x, int y, int z,
+template <typename TV>
+__device__ inline void grad_u(const DGrid &g, const TV *U /* field 2 plane */, int x, int y, int z,
                               double (&Du)[3][3])
 {
     const double i2h = 0.5 / g.h;
     for (int I = 0; I < g.dim; I++)
         for (int J = 0; J < g.dim; J++)
-            Du[I][J] = (U[I * g.N + nbrJ(g, x, y, z, J, +1)] - U[I * g.N + nbrJ(g, x, y, z, J, -1)]) * i2h;
+            Du[I][J] = ((double)U[I * g.N + nbrJ(g, x, y, z, J, +1)] - (double)U[I * g.N + nbrJ(g, x, y, z, J, -1)]) * i2h;
 }
 
 // sigma = C : (sym(Du) - s I) for the cubic Hooke law, packed by scomp()
@@ -272,10 +273,13 @@ __global__ void __launch_bounds__(kRedThreads) k_res_b(DGrid g, DCoef k, double 
     block_reduce_store<1>(acc, partials);
 }
 
-// Jacobian action, pass A: dG_c (linearised G_c), (J v)_eta, sigma(eps(v_u) - eps0 v_c I)
+// Jacobian action, pass A: dG_c (linearised G_c), (J v)_eta, sigma(eps(v_u) - eps0 v_c I).
+// v and J v are stored as TV (FP64, or FP32 in the mixed-precision Krylov basis);
+// the arithmetic is FP64.
+template <typename TV>
 __global__ void k_jv_a(DGrid g, DCoef k, double dt, int mode, const double *__restrict__ part,
-                       const double *__restrict__ v, double *__restrict__ dG, double *__restrict__ sig,
-                       double *__restrict__ Jv)
+                       const TV *__restrict__ v, double *__restrict__ dG, double *__restrict__ sig,
+                       TV *__restrict__ Jv)
 {
     long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (p >= g.N) return;
@@ -291,26 +295,27 @@ __global__ void k_jv_a(DGrid g, DCoef k, double dt, int mode, const double *__re
         for (int K = 0; K < g.dim; K++) trv += Du[K][K];
     }
     if (mode != 0) {
-        Jv[N + p] = ve;
+        Jv[N + p] = (TV)ve;
         return;
     }
     const double ih2 = 1.0 / (g.h * g.h);
     double lc = 0.0, le = 0.0;
     for (int J = 0; J < g.dim; J++) {
         const long long pp = nbrJ(g, x, y, z, J, +1), pm = nbrJ(g, x, y, z, J, -1);
-        lc += v[pp] + v[pm] - 2.0 * vc;
-        le += v[N + pp] + v[N + pm] - 2.0 * ve;
+        lc += (double)v[pp] + (double)v[pm] - 2.0 * vc;
+        le += (double)v[N + pp] + (double)v[N + pm] - 2.0 * ve;
     }
     double dg = part[p] * vc + part[N + p] * ve - 0.5 * k.gamma_c * lc * ih2;
     if (k.elastic) dg += -0.5 * k.eps0 * k.lam * (trv - g.dim * k.eps0 * vc);
     dG[p] = dg;
-    Jv[N + p] = ve / dt + part[2 * N + p] * vc + part[3 * N + p] * ve - 1.5 * k.gamma_eta * le * ih2;
+    Jv[N + p] = (TV)(ve / dt + part[2 * N + p] * vc + part[3 * N + p] * ve - 1.5 * k.gamma_eta * le * ih2);
 }
 
 // Jacobian action, pass B: (J v)_c = v_c/dt - D M D dG_c, (J v)_u = sum_J Dhat_J sigma(v)_IJ
+template <typename TV>
 __global__ void k_jv_b(DGrid g, DCoef k, double dt, int mode, const double *__restrict__ mob,
-                       const double *__restrict__ v, const double *__restrict__ dG, const double *__restrict__ sig,
-                       double *__restrict__ Jv)
+                       const TV *__restrict__ v, const double *__restrict__ dG, const double *__restrict__ sig,
+                       TV *__restrict__ Jv)
 {
     long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (p >= g.N) return;
@@ -325,7 +330,7 @@ __global__ void k_jv_b(DGrid g, DCoef k, double dt, int mode, const double *__re
             const long long pp = nbrJ(g, x, y, z, J, +1), pm = nbrJ(g, x, y, z, J, -1);
             flux += mob[J * N + p] * (dG[pp] - G0) - mob[J * N + pm] * (G0 - dG[pm]);
         }
-        Jv[p] = v[p] / dt - flux * ih2;
+        Jv[p] = (TV)((double)v[p] / dt - flux * ih2);
     } else {
         Jv[p] = v[p];
     }
@@ -337,7 +342,7 @@ __global__ void k_jv_b(DGrid g, DCoef k, double dt, int mode, const double *__re
                 const int cmp = scomp(g.dim, I, J);
                 div += (sig[cmp * N + nbrJ(g, x, y, z, J, +1)] - sig[cmp * N + nbrJ(g, x, y, z, J, -1)]) * i2h;
             }
-            Jv[(2 + I) * N + p] = div;
+            Jv[(2 + I) * N + p] = (TV)div;
         }
     }
 }
@@ -437,12 +442,23 @@ int launch_residual(const DGrid &g, const DCoef &k, double dt, int mode, const d
     return 2;
 }
 
-int launch_jv(const DGrid &g, const DCoef &k, double dt, int mode, const double *part, const double *mob,
-               const double *v, double *dG, double *sig, double *Jv, cudaStream_t st)
+template <typename TV>
+int launch_jv_t(const DGrid &g, const DCoef &k, double dt, int mode, const double *part, const double *mob,
+                const TV *v, double *dG, double *sig, TV *Jv, cudaStream_t st)
 {
-    k_jv_a<<<blocks_for(g.N), kThreads, 0, st>>>(g, k, dt, mode, part, v, dG, sig, Jv);
-    k_jv_b<<<blocks_for(g.N), kThreads, 0, st>>>(g, k, dt, mode, mob, v, dG, sig, Jv);
+    k_jv_a<TV><<<blocks_for(g.N), kThreads, 0, st>>>(g, k, dt, mode, part, v, dG, sig, Jv);
+    k_jv_b<TV><<<blocks_for(g.N), kThreads, 0, st>>>(g, k, dt, mode, mob, v, dG, sig, Jv);
     return 2;
+}
+template int launch_jv_t<double>(const DGrid &, const DCoef &, double, int, const double *, const double *,
+                                 const double *, double *, double *, double *, cudaStream_t);
+template int launch_jv_t<float>(const DGrid &, const DCoef &, double, int, const double *, const double *,
+                                const float *, double *, double *, float *, cudaStream_t);
+
+int launch_jv(const DGrid &g, const DCoef &k, double dt, int mode, const double *part, const double *mob,
+              const double *v, double *dG, double *sig, double *Jv, cudaStream_t st)
+{
+    return launch_jv_t<double>(g, k, dt, mode, part, mob, v, dG, sig, Jv, st);
 }
 
 int launch_energy(const DGrid &g, const DCoef &k, const double *X, double *partials, cudaStream_t st)

@@ -225,3 +225,62 @@ def test_full_size_2d1024_step_checked_by_oracle_residual(nks):
     assert abs(info["mass"] - m0) <= 1e-12 * m0
     assert info["energy"] <= O.energy(X0, cb)
     P.destroy()
+
+
+# ---------------------------------------------------------------------------
+# mixed precision: FP32 Schwarz factors/sweeps and Krylov basis, FP64 residual,
+# update, logarithms, energy and mass; results must still match the FP64 oracle
+# ---------------------------------------------------------------------------
+
+def test_mixed_precision_config_2d64_matches_fp64_oracle(nks):
+    cfg = S.CONFIGS["2d64"]
+    op = S.options(**dict(cfg["opts"], precision="mixed"))
+    P, (c, e), (cg, eg, ug), (co, eo, uo), infos, oinf, e0 = _run_both(nks, 2, cfg["n"], cfg["cbar"], cfg["seed"],
+                                                                        cfg["steps"], op)
+    assert rel(cg, co) <= 1e-8 and rel(eg, eo) <= 1e-8 and rel(ug, uo) <= 1e-8
+    m0 = c.sum() * 0.25 ** 2
+    E = [e0] + [i["energy"] for i in infos]
+    for i in infos:
+        assert abs(i["mass"] - m0) <= 1e-12 * m0
+    for a, b in zip(E[:-1], E[1:]):
+        assert b <= a + 1e-12 * abs(a)
+    P.destroy()
+
+
+def test_mixed_precision_3d_small(nks):
+    op = S.options(sub=(2, 2, 2), overlap=1, precision="mixed")
+    P, _, (cg, eg, ug), (co, eo, uo), infos, oinf, _ = _run_both(nks, 3, (16, 14, 12), 0.18, 9, 3, op)
+    assert rel(cg, co) <= 1e-8 and rel(eg, eo) <= 1e-8 and rel(ug, uo) <= 1e-8
+    P.destroy()
+
+
+def test_full_size_3d128_fp64_and_mixed_steps(nks):
+    """One step of the 3-D 128^3 workload in FP64 and in mixed precision: both solve
+    the oracle's equations (its residual on the GPU result) and agree with each other."""
+    cfg = S.CONFIGS["3d128"]
+    cf = S.coefficients()
+    n = cfg["n"]
+    c, e = S.initial_fields(3, n, cfg["cbar"], cfg["seed"])
+    out = {}
+    for prec in ("fp64", "mixed"):
+        op = S.options(**dict(cfg["opts"], precision=prec))
+        P = nks.Problem(3, n, 0.25, c, e, cf, op)
+        _, _, u0 = P.get_fields()
+        info = P.step()
+        assert info["status"] == 0
+        out[prec] = (u0, P.get_fields(), info)
+        P.destroy()
+    O = oracle.Problem(3, n, 0.25, cf, S.options(**cfg["opts"]))
+    cb = float(np.sum(c) / c.size)
+    for prec in ("fp64", "mixed"):
+        u0, (cg, eg, ug), info = out[prec]
+        X0 = O.interleave(c, e, u0)
+        X1 = O.interleave(cg, eg, ug)
+        F = O.residual(X1, X0, cb, info["dt"])
+        F0 = O.residual(X0, X0, cb, info["dt"])
+        assert np.linalg.norm(F) <= 1e-9 * np.linalg.norm(F0), prec
+        m0 = O.mass(X0)
+        assert abs(info["mass"] - m0) <= 1e-12 * m0
+        assert info["energy"] <= O.energy(X0, cb)
+    (_, (c64, e64, u64), _), (_, (c32, e32, u32), _) = out["fp64"], out["mixed"]
+    assert rel(c32, c64) <= 1e-8 and rel(e32, e64) <= 1e-8 and rel(u32, u64) <= 1e-8
