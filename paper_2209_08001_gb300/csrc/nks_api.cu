@@ -405,6 +405,8 @@ int nks_create_problem(const nks_grid *grid, const double *c, const double *eta,
          (P->partials = (double *)P->dalloc(sizeof(double) * kRedBlocks * 64)) &&
          (P->dscal = (double *)P->dalloc(sizeof(double) * 64)) && (P->dflag = (int *)P->dalloc(sizeof(int) * 4)) &&
          (P->tickets = (unsigned int *)P->dalloc(sizeof(unsigned int) * 16)) &&
+         (P->zsum = (double *)P->dalloc(sizeof(double) * 8)) && (P->Jec = (double *)P->dalloc(vb)) &&
+         (P->ec = (double *)P->dalloc(vb)) &&
          (P->V = (double *)P->dalloc(vb * (opts->precision == NKS_MIXED ? 1 : m + 1))) &&
          (P->T64 = (double *)P->dalloc(vb)) &&
          (P->gm = (double *)P->dalloc(sizeof(double) * gmres_state_doubles(m)));
@@ -431,6 +433,14 @@ int nks_create_problem(const nks_grid *grid, const double *c, const double *eta,
     cudaMemcpyAsync(P->Xn + g.N, eta, fb, cudaMemcpyHostToDevice, P->stream);
     cudaMemsetAsync(P->tr0, 0, fb, P->stream);
     cudaMemsetAsync(P->tickets, 0, sizeof(unsigned int) * 16, P->stream);
+    cudaMemsetAsync(P->zsum, 0, sizeof(double) * 8, P->stream);
+    cudaMemsetAsync(P->Jec, 0, vb, P->stream);
+    cudaMemsetAsync(P->ec, 0, vb, P->stream);
+    {
+        const std::vector<double> ones((size_t)g.N, 1.0);
+        cudaMemcpyAsync(P->ec, ones.data(), fb, cudaMemcpyHostToDevice, P->stream);
+        cudaStreamSynchronize(P->stream);
+    }
     std::string err;
     int rc = ras_plan_create(P, err);
     if (rc) {
@@ -716,7 +726,7 @@ int nks_apply_preconditioner(nks_problem *H, const double *X1, const double *X0,
         if (P->opts.precision == NKS_MIXED) {
             // as the solver applies it: FP32 vectors and factors
             P->count(launch_convert(P->nvec, P->B, P->Wf, P->stream));
-            ras_apply_t<float>(P, P->Wf, P->Zf);
+            ras_apply_projected<float>(P, P->Wf, P->Zf);
             P->count(launch_convert(P->nvec, P->Zf, P->Z, P->stream));
         } else {
             ras_apply(P, P->B, P->Z);

@@ -78,10 +78,12 @@ __device__ inline long long nbrJ(const DGrid &g, int x, int y, int z, int J, int
 // deterministic block reduction of K values (fixed tree, fixed grid)
 // ---------------------------------------------------------------------------
 
+// reduce K values over a block of any multiple of 32 threads (up to 1024) and
+// store them as row blockIdx.x of partials
 template <int K>
-__device__ inline void block_reduce_store(double (&v)[K], double *partials /* [gridDim.x][K] */)
+__device__ inline void block_reduce_store_n(double (&v)[K], double *partials /* [gridDim.x][K] */)
 {
-    __shared__ double red[K][kRedThreads / 32];
+    __shared__ double red[K][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < K; k++) {
@@ -96,6 +98,12 @@ __device__ inline void block_reduce_store(double (&v)[K], double *partials /* [g
         for (int w = 0; w < (int)(blockDim.x >> 5); w++) a += red[threadIdx.x][w];
         partials[(size_t)blockIdx.x * K + threadIdx.x] = a;
     }
+}
+
+template <int K>
+__device__ inline void block_reduce_store(double (&v)[K], double *partials /* [gridDim.x][K] */)
+{
+    block_reduce_store_n<K>(v, partials);
 }
 
 // Last-block finalisation: after every block stored its K partial sums, the
@@ -134,9 +142,11 @@ int launch_residual(const DGrid &g, const DCoef &k, double dt, int mode, const d
                      int *flag, double *partials, cudaStream_t st);
 int launch_jv(const DGrid &g, const DCoef &k, double dt, int mode, const double *part, const double *mob,
                const double *v, double *dG, double *sig, double *Jv, cudaStream_t st);
+// J v, or J P v with Jec = J e_c and zsum[0] = sum of v_c (P: mean of v_c removed)
 template <typename TV>
 int launch_jv_t(const DGrid &g, const DCoef &k, double dt, int mode, const double *part, const double *mob,
-                const TV *v, double *dG, double *sig, TV *Jv, cudaStream_t st);
+                const TV *v, double *dG, double *sig, TV *Jv, cudaStream_t st, const double *Jec = nullptr,
+                const double *zsum = nullptr);
 int launch_energy(const DGrid &g, const DCoef &k, const double *X, double *partials, cudaStream_t st);
 int launch_finalize(const double *partials, int nblocks, int K, double *out, cudaStream_t st);
 
@@ -164,8 +174,11 @@ int ras_plan_create(Problem *P, std::string &err);
 void ras_plan_destroy(Problem *P);
 int ras_factor(Problem *P, int mode);                              // assemble J restricted + ILU(0)
 void ras_apply(Problem *P, const double *r, double *z);           // z = P RAS^-1 r
+// z = RAS^-1 r without P (FP64 or FP32 vectors); the sum of z_c goes to P->zsum[0]
 template <typename TV>
-void ras_apply_t(Problem *P, const TV *r, TV *z);                  // FP64 or FP32 (mixed) vectors
+void ras_apply_t(Problem *P, const TV *r, TV *z);
+template <typename TV>
+void ras_apply_projected(Problem *P, const TV *r, TV *z);         // with P
 void project(Problem *P, double *z);
 void ras_work(const Problem *P, double *bytes, double *flops);  // algorithmic work of one sweep
 
@@ -211,6 +224,9 @@ struct Problem {
     double *dscal = nullptr;                    // small device scalars
     double *hscal = nullptr;                    // pinned host mirror
     int *dflag = nullptr;
+    double *zsum = nullptr;                     // sum of z_c of the last Schwarz sweep (device)
+    double *Jec = nullptr;                      // J e_c at the current iterate (c and eta planes used)
+    double *ec = nullptr;                       // e_c: 1 on the c plane, 0 elsewhere
     unsigned int *tickets = nullptr;            // last-block counters of the fused reductions (start at 0)
 
     // Krylov workspace

@@ -384,10 +384,21 @@ static double norm2_host(Problem *P, const double *x)
 }
 
 template <typename TV>
-static void apply_J(Problem *P, int mode, const TV *v, TV *out)
+static void apply_J(Problem *P, int mode, const TV *v, TV *out, bool project_input)
 {
     P->tick(1);
-    P->count(launch_jv_t<TV>(P->g, P->k, P->cur_dt, mode, P->part, P->mob, v, P->Gc, P->sig, out, P->stream));
+    P->count(launch_jv_t<TV>(P->g, P->k, P->cur_dt, mode, P->part, P->mob, v, P->Gc, P->sig, out, P->stream,
+                             project_input ? P->Jec : nullptr, project_input ? P->zsum : nullptr));
+    P->tock(1);
+}
+
+// J e_c at the current iterate: with it the Arnoldi step applies J P z without
+// projecting z (see k_jv_a)
+void prepare_projection(Problem *P, int mode)
+{
+    P->tick(1);
+    P->count(launch_jv_t<double>(P->g, P->k, P->cur_dt, mode, P->part, P->mob, P->ec, P->Gc, P->sig, P->Jec,
+                                 P->stream));
     P->tock(1);
 }
 
@@ -422,8 +433,8 @@ static int gmres_t(Problem *P, Basis<TV> K, int mode, const double *b, double *x
         int kdim = 0;
         for (int j = 0; j < m; j++) {
             TV *vj = V + (size_t)j * ldv, *vn = V + (size_t)(j + 1) * ldv;
-            ras_apply_t<TV>(P, vj, Z);
-            apply_J<TV>(P, mode, Z, W);
+            ras_apply_t<TV>(P, vj, Z);    // z = RAS^-1 v_j (sum of z_c to P->zsum)
+            apply_J<TV>(P, mode, Z, W, true);  // w = J P z
             // CGS pass 1 and 2
             P->tick(4);
             launch_multidot<TV>(j + 1, ldv, V, W, P->partials, nullptr, gm + L.hcol, P->tickets, st);
@@ -464,11 +475,11 @@ static int gmres_t(Problem *P, Basis<TV> K, int mode, const double *b, double *x
         ras_apply_t<TV>(P, W, Z);
         k_add<TV><<<nb(n), kT, 0, st>>>(n, Z, x);
         P->count(1);
-        // FP32 corrections are mass-neutral only to FP32 rounding: apply P to the FP64
-        // sum once more (P is linear and idempotent), so every Newton correction keeps
+        // x = x + P z: x is already in the range of P and P is linear and idempotent,
+        // so P is applied once to the FP64 sum; every Newton correction keeps
         // sum s_c = 0 and the gauge of u to FP64 rounding
-        if constexpr (sizeof(TV) == sizeof(float)) project(P, x);
-        apply_J<double>(P, mode, x, Jx);
+        project(P, x);
+        apply_J<double>(P, mode, x, Jx, false);
         P->count(launch_waxpy(n, b, -1.0, Jx, R, st));
         beta = sqrt(norm2_host(P, R));
         if (!(beta == beta)) break;
@@ -480,6 +491,7 @@ static int gmres_t(Problem *P, Basis<TV> K, int mode, const double *b, double *x
 
 int gmres_solve(Problem *P, int mode, const double *b, double *x, double tol, int *its_out, double *res_out)
 {
+    prepare_projection(P, mode);
     if (P->opts.precision == NKS_MIXED) return gmres_t<float>(P, basis32(P), mode, b, x, tol, its_out, res_out);
     return gmres_t<double>(P, basis64(P), mode, b, x, tol, its_out, res_out);
 }

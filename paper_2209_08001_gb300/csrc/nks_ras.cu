@@ -202,6 +202,11 @@ int ras_plan_create(Problem *P, std::string &err)
     for (int J = 0; J < d; J++) sub[J] = std::max(1, P->opts.sub[J]);
     const int delta = P->opts.overlap;
     R->nsub = sub[0] * sub[1] * sub[2];
+    if ((long long)sub[0] * sub[1] * sub[2] > (long long)kRedBlocks * 64) {
+        // one reduction partial per subdomain sweep
+        err = "decomposition: too many subdomains";
+        return NKS_EINVAL;
+    }
     std::vector<SubInfo> infos(R->nsub);
     std::vector<int> lvl_ptr, lvl_lp;
     std::vector<long long> lvl_blk;
@@ -596,7 +601,8 @@ __global__ void __launch_bounds__(1024) k_ras_apply(DGrid g, const SubInfo *__re
                             const long long *__restrict__ lvl_blk, const int *__restrict__ lvl_lp,
                             const T *__restrict__ fac, const TV *__restrict__ r, TV *__restrict__ z,
                             T *__restrict__ scratch, int x_in_smem, int maxnp, long long maxblk, int wpt,
-                            int pstride, int *flag)
+                            int pstride, int *flag, double *__restrict__ cpart, double *__restrict__ csum,
+                            unsigned int *ticket)
 {
     constexpr Pattern PT = Pat<D, NF>::v;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -683,16 +689,18 @@ __global__ void __launch_bounds__(1024) k_ras_apply(DGrid g, const SubInfo *__re
         if (failed) break;
     }
     if (failed) {
-        // a copy never completed: report it, let outstanding copies land (bounded), leave
+        // a copy never completed: report it, let outstanding copies land (bounded), and
+        // write nothing (the block still takes its turn in the sum below)
         if (tid == 0) {
             atomicOr(flag, 4);
             mbar_wait_bounded(&bar[0], 0);
             mbar_wait_bounded(&bar[1], 0);
         }
-        return;
     }
-    // restricted prolongation: owned points only
-    for (int q = tid; q < np; q += blockDim.x) {
+    // restricted prolongation: owned points only; the sum of the written z_c feeds the
+    // projection's mean (FP64 per thread, fixed block tree, last block adds the blocks in order)
+    double cs[1] = {0.0};
+    for (int q = failed ? np : tid; q < np; q += blockDim.x) {
         const int lx = q % si.L[0], ly = (q / si.L[0]) % si.L[1], lz = q / (si.L[0] * si.L[1]);
         if (lx < si.own0[0] || lx >= si.own1[0] || ly < si.own0[1] || ly >= si.own1[1] || lz < si.own0[2] ||
             lz >= si.own1[2])
@@ -702,6 +710,12 @@ __global__ void __launch_bounds__(1024) k_ras_apply(DGrid g, const SubInfo *__re
                                       wrapi(si.org[2] + lz, g.n[2]));
 #pragma unroll
         for (int f = 0; f < NF; f++) z[f * N + gp] = (TV)x[f * npx + lp];
+        cs[0] += (double)(TV)x[lp];
+    }
+    if (csum) {
+        __syncthreads();
+        block_reduce_store_n<1>(cs, cpart);
+        grid_finalize(cpart, 1, csum, ticket);
     }
 }
 
@@ -821,9 +835,9 @@ void launch_apply_t(Problem *P, const TV *r, TV *z)
     const T *fac = f32 ? reinterpret_cast<const T *>(R->fac32) : reinterpret_cast<const T *>(R->fac);
     T *scr = f32 ? reinterpret_cast<T *>(R->scratch32) : reinterpret_cast<T *>(R->scratch);
     const int xs = f32 ? R->x_smem32 : R->x_smem;
-    k_ras_apply<D, NF, T, TV><<<R->nsub, threads, smem, P->stream>>>(P->g, R->sub, R->lvl_ptr, R->lvl_blk, R->lvl_lp,
-                                                                    fac, r, z, scr, xs ? 1 : 0, R->maxnp, R->maxblk,
-                                                                    wpt, pstride, P->dflag);
+    k_ras_apply<D, NF, T, TV><<<R->nsub, threads, smem, P->stream>>>(
+        P->g, R->sub, R->lvl_ptr, R->lvl_blk, R->lvl_lp, fac, r, z, scr, xs ? 1 : 0, R->maxnp, R->maxblk, wpt, pstride,
+        P->dflag, P->partials, P->zsum, P->tickets + 3);
 }
 
 }  // namespace
@@ -901,12 +915,23 @@ void ras_apply_t(Problem *P, const TV *r, TV *z)
     }
     P->count(1);
     P->tock(2);
-    project_t<TV>(P, z);
 }
 template void ras_apply_t<double>(Problem *, const double *, double *);
 template void ras_apply_t<float>(Problem *, const float *, float *);
 
-void ras_apply(Problem *P, const double *r, double *z) { ras_apply_t<double>(P, r, z); }
+void ras_apply(Problem *P, const double *r, double *z)
+{
+    ras_apply_t<double>(P, r, z);
+    project(P, z);
+}
+
+template <typename TV>
+void ras_apply_projected(Problem *P, const TV *r, TV *z)
+{
+    ras_apply_t<TV>(P, r, z);
+    project_t<TV>(P, z);
+}
+template void ras_apply_projected<float>(Problem *, const float *, float *);
 
 // algorithmic work of one Schwarz sweep (both triangular solves over every
 // overlapped point): bytes of factors + gathered and written vectors, FLOPs

@@ -276,10 +276,13 @@ __global__ void __launch_bounds__(kRedThreads) k_res_b(DGrid g, DCoef k, double 
 // Jacobian action, pass A: dG_c (linearised G_c), (J v)_eta, sigma(eps(v_u) - eps0 v_c I).
 // v and J v are stored as TV (FP64, or FP32 in the mixed-precision Krylov basis);
 // the arithmetic is FP64.
+// With Jec != nullptr the action is applied to P v instead of v, where P removes the
+// mean of v_c (and null modes of v_u, which J annihilates): J P v = J v - mean(v_c) J e_c,
+// mean(v_c) = zsum[0] / N.
 template <typename TV>
 __global__ void k_jv_a(DGrid g, DCoef k, double dt, int mode, const double *__restrict__ part,
                        const TV *__restrict__ v, double *__restrict__ dG, double *__restrict__ sig,
-                       TV *__restrict__ Jv)
+                       TV *__restrict__ Jv, const double *__restrict__ Jec, const double *__restrict__ zsum)
 {
     long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (p >= g.N) return;
@@ -294,8 +297,9 @@ __global__ void k_jv_a(DGrid g, DCoef k, double dt, int mode, const double *__re
         hooke_packed(g, k, Du, k.eps0 * vc, sig, p);
         for (int K = 0; K < g.dim; K++) trv += Du[K][K];
     }
+    const double corr = Jec ? zsum[0] / (double)N : 0.0;
     if (mode != 0) {
-        Jv[N + p] = (TV)ve;
+        Jv[N + p] = (TV)(ve - (Jec ? corr * Jec[N + p] : 0.0));
         return;
     }
     const double ih2 = 1.0 / (g.h * g.h);
@@ -308,20 +312,23 @@ __global__ void k_jv_a(DGrid g, DCoef k, double dt, int mode, const double *__re
     double dg = part[p] * vc + part[N + p] * ve - 0.5 * k.gamma_c * lc * ih2;
     if (k.elastic) dg += -0.5 * k.eps0 * k.lam * (trv - g.dim * k.eps0 * vc);
     dG[p] = dg;
-    Jv[N + p] = (TV)(ve / dt + part[2 * N + p] * vc + part[3 * N + p] * ve - 1.5 * k.gamma_eta * le * ih2);
+    double je = ve / dt + part[2 * N + p] * vc + part[3 * N + p] * ve - 1.5 * k.gamma_eta * le * ih2;
+    if (Jec) je -= corr * Jec[N + p];
+    Jv[N + p] = (TV)je;
 }
 
 // Jacobian action, pass B: (J v)_c = v_c/dt - D M D dG_c, (J v)_u = sum_J Dhat_J sigma(v)_IJ
 template <typename TV>
 __global__ void k_jv_b(DGrid g, DCoef k, double dt, int mode, const double *__restrict__ mob,
                        const TV *__restrict__ v, const double *__restrict__ dG, const double *__restrict__ sig,
-                       TV *__restrict__ Jv)
+                       TV *__restrict__ Jv, const double *__restrict__ Jec, const double *__restrict__ zsum)
 {
     long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (p >= g.N) return;
     int x, y, z;
     coords_of(g, p, x, y, z);
     const long long N = g.N;
+    const double corr = Jec ? zsum[0] / (double)N * Jec[p] : 0.0;
     if (mode == 0) {
         const double ih2 = 1.0 / (g.h * g.h);
         double flux = 0.0;
@@ -330,9 +337,9 @@ __global__ void k_jv_b(DGrid g, DCoef k, double dt, int mode, const double *__re
             const long long pp = nbrJ(g, x, y, z, J, +1), pm = nbrJ(g, x, y, z, J, -1);
             flux += mob[J * N + p] * (dG[pp] - G0) - mob[J * N + pm] * (G0 - dG[pm]);
         }
-        Jv[p] = (TV)((double)v[p] / dt - flux * ih2);
+        Jv[p] = (TV)((double)v[p] / dt - flux * ih2 - corr);
     } else {
-        Jv[p] = v[p];
+        Jv[p] = (TV)((double)v[p] - corr);
     }
     if (k.elastic) {
         const double i2h = 0.5 / g.h;
@@ -444,21 +451,23 @@ int launch_residual(const DGrid &g, const DCoef &k, double dt, int mode, const d
 
 template <typename TV>
 int launch_jv_t(const DGrid &g, const DCoef &k, double dt, int mode, const double *part, const double *mob,
-                const TV *v, double *dG, double *sig, TV *Jv, cudaStream_t st)
+                const TV *v, double *dG, double *sig, TV *Jv, cudaStream_t st, const double *Jec, const double *zsum)
 {
-    k_jv_a<TV><<<blocks_for(g.N), kThreads, 0, st>>>(g, k, dt, mode, part, v, dG, sig, Jv);
-    k_jv_b<TV><<<blocks_for(g.N), kThreads, 0, st>>>(g, k, dt, mode, mob, v, dG, sig, Jv);
+    k_jv_a<TV><<<blocks_for(g.N), kThreads, 0, st>>>(g, k, dt, mode, part, v, dG, sig, Jv, Jec, zsum);
+    k_jv_b<TV><<<blocks_for(g.N), kThreads, 0, st>>>(g, k, dt, mode, mob, v, dG, sig, Jv, Jec, zsum);
     return 2;
 }
 template int launch_jv_t<double>(const DGrid &, const DCoef &, double, int, const double *, const double *,
-                                 const double *, double *, double *, double *, cudaStream_t);
+                                 const double *, double *, double *, double *, cudaStream_t, const double *,
+                                 const double *);
 template int launch_jv_t<float>(const DGrid &, const DCoef &, double, int, const double *, const double *,
-                                const float *, double *, double *, float *, cudaStream_t);
+                                const float *, double *, double *, float *, cudaStream_t, const double *,
+                                const double *);
 
 int launch_jv(const DGrid &g, const DCoef &k, double dt, int mode, const double *part, const double *mob,
               const double *v, double *dG, double *sig, double *Jv, cudaStream_t st)
 {
-    return launch_jv_t<double>(g, k, dt, mode, part, mob, v, dG, sig, Jv, st);
+    return launch_jv_t<double>(g, k, dt, mode, part, mob, v, dG, sig, Jv, st, nullptr, nullptr);
 }
 
 int launch_energy(const DGrid &g, const DCoef &k, const double *X, double *partials, cudaStream_t st)
