@@ -323,13 +323,15 @@ def run_reference(args):
 def run_probe(args):
     """Small fixed cases for profiling single kernels (ncu -k ...): 'gmres512' builds
     the 2-D 512^2 problem with 8x8 subdomains, overlap 2 (the 68x68 boxes of the
-    1024^2 workload) and runs 40 GMRES iterations of the first Newton solve."""
+    1024^2 workload) and runs 40 GMRES iterations of the first Newton solve
+    (FP64, or FP32 sweeps and basis with --precision mixed)."""
     import torch
     import paper_2209_08001_gb300 as nks
     torch.cuda.set_device(0)
     if args.probe == "gmres512":
         n = (512, 512)
-        op = S.options(sub=(8, 8), overlap=2, u0_maxit=1, gmres_maxit=40, u0_rtol=1e-2)
+        op = S.options(sub=(8, 8), overlap=2, u0_maxit=1, gmres_maxit=40, u0_rtol=1e-2,
+                       precision=args.precision or "fp64")
         c, e = S.initial_fields(2, n, 0.2, 1)
         P = nks.Problem(2, n, 0.25, c, e, S.coefficients(), op)
         cg, eg, ug = P.get_fields()

@@ -232,7 +232,10 @@ const char *nks_last_error(const nks_problem *p);
  * (mode 1: F_c = F_eta = 0) used for the initial equilibrium. */
 int nks_eval_residual(nks_problem *p, const double *X1, const double *X0, double dt, int mode, double *F);
 
-/* Jv = J(X1; X0, dt) v with J = dF/dX1 (Sec. 4, J_m = grad F(X_m)). */
+/* Jv = J(X1; X0, dt) v with J = dF/dX1 (Sec. 4, J_m = grad F(X_m)).  In the
+ * NKS_MIXED mode the action runs as the solver's Arnoldi step runs it: v
+ * rounded to FP32, FP32 copies of the pointwise coefficients, FP32 arithmetic;
+ * the result is widened to FP64 (the FP64 form is used for true residuals). */
 int nks_apply_jacobian(nks_problem *p, const double *X1, const double *X0, double dt, int mode, const double *v,
                        double *Jv);
 

@@ -341,11 +341,19 @@ int nks_create_problem(const nks_grid *grid, const double *c, const double *eta,
         g_create_error = "grid: dim must be 1..3 and h > 0";
         return NKS_EINVAL;
     }
-    for (int J = 0; J < grid->dim; J++)
+    long long npts = 1;
+    for (int J = 0; J < grid->dim; J++) {
         if (grid->n[J] < 3) {
             g_create_error = "grid: at least 3 cells per axis";
             return NKS_EINVAL;
         }
+        npts *= grid->n[J];
+    }
+    if (npts * (2 + grid->dim) >= (1LL << 31)) {
+        // stencil kernels index the field planes with 32-bit offsets
+        g_create_error = "grid: (2 + dim) * points must be below 2^31";
+        return NKS_EINVAL;
+    }
     if (coeffs->S < 1 || coeffs->S > 16) {
         g_create_error = "coeffs: S must be in 1..16";
         return NKS_EINVAL;
@@ -413,7 +421,10 @@ int nks_create_problem(const nks_grid *grid, const double *c, const double *eta,
     if (ok && opts->precision == NKS_MIXED) {
         const size_t fvb = sizeof(float) * (size_t)P->ldvf;
         ok = (P->Vf = (float *)P->dalloc(fvb * (m + 1))) && (P->Wf = (float *)P->dalloc(fvb)) &&
-             (P->Zf = (float *)P->dalloc(fvb));
+             (P->Zf = (float *)P->dalloc(fvb)) &&
+             (P->partf = (float *)P->dalloc(sizeof(float) * 4 * (size_t)g.N)) &&
+             (P->mobf = (float *)P->dalloc(sizeof(float) * g.dim * (size_t)g.N)) &&
+             (P->Jecf = (float *)P->dalloc(sizeof(float) * 2 * (size_t)g.N));
         if (ok) {
             cudaMemsetAsync(P->Vf, 0, fvb * (m + 1), P->stream);
             cudaMemsetAsync(P->Wf, 0, fvb, P->stream);
@@ -707,7 +718,15 @@ int nks_apply_jacobian(nks_problem *H, const double *X1, const double *X0, doubl
         const size_t vb = sizeof(double) * (size_t)P->nvec;
         cudaMemcpyAsync(P->B, v, vb, cudaMemcpyHostToDevice, P->stream);
         P->tick(1);
-        P->count(launch_jv(P->g, P->k, dt, mode, P->part, P->mob, P->B, P->Gc, P->sig, P->W, P->stream));
+        if (P->opts.precision == NKS_MIXED) {
+            // as the Arnoldi step applies it: FP32 vectors, coefficients and arithmetic
+            refresh_f32_coefficients(P);
+            P->count(launch_convert(P->nvec, P->B, P->Zf, P->stream));
+            P->count(launch_jv32(P->g, P->k, dt, mode, P->partf, P->mobf, P->Zf, P->Wf, P->stream, nullptr, nullptr));
+            P->count(launch_convert(P->nvec, P->Wf, P->W, P->stream));
+        } else {
+            P->count(launch_jv(P->g, P->k, dt, mode, P->part, P->mob, P->B, P->Gc, P->sig, P->W, P->stream));
+        }
         P->tock(1);
         cudaMemcpyAsync(Jv, P->W, vb, cudaMemcpyDeviceToHost, P->stream);
         rc = P->sync_check("apply_jacobian");

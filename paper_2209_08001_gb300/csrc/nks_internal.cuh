@@ -142,11 +142,14 @@ int launch_residual(const DGrid &g, const DCoef &k, double dt, int mode, const d
                      int *flag, double *partials, cudaStream_t st);
 int launch_jv(const DGrid &g, const DCoef &k, double dt, int mode, const double *part, const double *mob,
                const double *v, double *dG, double *sig, double *Jv, cudaStream_t st);
-// J v, or J P v with Jec = J e_c and zsum[0] = sum of v_c (P: mean of v_c removed)
-template <typename TV>
-int launch_jv_t(const DGrid &g, const DCoef &k, double dt, int mode, const double *part, const double *mob,
-                const TV *v, double *dG, double *sig, TV *Jv, cudaStream_t st, const double *Jec = nullptr,
+// J v, or J P v with Jec = J e_c and zsum[0] = sum of v_c (P: mean of v_c removed).
+// FP64: two passes through the dG / sig temporaries (N and d(d+1)/2 N doubles).
+int launch_jv64(const DGrid &g, const DCoef &k, double dt, int mode, const double *part, const double *mob,
+                const double *v, double *dG, double *sig, double *Jv, cudaStream_t st, const double *Jec = nullptr,
                 const double *zsum = nullptr);
+// FP32 arithmetic and storage (FP32 copies of part, mob and the c/eta planes of J e_c)
+int launch_jv32(const DGrid &g, const DCoef &k, double dt, int mode, const float *part, const float *mob,
+                const float *v, float *Jv, cudaStream_t st, const float *Jec, const double *zsum);
 int launch_energy(const DGrid &g, const DCoef &k, const double *X, double *partials, cudaStream_t st);
 int launch_finalize(const double *partials, int nblocks, int K, double *out, cudaStream_t st);
 
@@ -178,7 +181,9 @@ void ras_apply(Problem *P, const double *r, double *z);           // z = P RAS^-
 template <typename TV>
 void ras_apply_t(Problem *P, const TV *r, TV *z);
 template <typename TV>
-void ras_apply_projected(Problem *P, const TV *r, TV *z);         // with P
+void ras_apply_projected(Problem *P, const TV *r, TV *z);
+// mixed precision: FP32 copies of part and mob for the FP32 Jacobian action
+void refresh_f32_coefficients(Problem *P);         // with P
 void project(Problem *P, double *z);
 void ras_work(const Problem *P, double *bytes, double *flops);  // algorithmic work of one sweep
 
@@ -227,6 +232,8 @@ struct Problem {
     double *zsum = nullptr;                     // sum of z_c of the last Schwarz sweep (device)
     double *Jec = nullptr;                      // J e_c at the current iterate (c and eta planes used)
     double *ec = nullptr;                       // e_c: 1 on the c plane, 0 elsewhere
+    float *partf = nullptr, *mobf = nullptr;    // mixed precision: FP32 copies of part and mob for J v
+    float *Jecf = nullptr;                      // mixed precision: c and eta planes of J e_c in FP32
     unsigned int *tickets = nullptr;            // last-block counters of the fused reductions (start at 0)
 
     // Krylov workspace

@@ -387,19 +387,34 @@ template <typename TV>
 static void apply_J(Problem *P, int mode, const TV *v, TV *out, bool project_input)
 {
     P->tick(1);
-    P->count(launch_jv_t<TV>(P->g, P->k, P->cur_dt, mode, P->part, P->mob, v, P->Gc, P->sig, out, P->stream,
-                             project_input ? P->Jec : nullptr, project_input ? P->zsum : nullptr));
+    if constexpr (sizeof(TV) == sizeof(float))
+        P->count(launch_jv32(P->g, P->k, P->cur_dt, mode, P->partf, P->mobf, v, out, P->stream,
+                             project_input ? P->Jecf : nullptr, P->zsum));
+    else
+        P->count(launch_jv64(P->g, P->k, P->cur_dt, mode, P->part, P->mob, v, P->Gc, P->sig, out, P->stream,
+                             project_input ? P->Jec : nullptr, P->zsum));
     P->tock(1);
 }
 
 // J e_c at the current iterate: with it the Arnoldi step applies J P z without
-// projecting z (see k_jv_a)
+// projecting z (see the Jacobian action).  In mixed precision the FP32 copies
+// of the operator's coefficients are refreshed here as well.
 void prepare_projection(Problem *P, int mode)
 {
     P->tick(1);
-    P->count(launch_jv_t<double>(P->g, P->k, P->cur_dt, mode, P->part, P->mob, P->ec, P->Gc, P->sig, P->Jec,
-                                 P->stream));
+    P->count(launch_jv64(P->g, P->k, P->cur_dt, mode, P->part, P->mob, P->ec, P->Gc, P->sig, P->Jec, P->stream));
+    if (P->opts.precision == NKS_MIXED) {
+        P->count(launch_convert(2 * P->N, P->Jec, P->Jecf, P->stream));
+        refresh_f32_coefficients(P);
+    }
     P->tock(1);
+}
+
+// FP32 copies of the Jacobian action's coefficients at the current iterate
+void refresh_f32_coefficients(Problem *P)
+{
+    P->count(launch_convert(4 * P->N, P->part, P->partf, P->stream));
+    P->count(launch_convert(P->g.dim * P->N, P->mob, P->mobf, P->stream));
 }
 
 // Krylov work vectors of the basis type

@@ -9,7 +9,8 @@
 //           sigma(eps^el(u1, c1)) at each point;
 //   pass B: F_c = (c1 - c0)/dt - D M D G_c (flux form with level-n edge
 //           mobilities) and F_u = sum_J Dhat_J sigma_IJ, plus ||F||^2 partials.
-// The Jacobian action J v uses the same two passes on the linearisation.
+// The Jacobian action J v has an FP64 two-pass form and an FP32 tiled form
+// (mixed-precision Arnoldi vectors).
 #include <math.h>
 
 #include "nks_internal.cuh"
@@ -273,83 +274,293 @@ __global__ void __launch_bounds__(kRedThreads) k_res_b(DGrid g, DCoef k, double 
     block_reduce_store<1>(acc, partials);
 }
 
-// Jacobian action, pass A: dG_c (linearised G_c), (J v)_eta, sigma(eps(v_u) - eps0 v_c I).
-// v and J v are stored as TV (FP64, or FP32 in the mixed-precision Krylov basis);
-// the arithmetic is FP64.
-// With Jec != nullptr the action is applied to P v instead of v, where P removes the
-// mean of v_c (and null modes of v_u, which J annihilates): J P v = J v - mean(v_c) J e_c,
-// mean(v_c) = zsum[0] / N.
-template <typename TV>
-__global__ void k_jv_a(DGrid g, DCoef k, double dt, int mode, const double *__restrict__ part,
-                       const TV *__restrict__ v, double *__restrict__ dG, double *__restrict__ sig,
-                       TV *__restrict__ Jv, const double *__restrict__ Jec, const double *__restrict__ zsum)
+// Jacobian action J v: the linearisation of the residual at the current Newton
+// iterate applied to v,
+//   dG_c      = dcc v_c + dce v_eta - 1/2 gamma_c Lap_h v_c - 1/2 eps0 lam (tr Dhat v_u - d eps0 v_c)
+//   sigma     = C : (sym Dhat v_u - eps0 v_c I)
+//   (J v)_c   = v_c/dt - div_h(M^n grad_h dG_c)          (edge mobilities at level n)
+//   (J v)_eta = v_eta/dt + dec v_c + dee v_eta - 3/2 gamma_eta Lap_h v_eta
+//   (J v)_u_I = sum_J Dhat_J sigma_IJ,
+// with the pointwise derivatives (dcc, dce, dec, dee) of the last residual
+// evaluation (part).  mode 1 (displacement-only system) keeps the identity on the
+// c and eta rows.  With Jec != nullptr the action is applied to P v instead of v,
+// where P removes the mean of v_c (and the null modes of v_u, which J annihilates):
+// J P v = J v - mean(v_c) J e_c with mean(v_c) = zsum[0] / N.
+// Indices are 32-bit (the problem constructor checks nf N < 2^31).
+//
+// GB300 executes FP64 at 1/64 of the FP32 rate, so the FP64 form is organised to
+// do each FP64 operation once: two passes over the grid (dG_c and sigma written
+// once per point, then the flux and divergence forms), constants folded on the
+// host (JvConst).  The FP32 form (mixed precision: Arnoldi vectors, FP32 copies
+// of the coefficients) is one tiled kernel that recomputes dG_c and sigma on a
+// one-point halo in shared memory instead of writing them out.
+
+// per-operator constants with the grid spacings folded in
+struct JvConst {
+    double idt;       // 1/dt
+    double gc;        // 1/2 gamma_c / h^2
+    double ge;        // 3/2 gamma_eta / h^2
+    double ih2;       // 1/h^2
+    double el_t;      // 1/2 eps0 lam / (2h)  (times the undivided trace)
+    double el_c;      // 1/2 eps0 lam d eps0
+    double ab, b, c4; // (C11 - C12)/(2h), C12/(2h), C44/(2h)
+    double ls;        // lam eps0
+    double i2h;       // 1/(2h)
+    int mode;
+};
+
+static JvConst jv_const(const DGrid &g, const DCoef &k, double dt, int mode)
 {
-    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (p >= g.N) return;
-    int x, y, z;
-    coords_of(g, p, x, y, z);
-    const long long N = g.N;
-    const double vc = v[p], ve = v[N + p];
-    double Du[3][3];
-    double trv = 0.0;
-    if (k.elastic) {
-        grad_u(g, v + 2 * N, x, y, z, Du);
-        hooke_packed(g, k, Du, k.eps0 * vc, sig, p);
-        for (int K = 0; K < g.dim; K++) trv += Du[K][K];
-    }
-    const double corr = Jec ? zsum[0] / (double)N : 0.0;
-    if (mode != 0) {
-        Jv[N + p] = (TV)(ve - (Jec ? corr * Jec[N + p] : 0.0));
-        return;
-    }
-    const double ih2 = 1.0 / (g.h * g.h);
-    double lc = 0.0, le = 0.0;
-    for (int J = 0; J < g.dim; J++) {
-        const long long pp = nbrJ(g, x, y, z, J, +1), pm = nbrJ(g, x, y, z, J, -1);
-        lc += (double)v[pp] + (double)v[pm] - 2.0 * vc;
-        le += (double)v[N + pp] + (double)v[N + pm] - 2.0 * ve;
-    }
-    double dg = part[p] * vc + part[N + p] * ve - 0.5 * k.gamma_c * lc * ih2;
-    if (k.elastic) dg += -0.5 * k.eps0 * k.lam * (trv - g.dim * k.eps0 * vc);
-    dG[p] = dg;
-    double je = ve / dt + part[2 * N + p] * vc + part[3 * N + p] * ve - 1.5 * k.gamma_eta * le * ih2;
-    if (Jec) je -= corr * Jec[N + p];
-    Jv[N + p] = (TV)je;
+    JvConst c;
+    const double i2h = 0.5 / g.h, ih2 = 1.0 / (g.h * g.h);
+    c.idt = 1.0 / dt;
+    c.gc = 0.5 * k.gamma_c * ih2;
+    c.ge = 1.5 * k.gamma_eta * ih2;
+    c.ih2 = ih2;
+    c.el_t = 0.5 * k.eps0 * k.lam * i2h;
+    c.el_c = 0.5 * k.eps0 * k.lam * g.dim * k.eps0;
+    c.ab = (k.C11 - k.C12) * i2h;
+    c.b = k.C12 * i2h;
+    c.c4 = k.C44 * i2h;
+    c.ls = k.lam * k.eps0;
+    c.i2h = i2h;
+    c.mode = mode;
+    return c;
 }
 
-// Jacobian action, pass B: (J v)_c = v_c/dt - D M D dG_c, (J v)_u = sum_J Dhat_J sigma(v)_IJ
-template <typename TV>
-__global__ void k_jv_b(DGrid g, DCoef k, double dt, int mode, const double *__restrict__ mob,
-                       const TV *__restrict__ v, const double *__restrict__ dG, const double *__restrict__ sig,
-                       TV *__restrict__ Jv, const double *__restrict__ Jec, const double *__restrict__ zsum)
+// neighbour offsets of point (x, y, z) along each axis, periodic, 32-bit
+template <int D>
+__device__ __forceinline__ void nbr_offsets(const int (&c3)[3], const int (&nn)[3], int p, int (&im)[3], int (&ip)[3])
 {
-    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (p >= g.N) return;
-    int x, y, z;
-    coords_of(g, p, x, y, z);
-    const long long N = g.N;
-    const double corr = Jec ? zsum[0] / (double)N * Jec[p] : 0.0;
-    if (mode == 0) {
-        const double ih2 = 1.0 / (g.h * g.h);
-        double flux = 0.0;
-        const double G0 = dG[p];
-        for (int J = 0; J < g.dim; J++) {
-            const long long pp = nbrJ(g, x, y, z, J, +1), pm = nbrJ(g, x, y, z, J, -1);
-            flux += mob[J * N + p] * (dG[pp] - G0) - mob[J * N + pm] * (G0 - dG[pm]);
-        }
-        Jv[p] = (TV)((double)v[p] / dt - flux * ih2 - corr);
-    } else {
-        Jv[p] = (TV)((double)v[p] - corr);
+    int st = 1;
+#pragma unroll
+    for (int J = 0; J < D; J++) {
+        im[J] = p + (c3[J] == 0 ? (nn[J] - 1) * st : -st);
+        ip[J] = p + (c3[J] == nn[J] - 1 ? -(nn[J] - 1) * st : st);
+        st *= nn[J];
     }
-    if (k.elastic) {
-        const double i2h = 0.5 / g.h;
-        for (int I = 0; I < g.dim; I++) {
+}
+
+// dG_c and sigma at one point; T is the arithmetic type
+template <int D, bool EL, typename T, typename TV, typename TC>
+__device__ __forceinline__ void jv_point(const JvConst &c, int mode, int N, int idx, const int (&im)[3],
+                                         const int (&ip)[3], const TV *__restrict__ v, const TC *__restrict__ part,
+                                         T &dg, T (&sg)[EL ? D * (D + 1) / 2 : 1])
+{
+    const T vc = (T)v[idx];
+    T trd = (T)0;
+    if constexpr (EL) {
+        T Dd[D][D];
+#pragma unroll
+        for (int I = 0; I < D; I++)
+#pragma unroll
+            for (int J = 0; J < D; J++) Dd[I][J] = (T)v[(2 + I) * N + ip[J]] - (T)v[(2 + I) * N + im[J]];
+#pragma unroll
+        for (int I = 0; I < D; I++) trd += Dd[I][I];
+        // sigma_II = (C11 - C12) e_II + C12 tr e - lam eps0 v_c;  sigma_IJ = C44 (D_IJ + D_JI)
+        const T common = (T)c.b * trd - (T)c.ls * vc;
+#pragma unroll
+        for (int I = 0; I < D; I++) {
+            sg[I] = (T)c.ab * Dd[I][I] + common;
+#pragma unroll
+            for (int J = I + 1; J < D; J++) sg[scomp(D, I, J)] = (T)c.c4 * (Dd[I][J] + Dd[J][I]);
+        }
+    }
+    if (mode == 0) {
+        T sn = (T)0;
+#pragma unroll
+        for (int J = 0; J < D; J++) sn += (T)v[ip[J]] + (T)v[im[J]];
+        const T lc = sn - (T)(2 * D) * vc;
+        dg = (T)part[idx] * vc + (T)part[N + idx] * (T)v[N + idx] - (T)c.gc * lc;
+        if constexpr (EL) dg += (T)c.el_c * vc - (T)c.el_t * trd;
+    }
+}
+
+// ---- FP64: two passes --------------------------------------------------------
+
+template <int D>
+__device__ __forceinline__ bool grid_point(const DGrid &g, int (&c3)[3], int &p)
+{
+    c3[0] = blockIdx.x * blockDim.x + threadIdx.x;
+    c3[1] = D >= 2 ? (int)(blockIdx.y * blockDim.y + threadIdx.y) : 0;
+    c3[2] = D == 3 ? (int)blockIdx.z : 0;
+    if (c3[0] >= g.n[0] || c3[1] >= g.n[1]) return false;
+    p = c3[0] + g.n[0] * (c3[1] + g.n[1] * c3[2]);
+    return true;
+}
+
+template <int D, bool EL>
+__global__ void __launch_bounds__(256) k_jv64_a(DGrid g, JvConst c, const double *__restrict__ part,
+                                                const double *__restrict__ v, double *__restrict__ dG,
+                                                double *__restrict__ sig)
+{
+    int c3[3], p;
+    if (!grid_point<D>(g, c3, p)) return;
+    const int nn[3] = {g.n[0], g.n[1], g.n[2]};
+    const int N = (int)g.N;
+    int im[3], ip[3];
+    nbr_offsets<D>(c3, nn, p, im, ip);
+    double dg = 0.0, sg[EL ? D * (D + 1) / 2 : 1];
+    jv_point<D, EL, double, double, double>(c, c.mode, N, p, im, ip, v, part, dg, sg);
+    if (c.mode == 0) dG[p] = dg;
+    if constexpr (EL) {
+#pragma unroll
+        for (int q = 0; q < D * (D + 1) / 2; q++) sig[q * N + p] = sg[q];
+    }
+}
+
+template <int D, bool EL>
+__global__ void __launch_bounds__(256) k_jv64_b(DGrid g, JvConst c, const double *__restrict__ part,
+                                                const double *__restrict__ mob, const double *__restrict__ v,
+                                                const double *__restrict__ dG, const double *__restrict__ sig,
+                                                double *__restrict__ Jv, const double *__restrict__ Jec,
+                                                const double *__restrict__ zsum)
+{
+    int c3[3], p;
+    if (!grid_point<D>(g, c3, p)) return;
+    const int nn[3] = {g.n[0], g.n[1], g.n[2]};
+    const int N = (int)g.N;
+    int im[3], ip[3];
+    nbr_offsets<D>(c3, nn, p, im, ip);
+    const double vc = v[p], ve = v[N + p];
+    double jc, je;
+    if (c.mode == 0) {
+        const double G0 = dG[p];
+        double flux = 0.0, sn = 0.0;
+#pragma unroll
+        for (int J = 0; J < D; J++) {
+            flux += mob[J * N + p] * (dG[ip[J]] - G0) - mob[J * N + im[J]] * (G0 - dG[im[J]]);
+            sn += v[N + ip[J]] + v[N + im[J]];
+        }
+        jc = vc * c.idt - flux * c.ih2;
+        je = ve * c.idt + part[2 * N + p] * vc + part[3 * N + p] * ve - c.ge * (sn - (2 * D) * ve);
+    } else {
+        jc = vc;
+        je = ve;
+    }
+    if (Jec) {
+        const double m = zsum[0] / (double)N;
+        jc -= m * Jec[p];
+        je -= m * Jec[N + p];
+    }
+    Jv[p] = jc;
+    Jv[N + p] = je;
+    if constexpr (EL) {
+#pragma unroll
+        for (int I = 0; I < D; I++) {
             double div = 0.0;
-            for (int J = 0; J < g.dim; J++) {
-                const int cmp = scomp(g.dim, I, J);
-                div += (sig[cmp * N + nbrJ(g, x, y, z, J, +1)] - sig[cmp * N + nbrJ(g, x, y, z, J, -1)]) * i2h;
+#pragma unroll
+            for (int J = 0; J < D; J++) {
+                const int q = scomp(D, I, J) * N;
+                div += sig[q + ip[J]] - sig[q + im[J]];
             }
-            Jv[(2 + I) * N + p] = (TV)div;
+            Jv[(2 + I) * N + p] = div * c.i2h;
+        }
+    }
+}
+
+// ---- FP32: one tiled kernel --------------------------------------------------
+
+template <int D>
+struct JvTile;
+template <>
+struct JvTile<1> {
+    static constexpr int TX = 256, TY = 1, TZ = 1;
+};
+template <>
+struct JvTile<2> {
+    static constexpr int TX = 32, TY = 8, TZ = 1;
+};
+template <>
+struct JvTile<3> {
+    static constexpr int TX = 16, TY = 4, TZ = 4;
+};
+
+template <int D, bool EL>
+__global__ void __launch_bounds__(256) k_jv32(DGrid g, JvConst c, const float *__restrict__ part,
+                                              const float *__restrict__ mob, const float *__restrict__ v,
+                                              float *__restrict__ Jv, const float *__restrict__ Jec,
+                                              const double *__restrict__ zsum)
+{
+    constexpr int TX = JvTile<D>::TX, TY = JvTile<D>::TY, TZ = JvTile<D>::TZ;
+    constexpr int HX = TX + 2, HY = D >= 2 ? TY + 2 : 1, HZ = D == 3 ? TZ + 2 : 1;
+    constexpr int NH = HX * HY * HZ;
+    constexpr int NS = EL ? D * (D + 1) / 2 : 1;
+    __shared__ float sG[NH];
+    __shared__ float sS[NS][EL ? NH : 1];
+    const int nn[3] = {g.n[0], g.n[1], g.n[2]};
+    const int N = (int)g.N;
+    const int tx_n = (nn[0] + TX - 1) / TX, ty_n = (nn[1] + TY - 1) / TY;
+    int b = blockIdx.x;
+    const int x0 = (b % tx_n) * TX;
+    b /= tx_n;
+    const int y0 = (b % ty_n) * TY;
+    const int z0 = (b / ty_n) * TZ;
+    const int sh[3] = {1, HX, HX * HY};
+
+    // tile + halo: dG_c and sigma
+    for (int q = threadIdx.x; q < NH; q += blockDim.x) {
+        const int hx = q % HX, hy = (q / HX) % HY, hz = q / (HX * HY);
+        int c3[3] = {x0 - 1 + hx, D >= 2 ? y0 - 1 + hy : 0, D == 3 ? z0 - 1 + hz : 0};
+        if (c3[0] > nn[0] || c3[1] > nn[1] || c3[2] > nn[2]) continue;  // beyond a ragged tile: never read
+#pragma unroll
+        for (int J = 0; J < 3; J++) c3[J] = wrapi(c3[J], nn[J]);
+        const int idx = c3[0] + nn[0] * (c3[1] + nn[1] * c3[2]);
+        int im[3], ip[3];
+        nbr_offsets<D>(c3, nn, idx, im, ip);
+        float dg = 0.f, sg[NS];
+        jv_point<D, EL, float, float, float>(c, c.mode, N, idx, im, ip, v, part, dg, sg);
+        sG[q] = dg;
+        if constexpr (EL) {
+#pragma unroll
+            for (int s = 0; s < NS; s++) sS[s][q] = sg[s];
+        }
+    }
+    __syncthreads();
+
+    const float m = Jec ? (float)(zsum[0] / (double)N) : 0.f;
+    const float idt = (float)c.idt, ih2 = (float)c.ih2, ge = (float)c.ge, i2h = (float)c.i2h;
+    for (int t = threadIdx.x; t < TX * TY * TZ; t += blockDim.x) {
+        const int tx = t % TX, ty = (t / TX) % TY, tz = t / (TX * TY);
+        const int c3[3] = {x0 + tx, y0 + ty, z0 + tz};
+        if (c3[0] >= nn[0] || c3[1] >= nn[1] || c3[2] >= nn[2]) continue;
+        const int p = c3[0] + nn[0] * (c3[1] + nn[1] * c3[2]);
+        int im[3], ip[3];
+        nbr_offsets<D>(c3, nn, p, im, ip);
+        const int hq = (tx + 1) + (D >= 2 ? HX * (ty + 1) : 0) + (D == 3 ? HX * HY * (tz + 1) : 0);
+        const float vc = v[p], ve = v[N + p];
+        float jc, je;
+        if (c.mode == 0) {
+            const float G0 = sG[hq];
+            float flux = 0.f, sn = 0.f;
+#pragma unroll
+            for (int J = 0; J < D; J++) {
+                flux += mob[J * N + p] * (sG[hq + sh[J]] - G0) - mob[J * N + im[J]] * (G0 - sG[hq - sh[J]]);
+                sn += v[N + ip[J]] + v[N + im[J]];
+            }
+            jc = vc * idt - flux * ih2;
+            je = ve * idt + part[2 * N + p] * vc + part[3 * N + p] * ve - ge * (sn - (float)(2 * D) * ve);
+        } else {
+            jc = vc;
+            je = ve;
+        }
+        if (Jec) {
+            jc -= m * Jec[p];
+            je -= m * Jec[N + p];
+        }
+        Jv[p] = jc;
+        Jv[N + p] = je;
+        if constexpr (EL) {
+#pragma unroll
+            for (int I = 0; I < D; I++) {
+                float div = 0.f;
+#pragma unroll
+                for (int J = 0; J < D; J++) {
+                    const int s = scomp(D, I, J);
+                    div += sS[s][hq + sh[J]] - sS[s][hq - sh[J]];
+                }
+                Jv[(2 + I) * N + p] = div * i2h;
+            }
         }
     }
 }
@@ -449,25 +660,56 @@ int launch_residual(const DGrid &g, const DCoef &k, double dt, int mode, const d
     return 2;
 }
 
-template <typename TV>
-int launch_jv_t(const DGrid &g, const DCoef &k, double dt, int mode, const double *part, const double *mob,
-                const TV *v, double *dG, double *sig, TV *Jv, cudaStream_t st, const double *Jec, const double *zsum)
+template <int D, bool EL>
+static void launch_jv64_d(const DGrid &g, const JvConst &c, const double *part, const double *mob, const double *v,
+                          double *dG, double *sig, double *Jv, cudaStream_t st, const double *Jec, const double *zsum)
 {
-    k_jv_a<TV><<<blocks_for(g.N), kThreads, 0, st>>>(g, k, dt, mode, part, v, dG, sig, Jv, Jec, zsum);
-    k_jv_b<TV><<<blocks_for(g.N), kThreads, 0, st>>>(g, k, dt, mode, mob, v, dG, sig, Jv, Jec, zsum);
+    const dim3 blk(D == 1 ? 256 : 32, D == 1 ? 1 : 8);
+    const dim3 grd((g.n[0] + blk.x - 1) / blk.x, (g.n[1] + blk.y - 1) / blk.y, g.n[2]);
+    k_jv64_a<D, EL><<<grd, blk, 0, st>>>(g, c, part, v, dG, sig);
+    k_jv64_b<D, EL><<<grd, blk, 0, st>>>(g, c, part, mob, v, dG, sig, Jv, Jec, zsum);
+}
+
+template <int D, bool EL>
+static void launch_jv32_d(const DGrid &g, const JvConst &c, const float *part, const float *mob, const float *v,
+                          float *Jv, cudaStream_t st, const float *Jec, const double *zsum)
+{
+    constexpr int TX = JvTile<D>::TX, TY = JvTile<D>::TY, TZ = JvTile<D>::TZ;
+    const long long tiles = (long long)((g.n[0] + TX - 1) / TX) * ((g.n[1] + TY - 1) / TY) * ((g.n[2] + TZ - 1) / TZ);
+    k_jv32<D, EL><<<(unsigned)tiles, 256, 0, st>>>(g, c, part, mob, v, Jv, Jec, zsum);
+}
+
+#define NKS_JV_DISPATCH(FN, ...)                                  \
+    switch (g.dim * 2 + (k.elastic ? 1 : 0)) {                    \
+    case 2: FN<1, false>(__VA_ARGS__); break;                     \
+    case 3: FN<1, true>(__VA_ARGS__); break;                      \
+    case 4: FN<2, false>(__VA_ARGS__); break;                     \
+    case 5: FN<2, true>(__VA_ARGS__); break;                      \
+    case 6: FN<3, false>(__VA_ARGS__); break;                     \
+    default: FN<3, true>(__VA_ARGS__); break;                     \
+    }
+
+int launch_jv64(const DGrid &g, const DCoef &k, double dt, int mode, const double *part, const double *mob,
+                const double *v, double *dG, double *sig, double *Jv, cudaStream_t st, const double *Jec,
+                const double *zsum)
+{
+    const JvConst c = jv_const(g, k, dt, mode);
+    NKS_JV_DISPATCH(launch_jv64_d, g, c, part, mob, v, dG, sig, Jv, st, Jec, zsum);
     return 2;
 }
-template int launch_jv_t<double>(const DGrid &, const DCoef &, double, int, const double *, const double *,
-                                 const double *, double *, double *, double *, cudaStream_t, const double *,
-                                 const double *);
-template int launch_jv_t<float>(const DGrid &, const DCoef &, double, int, const double *, const double *,
-                                const float *, double *, double *, float *, cudaStream_t, const double *,
-                                const double *);
+
+int launch_jv32(const DGrid &g, const DCoef &k, double dt, int mode, const float *part, const float *mob,
+                const float *v, float *Jv, cudaStream_t st, const float *Jec, const double *zsum)
+{
+    const JvConst c = jv_const(g, k, dt, mode);
+    NKS_JV_DISPATCH(launch_jv32_d, g, c, part, mob, v, Jv, st, Jec, zsum);
+    return 1;
+}
 
 int launch_jv(const DGrid &g, const DCoef &k, double dt, int mode, const double *part, const double *mob,
               const double *v, double *dG, double *sig, double *Jv, cudaStream_t st)
 {
-    return launch_jv_t<double>(g, k, dt, mode, part, mob, v, dG, sig, Jv, st, nullptr, nullptr);
+    return launch_jv64(g, k, dt, mode, part, mob, v, dG, sig, Jv, st, nullptr, nullptr);
 }
 
 int launch_energy(const DGrid &g, const DCoef &k, const double *X, double *partials, cudaStream_t st)

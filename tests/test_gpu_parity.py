@@ -50,18 +50,23 @@ def _pair(dim, n, seed, du=0.01):
     return (c1, e1, u1), (c0, e0, u0)
 
 
-CASES = [(2, (37, 29), (3, 2), 1), (2, (40, 36), (2, 3), 2), (3, (11, 10, 9), (2, 2, 2), 1)]
+# (dim, grid, subdomains, overlap, elastic): ragged tiles of the stencil kernels and
+# unequal Schwarz boxes; 1-D and the elasticity-free model (nf = 2) included
+CASES = [(2, (37, 29), (3, 2), 1, True), (2, (40, 36), (2, 3), 2, True), (3, (11, 10, 9), (2, 2, 2), 1, True),
+         (1, (61,), (3,), 2, True), (2, (35, 33), (2, 2), 1, False), (3, (9, 11, 10), (2, 2, 2), 1, False)]
 
 
-@pytest.mark.parametrize("dim,n,sub,ov", CASES)
-def test_operators_match_oracle(nks, dim, n, sub, ov):
-    cf = S.coefficients()
+@pytest.mark.parametrize("dim,n,sub,ov,elastic", CASES)
+def test_operators_match_oracle(nks, dim, n, sub, ov, elastic):
+    cf = S.coefficients() if elastic else S.coefficients(Lscale=0.0)
     op = S.options(sub=sub, overlap=ov)
     (c1, e1, u1), (c0, e0, u0) = _pair(dim, n, 100 + dim)
     P = nks.Problem(dim, n, 0.25, c0, e0, cf, op)
     O = oracle.Problem(dim, n, 0.25, cf, op)
     N, nf = P.N, P.nf
     cb = float(np.sum(c0) / N)
+    if nf == 2:
+        u1 = u0 = None
     X1g, X0g = soa(c1, e1, u1), soa(c0, e0, u0)
     X1o, X0o = O.interleave(c1, e1, u1), O.interleave(c0, e0, u0)
     to_soa = lambda Xo: soa(*O.split(Xo)) if nf > 2 else soa(*O.split(Xo)[:2])
@@ -103,6 +108,43 @@ def test_operators_match_oracle(nks, dim, n, sub, ov):
     rc, xo, its_o, res_o = O.linear_solve(X1o, X0o, cb, dt, O.interleave(*split_soa(b, N, nf)), tol)
     assert rel(x, to_soa(xo)) <= 1e-8
     assert abs(its - its_o) <= max(2, its_o // 5)
+    P.destroy()
+
+
+@pytest.mark.parametrize("dim,n,sub,ov,elastic", CASES)
+def test_mixed_operators_match_oracle(nks, dim, n, sub, ov, elastic):
+    """The mixed-precision forms as the solver applies them: the FP32 Jacobian action
+    (FP32 vectors, coefficients and arithmetic) and the FP32 Schwarz sweeps, against
+    the FP64 oracle within FP32 rounding of the largest term of each row."""
+    cf = S.coefficients() if elastic else S.coefficients(Lscale=0.0)
+    op = S.options(sub=sub, overlap=ov, precision="mixed")
+    (c1, e1, u1), (c0, e0, u0) = _pair(dim, n, 200 + dim)
+    P = nks.Problem(dim, n, 0.25, c0, e0, cf, op)
+    O = oracle.Problem(dim, n, 0.25, cf, op)
+    N, nf = P.N, P.nf
+    cb = float(np.sum(c0) / N)
+    if nf == 2:
+        u1 = u0 = None
+    X1g, X0g = soa(c1, e1, u1), soa(c0, e0, u0)
+    X1o, X0o = O.interleave(c1, e1, u1), O.interleave(c0, e0, u0)
+    to_soa = lambda Xo: soa(*O.split(Xo)) if nf > 2 else soa(*O.split(Xo)[:2])
+    dt = 0.07
+    v = np.random.default_rng(7).standard_normal(nf * N)
+    vo = O.interleave(*split_soa(v, N, nf))
+    for mode in (0, 1):
+        Jv = P.apply_jacobian(X1g, X0g, dt, v, mode)
+        Jm = O.jacobian_scipy(X1o, X0o, cb, dt, mode)
+        Jo = to_soa(Jm @ vo)
+        # scale of the row terms: |J| |v|
+        scale = to_soa(abs(Jm) @ np.abs(vo))
+        err = np.abs(Jv - Jo)
+        assert np.all(err <= 1e-5 * scale + 1e-30), (mode, float(np.max(err / (scale + 1e-300))))
+        assert rel(Jv, Jo) <= 1e-5, mode
+    r = np.random.default_rng(8).standard_normal(nf * N)
+    z = P.apply_preconditioner(X1g, X0g, dt, r)
+    rc, zo = O.precond_apply(X1o, X0o, cb, dt, O.interleave(*split_soa(r, N, nf)))
+    assert rc == 0
+    assert rel(z, to_soa(zo)) <= 1e-4
     P.destroy()
 
 
