@@ -206,8 +206,8 @@ int nks_mass(const nks_problem *p, double *out);
 int nks_get_fields(const nks_problem *p, double *c, double *eta, double *u);
 
 /* Checkpoint: bytes needed, then save / restore X^n, X^{n-1}, t, step count,
- * dt_{n-1}, zeta and the two last energies (HOST buffer). Restoring gives a
- * bitwise-identical continuation. */
+ * dt_{n-1}, zeta, the two last energies and cbar0 (HOST buffer). Restoring
+ * gives a bitwise-identical continuation. */
 size_t nks_state_size(const nks_problem *p);
 int nks_get_state(const nks_problem *p, void *buf, size_t bytes);
 int nks_set_state(nks_problem *p, const void *buf, size_t bytes);
@@ -219,8 +219,62 @@ int nks_reset_stats(nks_problem *p);
 void nks_destroy(nks_problem *p);
 
 /* Message of the last failure on this problem ("" if none); p may be NULL for
- * failures of nks_create_problem on the calling thread. */
+ * failures of nks_create_problem / nks_create_batch on the calling thread. */
 const char *nks_last_error(const nks_problem *p);
+
+/* ------------------------------------------------------------------------ */
+/* Batches: nb independent problems of the same grid, coefficients and       */
+/* options in one object (no counterpart in the paper, which solves one      */
+/* problem at a time).  Each phase of the solver (residual, Jacobian action, */
+/* Schwarz factorisation and sweeps, Gram-Schmidt passes, small GMRES        */
+/* kernels) is ONE kernel launch over all instances; every instance keeps    */
+/* its own Newton / GMRES iteration, step size and retries, and an instance  */
+/* that has converged is masked out of the remaining launches, so each      */
+/* instance's result is bitwise the result of solving it alone.  The        */
+/* problem API above acts on slot 0 (a problem is a batch of one).  Device  */
+/* memory: one allocation of nks_device_bytes() for all slots.              */
+/* ------------------------------------------------------------------------ */
+
+/* Create a batch of nb slots (1 <= nb <= 65535; in 3-D n_z * nb <= 65535).
+ *   c, eta   HOST, nb * N doubles each (slot-major), or both NULL: every slot
+ *            starts empty (fill slots with nks_batch_load).
+ * Each loaded slot takes its own mean composition cbar0 and initial
+ * mechanical equilibrium, as nks_create_problem does.  Errors as there. */
+int nks_create_batch(const nks_grid *grid, int nb, const double *c, const double *eta, const nks_coeffs *coeffs,
+                     const nks_opts *opts, const nks_allocator *alloc, void *stream, nks_problem **out);
+
+/* Number of slots. */
+int nks_batch_size(const nks_problem *p);
+
+/* Load initial fields (HOST, N doubles each) into a slot: resets its time,
+ * step count and step-size state, solves its initial equilibrium.  Other
+ * slots are untouched.  NKS_EINVAL for a bad slot, NKS_EDOMAIN as above. */
+int nks_batch_load(nks_problem *p, int slot, const double *c, const double *eta);
+
+/* Mark a slot empty (its buffers stay allocated for the next load). */
+int nks_batch_unload(nks_problem *p, int slot);
+
+/* 1 when the slot holds a problem, else 0. */
+int nks_batch_loaded(const nks_problem *p, int slot);
+
+/* One time step of every loaded slot with active[slot] != 0 (active NULL: all
+ * loaded slots).  dt: nb step sizes (> 0 fixed, <= 0 adaptive as in nks_step)
+ * or NULL (all adaptive).  infos: nb entries (written for the stepped slots).
+ * Returns NKS_OK unless a CUDA error stops the batch; per-slot failures are
+ * in infos[slot].status (the slot then stays at its X^n). */
+int nks_batch_step(nks_problem *p, const int *active, const double *dt, nks_step_info *infos);
+
+/* Per-slot versions of nks_energy, nks_mass, nks_get_fields, nks_get_state
+ * and nks_set_state (set_state also marks the slot loaded). */
+int nks_batch_energy(const nks_problem *p, int slot, double *out);
+int nks_batch_mass(const nks_problem *p, int slot, double *out);
+int nks_batch_get_fields(const nks_problem *p, int slot, double *c, double *eta, double *u);
+int nks_batch_get_state(const nks_problem *p, int slot, void *buf, size_t bytes);
+int nks_batch_set_state(nks_problem *p, int slot, const void *buf, size_t bytes);
+
+/* Device bytes of the per-slot buffers of all slots (state, Krylov basis,
+ * Schwarz factors, scratch). */
+size_t nks_device_bytes(const nks_problem *p);
 
 /* ------------------------------------------------------------------------ */
 /* Operator-level entry points (the stages of one Newton iteration).         */

@@ -130,6 +130,19 @@ def load():
         "nks_eval_energy": (ctypes.c_int, [_P, _D, _D, _D]),
         "nks_residual_noalloc": (ctypes.c_int, [ctypes.POINTER(nks_grid), ctypes.POINTER(nks_coeffs),
                                                 ctypes.c_double, ctypes.c_double, ctypes.c_int, _P, _P, _P, _P, _P]),
+        "nks_create_batch": (ctypes.c_int, [ctypes.POINTER(nks_grid), ctypes.c_int, _D, _D, ctypes.POINTER(nks_coeffs),
+                                            ctypes.POINTER(nks_opts), ctypes.POINTER(nks_allocator), _P, pp]),
+        "nks_batch_size": (ctypes.c_int, [_P]),
+        "nks_batch_load": (ctypes.c_int, [_P, ctypes.c_int, _D, _D]),
+        "nks_batch_unload": (ctypes.c_int, [_P, ctypes.c_int]),
+        "nks_batch_loaded": (ctypes.c_int, [_P, ctypes.c_int]),
+        "nks_batch_step": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), _D, ctypes.POINTER(nks_step_info)]),
+        "nks_batch_energy": (ctypes.c_int, [_P, ctypes.c_int, _D]),
+        "nks_batch_mass": (ctypes.c_int, [_P, ctypes.c_int, _D]),
+        "nks_batch_get_fields": (ctypes.c_int, [_P, ctypes.c_int, _D, _D, _D]),
+        "nks_batch_get_state": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_size_t]),
+        "nks_batch_set_state": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_size_t]),
+        "nks_device_bytes": (ctypes.c_size_t, [_P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -144,7 +157,10 @@ def exported_symbols():
     return ["nks_default_opts", "nks_create_problem", "nks_step", "nks_energy", "nks_mass", "nks_get_fields",
             "nks_state_size", "nks_get_state", "nks_set_state", "nks_get_stats", "nks_reset_stats", "nks_destroy",
             "nks_last_error", "nks_eval_residual", "nks_apply_jacobian", "nks_apply_preconditioner",
-            "nks_linear_solve", "nks_eval_energy", "nks_residual_noalloc"]
+            "nks_linear_solve", "nks_eval_energy", "nks_residual_noalloc", "nks_create_batch", "nks_batch_size",
+            "nks_batch_load", "nks_batch_unload", "nks_batch_loaded", "nks_batch_step", "nks_batch_energy",
+            "nks_batch_mass", "nks_batch_get_fields", "nks_batch_get_state", "nks_batch_set_state",
+            "nks_device_bytes"]
 
 
 def _ptr(a):
@@ -316,6 +332,110 @@ class Problem:
         parts, mass = np.empty(5), ctypes.c_double()
         _check(load().nks_eval_energy(self._h, _ptr(X), _ptr(parts), ctypes.byref(mass)), self._h)
         return parts, mass.value
+
+
+class Batch:
+    """nb same-shape problems stepped together (``nks_create_batch``): one kernel
+    launch per solver phase for all slots; each slot keeps its own Newton/GMRES
+    iteration and step size.  c, eta: (nb, N) arrays, or None for empty slots."""
+
+    def __init__(self, dim, n, h, nb, coeffs: dict, opts: dict, c=None, eta=None, stream=None, allocator=None,
+                 timing=False):
+        L = load()
+        self.dim, self.n, self.nb = dim, tuple(n[:dim]), int(nb)
+        self.N = int(np.prod(self.n))
+        self._grid = make_grid(dim, n, h)
+        self._coeffs = make_coeffs(coeffs)
+        self._opts = make_opts(opts, timing)
+        elastic = any(coeffs[k] != 0.0 for k in ("C11", "C12", "C44")) and coeffs.get("Lscale", 1.0) != 0.0
+        self.nf = 2 + (dim if elastic else 0)
+        cp = ep = None
+        if c is not None:
+            c, eta = _c64(c).reshape(-1), _c64(eta).reshape(-1)
+            assert c.size == self.N * self.nb and eta.size == self.N * self.nb
+            cp, ep = _ptr(c), _ptr(eta)
+        self._alloc = allocator
+        handle = ctypes.c_void_p()
+        rc = L.nks_create_batch(ctypes.byref(self._grid), self.nb, cp, ep, ctypes.byref(self._coeffs),
+                                ctypes.byref(self._opts), ctypes.byref(allocator) if allocator else None,
+                                ctypes.c_void_p(stream) if stream else None, ctypes.byref(handle))
+        _check(rc, None)
+        self._h = handle
+
+    def __del__(self):
+        self.destroy()
+
+    def destroy(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            load().nks_destroy(h)
+            self._h = None
+
+    def load(self, slot, c, eta):
+        c, eta = _c64(c), _c64(eta)
+        _check(load().nks_batch_load(self._h, int(slot), _ptr(c), _ptr(eta)), self._h)
+
+    def unload(self, slot):
+        _check(load().nks_batch_unload(self._h, int(slot)), self._h)
+
+    def loaded(self, slot):
+        return bool(load().nks_batch_loaded(self._h, int(slot)))
+
+    def step(self, active=None, dt=None):
+        """One step of the active loaded slots; returns one info dict per slot
+        (None for slots not stepped)."""
+        act = None
+        if active is not None:
+            a = (ctypes.c_int * self.nb)(*[1 if x else 0 for x in active])
+            act = ctypes.cast(a, ctypes.POINTER(ctypes.c_int))
+        dtp = None
+        if dt is not None:
+            d = np.full(self.nb, float(dt)) if np.isscalar(dt) else _c64(dt)
+            dtp = _ptr(d)
+        infos = (nks_step_info * self.nb)()
+        stepped = [load().nks_batch_loaded(self._h, i) and (active is None or bool(active[i]))
+                   for i in range(self.nb)]
+        _check(load().nks_batch_step(self._h, act, dtp, infos), self._h)
+        return [infos[i].as_dict() if stepped[i] else None for i in range(self.nb)]
+
+    def energy(self, slot):
+        v = ctypes.c_double()
+        _check(load().nks_batch_energy(self._h, int(slot), ctypes.byref(v)), self._h)
+        return v.value
+
+    def mass(self, slot):
+        v = ctypes.c_double()
+        _check(load().nks_batch_mass(self._h, int(slot), ctypes.byref(v)), self._h)
+        return v.value
+
+    def get_fields(self, slot):
+        c, eta = np.empty(self.N), np.empty(self.N)
+        u = np.empty((self.nf - 2, self.N)) if self.nf > 2 else None
+        _check(load().nks_batch_get_fields(self._h, int(slot), _ptr(c), _ptr(eta),
+                                           _ptr(u) if u is not None else None), self._h)
+        return c, eta, u
+
+    def get_state(self, slot) -> bytes:
+        L = load()
+        n = L.nks_state_size(self._h)
+        buf = ctypes.create_string_buffer(n)
+        _check(L.nks_batch_get_state(self._h, int(slot), buf, n), self._h)
+        return buf.raw
+
+    def set_state(self, slot, blob: bytes):
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        _check(load().nks_batch_set_state(self._h, int(slot), buf, len(blob)), self._h)
+
+    def get_stats(self):
+        s = nks_stats()
+        _check(load().nks_get_stats(self._h, ctypes.byref(s)), self._h)
+        return s.as_dict()
+
+    def reset_stats(self):
+        _check(load().nks_reset_stats(self._h), self._h)
+
+    def device_bytes(self):
+        return int(load().nks_device_bytes(self._h))
 
 
 NOALLOC_MAX_POINTS = 65536

@@ -1,4 +1,5 @@
-// nks_api.cu -- C ABI, Newton iteration (Sec. 4) and adaptive time stepping.
+// nks_api.cu -- C ABI, Newton iteration (Sec. 4) and adaptive time stepping,
+// for batches of same-shape instances (a single problem is a batch of one).
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -104,6 +105,64 @@ int Problem::sync_check(const char *where)
     return NKS_OK;
 }
 
+// ---------------------------------------------------------------------------
+// batch helpers.  Uploads go through a ring of pinned staging slots: an
+// asynchronous copy reads its slot when the stream reaches it, and the driver
+// synchronises far more often than the ring wraps.
+// ---------------------------------------------------------------------------
+
+constexpr int kRing = 256;
+
+Bat Problem::set_mask(int m, const std::vector<char> &on)
+{
+    int *h = hmask_ring + (size_t)(ring_pos++ % kRing) * nb;
+    for (int i = 0; i < nb; i++) h[i] = on[i] ? 1 : 0;
+    cudaMemcpyAsync(dmask + (size_t)m * nb, h, sizeof(int) * nb, cudaMemcpyHostToDevice, stream);
+    return masked(m);
+}
+
+void Problem::upload_isc()
+{
+    double *h = hsc_ring + (size_t)(ring_pos++ % kRing) * nb * I_NSC;
+    for (int i = 0; i < nb; i++) {
+        double *r = h + (size_t)i * I_NSC;
+        for (int q = 0; q < I_NSC; q++) r[q] = 0.0;
+        r[I_DT] = is[i].dt > 0.0 ? is[i].dt : 1.0;
+        r[I_CBAR0] = is[i].cbar0;
+        r[I_LAM] = is[i].lam;
+    }
+    cudaMemcpy2DAsync(isc, (size_t)stride, h, sizeof(double) * I_NSC, sizeof(double) * I_NSC, (size_t)nb,
+                      cudaMemcpyHostToDevice, stream);
+}
+
+// count doubles at dev0 (instance 0's address) of every instance -> hread[i * 64 + q],
+// and both flag words of every instance -> hflags[2 i + q]; synchronises
+int Problem::read_scalars(const double *dev0, int count, const char *where)
+{
+    if (dev0 && count > 0)
+        cudaMemcpy2DAsync(hread, sizeof(double) * 64, dev0, (size_t)stride, sizeof(double) * count, (size_t)nb,
+                          cudaMemcpyDeviceToHost, stream);
+    cudaMemcpy2DAsync(hflags, sizeof(int) * 2, dflag, (size_t)stride, sizeof(int) * 2, (size_t)nb,
+                      cudaMemcpyDeviceToHost, stream);
+    return sync_check(where);
+}
+
+int Problem::read_flags(const char *where) { return read_scalars(nullptr, 0, where); }
+
+static std::vector<char> only(int nb, int i)
+{
+    std::vector<char> v(nb, 0);
+    v[i] = 1;
+    return v;
+}
+
+static bool any_of(const std::vector<char> &v)
+{
+    for (char c : v)
+        if (c) return true;
+    return false;
+}
+
 // App. B: dE_G/dc = M0 + M1(phi) c + M2(phi) c^2 + M3 c^3 + M4 c^4 + ..., with the
 // coefficients expressed through the App. A parameters (all divided by V_m dE).
 DCoef derive_coefficients(const nks_coeffs &c, int dim, double cbar0)
@@ -144,138 +203,323 @@ DCoef derive_coefficients(const nks_coeffs &c, int dim, double cbar0)
     return k;
 }
 
-// ||F||^2 after launch_residual; returns the domain flag too
-static int residual(Problem *P, double dt, int mode, const double *X1, const double *X0, double *F, double *part,
-                    double *fn, bool *domain_ok)
+// ||F||^2 and the domain flag of every instance in `on` (one launch each)
+static int residual(Problem *P, int mode, const double *X1, const double *X0, double *F, double *part,
+                    const std::vector<char> &on, std::vector<double> &fn, std::vector<char> &dok)
 {
-    cudaMemsetAsync(P->dflag, 0, sizeof(int), P->stream);
+    const Bat bt = P->set_mask(M_X1, on);
+    cudaMemset2DAsync(P->dflag, (size_t)P->stride, 0, sizeof(int), (size_t)P->nb, P->stream);
     P->tick(0);
-    P->count(launch_residual(P->g, P->k, dt, mode, X1, X0, P->tr0, P->mob, P->Gc, P->sig, part, F, P->dflag,
-                             P->partials, P->stream));
-    P->count(launch_finalize(P->partials, kRedBlocks, 1, P->dscal, P->stream));
+    P->count(launch_residual(P->g, P->k, P->isc, mode, X1, X0, P->tr0, P->mob, P->Gc, P->sig, part, F, P->dflag,
+                             P->partials, P->rb, P->stream, bt));
+    P->count(launch_finalize(P->partials, P->rb, 1, P->dscal, P->stream, bt));
     P->tock(0);
-    cudaMemcpyAsync(P->hscal, P->dscal, sizeof(double), cudaMemcpyDeviceToHost, P->stream);
-    cudaMemcpyAsync(P->hscal + 1, P->dflag, sizeof(int), cudaMemcpyDeviceToHost, P->stream);
-    int rc = P->sync_check("residual");
+    int rc = P->read_scalars(P->dscal, 1, "residual");
     if (rc) return rc;
-    int flag = 0;
-    memcpy(&flag, P->hscal + 1, sizeof(int));
-    *fn = sqrt(P->hscal[0]);
-    *domain_ok = (flag & 1) == 0;
+    fn.assign(P->nb, 0.0);
+    dok.assign(P->nb, 1);
+    for (int i = 0; i < P->nb; i++) {
+        if (!on[i]) continue;
+        fn[i] = sqrt(P->hread[(size_t)i * 64]);
+        dok[i] = (P->hflags[2 * i] & 1) == 0;
+    }
     return NKS_OK;
 }
 
 // level-n quantities used by every residual of the step
-static void prepare_level(Problem *P, const double *X0)
+static void prepare_level(Problem *P, const double *X0, const Bat &bt)
 {
     P->tick(8);
-    P->count(launch_mobility(P->g, P->k, X0, P->mob, P->stream));
-    if (P->k.elastic) P->count(launch_trace0(P->g, P->k, X0, P->tr0, P->stream));
+    P->count(launch_mobility(P->g, P->k, X0, P->mob, P->stream, bt));
+    if (P->k.elastic) P->count(launch_trace0(P->g, P->k, P->isc, X0, P->tr0, P->stream, bt));
     P->tock(8);
 }
 
-// One NKS solve (Sec. 4) for X^{n+1} from X = X^n on entry; P->Xn holds X^n.
-// mode 1 solves the displacement-only system (initial equilibrium).
-static int newton(Problem *P, double dt, int mode, double rtol, double atol, int maxit, nks_step_info *info)
+// One NKS solve (Sec. 4) for X^{n+1} of every instance in `on`: X holds the
+// starting iterate (X^n), Xn holds X^n, is[i].dt the step (uploaded to isc).
+// mode 1 solves the displacement-only system (initial equilibrium).  Outcome
+// per instance in is[i]: nst = 0 converged, -status when it failed.  The
+// instances run in lockstep; each one does exactly the work it does alone.
+static int newton(Problem *P, int mode, double rtol, double atol, int maxit, const std::vector<char> &on)
 {
     const long long n = P->nvec;
-    P->cur_dt = dt;
+    const int nbt = P->nb;
     P->cur_mode = mode;
-    P->factored = false;
-    double fn0;
-    bool ok;
-    int rc = residual(P, dt, mode, P->X, P->Xn, P->F, P->part, &fn0, &ok);
+    std::vector<double> fn;
+    std::vector<char> dok;
+    int rc = residual(P, mode, P->X, P->Xn, P->F, P->part, on, fn, dok);
     if (rc) return rc;
-    info->fnorm0 = fn0;
-    info->fnorm = fn0;
-    info->newton_its = 0;
-    info->gmres_its = 0;
-    if (!ok) {
-        P->err = "state outside the domain of the logarithms";
-        return NKS_EDOMAIN;
+    std::vector<char> run(nbt, 0);
+    for (int i = 0; i < nbt; i++) {
+        if (!on[i]) continue;
+        IState &s = P->is[i];
+        s.fn0 = s.fn = fn[i];
+        s.newton_its = s.gmres_its = 0;
+        s.err.clear();
+        s.nst = 0;
+        if (!dok[i]) {
+            s.nst = -NKS_EDOMAIN;
+            s.err = "state outside the domain of the logarithms";
+        } else if (!(fn[i] == fn[i]) || isinf(fn[i])) {
+            s.nst = -NKS_EDIVERGED;
+            s.err = "non-finite residual";
+        } else {
+            s.tol = std::max(rtol * s.fn0, atol);
+            if (s.fn0 > s.tol) {
+                s.nst = 1;
+                run[i] = 1;
+            }
+        }
     }
-    if (!(fn0 == fn0) || isinf(fn0)) {
-        P->err = "non-finite residual";
-        return NKS_EDIVERGED;
-    }
-    const double tol = std::max(rtol * fn0, atol);
-    if (fn0 <= tol) return NKS_OK;
-    double fn = fn0;
-    for (int it = 0; it < maxit; it++) {
-        if (!P->factored || !P->opts.ilu_reuse) {
-            rc = ras_factor(P, mode);
+    for (int it = 0; it < maxit && any_of(run); it++) {
+        Bat br = P->set_mask(M_RUN, run);
+        if (it == 0 || !P->opts.ilu_reuse) {
+            rc = ras_factor(P, mode, br, run);
             if (rc) return rc;
+            bool changed = false;
+            for (int i = 0; i < nbt; i++)
+                if (run[i] && P->is[i].nst < 0) {
+                    run[i] = 0;
+                    changed = true;
+                }
+            if (!any_of(run)) break;
+            if (changed) br = P->set_mask(M_RUN, run);
         }
         P->tick(8);
-        P->count(launch_axpby(n, -1.0, P->F, 0.0, P->B, P->stream));
+        P->count(launch_axpby(n, -1.0, P->F, 0.0, P->B, P->stream, br));
         P->tock(8);
-        int gits = 0;
-        double gres = 0.0;
-        rc = gmres_solve(P, mode, P->B, P->S, std::max(P->opts.gmres_rtol * fn, P->opts.gmres_atol), &gits, &gres);
+        for (int i = 0; i < nbt; i++) {
+            IState &s = P->is[i];
+            s.gin = run[i] != 0;
+            if (s.gin) s.gtol = std::max(P->opts.gmres_rtol * s.fn, P->opts.gmres_atol);
+        }
+        rc = gmres_solve(P, mode, P->B, P->S);
         if (rc) return rc;
-        info->gmres_its += gits;
-        P->stats.gmres_its += gits;
-        double lam = 1.0, ftn = 0.0;
-        bool accepted = false;
-        while (lam >= P->opts.ls_lambda_min) {
-            P->tick(8);
-            P->count(launch_waxpy(n, P->X, lam, P->S, P->Xt, P->stream));
-            P->tock(8);
-            bool dok;
-            rc = residual(P, dt, mode, P->Xt, P->Xn, P->Ft, P->part_t, &ftn, &dok);
-            if (rc) return rc;
-            if (dok && ftn == ftn && !isinf(ftn) && ftn * ftn <= (1.0 - 2.0 * P->opts.ls_alpha * lam) * fn * fn) {
-                accepted = true;
-                break;
+        for (int i = 0; i < nbt; i++)
+            if (run[i]) {
+                P->is[i].gmres_its += P->is[i].gits;
+                P->stats.gmres_its += P->is[i].gits;
             }
-            lam *= 0.5;
+        // backtracking line search, each instance with its own lambda
+        std::vector<char> ls = run;
+        for (int i = 0; i < nbt; i++)
+            if (run[i]) {
+                P->is[i].lam = 1.0;
+                P->is[i].accepted = false;
+            }
+        while (any_of(ls)) {
+            P->upload_isc();
+            const Bat bl = P->set_mask(M_LS, ls);
+            P->tick(8);
+            P->count(launch_waxpy_lam(n, P->X, P->isc, P->S, P->Xt, P->stream, bl));
+            P->tock(8);
+            rc = residual(P, mode, P->Xt, P->Xn, P->Ft, P->part_t, ls, fn, dok);
+            if (rc) return rc;
+            for (int i = 0; i < nbt; i++) {
+                if (!ls[i]) continue;
+                IState &s = P->is[i];
+                const double f = fn[i];
+                if (dok[i] && f == f && !isinf(f) && f * f <= (1.0 - 2.0 * P->opts.ls_alpha * s.lam) * s.fn * s.fn) {
+                    s.accepted = true;
+                    s.ftn = f;
+                    ls[i] = 0;
+                } else {
+                    s.lam *= 0.5;
+                    if (s.lam < P->opts.ls_lambda_min) ls[i] = 0;
+                }
+            }
         }
-        info->newton_its = it + 1;
-        P->stats.newton_its++;
-        if (!accepted) {
-            P->err = "line search failed";
-            return NKS_EDIVERGED;
+        std::vector<char> acc(nbt, 0);
+        for (int i = 0; i < nbt; i++) {
+            if (!run[i]) continue;
+            IState &s = P->is[i];
+            s.newton_its = it + 1;
+            P->stats.newton_its++;
+            if (!s.accepted) {
+                s.nst = -NKS_EDIVERGED;
+                s.err = "line search failed";
+                run[i] = 0;
+            } else {
+                acc[i] = 1;
+            }
         }
-        std::swap(P->X, P->Xt);
-        std::swap(P->F, P->Ft);
-        std::swap(P->part, P->part_t);
-        fn = ftn;
-        info->fnorm = fn;
-        if (fn <= tol) return NKS_OK;
+        if (any_of(acc)) {
+            const Bat ba = P->set_mask(M_ACC, acc);
+            P->tick(8);
+            P->count(launch_copy(n, P->Xt, P->X, P->stream, ba));
+            P->count(launch_copy(n, P->Ft, P->F, P->stream, ba));
+            P->count(launch_copy(4 * P->N, P->part_t, P->part, P->stream, ba));
+            P->tock(8);
+        }
+        for (int i = 0; i < nbt; i++) {
+            if (!acc[i]) continue;
+            IState &s = P->is[i];
+            s.fn = s.ftn;
+            if (s.fn <= s.tol) {
+                s.nst = 0;
+                run[i] = 0;
+            }
+        }
     }
-    P->err = "Newton iteration limit reached";
-    return NKS_EDIVERGED;
-}
-
-static int energy_mass(Problem *P, const double *X, double *parts5, double *mass)
-{
-    P->tick(7);
-    P->count(launch_energy(P->g, P->k, X, P->partials, P->stream));
-    P->count(launch_finalize(P->partials, kRedBlocks, 5, P->dscal, P->stream));
-    P->tock(7);
-    cudaMemcpyAsync(P->hscal, P->dscal, 5 * sizeof(double), cudaMemcpyDeviceToHost, P->stream);
-    int rc = P->sync_check("energy");
-    if (rc) return rc;
-    double v = 1.0;
-    for (int J = 0; J < P->g.dim; J++) v *= P->g.h;
-    const double *s = P->hscal;
-    if (parts5) {
-        for (int i = 0; i < 4; i++) parts5[i] = s[i] * v;
-        parts5[4] = (s[0] + s[1] + s[2] + s[3]) * v;
-    }
-    if (mass) *mass = s[4] * v;
+    for (int i = 0; i < nbt; i++)
+        if (run[i]) {
+            P->is[i].nst = -NKS_EDIVERGED;
+            P->is[i].err = "Newton iteration limit reached";
+        }
     return NKS_OK;
 }
 
-static int equilibrate(Problem *P)
+// energy parts (e1..e4, total) and mass of every instance in `on`: parts[5 i + q], mass[i]
+static int energy_mass(Problem *P, const double *X, const std::vector<char> &on, std::vector<double> &parts,
+                       std::vector<double> &mass)
+{
+    const Bat bt = P->set_mask(M_X1, on);
+    P->tick(7);
+    P->count(launch_energy(P->g, P->k, P->isc, X, P->partials, P->rb, P->stream, bt));
+    P->count(launch_finalize(P->partials, P->rb, 5, P->dscal, P->stream, bt));
+    P->tock(7);
+    int rc = P->read_scalars(P->dscal, 5, "energy");
+    if (rc) return rc;
+    double v = 1.0;
+    for (int J = 0; J < P->g.dim; J++) v *= P->g.h;
+    parts.assign((size_t)P->nb * 5, 0.0);
+    mass.assign(P->nb, 0.0);
+    for (int i = 0; i < P->nb; i++) {
+        if (!on[i]) continue;
+        const double *s = P->hread + (size_t)i * 64;
+        for (int q = 0; q < 4; q++) parts[5 * i + q] = s[q] * v;
+        parts[5 * i + 4] = (s[0] + s[1] + s[2] + s[3]) * v;
+        mass[i] = s[4] * v;
+    }
+    return NKS_OK;
+}
+
+// initial mechanical equilibrium of the instances in `on` (u solved with c, eta fixed)
+static int equilibrate(Problem *P, const std::vector<char> &on)
 {
     if (!P->k.elastic) return NKS_OK;
-    cudaMemcpyAsync(P->X, P->Xn, sizeof(double) * P->nvec, cudaMemcpyDeviceToDevice, P->stream);
-    prepare_level(P, P->Xn);
-    nks_step_info info{};
-    int rc = newton(P, 1.0, 1, P->opts.u0_rtol, P->opts.u0_atol, P->opts.u0_maxit, &info);
+    const Bat bt = P->set_mask(M_X2, on);
+    P->count(launch_copy(P->nvec, P->Xn, P->X, P->stream, bt));
+    for (int i = 0; i < P->nb; i++)
+        if (on[i]) P->is[i].dt = 1.0;
+    P->upload_isc();
+    prepare_level(P, P->Xn, bt);
+    int rc = newton(P, 1, P->opts.u0_rtol, P->opts.u0_atol, P->opts.u0_maxit, on);
     if (rc) return rc;
-    std::swap(P->Xn, P->X);
+    for (int i = 0; i < P->nb; i++)
+        if (on[i] && P->is[i].nst != 0) {
+            P->err = P->is[i].err;
+            return -P->is[i].nst;
+        }
+    const Bat b2 = P->set_mask(M_X2, on);
+    P->count(launch_copy(P->nvec, P->X, P->Xn, P->stream, b2));
+    return NKS_OK;
+}
+
+// one accepted time step of every instance in `on` (dt[i] > 0 fixed, else the
+// adaptive rule of Sec. 4); per-instance results in info[i]
+static int step_batch(Problem *P, const std::vector<char> &on, const double *dt_arg, nks_step_info *info)
+{
+    const int nbt = P->nb;
+    const long long n = P->nvec;
+    std::vector<double> dt(nbt, 0.0);
+    std::vector<char> fixed(nbt, 0), need(nbt, 0);
+    for (int i = 0; i < nbt; i++) {
+        if (!on[i]) continue;
+        IState &s = P->is[i];
+        if (dt_arg && dt_arg[i] > 0.0) {
+            dt[i] = dt_arg[i];
+            fixed[i] = 1;
+        } else if (s.nstep == 0 || P->opts.dt_mode == NKS_DT_FIXED) {
+            dt[i] = P->opts.dt_init;
+        } else if (P->opts.dt_mode == NKS_DT_SOLUTION) {
+            need[i] = 1;
+        } else {
+            const double Xd = fabs(s.E - s.Eprev) / s.dt_prev;
+            dt[i] = std::max(P->opts.dt_min, P->opts.dt_max / sqrt(1.0 + s.zeta * Xd * Xd));  // Eq. sencondt
+        }
+    }
+    if (any_of(need)) {
+        const Bat bn = P->set_mask(M_X2, need);
+        P->count(launch_waxpy(n, P->Xn, -1.0, P->Xprev, P->W, P->stream, bn));
+        P->count(launch_dot2(n, P->W, P->W, P->partials, P->rb, P->stream, bn));
+        P->count(launch_finalize(P->partials, P->rb, 2, P->dscal, P->stream, bn));
+        int rc = P->read_scalars(P->dscal + 1, 1, "dt");
+        if (rc) return rc;
+        for (int i = 0; i < nbt; i++)
+            if (need[i]) {
+                const IState &s = P->is[i];
+                const double Xd = sqrt(P->hread[(size_t)i * 64]) / s.dt_prev;
+                dt[i] = std::max(P->opts.dt_min, P->opts.dt_max / sqrt(1.0 + s.zeta * Xd * Xd));
+            }
+    }
+    std::vector<int> retries(nbt, 0), status(nbt, NKS_OK);
+    for (int i = 0; i < nbt; i++)
+        if (on[i] && !P->opts.zeta_persist) P->is[i].zeta = P->opts.zeta;
+    std::vector<char> pend = on;
+    while (any_of(pend)) {
+        const Bat bp = P->set_mask(M_X2, pend);
+        P->count(launch_copy(n, P->Xn, P->X, P->stream, bp));
+        for (int i = 0; i < nbt; i++)
+            if (pend[i]) P->is[i].dt = dt[i];
+        P->upload_isc();
+        prepare_level(P, P->Xn, bp);
+        int rc = newton(P, 0, P->opts.newton_rtol, P->opts.newton_atol, P->opts.newton_maxit, pend);
+        if (rc) return rc;
+        for (int i = 0; i < nbt; i++) {
+            if (!pend[i]) continue;
+            IState &s = P->is[i];
+            if (s.nst == 0) {
+                pend[i] = 0;
+                continue;
+            }
+            const int st = -s.nst;
+            if (st == NKS_ECUDA || fixed[i] || retries[i] >= P->opts.max_retries) {
+                status[i] = st;
+                pend[i] = 0;
+                continue;
+            }
+            // Sec. 4: a diverged NKS solve restarts with dt / sqrt(2) and zeta doubled
+            dt[i] /= sqrt(2.0);
+            s.zeta *= 2.0;
+            retries[i]++;
+            P->stats.retries++;
+        }
+    }
+    std::vector<char> ok(nbt, 0);
+    for (int i = 0; i < nbt; i++) ok[i] = on[i] && status[i] == NKS_OK;
+    std::vector<double> parts, mass;
+    if (any_of(ok)) {
+        const Bat bs = P->set_mask(M_X2, ok);
+        P->count(launch_copy(n, P->Xn, P->Xprev, P->stream, bs));  // X^{n-1} <- X^n
+        P->count(launch_copy(n, P->X, P->Xn, P->stream, bs));      // X^n <- X^{n+1}
+        int rc = energy_mass(P, P->Xn, ok, parts, mass);
+        if (rc) return rc;
+    }
+    for (int i = 0; i < nbt; i++) {
+        if (!on[i]) continue;
+        IState &s = P->is[i];
+        nks_step_info f{};
+        f.dt = dt[i];
+        f.retries = retries[i];
+        f.newton_its = s.newton_its;
+        f.gmres_its = s.gmres_its;
+        f.fnorm0 = s.fn0;
+        f.fnorm = s.fn;
+        if (ok[i]) {
+            s.Eprev = s.E;
+            s.E = parts[5 * i + 4];
+            s.t += dt[i];
+            s.dt_prev = dt[i];
+            s.nstep++;
+            P->stats.steps++;
+            f.mass = mass[i];
+        }
+        f.t = s.t;
+        f.energy = s.E;
+        f.status = status[i];
+        if (info) info[i] = f;
+    }
     return NKS_OK;
 }
 
@@ -288,6 +532,44 @@ static bool host_in_domain(long long N, const double *c, const double *e)
     return true;
 }
 
+// fields of one instance into its X^n (c, eta; u = 0) and its level-0 scalars
+static void load_fields(Problem *P, int i, const double *c, const double *eta)
+{
+    const size_t fb = sizeof(double) * (size_t)P->N;
+    double *Xn = shift(P->Xn, (long long)i * P->stride);
+    cudaMemsetAsync(Xn, 0, sizeof(double) * (size_t)P->ldv, P->stream);
+    cudaMemcpyAsync(Xn, c, fb, cudaMemcpyHostToDevice, P->stream);
+    cudaMemcpyAsync(Xn + P->N, eta, fb, cudaMemcpyHostToDevice, P->stream);
+    double s = 0.0;
+    for (long long p = 0; p < P->N; p++) s += c[p];
+    IState &st = P->is[i];
+    st = IState{};
+    st.cbar0 = s / (double)P->N;
+    st.zeta = P->opts.zeta;
+    st.dt_prev = P->opts.dt_init;
+    st.lam = 1.0;
+}
+
+// after load_fields: equilibrium, X^{n-1} = X^n, energy
+static int init_instances(Problem *P, const std::vector<char> &on)
+{
+    P->upload_isc();
+    int rc = P->sync_check("load");
+    if (!rc) rc = equilibrate(P, on);
+    if (rc) return rc;
+    const Bat bt = P->set_mask(M_X2, on);
+    P->count(launch_copy(P->nvec, P->Xn, P->Xprev, P->stream, bt));
+    std::vector<double> parts, mass;
+    rc = energy_mass(P, P->Xn, on, parts, mass);
+    if (rc) return rc;
+    for (int i = 0; i < P->nb; i++)
+        if (on[i]) {
+            P->is[i].E = P->is[i].Eprev = parts[5 * i + 4];
+            P->is[i].loaded = true;
+        }
+    return NKS_OK;
+}
+
 }  // namespace nks
 
 using namespace nks;
@@ -295,6 +577,7 @@ using namespace nks;
 struct nks_problem {
     Problem P;
 };
+
 
 extern "C" {
 
@@ -328,12 +611,9 @@ void nks_default_opts(nks_opts *o)
     o->timing = 0;
 }
 
-int nks_create_problem(const nks_grid *grid, const double *c, const double *eta, const nks_coeffs *coeffs,
-                       const nks_opts *opts, const nks_allocator *alloc, void *stream, nks_problem **out)
+static int validate(const nks_grid *grid, const nks_coeffs *coeffs, const nks_opts *opts, int nb)
 {
-    *out = nullptr;
-    g_create_error.clear();
-    if (!grid || !c || !eta || !coeffs || !opts) {
+    if (!grid || !coeffs || !opts) {
         g_create_error = "null argument";
         return NKS_EINVAL;
     }
@@ -354,6 +634,10 @@ int nks_create_problem(const nks_grid *grid, const double *c, const double *eta,
         g_create_error = "grid: (2 + dim) * points must be below 2^31";
         return NKS_EINVAL;
     }
+    if (nb < 1 || nb > 65535 || (grid->dim == 3 && (long long)grid->n[2] * nb > 65535)) {
+        g_create_error = "batch: 1 <= nb <= 65535 (and n_z * nb <= 65535 in 3-D)";
+        return NKS_EINVAL;
+    }
     if (coeffs->S < 1 || coeffs->S > 16) {
         g_create_error = "coeffs: S must be in 1..16";
         return NKS_EINVAL;
@@ -366,12 +650,40 @@ int nks_create_problem(const nks_grid *grid, const double *c, const double *eta,
         g_create_error = "opts: precision must be NKS_FP64 or NKS_MIXED";
         return NKS_EINVAL;
     }
+    return NKS_OK;
+}
+
+int nks_create_batch(const nks_grid *grid, int nb, const double *c, const double *eta, const nks_coeffs *coeffs,
+                     const nks_opts *opts, const nks_allocator *alloc, void *stream, nks_problem **out)
+{
+    if (!out) {
+        g_create_error = "null argument";
+        return NKS_EINVAL;
+    }
+    *out = nullptr;
+    g_create_error.clear();
+    int rc = validate(grid, coeffs, opts, nb);
+    if (rc) return rc;
+    if ((c == nullptr) != (eta == nullptr)) {
+        g_create_error = "c and eta must both be given or both be NULL";
+        return NKS_EINVAL;
+    }
+    long long N = 1;
+    for (int J = 0; J < grid->dim; J++) N *= grid->n[J];
+    if (c)
+        for (int i = 0; i < nb; i++)
+            if (!host_in_domain(N, c + (size_t)i * N, eta + (size_t)i * N)) {
+                g_create_error = "initial state outside the domain: c, c*eta and c*(4-3*eta) must lie in (0, 1)";
+                return NKS_EDOMAIN;
+            }
     nks_problem *H = new nks_problem();
     Problem *P = &H->P;
     cudaGetDevice(&P->device);
     P->grid = *grid;
     P->coeffs = *coeffs;
     P->opts = *opts;
+    P->nb = nb;
+    P->is.assign(nb, IState{});
     if (alloc && alloc->alloc && alloc->free) {
         P->alloc = *alloc;
         P->have_alloc = true;
@@ -385,97 +697,175 @@ int nks_create_problem(const nks_grid *grid, const double *c, const double *eta,
     DGrid &g = P->g;
     g.dim = grid->dim;
     for (int J = 0; J < 3; J++) g.n[J] = J < grid->dim ? grid->n[J] : 1;
-    g.N = (long long)g.n[0] * g.n[1] * g.n[2];
+    g.N = N;
     g.h = grid->h;
-    P->N = g.N;
-    if (!host_in_domain(g.N, c, eta)) {
-        g_create_error = "initial state outside the domain: c, c*eta and c*(4-3*eta) must lie in (0, 1)";
-        nks_destroy(H);
-        return NKS_EDOMAIN;
-    }
-    double s = 0.0;
-    for (long long p = 0; p < g.N; p++) s += c[p];
-    P->cbar0 = s / (double)g.N;
-    P->k = derive_coefficients(*coeffs, g.dim, P->cbar0);
+    P->N = N;
+    P->k = derive_coefficients(*coeffs, g.dim, 0.0);  // the mean composition of each instance lives in isc
     P->nf = P->k.nf;
     P->nvec = P->nf * g.N;
     P->ldv = (P->nvec + 1) & ~1LL;
     P->ldvf = (P->nvec + 3) & ~3LL;
-    // every work vector holds ldv entries; the entry past nvec stays zero (16-byte pair loads)
-    const size_t vb = sizeof(double) * (size_t)P->ldv, fb = sizeof(double) * (size_t)g.N;
-    const int m = opts->gmres_restart;
-    double **vecs[] = {&P->Xn, &P->Xprev, &P->X, &P->Xt, &P->F, &P->Ft, &P->S, &P->B, &P->W, &P->Z, &P->R};
-    bool ok = true;
-    for (double **v : vecs) ok = ok && ((*v = (double *)P->dalloc(vb)) != nullptr);
-    ok = ok && (P->part = (double *)P->dalloc(4 * fb)) && (P->part_t = (double *)P->dalloc(4 * fb)) &&
-         (P->mob = (double *)P->dalloc(3 * fb)) && (P->tr0 = (double *)P->dalloc(fb)) &&
-         (P->Gc = (double *)P->dalloc(fb)) && (P->sig = (double *)P->dalloc(6 * fb)) &&
-         (P->partials = (double *)P->dalloc(sizeof(double) * kRedBlocks * 64)) &&
-         (P->dscal = (double *)P->dalloc(sizeof(double) * 64)) && (P->dflag = (int *)P->dalloc(sizeof(int) * 4)) &&
-         (P->tickets = (unsigned int *)P->dalloc(sizeof(unsigned int) * 16)) &&
-         (P->zsum = (double *)P->dalloc(sizeof(double) * 8)) && (P->Jec = (double *)P->dalloc(vb)) &&
-         (P->ec = (double *)P->dalloc(vb)) &&
-         (P->V = (double *)P->dalloc(vb * (opts->precision == NKS_MIXED ? 1 : m + 1))) &&
-         (P->T64 = (double *)P->dalloc(vb)) &&
-         (P->gm = (double *)P->dalloc(sizeof(double) * gmres_state_doubles(m)));
-    if (ok && opts->precision == NKS_MIXED) {
-        const size_t fvb = sizeof(float) * (size_t)P->ldvf;
-        ok = (P->Vf = (float *)P->dalloc(fvb * (m + 1))) && (P->Wf = (float *)P->dalloc(fvb)) &&
-             (P->Zf = (float *)P->dalloc(fvb)) &&
-             (P->partf = (float *)P->dalloc(sizeof(float) * 4 * (size_t)g.N)) &&
-             (P->mobf = (float *)P->dalloc(sizeof(float) * g.dim * (size_t)g.N)) &&
-             (P->Jecf = (float *)P->dalloc(sizeof(float) * 2 * (size_t)g.N));
-        if (ok) {
-            cudaMemsetAsync(P->Vf, 0, fvb * (m + 1), P->stream);
-            cudaMemsetAsync(P->Wf, 0, fvb, P->stream);
-            cudaMemsetAsync(P->Zf, 0, fvb, P->stream);
-        }
-    }
-    if (ok && cudaMallocHost((void **)&P->hscal, 64 * sizeof(double)) != cudaSuccess) ok = false;
-    if (!ok) {
-        g_create_error = "out of device memory";
-        nks_destroy(H);
-        return NKS_ENOMEM;
-    }
-    for (double **v : vecs) cudaMemsetAsync(*v, 0, vb, P->stream);
-    cudaMemsetAsync(P->V, 0, vb * (opts->precision == NKS_MIXED ? 1 : m + 1), P->stream);
-    cudaMemsetAsync(P->T64, 0, vb, P->stream);
-    cudaMemcpyAsync(P->Xn, c, fb, cudaMemcpyHostToDevice, P->stream);
-    cudaMemcpyAsync(P->Xn + g.N, eta, fb, cudaMemcpyHostToDevice, P->stream);
-    cudaMemsetAsync(P->tr0, 0, fb, P->stream);
-    cudaMemsetAsync(P->tickets, 0, sizeof(unsigned int) * 16, P->stream);
-    cudaMemsetAsync(P->zsum, 0, sizeof(double) * 8, P->stream);
-    cudaMemsetAsync(P->Jec, 0, vb, P->stream);
-    cudaMemsetAsync(P->ec, 0, vb, P->stream);
-    {
-        const std::vector<double> ones((size_t)g.N, 1.0);
-        cudaMemcpyAsync(P->ec, ones.data(), fb, cudaMemcpyHostToDevice, P->stream);
-        cudaStreamSynchronize(P->stream);
-    }
+    P->rb = (int)std::min<long long>(kRedBlocks, std::max<long long>(1, (P->ldv / 2 + 4 * kRedThreads - 1) /
+                                                                           (4 * kRedThreads)));
     std::string err;
-    int rc = ras_plan_create(P, err);
+    rc = ras_plan_create(P, err);
     if (rc) {
         g_create_error = err;
         nks_destroy(H);
         return rc;
     }
-    rc = P->sync_check("create");
-    if (!rc) rc = equilibrate(P);
-    if (!rc) {
-        cudaMemcpyAsync(P->Xprev, P->Xn, vb, cudaMemcpyDeviceToDevice, P->stream);
-        double parts[5] = {0, 0, 0, 0, 0};
-        rc = energy_mass(P, P->Xn, parts, nullptr);
-        P->E = P->Eprev = parts[4];
+
+    // per-instance slab: every buffer an instance owns, 256-byte aligned
+    const size_t vb = sizeof(double) * (size_t)P->ldv, fb = sizeof(double) * (size_t)g.N;
+    const int m = opts->gmres_restart;
+    const bool mixed = opts->precision == NKS_MIXED;
+    std::vector<SlabItem> items;
+    auto add = [&](void *pp, size_t bytes) { items.push_back({(void **)pp, bytes}); };
+    double **vecs[] = {&P->Xn, &P->Xprev, &P->X, &P->Xt, &P->F, &P->Ft, &P->S, &P->B, &P->W, &P->Z, &P->R,
+                       &P->T64, &P->Jec, &P->ec};
+    for (double **v : vecs) add(v, vb);
+    add(&P->V, vb * (mixed ? 1 : m + 1));
+    add(&P->part, 4 * fb);
+    add(&P->part_t, 4 * fb);
+    add(&P->mob, (size_t)g.dim * fb);
+    add(&P->tr0, fb);
+    add(&P->Gc, fb);
+    add(&P->sig, 6 * fb);
+    add(&P->partials, sizeof(double) * kRedBlocks * 64);
+    add(&P->dscal, sizeof(double) * 64);
+    add(&P->dflag, sizeof(int) * 4);
+    add(&P->tickets, sizeof(unsigned int) * 16);
+    add(&P->zsum, sizeof(double) * 8);
+    add(&P->gm, sizeof(double) * gmres_state_doubles(m));
+    add(&P->isc, sizeof(double) * I_NSC);
+    if (mixed) {
+        const size_t fvb = sizeof(float) * (size_t)P->ldvf;
+        add(&P->Vf, fvb * (m + 1));
+        add(&P->Wf, fvb);
+        add(&P->Zf, fvb);
+        add(&P->partf, sizeof(float) * 4 * (size_t)g.N);
+        add(&P->mobf, sizeof(float) * g.dim * (size_t)g.N);
+        add(&P->Jecf, sizeof(float) * 2 * (size_t)g.N);
+    }
+    ras_slab_items(P, items);
+    std::vector<size_t> off(items.size());
+    size_t total = 0;
+    for (size_t q = 0; q < items.size(); q++) {
+        total = (total + 255) & ~(size_t)255;
+        off[q] = total;
+        total += items[q].bytes;
+    }
+    P->stride = (long long)((total + 255) & ~(size_t)255);
+    P->slab = (char *)P->dalloc((size_t)P->stride * nb);
+    P->dmask = (int *)P->dalloc(sizeof(int) * kMasks * nb);
+    bool ok = P->slab && P->dmask &&
+              cudaMallocHost((void **)&P->hread, sizeof(double) * 64 * nb) == cudaSuccess &&
+              cudaMallocHost((void **)&P->hflags, sizeof(int) * 2 * nb) == cudaSuccess &&
+              cudaMallocHost((void **)&P->hmask_ring, sizeof(int) * kRing * nb) == cudaSuccess &&
+              cudaMallocHost((void **)&P->hsc_ring, sizeof(double) * kRing * nb * I_NSC) == cudaSuccess;
+    if (!ok) {
+        g_create_error = "out of device memory";
+        nks_destroy(H);
+        return NKS_ENOMEM;
+    }
+    for (size_t q = 0; q < items.size(); q++) *items[q].ptr = P->slab + off[q];
+    cudaMemsetAsync(P->slab, 0, (size_t)P->stride * nb, P->stream);
+    cudaMemsetAsync(P->dmask, 0, sizeof(int) * kMasks * nb, P->stream);
+    {
+        // e_c: 1 on the c plane of every instance
+        const std::vector<double> ones((size_t)g.N, 1.0);
+        for (int i = 0; i < nb; i++)
+            cudaMemcpyAsync(shift(P->ec, (long long)i * P->stride), ones.data(), fb, cudaMemcpyHostToDevice,
+                            P->stream);
+        rc = P->sync_check("create");
+    }
+    if (!rc && c) {
+        for (int i = 0; i < nb; i++) load_fields(P, i, c + (size_t)i * N, eta + (size_t)i * N);
+        rc = init_instances(P, std::vector<char>(nb, 1));
     }
     if (rc) {
         g_create_error = P->err.empty() ? "initial equilibrium failed" : P->err;
         nks_destroy(H);
         return rc;
     }
-    P->zeta = opts->zeta;
-    P->dt_prev = opts->dt_init;
     harvest_timers(P);
     *out = H;
+    return NKS_OK;
+}
+
+int nks_create_problem(const nks_grid *grid, const double *c, const double *eta, const nks_coeffs *coeffs,
+                       const nks_opts *opts, const nks_allocator *alloc, void *stream, nks_problem **out)
+{
+    if (!c || !eta) {
+        g_create_error = "null argument";
+        if (out) *out = nullptr;
+        return NKS_EINVAL;
+    }
+    return nks_create_batch(grid, 1, c, eta, coeffs, opts, alloc, stream, out);
+}
+
+int nks_batch_size(const nks_problem *H) { return H ? H->P.nb : 0; }
+
+static int check_slot(Problem *P, int slot, bool loaded)
+{
+    if (slot < 0 || slot >= P->nb) {
+        P->err = "slot out of range";
+        return NKS_EINVAL;
+    }
+    if (loaded && !P->is[slot].loaded) {
+        P->err = "slot holds no problem";
+        return NKS_EINVAL;
+    }
+    return NKS_OK;
+}
+
+int nks_batch_load(nks_problem *H, int slot, const double *c, const double *eta)
+{
+    Problem *P = &H->P;
+    P->err.clear();
+    int rc = check_slot(P, slot, false);
+    if (rc) return rc;
+    if (!c || !eta) {
+        P->err = "null argument";
+        return NKS_EINVAL;
+    }
+    if (!host_in_domain(P->N, c, eta)) {
+        P->err = "initial state outside the domain: c, c*eta and c*(4-3*eta) must lie in (0, 1)";
+        return NKS_EDOMAIN;
+    }
+    load_fields(P, slot, c, eta);
+    rc = init_instances(P, only(P->nb, slot));
+    if (rc) P->is[slot].loaded = false;
+    harvest_timers(P);
+    return rc;
+}
+
+int nks_batch_unload(nks_problem *H, int slot)
+{
+    Problem *P = &H->P;
+    int rc = check_slot(P, slot, false);
+    if (rc) return rc;
+    P->is[slot].loaded = false;
+    return NKS_OK;
+}
+
+int nks_batch_loaded(const nks_problem *H, int slot)
+{
+    const Problem *P = &H->P;
+    return slot >= 0 && slot < P->nb && P->is[slot].loaded ? 1 : 0;
+}
+
+int nks_batch_step(nks_problem *H, const int *active, const double *dt, nks_step_info *infos)
+{
+    Problem *P = &H->P;
+    P->err.clear();
+    std::vector<char> on(P->nb, 0);
+    for (int i = 0; i < P->nb; i++) on[i] = P->is[i].loaded && (!active || active[i]);
+    int rc = step_batch(P, on, dt, infos);
+    harvest_timers(P);
+    if (rc) return rc;
+    for (int i = 0; i < P->nb; i++)
+        if (on[i] && infos && infos[i].status != NKS_OK && P->err.empty()) P->err = P->is[i].err;
     return NKS_OK;
 }
 
@@ -483,153 +873,145 @@ int nks_step(nks_problem *H, double dt_arg, nks_step_info *info_out)
 {
     Problem *P = &H->P;
     P->err.clear();
-    nks_step_info info{};
-    const long long n = P->nvec;
-    double dt;
-    if (dt_arg > 0.0) {
-        dt = dt_arg;
-    } else if (P->nstep == 0 || P->opts.dt_mode == NKS_DT_FIXED) {
-        dt = P->opts.dt_init;
-    } else {
-        double Xd;
-        if (P->opts.dt_mode == NKS_DT_SOLUTION) {
-            P->count(launch_waxpy(n, P->Xn, -1.0, P->Xprev, P->W, P->stream));
-            P->count(launch_dot2(n, P->W, P->W, P->partials, P->stream));
-            P->count(launch_finalize(P->partials, kRedBlocks, 2, P->dscal, P->stream));
-            cudaMemcpyAsync(P->hscal, P->dscal + 1, sizeof(double), cudaMemcpyDeviceToHost, P->stream);
-            int rc = P->sync_check("dt");
-            if (rc) return rc;
-            Xd = sqrt(P->hscal[0]) / P->dt_prev;
-        } else {
-            Xd = fabs(P->E - P->Eprev) / P->dt_prev;
-        }
-        // Eq. sencondt
-        dt = std::max(P->opts.dt_min, P->opts.dt_max / sqrt(1.0 + P->zeta * Xd * Xd));
-    }
-    if (!P->opts.zeta_persist) P->zeta = P->opts.zeta;
-    int rc = NKS_OK;
-    int retries = 0;
-    for (;;) {
-        cudaMemcpyAsync(P->X, P->Xn, sizeof(double) * n, cudaMemcpyDeviceToDevice, P->stream);
-        prepare_level(P, P->Xn);
-        rc = newton(P, dt, 0, P->opts.newton_rtol, P->opts.newton_atol, P->opts.newton_maxit, &info);
-        if (rc == NKS_OK) break;
-        if (rc == NKS_ECUDA || dt_arg > 0.0 || retries >= P->opts.max_retries) break;
-        // Sec. 4: a diverged NKS solve restarts with dt / sqrt(2) and zeta doubled
-        dt /= sqrt(2.0);
-        P->zeta *= 2.0;
-        retries++;
-        P->stats.retries++;
-    }
-    info.dt = dt;
-    info.retries = retries;
-    if (rc != NKS_OK) {
-        info.status = rc;
-        info.t = P->t;
-        info.energy = P->E;
-        if (info_out) *info_out = info;
-        harvest_timers(P);
-        return rc;
-    }
-    std::swap(P->Xprev, P->Xn);  // X^{n-1} <- X^n
-    std::swap(P->Xn, P->X);      // X^n <- X^{n+1}
-    double parts[5], mass;
-    rc = energy_mass(P, P->Xn, parts, &mass);
+    int rc = check_slot(P, 0, true);
     if (rc) return rc;
-    P->Eprev = P->E;
-    P->E = parts[4];
-    P->t += dt;
-    P->dt_prev = dt;
-    P->nstep++;
-    P->stats.steps++;
-    info.t = P->t;
-    info.energy = P->E;
-    info.mass = mass;
-    info.status = NKS_OK;
-    if (info_out) *info_out = info;
+    std::vector<double> dts(P->nb, 0.0);
+    dts[0] = dt_arg;
+    std::vector<nks_step_info> infos(P->nb);
+    rc = step_batch(P, only(P->nb, 0), dts.data(), infos.data());
     harvest_timers(P);
+    if (rc) return rc;
+    if (info_out) *info_out = infos[0];
+    if (infos[0].status != NKS_OK) {
+        P->err = P->is[0].err;
+        return infos[0].status;
+    }
     return NKS_OK;
 }
 
-int nks_energy(const nks_problem *H, double *out)
-{
-    *out = H->P.E;
-    return NKS_OK;
-}
-
-int nks_mass(const nks_problem *H, double *out)
+int nks_batch_energy(const nks_problem *H, int slot, double *out)
 {
     Problem *P = const_cast<Problem *>(&H->P);
-    return energy_mass(P, P->Xn, nullptr, out);
+    int rc = check_slot(P, slot, true);
+    if (rc) return rc;
+    *out = P->is[slot].E;
+    return NKS_OK;
 }
+
+int nks_batch_mass(const nks_problem *H, int slot, double *out)
+{
+    Problem *P = const_cast<Problem *>(&H->P);
+    int rc = check_slot(P, slot, true);
+    if (rc) return rc;
+    std::vector<double> parts, mass;
+    rc = energy_mass(P, P->Xn, only(P->nb, slot), parts, mass);
+    if (!rc) *out = mass[slot];
+    return rc;
+}
+
+int nks_batch_get_fields(const nks_problem *H, int slot, double *c, double *eta, double *u)
+{
+    Problem *P = const_cast<Problem *>(&H->P);
+    int rc = check_slot(P, slot, true);
+    if (rc) return rc;
+    const size_t fb = sizeof(double) * (size_t)P->N;
+    const double *Xn = shift(P->Xn, (long long)slot * P->stride);
+    if (c) cudaMemcpyAsync(c, Xn, fb, cudaMemcpyDeviceToHost, P->stream);
+    if (eta) cudaMemcpyAsync(eta, Xn + P->N, fb, cudaMemcpyDeviceToHost, P->stream);
+    if (u && P->k.elastic) cudaMemcpyAsync(u, Xn + 2 * P->N, fb * P->g.dim, cudaMemcpyDeviceToHost, P->stream);
+    return P->sync_check("get_fields");
+}
+
+int nks_energy(const nks_problem *H, double *out) { return nks_batch_energy(H, 0, out); }
+
+int nks_mass(const nks_problem *H, double *out) { return nks_batch_mass(H, 0, out); }
 
 int nks_get_fields(const nks_problem *H, double *c, double *eta, double *u)
 {
-    Problem *P = const_cast<Problem *>(&H->P);
-    const size_t fb = sizeof(double) * (size_t)P->N;
-    if (c) cudaMemcpyAsync(c, P->Xn, fb, cudaMemcpyDeviceToHost, P->stream);
-    if (eta) cudaMemcpyAsync(eta, P->Xn + P->N, fb, cudaMemcpyDeviceToHost, P->stream);
-    if (u && P->k.elastic) cudaMemcpyAsync(u, P->Xn + 2 * P->N, fb * P->g.dim, cudaMemcpyDeviceToHost, P->stream);
-    return P->sync_check("get_fields");
+    return nks_batch_get_fields(H, 0, c, eta, u);
+}
+
+size_t nks_device_bytes(const nks_problem *H)
+{
+    const Problem *P = &H->P;
+    return (size_t)P->stride * P->nb;
 }
 
 struct StateHeader {
     char magic[8];
     long long nvec, nstep;
-    double t, dt_prev, zeta, E, Eprev;
+    double t, dt_prev, zeta, E, Eprev, cbar0;
 };
 
 size_t nks_state_size(const nks_problem *H) { return sizeof(StateHeader) + 2 * sizeof(double) * (size_t)H->P.nvec; }
 
-int nks_get_state(const nks_problem *H, void *buf, size_t bytes)
+int nks_batch_get_state(const nks_problem *H, int slot, void *buf, size_t bytes)
 {
     Problem *P = const_cast<Problem *>(&H->P);
-    if (bytes < nks_state_size(H)) {
+    int rc = check_slot(P, slot, true);
+    if (rc) return rc;
+    if (!buf || bytes < nks_state_size(H)) {
         P->err = "state buffer too small";
         return NKS_EINVAL;
     }
+    const IState &s = P->is[slot];
     StateHeader hd;
-    memcpy(hd.magic, "NKSSTAT1", 8);
+    memcpy(hd.magic, "NKSSTAT2", 8);
     hd.nvec = P->nvec;
-    hd.nstep = P->nstep;
-    hd.t = P->t;
-    hd.dt_prev = P->dt_prev;
-    hd.zeta = P->zeta;
-    hd.E = P->E;
-    hd.Eprev = P->Eprev;
+    hd.nstep = s.nstep;
+    hd.t = s.t;
+    hd.dt_prev = s.dt_prev;
+    hd.zeta = s.zeta;
+    hd.E = s.E;
+    hd.Eprev = s.Eprev;
+    hd.cbar0 = s.cbar0;
     memcpy(buf, &hd, sizeof(hd));
     char *b = (char *)buf + sizeof(hd);
     const size_t vb = sizeof(double) * (size_t)P->nvec;
-    cudaMemcpyAsync(b, P->Xn, vb, cudaMemcpyDeviceToHost, P->stream);
-    cudaMemcpyAsync(b + vb, P->Xprev, vb, cudaMemcpyDeviceToHost, P->stream);
+    const long long io = (long long)slot * P->stride;
+    cudaMemcpyAsync(b, shift(P->Xn, io), vb, cudaMemcpyDeviceToHost, P->stream);
+    cudaMemcpyAsync(b + vb, shift(P->Xprev, io), vb, cudaMemcpyDeviceToHost, P->stream);
     return P->sync_check("get_state");
 }
 
-int nks_set_state(nks_problem *H, const void *buf, size_t bytes)
+int nks_batch_set_state(nks_problem *H, int slot, const void *buf, size_t bytes)
 {
     Problem *P = &H->P;
+    int rc = check_slot(P, slot, false);
+    if (rc) return rc;
     StateHeader hd;
-    if (bytes < sizeof(hd)) {
+    if (!buf || bytes < sizeof(hd)) {
         P->err = "state buffer too small";
         return NKS_EINVAL;
     }
     memcpy(&hd, buf, sizeof(hd));
-    if (memcmp(hd.magic, "NKSSTAT1", 8) != 0 || hd.nvec != P->nvec || bytes < nks_state_size(H)) {
+    if (memcmp(hd.magic, "NKSSTAT2", 8) != 0 || hd.nvec != P->nvec || bytes < nks_state_size(H)) {
         P->err = "state buffer does not match this problem";
         return NKS_EINVAL;
     }
     const char *b = (const char *)buf + sizeof(hd);
     const size_t vb = sizeof(double) * (size_t)P->nvec;
-    cudaMemcpyAsync(P->Xn, b, vb, cudaMemcpyHostToDevice, P->stream);
-    cudaMemcpyAsync(P->Xprev, b + vb, vb, cudaMemcpyHostToDevice, P->stream);
-    P->nstep = hd.nstep;
-    P->t = hd.t;
-    P->dt_prev = hd.dt_prev;
-    P->zeta = hd.zeta;
-    P->E = hd.E;
-    P->Eprev = hd.Eprev;
+    const long long io = (long long)slot * P->stride;
+    cudaMemcpyAsync(shift(P->Xn, io), b, vb, cudaMemcpyHostToDevice, P->stream);
+    cudaMemcpyAsync(shift(P->Xprev, io), b + vb, vb, cudaMemcpyHostToDevice, P->stream);
+    IState &s = P->is[slot];
+    s = IState{};
+    s.nstep = hd.nstep;
+    s.t = hd.t;
+    s.dt_prev = hd.dt_prev;
+    s.zeta = hd.zeta;
+    s.E = hd.E;
+    s.Eprev = hd.Eprev;
+    s.cbar0 = hd.cbar0;
+    s.lam = 1.0;
+    s.loaded = true;
+    P->upload_isc();
     return P->sync_check("set_state");
 }
+
+int nks_get_state(const nks_problem *H, void *buf, size_t bytes) { return nks_batch_get_state(H, 0, buf, bytes); }
+
+int nks_set_state(nks_problem *H, const void *buf, size_t bytes) { return nks_batch_set_state(H, 0, buf, bytes); }
 
 int nks_get_stats(const nks_problem *H, nks_stats *out)
 {
@@ -657,7 +1039,10 @@ void nks_destroy(nks_problem *H)
     destroy_timers(P);
     ras_plan_destroy(P);
     P->dfree_all();
-    if (P->hscal) cudaFreeHost(P->hscal);
+    if (P->hread) cudaFreeHost(P->hread);
+    if (P->hflags) cudaFreeHost(P->hflags);
+    if (P->hmask_ring) cudaFreeHost(P->hmask_ring);
+    if (P->hsc_ring) cudaFreeHost(P->hsc_ring);
     if (P->own_stream && P->stream) cudaStreamDestroy(P->stream);
     delete H;
 }
@@ -669,30 +1054,31 @@ const char *nks_last_error(const nks_problem *H)
 }
 
 // ---------------------------------------------------------------------------
-// operator-level entry points
+// operator-level entry points (instance 0)
 // ---------------------------------------------------------------------------
 
 static int op_setup(Problem *P, const double *X1, const double *X0, double dt, int mode)
 {
+    P->err.clear();
     const size_t vb = sizeof(double) * (size_t)P->nvec;
     cudaMemcpyAsync(P->X, X1, vb, cudaMemcpyHostToDevice, P->stream);
     cudaMemcpyAsync(P->Xt, X0, vb, cudaMemcpyHostToDevice, P->stream);
-    P->cur_dt = dt;
     P->cur_mode = mode;
+    P->is[0].dt = dt;
+    P->upload_isc();
+    const std::vector<char> on = only(P->nb, 0);
+    const Bat bt = P->set_mask(M_X2, on);
     P->tick(8);
-    P->count(launch_mobility(P->g, P->k, P->Xt, P->mob, P->stream));
-    if (P->k.elastic) P->count(launch_trace0(P->g, P->k, P->Xt, P->tr0, P->stream));
+    P->count(launch_mobility(P->g, P->k, P->Xt, P->mob, P->stream, bt));
+    if (P->k.elastic) P->count(launch_trace0(P->g, P->k, P->isc, P->Xt, P->tr0, P->stream, bt));
     P->tock(8);
-    double fn;
-    bool ok;
-    return residual(P, dt, mode, P->X, P->Xt, P->F, P->part, &fn, &ok);
+    std::vector<double> fn;
+    std::vector<char> dok;
+    return residual(P, mode, P->X, P->Xt, P->F, P->part, on, fn, dok);
 }
 
 static int op_finish(Problem *P, int rc)
 {
-    // the operator calls reuse the step's work buffers: level-n data must be rebuilt
-    prepare_level(P, P->Xn);
-    P->factored = false;
     int r2 = P->sync_check("operator");
     harvest_timers(P);
     return rc ? rc : r2;
@@ -716,16 +1102,19 @@ int nks_apply_jacobian(nks_problem *H, const double *X1, const double *X0, doubl
     int rc = op_setup(P, X1, X0, dt, mode);
     if (!rc) {
         const size_t vb = sizeof(double) * (size_t)P->nvec;
+        const Bat bt = P->set_mask(M_X2, only(P->nb, 0));
         cudaMemcpyAsync(P->B, v, vb, cudaMemcpyHostToDevice, P->stream);
         P->tick(1);
         if (P->opts.precision == NKS_MIXED) {
             // as the Arnoldi step applies it: FP32 vectors, coefficients and arithmetic
-            refresh_f32_coefficients(P);
-            P->count(launch_convert(P->nvec, P->B, P->Zf, P->stream));
-            P->count(launch_jv32(P->g, P->k, dt, mode, P->partf, P->mobf, P->Zf, P->Wf, P->stream, nullptr, nullptr));
-            P->count(launch_convert(P->nvec, P->Wf, P->W, P->stream));
+            refresh_f32_coefficients(P, bt);
+            P->count(launch_convert(P->nvec, P->B, P->Zf, P->stream, bt));
+            P->count(launch_jv32(P->g, P->k, P->isc, mode, P->partf, P->mobf, P->Zf, P->Wf, P->stream, bt, nullptr,
+                                 nullptr));
+            P->count(launch_convert(P->nvec, P->Wf, P->W, P->stream, bt));
         } else {
-            P->count(launch_jv(P->g, P->k, dt, mode, P->part, P->mob, P->B, P->Gc, P->sig, P->W, P->stream));
+            P->count(launch_jv64(P->g, P->k, P->isc, mode, P->part, P->mob, P->B, P->Gc, P->sig, P->W, P->stream,
+                                 bt));
         }
         P->tock(1);
         cudaMemcpyAsync(Jv, P->W, vb, cudaMemcpyDeviceToHost, P->stream);
@@ -738,17 +1127,24 @@ int nks_apply_preconditioner(nks_problem *H, const double *X1, const double *X0,
 {
     Problem *P = &H->P;
     int rc = op_setup(P, X1, X0, dt, 0);
-    if (!rc) rc = ras_factor(P, 0);
+    const std::vector<char> on = only(P->nb, 0);
+    const Bat bt = P->set_mask(M_X2, on);
+    P->is[0].nst = 1;
+    if (!rc) rc = ras_factor(P, 0, bt, on);
+    if (!rc && P->is[0].nst < 0) {
+        P->err = P->is[0].err;
+        rc = -P->is[0].nst;
+    }
     if (!rc) {
         const size_t vb = sizeof(double) * (size_t)P->nvec;
         cudaMemcpyAsync(P->B, r, vb, cudaMemcpyHostToDevice, P->stream);
         if (P->opts.precision == NKS_MIXED) {
             // as the solver applies it: FP32 vectors and factors
-            P->count(launch_convert(P->nvec, P->B, P->Wf, P->stream));
-            ras_apply_projected<float>(P, P->Wf, P->Zf);
-            P->count(launch_convert(P->nvec, P->Zf, P->Z, P->stream));
+            P->count(launch_convert(P->nvec, P->B, P->Wf, P->stream, bt));
+            ras_apply_projected<float>(P, P->Wf, P->Zf, bt);
+            P->count(launch_convert(P->nvec, P->Zf, P->Z, P->stream, bt));
         } else {
-            ras_apply(P, P->B, P->Z);
+            ras_apply(P, P->B, P->Z, bt);
         }
         cudaMemcpyAsync(z, P->Z, vb, cudaMemcpyDeviceToHost, P->stream);
         rc = P->sync_check("apply_preconditioner");
@@ -761,12 +1157,23 @@ int nks_linear_solve(nks_problem *H, const double *X1, const double *X0, double 
 {
     Problem *P = &H->P;
     int rc = op_setup(P, X1, X0, dt, mode);
-    if (!rc) rc = ras_factor(P, mode);
+    const std::vector<char> on = only(P->nb, 0);
+    const Bat bt = P->set_mask(M_X2, on);
+    P->is[0].nst = 1;
+    if (!rc) rc = ras_factor(P, mode, bt, on);
+    if (!rc && P->is[0].nst < 0) {
+        P->err = P->is[0].err;
+        rc = -P->is[0].nst;
+    }
     if (!rc) {
         const size_t vb = sizeof(double) * (size_t)P->nvec;
         cudaMemcpyAsync(P->B, b, vb, cudaMemcpyHostToDevice, P->stream);
-        rc = gmres_solve(P, mode, P->B, P->S, tol, its, res);
+        for (int i = 0; i < P->nb; i++) P->is[i].gin = i == 0;
+        P->is[0].gtol = tol;
+        rc = gmres_solve(P, mode, P->B, P->S);
         if (!rc) {
+            if (its) *its = P->is[0].gits;
+            if (res) *res = P->is[0].res;
             cudaMemcpyAsync(x, P->S, vb, cudaMemcpyDeviceToHost, P->stream);
             rc = P->sync_check("linear_solve");
         }
@@ -778,7 +1185,13 @@ int nks_eval_energy(nks_problem *H, const double *X, double *parts, double *mass
 {
     Problem *P = &H->P;
     cudaMemcpyAsync(P->W, X, sizeof(double) * (size_t)P->nvec, cudaMemcpyHostToDevice, P->stream);
-    int rc = energy_mass(P, P->W, parts, mass);
+    std::vector<double> pv, mv;
+    int rc = energy_mass(P, P->W, only(P->nb, 0), pv, mv);
+    if (!rc) {
+        if (parts)
+            for (int q = 0; q < 5; q++) parts[q] = pv[q];
+        if (mass) *mass = mv[0];
+    }
     harvest_timers(P);
     return rc;
 }

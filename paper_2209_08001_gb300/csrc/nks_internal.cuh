@@ -44,6 +44,33 @@ struct DCoef {
     int nf;
 };
 
+// Batches.  A problem holds nb instances of the same grid, coefficients and
+// options (a single problem is a batch of one).  Every per-instance buffer is
+// carved from the instance's slab at the same offset, so instance b's copy of
+// any per-instance buffer lies b * stride bytes after instance 0's.  One launch
+// runs all instances of a phase: the instance is blockIdx.y (or the dimension
+// a kernel states), and an instance whose mask entry is 0 is skipped.
+struct Bat {
+    long long stride = 0;        // bytes between the slabs of consecutive instances
+    const int *mask = nullptr;   // [nb] (device): run instance b when mask[b] != 0; nullptr: all
+    int nb = 1;
+};
+
+template <class T>
+__host__ __device__ __forceinline__ T *shift(T *p, long long off)
+{
+    return p ? (T *)((const char *)p + off) : p;
+}
+
+__device__ __forceinline__ bool inst_off(const Bat &bt, int b, long long &off)
+{
+    off = (long long)b * bt.stride;
+    return !bt.mask || bt.mask[b] != 0;
+}
+
+// per-instance device scalars (isc, 8 doubles in each slab)
+enum { I_DT = 0, I_CBAR0 = 1, I_LAM = 2, I_NSC = 8 };
+
 // ---------------------------------------------------------------------------
 // index helpers
 // ---------------------------------------------------------------------------
@@ -135,56 +162,70 @@ __device__ inline void grid_finalize(const double *partials, int K, double *out,
 // stencil / reduction kernels (nks_stencil.cu)
 // ---------------------------------------------------------------------------
 
-int launch_mobility(const DGrid &g, const DCoef &k, const double *c0, double *mob, cudaStream_t st);
-int launch_trace0(const DGrid &g, const DCoef &k, const double *X0, double *tr0, cudaStream_t st);
-int launch_residual(const DGrid &g, const DCoef &k, double dt, int mode, const double *X1, const double *X0,
-                     const double *tr0, const double *mob, double *Gc, double *sig, double *part, double *F,
-                     int *flag, double *partials, cudaStream_t st);
-int launch_jv(const DGrid &g, const DCoef &k, double dt, int mode, const double *part, const double *mob,
-               const double *v, double *dG, double *sig, double *Jv, cudaStream_t st);
+// isc: the instance's scalars (I_DT, I_CBAR0, I_LAM); rb: reduction blocks per instance
+int launch_mobility(const DGrid &g, const DCoef &k, const double *c0, double *mob, cudaStream_t st, const Bat &bt);
+int launch_trace0(const DGrid &g, const DCoef &k, const double *isc, const double *X0, double *tr0, cudaStream_t st,
+                  const Bat &bt);
+int launch_residual(const DGrid &g, const DCoef &k, const double *isc, int mode, const double *X1, const double *X0,
+                    const double *tr0, const double *mob, double *Gc, double *sig, double *part, double *F, int *flag,
+                    double *partials, int rb, cudaStream_t st, const Bat &bt);
 // J v, or J P v with Jec = J e_c and zsum[0] = sum of v_c (P: mean of v_c removed).
 // FP64: two passes through the dG / sig temporaries (N and d(d+1)/2 N doubles).
-int launch_jv64(const DGrid &g, const DCoef &k, double dt, int mode, const double *part, const double *mob,
-                const double *v, double *dG, double *sig, double *Jv, cudaStream_t st, const double *Jec = nullptr,
-                const double *zsum = nullptr);
+int launch_jv64(const DGrid &g, const DCoef &k, const double *isc, int mode, const double *part, const double *mob,
+                const double *v, double *dG, double *sig, double *Jv, cudaStream_t st, const Bat &bt,
+                const double *Jec = nullptr, const double *zsum = nullptr);
 // FP32 arithmetic and storage (FP32 copies of part, mob and the c/eta planes of J e_c)
-int launch_jv32(const DGrid &g, const DCoef &k, double dt, int mode, const float *part, const float *mob,
-                const float *v, float *Jv, cudaStream_t st, const float *Jec, const double *zsum);
-int launch_energy(const DGrid &g, const DCoef &k, const double *X, double *partials, cudaStream_t st);
-int launch_finalize(const double *partials, int nblocks, int K, double *out, cudaStream_t st);
+int launch_jv32(const DGrid &g, const DCoef &k, const double *isc, int mode, const float *part, const float *mob,
+                const float *v, float *Jv, cudaStream_t st, const Bat &bt, const float *Jec, const double *zsum);
+int launch_energy(const DGrid &g, const DCoef &k, const double *isc, const double *X, double *partials, int rb,
+                  cudaStream_t st, const Bat &bt);
+int launch_finalize(const double *partials, int nblocks, int K, double *out, cudaStream_t st, const Bat &bt);
 
 // ---------------------------------------------------------------------------
-// vector kernels (nks_krylov.cu)
+// vector kernels (nks_krylov.cu); n entries per instance
 // ---------------------------------------------------------------------------
 
-int launch_axpby(long long n, double a, const double *x, double b, double *y, cudaStream_t st);   // y = a x + b y
-int launch_waxpy(long long n, const double *x, double a, const double *y, double *w, cudaStream_t st); // w = x + a y
-int launch_scale_dev(long long n, const double *src, const double *inv_norm, double *dst, cudaStream_t st);
-int launch_dot2(long long n, const double *x, const double *y, double *partials, cudaStream_t st); // x.y, y.y
-int launch_convert(long long n, const double *a, float *b, cudaStream_t st);
-int launch_convert(long long n, const float *a, double *b, cudaStream_t st);
+int launch_axpby(long long n, double a, const double *x, double b, double *y, cudaStream_t st, const Bat &bt);
+int launch_waxpy(long long n, const double *x, double a, const double *y, double *w, cudaStream_t st,
+                 const Bat &bt);  // w = x + a y
+// w = x + lam y with lam = isc[I_LAM] of the instance
+int launch_waxpy_lam(long long n, const double *x, const double *isc, const double *y, double *w, cudaStream_t st,
+                     const Bat &bt);
+int launch_copy(long long n, const double *x, double *y, cudaStream_t st, const Bat &bt);
+int launch_dot2(long long n, const double *x, const double *y, double *partials, int rb, cudaStream_t st,
+                const Bat &bt);  // x.y, y.y
+int launch_convert(long long n, const double *a, float *b, cudaStream_t st, const Bat &bt);
+int launch_convert(long long n, const float *a, double *b, cudaStream_t st, const Bat &bt);
 
-// GMRES(m) with right preconditioning; see nks_krylov.cu.
+// GMRES(m) with right preconditioning; see nks_krylov.cu.  Solves J x = b for
+// every instance with is[i].gin set, to is[i].gtol; leaves is[i].gits, is[i].res.
 struct Problem;
-int gmres_solve(Problem *P, int mode, const double *b, double *x, double tol, int *its, double *res);
+int gmres_solve(Problem *P, int mode, const double *b, double *x);
 
 // ---------------------------------------------------------------------------
 // restricted additive Schwarz (nks_ras.cu)
 // ---------------------------------------------------------------------------
 
 struct RasPlan;
-int ras_plan_create(Problem *P, std::string &err);
+int ras_plan_create(Problem *P, std::string &err);     // shared tables; per-instance sizes
+struct SlabItem {
+    void **ptr;
+    size_t bytes;
+};
+void ras_slab_items(Problem *P, std::vector<SlabItem> &items);  // per-instance Schwarz buffers
 void ras_plan_destroy(Problem *P);
-int ras_factor(Problem *P, int mode);                              // assemble J restricted + ILU(0)
-void ras_apply(Problem *P, const double *r, double *z);           // z = P RAS^-1 r
-// z = RAS^-1 r without P (FP64 or FP32 vectors); the sum of z_c goes to P->zsum[0]
+// assemble J restricted + ILU(0) for the instances of bt (on: the same set on the host);
+// a zero pivot marks the instance failed in is[]
+int ras_factor(Problem *P, int mode, const Bat &bt, const std::vector<char> &on);
+void ras_apply(Problem *P, const double *r, double *z, const Bat &bt);  // z = P RAS^-1 r
+// z = RAS^-1 r without P (FP64 or FP32 vectors); the sum of z_c goes to zsum[0]
 template <typename TV>
-void ras_apply_t(Problem *P, const TV *r, TV *z);
+void ras_apply_t(Problem *P, const TV *r, TV *z, const Bat &bt);
 template <typename TV>
-void ras_apply_projected(Problem *P, const TV *r, TV *z);
+void ras_apply_projected(Problem *P, const TV *r, TV *z, const Bat &bt);
 // mixed precision: FP32 copies of part and mob for the FP32 Jacobian action
-void refresh_f32_coefficients(Problem *P);         // with P
-void project(Problem *P, double *z);
+void refresh_f32_coefficients(Problem *P, const Bat &bt);
+void project(Problem *P, double *z, const Bat &bt);   // with P
 void ras_work(const Problem *P, double *bytes, double *flops);  // algorithmic work of one sweep
 
 // ---------------------------------------------------------------------------
@@ -200,6 +241,30 @@ struct TimerPool {
     std::vector<Timer> ev;
     size_t used = 0;
 };
+
+// host state of one instance
+struct IState {
+    bool loaded = false;                        // holds a state (serving slots may be empty)
+    // time stepping
+    double t = 0.0, dt_prev = 0.0, zeta = 0.0, E = 0.0, Eprev = 0.0;
+    long long nstep = 0;
+    double cbar0 = 0.0;
+    double dt = 0.0;                            // dt of the system being solved
+    // Newton
+    int nst = 0;                                // 1 running, 0 converged, < 0: -status
+    double fn0 = 0.0, fn = 0.0, tol = 0.0, lam = 1.0, ftn = 0.0;
+    int newton_its = 0, gmres_its = 0;
+    bool searching = false, accepted = false, dom_ok = true;
+    std::string err;
+    // GMRES
+    double beta = 0.0, gtol = 0.0, res = 0.0;
+    int gits = 0;
+    bool gin = false, cyc = false;
+};
+
+// device masks: Newton running set, GMRES (solving, in the current cycle, still
+// iterating), line search, accepted, spare
+enum { M_RUN = 0, M_GIN, M_CYC, M_ACT, M_LS, M_ACC, M_X1, M_X2, kMasks };
 
 struct Problem {
     int device = 0;
@@ -217,6 +282,19 @@ struct Problem {
     int nf = 2;
     long long N = 0, nvec = 0;
     long long ldv = 0;                          // stride of the Krylov basis: nvec rounded up to even
+    int rb = kRedBlocks;                        // reduction blocks per instance (from the vector length)
+
+    // batch: nb instances; per-instance buffers in slabs of stride bytes
+    int nb = 1;
+    long long stride = 0;
+    char *slab = nullptr;
+    int *dmask = nullptr;                       // kMasks x nb device masks
+    int *hmask_ring = nullptr;                  // pinned staging ring for mask and scalar uploads
+    double *hsc_ring = nullptr;
+    int ring_pos = 0;
+    double *isc = nullptr;                      // per-instance device scalars (I_DT, ...)
+    double *hread = nullptr;                    // pinned: per-instance scalars read back (nb x 64)
+    int *hflags = nullptr;                      // pinned: both flag words of every instance (nb x 2)
 
     // state
     double *Xn = nullptr, *Xprev = nullptr, *X = nullptr, *Xt = nullptr;
@@ -227,7 +305,6 @@ struct Problem {
     double *Gc = nullptr, *sig = nullptr;       // residual / Jv temporaries
     double *partials = nullptr;                 // kRedBlocks * 64
     double *dscal = nullptr;                    // small device scalars
-    double *hscal = nullptr;                    // pinned host mirror
     int *dflag = nullptr;
     double *zsum = nullptr;                     // sum of z_c of the last Schwarz sweep (device)
     double *Jec = nullptr;                      // J e_c at the current iterate (c and eta planes used)
@@ -245,15 +322,11 @@ struct Problem {
     double *gm = nullptr;                       // device GMRES small state
 
     RasPlan *ras = nullptr;
-    bool factored = false;
 
-    double cur_dt = 1.0;                        // dt of the system being solved
     int cur_mode = 0;                           // 0 full system, 1 displacement only
 
-    // time stepping
-    double t = 0.0, dt_prev = 0.0, zeta = 0.0, E = 0.0, Eprev = 0.0;
-    long long nstep = 0;
-    double cbar0 = 0.0;
+    // per-instance host state
+    std::vector<IState> is;
 
     nks_stats stats{};
     TimerPool timers[NKS_NCLASS];
@@ -261,6 +334,13 @@ struct Problem {
 
     void *dalloc(size_t bytes);
     void dfree_all();
+    // batch helpers (nks_api.cu)
+    Bat all() const { return Bat{stride, nullptr, nb}; }
+    Bat masked(int m) const { return Bat{stride, dmask + (size_t)m * nb, nb}; }
+    Bat set_mask(int m, const std::vector<char> &on);   // upload mask m, return its Bat
+    void upload_isc();                                  // isc of every instance from is[]
+    int read_scalars(const double *dev0, int count, const char *where);  // -> hread[b * 64 + i], hflags
+    int read_flags(const char *where);                                   // -> hflags[2 b + q]
     void count(int n) { stats.kernel_launches += n; }  // kernels launched on this problem
     void tick(int cls);                         // count a launch of class cls (and start a timer)
     void tock(int cls);                         // stop its timer

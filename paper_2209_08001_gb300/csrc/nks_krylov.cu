@@ -52,40 +52,75 @@ struct GmLayout {
     }
 };
 // scal slots
-enum { S_WN0 = 0, S_WN = 1, S_RES = 2, S_INV = 3, S_FLAG = 4, S_BETA = 5 };
+enum { S_WN0 = 0, S_WN = 1, S_RES = 2, S_INV = 3, S_FLAG = 4, S_BETA = 5, S_KDIM = 6 };
 
-__global__ void k_axpby(long long n, double a, const double *__restrict__ x, double b, double *__restrict__ y)
+// Element-wise kernels run instance blockIdx.y of the batch.
+#define NKS_INST(...)                         \
+    long long io;                             \
+    if (!inst_off(bt, blockIdx.y, io)) return; \
+    __VA_ARGS__
+
+__global__ void k_axpby(Bat bt, long long n, double a, const double *__restrict__ x, double b, double *__restrict__ y)
 {
+    NKS_INST(x = shift(x, io); y = shift(y, io);)
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i < n) y[i] = a * x[i] + b * y[i];
 }
 
-__global__ void k_waxpy(long long n, const double *__restrict__ x, double a, const double *__restrict__ y,
+__global__ void k_waxpy(Bat bt, long long n, const double *__restrict__ x, double a, const double *__restrict__ y,
                         double *__restrict__ w)
 {
+    NKS_INST(x = shift(x, io); y = shift(y, io); w = shift(w, io);)
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i < n) w[i] = x[i] + a * y[i];
 }
 
+// w = x + lam y, lam = isc[I_LAM] of the instance
+__global__ void k_waxpy_lam(Bat bt, long long n, const double *__restrict__ x, const double *__restrict__ isc,
+                            const double *__restrict__ y, double *__restrict__ w)
+{
+    NKS_INST(x = shift(x, io); y = shift(y, io); w = shift(w, io); isc = shift(isc, io);)
+    const double a = isc[I_LAM];
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) w[i] = x[i] + a * y[i];
+}
+
+__global__ void k_copy(Bat bt, long long n, const double *__restrict__ x, double *__restrict__ y)
+{
+    NKS_INST(x = shift(x, io); y = shift(y, io);)
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) y[i] = x[i];
+}
+
+__global__ void k_zero(Bat bt, long long n, double *__restrict__ y)
+{
+    NKS_INST(y = shift(y, io);)
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) y[i] = 0.0;
+}
+
 template <typename TS, typename TD>
-__global__ void k_scale_dev(long long n, const TS *__restrict__ src, const double *__restrict__ s,
+__global__ void k_scale_dev(Bat bt, long long n, const TS *__restrict__ src, const double *__restrict__ s,
                             TD *__restrict__ dst)
 {
+    NKS_INST(src = shift(src, io); s = shift(s, io); dst = shift(dst, io);)
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i < n) dst[i] = (TD)((double)src[i] * (*s));
 }
 
 // y += x (x stored as TV)
 template <typename TV>
-__global__ void k_add(long long n, const TV *__restrict__ x, double *__restrict__ y)
+__global__ void k_add(Bat bt, long long n, const TV *__restrict__ x, double *__restrict__ y)
 {
+    NKS_INST(x = shift(x, io); y = shift(y, io);)
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i < n) y[i] += (double)x[i];
 }
 
-__global__ void __launch_bounds__(kRedThreads) k_dot2(long long n, const double *__restrict__ x,
+__global__ void __launch_bounds__(kRedThreads) k_dot2(Bat bt, long long n, const double *__restrict__ x,
                                                       const double *__restrict__ y, double *__restrict__ partials)
 {
+    NKS_INST(x = shift(x, io); y = shift(y, io); partials = shift(partials, io);)
     double acc[2] = {0.0, 0.0};
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const double a = x[i], b = y[i];
@@ -137,10 +172,13 @@ __device__ __forceinline__ typename Vec<TV>::type pack(const TV (&a)[Vec<TV>::W]
 // pack and entries past the vector length are zero.  gate (optional): skip
 // unless gate[0] != 0.
 template <int NV, typename TV>
-__global__ void __launch_bounds__(kRedThreads, 4) k_multidot(long long nq, const TV *__restrict__ V, long long ldv,
-                                                             const TV *__restrict__ w, double *__restrict__ partials,
-                                                             const double *gate, double *out, unsigned int *ticket)
+__global__ void __launch_bounds__(kRedThreads, 4) k_multidot(Bat bt, long long nq, const TV *__restrict__ V,
+                                                             long long ldv, const TV *__restrict__ w,
+                                                             double *__restrict__ partials, const double *gate,
+                                                             double *out, unsigned int *ticket)
 {
+    NKS_INST(V = shift(V, io); w = shift(w, io); partials = shift(partials, io); gate = shift(gate, io);
+             out = shift(out, io); ticket = shift(ticket, io);)
     if (gate && gate[0] == 0.0) return;
     using VT = typename Vec<TV>::type;
     constexpr int WD = Vec<TV>::W;
@@ -169,11 +207,13 @@ __global__ void __launch_bounds__(kRedThreads, 4) k_multidot(long long nq, const
 
 // CGS pass 2: w -= sum_i h_i v_i, accumulating ||w||^2.
 template <int NV, typename TV>
-__global__ void __launch_bounds__(kRedThreads, 4) k_cgs_update(long long nq, const TV *__restrict__ V, long long ldv,
-                                                               const double *__restrict__ h, TV *__restrict__ w,
-                                                               double *__restrict__ partials, const double *gate,
-                                                               double *out, unsigned int *ticket)
+__global__ void __launch_bounds__(kRedThreads, 4) k_cgs_update(Bat bt, long long nq, const TV *__restrict__ V,
+                                                               long long ldv, const double *__restrict__ h,
+                                                               TV *__restrict__ w, double *__restrict__ partials,
+                                                               const double *gate, double *out, unsigned int *ticket)
 {
+    NKS_INST(V = shift(V, io); h = shift(h, io); w = shift(w, io); partials = shift(partials, io);
+             gate = shift(gate, io); out = shift(out, io); ticket = shift(ticket, io);)
     if (gate && gate[0] == 0.0) return;
     using VT = typename Vec<TV>::type;
     constexpr int WD = Vec<TV>::W;
@@ -201,11 +241,11 @@ __global__ void __launch_bounds__(kRedThreads, 4) k_cgs_update(long long nq, con
 }
 
 template <typename TV>
-using MultidotFn = void (*)(long long, const TV *, long long, const TV *, double *, const double *, double *,
+using MultidotFn = void (*)(Bat, long long, const TV *, long long, const TV *, double *, const double *, double *,
                             unsigned int *);
 template <typename TV>
-using UpdateFn = void (*)(long long, const TV *, long long, const double *, TV *, double *, const double *, double *,
-                          unsigned int *);
+using UpdateFn = void (*)(Bat, long long, const TV *, long long, const double *, TV *, double *, const double *,
+                          double *, unsigned int *);
 
 template <typename TV, int... I>
 constexpr auto multidot_table(std::integer_sequence<int, I...>)
@@ -226,30 +266,39 @@ const auto g_update32 = update_table<float>(std::make_integer_sequence<int, kMax
 // h_i = v_i . w (i < nv) and w . w into out[0..nv]; ldv a multiple of the 16-byte pack
 template <typename TV>
 void launch_multidot(int nv, long long ldv, const TV *V, const TV *w, double *partials, const double *gate,
-                     double *out, unsigned int *ticket, cudaStream_t st)
+                     double *out, unsigned int *ticket, int rb, cudaStream_t st, const Bat &bt)
 {
     constexpr int WD = Vec<TV>::W;
+    const dim3 grd(rb, bt.nb);
     if constexpr (sizeof(TV) == 8)
-        g_multidot64[nv - 1]<<<kRedBlocks, kRedThreads, 0, st>>>(ldv / WD, V, ldv, w, partials, gate, out, ticket);
+        g_multidot64[nv - 1]<<<grd, kRedThreads, 0, st>>>(bt, ldv / WD, V, ldv, w, partials, gate, out, ticket);
     else
-        g_multidot32[nv - 1]<<<kRedBlocks, kRedThreads, 0, st>>>(ldv / WD, V, ldv, w, partials, gate, out, ticket);
+        g_multidot32[nv - 1]<<<grd, kRedThreads, 0, st>>>(bt, ldv / WD, V, ldv, w, partials, gate, out, ticket);
 }
 
 // w -= V h, ||w||^2 into out[0]
 template <typename TV>
 void launch_update(int nv, long long ldv, const TV *V, const double *h, TV *w, double *partials, const double *gate,
-                   double *out, unsigned int *ticket, cudaStream_t st)
+                   double *out, unsigned int *ticket, int rb, cudaStream_t st, const Bat &bt)
 {
     constexpr int WD = Vec<TV>::W;
+    const dim3 grd(rb, bt.nb);
     if constexpr (sizeof(TV) == 8)
-        g_update64[nv - 1]<<<kRedBlocks, kRedThreads, 0, st>>>(ldv / WD, V, ldv, h, w, partials, gate, out, ticket);
+        g_update64[nv - 1]<<<grd, kRedThreads, 0, st>>>(bt, ldv / WD, V, ldv, h, w, partials, gate, out, ticket);
     else
-        g_update32[nv - 1]<<<kRedBlocks, kRedThreads, 0, st>>>(ldv / WD, V, ldv, h, w, partials, gate, out, ticket);
+        g_update32[nv - 1]<<<grd, kRedThreads, 0, st>>>(bt, ldv / WD, V, ldv, h, w, partials, gate, out, ticket);
 }
 
+// Small GMRES kernels: one thread per instance, instance = blockIdx.x.
+#define NKS_GM_INST()                          \
+    long long io;                              \
+    if (!inst_off(bt, blockIdx.x, io)) return; \
+    gm = shift(gm, io);
+
 // after pass 2: remember ||w||^2 before orthogonalisation, decide on a second pass
-__global__ void k_cgs_decide(double *gm, GmLayout L, int j)
+__global__ void k_cgs_decide(Bat bt, double *gm, GmLayout L, int j)
 {
+    NKS_GM_INST()
     double *sc = gm + L.scal;
     sc[S_WN0] = gm[L.hcol + j + 1];  // w . w from pass 1
     const double wn = sqrt(sc[S_WN]), wn0 = sqrt(sc[S_WN0]);
@@ -257,15 +306,17 @@ __global__ void k_cgs_decide(double *gm, GmLayout L, int j)
 }
 
 // second pass accumulated into the projection coefficients
-__global__ void k_cgs_accum(double *gm, GmLayout L, int j)
+__global__ void k_cgs_accum(Bat bt, double *gm, GmLayout L, int j)
 {
+    NKS_GM_INST()
     if (gm[L.scal + S_FLAG] == 0.0) return;
     for (int i = 0; i <= j; i++) gm[L.hcol + i] += gm[L.h2 + i];
 }
 
 // Arnoldi column j: Hessenberg entries, Givens rotations, residual estimate
-__global__ void k_arnoldi(double *gm, GmLayout L, int j)
+__global__ void k_arnoldi(Bat bt, double *gm, GmLayout L, int j)
 {
+    NKS_GM_INST()
     const int m = L.m;
     double *H = gm + L.H, *cs = gm + L.cs, *sn = gm + L.sn, *g = gm + L.g, *sc = gm + L.scal;
     const double wn = sqrt(sc[S_WN]);
@@ -286,18 +337,25 @@ __global__ void k_arnoldi(double *gm, GmLayout L, int j)
     g[j] = cs[j] * g[j];
     sc[S_RES] = fabs(g[j + 1]);
     sc[S_INV] = (wn != 0.0) ? 1.0 / wn : 0.0;
+    sc[S_KDIM] = j + 1;
 }
 
-__global__ void k_gm_start(double *gm, GmLayout L, double beta)
+// beta = sqrt(beta2[0]): the norm of the starting residual
+__global__ void k_gm_start(Bat bt, double *gm, GmLayout L, const double *beta2)
 {
+    NKS_GM_INST()
+    const double beta = sqrt(shift(beta2, io)[0]);
     for (int i = 0; i <= L.m; i++) gm[L.g + i] = 0.0;
+    gm[L.scal + S_KDIM] = 0.0;
     gm[L.g] = beta;
     gm[L.scal + S_INV] = 1.0 / beta;
 }
 
 // upper-triangular solve H y = g for the first kdim columns
-__global__ void k_hsolve(double *gm, GmLayout L, int kdim)
+__global__ void k_hsolve(Bat bt, double *gm, GmLayout L)
 {
+    NKS_GM_INST()
+    const int kdim = (int)gm[L.scal + S_KDIM];
     const int m = L.m;
     double *H = gm + L.H, *g = gm + L.g, *y = gm + L.y;
     for (int i = kdim - 1; i >= 0; i--) {
@@ -308,10 +366,14 @@ __global__ void k_hsolve(double *gm, GmLayout L, int kdim)
 }
 
 // out = sum_{i < kdim} y_i v_i (FP64 sums)
+// kdim = the instance's Krylov dimension (gm scalar)
 template <typename TV>
-__global__ void k_lincomb(long long n, const TV *__restrict__ V, long long ldv, int kdim,
-                          const double *__restrict__ y, TV *__restrict__ out)
+__global__ void k_lincomb(Bat bt, long long n, const TV *__restrict__ V, long long ldv, const double *__restrict__ gm,
+                          GmLayout L, TV *__restrict__ out)
 {
+    NKS_INST(V = shift(V, io); gm = shift(gm, io); out = shift(out, io);)
+    const int kdim = (int)gm[L.scal + S_KDIM];
+    const double *y = gm + L.y;
     __shared__ double ys[kMaxDots];
     if ((int)threadIdx.x < kdim) ys[threadIdx.x] = y[threadIdx.x];
     __syncthreads();
@@ -326,72 +388,90 @@ __global__ void k_lincomb(long long n, const TV *__restrict__ V, long long ldv, 
 
 }  // namespace
 
-int launch_axpby(long long n, double a, const double *x, double b, double *y, cudaStream_t st)
+int launch_axpby(long long n, double a, const double *x, double b, double *y, cudaStream_t st, const Bat &bt)
 {
-    k_axpby<<<nb(n), kT, 0, st>>>(n, a, x, b, y);
+    k_axpby<<<dim3(nb(n), bt.nb), kT, 0, st>>>(bt, n, a, x, b, y);
     return 1;
 }
 
-int launch_waxpy(long long n, const double *x, double a, const double *y, double *w, cudaStream_t st)
+int launch_waxpy(long long n, const double *x, double a, const double *y, double *w, cudaStream_t st, const Bat &bt)
 {
-    k_waxpy<<<nb(n), kT, 0, st>>>(n, x, a, y, w);
+    k_waxpy<<<dim3(nb(n), bt.nb), kT, 0, st>>>(bt, n, x, a, y, w);
+    return 1;
+}
+
+int launch_waxpy_lam(long long n, const double *x, const double *isc, const double *y, double *w, cudaStream_t st,
+                     const Bat &bt)
+{
+    k_waxpy_lam<<<dim3(nb(n), bt.nb), kT, 0, st>>>(bt, n, x, isc, y, w);
+    return 1;
+}
+
+int launch_copy(long long n, const double *x, double *y, cudaStream_t st, const Bat &bt)
+{
+    k_copy<<<dim3(nb(n), bt.nb), kT, 0, st>>>(bt, n, x, y);
+    return 1;
+}
+
+static int launch_zero(long long n, double *y, cudaStream_t st, const Bat &bt)
+{
+    k_zero<<<dim3(nb(n), bt.nb), kT, 0, st>>>(bt, n, y);
     return 1;
 }
 
 template <typename TS, typename TD>
-__global__ void k_convert(long long n, const TS *__restrict__ a, TD *__restrict__ b)
+__global__ void k_convert(Bat bt, long long n, const TS *__restrict__ a, TD *__restrict__ b)
 {
+    NKS_INST(a = shift(a, io); b = shift(b, io);)
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i < n) b[i] = (TD)a[i];
 }
 
-int launch_convert(long long n, const double *a, float *b, cudaStream_t st)
+int launch_convert(long long n, const double *a, float *b, cudaStream_t st, const Bat &bt)
 {
-    k_convert<double, float><<<nb(n), kT, 0, st>>>(n, a, b);
+    k_convert<double, float><<<dim3(nb(n), bt.nb), kT, 0, st>>>(bt, n, a, b);
     return 1;
 }
 
-int launch_convert(long long n, const float *a, double *b, cudaStream_t st)
+int launch_convert(long long n, const float *a, double *b, cudaStream_t st, const Bat &bt)
 {
-    k_convert<float, double><<<nb(n), kT, 0, st>>>(n, a, b);
+    k_convert<float, double><<<dim3(nb(n), bt.nb), kT, 0, st>>>(bt, n, a, b);
     return 1;
 }
 
-int launch_scale_dev(long long n, const double *src, const double *inv, double *dst, cudaStream_t st)
+int launch_dot2(long long n, const double *x, const double *y, double *partials, int rb, cudaStream_t st,
+                const Bat &bt)
 {
-    k_scale_dev<double, double><<<nb(n), kT, 0, st>>>(n, src, inv, dst);
-    return 1;
-}
-
-int launch_dot2(long long n, const double *x, const double *y, double *partials, cudaStream_t st)
-{
-    k_dot2<<<kRedBlocks, kRedThreads, 0, st>>>(n, x, y, partials);
+    k_dot2<<<dim3(rb, bt.nb), kRedThreads, 0, st>>>(bt, n, x, y, partials);
     return 1;
 }
 
 size_t gmres_state_doubles(int m) { return (size_t)GmLayout(m).total; }
 
-// ||x||^2 of a device vector into P->hscal[0] (synchronises)
-static double norm2_host(Problem *P, const double *x)
+// ||x||^2 of each instance's vector (bt's instances) into beta2[i] (synchronises);
+// the squared norm stays in dscal[1] of each instance
+static int norm2_batch(Problem *P, const double *x, const Bat &bt, std::vector<double> &beta2)
 {
     P->tick(8);
-    P->count(launch_dot2(P->nvec, x, x, P->partials, P->stream));
-    P->count(launch_finalize(P->partials, kRedBlocks, 2, P->dscal, P->stream));
+    P->count(launch_dot2(P->nvec, x, x, P->partials, P->rb, P->stream, bt));
+    P->count(launch_finalize(P->partials, P->rb, 2, P->dscal, P->stream, bt));
     P->tock(8);
-    cudaMemcpyAsync(P->hscal, P->dscal + 1, sizeof(double), cudaMemcpyDeviceToHost, P->stream);
-    cudaStreamSynchronize(P->stream);
-    return P->hscal[0];
+    int rc = P->read_scalars(P->dscal + 1, 1, "gmres norm");
+    if (rc) return rc;
+    beta2.resize(P->nb);
+    for (int i = 0; i < P->nb; i++) beta2[i] = P->hread[(size_t)i * 64];
+    return NKS_OK;
 }
 
 template <typename TV>
-static void apply_J(Problem *P, int mode, const TV *v, TV *out, bool project_input)
+static void apply_J(Problem *P, int mode, const TV *v, TV *out, bool project_input, const Bat &bt)
 {
     P->tick(1);
     if constexpr (sizeof(TV) == sizeof(float))
-        P->count(launch_jv32(P->g, P->k, P->cur_dt, mode, P->partf, P->mobf, v, out, P->stream,
+        P->count(launch_jv32(P->g, P->k, P->isc, mode, P->partf, P->mobf, v, out, P->stream, bt,
                              project_input ? P->Jecf : nullptr, P->zsum));
     else
-        P->count(launch_jv64(P->g, P->k, P->cur_dt, mode, P->part, P->mob, v, P->Gc, P->sig, out, P->stream,
+        P->count(launch_jv64(P->g, P->k, P->isc, mode, P->part, P->mob, v, P->Gc, P->sig, out, P->stream, bt,
                              project_input ? P->Jec : nullptr, P->zsum));
     P->tock(1);
 }
@@ -399,22 +479,22 @@ static void apply_J(Problem *P, int mode, const TV *v, TV *out, bool project_inp
 // J e_c at the current iterate: with it the Arnoldi step applies J P z without
 // projecting z (see the Jacobian action).  In mixed precision the FP32 copies
 // of the operator's coefficients are refreshed here as well.
-void prepare_projection(Problem *P, int mode)
+static void prepare_projection(Problem *P, int mode, const Bat &bt)
 {
     P->tick(1);
-    P->count(launch_jv64(P->g, P->k, P->cur_dt, mode, P->part, P->mob, P->ec, P->Gc, P->sig, P->Jec, P->stream));
+    P->count(launch_jv64(P->g, P->k, P->isc, mode, P->part, P->mob, P->ec, P->Gc, P->sig, P->Jec, P->stream, bt));
     if (P->opts.precision == NKS_MIXED) {
-        P->count(launch_convert(2 * P->N, P->Jec, P->Jecf, P->stream));
-        refresh_f32_coefficients(P);
+        P->count(launch_convert(2 * P->N, P->Jec, P->Jecf, P->stream, bt));
+        refresh_f32_coefficients(P, bt);
     }
     P->tock(1);
 }
 
 // FP32 copies of the Jacobian action's coefficients at the current iterate
-void refresh_f32_coefficients(Problem *P)
+void refresh_f32_coefficients(Problem *P, const Bat &bt)
 {
-    P->count(launch_convert(4 * P->N, P->part, P->partf, P->stream));
-    P->count(launch_convert(P->g.dim * P->N, P->mob, P->mobf, P->stream));
+    P->count(launch_convert(4 * P->N, P->part, P->partf, P->stream, bt));
+    P->count(launch_convert(P->g.dim * P->N, P->mob, P->mobf, P->stream, bt));
 }
 
 // Krylov work vectors of the basis type
@@ -426,89 +506,131 @@ struct Basis {
 static Basis<double> basis64(Problem *P) { return {P->V, P->W, P->Z, P->ldv}; }
 static Basis<float> basis32(Problem *P) { return {P->Vf, P->Wf, P->Zf, P->ldvf}; }
 
+// Batched GMRES(m): every instance with is[i].gin runs its own Arnoldi process
+// (own Hessenberg matrix, own stopping test) in lockstep with the others; an
+// instance that has met its test is masked out of the remaining launches, so
+// each instance performs exactly the operations it performs alone.
 template <typename TV>
-static int gmres_t(Problem *P, Basis<TV> K, int mode, const double *b, double *x, double tol, int *its_out,
-                   double *res_out)
+static int gmres_t(Problem *P, Basis<TV> K, int mode, const double *b, double *x)
 {
     const int m = P->opts.gmres_restart;
     const GmLayout L(m);
     const long long n = P->nvec, ldv = K.ldv;
+    const int nbt = P->nb;
     cudaStream_t st = P->stream;
     TV *V = K.V, *W = K.W, *Z = K.Z;
     double *R = P->R, *gm = P->gm, *Jx = P->T64;
-    cudaMemsetAsync(x, 0, sizeof(double) * n, st);
-    cudaMemcpyAsync(R, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
-    double beta = sqrt(norm2_host(P, R));
-    int its = 0;
     const int maxit = P->opts.gmres_maxit;
-    while (beta > tol && its < maxit) {
-        k_gm_start<<<1, 1, 0, st>>>(gm, L, beta);
-        k_scale_dev<double, TV><<<nb(n), kT, 0, st>>>(n, R, gm + L.scal + S_INV, V);
+    std::vector<char> in(nbt), cyc(nbt), act(nbt);
+    for (int i = 0; i < nbt; i++) {
+        in[i] = P->is[i].gin ? 1 : 0;
+        P->is[i].gits = 0;
+    }
+    const Bat bin = P->set_mask(M_GIN, in);
+    P->count(launch_zero(n, x, st, bin));
+    P->count(launch_copy(n, b, R, st, bin));
+    prepare_projection(P, mode, bin);
+    std::vector<double> b2;
+    int rc = norm2_batch(P, R, bin, b2);
+    if (rc) return rc;
+    for (int i = 0; i < nbt; i++)
+        if (in[i]) P->is[i].beta = sqrt(b2[i]);
+    for (;;) {
+        bool any = false;
+        for (int i = 0; i < nbt; i++) {
+            const IState &s = P->is[i];
+            cyc[i] = in[i] && s.beta == s.beta && s.beta > s.gtol && s.gits < maxit;
+            any = any || cyc[i];
+        }
+        if (!any) break;
+        const Bat bc = P->set_mask(M_CYC, cyc);
+        act = cyc;
+        Bat ba = P->set_mask(M_ACT, act);
+        k_gm_start<<<nbt, 1, 0, st>>>(bc, gm, L, P->dscal + 1);
+        k_scale_dev<double, TV><<<dim3(nb(n), nbt), kT, 0, st>>>(bc, n, R, gm + L.scal + S_INV, V);
         P->count(2);
-        int kdim = 0;
         for (int j = 0; j < m; j++) {
             TV *vj = V + (size_t)j * ldv, *vn = V + (size_t)(j + 1) * ldv;
-            ras_apply_t<TV>(P, vj, Z);    // z = RAS^-1 v_j (sum of z_c to P->zsum)
-            apply_J<TV>(P, mode, Z, W, true);  // w = J P z
+            ras_apply_t<TV>(P, vj, Z, ba);         // z = RAS^-1 v_j (sum of z_c to zsum)
+            apply_J<TV>(P, mode, Z, W, true, ba);  // w = J P z
             // CGS pass 1 and 2
             P->tick(4);
-            launch_multidot<TV>(j + 1, ldv, V, W, P->partials, nullptr, gm + L.hcol, P->tickets, st);
+            launch_multidot<TV>(j + 1, ldv, V, W, P->partials, nullptr, gm + L.hcol, P->tickets, P->rb, st, ba);
             P->tock(4);
             P->tick(5);
             launch_update<TV>(j + 1, ldv, V, gm + L.hcol, W, P->partials, nullptr, gm + L.scal + S_WN,
-                              P->tickets + 1, st);
+                              P->tickets + 1, P->rb, st, ba);
             P->tock(5);
             // optional second pass (CGS2), gated on the device
-            k_cgs_decide<<<1, 1, 0, st>>>(gm, L, j);
+            k_cgs_decide<<<nbt, 1, 0, st>>>(ba, gm, L, j);
             const double *gate = gm + L.scal + S_FLAG;
             P->tick(4);
-            launch_multidot<TV>(j + 1, ldv, V, W, P->partials, gate, gm + L.h2, P->tickets, st);
+            launch_multidot<TV>(j + 1, ldv, V, W, P->partials, gate, gm + L.h2, P->tickets, P->rb, st, ba);
             P->tock(4);
             P->tick(5);
             launch_update<TV>(j + 1, ldv, V, gm + L.h2, W, P->partials, gate, gm + L.scal + S_WN, P->tickets + 1,
-                              st);
+                              P->rb, st, ba);
             P->tock(5);
-            k_cgs_accum<<<1, 1, 0, st>>>(gm, L, j);
+            k_cgs_accum<<<nbt, 1, 0, st>>>(ba, gm, L, j);
             P->tick(9);
-            k_arnoldi<<<1, 1, 0, st>>>(gm, L, j);
+            k_arnoldi<<<nbt, 1, 0, st>>>(ba, gm, L, j);
             P->tock(9);
-            k_scale_dev<TV, TV><<<nb(n), kT, 0, st>>>(n, W, gm + L.scal + S_INV, vn);
+            k_scale_dev<TV, TV><<<dim3(nb(n), nbt), kT, 0, st>>>(ba, n, W, gm + L.scal + S_INV, vn);
             P->count(8);  // 2 multidot + 2 update + decide + accum + arnoldi + scale
-            its++;
-            kdim = j + 1;
-            cudaMemcpyAsync(P->hscal, gm + L.scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, st);
-            cudaError_t e = cudaStreamSynchronize(st);
-            if (e != cudaSuccess) return cuda_fail(P, e, "gmres");
-            const double res = P->hscal[S_RES], wn = sqrt(P->hscal[S_WN]);
-            if (!(res == res)) break;  // NaN: leave the cycle, the true residual decides
-            if (res <= tol || its >= maxit || wn == 0.0) break;
+            rc = P->read_scalars(gm + L.scal, 8, "gmres");
+            if (rc) return rc;
+            bool changed = false, left = false;
+            for (int i = 0; i < nbt; i++) {
+                if (!act[i]) continue;
+                IState &s = P->is[i];
+                s.gits++;
+                const double res = P->hread[(size_t)i * 64 + S_RES], wn = sqrt(P->hread[(size_t)i * 64 + S_WN]);
+                // NaN leaves the cycle (the true residual decides)
+                if (!(res == res) || res <= s.gtol || s.gits >= maxit || wn == 0.0) {
+                    act[i] = 0;
+                    changed = true;
+                } else {
+                    left = true;
+                }
+            }
+            if (!left) break;
+            if (changed) ba = P->set_mask(M_ACT, act);
         }
         // x += M^-1 (V y), then the true residual in FP64
-        k_hsolve<<<1, 1, 0, st>>>(gm, L, kdim);
-        k_lincomb<TV><<<nb(n), kT, 0, st>>>(n, V, ldv, kdim, gm + L.y, W);
+        k_hsolve<<<nbt, 1, 0, st>>>(bc, gm, L);
+        k_lincomb<TV><<<dim3(nb(n), nbt), kT, 0, st>>>(bc, n, V, ldv, gm, L, W);
         P->count(2);
-        ras_apply_t<TV>(P, W, Z);
-        k_add<TV><<<nb(n), kT, 0, st>>>(n, Z, x);
+        ras_apply_t<TV>(P, W, Z, bc);
+        k_add<TV><<<dim3(nb(n), nbt), kT, 0, st>>>(bc, n, Z, x);
         P->count(1);
         // x = x + P z: x is already in the range of P and P is linear and idempotent,
         // so P is applied once to the FP64 sum; every Newton correction keeps
         // sum s_c = 0 and the gauge of u to FP64 rounding
-        project(P, x);
-        apply_J<double>(P, mode, x, Jx, false);
-        P->count(launch_waxpy(n, b, -1.0, Jx, R, st));
-        beta = sqrt(norm2_host(P, R));
-        if (!(beta == beta)) break;
+        project(P, x, bc);
+        apply_J<double>(P, mode, x, Jx, false, bc);
+        P->count(launch_waxpy(n, b, -1.0, Jx, R, st, bc));
+        rc = norm2_batch(P, R, bc, b2);
+        if (rc) return rc;
+        for (int i = 0; i < nbt; i++)
+            if (cyc[i]) P->is[i].beta = sqrt(b2[i]);
     }
-    *its_out = its;
-    *res_out = beta;
+    for (int i = 0; i < nbt; i++)
+        if (in[i]) P->is[i].res = P->is[i].beta;
+    // a Schwarz sweep whose factor copy never completed flags its instance (bounded wait)
+    rc = P->read_flags("gmres");
+    if (rc) return rc;
+    for (int i = 0; i < nbt; i++)
+        if (in[i] && (P->hflags[2 * i + 1] & 4)) {
+            P->err = "Schwarz sweep: a bulk copy of the factors did not complete";
+            return NKS_ETIMEOUT;
+        }
     return NKS_OK;
 }
 
-int gmres_solve(Problem *P, int mode, const double *b, double *x, double tol, int *its_out, double *res_out)
+int gmres_solve(Problem *P, int mode, const double *b, double *x)
 {
-    prepare_projection(P, mode);
-    if (P->opts.precision == NKS_MIXED) return gmres_t<float>(P, basis32(P), mode, b, x, tol, its_out, res_out);
-    return gmres_t<double>(P, basis64(P), mode, b, x, tol, its_out, res_out);
+    if (P->opts.precision == NKS_MIXED) return gmres_t<float>(P, basis32(P), mode, b, x);
+    return gmres_t<double>(P, basis64(P), mode, b, x);
 }
 
 }  // namespace nks

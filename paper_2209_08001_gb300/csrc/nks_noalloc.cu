@@ -78,12 +78,19 @@ extern "C" int nks_residual_noalloc(const nks_grid *grid, const nks_coeffs *coef
     double *partials = base + kPerPoint * NKS_NOALLOC_MAX_POINTS;
     double *sums = partials + kRedBlocks * 64;  // 64 doubles after the partials
     int *flag = reinterpret_cast<int *>(sums + 8);
+    double *isc = sums + 16;  // the kernels' per-instance scalars (dt, cbar0)
     // the scratch keeps the previous call's contents: only the domain flag must start at zero
     cudaMemsetAsync(flag, 0, sizeof(int), st);
-    launch_mobility(g, k, X0, mob, st);
-    if (k.elastic) launch_trace0(g, k, X0, tr0, st);
-    launch_residual(g, k, dt, mode, X1, X0, tr0, mob, Gc, sig, part, F, flag, partials, st);
-    launch_finalize(partials, kRedBlocks, 1, fnorm2 ? fnorm2 : sums, st);
+    double hisc[I_NSC] = {0.0};
+    hisc[I_DT] = dt;
+    hisc[I_CBAR0] = cbar0;
+    // from pageable memory: the source is staged before the call returns
+    cudaMemcpyAsync(isc, hisc, sizeof(hisc), cudaMemcpyHostToDevice, st);
+    const Bat one{};
+    launch_mobility(g, k, X0, mob, st, one);
+    if (k.elastic) launch_trace0(g, k, isc, X0, tr0, st, one);
+    launch_residual(g, k, isc, mode, X1, X0, tr0, mob, Gc, sig, part, F, flag, partials, kRedBlocks, st, one);
+    launch_finalize(partials, kRedBlocks, 1, fnorm2 ? fnorm2 : sums, st, one);
     int hflag = 0;
     cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
     cudaError_t e = cudaStreamSynchronize(st);

@@ -56,6 +56,7 @@ struct RasPlan {
     int npart = 0;                  // stage-A partial sums per point (largest of the two sweeps)
     long long maxblk = 0;           // largest forward or backward part of a level (elements)
     long long fac_elems = 0;
+    long long scr_elems = 0;        // global scratch vector of the sweeps (when x is not in shared memory)
     long long total_np = 0;         // overlapped points of all subdomains
     bool x_smem = true;
     size_t smem_bytes = 0;          // dynamic shared memory of the apply kernel (FP64 factors)
@@ -312,20 +313,7 @@ int ras_plan_create(Problem *P, std::string &err)
         err = "out of device memory (Schwarz tables)";
         return NKS_ENOMEM;
     }
-    R->fac = (double *)P->dalloc(sizeof(double) * (size_t)fac_off);
-    R->proj = (double *)P->dalloc(sizeof(double) * 64);
-    const bool mixed = P->opts.precision == NKS_MIXED;
-    if (!R->x_smem && !mixed) R->scratch = (double *)P->dalloc(sizeof(double) * (size_t)scr_off);
-    if (mixed) {
-        R->fac32 = (float *)P->dalloc(sizeof(float) * (size_t)fac_off);
-        if (!R->x_smem32) R->scratch32 = (float *)P->dalloc(sizeof(float) * (size_t)scr_off);
-    }
-    if (!R->fac || !R->proj || (!R->x_smem && !mixed && !R->scratch) || (mixed && !R->fac32) ||
-        (mixed && !R->x_smem32 && !R->scratch32)) {
-        err = "out of device memory (Schwarz factors)";
-        return NKS_ENOMEM;
-    }
-    cudaMemset(R->fac, 0, sizeof(double) * (size_t)fac_off);  // padding entries stay 0
+    R->scr_elems = scr_off;
     P->stats.factor_bytes = (long long)(sizeof(double) * (size_t)fac_off);
     P->stats.schwarz_points = (double)R->total_np;
     ras_work(P, &P->stats.schwarz_bytes, &P->stats.schwarz_flops);
@@ -380,7 +368,8 @@ struct DevAcc {
 
 // Fused assembly + ILU(0) (textbook IKJ order within a row) of J restricted to
 // each overlapped box.  Rows of earlier points are final when a level starts.
-__global__ void k_ras_factor(DGrid g, DCoef k, double dt, int mode, FacTables T, const SubInfo *__restrict__ subs,
+__global__ void k_ras_factor(DGrid g, DCoef k, Bat bt, const double *__restrict__ isc, int mode, FacTables T,
+                             const SubInfo *__restrict__ subs,
                              const int *__restrict__ lvl_ptr, const long long *__restrict__ lvl_blk,
                              const int *__restrict__ lvl_lp, const char4 *__restrict__ tmpl,
                              const short *__restrict__ st, const short *__restrict__ slotmap,
@@ -388,6 +377,13 @@ __global__ void k_ras_factor(DGrid g, DCoef k, double dt, int mode, FacTables T,
                              const double *__restrict__ part, const double *__restrict__ mob,
                              double *__restrict__ fac, int *__restrict__ flag)
 {
+    long long io;
+    if (!inst_off(bt, blockIdx.y, io)) return;
+    part = shift(part, io);
+    mob = shift(mob, io);
+    fac = shift(fac, io);
+    flag = shift(flag, io);
+    const double dt = shift(isc, io)[I_DT];
     const SubInfo si = subs[blockIdx.x];
     const int nf = T.nf, D = g.dim;
     const int *lptr = lvl_ptr + si.lvl_off;
@@ -597,13 +593,23 @@ __device__ __forceinline__ void stage_b(int kk, int lp, int lx, int ly, int lz, 
 // schedule inside a level), restricted prolongation.  Threads are grouped in
 // warps per stage-A task: warp w serves task w / wpt, points (w % wpt) * 32 + lane.
 template <int D, int NF, typename T, typename TV>
-__global__ void __launch_bounds__(1024) k_ras_apply(DGrid g, const SubInfo *__restrict__ subs, const int *__restrict__ lvl_ptr,
+__global__ void __launch_bounds__(1024) k_ras_apply(DGrid g, Bat bt, const SubInfo *__restrict__ subs, const int *__restrict__ lvl_ptr,
                             const long long *__restrict__ lvl_blk, const int *__restrict__ lvl_lp,
                             const T *__restrict__ fac, const TV *__restrict__ r, TV *__restrict__ z,
                             T *__restrict__ scratch, int x_in_smem, int maxnp, long long maxblk, int wpt,
                             int pstride, int *flag, double *__restrict__ cpart, double *__restrict__ csum,
                             unsigned int *ticket)
 {
+    long long io;
+    if (!inst_off(bt, blockIdx.y, io)) return;
+    fac = shift(fac, io);
+    r = shift(r, io);
+    z = shift(z, io);
+    scratch = shift(scratch, io);
+    flag = shift(flag, io);
+    cpart = shift(cpart, io);
+    csum = shift(csum, io);
+    ticket = shift(ticket, io);
     constexpr Pattern PT = Pat<D, NF>::v;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
@@ -692,7 +698,7 @@ __global__ void __launch_bounds__(1024) k_ras_apply(DGrid g, const SubInfo *__re
         // a copy never completed: report it, let outstanding copies land (bounded), and
         // write nothing (the block still takes its turn in the sum below)
         if (tid == 0) {
-            atomicOr(flag, 4);
+            atomicOr(flag + 1, 4);
             mbar_wait_bounded(&bar[0], 0);
             mbar_wait_bounded(&bar[1], 0);
         }
@@ -726,10 +732,16 @@ struct ModeMasks {
 };
 
 template <int NF, int NM, typename TV>
-__global__ void __launch_bounds__(kRedThreads, 4) k_proj_dots(DGrid g, ModeMasks mm, const TV *__restrict__ z,
+__global__ void __launch_bounds__(kRedThreads, 4) k_proj_dots(DGrid g, Bat bt, ModeMasks mm, const TV *__restrict__ z,
                                                               double *__restrict__ partials, double *__restrict__ out,
                                                               unsigned int *ticket)
 {
+    long long io;
+    if (!inst_off(bt, blockIdx.y, io)) return;
+    z = shift(z, io);
+    partials = shift(partials, io);
+    out = shift(out, io);
+    ticket = shift(ticket, io);
     constexpr int K = 1 + (NF - 2) * NM;
     const long long N = g.N;
     double acc[K];
@@ -754,8 +766,12 @@ __global__ void __launch_bounds__(kRedThreads, 4) k_proj_dots(DGrid g, ModeMasks
 }
 
 template <int NF, int NM, typename TV>
-__global__ void k_proj_sub(DGrid g, ModeMasks mm, const double *__restrict__ sums, TV *__restrict__ z)
+__global__ void k_proj_sub(DGrid g, Bat bt, ModeMasks mm, const double *__restrict__ sums, TV *__restrict__ z)
 {
+    long long io;
+    if (!inst_off(bt, blockIdx.y, io)) return;
+    sums = shift(sums, io);
+    z = shift(z, io);
     long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long N = g.N;
     if (p >= N) return;
@@ -779,25 +795,30 @@ __global__ void k_proj_sub(DGrid g, ModeMasks mm, const double *__restrict__ sum
 }
 
 template <int NF, int NM, typename TV>
-void launch_project_t(Problem *P, TV *z)
+void launch_project_t(Problem *P, TV *z, const Bat &bt)
 {
     RasPlan *R = P->ras;
     ModeMasks mm{};
     int mi = 0;
     for (int m = 0; m < (1 << P->g.dim); m++)
         if ((m & ~R->evenmask) == 0) mm.m[mi++] = m;
-    k_proj_dots<NF, NM, TV><<<kRedBlocks, kRedThreads, 0, P->stream>>>(P->g, mm, z, P->partials, R->proj,
-                                                                         P->tickets + 2);
-    k_proj_sub<NF, NM, TV><<<(int)((P->N + 255) / 256), 256, 0, P->stream>>>(P->g, mm, R->proj, z);
+    k_proj_dots<NF, NM, TV><<<dim3(P->rb, bt.nb), kRedThreads, 0, P->stream>>>(P->g, bt, mm, z, P->partials,
+                                                                                R->proj, P->tickets + 2);
+    k_proj_sub<NF, NM, TV><<<dim3((unsigned)((P->N + 255) / 256), bt.nb), 256, 0, P->stream>>>(P->g, bt, mm, R->proj,
+                                                                                               z);
 }
 
-__global__ void k_to_float(long long n, const double *__restrict__ a, float *__restrict__ b)
+__global__ void k_to_float(Bat bt, long long n, const double *__restrict__ a, float *__restrict__ b)
 {
+    long long io;
+    if (!inst_off(bt, blockIdx.y, io)) return;
+    a = shift(a, io);
+    b = shift(b, io);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         b[i] = (float)a[i];
 }
 
-void launch_factor(Problem *P, int mode)
+void launch_factor(Problem *P, int mode, const Bat &bt)
 {
     RasPlan *R = P->ras;
     const Pattern CP = compile_time_pattern(P->g.dim, P->nf);
@@ -810,14 +831,15 @@ void launch_factor(Problem *P, int mode)
     T.nlow = CP.nlow;
     T.nup = CP.nup;
     T.nf = P->nf;
-    k_ras_factor<<<R->nsub, 64, 0, P->stream>>>(P->g, P->k, P->cur_dt, mode, T, R->sub, R->lvl_ptr, R->lvl_blk,
+    k_ras_factor<<<dim3(R->nsub, bt.nb), 64, 0, P->stream>>>(P->g, P->k, bt, P->isc, mode, T, R->sub, R->lvl_ptr,
+                                                             R->lvl_blk,
                                                 R->lvl_lp, R->tmpl, R->st, R->slotmap, R->upd_ptr, R->upd, P->part,
                                                 P->mob, R->fac, P->dflag);
 }
 
 // FP64 vectors use the FP64 factors; FP32 vectors (mixed precision) the FP32 copy
 template <int D, int NF, typename TV>
-void launch_apply_t(Problem *P, const TV *r, TV *z)
+void launch_apply_t(Problem *P, const TV *r, TV *z, const Bat &bt)
 {
     RasPlan *R = P->ras;
     const int ntask = Sched<D, NF>::ntask;
@@ -835,8 +857,8 @@ void launch_apply_t(Problem *P, const TV *r, TV *z)
     const T *fac = f32 ? reinterpret_cast<const T *>(R->fac32) : reinterpret_cast<const T *>(R->fac);
     T *scr = f32 ? reinterpret_cast<T *>(R->scratch32) : reinterpret_cast<T *>(R->scratch);
     const int xs = f32 ? R->x_smem32 : R->x_smem;
-    k_ras_apply<D, NF, T, TV><<<R->nsub, threads, smem, P->stream>>>(
-        P->g, R->sub, R->lvl_ptr, R->lvl_blk, R->lvl_lp, fac, r, z, scr, xs ? 1 : 0, R->maxnp, R->maxblk, wpt, pstride,
+    k_ras_apply<D, NF, T, TV><<<dim3(R->nsub, bt.nb), threads, smem, P->stream>>>(
+        P->g, bt, R->sub, R->lvl_ptr, R->lvl_blk, R->lvl_lp, fac, r, z, scr, xs ? 1 : 0, R->maxnp, R->maxblk, wpt, pstride,
         P->dflag, P->partials, P->zsum, P->tickets + 3);
 }
 
@@ -852,86 +874,102 @@ void launch_apply_t(Problem *P, const TV *r, TV *z)
     case 35: FN<3, 5>(__VA_ARGS__); break; \
     }
 
-int ras_factor(Problem *P, int mode)
+// factors of the instances of bt; an instance whose factorisation meets a zero
+// pivot is marked failed (is[i].nst = -NKS_EPIVOT); on[i] mirrors bt's mask
+int ras_factor(Problem *P, int mode, const Bat &bt, const std::vector<char> &on)
 {
-    cudaMemsetAsync(P->dflag, 0, sizeof(int), P->stream);
+    cudaMemset2DAsync(P->dflag, (size_t)P->stride, 0, sizeof(int), (size_t)P->nb, P->stream);
     P->tick(3);
-    launch_factor(P, mode);
+    launch_factor(P, mode, bt);
     P->count(1);
     P->tock(3);
-    int hflag = 0;
-    cudaMemcpyAsync(&hflag, P->dflag, sizeof(int), cudaMemcpyDeviceToHost, P->stream);
-    cudaError_t e = cudaStreamSynchronize(P->stream);
-    if (e != cudaSuccess) return cuda_fail(P, e, "ras_factor");
-    if (hflag & 2) {
-        P->err = "zero pivot in an ILU(0) subdomain factorisation";
-        return NKS_EPIVOT;
+    int rc = P->read_flags("ras_factor");
+    if (rc) return rc;
+    for (int i = 0; i < P->nb; i++) {
+        if (!on[i]) continue;
+        if (P->hflags[2 * i] & 2) {
+            P->is[i].nst = -NKS_EPIVOT;
+            P->is[i].err = "zero pivot in an ILU(0) subdomain factorisation";
+        }
     }
     if (P->opts.precision == NKS_MIXED) {
-        k_to_float<<<4 * 152, 256, 0, P->stream>>>(P->ras->fac_elems, P->ras->fac, P->ras->fac32);
+        k_to_float<<<dim3(4 * 152, bt.nb), 256, 0, P->stream>>>(bt, P->ras->fac_elems, P->ras->fac, P->ras->fac32);
         P->count(1);
     }
-    P->factored = true;
     return NKS_OK;
 }
 
 template <typename TV>
-void project_t(Problem *P, TV *z)
+void project_t(Problem *P, TV *z, const Bat &bt)
 {
     RasPlan *R = P->ras;
     P->tick(6);
-    if (P->nf == 2) launch_project_t<2, 1, TV>(P, z);
+    if (P->nf == 2) launch_project_t<2, 1, TV>(P, z, bt);
     else {
         const int code = P->nf * 10 + R->nmodes;
         switch (code) {
-        case 31: launch_project_t<3, 1, TV>(P, z); break;
-        case 32: launch_project_t<3, 2, TV>(P, z); break;
-        case 41: launch_project_t<4, 1, TV>(P, z); break;
-        case 42: launch_project_t<4, 2, TV>(P, z); break;
-        case 44: launch_project_t<4, 4, TV>(P, z); break;
-        case 51: launch_project_t<5, 1, TV>(P, z); break;
-        case 52: launch_project_t<5, 2, TV>(P, z); break;
-        case 54: launch_project_t<5, 4, TV>(P, z); break;
-        case 58: launch_project_t<5, 8, TV>(P, z); break;
+        case 31: launch_project_t<3, 1, TV>(P, z, bt); break;
+        case 32: launch_project_t<3, 2, TV>(P, z, bt); break;
+        case 41: launch_project_t<4, 1, TV>(P, z, bt); break;
+        case 42: launch_project_t<4, 2, TV>(P, z, bt); break;
+        case 44: launch_project_t<4, 4, TV>(P, z, bt); break;
+        case 51: launch_project_t<5, 1, TV>(P, z, bt); break;
+        case 52: launch_project_t<5, 2, TV>(P, z, bt); break;
+        case 54: launch_project_t<5, 4, TV>(P, z, bt); break;
+        case 58: launch_project_t<5, 8, TV>(P, z, bt); break;
         }
     }
     P->count(2);
     P->tock(6);
 }
 
-void project(Problem *P, double *z) { project_t<double>(P, z); }
+void project(Problem *P, double *z, const Bat &bt) { project_t<double>(P, z, bt); }
 
 template <typename TV>
-void ras_apply_t(Problem *P, const TV *r, TV *z)
+void ras_apply_t(Problem *P, const TV *r, TV *z, const Bat &bt)
 {
     P->tick(2);
     switch (P->g.dim * 10 + P->nf) {
-    case 12: launch_apply_t<1, 2, TV>(P, r, z); break;
-    case 13: launch_apply_t<1, 3, TV>(P, r, z); break;
-    case 22: launch_apply_t<2, 2, TV>(P, r, z); break;
-    case 24: launch_apply_t<2, 4, TV>(P, r, z); break;
-    case 32: launch_apply_t<3, 2, TV>(P, r, z); break;
-    case 35: launch_apply_t<3, 5, TV>(P, r, z); break;
+    case 12: launch_apply_t<1, 2, TV>(P, r, z, bt); break;
+    case 13: launch_apply_t<1, 3, TV>(P, r, z, bt); break;
+    case 22: launch_apply_t<2, 2, TV>(P, r, z, bt); break;
+    case 24: launch_apply_t<2, 4, TV>(P, r, z, bt); break;
+    case 32: launch_apply_t<3, 2, TV>(P, r, z, bt); break;
+    case 35: launch_apply_t<3, 5, TV>(P, r, z, bt); break;
     }
     P->count(1);
     P->tock(2);
 }
-template void ras_apply_t<double>(Problem *, const double *, double *);
-template void ras_apply_t<float>(Problem *, const float *, float *);
+template void ras_apply_t<double>(Problem *, const double *, double *, const Bat &);
+template void ras_apply_t<float>(Problem *, const float *, float *, const Bat &);
 
-void ras_apply(Problem *P, const double *r, double *z)
+void ras_apply(Problem *P, const double *r, double *z, const Bat &bt)
 {
-    ras_apply_t<double>(P, r, z);
-    project(P, z);
+    ras_apply_t<double>(P, r, z, bt);
+    project(P, z, bt);
 }
 
 template <typename TV>
-void ras_apply_projected(Problem *P, const TV *r, TV *z)
+void ras_apply_projected(Problem *P, const TV *r, TV *z, const Bat &bt)
 {
-    ras_apply_t<TV>(P, r, z);
-    project_t<TV>(P, z);
+    ras_apply_t<TV>(P, r, z, bt);
+    project_t<TV>(P, z, bt);
 }
-template void ras_apply_projected<float>(Problem *, const float *, float *);
+template void ras_apply_projected<float>(Problem *, const float *, float *, const Bat &);
+
+// per-instance buffers of the Schwarz preconditioner (carved from each instance's slab)
+void ras_slab_items(Problem *P, std::vector<SlabItem> &items)
+{
+    RasPlan *R = P->ras;
+    const bool mixed = P->opts.precision == NKS_MIXED;
+    items.push_back({(void **)&R->fac, sizeof(double) * (size_t)R->fac_elems});
+    items.push_back({(void **)&R->proj, sizeof(double) * 64});
+    if (!R->x_smem && !mixed) items.push_back({(void **)&R->scratch, sizeof(double) * (size_t)R->scr_elems});
+    if (mixed) {
+        items.push_back({(void **)&R->fac32, sizeof(float) * (size_t)R->fac_elems});
+        if (!R->x_smem32) items.push_back({(void **)&R->scratch32, sizeof(float) * (size_t)R->scr_elems});
+    }
+}
 
 // algorithmic work of one Schwarz sweep (both triangular solves over every
 // overlapped point): bytes of factors + gathered and written vectors, FLOPs

@@ -156,8 +156,12 @@ __device__ inline void hooke_packed(const DGrid &g, const DCoef &k, const double
 
 // ---------------------------------------------------------------------------
 
-__global__ void k_mobility(DGrid g, DCoef k, const double *__restrict__ c0, double *__restrict__ mob)
+__global__ void k_mobility(DGrid g, DCoef k, Bat bt, const double *__restrict__ c0, double *__restrict__ mob)
 {
+    long long io;
+    if (!inst_off(bt, blockIdx.y, io)) return;
+    c0 = shift(c0, io);
+    mob = shift(mob, io);
     long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (p >= g.N) return;
     int x, y, z;
@@ -170,8 +174,14 @@ __global__ void k_mobility(DGrid g, DCoef k, const double *__restrict__ c0, doub
 }
 
 // tr eps^el of the level-n state (used by G^3 at n + 1/2)
-__global__ void k_trace0(DGrid g, DCoef k, const double *__restrict__ X0, double *__restrict__ tr0)
+__global__ void k_trace0(DGrid g, DCoef k, Bat bt, const double *__restrict__ isc, const double *__restrict__ X0,
+                         double *__restrict__ tr0)
 {
+    long long io;
+    if (!inst_off(bt, blockIdx.y, io)) return;
+    X0 = shift(X0, io);
+    tr0 = shift(tr0, io);
+    const double cbar0 = shift(isc, io)[I_CBAR0];
     long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (p >= g.N) return;
     int x, y, z;
@@ -180,14 +190,25 @@ __global__ void k_trace0(DGrid g, DCoef k, const double *__restrict__ X0, double
     double tr = 0.0;
     for (int K = 0; K < g.dim; K++)
         tr += (U[K * g.N + nbrJ(g, x, y, z, K, +1)] - U[K * g.N + nbrJ(g, x, y, z, K, -1)]) * (0.5 / g.h);
-    tr0[p] = tr - g.dim * k.eps0 * (X0[p] - k.cbar0);
+    tr0[p] = tr - g.dim * k.eps0 * (X0[p] - cbar0);
 }
 
-__global__ void k_res_a(DGrid g, DCoef k, double dt, int mode, const double *__restrict__ X1,
-                        const double *__restrict__ X0, const double *__restrict__ tr0, double *__restrict__ Gc,
-                        double *__restrict__ sig, double *__restrict__ part, double *__restrict__ F,
-                        int *__restrict__ flag)
+__global__ void k_res_a(DGrid g, DCoef k, Bat bt, const double *__restrict__ isc, int mode,
+                        const double *__restrict__ X1, const double *__restrict__ X0, const double *__restrict__ tr0,
+                        double *__restrict__ Gc, double *__restrict__ sig, double *__restrict__ part,
+                        double *__restrict__ F, int *__restrict__ flag)
 {
+    long long io;
+    if (!inst_off(bt, blockIdx.y, io)) return;
+    X1 = shift(X1, io);
+    X0 = shift(X0, io);
+    tr0 = shift(tr0, io);
+    Gc = shift(Gc, io);
+    sig = shift(sig, io);
+    part = shift(part, io);
+    F = shift(F, io);
+    flag = shift(flag, io);
+    const double dt = shift(isc, io)[I_DT], cbar0 = shift(isc, io)[I_CBAR0];
     long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (p >= g.N) return;
     int x, y, z;
@@ -198,7 +219,7 @@ __global__ void k_res_a(DGrid g, DCoef k, double dt, int mode, const double *__r
     double Du[3][3];
     if (k.elastic) {
         grad_u(g, X1 + 2 * N, x, y, z, Du);
-        hooke_packed(g, k, Du, k.eps0 * (c1 - k.cbar0), sig, p);
+        hooke_packed(g, k, Du, k.eps0 * (c1 - cbar0), sig, p);
     }
     if (mode != 0) {
         F[N + p] = 0.0;
@@ -209,7 +230,7 @@ __global__ void k_res_a(DGrid g, DCoef k, double dt, int mode, const double *__r
     double gc = G.gc, ge = G.ge;
     if (k.elastic) {
         // G^3_c = -eps0 sum_I sigma_II(eps^el_{n+1/2}) = -eps0 lam (tr1 + tr0)/2
-        double tr1 = -g.dim * k.eps0 * (c1 - k.cbar0);
+        double tr1 = -g.dim * k.eps0 * (c1 - cbar0);
         for (int K = 0; K < g.dim; K++) tr1 += Du[K][K];
         gc += -k.eps0 * k.lam * 0.5 * (tr1 + tr0[p]);
     }
@@ -232,12 +253,22 @@ __global__ void k_res_a(DGrid g, DCoef k, double dt, int mode, const double *__r
     part[3 * N + p] = G.dee;
 }
 
-__global__ void __launch_bounds__(kRedThreads) k_res_b(DGrid g, DCoef k, double dt, int mode,
-                                                       const double *__restrict__ X1, const double *__restrict__ X0,
-                                                       const double *__restrict__ Gc, const double *__restrict__ mob,
-                                                       const double *__restrict__ sig, double *__restrict__ F,
-                                                       double *__restrict__ partials)
+__global__ void __launch_bounds__(kRedThreads) k_res_b(DGrid g, DCoef k, Bat bt, const double *__restrict__ isc,
+                                                       int mode, const double *__restrict__ X1,
+                                                       const double *__restrict__ X0, const double *__restrict__ Gc,
+                                                       const double *__restrict__ mob, const double *__restrict__ sig,
+                                                       double *__restrict__ F, double *__restrict__ partials)
 {
+    long long io;
+    if (!inst_off(bt, blockIdx.y, io)) return;
+    X1 = shift(X1, io);
+    X0 = shift(X0, io);
+    Gc = shift(Gc, io);
+    mob = shift(mob, io);
+    sig = shift(sig, io);
+    F = shift(F, io);
+    partials = shift(partials, io);
+    const double dt = shift(isc, io)[I_DT];
     const long long N = g.N;
     const double ih2 = 1.0 / (g.h * g.h), i2h = 0.5 / g.h;
     double acc[1] = {0.0};
@@ -297,7 +328,6 @@ __global__ void __launch_bounds__(kRedThreads) k_res_b(DGrid g, DCoef k, double 
 
 // per-operator constants with the grid spacings folded in
 struct JvConst {
-    double idt;       // 1/dt
     double gc;        // 1/2 gamma_c / h^2
     double ge;        // 3/2 gamma_eta / h^2
     double ih2;       // 1/h^2
@@ -309,11 +339,10 @@ struct JvConst {
     int mode;
 };
 
-static JvConst jv_const(const DGrid &g, const DCoef &k, double dt, int mode)
+static JvConst jv_const(const DGrid &g, const DCoef &k, int mode)
 {
     JvConst c;
     const double i2h = 0.5 / g.h, ih2 = 1.0 / (g.h * g.h);
-    c.idt = 1.0 / dt;
     c.gc = 0.5 * k.gamma_c * ih2;
     c.ge = 1.5 * k.gamma_eta * ih2;
     c.ih2 = ih2;
@@ -378,22 +407,29 @@ __device__ __forceinline__ void jv_point(const JvConst &c, int mode, int N, int 
 
 // ---- FP64: two passes --------------------------------------------------------
 
+// grid: (x tiles, y tiles, n_z x instances); the instance is blockIdx.z / n_z
 template <int D>
 __device__ __forceinline__ bool grid_point(const DGrid &g, int (&c3)[3], int &p)
 {
     c3[0] = blockIdx.x * blockDim.x + threadIdx.x;
     c3[1] = D >= 2 ? (int)(blockIdx.y * blockDim.y + threadIdx.y) : 0;
-    c3[2] = D == 3 ? (int)blockIdx.z : 0;
+    c3[2] = D == 3 ? (int)(blockIdx.z % g.n[2]) : 0;
     if (c3[0] >= g.n[0] || c3[1] >= g.n[1]) return false;
     p = c3[0] + g.n[0] * (c3[1] + g.n[1] * c3[2]);
     return true;
 }
 
 template <int D, bool EL>
-__global__ void __launch_bounds__(256) k_jv64_a(DGrid g, JvConst c, const double *__restrict__ part,
+__global__ void __launch_bounds__(256) k_jv64_a(DGrid g, JvConst c, Bat bt, const double *__restrict__ part,
                                                 const double *__restrict__ v, double *__restrict__ dG,
                                                 double *__restrict__ sig)
 {
+    long long io;
+    if (!inst_off(bt, blockIdx.z / g.n[2], io)) return;
+    part = shift(part, io);
+    v = shift(v, io);
+    dG = shift(dG, io);
+    sig = shift(sig, io);
     int c3[3], p;
     if (!grid_point<D>(g, c3, p)) return;
     const int nn[3] = {g.n[0], g.n[1], g.n[2]};
@@ -410,12 +446,23 @@ __global__ void __launch_bounds__(256) k_jv64_a(DGrid g, JvConst c, const double
 }
 
 template <int D, bool EL>
-__global__ void __launch_bounds__(256) k_jv64_b(DGrid g, JvConst c, const double *__restrict__ part,
-                                                const double *__restrict__ mob, const double *__restrict__ v,
-                                                const double *__restrict__ dG, const double *__restrict__ sig,
-                                                double *__restrict__ Jv, const double *__restrict__ Jec,
-                                                const double *__restrict__ zsum)
+__global__ void __launch_bounds__(256) k_jv64_b(DGrid g, JvConst c, Bat bt, const double *__restrict__ isc,
+                                                const double *__restrict__ part, const double *__restrict__ mob,
+                                                const double *__restrict__ v, const double *__restrict__ dG,
+                                                const double *__restrict__ sig, double *__restrict__ Jv,
+                                                const double *__restrict__ Jec, const double *__restrict__ zsum)
 {
+    long long io;
+    if (!inst_off(bt, blockIdx.z / g.n[2], io)) return;
+    part = shift(part, io);
+    mob = shift(mob, io);
+    v = shift(v, io);
+    dG = shift(dG, io);
+    sig = shift(sig, io);
+    Jv = shift(Jv, io);
+    Jec = shift(Jec, io);
+    zsum = shift(zsum, io);
+    const double idt = 1.0 / shift(isc, io)[I_DT];
     int c3[3], p;
     if (!grid_point<D>(g, c3, p)) return;
     const int nn[3] = {g.n[0], g.n[1], g.n[2]};
@@ -432,8 +479,8 @@ __global__ void __launch_bounds__(256) k_jv64_b(DGrid g, JvConst c, const double
             flux += mob[J * N + p] * (dG[ip[J]] - G0) - mob[J * N + im[J]] * (G0 - dG[im[J]]);
             sn += v[N + ip[J]] + v[N + im[J]];
         }
-        jc = vc * c.idt - flux * c.ih2;
-        je = ve * c.idt + part[2 * N + p] * vc + part[3 * N + p] * ve - c.ge * (sn - (2 * D) * ve);
+        jc = vc * idt - flux * c.ih2;
+        je = ve * idt + part[2 * N + p] * vc + part[3 * N + p] * ve - c.ge * (sn - (2 * D) * ve);
     } else {
         jc = vc;
         je = ve;
@@ -477,11 +524,19 @@ struct JvTile<3> {
 };
 
 template <int D, bool EL>
-__global__ void __launch_bounds__(256) k_jv32(DGrid g, JvConst c, const float *__restrict__ part,
-                                              const float *__restrict__ mob, const float *__restrict__ v,
-                                              float *__restrict__ Jv, const float *__restrict__ Jec,
-                                              const double *__restrict__ zsum)
+__global__ void __launch_bounds__(256) k_jv32(DGrid g, JvConst c, Bat bt, const double *__restrict__ isc,
+                                              const float *__restrict__ part, const float *__restrict__ mob,
+                                              const float *__restrict__ v, float *__restrict__ Jv,
+                                              const float *__restrict__ Jec, const double *__restrict__ zsum)
 {
+    long long io;
+    if (!inst_off(bt, blockIdx.y, io)) return;
+    part = shift(part, io);
+    mob = shift(mob, io);
+    v = shift(v, io);
+    Jv = shift(Jv, io);
+    Jec = shift(Jec, io);
+    zsum = shift(zsum, io);
     constexpr int TX = JvTile<D>::TX, TY = JvTile<D>::TY, TZ = JvTile<D>::TZ;
     constexpr int HX = TX + 2, HY = D >= 2 ? TY + 2 : 1, HZ = D == 3 ? TZ + 2 : 1;
     constexpr int NH = HX * HY * HZ;
@@ -519,7 +574,7 @@ __global__ void __launch_bounds__(256) k_jv32(DGrid g, JvConst c, const float *_
     __syncthreads();
 
     const float m = Jec ? (float)(zsum[0] / (double)N) : 0.f;
-    const float idt = (float)c.idt, ih2 = (float)c.ih2, ge = (float)c.ge, i2h = (float)c.i2h;
+    const float idt = (float)(1.0 / shift(isc, io)[I_DT]), ih2 = (float)c.ih2, ge = (float)c.ge, i2h = (float)c.i2h;
     for (int t = threadIdx.x; t < TX * TY * TZ; t += blockDim.x) {
         const int tx = t % TX, ty = (t / TX) % TY, tz = t / (TX * TY);
         const int c3[3] = {x0 + tx, y0 + ty, z0 + tz};
@@ -568,9 +623,14 @@ __global__ void __launch_bounds__(256) k_jv32(DGrid g, JvConst c, const float *_
 __device__ inline double Psi(double z) { return z * log(z) + (1.0 - z) * log1p(-z); }
 
 // energy parts e1..e4 (Eq. relations) and mass, per-block partial sums
-__global__ void __launch_bounds__(kRedThreads) k_energy(DGrid g, DCoef k, const double *__restrict__ X,
-                                                        double *__restrict__ partials)
+__global__ void __launch_bounds__(kRedThreads) k_energy(DGrid g, DCoef k, Bat bt, const double *__restrict__ isc,
+                                                        const double *__restrict__ X, double *__restrict__ partials)
 {
+    long long io;
+    if (!inst_off(bt, blockIdx.y, io)) return;
+    X = shift(X, io);
+    partials = shift(partials, io);
+    const double cbar0 = shift(isc, io)[I_CBAR0];
     const long long N = g.N;
     const double ih = 1.0 / g.h;
     double acc[5] = {0, 0, 0, 0, 0};
@@ -589,7 +649,7 @@ __global__ void __launch_bounds__(kRedThreads) k_energy(DGrid g, DCoef k, const 
         if (k.elastic) {
             double Du[3][3];
             grad_u(g, X + 2 * N, x, y, z, Du);
-            const double s0 = k.eps0 * (c - k.cbar0);
+            const double s0 = k.eps0 * (c - cbar0);
             double tr = 0.0, sq = 0.0, off = 0.0;
             for (int I = 0; I < g.dim; I++) {
                 const double eII = Du[I][I] - s0;
@@ -620,8 +680,12 @@ __global__ void __launch_bounds__(kRedThreads) k_energy(DGrid g, DCoef k, const 
 }
 
 // sums K columns of nblocks partial rows in a fixed order (one block)
-__global__ void k_finalize(const double *__restrict__ partials, int nblocks, int K, double *__restrict__ out)
+__global__ void k_finalize(Bat bt, const double *__restrict__ partials, int nblocks, int K, double *__restrict__ out)
 {
+    long long io;
+    if (!inst_off(bt, blockIdx.x, io)) return;
+    partials = shift(partials, io);
+    out = shift(out, io);
     __shared__ double red[kRedThreads];
     for (int kk = 0; kk < K; kk++) {
         double a = 0.0;
@@ -639,44 +703,48 @@ __global__ void k_finalize(const double *__restrict__ partials, int nblocks, int
 
 }  // namespace
 
-int launch_mobility(const DGrid &g, const DCoef &k, const double *c0, double *mob, cudaStream_t st)
+int launch_mobility(const DGrid &g, const DCoef &k, const double *c0, double *mob, cudaStream_t st, const Bat &bt)
 {
-    k_mobility<<<blocks_for(g.N), kThreads, 0, st>>>(g, k, c0, mob);
+    k_mobility<<<dim3(blocks_for(g.N), bt.nb), kThreads, 0, st>>>(g, k, bt, c0, mob);
     return 1;
 }
 
-int launch_trace0(const DGrid &g, const DCoef &k, const double *X0, double *tr0, cudaStream_t st)
+int launch_trace0(const DGrid &g, const DCoef &k, const double *isc, const double *X0, double *tr0, cudaStream_t st,
+                  const Bat &bt)
 {
-    k_trace0<<<blocks_for(g.N), kThreads, 0, st>>>(g, k, X0, tr0);
+    k_trace0<<<dim3(blocks_for(g.N), bt.nb), kThreads, 0, st>>>(g, k, bt, isc, X0, tr0);
     return 1;
 }
 
-int launch_residual(const DGrid &g, const DCoef &k, double dt, int mode, const double *X1, const double *X0,
-                     const double *tr0, const double *mob, double *Gc, double *sig, double *part, double *F, int *flag,
-                     double *partials, cudaStream_t st)
+int launch_residual(const DGrid &g, const DCoef &k, const double *isc, int mode, const double *X1, const double *X0,
+                    const double *tr0, const double *mob, double *Gc, double *sig, double *part, double *F, int *flag,
+                    double *partials, int rb, cudaStream_t st, const Bat &bt)
 {
-    k_res_a<<<blocks_for(g.N), kThreads, 0, st>>>(g, k, dt, mode, X1, X0, tr0, Gc, sig, part, F, flag);
-    k_res_b<<<kRedBlocks, kRedThreads, 0, st>>>(g, k, dt, mode, X1, X0, Gc, mob, sig, F, partials);
+    k_res_a<<<dim3(blocks_for(g.N), bt.nb), kThreads, 0, st>>>(g, k, bt, isc, mode, X1, X0, tr0, Gc, sig, part, F,
+                                                                flag);
+    k_res_b<<<dim3(rb, bt.nb), kRedThreads, 0, st>>>(g, k, bt, isc, mode, X1, X0, Gc, mob, sig, F, partials);
     return 2;
 }
 
 template <int D, bool EL>
-static void launch_jv64_d(const DGrid &g, const JvConst &c, const double *part, const double *mob, const double *v,
-                          double *dG, double *sig, double *Jv, cudaStream_t st, const double *Jec, const double *zsum)
+static void launch_jv64_d(const DGrid &g, const JvConst &c, const Bat &bt, const double *isc, const double *part,
+                          const double *mob, const double *v, double *dG, double *sig, double *Jv, cudaStream_t st,
+                          const double *Jec, const double *zsum)
 {
     const dim3 blk(D == 1 ? 256 : 32, D == 1 ? 1 : 8);
-    const dim3 grd((g.n[0] + blk.x - 1) / blk.x, (g.n[1] + blk.y - 1) / blk.y, g.n[2]);
-    k_jv64_a<D, EL><<<grd, blk, 0, st>>>(g, c, part, v, dG, sig);
-    k_jv64_b<D, EL><<<grd, blk, 0, st>>>(g, c, part, mob, v, dG, sig, Jv, Jec, zsum);
+    const dim3 grd((g.n[0] + blk.x - 1) / blk.x, (g.n[1] + blk.y - 1) / blk.y, g.n[2] * bt.nb);
+    k_jv64_a<D, EL><<<grd, blk, 0, st>>>(g, c, bt, part, v, dG, sig);
+    k_jv64_b<D, EL><<<grd, blk, 0, st>>>(g, c, bt, isc, part, mob, v, dG, sig, Jv, Jec, zsum);
 }
 
 template <int D, bool EL>
-static void launch_jv32_d(const DGrid &g, const JvConst &c, const float *part, const float *mob, const float *v,
-                          float *Jv, cudaStream_t st, const float *Jec, const double *zsum)
+static void launch_jv32_d(const DGrid &g, const JvConst &c, const Bat &bt, const double *isc, const float *part,
+                          const float *mob, const float *v, float *Jv, cudaStream_t st, const float *Jec,
+                          const double *zsum)
 {
     constexpr int TX = JvTile<D>::TX, TY = JvTile<D>::TY, TZ = JvTile<D>::TZ;
     const long long tiles = (long long)((g.n[0] + TX - 1) / TX) * ((g.n[1] + TY - 1) / TY) * ((g.n[2] + TZ - 1) / TZ);
-    k_jv32<D, EL><<<(unsigned)tiles, 256, 0, st>>>(g, c, part, mob, v, Jv, Jec, zsum);
+    k_jv32<D, EL><<<dim3((unsigned)tiles, bt.nb), 256, 0, st>>>(g, c, bt, isc, part, mob, v, Jv, Jec, zsum);
 }
 
 #define NKS_JV_DISPATCH(FN, ...)                                  \
@@ -689,38 +757,33 @@ static void launch_jv32_d(const DGrid &g, const JvConst &c, const float *part, c
     default: FN<3, true>(__VA_ARGS__); break;                     \
     }
 
-int launch_jv64(const DGrid &g, const DCoef &k, double dt, int mode, const double *part, const double *mob,
-                const double *v, double *dG, double *sig, double *Jv, cudaStream_t st, const double *Jec,
-                const double *zsum)
+int launch_jv64(const DGrid &g, const DCoef &k, const double *isc, int mode, const double *part, const double *mob,
+                const double *v, double *dG, double *sig, double *Jv, cudaStream_t st, const Bat &bt,
+                const double *Jec, const double *zsum)
 {
-    const JvConst c = jv_const(g, k, dt, mode);
-    NKS_JV_DISPATCH(launch_jv64_d, g, c, part, mob, v, dG, sig, Jv, st, Jec, zsum);
+    const JvConst c = jv_const(g, k, mode);
+    NKS_JV_DISPATCH(launch_jv64_d, g, c, bt, isc, part, mob, v, dG, sig, Jv, st, Jec, zsum);
     return 2;
 }
 
-int launch_jv32(const DGrid &g, const DCoef &k, double dt, int mode, const float *part, const float *mob,
-                const float *v, float *Jv, cudaStream_t st, const float *Jec, const double *zsum)
+int launch_jv32(const DGrid &g, const DCoef &k, const double *isc, int mode, const float *part, const float *mob,
+                const float *v, float *Jv, cudaStream_t st, const Bat &bt, const float *Jec, const double *zsum)
 {
-    const JvConst c = jv_const(g, k, dt, mode);
-    NKS_JV_DISPATCH(launch_jv32_d, g, c, part, mob, v, Jv, st, Jec, zsum);
+    const JvConst c = jv_const(g, k, mode);
+    NKS_JV_DISPATCH(launch_jv32_d, g, c, bt, isc, part, mob, v, Jv, st, Jec, zsum);
     return 1;
 }
 
-int launch_jv(const DGrid &g, const DCoef &k, double dt, int mode, const double *part, const double *mob,
-              const double *v, double *dG, double *sig, double *Jv, cudaStream_t st)
+int launch_energy(const DGrid &g, const DCoef &k, const double *isc, const double *X, double *partials, int rb,
+                  cudaStream_t st, const Bat &bt)
 {
-    return launch_jv64(g, k, dt, mode, part, mob, v, dG, sig, Jv, st, nullptr, nullptr);
-}
-
-int launch_energy(const DGrid &g, const DCoef &k, const double *X, double *partials, cudaStream_t st)
-{
-    k_energy<<<kRedBlocks, kRedThreads, 0, st>>>(g, k, X, partials);
+    k_energy<<<dim3(rb, bt.nb), kRedThreads, 0, st>>>(g, k, bt, isc, X, partials);
     return 1;
 }
 
-int launch_finalize(const double *partials, int nblocks, int K, double *out, cudaStream_t st)
+int launch_finalize(const double *partials, int nblocks, int K, double *out, cudaStream_t st, const Bat &bt)
 {
-    k_finalize<<<1, kRedThreads, 0, st>>>(partials, nblocks, K, out);
+    k_finalize<<<bt.nb, kRedThreads, 0, st>>>(bt, partials, nblocks, K, out);
     return 1;
 }
 
