@@ -320,6 +320,73 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_batch(args):
+    """--batch B: B instances of the workload (seeds seed, seed + 1, ...) stepped as
+    one batch (one launch per solver phase, GMRES iterations replayed from CUDA
+    graphs), beside the same workload stepped alone; one JSON line."""
+    import torch
+    import paper_2209_08001_gb300 as nks
+    import __graft_entry__ as g
+    g.build()
+    torch.cuda.set_device(0)
+    cfg = S.CONFIGS[args.config]
+    op = S.options(**cfg["opts"])
+    if args.precision:
+        op["precision"] = args.precision
+    B = args.batch
+    fields = [S.initial_fields(cfg["dim"], cfg["n"], cfg["cbar"], cfg["seed"] + i) for i in range(B)]
+    c = np.stack([f[0] for f in fields])
+    e = np.stack([f[1] for f in fields])
+    N = c.shape[1]
+    stream = torch.cuda.current_stream()
+
+    def timed(run_steps, reset):
+        for _ in range(args.warmup):
+            run_steps()
+        reset()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            run_steps()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1), (time.perf_counter() - t0) * 1e3
+
+    Bt = nks.Batch(cfg["dim"], cfg["n"], cfg["h"], B, S.coefficients(), op, c=c, eta=e,
+                   allocator=nks.torch_allocator())
+    st0 = [Bt.get_state(i) for i in range(B)]
+    clocks = ClockSampler(0)
+    clocks.start()
+    ms_b, wall_b = timed(lambda: Bt.step(), lambda: [Bt.set_state(i, st0[i]) for i in range(B)])
+    clk = clocks.stop()
+    stats = Bt.get_stats()
+    P = nks.Problem(cfg["dim"], cfg["n"], cfg["h"], c[0], e[0], S.coefficients(), op,
+                    allocator=nks.torch_allocator())
+    s1 = P.get_state()
+    ms_1, _ = timed(lambda: P.step(), lambda: P.set_state(s1))
+    value = B * N * args.steps / (wall_b / 1e3)
+    out = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": wall_b / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64" if op["precision"] == "fp64" else "f64+f32",
+           "data": "synthetic (seeded SplitMix64 initial fields, one seed per instance)",
+           "config": {"workload": "%d instances of: %s" % (B, cfg["desc"]), "batch": B, "precision": op["precision"],
+                      "grid": list(cfg["n"]), "points_per_instance": N,
+                      "timed_steps": "steps 1..K of every instance from its initial state",
+                      "l2": "small grids: the working set fits in L2 (latency- and launch-bound, no HBM fraction)"},
+           "device_ms_per_step": ms_b / args.steps,
+           "single_instance": {"value": N * args.steps / (ms_1 / 1e3), "ms_per_step": ms_1 / args.steps},
+           "batch_speedup_over_single": (value / (N * args.steps / (ms_1 / 1e3))),
+           "gpu_launches": int(stats["kernel_launches"]),
+           "iterations": {"gmres_per_instance_step": stats["gmres_its"] / max(stats["steps"], 1),
+                          "newton_per_instance_step": stats["newton_its"] / max(stats["steps"], 1)},
+           "device_bytes": Bt.device_bytes(), "clocks": clk, "roofline": None}
+    Bt.destroy()
+    P.destroy()
+    print(json.dumps(out), flush=True)
+
+
 def run_probe(args):
     """Small fixed cases for profiling single kernels (ncu -k ...): 'gmres512' builds
     the 2-D 512^2 problem with 8x8 subdomains, overlap 2 (the 68x68 boxes of the
@@ -357,9 +424,13 @@ def main():
     ap.add_argument("--ref-gmres-per-step", type=float, default=1800.0)
     ap.add_argument("--ref-newton-per-step", type=float, default=6.0)
     ap.add_argument("--probe", default=None, choices=["gmres512"], help="small profiling case, no JSON bench line")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="B > 0: B instances of the workload stepped as one batch (beside one alone)")
     args = ap.parse_args()
     if args.probe:
         run_probe(args)
+    elif args.batch > 0 and args.impl == "ours":
+        run_batch(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -106,6 +106,9 @@ typedef struct {
  *   max_retries        divergence retries (dt /= sqrt 2, zeta *= 2) per step
  *   u0_rtol/atol/maxit initial mechanical equilibrium solve
  *   timing             1: record per-kernel CUDA-event times (nks_get_stats)
+ *   graphs             1: each GMRES iteration replays a CUDA graph captured on
+ *                      its first use (kernels of all batch slots and the read-back
+ *                      of the iteration's scalars); ignored when timing = 1
  */
 typedef struct {
     double newton_rtol, newton_atol;
@@ -124,6 +127,7 @@ typedef struct {
     double u0_rtol, u0_atol;
     int u0_maxit;
     int timing;
+    int graphs;
 } nks_opts;
 
 /* Optional device allocator (for example a framework's caching allocator).

@@ -51,7 +51,7 @@ class nks_opts(ctypes.Structure):
                 ("dt_init", ctypes.c_double), ("dt_min", ctypes.c_double), ("dt_max", ctypes.c_double),
                 ("zeta", ctypes.c_double), ("dt_mode", ctypes.c_int), ("zeta_persist", ctypes.c_int),
                 ("max_retries", ctypes.c_int), ("u0_rtol", ctypes.c_double), ("u0_atol", ctypes.c_double),
-                ("u0_maxit", ctypes.c_int), ("timing", ctypes.c_int)]
+                ("u0_maxit", ctypes.c_int), ("timing", ctypes.c_int), ("graphs", ctypes.c_int)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -200,7 +200,7 @@ def make_opts(op: dict, timing=False):
         if name in op:
             setattr(o, name, float(op[name]))
     for name in ("newton_maxit", "gmres_restart", "gmres_maxit", "overlap", "ilu_reuse", "zeta_persist",
-                 "max_retries", "u0_maxit"):
+                 "max_retries", "u0_maxit", "graphs"):
         if name in op:
             setattr(o, name, int(op[name]))
     if "sub" in op:

@@ -137,13 +137,18 @@ void Problem::upload_isc()
 
 // count doubles at dev0 (instance 0's address) of every instance -> hread[i * 64 + q],
 // and both flag words of every instance -> hflags[2 i + q]; synchronises
-int Problem::read_scalars(const double *dev0, int count, const char *where)
+void Problem::enqueue_readback(const double *dev0, int count)
 {
     if (dev0 && count > 0)
         cudaMemcpy2DAsync(hread, sizeof(double) * 64, dev0, (size_t)stride, sizeof(double) * count, (size_t)nb,
                           cudaMemcpyDeviceToHost, stream);
     cudaMemcpy2DAsync(hflags, sizeof(int) * 2, dflag, (size_t)stride, sizeof(int) * 2, (size_t)nb,
                       cudaMemcpyDeviceToHost, stream);
+}
+
+int Problem::read_scalars(const double *dev0, int count, const char *where)
+{
+    enqueue_readback(dev0, count);
     return sync_check(where);
 }
 
@@ -609,6 +614,7 @@ void nks_default_opts(nks_opts *o)
     o->u0_atol = 1e-13;
     o->u0_maxit = 10;
     o->timing = 0;
+    o->graphs = 1;
 }
 
 static int validate(const nks_grid *grid, const nks_coeffs *coeffs, const nks_opts *opts, int nb)
@@ -769,6 +775,7 @@ int nks_create_batch(const nks_grid *grid, int nb, const double *c, const double
         return NKS_ENOMEM;
     }
     for (size_t q = 0; q < items.size(); q++) *items[q].ptr = P->slab + off[q];
+    ras_prepare_launch(P);
     cudaMemsetAsync(P->slab, 0, (size_t)P->stride * nb, P->stream);
     cudaMemsetAsync(P->dmask, 0, sizeof(int) * kMasks * nb, P->stream);
     {
@@ -1037,6 +1044,7 @@ void nks_destroy(nks_problem *H)
     if (P->stream) cudaStreamSynchronize(P->stream);
     harvest_timers(P);
     destroy_timers(P);
+    destroy_graphs(P);
     ras_plan_destroy(P);
     P->dfree_all();
     if (P->hread) cudaFreeHost(P->hread);

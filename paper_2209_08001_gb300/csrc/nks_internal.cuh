@@ -213,6 +213,7 @@ struct SlabItem {
     size_t bytes;
 };
 void ras_slab_items(Problem *P, std::vector<SlabItem> &items);  // per-instance Schwarz buffers
+void ras_prepare_launch(Problem *P);                             // kernel attributes (before any capture)
 void ras_plan_destroy(Problem *P);
 // assemble J restricted + ILU(0) for the instances of bt (on: the same set on the host);
 // a zero pivot marks the instance failed in is[]
@@ -330,6 +331,14 @@ struct Problem {
 
     nks_stats stats{};
     TimerPool timers[NKS_NCLASS];
+    // captured GMRES iterations: [mode][j], with the counters one replay adds
+    struct IterGraph {
+        cudaGraphExec_t exec = nullptr;
+        long long kernels = 0;
+        long long launches[NKS_NCLASS] = {};
+    };
+    IterGraph graphs[2][kMaxRestart];
+    bool graphs_off = false;                    // a capture failed: launch directly
     std::string err;
 
     void *dalloc(size_t bytes);
@@ -341,6 +350,7 @@ struct Problem {
     void upload_isc();                                  // isc of every instance from is[]
     int read_scalars(const double *dev0, int count, const char *where);  // -> hread[b * 64 + i], hflags
     int read_flags(const char *where);                                   // -> hflags[2 b + q]
+    void enqueue_readback(const double *dev0, int count);                // the copies of read_scalars
     void count(int n) { stats.kernel_launches += n; }  // kernels launched on this problem
     void tick(int cls);                         // count a launch of class cls (and start a timer)
     void tock(int cls);                         // stop its timer
@@ -348,6 +358,7 @@ struct Problem {
 };
 
 int cuda_fail(Problem *P, cudaError_t e, const char *where);
+void destroy_graphs(Problem *P);
 DCoef derive_coefficients(const nks_coeffs &c, int dim, double cbar0);  // App. B reduction
 void set_thread_error(const char *msg);                                 // for nks_last_error(NULL)
 

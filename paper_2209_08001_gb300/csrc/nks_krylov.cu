@@ -506,6 +506,43 @@ struct Basis {
 static Basis<double> basis64(Problem *P) { return {P->V, P->W, P->Z, P->ldv}; }
 static Basis<float> basis32(Problem *P) { return {P->Vf, P->Wf, P->Zf, P->ldvf}; }
 
+// Replay the captured graph of GMRES iteration j (capturing it on first use).
+// Returns false when graphs are unavailable (the caller launches directly).
+template <class Fn>
+static bool run_graph(Problem *P, int mode, int j, Fn &&enqueue)
+{
+    Problem::IterGraph &G = P->graphs[mode & 1][j];
+    if (!G.exec) {
+        const nks_stats before = P->stats;
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(P->stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            enqueue();
+            e = cudaStreamEndCapture(P->stream, &graph);
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&G.exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        // the capture counted one replay's launches: keep them per graph instead
+        G.kernels = P->stats.kernel_launches - before.kernel_launches;
+        for (int c = 0; c < NKS_NCLASS; c++) G.launches[c] = P->stats.launches[c] - before.launches[c];
+        P->stats = before;
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            G.exec = nullptr;
+            P->graphs_off = true;
+            return false;
+        }
+    }
+    if (cudaGraphLaunch(G.exec, P->stream) != cudaSuccess) {
+        cudaGetLastError();
+        P->graphs_off = true;
+        return false;
+    }
+    P->stats.kernel_launches += G.kernels;
+    for (int c = 0; c < NKS_NCLASS; c++) P->stats.launches[c] += G.launches[c];
+    return true;
+}
+
 // Batched GMRES(m): every instance with is[i].gin runs its own Arnoldi process
 // (own Hessenberg matrix, own stopping test) in lockstep with the others; an
 // instance that has met its test is masked out of the remaining launches, so
@@ -521,6 +558,7 @@ static int gmres_t(Problem *P, Basis<TV> K, int mode, const double *b, double *x
     TV *V = K.V, *W = K.W, *Z = K.Z;
     double *R = P->R, *gm = P->gm, *Jx = P->T64;
     const int maxit = P->opts.gmres_maxit;
+    const bool use_graphs = P->opts.graphs && !P->opts.timing && !P->graphs_off;
     std::vector<char> in(nbt), cyc(nbt), act(nbt);
     for (int i = 0; i < nbt; i++) {
         in[i] = P->is[i].gin ? 1 : 0;
@@ -550,34 +588,44 @@ static int gmres_t(Problem *P, Basis<TV> K, int mode, const double *b, double *x
         k_scale_dev<double, TV><<<dim3(nb(n), nbt), kT, 0, st>>>(bc, n, R, gm + L.scal + S_INV, V);
         P->count(2);
         for (int j = 0; j < m; j++) {
-            TV *vj = V + (size_t)j * ldv, *vn = V + (size_t)(j + 1) * ldv;
-            ras_apply_t<TV>(P, vj, Z, ba);         // z = RAS^-1 v_j (sum of z_c to zsum)
-            apply_J<TV>(P, mode, Z, W, true, ba);  // w = J P z
-            // CGS pass 1 and 2
-            P->tick(4);
-            launch_multidot<TV>(j + 1, ldv, V, W, P->partials, nullptr, gm + L.hcol, P->tickets, P->rb, st, ba);
-            P->tock(4);
-            P->tick(5);
-            launch_update<TV>(j + 1, ldv, V, gm + L.hcol, W, P->partials, nullptr, gm + L.scal + S_WN,
-                              P->tickets + 1, P->rb, st, ba);
-            P->tock(5);
-            // optional second pass (CGS2), gated on the device
-            k_cgs_decide<<<nbt, 1, 0, st>>>(ba, gm, L, j);
-            const double *gate = gm + L.scal + S_FLAG;
-            P->tick(4);
-            launch_multidot<TV>(j + 1, ldv, V, W, P->partials, gate, gm + L.h2, P->tickets, P->rb, st, ba);
-            P->tock(4);
-            P->tick(5);
-            launch_update<TV>(j + 1, ldv, V, gm + L.h2, W, P->partials, gate, gm + L.scal + S_WN, P->tickets + 1,
-                              P->rb, st, ba);
-            P->tock(5);
-            k_cgs_accum<<<nbt, 1, 0, st>>>(ba, gm, L, j);
-            P->tick(9);
-            k_arnoldi<<<nbt, 1, 0, st>>>(ba, gm, L, j);
-            P->tock(9);
-            k_scale_dev<TV, TV><<<dim3(nb(n), nbt), kT, 0, st>>>(ba, n, W, gm + L.scal + S_INV, vn);
-            P->count(8);  // 2 multidot + 2 update + decide + accum + arnoldi + scale
-            rc = P->read_scalars(gm + L.scal, 8, "gmres");
+            // one Arnoldi step of every instance still iterating, then the read-back
+            // of its scalars (captured together when graphs are on)
+            auto iteration = [&](bool readback) {
+                TV *vj = V + (size_t)j * ldv, *vn = V + (size_t)(j + 1) * ldv;
+                ras_apply_t<TV>(P, vj, Z, ba);         // z = RAS^-1 v_j (sum of z_c to zsum)
+                apply_J<TV>(P, mode, Z, W, true, ba);  // w = J P z
+                // CGS pass 1 and 2
+                P->tick(4);
+                launch_multidot<TV>(j + 1, ldv, V, W, P->partials, nullptr, gm + L.hcol, P->tickets, P->rb, st, ba);
+                P->tock(4);
+                P->tick(5);
+                launch_update<TV>(j + 1, ldv, V, gm + L.hcol, W, P->partials, nullptr, gm + L.scal + S_WN,
+                                  P->tickets + 1, P->rb, st, ba);
+                P->tock(5);
+                // optional second pass (CGS2), gated on the device
+                k_cgs_decide<<<nbt, 1, 0, st>>>(ba, gm, L, j);
+                const double *gate = gm + L.scal + S_FLAG;
+                P->tick(4);
+                launch_multidot<TV>(j + 1, ldv, V, W, P->partials, gate, gm + L.h2, P->tickets, P->rb, st, ba);
+                P->tock(4);
+                P->tick(5);
+                launch_update<TV>(j + 1, ldv, V, gm + L.h2, W, P->partials, gate, gm + L.scal + S_WN,
+                                  P->tickets + 1, P->rb, st, ba);
+                P->tock(5);
+                k_cgs_accum<<<nbt, 1, 0, st>>>(ba, gm, L, j);
+                P->tick(9);
+                k_arnoldi<<<nbt, 1, 0, st>>>(ba, gm, L, j);
+                P->tock(9);
+                k_scale_dev<TV, TV><<<dim3(nb(n), nbt), kT, 0, st>>>(ba, n, W, gm + L.scal + S_INV, vn);
+                P->count(8);  // 2 multidot + 2 update + decide + accum + arnoldi + scale
+                if (readback) P->enqueue_readback(gm + L.scal, 8);
+            };
+            if (use_graphs && run_graph(P, mode, j, [&] { iteration(true); })) {
+                rc = P->sync_check("gmres");
+            } else {
+                iteration(false);
+                rc = P->read_scalars(gm + L.scal, 8, "gmres");
+            }
             if (rc) return rc;
             bool changed = false, left = false;
             for (int i = 0; i < nbt; i++) {
@@ -625,6 +673,16 @@ static int gmres_t(Problem *P, Basis<TV> K, int mode, const double *b, double *x
             return NKS_ETIMEOUT;
         }
     return NKS_OK;
+}
+
+void destroy_graphs(Problem *P)
+{
+    for (auto &row : P->graphs)
+        for (auto &G : row)
+            if (G.exec) {
+                cudaGraphExecDestroy(G.exec);
+                G.exec = nullptr;
+            }
 }
 
 int gmres_solve(Problem *P, int mode, const double *b, double *x)

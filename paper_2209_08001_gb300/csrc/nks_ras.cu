@@ -837,6 +837,27 @@ void launch_factor(Problem *P, int mode, const Bat &bt)
                                                 P->mob, R->fac, P->dflag);
 }
 
+// the sweep kernel's dynamic shared memory limit (set once, before any graph capture)
+template <int D, int NF, typename TV>
+void apply_attr(Problem *P)
+{
+    RasPlan *R = P->ras;
+    constexpr bool f32 = sizeof(TV) == sizeof(float);
+    const size_t smem = f32 ? R->smem_bytes32 : R->smem_bytes;
+    bool &attr = f32 ? R->attr_set32 : R->attr_set;
+    if (smem > 48 * 1024 && !attr) {
+        cudaFuncSetAttribute(k_ras_apply<D, NF, TV, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
+}
+
+template <int D, int NF>
+void apply_attrs(Problem *P)
+{
+    apply_attr<D, NF, double>(P);
+    if (P->opts.precision == NKS_MIXED) apply_attr<D, NF, float>(P);
+}
+
 // FP64 vectors use the FP64 factors; FP32 vectors (mixed precision) the FP32 copy
 template <int D, int NF, typename TV>
 void launch_apply_t(Problem *P, const TV *r, TV *z, const Bat &bt)
@@ -849,11 +870,7 @@ void launch_apply_t(Problem *P, const TV *r, TV *z, const Bat &bt)
     constexpr bool f32 = sizeof(TV) == sizeof(float);
     using T = TV;
     const size_t smem = f32 ? R->smem_bytes32 : R->smem_bytes;
-    bool &attr = f32 ? R->attr_set32 : R->attr_set;
-    if (smem > 48 * 1024 && !attr) {
-        cudaFuncSetAttribute(k_ras_apply<D, NF, T, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
-    }
+    apply_attr<D, NF, TV>(P);
     const T *fac = f32 ? reinterpret_cast<const T *>(R->fac32) : reinterpret_cast<const T *>(R->fac);
     T *scr = f32 ? reinterpret_cast<T *>(R->scratch32) : reinterpret_cast<T *>(R->scratch);
     const int xs = f32 ? R->x_smem32 : R->x_smem;
@@ -956,6 +973,8 @@ void ras_apply_projected(Problem *P, const TV *r, TV *z, const Bat &bt)
     project_t<TV>(P, z, bt);
 }
 template void ras_apply_projected<float>(Problem *, const float *, float *, const Bat &);
+
+void ras_prepare_launch(Problem *P) { NKS_DISPATCH(apply_attrs, P); }
 
 // per-instance buffers of the Schwarz preconditioner (carved from each instance's slab)
 void ras_slab_items(Problem *P, std::vector<SlabItem> &items)
