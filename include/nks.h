@@ -281,6 +281,85 @@ int nks_batch_set_state(nks_problem *p, int slot, const void *buf, size_t bytes)
 size_t nks_device_bytes(const nks_problem *p);
 
 /* ------------------------------------------------------------------------ */
+/* Serving: a request loop for many simulations on one GPU (no counterpart   */
+/* in the paper).  Requests of the same grid shape share one batch (above)   */
+/* with a fixed number of slots, a CUDA stream and a worker thread; between  */
+/* two batch steps the worker loads newly admitted requests into free slots, */
+/* steps every occupied slot, and retires finished requests (continuous      */
+/* batching).  Shape groups run concurrently, so their kernels overlap on    */
+/* the device.  Admission is by device memory: a group reserves slots x the  */
+/* measured bytes of one slot out of mem_budget and returns them when it     */
+/* empties.  Each result is bitwise the result of the request run alone.     */
+/* Thread-safe: submit and wait may be called from any host threads.         */
+/* ------------------------------------------------------------------------ */
+
+typedef struct nks_server nks_server;
+
+typedef struct {
+    nks_opts opts;         /* solver options of every request (sub is set per shape) */
+    size_t mem_budget;     /* device bytes for all batches; 0: 80% of the free memory */
+    int max_slots;         /* slots per shape group */
+    int max_groups;        /* shape groups alive at once (worker threads / streams) */
+    int box_side_2d;       /* owned Schwarz box side for 2-D (and 4x for 1-D) grids */
+    int box_side_3d;       /* owned Schwarz box side for 3-D grids */
+} nks_server_opts;
+
+typedef struct {
+    long long id;
+    int status;            /* NKS_OK or the failure code of the request */
+    int steps;             /* steps completed */
+    int newton_its, gmres_its, retries;   /* summed over the steps */
+    long long points;      /* grid points */
+    double t_submit, t_admit, t_done;     /* seconds since nks_server_create */
+    double t, energy, mass;               /* after the last step */
+} nks_request_result;
+
+typedef struct {
+    int waiting;           /* submitted, not yet in a group */
+    int groups;            /* live shape groups */
+    int in_flight;         /* requests in groups (loaded or queued) */
+    size_t bytes_reserved, mem_budget;
+} nks_server_state;
+
+/* mixed precision, energy-driven dt, 16 slots, 8 groups, boxes 32 (2-D) / 16 (3-D) */
+void nks_server_default_opts(nks_server_opts *o);
+int nks_server_create(const nks_coeffs *coeffs, const nks_server_opts *opts, nks_server **out);
+
+/* Queue a request: grid, initial fields (HOST, N doubles each; copied),
+ * number of time steps (adaptive dt).  Never blocks on the GPU work. */
+int nks_server_submit(nks_server *s, const nks_grid *grid, const double *c, const double *eta, int steps,
+                      long long *id);
+
+/* Wait for a request (timeout_s < 0: no limit; NKS_ETIMEOUT on expiry), copy its
+ * result and final fields (c, eta: N doubles, u: d N doubles; any may be NULL)
+ * and release it. */
+int nks_server_wait(nks_server *s, long long id, nks_request_result *res, double *c, double *eta, double *u,
+                    double timeout_s);
+
+int nks_server_status(nks_server *s, nks_server_state *st);
+
+/* Finish every submitted request, stop the workers, free everything. */
+void nks_server_destroy(nks_server *s);
+
+/* Autotuner of the Schwarz decomposition (no counterpart in the paper, which
+ * fixes it per experiment): for each candidate (owned-box counts per axis and
+ * overlap delta) a problem is created from c, eta (HOST, N doubles each) and
+ * base, one step of dt_trial is taken (it captures the iteration graphs), and
+ * the wall time of a second step is measured; best receives base with the
+ * fastest candidate's sub and overlap.
+ *   cands   ncand x 4 ints (sub_x, sub_y, sub_z, overlap), or NULL for the
+ *           built-in list: square / cubic owned boxes of side 16..128 (2-D) or
+ *           8..32 (3-D) that give at least two boxes per axis, overlap 1 and 2
+ *   times   seconds of each candidate's timed step (-1: rejected or failed),
+ *           as many entries as candidates (the built-in list has at most 12);
+ *           may be NULL
+ *   chosen  index of the chosen candidate, may be NULL
+ * Returns NKS_OK, NKS_EINVAL, or NKS_EDIVERGED when every candidate failed. */
+int nks_autotune(const nks_grid *grid, const double *c, const double *eta, const nks_coeffs *coeffs,
+                 const nks_opts *base, const int *cands, int ncand, double dt_trial, nks_opts *best, double *times,
+                 int *chosen);
+
+/* ------------------------------------------------------------------------ */
 /* Operator-level entry points (the stages of one Newton iteration).         */
 /* They use the problem's grid, coefficients and decomposition and leave its */
 /* state untouched.  All arrays are HOST state arrays of length nf*N.        */

@@ -54,6 +54,27 @@ class nks_opts(ctypes.Structure):
                 ("u0_maxit", ctypes.c_int), ("timing", ctypes.c_int), ("graphs", ctypes.c_int)]
 
 
+class nks_server_opts(ctypes.Structure):
+    _fields_ = [("opts", nks_opts), ("mem_budget", ctypes.c_size_t), ("max_slots", ctypes.c_int),
+                ("max_groups", ctypes.c_int), ("box_side_2d", ctypes.c_int), ("box_side_3d", ctypes.c_int)]
+
+
+class nks_request_result(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_longlong), ("status", ctypes.c_int), ("steps", ctypes.c_int),
+                ("newton_its", ctypes.c_int), ("gmres_its", ctypes.c_int), ("retries", ctypes.c_int),
+                ("points", ctypes.c_longlong), ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_done", ctypes.c_double), ("t", ctypes.c_double), ("energy", ctypes.c_double),
+                ("mass", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class nks_server_state(ctypes.Structure):
+    _fields_ = [("waiting", ctypes.c_int), ("groups", ctypes.c_int), ("in_flight", ctypes.c_int),
+                ("bytes_reserved", ctypes.c_size_t), ("mem_budget", ctypes.c_size_t)]
+
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -143,6 +164,17 @@ def load():
         "nks_batch_get_state": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_size_t]),
         "nks_batch_set_state": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_size_t]),
         "nks_device_bytes": (ctypes.c_size_t, [_P]),
+        "nks_server_default_opts": (None, [ctypes.POINTER(nks_server_opts)]),
+        "nks_server_create": (ctypes.c_int, [ctypes.POINTER(nks_coeffs), ctypes.POINTER(nks_server_opts), pp]),
+        "nks_server_submit": (ctypes.c_int, [_P, ctypes.POINTER(nks_grid), _D, _D, ctypes.c_int,
+                                             ctypes.POINTER(ctypes.c_longlong)]),
+        "nks_server_wait": (ctypes.c_int, [_P, ctypes.c_longlong, ctypes.POINTER(nks_request_result), _D, _D, _D,
+                                           ctypes.c_double]),
+        "nks_server_status": (ctypes.c_int, [_P, ctypes.POINTER(nks_server_state)]),
+        "nks_server_destroy": (None, [_P]),
+        "nks_autotune": (ctypes.c_int, [ctypes.POINTER(nks_grid), _D, _D, ctypes.POINTER(nks_coeffs),
+                                        ctypes.POINTER(nks_opts), ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                        ctypes.c_double, ctypes.POINTER(nks_opts), _D, ctypes.POINTER(ctypes.c_int)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -160,7 +192,8 @@ def exported_symbols():
             "nks_linear_solve", "nks_eval_energy", "nks_residual_noalloc", "nks_create_batch", "nks_batch_size",
             "nks_batch_load", "nks_batch_unload", "nks_batch_loaded", "nks_batch_step", "nks_batch_energy",
             "nks_batch_mass", "nks_batch_get_fields", "nks_batch_get_state", "nks_batch_set_state",
-            "nks_device_bytes"]
+            "nks_device_bytes", "nks_autotune", "nks_server_default_opts", "nks_server_create",
+            "nks_server_submit", "nks_server_wait", "nks_server_status", "nks_server_destroy"]
 
 
 def _ptr(a):
@@ -436,6 +469,91 @@ class Batch:
 
     def device_bytes(self):
         return int(load().nks_device_bytes(self._h))
+
+
+def autotune(dim, n, h, c, eta, coeffs: dict, opts: dict, candidates=None, dt_trial=0.01):
+    """Pick the Schwarz decomposition (sub, overlap) with the shortest time step
+    (nks_autotune).  candidates: list of (sub tuple, overlap) or None for the
+    built-in list.  Returns (opts dict with the choice, [(sub, overlap, seconds)])."""
+    L = load()
+    g, k, o = make_grid(dim, n, h), make_coeffs(coeffs), make_opts(opts)
+    c, eta = _c64(c), _c64(eta)
+    if candidates is not None:
+        flat = []
+        for sub, ov in candidates:
+            sub = list(sub) + [1] * (3 - len(sub))
+            flat += [int(sub[0]), int(sub[1]), int(sub[2]), int(ov)]
+        arr = (ctypes.c_int * len(flat))(*flat)
+        cp, nc = ctypes.cast(arr, ctypes.POINTER(ctypes.c_int)), len(candidates)
+    else:
+        cp, nc = None, 0
+    best = nks_opts()
+    times = np.full(max(nc, 64), -1.0)
+    chosen = ctypes.c_int(-1)
+    _check(L.nks_autotune(ctypes.byref(g), _ptr(c), _ptr(eta), ctypes.byref(k), ctypes.byref(o), cp, nc,
+                          float(dt_trial), ctypes.byref(best), _ptr(times), ctypes.byref(chosen)), None)
+    out = dict(opts)
+    out["sub"] = tuple(best.sub[J] for J in range(dim))
+    out["overlap"] = best.overlap
+    if candidates is not None:
+        table = [(tuple(sub), ov, float(times[i])) for i, (sub, ov) in enumerate(candidates)]
+    else:
+        table = [(None, None, float(t)) for t in times if t != -1.0]
+    return out, table, chosen.value
+
+
+class Server:
+    """Request loop for many simulations on the current device (nks_server_*):
+    same-shape requests share a batch, admitted into free slots between batch
+    steps; shape groups run on their own streams and worker threads."""
+
+    def __init__(self, coeffs: dict, opts: dict = None, mem_budget=0, max_slots=16, max_groups=8, box_side_2d=32,
+                 box_side_3d=16):
+        L = load()
+        so = nks_server_opts()
+        L.nks_server_default_opts(ctypes.byref(so))
+        if opts:
+            so.opts = make_opts(dict(opts))
+        so.mem_budget = int(mem_budget)
+        so.max_slots, so.max_groups = int(max_slots), int(max_groups)
+        so.box_side_2d, so.box_side_3d = int(box_side_2d), int(box_side_3d)
+        self._coeffs = make_coeffs(coeffs)
+        h = ctypes.c_void_p()
+        _check(L.nks_server_create(ctypes.byref(self._coeffs), ctypes.byref(so), ctypes.byref(h)), None)
+        self._h = h
+        self._shape = {}
+
+    def submit(self, dim, n, h, c, eta, steps):
+        g = make_grid(dim, n, h)
+        c, eta = _c64(c), _c64(eta)
+        rid = ctypes.c_longlong()
+        _check(load().nks_server_submit(self._h, ctypes.byref(g), _ptr(c), _ptr(eta), int(steps), ctypes.byref(rid)),
+               None)
+        self._shape[rid.value] = (dim, int(np.prod(n[:dim])))
+        return rid.value
+
+    def wait(self, rid, timeout=-1.0):
+        """(result dict, (c, eta, u)) of a finished request."""
+        dim, N = self._shape.pop(rid)
+        c, eta, u = np.empty(N), np.empty(N), np.empty((dim, N))
+        r = nks_request_result()
+        _check(load().nks_server_wait(self._h, int(rid), ctypes.byref(r), _ptr(c), _ptr(eta), _ptr(u),
+                                      float(timeout)), None)
+        return r.as_dict(), (c, eta, u)
+
+    def status(self):
+        st = nks_server_state()
+        _check(load().nks_server_status(self._h, ctypes.byref(st)), None)
+        return {k: getattr(st, k) for k, _ in st._fields_}
+
+    def destroy(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            load().nks_server_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        self.destroy()
 
 
 NOALLOC_MAX_POINTS = 65536

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libnks.so")
-SOURCES = ["nks_stencil.cu", "nks_krylov.cu", "nks_ras.cu", "nks_api.cu", "nks_noalloc.cu"]
+SOURCES = ["nks_stencil.cu", "nks_krylov.cu", "nks_ras.cu", "nks_api.cu", "nks_noalloc.cu", "nks_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
          "-I", CSRC]

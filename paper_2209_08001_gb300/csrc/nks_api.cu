@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
 #include <string>
 
 #include "nks_internal.cuh"
@@ -1202,6 +1203,86 @@ int nks_eval_energy(nks_problem *H, const double *X, double *parts, double *mass
     }
     harvest_timers(P);
     return rc;
+}
+
+// ---------------------------------------------------------------------------
+// autotuner of the Schwarz decomposition
+// ---------------------------------------------------------------------------
+
+// built-in candidates: owned boxes of side b per axis (squares / cubes) with
+// overlap 1 or 2, for the sides that give at least two boxes per axis
+static std::vector<int> default_candidates(const nks_grid *g)
+{
+    static const int sides2[] = {16, 24, 32, 48, 64, 128};
+    static const int sides3[] = {8, 12, 16, 24, 32};
+    std::vector<int> out;
+    const int *sides = g->dim == 3 ? sides3 : sides2;
+    const int ns = g->dim == 3 ? 5 : 6;
+    int nmin = g->n[0];
+    for (int J = 1; J < g->dim; J++) nmin = std::min(nmin, g->n[J]);
+    for (int q = 0; q < ns; q++) {
+        const int b = g->dim == 1 ? sides[q] * 4 : sides[q];
+        if (2 * b > nmin) continue;
+        for (int ov = 1; ov <= 2; ov++) {
+            int sub[3] = {1, 1, 1};
+            for (int J = 0; J < g->dim; J++) sub[J] = std::max(1, (g->n[J] + b / 2) / b);
+            out.insert(out.end(), {sub[0], sub[1], sub[2], ov});
+        }
+    }
+    return out;
+}
+
+int nks_autotune(const nks_grid *grid, const double *c, const double *eta, const nks_coeffs *coeffs,
+                 const nks_opts *base, const int *cands, int ncand, double dt_trial, nks_opts *best, double *times,
+                 int *chosen)
+{
+    g_create_error.clear();
+    if (!grid || !c || !eta || !coeffs || !base || !best || !(dt_trial > 0.0) || (cands && ncand < 1)) {
+        g_create_error = "nks_autotune: invalid argument";
+        return NKS_EINVAL;
+    }
+    std::vector<int> list = cands ? std::vector<int>(cands, cands + 4 * ncand) : default_candidates(grid);
+    const int nc = (int)list.size() / 4;
+    if (nc == 0) {
+        g_create_error = "nks_autotune: no candidate decomposition fits this grid";
+        return NKS_EINVAL;
+    }
+    double best_t = -1.0;
+    int best_q = -1;
+    for (int q = 0; q < nc; q++) {
+        nks_opts o = *base;
+        for (int J = 0; J < 3; J++) o.sub[J] = list[4 * q + J];
+        o.overlap = list[4 * q + 3];
+        o.timing = 0;
+        double t = -1.0;
+        nks_problem *H = nullptr;
+        if (nks_create_problem(grid, c, eta, coeffs, &o, nullptr, nullptr, &H) == NKS_OK) {
+            // the first step captures the iteration graphs; the second is timed
+            nks_step_info info{};
+            if (nks_step(H, dt_trial, &info) == NKS_OK) {
+                const auto t0 = std::chrono::steady_clock::now();
+                const int rc = nks_step(H, dt_trial, &info);
+                const auto t1 = std::chrono::steady_clock::now();
+                if (rc == NKS_OK) t = std::chrono::duration<double>(t1 - t0).count();
+            }
+            nks_destroy(H);
+        }
+        cudaGetLastError();
+        if (times) times[q] = t;
+        if (t > 0.0 && (best_q < 0 || t < best_t)) {
+            best_t = t;
+            best_q = q;
+        }
+    }
+    if (best_q < 0) {
+        g_create_error = "nks_autotune: every candidate failed";
+        return NKS_EDIVERGED;
+    }
+    *best = *base;
+    for (int J = 0; J < 3; J++) best->sub[J] = list[4 * best_q + J];
+    best->overlap = list[4 * best_q + 3];
+    if (chosen) *chosen = best_q;
+    return NKS_OK;
 }
 
 }  // extern "C"

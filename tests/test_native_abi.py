@@ -38,15 +38,19 @@ def test_struct_layouts_match_header(tmp_path, lib):
     import paper_2209_08001_gb300 as nks
     prog = tmp_path / "sizes.c"
     prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "nks.h"\n'
-                    'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(nks_grid), '
-                    'sizeof(nks_coeffs), sizeof(nks_opts), sizeof(nks_step_info), sizeof(nks_stats), '
-                    'sizeof(nks_allocator), offsetof(nks_opts, timing), offsetof(nks_coeffs, S));return 0;}\n')
+                    'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", '
+                    'sizeof(nks_grid), sizeof(nks_coeffs), sizeof(nks_opts), sizeof(nks_step_info), '
+                    'sizeof(nks_stats), sizeof(nks_allocator), offsetof(nks_opts, timing), offsetof(nks_coeffs, S), '
+                    'offsetof(nks_opts, graphs), sizeof(nks_server_opts), sizeof(nks_request_result), '
+                    'sizeof(nks_server_state), offsetof(nks_request_result, t_submit));return 0;}\n')
     exe = tmp_path / "sizes"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
     got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
     want = [ctypes.sizeof(nks.nks_grid), ctypes.sizeof(nks.nks_coeffs), ctypes.sizeof(nks.nks_opts),
             ctypes.sizeof(nks.nks_step_info), ctypes.sizeof(nks.nks_stats), ctypes.sizeof(nks.nks_allocator),
-            nks.nks_opts.timing.offset, nks.nks_coeffs.S.offset]
+            nks.nks_opts.timing.offset, nks.nks_coeffs.S.offset, nks.nks_opts.graphs.offset,
+            ctypes.sizeof(nks.nks_server_opts), ctypes.sizeof(nks.nks_request_result),
+            ctypes.sizeof(nks.nks_server_state), nks.nks_request_result.t_submit.offset]
     assert got == want
 
 
