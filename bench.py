@@ -190,6 +190,15 @@ def run_ours(args):
     seed = cfg["seed"] + 1000 * rank  # independent replica per rank
     c, e = S.initial_fields(cfg["dim"], cfg["n"], cfg["cbar"], seed)
     N = c.size
+    tuned = None
+    if args.autotune:
+        # owned box sides 8..16 (3-D) or 32..128 (2-D), overlap 1 and 2; one timed step each
+        sides = (8, 12, 16) if cfg["dim"] == 3 else (32, 64, 128)
+        cands = [(tuple(max(2, (nn + b // 2) // b) for nn in cfg["n"]), ov) for b in sides for ov in (1, 2)]
+        op, table, chosen = nks.autotune(cfg["dim"], cfg["n"], cfg["h"], c, e, S.coefficients(), op,
+                                         candidates=cands, dt_trial=op["dt_init"])
+        tuned = {"candidates": [{"sub": list(sb), "overlap": ov, "step_s": t} for sb, ov, t in table],
+                 "chosen": {"sub": list(op["sub"]), "overlap": op["overlap"]}}
     stream = torch.cuda.current_stream()
     alloc = nks.torch_allocator()
     P = nks.Problem(cfg["dim"], cfg["n"], cfg["h"], c, e, S.coefficients(), op, stream=stream.cuda_stream,
@@ -274,11 +283,13 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f64" if op["precision"] == "fp64" else "f64+f32",
         "data": "synthetic (seeded SplitMix64 initial fields)",
         "config": {"workload": cfg["desc"], "precision": op["precision"], "grid": list(cfg["n"]), "points": N,
+                   "decomposition": {"sub": list(op["sub"]), "overlap": op["overlap"]},
                    "steps_in_workload": cfg["steps"],
                    "timed_steps": "steps 1..K of the workload from its initial state",
                    "l2": "working set (state, Krylov basis, ~0.65 GB of Schwarz factors) far above the 129 MB L2",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "gpu_launches": None,
+        "autotune": tuned,
         "roofline": roof,
         "kernel_time_share": breakdown,
         "iterations": {"newton_per_step": st["newton_its"] / max(st["steps"], 1),
@@ -387,6 +398,80 @@ def run_batch(args):
     print(json.dumps(out), flush=True)
 
 
+def run_serve(args):
+    """--serve: the serving workload.  Requests from the synthetic stream (2-D grids
+    64^2..512^2 or 3-D 32^3..96^3, log-uniform sides, mean composition U(0.10,
+    0.25), mixed precision, adaptive dt) go through the native request loop.  A
+    closed-loop pass over the first requests measures the saturated request
+    rate; the timed pass submits every request at its Poisson arrival time with
+    rate 0.8 x that, and reports p50 / p99 time-to-completion and the aggregate
+    point-steps/s (points x steps of all requests / makespan)."""
+    import threading
+    import torch
+    import paper_2209_08001_gb300 as nks
+    import __graft_entry__ as g
+    g.build()
+    torch.cuda.set_device(0)
+    op = S.options(precision=args.precision or "mixed", dt_mode="energy", overlap=1)
+    R, steps = args.requests, args.req_steps
+
+    def stream_run(reqs, rate):
+        srv = nks.Server(S.coefficients(), op, max_slots=args.slots, max_groups=args.groups)
+        ids = {}
+        t0 = time.perf_counter()
+
+        def feeder():
+            for r in reqs:
+                if rate > 0:
+                    dt = r["arrival"] - (time.perf_counter() - t0)
+                    if dt > 0:
+                        time.sleep(dt)
+                c, e = S.initial_fields(r["dim"], r["n"], r["cbar"], r["seed"])
+                ids[r["id"]] = srv.submit(r["dim"], r["n"], r["h"], c, e, steps)
+
+        th = threading.Thread(target=feeder)
+        th.start()
+        th.join()
+        res = [srv.wait(ids[r["id"]])[0] for r in reqs]
+        wall = time.perf_counter() - t0
+        srv.destroy()
+        return res, wall
+
+    base = S.serving_requests(count=R, seed=4, rate=1.0)
+    # saturated rate: the first requests all at once
+    nsat = min(R, max(8, R // 4))
+    sat, wall_sat = stream_run(base[:nsat], 0.0)
+    span = max(r["t_done"] for r in sat) - min(r["t_submit"] for r in sat)
+    rate_sat = nsat / max(span, 1e-9)
+    rate = 0.8 * rate_sat
+    reqs = S.serving_requests(count=R, seed=4, rate=rate)
+    clocks = ClockSampler(0)
+    clocks.start()
+    res, wall = stream_run(reqs, rate)
+    clk = clocks.stop()
+    lat = np.array([r["t_done"] - r["t_submit"] for r in res])
+    qwait = np.array([r["t_admit"] - r["t_submit"] for r in res])
+    bad = sum(1 for r in res if r["status"] != 0)
+    t_first = min(r["t_submit"] for r in res)
+    makespan = max(r["t_done"] for r in res) - t_first
+    pts = float(sum(r["points"] * r["steps"] for r in res))
+    out = {"metric": "serving p50/p99 time-to-completion; aggregate point-steps/s", "value": pts / makespan,
+           "unit": METRIC, "n_gpus": 1, "steps": steps, "warmup": 0, "ms_per_step": None, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32" if op["precision"] == "mixed" else "f64",
+           "data": "synthetic request stream (seeded; Poisson arrivals)",
+           "config": {"workload": "%d requests, %d adaptive steps each: 2-D 64^2..512^2 or 3-D 32^3..96^3 "
+                                  "(log-uniform sides, multiples of 16), cbar ~ U(0.10, 0.25), %s precision"
+                                  % (R, steps, op["precision"]),
+                      "requests": R, "steps_per_request": steps, "slots_per_group": args.slots,
+                      "groups": args.groups},
+           "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                         "mean": float(lat.mean()), "max": float(lat.max())},
+           "queue_wait_s": {"p50": float(np.percentile(qwait, 50)), "p99": float(np.percentile(qwait, 99))},
+           "arrival_rate_req_s": rate, "saturated_rate_req_s": rate_sat, "makespan_s": makespan,
+           "failed_requests": bad, "clocks": clk, "roofline": None}
+    print(json.dumps(out), flush=True)
+
+
 def run_probe(args):
     """Small fixed cases for profiling single kernels (ncu -k ...): 'gmres512' builds
     the 2-D 512^2 problem with 8x8 subdomains, overlap 2 (the 68x68 boxes of the
@@ -426,11 +511,20 @@ def main():
     ap.add_argument("--probe", default=None, choices=["gmres512"], help="small profiling case, no JSON bench line")
     ap.add_argument("--batch", type=int, default=0,
                     help="B > 0: B instances of the workload stepped as one batch (beside one alone)")
+    ap.add_argument("--serve", action="store_true", help="the serving workload (p50/p99 latency, throughput)")
+    ap.add_argument("--autotune", action="store_true",
+                    help="pick the Schwarz decomposition with nks_autotune before timing")
+    ap.add_argument("--requests", type=int, default=64, help="--serve: requests in the stream")
+    ap.add_argument("--req-steps", type=int, default=10, help="--serve: time steps per request")
+    ap.add_argument("--slots", type=int, default=16, help="--serve: slots per shape group")
+    ap.add_argument("--groups", type=int, default=8, help="--serve: shape groups alive at once")
     args = ap.parse_args()
     if args.probe:
         run_probe(args)
     elif args.batch > 0 and args.impl == "ours":
         run_batch(args)
+    elif args.serve and args.impl == "ours":
+        run_serve(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

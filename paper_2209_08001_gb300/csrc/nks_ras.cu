@@ -5,7 +5,7 @@
 // the whole time step.  Here one overlapping subdomain is one thread block:
 //
 //   * plan (host, once): per subdomain the overlapped box, its owned part and
-//     its wavefront levels lv = x + 2y + 4z, which order every lower
+//     its wavefront levels lv = x + 2y + 3z, which order every lower
 //     neighbour of a point (every column left of the diagonal in the exact
 //     Jacobian pattern, x-fastest point-interleaved numbering) before the
 //     point itself;
@@ -114,6 +114,12 @@ static Pattern compile_time_pattern(int d, int nf)
 }
 
 __host__ __device__ static inline long long pad4(long long n) { return (n + 3) & ~3LL; }
+
+// Wavefront level of a box point.  Every lower neighbour of the stencil
+// (offsets (1,-1,0), (1,0,-1), (0,1,-1) and the axis offsets) must lie on an
+// earlier level, which the weights 1 < 2 < 3 give with the fewest levels; the
+// plan checks it against the pattern.
+__host__ __device__ static inline int wave(int x, int y, int z) { return x + 2 * y + 3 * z; }
 __host__ __device__ static inline size_t pad16(size_t n) { return (n + 15) & ~(size_t)15; }
 
 // dynamic shared memory of the apply kernel: barriers, point table, two level
@@ -154,7 +160,7 @@ int ras_plan_create(Problem *P, std::string &err)
     for (int f = 0; f < nf; f++)
         for (int a = 0; a < CP.diag[f]; a++) {
             const int i = CP.rowoff[f] + a;
-            const int lv = CP.dx[i] + 2 * CP.dy[i] + 4 * CP.dz[i];
+            const int lv = wave(CP.dx[i], CP.dy[i], CP.dz[i]);
             if (!((CP.dx[i] == 0 && CP.dy[i] == 0 && CP.dz[i] == 0) || lv < 0)) {
                 err = "internal: wavefront ordering";
                 return NKS_EINVAL;
@@ -248,7 +254,7 @@ int ras_plan_create(Problem *P, std::string &err)
                 si.npx = si.px * si.py * si.L[2];
                 R->maxnpx = std::max(R->maxnpx, si.npx);
                 R->total_np += si.np;
-                const int nlev = (si.L[0] - 1) + 2 * (si.L[1] - 1) + 4 * (si.L[2] - 1) + 1;
+                const int nlev = wave(si.L[0] - 1, si.L[1] - 1, si.L[2] - 1) + 1;
                 si.nlev = nlev;
                 si.lvl_off = (long long)lvl_ptr.size();
                 si.pos_off = (long long)lvl_lp.size();
@@ -257,7 +263,7 @@ int ras_plan_create(Problem *P, std::string &err)
                 for (int lz = 0; lz < si.L[2]; lz++)
                     for (int ly = 0; ly < si.L[1]; ly++)
                         for (int lx = 0; lx < si.L[0]; lx++)
-                            bylev[lx + 2 * ly + 4 * lz].push_back(lx | (ly << 10) | (lz << 20));
+                            bylev[wave(lx, ly, lz)].push_back(lx | (ly << 10) | (lz << 20));
                 int cnt = 0;
                 long long blk = 0;
                 for (int l = 0; l < nlev; l++) {
@@ -429,7 +435,7 @@ __global__ void k_ras_factor(DGrid g, DCoef k, Bat bt, const double *__restrict_
                     if (!inbox(si, nx, ny, nz)) continue;  // stays exactly 0
                     const int fk = o.w;
                     // level-major position of the earlier point (points of a level are stored in lp order)
-                    const int lv = nx + 2 * ny + 4 * nz;
+                    const int lv = wave(nx, ny, nz);
                     const int lpk = nx | (ny << 10) | (nz << 20);  // points of a level are stored in this key's order
                     int lo = lptr[lv], hi = lptr[lv + 1] - 1;
                     while (lo < hi) {
@@ -631,6 +637,7 @@ __global__ void __launch_bounds__(1024) k_ras_apply(DGrid g, Bat bt, const SubIn
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
     const int task = warp / wpt, kq0 = (warp % wpt) * 32 + lane;
+    const int nwb = min(4, (int)(blockDim.x >> 5));
     const int nuse = 2 * nlev;  // forward parts of levels 0..nlev-1, then backward parts of nlev-1..0
 
     // the copy of use `it` into buffer it & 1
@@ -682,9 +689,10 @@ __global__ void __launch_bounds__(1024) k_ras_apply(DGrid g, Bat bt, const SubIn
                 else stage_a<D, NF, false, T>(task, kq, lp, lx, ly, lz, B, cp, x, npx, pt, pstride, si, sy, sz);
             }
         __syncthreads();
-        // stage B: one thread per point
-        if (ok)
-            for (int k = tid; k < cnt; k += blockDim.x) {
+        // stage B: one thread per point, the points spread over the first four warps
+        // (one per SM sub-partition: their FP64 pipes run the row chains side by side)
+        if (ok && warp < nwb)
+            for (int k = lane * nwb + warp; k < cnt; k += 32 * nwb) {
                 const int pk = lps[base + k];
                 const int lx = pk & 1023, ly = (pk >> 10) & 1023, lz = pk >> 20;
                 const int lp = lx + sy * ly + sz * lz;
