@@ -38,7 +38,48 @@ METRIC = "point-steps/s"
 # FP64 FMA peak derived from the unit counts: 152 SMs x 2 FP64 FMA/clk x 2 FLOP x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM traffic per launch of the dominant kernels from an ncu capture (None once the kernel changed)
+# keyed by (workload, precision, kernel class)
 NCU_TRAFFIC = {}
+
+
+def kernel_rates(st, cfg, mixed, pk):
+    """Achieved rates per kernel class from the CUDA-event times of the timed steps:
+    HBM-bound classes against the measured copy bandwidth, FP64-bound ones against
+    the derived FP64 peak (algorithmic bytes / FLOPs per unit as in the design notes)."""
+    d = cfg["dim"]
+    N = float(np.prod(cfg["n"]))
+    f = 2 + d
+    b = 4.0 if mixed else 8.0
+    out = {}
+    hbm = pk.get("hbm_gbs")
+
+    def rate(cls, nbytes, nflops=None, bound="hbm"):
+        ms = st["ms"].get(cls, 0.0)
+        if ms <= 0 or nbytes <= 0:
+            return
+        gbs = nbytes / (ms / 1e3) / 1e9
+        e = {"algorithmic_bytes": nbytes, "ms": ms, "launches": st["launches"][cls], "achieved_gbs": gbs,
+             "hbm_frac": gbs / hbm if hbm else None, "bound": bound}
+        if nflops:
+            e["achieved_tflops"] = nflops / (ms / 1e3) / 1e12
+            e["fp64_frac"] = e["achieved_tflops"] / FP64_PEAK_TFLOPS
+        out[cls] = e
+
+    # Jacobian action: (2f + 5) words per point per application (v, 4 coefficients + edge
+    # mobility, J v), FP32 words in the Arnoldi step of the mixed mode
+    rate("jacobian_action", st["launches"]["jacobian_action"] * (2 * f + 5) * b * N,
+         bound="hbm" if mixed else "alu")
+    # Gram-Schmidt: (2j + 5) basis-vector transfers per pass of Arnoldi step j (counted by the library)
+    gs_ms = st["ms"].get("gs_dots", 0.0) + st["ms"].get("gs_update", 0.0)
+    if gs_ms > 0 and st.get("cgs_bytes", 0) > 0:
+        gbs = st["cgs_bytes"] / (gs_ms / 1e3) / 1e9
+        out["gram_schmidt"] = {"algorithmic_bytes": st["cgs_bytes"], "ms": gs_ms, "achieved_gbs": gbs,
+                               "hbm_frac": gbs / hbm if hbm else None, "bound": "hbm" if mixed else "alu",
+                               "second_passes": st.get("reorth"), "arnoldi_steps": st["gmres_its"]}
+    # Schwarz sweeps
+    rate("schwarz_apply", st["launches"]["schwarz_apply"] * st["schwarz_bytes"],
+         None if mixed else st["launches"]["schwarz_apply"] * st["schwarz_flops"], bound="hbm" if mixed else "alu")
+    return out
 
 
 def peaks():
@@ -227,24 +268,36 @@ def run_ours(args):
     st = P.get_stats()
     value = points_all / (ms_max / 1e3)
 
-    # roofline of the dominant kernel class
+    # roofline of the dominant kernel class, and achieved rates of the others
+    pk = peaks()
+    mixed = op["precision"] == "mixed"
+    kernels = kernel_rates(st, cfg, mixed, pk)
     cls = max(st["ms"], key=lambda k: st["ms"][k])
     launches = max(st["launches"][cls], 1)
     avg_s = st["ms"][cls] / launches / 1e3
-    pk = peaks()
-    if cls == "schwarz_apply":
-        # FP64 sweep: 2 FLOP per stored factor entry per point; bound by the FP64 pipe on GB300
+    if cls == "schwarz_apply" and not mixed:
+        # FP64 sweeps: 2 FLOP per stored factor entry per point; bound by the FP64 pipe on GB300
         flops = st["schwarz_flops"]
-        roof = {"kernel": "k_ras_apply (FP64 ILU(0) sweeps, TMA-staged)", "bound": "alu",
+        roof = {"kernel": "k_ras_apply<FP64> (ILU(0) sweeps, TMA-staged factors)", "bound": "alu",
                 "achieved": flops / avg_s / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": flops / avg_s / 1e12 / FP64_PEAK_TFLOPS,
-                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 FLOP x 2.07 GHz (probe measured 1.20)",
+                "peak_source": "derived FP64 FMA peak: 152 SMs x 2 FP64 FMA/clk x 2 FLOP x 2.07 GHz "
+                               "(a measured FMA loop reached 1.20)",
                 "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": st["schwarz_bytes"],
                 "hbm_achieved_gbs": st["schwarz_bytes"] / avg_s / 1e9, "hbm_peak_gbs": pk.get("hbm_gbs"),
-                "traffic": NCU_TRAFFIC.get(cls), "avg_launch_ms": avg_s * 1e3, "launches": launches}
+                "traffic": NCU_TRAFFIC.get((args.config, op["precision"], cls)), "avg_launch_ms": avg_s * 1e3,
+                "launches": launches}
+    elif cls == "schwarz_apply":
+        # FP32 sweeps (mixed precision): factors and sub-vectors streamed once per sweep
+        by = st["schwarz_bytes"]
+        roof = {"kernel": "k_ras_apply<FP32> (ILU(0) sweeps, TMA-staged factors)", "bound": "hbm",
+                "achieved": by / avg_s / 1e9, "peak": pk.get("hbm_gbs"), "unit": "GB/s",
+                "frac": by / avg_s / 1e9 / pk.get("hbm_gbs"), "peak_source": "measured copy bandwidth (burst)",
+                "algorithmic_bytes_per_launch": by, "algorithmic_flops_per_launch": st["schwarz_flops"],
+                "traffic": NCU_TRAFFIC.get((args.config, op["precision"], cls)), "avg_launch_ms": avg_s * 1e3,
+                "launches": launches}
     else:
-        roof = {"kernel": cls, "bound": "alu", "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": None, "traffic": NCU_TRAFFIC.get(cls), "avg_launch_ms": avg_s * 1e3, "launches": launches}
+        roof = dict(kernels.get(cls, {}), kernel=cls, traffic=NCU_TRAFFIC.get((args.config, op["precision"], cls)))
     total_ms = sum(st["ms"].values())
     breakdown = {k: round(v / max(total_ms, 1e-9), 4) for k, v in st["ms"].items() if v > 0}
 
@@ -291,6 +344,7 @@ def run_ours(args):
         "gpu_launches": None,
         "autotune": tuned,
         "roofline": roof,
+        "kernels": kernels,
         "kernel_time_share": breakdown,
         "iterations": {"newton_per_step": st["newton_its"] / max(st["steps"], 1),
                        "gmres_per_step": st["gmres_its"] / max(st["steps"], 1),

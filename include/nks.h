@@ -168,6 +168,10 @@ typedef struct {
                                        gathered sub-vectors and the owned output */
     double schwarz_flops;           /* algorithmic FLOPs of one Schwarz sweep   */
     long long kernel_launches;      /* CUDA kernels this problem launched       */
+    long long reorth;               /* Gram-Schmidt second passes taken         */
+    double cgs_bytes;               /* algorithmic bytes of the Gram-Schmidt
+                                       passes: (2j + 5) basis-vector reads and
+                                       writes for Arnoldi step j, per pass      */
 } nks_stats;
 /* kernel classes: 0 residual, 1 Jacobian action, 2 Schwarz apply,
  * 3 assembly + ILU(0), 4 Gram-Schmidt dots, 5 Gram-Schmidt update,

@@ -102,7 +102,7 @@ class nks_stats(ctypes.Structure):
                 ("steps", ctypes.c_longlong), ("retries", ctypes.c_longlong),
                 ("factor_bytes", ctypes.c_longlong), ("schwarz_points", ctypes.c_double),
                 ("schwarz_bytes", ctypes.c_double), ("schwarz_flops", ctypes.c_double),
-                ("kernel_launches", ctypes.c_longlong)]
+                ("kernel_launches", ctypes.c_longlong), ("reorth", ctypes.c_longlong), ("cgs_bytes", ctypes.c_double)]
 
     def as_dict(self):
         return {"launches": {KERNEL_CLASSES[i]: self.launches[i] for i in range(NCLASS)},
@@ -110,7 +110,8 @@ class nks_stats(ctypes.Structure):
                 "newton_its": self.newton_its, "gmres_its": self.gmres_its, "steps": self.steps,
                 "retries": self.retries, "factor_bytes": self.factor_bytes,
                 "schwarz_points": self.schwarz_points, "schwarz_bytes": self.schwarz_bytes,
-                "schwarz_flops": self.schwarz_flops, "kernel_launches": self.kernel_launches}
+                "schwarz_flops": self.schwarz_flops, "kernel_launches": self.kernel_launches,
+                "reorth": self.reorth, "cgs_bytes": self.cgs_bytes}
 
 
 _lib = None

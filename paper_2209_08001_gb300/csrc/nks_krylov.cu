@@ -105,7 +105,11 @@ __global__ void k_scale_dev(Bat bt, long long n, const TS *__restrict__ src, con
 {
     NKS_INST(src = shift(src, io); s = shift(s, io); dst = shift(dst, io);)
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i < n) dst[i] = (TD)((double)src[i] * (*s));
+    if (i >= n) return;
+    if constexpr (sizeof(TS) == sizeof(float) && sizeof(TD) == sizeof(float))
+        dst[i] = src[i] * (float)(*s);  // FP32 basis: FP32 arithmetic
+    else
+        dst[i] = (TD)((double)src[i] * (*s));
 }
 
 // y += x (x stored as TV)
@@ -167,6 +171,34 @@ __device__ __forceinline__ typename Vec<TV>::type pack(const TV (&a)[Vec<TV>::W]
     return t;
 }
 
+// Per-thread sums of the basis type: each warp adds its lanes in that type (a
+// fixed shuffle tree), the warps' sums are added in FP64 (fixed order) and
+// stored as row blockIdx.x of partials.  For FP32 sums this keeps FP64
+// arithmetic to one add per warp: GB300 runs FP64 at 1/64 of the FP32 rate.
+template <int K, typename TV>
+__device__ __forceinline__ void warp_then_block_store(TV (&v)[K], double *partials)
+{
+    if constexpr (sizeof(TV) == sizeof(double)) {
+        block_reduce_store<K>(v, partials);
+    } else {
+        __shared__ double red[K][32];
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            TV a = v[k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+            if (lane == 0) red[k][warp] = (double)a;
+        }
+        __syncthreads();
+        if (threadIdx.x < K) {
+            double a = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); w++) a += red[threadIdx.x][w];
+            partials[(size_t)blockIdx.x * K + threadIdx.x] = a;
+        }
+    }
+}
+
 // CGS pass 1: h_i = v_i . w (i < NV) and w . w, one read of V and w.
 // Vectors are read as 16-byte packs (nq packs each): ldv is a multiple of the
 // pack and entries past the vector length are zero.  gate (optional): skip
@@ -198,10 +230,7 @@ __global__ void __launch_bounds__(kRedThreads, 4) k_multidot(Bat bt, long long n
 #pragma unroll
         for (int e = 0; e < WD; e++) acc[NV] += wa[e] * wa[e];
     }
-    double accd[NV + 1];
-#pragma unroll
-    for (int k = 0; k <= NV; k++) accd[k] = (double)acc[k];
-    block_reduce_store<NV + 1>(accd, partials);
+    warp_then_block_store<NV + 1, TV>(acc, partials);
     grid_finalize(partials, NV + 1, out, ticket);
 }
 
@@ -217,9 +246,13 @@ __global__ void __launch_bounds__(kRedThreads, 4) k_cgs_update(Bat bt, long long
     if (gate && gate[0] == 0.0) return;
     using VT = typename Vec<TV>::type;
     constexpr int WD = Vec<TV>::W;
+    // the coefficients in the basis type, converted once per block
+    __shared__ TV hs[NV];
+    if ((int)threadIdx.x < NV) hs[threadIdx.x] = (TV)h[threadIdx.x];
+    __syncthreads();
     TV hk[NV];
 #pragma unroll
-    for (int k = 0; k < NV; k++) hk[k] = (TV)h[k];
+    for (int k = 0; k < NV; k++) hk[k] = hs[k];
     TV acc = (TV)0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nq; i += (long long)gridDim.x * blockDim.x) {
         TV sa[WD];
@@ -235,8 +268,8 @@ __global__ void __launch_bounds__(kRedThreads, 4) k_cgs_update(Bat bt, long long
 #pragma unroll
         for (int e = 0; e < WD; e++) acc += sa[e] * sa[e];
     }
-    double accd[1] = {(double)acc};
-    block_reduce_store<1>(accd, partials);
+    TV acc1[1] = {acc};
+    warp_then_block_store<1, TV>(acc1, partials);
     grid_finalize(partials, 1, out, ticket);
 }
 
@@ -632,6 +665,11 @@ static int gmres_t(Problem *P, Basis<TV> K, int mode, const double *b, double *x
                 if (!act[i]) continue;
                 IState &s = P->is[i];
                 s.gits++;
+                // algorithmic traffic of this step's Gram-Schmidt passes: pass 1 reads j + 2
+                // vectors, the update reads j + 2 and writes 1; the second pass repeats both
+                const bool second = P->hread[(size_t)i * 64 + S_FLAG] != 0.0;
+                P->stats.reorth += second ? 1 : 0;
+                P->stats.cgs_bytes += (2.0 * j + 5.0) * (double)n * sizeof(TV) * (second ? 2.0 : 1.0);
                 const double res = P->hread[(size_t)i * 64 + S_RES], wn = sqrt(P->hread[(size_t)i * 64 + S_WN]);
                 // NaN leaves the cycle (the true residual decides)
                 if (!(res == res) || res <= s.gtol || s.gits >= maxit || wn == 0.0) {

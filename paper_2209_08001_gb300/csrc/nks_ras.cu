@@ -1004,10 +1004,10 @@ void ras_work(const Problem *P, double *bytes, double *flops)
 {
     const RasPlan *R = P->ras;
     const double pts = (double)R->total_np, owned = (double)P->N;
+    const double b = P->opts.precision == NKS_MIXED ? 4.0 : 8.0;  // FP32 factors and vectors in mixed mode
     // factors (lower + upper entries + inverse pivots) of every overlapped point, the
     // gathered sub-vectors and the owned output, each moved once
-    *bytes = pts * (R->nlow + R->nup + P->nf) * sizeof(double) + pts * P->nf * sizeof(double) +
-             owned * P->nf * sizeof(double);
+    *bytes = pts * (R->nlow + R->nup + P->nf) * b + pts * P->nf * b + owned * P->nf * b;
     *flops = pts * (2.0 * (R->nlow + R->nup) + P->nf);
 }
 

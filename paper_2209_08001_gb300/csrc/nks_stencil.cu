@@ -326,33 +326,37 @@ __global__ void __launch_bounds__(kRedThreads) k_res_b(DGrid g, DCoef k, Bat bt,
 // of the coefficients) is one tiled kernel that recomputes dG_c and sigma on a
 // one-point halo in shared memory instead of writing them out.
 
-// per-operator constants with the grid spacings folded in
+// per-operator constants with the grid spacings folded in, in the arithmetic
+// type of the kernel (converted once on the host: on GB300 a double-to-float
+// conversion per use would occupy the FP64 pipe)
+template <typename T>
 struct JvConst {
-    double gc;        // 1/2 gamma_c / h^2
-    double ge;        // 3/2 gamma_eta / h^2
-    double ih2;       // 1/h^2
-    double el_t;      // 1/2 eps0 lam / (2h)  (times the undivided trace)
-    double el_c;      // 1/2 eps0 lam d eps0
-    double ab, b, c4; // (C11 - C12)/(2h), C12/(2h), C44/(2h)
-    double ls;        // lam eps0
-    double i2h;       // 1/(2h)
+    T gc;        // 1/2 gamma_c / h^2
+    T ge;        // 3/2 gamma_eta / h^2
+    T ih2;       // 1/h^2
+    T el_t;      // 1/2 eps0 lam / (2h)  (times the undivided trace)
+    T el_c;      // 1/2 eps0 lam d eps0
+    T ab, b, c4; // (C11 - C12)/(2h), C12/(2h), C44/(2h)
+    T ls;        // lam eps0
+    T i2h;       // 1/(2h)
     int mode;
 };
 
-static JvConst jv_const(const DGrid &g, const DCoef &k, int mode)
+template <typename T>
+static JvConst<T> jv_const(const DGrid &g, const DCoef &k, int mode)
 {
-    JvConst c;
+    JvConst<T> c;
     const double i2h = 0.5 / g.h, ih2 = 1.0 / (g.h * g.h);
-    c.gc = 0.5 * k.gamma_c * ih2;
-    c.ge = 1.5 * k.gamma_eta * ih2;
-    c.ih2 = ih2;
-    c.el_t = 0.5 * k.eps0 * k.lam * i2h;
-    c.el_c = 0.5 * k.eps0 * k.lam * g.dim * k.eps0;
-    c.ab = (k.C11 - k.C12) * i2h;
-    c.b = k.C12 * i2h;
-    c.c4 = k.C44 * i2h;
-    c.ls = k.lam * k.eps0;
-    c.i2h = i2h;
+    c.gc = (T)(0.5 * k.gamma_c * ih2);
+    c.ge = (T)(1.5 * k.gamma_eta * ih2);
+    c.ih2 = (T)ih2;
+    c.el_t = (T)(0.5 * k.eps0 * k.lam * i2h);
+    c.el_c = (T)(0.5 * k.eps0 * k.lam * g.dim * k.eps0);
+    c.ab = (T)((k.C11 - k.C12) * i2h);
+    c.b = (T)(k.C12 * i2h);
+    c.c4 = (T)(k.C44 * i2h);
+    c.ls = (T)(k.lam * k.eps0);
+    c.i2h = (T)i2h;
     c.mode = mode;
     return c;
 }
@@ -372,7 +376,7 @@ __device__ __forceinline__ void nbr_offsets(const int (&c3)[3], const int (&nn)[
 
 // dG_c and sigma at one point; T is the arithmetic type
 template <int D, bool EL, typename T, typename TV, typename TC>
-__device__ __forceinline__ void jv_point(const JvConst &c, int mode, int N, int idx, const int (&im)[3],
+__device__ __forceinline__ void jv_point(const JvConst<T> &c, int mode, int N, int idx, const int (&im)[3],
                                          const int (&ip)[3], const TV *__restrict__ v, const TC *__restrict__ part,
                                          T &dg, T (&sg)[EL ? D * (D + 1) / 2 : 1])
 {
@@ -387,12 +391,12 @@ __device__ __forceinline__ void jv_point(const JvConst &c, int mode, int N, int 
 #pragma unroll
         for (int I = 0; I < D; I++) trd += Dd[I][I];
         // sigma_II = (C11 - C12) e_II + C12 tr e - lam eps0 v_c;  sigma_IJ = C44 (D_IJ + D_JI)
-        const T common = (T)c.b * trd - (T)c.ls * vc;
+        const T common = c.b * trd - c.ls * vc;
 #pragma unroll
         for (int I = 0; I < D; I++) {
-            sg[I] = (T)c.ab * Dd[I][I] + common;
+            sg[I] = c.ab * Dd[I][I] + common;
 #pragma unroll
-            for (int J = I + 1; J < D; J++) sg[scomp(D, I, J)] = (T)c.c4 * (Dd[I][J] + Dd[J][I]);
+            for (int J = I + 1; J < D; J++) sg[scomp(D, I, J)] = c.c4 * (Dd[I][J] + Dd[J][I]);
         }
     }
     if (mode == 0) {
@@ -400,8 +404,8 @@ __device__ __forceinline__ void jv_point(const JvConst &c, int mode, int N, int 
 #pragma unroll
         for (int J = 0; J < D; J++) sn += (T)v[ip[J]] + (T)v[im[J]];
         const T lc = sn - (T)(2 * D) * vc;
-        dg = (T)part[idx] * vc + (T)part[N + idx] * (T)v[N + idx] - (T)c.gc * lc;
-        if constexpr (EL) dg += (T)c.el_c * vc - (T)c.el_t * trd;
+        dg = (T)part[idx] * vc + (T)part[N + idx] * (T)v[N + idx] - c.gc * lc;
+        if constexpr (EL) dg += c.el_c * vc - c.el_t * trd;
     }
 }
 
@@ -420,7 +424,7 @@ __device__ __forceinline__ bool grid_point(const DGrid &g, int (&c3)[3], int &p)
 }
 
 template <int D, bool EL>
-__global__ void __launch_bounds__(256) k_jv64_a(DGrid g, JvConst c, Bat bt, const double *__restrict__ part,
+__global__ void __launch_bounds__(256) k_jv64_a(DGrid g, JvConst<double> c, Bat bt, const double *__restrict__ part,
                                                 const double *__restrict__ v, double *__restrict__ dG,
                                                 double *__restrict__ sig)
 {
@@ -446,7 +450,7 @@ __global__ void __launch_bounds__(256) k_jv64_a(DGrid g, JvConst c, Bat bt, cons
 }
 
 template <int D, bool EL>
-__global__ void __launch_bounds__(256) k_jv64_b(DGrid g, JvConst c, Bat bt, const double *__restrict__ isc,
+__global__ void __launch_bounds__(256) k_jv64_b(DGrid g, JvConst<double> c, Bat bt, const double *__restrict__ isc,
                                                 const double *__restrict__ part, const double *__restrict__ mob,
                                                 const double *__restrict__ v, const double *__restrict__ dG,
                                                 const double *__restrict__ sig, double *__restrict__ Jv,
@@ -524,7 +528,7 @@ struct JvTile<3> {
 };
 
 template <int D, bool EL>
-__global__ void __launch_bounds__(256) k_jv32(DGrid g, JvConst c, Bat bt, const double *__restrict__ isc,
+__global__ void __launch_bounds__(256) k_jv32(DGrid g, JvConst<float> c, Bat bt, const double *__restrict__ isc,
                                               const float *__restrict__ part, const float *__restrict__ mob,
                                               const float *__restrict__ v, float *__restrict__ Jv,
                                               const float *__restrict__ Jec, const double *__restrict__ zsum)
@@ -573,8 +577,8 @@ __global__ void __launch_bounds__(256) k_jv32(DGrid g, JvConst c, Bat bt, const 
     }
     __syncthreads();
 
-    const float m = Jec ? (float)(zsum[0] / (double)N) : 0.f;
-    const float idt = (float)(1.0 / shift(isc, io)[I_DT]), ih2 = (float)c.ih2, ge = (float)c.ge, i2h = (float)c.i2h;
+    const float m = Jec ? (float)zsum[0] * (1.0f / (float)N) : 0.f;
+    const float idt = 1.0f / (float)shift(isc, io)[I_DT], ih2 = c.ih2, ge = c.ge, i2h = c.i2h;
     for (int t = threadIdx.x; t < TX * TY * TZ; t += blockDim.x) {
         const int tx = t % TX, ty = (t / TX) % TY, tz = t / (TX * TY);
         const int c3[3] = {x0 + tx, y0 + ty, z0 + tz};
@@ -727,7 +731,7 @@ int launch_residual(const DGrid &g, const DCoef &k, const double *isc, int mode,
 }
 
 template <int D, bool EL>
-static void launch_jv64_d(const DGrid &g, const JvConst &c, const Bat &bt, const double *isc, const double *part,
+static void launch_jv64_d(const DGrid &g, const JvConst<double> &c, const Bat &bt, const double *isc, const double *part,
                           const double *mob, const double *v, double *dG, double *sig, double *Jv, cudaStream_t st,
                           const double *Jec, const double *zsum)
 {
@@ -738,7 +742,7 @@ static void launch_jv64_d(const DGrid &g, const JvConst &c, const Bat &bt, const
 }
 
 template <int D, bool EL>
-static void launch_jv32_d(const DGrid &g, const JvConst &c, const Bat &bt, const double *isc, const float *part,
+static void launch_jv32_d(const DGrid &g, const JvConst<float> &c, const Bat &bt, const double *isc, const float *part,
                           const float *mob, const float *v, float *Jv, cudaStream_t st, const float *Jec,
                           const double *zsum)
 {
@@ -761,7 +765,7 @@ int launch_jv64(const DGrid &g, const DCoef &k, const double *isc, int mode, con
                 const double *v, double *dG, double *sig, double *Jv, cudaStream_t st, const Bat &bt,
                 const double *Jec, const double *zsum)
 {
-    const JvConst c = jv_const(g, k, mode);
+    const JvConst<double> c = jv_const<double>(g, k, mode);
     NKS_JV_DISPATCH(launch_jv64_d, g, c, bt, isc, part, mob, v, dG, sig, Jv, st, Jec, zsum);
     return 2;
 }
@@ -769,7 +773,7 @@ int launch_jv64(const DGrid &g, const DCoef &k, const double *isc, int mode, con
 int launch_jv32(const DGrid &g, const DCoef &k, const double *isc, int mode, const float *part, const float *mob,
                 const float *v, float *Jv, cudaStream_t st, const Bat &bt, const float *Jec, const double *zsum)
 {
-    const JvConst c = jv_const(g, k, mode);
+    const JvConst<float> c = jv_const<float>(g, k, mode);
     NKS_JV_DISPATCH(launch_jv32_d, g, c, bt, isc, part, mob, v, Jv, st, Jec, zsum);
     return 1;
 }
