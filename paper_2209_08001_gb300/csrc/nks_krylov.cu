@@ -273,6 +273,43 @@ __global__ void __launch_bounds__(kRedThreads, 4) k_cgs_update(Bat bt, long long
     grid_finalize(partials, 1, out, ticket);
 }
 
+// CGS pass 2 fused with the dot products of the second pass (FP32 basis):
+// w -= sum_i h_i v_i, and with each updated element still in registers,
+// h2_i = v_i . w (i < NV) and w . w, written to out[0..NV].  One read of V
+// and w instead of two.  One element per thread and iteration keeps the NV
+// basis values of that element in registers; the coefficients are read from
+// shared memory.
+template <int NV, typename TV>
+__global__ void __launch_bounds__(kRedThreads, 2) k_cgs_update_dots(Bat bt, long long n, const TV *__restrict__ V,
+                                                                    long long ldv, const double *__restrict__ h,
+                                                                    TV *__restrict__ w, double *__restrict__ partials,
+                                                                    double *out, unsigned int *ticket)
+{
+    NKS_INST(V = shift(V, io); h = shift(h, io); w = shift(w, io); partials = shift(partials, io);
+             out = shift(out, io); ticket = shift(ticket, io);)
+    __shared__ TV hs[NV];
+    if ((int)threadIdx.x < NV) hs[threadIdx.x] = (TV)h[threadIdx.x];
+    __syncthreads();
+    TV acc[NV + 1];
+#pragma unroll
+    for (int k = 0; k <= NV; k++) acc[k] = (TV)0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        TV va[NV];
+        TV sa = w[i];
+#pragma unroll
+        for (int k = 0; k < NV; k++) {
+            va[k] = V[k * ldv + i];
+            sa -= hs[k] * va[k];
+        }
+        w[i] = sa;
+#pragma unroll
+        for (int k = 0; k < NV; k++) acc[k] += va[k] * sa;
+        acc[NV] += sa * sa;
+    }
+    warp_then_block_store<NV + 1, TV>(acc, partials);
+    grid_finalize(partials, NV + 1, out, ticket);
+}
+
 template <typename TV>
 using MultidotFn = void (*)(Bat, long long, const TV *, long long, const TV *, double *, const double *, double *,
                             unsigned int *);
@@ -290,11 +327,26 @@ constexpr auto update_table(std::integer_sequence<int, I...>)
 {
     return std::array<UpdateFn<TV>, sizeof...(I)>{{&k_cgs_update<I + 1, TV>...}};
 }
+using UpdDotsFn = void (*)(Bat, long long, const float *, long long, const double *, float *, double *, double *,
+                           unsigned int *);
+template <int... I>
+constexpr auto update_dots_table(std::integer_sequence<int, I...>)
+{
+    return std::array<UpdDotsFn, sizeof...(I)>{{&k_cgs_update_dots<I + 1, float>...}};
+}
 constexpr int kMaxNv = 31;
 const auto g_multidot64 = multidot_table<double>(std::make_integer_sequence<int, kMaxNv>{});
 const auto g_update64 = update_table<double>(std::make_integer_sequence<int, kMaxNv>{});
 const auto g_multidot32 = multidot_table<float>(std::make_integer_sequence<int, kMaxNv>{});
 const auto g_update32 = update_table<float>(std::make_integer_sequence<int, kMaxNv>{});
+const auto g_update_dots32 = update_dots_table(std::make_integer_sequence<int, kMaxNv>{});
+
+// FP32 basis: w -= V h, then h2 = V^T w and w . w into out[0..nv]
+void launch_update_dots(int nv, long long ldv, const float *V, const double *h, float *w, double *partials,
+                        double *out, unsigned int *ticket, int rb, cudaStream_t st, const Bat &bt)
+{
+    g_update_dots32[nv - 1]<<<dim3(rb, bt.nb), kRedThreads, 0, st>>>(bt, ldv, V, ldv, h, w, partials, out, ticket);
+}
 
 // h_i = v_i . w (i < nv) and w . w into out[0..nv]; ldv a multiple of the 16-byte pack
 template <typename TV>
@@ -334,6 +386,17 @@ __global__ void k_cgs_decide(Bat bt, double *gm, GmLayout L, int j)
     NKS_GM_INST()
     double *sc = gm + L.scal;
     sc[S_WN0] = gm[L.hcol + j + 1];  // w . w from pass 1
+    const double wn = sqrt(sc[S_WN]), wn0 = sqrt(sc[S_WN0]);
+    sc[S_FLAG] = (wn < 0.7 * wn0) ? 1.0 : 0.0;
+}
+
+// the fused form: w . w before the update is hcol[j + 1], after it h2[j + 1]
+__global__ void k_cgs_decide_fused(Bat bt, double *gm, GmLayout L, int j)
+{
+    NKS_GM_INST()
+    double *sc = gm + L.scal;
+    sc[S_WN0] = gm[L.hcol + j + 1];
+    sc[S_WN] = gm[L.h2 + j + 1];
     const double wn = sqrt(sc[S_WN]), wn0 = sqrt(sc[S_WN0]);
     sc[S_FLAG] = (wn < 0.7 * wn0) ? 1.0 : 0.0;
 }
@@ -631,16 +694,26 @@ static int gmres_t(Problem *P, Basis<TV> K, int mode, const double *b, double *x
                 P->tick(4);
                 launch_multidot<TV>(j + 1, ldv, V, W, P->partials, nullptr, gm + L.hcol, P->tickets, P->rb, st, ba);
                 P->tock(4);
-                P->tick(5);
-                launch_update<TV>(j + 1, ldv, V, gm + L.hcol, W, P->partials, nullptr, gm + L.scal + S_WN,
-                                  P->tickets + 1, P->rb, st, ba);
-                P->tock(5);
-                // optional second pass (CGS2), gated on the device
-                k_cgs_decide<<<nbt, 1, 0, st>>>(ba, gm, L, j);
                 const double *gate = gm + L.scal + S_FLAG;
-                P->tick(4);
-                launch_multidot<TV>(j + 1, ldv, V, W, P->partials, gate, gm + L.h2, P->tickets, P->rb, st, ba);
-                P->tock(4);
+                if constexpr (sizeof(TV) == sizeof(float)) {
+                    // FP32 basis: the update also forms the second pass's dot products
+                    P->tick(5);
+                    launch_update_dots(j + 1, ldv, V, gm + L.hcol, W, P->partials, gm + L.h2, P->tickets + 1,
+                                       P->rb, st, ba);
+                    P->tock(5);
+                    k_cgs_decide_fused<<<nbt, 1, 0, st>>>(ba, gm, L, j);
+                } else {
+                    P->tick(5);
+                    launch_update<TV>(j + 1, ldv, V, gm + L.hcol, W, P->partials, nullptr, gm + L.scal + S_WN,
+                                      P->tickets + 1, P->rb, st, ba);
+                    P->tock(5);
+                    // optional second pass (CGS2), gated on the device
+                    k_cgs_decide<<<nbt, 1, 0, st>>>(ba, gm, L, j);
+                    P->tick(4);
+                    launch_multidot<TV>(j + 1, ldv, V, W, P->partials, gate, gm + L.h2, P->tickets, P->rb, st, ba);
+                    P->tock(4);
+                    P->count(1);
+                }
                 P->tick(5);
                 launch_update<TV>(j + 1, ldv, V, gm + L.h2, W, P->partials, gate, gm + L.scal + S_WN,
                                   P->tickets + 1, P->rb, st, ba);
@@ -650,7 +723,7 @@ static int gmres_t(Problem *P, Basis<TV> K, int mode, const double *b, double *x
                 k_arnoldi<<<nbt, 1, 0, st>>>(ba, gm, L, j);
                 P->tock(9);
                 k_scale_dev<TV, TV><<<dim3(nb(n), nbt), kT, 0, st>>>(ba, n, W, gm + L.scal + S_INV, vn);
-                P->count(8);  // 2 multidot + 2 update + decide + accum + arnoldi + scale
+                P->count(7);  // multidot + update (+ dots) + decide + update + accum + arnoldi + scale
                 if (readback) P->enqueue_readback(gm + L.scal, 8);
             };
             if (use_graphs && run_graph(P, mode, j, [&] { iteration(true); })) {
@@ -667,9 +740,12 @@ static int gmres_t(Problem *P, Basis<TV> K, int mode, const double *b, double *x
                 s.gits++;
                 // algorithmic traffic of this step's Gram-Schmidt passes: pass 1 reads j + 2
                 // vectors, the update reads j + 2 and writes 1; the second pass repeats both
+                // (FP32 basis: the second pass's dot products ride on the first update, so a
+                // second pass adds only its update, j + 3 transfers)
                 const bool second = P->hread[(size_t)i * 64 + S_FLAG] != 0.0;
                 P->stats.reorth += second ? 1 : 0;
-                P->stats.cgs_bytes += (2.0 * j + 5.0) * (double)n * sizeof(TV) * (second ? 2.0 : 1.0);
+                const double extra = sizeof(TV) == sizeof(float) ? (j + 3.0) : (2.0 * j + 5.0);
+                P->stats.cgs_bytes += ((2.0 * j + 5.0) + (second ? extra : 0.0)) * (double)n * sizeof(TV);
                 const double res = P->hread[(size_t)i * 64 + S_RES], wn = sqrt(P->hread[(size_t)i * 64 + S_WN]);
                 // NaN leaves the cycle (the true residual decides)
                 if (!(res == res) || res <= s.gtol || s.gits >= maxit || wn == 0.0) {
