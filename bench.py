@@ -37,9 +37,12 @@ import synthetic as S  # noqa: E402
 METRIC = "point-steps/s"
 # FP64 FMA peak derived from the unit counts: 152 SMs x 2 FP64 FMA/clk x 2 FLOP x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-# DRAM traffic per launch of the dominant kernels from an ncu capture (None once the kernel changed)
-# keyed by (workload, precision, kernel class)
-NCU_TRAFFIC = {}
+# DRAM traffic per launch of the dominant kernel (dram__bytes_read.sum + dram__bytes_write.sum),
+# keyed by (workload, precision, kernel class), from one ncu capture of the 512^2 probe
+# (bench.py --probe gmres512: the same 68x68 boxes, 64 of them) scaled by the 256 boxes of
+# the 1024^2 launch; an entry is removed whenever the kernel changes
+NCU_TRAFFIC = {("2d1024", "fp64", "schwarz_apply"): 4 * (173.719808e6 + 4.763648e6),
+               ("2d1024", "mixed", "schwarz_apply"): 4 * (87.115264e6 + 2.790144e6)}
 
 
 def kernel_rates(st, cfg, mixed, pk):
