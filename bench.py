@@ -301,6 +301,21 @@ def run_ours(args):
                 "launches": launches}
     else:
         roof = dict(kernels.get(cls, {}), kernel=cls, traffic=NCU_TRAFFIC.get((args.config, op["precision"], cls)))
+    # mixed precision: error per field against the FP64 path on the same dt sequence
+    accuracy = None
+    if mixed and not args.no_accuracy and rank == 0:
+        cm, em, um = P.get_fields()
+        Q = nks.Problem(cfg["dim"], cfg["n"], cfg["h"], c, e, S.coefficients(), dict(op, precision="fp64"),
+                        stream=stream.cuda_stream, allocator=alloc)
+        for i in infos:
+            Q.step(i["dt"])
+        cd, ed, ud = Q.get_fields()
+        Q.destroy()
+        rel = lambda a, b: float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+        accuracy = {"reference": "FP64 GPU path (parity-tested against the FP64 oracle), same dt sequence, "
+                                 "after the K timed steps",
+                    "rel_l2": {"c": rel(cm, cd), "eta": rel(em, ed), "u": rel(um, ud) if um is not None else None},
+                    "tolerance": 1e-8}
     total_ms = sum(st["ms"].values())
     breakdown = {k: round(v / max(total_ms, 1e-9), 4) for k, v in st["ms"].items() if v > 0}
 
@@ -348,6 +363,7 @@ def run_ours(args):
         "autotune": tuned,
         "roofline": roof,
         "kernels": kernels,
+        "accuracy": accuracy,
         "kernel_time_share": breakdown,
         "iterations": {"newton_per_step": st["newton_its"] / max(st["steps"], 1),
                        "gmres_per_step": st["gmres_its"] / max(st["steps"], 1),
@@ -562,6 +578,7 @@ def main():
                     help="override the workload's precision mode (default: the workload's own)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true", help="mixed precision: skip the FP64 comparison")
     # iteration counts used to scale the oracle sample in the reference arm (measured on the GPU arm)
     ap.add_argument("--ref-gmres-per-step", type=float, default=1800.0)
     ap.add_argument("--ref-newton-per-step", type=float, default=6.0)
