@@ -61,6 +61,7 @@ struct RasPlan {
     bool x_smem = true;
     size_t smem_bytes = 0;          // dynamic shared memory of the apply kernel (FP64 factors)
     bool x_smem32 = true;
+    int lane_bufs = 2;              // factor buffers of the FP32 sweep
     size_t smem_bytes32 = 0;        // same for the FP32 factors of the mixed-precision mode
     SubInfo *sub = nullptr;
     // runtime copies of the pattern for the assembly kernel
@@ -115,6 +116,10 @@ static Pattern compile_time_pattern(int d, int nf)
 
 __host__ __device__ static inline long long pad4(long long n) { return (n + 3) & ~3LL; }
 
+// factor-part buffers of the one-thread-per-point sweep: three (copies two levels
+// ahead) when the sub-vector still fits in shared memory, else two
+constexpr int kLaneBufsMax = 3;
+
 // Wavefront level of a box point.  Every lower neighbour of the stencil
 // (offsets (1,-1,0), (1,0,-1), (0,1,-1) and the axis offsets) must lie on an
 // earlier level, which the weights 1 < 2 < 3 give with the fewest levels; the
@@ -124,6 +129,14 @@ __host__ __device__ static inline size_t pad16(size_t n) { return (n + 15) & ~(s
 
 // dynamic shared memory of the apply kernel: barriers, point table, two level
 // buffers, stage-A partial sums and (when it fits) the sub-vector
+// the same for the one-thread-per-point sweep (FP32): no partial sums, kLaneBufs buffers
+static size_t apply_smem_lane(const RasPlan *R, int nf, size_t tsize, bool with_x, int nbuf)
+{
+    size_t b = 32 + pad16((size_t)R->maxnp * sizeof(int)) + nbuf * pad16((size_t)R->maxblk * tsize);
+    if (with_x) b += pad16((size_t)R->maxnpx * nf * tsize);
+    return b;
+}
+
 static size_t apply_smem(const RasPlan *R, int nf, size_t tsize, bool with_x)
 {
     const int pstride = (R->maxcnt + 31) / 32 * 32;
@@ -288,8 +301,9 @@ int ras_plan_create(Problem *P, std::string &err)
     R->fac_elems = fac_off;
     R->x_smem = apply_smem(R, nf, sizeof(double), true) <= 227 * 1024;
     R->smem_bytes = apply_smem(R, nf, sizeof(double), R->x_smem);
-    R->x_smem32 = apply_smem(R, nf, sizeof(float), true) <= 227 * 1024;
-    R->smem_bytes32 = apply_smem(R, nf, sizeof(float), R->x_smem32);
+    R->lane_bufs = apply_smem_lane(R, nf, sizeof(float), true, kLaneBufsMax) <= 227 * 1024 ? kLaneBufsMax : 2;
+    R->x_smem32 = apply_smem_lane(R, nf, sizeof(float), true, R->lane_bufs) <= 227 * 1024;
+    R->smem_bytes32 = apply_smem_lane(R, nf, sizeof(float), R->x_smem32, R->lane_bufs);
     if (R->smem_bytes > 227 * 1024) {
         err = "decomposition: subdomain boxes too large for the Schwarz kernel (use more subdomains)";
         return NKS_EINVAL;
@@ -733,6 +747,150 @@ __global__ void __launch_bounds__(1024) k_ras_apply(DGrid g, Bat bt, const SubIn
     }
 }
 
+// All rows of one point in sweep order: each row's full lower (forward) or
+// upper (backward) part, including the same-point entries computed just before.
+template <int D, int NF, bool FWD, typename T>
+__device__ __forceinline__ void point_rows(int k, int lp, int lx, int ly, int lz, const T *B, long long cp, T *x,
+                                           int np, const SubInfo &si, int sy, int sz)
+{
+    constexpr Pattern PT = Pat<D, NF>::v;
+    static_for<0, NF>([&](auto fi) {
+        constexpr int f = FWD ? decltype(fi)::value : NF - 1 - decltype(fi)::value;
+        constexpr int b = FWD ? PT.rowoff[f] : PT.rowoff[f] + PT.diag[f] + 1;
+        constexpr int e = FWD ? PT.rowoff[f] + PT.diag[f] : PT.rowoff[f] + PT.len[f];
+        constexpr int drow = PT.nup + f;  // inverse pivot row in the backward part
+        const T s = slot_sum<D, NF, b, e, T>(B, cp, k, x, np, lp, lx, ly, lz, si, sy, sz);
+        if constexpr (FWD) x[f * np + lp] -= s;
+        else x[f * np + lp] = (x[f * np + lp] - s) * B[(long long)drow * cp + k];
+    });
+}
+
+// The same sweeps with one thread per point doing all its rows (every lower or
+// upper entry, then the next row): one block barrier per level instead of two
+// and no partial sums.  Used for FP32 factors, where the per-point instruction
+// stream is cheap and the latency of the two-stage schedule dominates; the FP64
+// pipe (1/64 rate) prefers the two-stage schedule's spread over warps.
+template <int D, int NF, typename T, typename TV, int NBUF>
+__global__ void __launch_bounds__(256) k_ras_apply_lane(DGrid g, Bat bt, const SubInfo *__restrict__ subs, const int *__restrict__ lvl_ptr,
+                            const long long *__restrict__ lvl_blk, const int *__restrict__ lvl_lp,
+                            const T *__restrict__ fac, const TV *__restrict__ r, TV *__restrict__ z,
+                            T *__restrict__ scratch, int x_in_smem, int maxnp, long long maxblk, int *flag,
+                            double *__restrict__ cpart, double *__restrict__ csum, unsigned int *ticket)
+{
+    long long io;
+    if (!inst_off(bt, blockIdx.y, io)) return;
+    fac = shift(fac, io);
+    r = shift(r, io);
+    z = shift(z, io);
+    scratch = shift(scratch, io);
+    flag = shift(flag, io);
+    cpart = shift(cpart, io);
+    csum = shift(csum, io);
+    ticket = shift(ticket, io);
+    constexpr Pattern PT = Pat<D, NF>::v;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    int *lps = reinterpret_cast<int *>(smem + 32);
+    const size_t bstride = pad16((size_t)maxblk * sizeof(T)) / sizeof(T);
+    T *const buf0 = reinterpret_cast<T *>(smem + 32 + pad16((size_t)maxnp * sizeof(int)));
+    const SubInfo si = subs[blockIdx.x];
+    T *x = x_in_smem ? buf0 + NBUF * bstride : scratch + si.scr_off;
+    const int np = si.np, nlev = si.nlev;  // x holds NF planes of si.npx (padded) entries
+    const int *lptr = lvl_ptr + si.lvl_off;
+    const long long *lblk = lvl_blk + si.lvl_off;
+    const T *F = fac + si.fac_off;
+    const long long N = g.N;
+    const int sy = si.px, sz = si.px * si.py;
+    const int npx = si.npx;
+    const int tid = threadIdx.x;
+    const int nuse = 2 * nlev;  // forward parts of levels 0..nlev-1, then backward parts of nlev-1..0
+
+    // the copy of use `it` into buffer it % NBUF (NBUF - 1 levels ahead)
+    auto issue = [&](int it) {
+        const int lev = it < nlev ? it : 2 * nlev - 1 - it;
+        const long long cp = pad4((long long)(lptr[lev + 1] - lptr[lev]));
+        const T *src = F + lblk[lev] + (it < nlev ? 0 : (long long)PT.nlow * cp);
+        const uint32_t bytes = (uint32_t)((it < nlev ? PT.nlow : PT.nup + NF) * cp * (long long)sizeof(T));
+        uint64_t *b = &bar[it % NBUF];
+        fence_proxy_async();
+        mbar_expect_tx(b, bytes);
+        bulk_g2s(buf0 + (it % NBUF) * bstride, src, bytes, b);
+    };
+
+    if (tid == 0) {
+        for (int q = 0; q < NBUF; q++) mbar_init(&bar[q], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0)
+        for (int q = 0; q < NBUF - 1 && q < nuse; q++) issue(q);
+    for (int i = tid; i < np; i += blockDim.x) lps[i] = lvl_lp[si.pos_off + i];
+    // gather R_i^delta r
+    for (int q = tid; q < np; q += blockDim.x) {
+        const int lx = q % si.L[0], ly = (q / si.L[0]) % si.L[1], lz = q / (si.L[0] * si.L[1]);
+        const int lp = lx + sy * ly + sz * lz;
+        const long long gp = index_of(g, wrapi(si.org[0] + lx, g.n[0]), wrapi(si.org[1] + ly, g.n[1]),
+                                      wrapi(si.org[2] + lz, g.n[2]));
+#pragma unroll
+        for (int f = 0; f < NF; f++) x[f * npx + lp] = (T)r[f * N + gp];
+    }
+    __syncthreads();
+    bool failed = false;
+    int failed_at = 0;
+    for (int it = 0; it < nuse; it++) {
+        // buffer (it + NBUF - 1) % NBUF last served use it - 1 (finished at the barrier)
+        if (tid == 0 && it + NBUF - 1 < nuse) issue(it + NBUF - 1);
+        const bool ok = mbar_wait_bounded(&bar[it % NBUF], (uint32_t)((it / NBUF) & 1));
+        const int lev = it < nlev ? it : 2 * nlev - 1 - it;
+        const int base = lptr[lev], cnt = lptr[lev + 1] - base;
+        const long long cp = pad4((long long)cnt);
+        const T *B = buf0 + (it % NBUF) * bstride;
+        const bool fwd = it < nlev;
+        if (ok)
+            for (int k = tid; k < cnt; k += blockDim.x) {
+                const int pk = lps[base + k];
+                const int lx = pk & 1023, ly = (pk >> 10) & 1023, lz = pk >> 20;
+                const int lp = lx + sy * ly + sz * lz;
+                if (fwd) point_rows<D, NF, true, T>(k, lp, lx, ly, lz, B, cp, x, npx, si, sy, sz);
+                else point_rows<D, NF, false, T>(k, lp, lx, ly, lz, B, cp, x, npx, si, sy, sz);
+            }
+        failed = __syncthreads_or(!ok);
+        if (failed) {
+            failed_at = it;
+            break;
+        }
+    }
+    if (failed) {
+        // a copy never completed: report it, let outstanding copies land (bounded), and
+        // write nothing (the block still takes its turn in the sum below)
+        if (tid == 0) {
+            atomicOr(flag + 1, 4);
+            for (int u = failed_at; u < nuse && u < failed_at + NBUF; u++)
+                mbar_wait_bounded(&bar[u % NBUF], (uint32_t)((u / NBUF) & 1));
+        }
+    }
+    // restricted prolongation: owned points only; the sum of the written z_c feeds the
+    // projection's mean (FP64 per thread, fixed block tree, last block adds the blocks in order)
+    double cs[1] = {0.0};
+    for (int q = failed ? np : tid; q < np; q += blockDim.x) {
+        const int lx = q % si.L[0], ly = (q / si.L[0]) % si.L[1], lz = q / (si.L[0] * si.L[1]);
+        if (lx < si.own0[0] || lx >= si.own1[0] || ly < si.own0[1] || ly >= si.own1[1] || lz < si.own0[2] ||
+            lz >= si.own1[2])
+            continue;
+        const int lp = lx + sy * ly + sz * lz;
+        const long long gp = index_of(g, wrapi(si.org[0] + lx, g.n[0]), wrapi(si.org[1] + ly, g.n[1]),
+                                      wrapi(si.org[2] + lz, g.n[2]));
+#pragma unroll
+        for (int f = 0; f < NF; f++) z[f * N + gp] = (TV)x[f * npx + lp];
+        cs[0] += (double)(TV)x[lp];
+    }
+    if (csum) {
+        __syncthreads();
+        block_reduce_store_n<1>(cs, cpart);
+        grid_finalize(cpart, 1, csum, ticket);
+    }
+}
+
 // projection P: sums of z_c and of sign_m(p) z_uI for every null mode m.
 // Mode mi is the sign pattern prod over the axes J in mask[mi] of (-1)^x_J.
 struct ModeMasks {
@@ -854,7 +1012,14 @@ void apply_attr(Problem *P)
     const size_t smem = f32 ? R->smem_bytes32 : R->smem_bytes;
     bool &attr = f32 ? R->attr_set32 : R->attr_set;
     if (smem > 48 * 1024 && !attr) {
-        cudaFuncSetAttribute(k_ras_apply<D, NF, TV, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if constexpr (f32) {
+            cudaFuncSetAttribute(k_ras_apply_lane<D, NF, TV, TV, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+            cudaFuncSetAttribute(k_ras_apply_lane<D, NF, TV, TV, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        }
+        else
+            cudaFuncSetAttribute(k_ras_apply<D, NF, TV, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = true;
     }
 }
@@ -882,9 +1047,18 @@ void launch_apply_t(Problem *P, const TV *r, TV *z, const Bat &bt)
     const T *fac = f32 ? reinterpret_cast<const T *>(R->fac32) : reinterpret_cast<const T *>(R->fac);
     T *scr = f32 ? reinterpret_cast<T *>(R->scratch32) : reinterpret_cast<T *>(R->scratch);
     const int xs = f32 ? R->x_smem32 : R->x_smem;
-    k_ras_apply<D, NF, T, TV><<<dim3(R->nsub, bt.nb), threads, smem, P->stream>>>(
-        P->g, bt, R->sub, R->lvl_ptr, R->lvl_blk, R->lvl_lp, fac, r, z, scr, xs ? 1 : 0, R->maxnp, R->maxblk, wpt, pstride,
-        P->dflag, P->partials, P->zsum, P->tickets + 3);
+    if constexpr (f32) {
+        // one thread per point of the widest level
+        const int tl = std::min(256, std::max(32, (R->maxcnt + 31) / 32 * 32));
+        auto kern = R->lane_bufs == 3 ? k_ras_apply_lane<D, NF, T, TV, 3> : k_ras_apply_lane<D, NF, T, TV, 2>;
+        kern<<<dim3(R->nsub, bt.nb), tl, smem, P->stream>>>(P->g, bt, R->sub, R->lvl_ptr, R->lvl_blk, R->lvl_lp, fac, r,
+                                                            z, scr, xs ? 1 : 0, R->maxnp, R->maxblk, P->dflag,
+                                                            P->partials, P->zsum, P->tickets + 3);
+    } else {
+        k_ras_apply<D, NF, T, TV><<<dim3(R->nsub, bt.nb), threads, smem, P->stream>>>(
+            P->g, bt, R->sub, R->lvl_ptr, R->lvl_blk, R->lvl_lp, fac, r, z, scr, xs ? 1 : 0, R->maxnp, R->maxblk, wpt,
+            pstride, P->dflag, P->partials, P->zsum, P->tickets + 3);
+    }
 }
 
 }  // namespace
