@@ -579,8 +579,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true", help="mixed precision: skip the FP64 comparison")
     # iteration counts used to scale the oracle sample in the reference arm (measured on the GPU arm)
-    ap.add_argument("--ref-gmres-per-step", type=float, default=1800.0)
-    ap.add_argument("--ref-newton-per-step", type=float, default=6.0)
+    ap.add_argument("--ref-gmres-per-step", type=float, default=1700.0)
+    ap.add_argument("--ref-newton-per-step", type=float, default=5.67)
     ap.add_argument("--probe", default=None, choices=["gmres512"], help="small profiling case, no JSON bench line")
     ap.add_argument("--batch", type=int, default=0,
                     help="B > 0: B instances of the workload stepped as one batch (beside one alone)")
