@@ -284,6 +284,14 @@ int nks_batch_set_state(nks_problem *p, int slot, const void *buf, size_t bytes)
  * Schwarz factors, scratch). */
 size_t nks_device_bytes(const nks_problem *p);
 
+/* Testing hook for failure detection (no counterpart in the paper): on != 0
+ * makes every Schwarz sweep withhold the first bulk copy of factors in each
+ * block, so the block's bounded mbarrier wait expires (about a second), the
+ * block writes nothing and flags the failure, and the running solve returns
+ * NKS_ETIMEOUT with the state left at X^n; the GPU context stays usable.
+ * on = 0 restores normal sweeps. */
+int nks_debug_withhold_copy(nks_problem *p, int on);
+
 /* ------------------------------------------------------------------------ */
 /* Serving: a request loop for many simulations on one GPU (no counterpart   */
 /* in the paper).  Requests of the same grid shape share one batch (above)   */

@@ -165,6 +165,7 @@ def load():
         "nks_batch_get_state": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_size_t]),
         "nks_batch_set_state": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_size_t]),
         "nks_device_bytes": (ctypes.c_size_t, [_P]),
+        "nks_debug_withhold_copy": (ctypes.c_int, [_P, ctypes.c_int]),
         "nks_server_default_opts": (None, [ctypes.POINTER(nks_server_opts)]),
         "nks_server_create": (ctypes.c_int, [ctypes.POINTER(nks_coeffs), ctypes.POINTER(nks_server_opts), pp]),
         "nks_server_submit": (ctypes.c_int, [_P, ctypes.POINTER(nks_grid), _D, _D, ctypes.c_int,
@@ -193,7 +194,7 @@ def exported_symbols():
             "nks_linear_solve", "nks_eval_energy", "nks_residual_noalloc", "nks_create_batch", "nks_batch_size",
             "nks_batch_load", "nks_batch_unload", "nks_batch_loaded", "nks_batch_step", "nks_batch_energy",
             "nks_batch_mass", "nks_batch_get_fields", "nks_batch_get_state", "nks_batch_set_state",
-            "nks_device_bytes", "nks_autotune", "nks_server_default_opts", "nks_server_create",
+            "nks_device_bytes", "nks_debug_withhold_copy", "nks_autotune", "nks_server_default_opts", "nks_server_create",
             "nks_server_submit", "nks_server_wait", "nks_server_status", "nks_server_destroy"]
 
 
@@ -360,6 +361,11 @@ class Problem:
         _check(load().nks_linear_solve(self._h, _ptr(X1), _ptr(X0), float(dt), int(mode), _ptr(b), _ptr(x),
                                        float(tol), ctypes.byref(its), ctypes.byref(res)), self._h)
         return x, its.value, res.value
+
+    def debug_withhold_copy(self, on=True):
+        """Testing hook: the Schwarz sweeps withhold a factor copy (their bounded
+        waits expire; the next solve fails with NKS_ETIMEOUT)."""
+        _check(load().nks_debug_withhold_copy(self._h, 1 if on else 0), self._h)
 
     def eval_energy(self, X):
         X = _c64(X)

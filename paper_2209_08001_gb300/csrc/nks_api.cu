@@ -939,6 +939,15 @@ int nks_get_fields(const nks_problem *H, double *c, double *eta, double *u)
     return nks_batch_get_fields(H, 0, c, eta, u);
 }
 
+int nks_debug_withhold_copy(nks_problem *H, int on)
+{
+    if (!H) return NKS_EINVAL;
+    H->P.withhold_copy = on ? 1 : 0;
+    // replayed graphs hold the flag in their kernel arguments: capture them again
+    destroy_graphs(&H->P);
+    return NKS_OK;
+}
+
 size_t nks_device_bytes(const nks_problem *H)
 {
     const Problem *P = &H->P;

@@ -339,6 +339,7 @@ struct Problem {
     };
     IterGraph graphs[2][kMaxRestart];
     bool graphs_off = false;                    // a capture failed: launch directly
+    int withhold_copy = 0;                      // test hook: sweeps withhold their first factor copy
     std::string err;
 
     void *dalloc(size_t bytes);

@@ -661,6 +661,8 @@ static int gmres_t(Problem *P, Basis<TV> K, int mode, const double *b, double *x
         P->is[i].gits = 0;
     }
     const Bat bin = P->set_mask(M_GIN, in);
+    // the sweeps' failure word starts clear for this solve
+    cudaMemset2DAsync(P->dflag + 1, (size_t)P->stride, 0, sizeof(int), (size_t)P->nb, st);
     P->count(launch_zero(n, x, st, bin));
     P->count(launch_copy(n, b, R, st, bin));
     prepare_projection(P, mode, bin);
@@ -733,6 +735,11 @@ static int gmres_t(Problem *P, Basis<TV> K, int mode, const double *b, double *x
                 rc = P->read_scalars(gm + L.scal, 8, "gmres");
             }
             if (rc) return rc;
+            for (int i = 0; i < nbt; i++)
+                if (act[i] && (P->hflags[2 * i + 1] & 4)) {
+                    P->err = "Schwarz sweep: a bulk copy of the factors did not complete";
+                    return NKS_ETIMEOUT;
+                }
             bool changed = false, left = false;
             for (int i = 0; i < nbt; i++) {
                 if (!act[i]) continue;

@@ -618,7 +618,7 @@ __global__ void __launch_bounds__(1024) k_ras_apply(DGrid g, Bat bt, const SubIn
                             const T *__restrict__ fac, const TV *__restrict__ r, TV *__restrict__ z,
                             T *__restrict__ scratch, int x_in_smem, int maxnp, long long maxblk, int wpt,
                             int pstride, int *flag, double *__restrict__ cpart, double *__restrict__ csum,
-                            unsigned int *ticket)
+                            unsigned int *ticket, int withhold)
 {
     long long io;
     if (!inst_off(bt, blockIdx.y, io)) return;
@@ -656,6 +656,7 @@ __global__ void __launch_bounds__(1024) k_ras_apply(DGrid g, Bat bt, const SubIn
 
     // the copy of use `it` into buffer it & 1
     auto issue = [&](int it) {
+        if (withhold && it == 0) return;  // test hook: this copy never lands, the bounded wait expires
         const int lev = it < nlev ? it : 2 * nlev - 1 - it;
         const long long cp = pad4((long long)(lptr[lev + 1] - lptr[lev]));
         const T *src = F + lblk[lev] + (it < nlev ? 0 : (long long)PT.nlow * cp);
@@ -775,7 +776,8 @@ __global__ void __launch_bounds__(256) k_ras_apply_lane(DGrid g, Bat bt, const S
                             const long long *__restrict__ lvl_blk, const int *__restrict__ lvl_lp,
                             const T *__restrict__ fac, const TV *__restrict__ r, TV *__restrict__ z,
                             T *__restrict__ scratch, int x_in_smem, int maxnp, long long maxblk, int *flag,
-                            double *__restrict__ cpart, double *__restrict__ csum, unsigned int *ticket)
+                            double *__restrict__ cpart, double *__restrict__ csum, unsigned int *ticket,
+                            int withhold)
 {
     long long io;
     if (!inst_off(bt, blockIdx.y, io)) return;
@@ -807,6 +809,7 @@ __global__ void __launch_bounds__(256) k_ras_apply_lane(DGrid g, Bat bt, const S
 
     // the copy of use `it` into buffer it % NBUF (NBUF - 1 levels ahead)
     auto issue = [&](int it) {
+        if (withhold && it == 0) return;  // test hook: this copy never lands, the bounded wait expires
         const int lev = it < nlev ? it : 2 * nlev - 1 - it;
         const long long cp = pad4((long long)(lptr[lev + 1] - lptr[lev]));
         const T *src = F + lblk[lev] + (it < nlev ? 0 : (long long)PT.nlow * cp);
@@ -1053,11 +1056,11 @@ void launch_apply_t(Problem *P, const TV *r, TV *z, const Bat &bt)
         auto kern = R->lane_bufs == 3 ? k_ras_apply_lane<D, NF, T, TV, 3> : k_ras_apply_lane<D, NF, T, TV, 2>;
         kern<<<dim3(R->nsub, bt.nb), tl, smem, P->stream>>>(P->g, bt, R->sub, R->lvl_ptr, R->lvl_blk, R->lvl_lp, fac, r,
                                                             z, scr, xs ? 1 : 0, R->maxnp, R->maxblk, P->dflag,
-                                                            P->partials, P->zsum, P->tickets + 3);
+                                                            P->partials, P->zsum, P->tickets + 3, P->withhold_copy);
     } else {
         k_ras_apply<D, NF, T, TV><<<dim3(R->nsub, bt.nb), threads, smem, P->stream>>>(
             P->g, bt, R->sub, R->lvl_ptr, R->lvl_blk, R->lvl_lp, fac, r, z, scr, xs ? 1 : 0, R->maxnp, R->maxblk, wpt,
-            pstride, P->dflag, P->partials, P->zsum, P->tickets + 3);
+            pstride, P->dflag, P->partials, P->zsum, P->tickets + 3, P->withhold_copy);
     }
 }
 

@@ -326,3 +326,35 @@ def test_full_size_3d128_fp64_and_mixed_steps(nks):
         assert info["energy"] <= O.energy(X0, cb)
     (_, (c64, e64, u64), _), (_, (c32, e32, u32), _) = out["fp64"], out["mixed"]
     assert rel(c32, c64) <= 1e-8 and rel(e32, e64) <= 1e-8 and rel(u32, u64) <= 1e-8
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_sweep_copy_timeout_is_reported_and_the_problem_recovers(nks, prec):
+    """Failure detection without a GPU fault: with a factor copy withheld, every
+    sweep block's bounded mbarrier wait expires (about a second); the solve
+    returns NKS_ETIMEOUT, the state stays at X^n, the context stays usable and
+    the next step matches a fresh problem bit for bit."""
+    import time
+    dim, n = 2, (24, 20)
+    op = S.options(sub=(2, 2), overlap=1, precision=prec)
+    c, e = S.initial_fields(dim, n, 0.18, 3)
+    P = nks.Problem(dim, n, 0.25, c, e, S.coefficients(), op)
+    before = P.get_fields()
+    P.debug_withhold_copy(True)
+    t0 = time.time()
+    with pytest.raises(nks.NksError) as ex:
+        P.step(0.01)
+    assert ex.value.code == 5, ex.value  # NKS_ETIMEOUT
+    assert "bulk copy" in str(ex.value)
+    assert time.time() - t0 < 60
+    after = P.get_fields()
+    for a, b in zip(before, after):
+        assert np.array_equal(a, b)
+    P.debug_withhold_copy(False)
+    P.step(0.01)
+    Q = nks.Problem(dim, n, 0.25, c, e, S.coefficients(), op)
+    Q.step(0.01)
+    for a, b in zip(P.get_fields(), Q.get_fields()):
+        assert np.array_equal(a, b)
+    P.destroy()
+    Q.destroy()
