@@ -73,7 +73,8 @@ class _Opts(ctypes.Structure):
                 ("dt_init", ctypes.c_double), ("dt_min", ctypes.c_double), ("dt_max", ctypes.c_double),
                 ("zeta", ctypes.c_double), ("dt_mode", ctypes.c_int), ("zeta_persist", ctypes.c_int),
                 ("max_retries", ctypes.c_int),
-                ("u0_rtol", ctypes.c_double), ("u0_atol", ctypes.c_double), ("u0_maxit", ctypes.c_int)]
+                ("u0_rtol", ctypes.c_double), ("u0_atol", ctypes.c_double), ("u0_maxit", ctypes.c_int),
+                ("variant", ctypes.c_int)]
 
 
 class StepInfo(ctypes.Structure):
@@ -177,7 +178,12 @@ def make_opts(op: dict):
     O.dt_mode = {"fixed": 0, "solution": 1, "energy": 2}[op["dt_mode"]]
     O.zeta_persist, O.max_retries = op["zeta_persist"], op["max_retries"]
     O.u0_rtol, O.u0_atol, O.u0_maxit = op["u0_rtol"], op["u0_atol"], op["u0_maxit"]
+    O.variant = RAS_VARIANTS[op.get("ras_variant", "left-ras")]
     return O
+
+
+# Schwarz preconditioner types of Sec. 4 / Table 2
+RAS_VARIANTS = {"left-ras": 0, "as": 1, "right-ras": 2}
 
 
 class Problem:

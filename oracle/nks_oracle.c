@@ -67,6 +67,8 @@ typedef struct {
     int max_retries;
     double u0_rtol, u0_atol;
     int u0_maxit;
+    int variant;                       /* Schwarz type (Sec. 4, Table 2): 0 left-RAS,
+                                          1 classical AS, 2 right-RAS                */
 } orc_opts;
 
 typedef struct {
@@ -876,6 +878,7 @@ typedef struct {
     double **dense;
     long **piv;
     int subsolver;
+    int variant;         /* 0 left-RAS, 1 classical AS, 2 right-RAS         */
 } ras_t;
 
 /* owned cells [o0, o1) of subdomain s along an axis of n cells split in nsub
@@ -923,6 +926,7 @@ static int ras_setup(const orc_grid *g, int nf, const orc_opts *o, const csr *J,
     R->nsub = sub[0] * sub[1] * sub[2];
     R->nf = nf;
     R->subsolver = o->subsolver;
+    R->variant = o->variant;
     R->next = (long *)calloc(R->nsub, sizeof(long));
     R->pts = (long **)calloc(R->nsub, sizeof(long *));
     R->own = (unsigned char **)calloc(R->nsub, sizeof(unsigned char *));
@@ -1065,7 +1069,15 @@ static void project(const orc_grid *g, int nf, double *z)
     }
 }
 
-/* z = P sum_i R_i^0T A_i^-1 R_i^delta r  (restricted prolongation: owned points only) */
+/*
+ * z = P M^-1 r for the three one-level Schwarz preconditioners of Sec. 4
+ * (A_i: J restricted to the overlapped box i, R_i^delta: restriction to the
+ * overlapped box, R_i^0: restriction to its owned points, zero elsewhere):
+ *   left-RAS     M^-1 = sum_i R_i^0T     A_i^-1 R_i^delta  (owned points written)
+ *   classical AS M^-1 = sum_i R_i^deltaT A_i^-1 R_i^delta  (overlaps summed)
+ *   right-RAS    M^-1 = sum_i R_i^deltaT A_i^-1 R_i^0      (owned input, overlaps summed)
+ * Sums run over the subdomains in index order.
+ */
 static void ras_apply(const orc_grid *g, const ras_t *R, int do_project, const double *r, double *z)
 {
     int nf = R->nf;
@@ -1075,12 +1087,18 @@ static void ras_apply(const orc_grid *g, const ras_t *R, int do_project, const d
         long np = R->next[s], n = np * nf;
         double *b = (double *)malloc(sizeof(double) * n), *x = (double *)malloc(sizeof(double) * n);
         for (long q = 0; q < np; q++)
-            for (int f = 0; f < nf; f++) b[q * nf + f] = r[R->pts[s][q] * nf + f];
+            for (int f = 0; f < nf; f++)
+                b[q * nf + f] = (R->variant == 2 && !R->own[s][q]) ? 0.0 : r[R->pts[s][q] * nf + f];
         if (R->subsolver == 0) ilu0_solve(&R->A[s], b, x);
         else dense_lu_solve(n, R->dense[s], R->piv[s], b, x);
-        for (long q = 0; q < np; q++)
-            if (R->own[s][q])
-                for (int f = 0; f < nf; f++) z[R->pts[s][q] * nf + f] = x[q * nf + f];
+        for (long q = 0; q < np; q++) {
+            if (R->variant == 0) {
+                if (R->own[s][q])
+                    for (int f = 0; f < nf; f++) z[R->pts[s][q] * nf + f] = x[q * nf + f];
+            } else {
+                for (int f = 0; f < nf; f++) z[R->pts[s][q] * nf + f] += x[q * nf + f];
+            }
+        }
         free(b);
         free(x);
     }

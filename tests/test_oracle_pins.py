@@ -521,3 +521,87 @@ def test_divergence_triggers_retry_with_smaller_dt():
     assert rc == oracle.ORC_EDIVERGED
     assert infos[0]["retries"] == 3
     assert infos[0]["dt"] == pytest.approx(0.01 / 2 ** 1.5, rel=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Schwarz preconditioner types (Sec. 4, Table 2) against their definitions
+# ---------------------------------------------------------------------------
+
+def _boxes(n, sub, delta):
+    """Box decomposition: per axis, box s owns [s n / sub, (s+1) n / sub) and is
+    extended by delta cells per side (periodic), or is the whole axis when the
+    extension would cover it; yields (points, owned mask) with x fastest."""
+    import itertools
+    per_axis = []
+    for nn, sb in zip(n, sub):
+        ax = []
+        for s in range(sb):
+            o0, o1 = s * nn // sb, (s + 1) * nn // sb
+            if o1 - o0 + 2 * delta >= nn:
+                cells = list(range(nn))
+            else:
+                cells = [(o0 - delta + t) % nn for t in range(o1 - o0 + 2 * delta)]
+            ax.append([(c, o0 <= c < o1) for c in cells])
+        per_axis.append(ax)
+    for combo in itertools.product(*[range(len(a)) for a in per_axis[::-1]]):
+        combo = combo[::-1]
+        cells = [per_axis[J][combo[J]] for J in range(len(n))]
+        pts, own = [], []
+        for idx in itertools.product(*[range(len(c)) for c in cells[::-1]]):
+            idx = idx[::-1]
+            p, stride, ok = 0, 1, True
+            for J in range(len(n)):
+                c, o = cells[J][idx[J]]
+                p += c * stride
+                stride *= n[J]
+                ok = ok and o
+            pts.append(p)
+            own.append(ok)
+        yield np.array(pts), np.array(own)
+
+
+@pytest.mark.parametrize("dim,n,sub,delta", [(1, (13,), (3,), 2), (2, (9, 8), (2, 2), 1), (2, (10, 9), (3, 2), 2)])
+def test_schwarz_types_match_their_definitions(dim, n, sub, delta):
+    """left-RAS, classical AS and right-RAS (exact subdomain solves, no projection)
+    against z = sum_i E_i (owned | all) A_i^-1 (all | owned) restrictions of r,
+    formed with dense inverses of J restricted to each overlapped box."""
+    cf = S.coefficients()
+    c0, e0, u0 = S.random_fields(dim, n, 31, u_amp=0.01)
+    c1 = c0 * 1.01
+    O0 = oracle.Problem(dim, n, 0.25, cf, S.options(sub=sub, overlap=delta))
+    nf = O0.nf
+    X1, X0 = O0.interleave(c1, e0, u0), O0.interleave(c0, e0, u0)
+    cb, dt = float(np.mean(c0)), 0.05
+    J = O0.jacobian_scipy(X1, X0, cb, dt, 0).toarray()
+    r = np.random.default_rng(4).standard_normal(J.shape[0])
+    want = {"left-ras": np.zeros_like(r), "as": np.zeros_like(r), "right-ras": np.zeros_like(r)}
+    for pts, own in _boxes(n, sub, delta):
+        idx = (pts[:, None] * nf + np.arange(nf)[None, :]).reshape(-1)
+        own_u = np.repeat(own, nf)
+        A = J[np.ix_(idx, idx)]
+        x = np.linalg.solve(A, r[idx])
+        want["left-ras"][idx[own_u]] = x[own_u]
+        want["as"][idx] += x
+        want["right-ras"][idx] += np.linalg.solve(A, np.where(own_u, r[idx], 0.0))
+    for var, zw in want.items():
+        O = oracle.Problem(dim, n, 0.25, cf, S.options(sub=sub, overlap=delta, subsolver=1, project=0,
+                                                       ras_variant=var))
+        rc, z = O.precond_apply(X1, X0, cb, dt, r)
+        assert rc == 0
+        assert np.linalg.norm(z - zw) <= 1e-11 * np.linalg.norm(zw), var
+
+
+def test_schwarz_types_coincide_without_overlap():
+    """delta = 0: the three types are block Jacobi (Table 2's classical AS, delta = 0)."""
+    dim, n = 2, (9, 8)
+    cf = S.coefficients()
+    c0, e0, u0 = S.random_fields(dim, n, 33, u_amp=0.01)
+    zs = []
+    for var in ("left-ras", "as", "right-ras"):
+        O = oracle.Problem(dim, n, 0.25, cf, S.options(sub=(3, 2), overlap=0, ras_variant=var))
+        X = O.interleave(c0, e0, u0)
+        r = np.random.default_rng(5).standard_normal(X.size)
+        rc, z = O.precond_apply(X, X, float(np.mean(c0)), 0.05, r)
+        assert rc == 0
+        zs.append(z)
+    assert np.array_equal(zs[0], zs[1]) and np.array_equal(zs[0], zs[2])
