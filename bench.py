@@ -230,6 +230,10 @@ def run_ours(args):
     op = S.options(**cfg["opts"])
     if args.precision:
         op["precision"] = args.precision
+    if args.variant:
+        op["ras_variant"] = args.variant
+    if args.overlap is not None:
+        op["overlap"] = args.overlap
     seed = cfg["seed"] + 1000 * rank  # independent replica per rank
     c, e = S.initial_fields(cfg["dim"], cfg["n"], cfg["cbar"], seed)
     N = c.size
@@ -353,7 +357,8 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f64" if op["precision"] == "fp64" else "f64+f32",
         "data": "synthetic (seeded SplitMix64 initial fields)",
         "config": {"workload": cfg["desc"], "precision": op["precision"], "grid": list(cfg["n"]), "points": N,
-                   "decomposition": {"sub": list(op["sub"]), "overlap": op["overlap"]},
+                   "decomposition": {"sub": list(op["sub"]), "overlap": op["overlap"],
+                                     "schwarz": op.get("ras_variant", "left-ras")},
                    "steps_in_workload": cfg["steps"],
                    "timed_steps": "steps 1..K of the workload from its initial state",
                    "l2": "working set (state, Krylov basis, ~0.65 GB of Schwarz factors) far above the 129 MB L2",
@@ -585,6 +590,9 @@ def main():
     ap.add_argument("--batch", type=int, default=0,
                     help="B > 0: B instances of the workload stepped as one batch (beside one alone)")
     ap.add_argument("--serve", action="store_true", help="the serving workload (p50/p99 latency, throughput)")
+    ap.add_argument("--variant", default=None, choices=["left-ras", "as", "right-ras"],
+                    help="Schwarz preconditioner type (default: the workload's, left-RAS)")
+    ap.add_argument("--overlap", type=int, default=None, help="override the workload's Schwarz overlap delta")
     ap.add_argument("--autotune", action="store_true",
                     help="pick the Schwarz decomposition with nks_autotune before timing")
     ap.add_argument("--requests", type=int, default=64, help="--serve: requests in the stream")

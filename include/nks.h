@@ -46,6 +46,11 @@ extern "C" {
 #define NKS_ECUDA 6      /* CUDA runtime error                                    */
 #define NKS_EPIVOT 7     /* zero pivot in an ILU(0) subdomain factorisation       */
 
+/* Schwarz preconditioner types (nks_opts.ras_variant, Sec. 4) */
+#define NKS_LEFT_RAS 0
+#define NKS_AS 1
+#define NKS_RIGHT_RAS 2
+
 /* precision modes */
 #define NKS_FP64 0       /* everything in FP64                                     */
 #define NKS_MIXED 1      /* FP32 Schwarz factors/sub-solves and Krylov basis;
@@ -106,6 +111,11 @@ typedef struct {
  *   max_retries        divergence retries (dt /= sqrt 2, zeta *= 2) per step
  *   u0_rtol/atol/maxit initial mechanical equilibrium solve
  *   timing             1: record per-kernel CUDA-event times (nks_get_stats)
+ *   ras_variant        Schwarz type (Sec. 4, Table 2): NKS_LEFT_RAS (default,
+ *                      sum_i R_i^0T A_i^-1 R_i^delta), NKS_AS (classical,
+ *                      sum_i R_i^deltaT A_i^-1 R_i^delta), NKS_RIGHT_RAS
+ *                      (sum_i R_i^deltaT A_i^-1 R_i^0); overlaps of the last two
+ *                      are summed in box order; all coincide for overlap 0
  *   graphs             1: each GMRES iteration replays a CUDA graph captured on
  *                      its first use (kernels of all batch slots and the read-back
  *                      of the iteration's scalars); ignored when timing = 1
@@ -128,6 +138,7 @@ typedef struct {
     int u0_maxit;
     int timing;
     int graphs;
+    int ras_variant;
 } nks_opts;
 
 /* Optional device allocator (for example a framework's caching allocator).

@@ -18,6 +18,8 @@ LIB_PATH = os.path.join(HERE, "libnks.so")
 
 NKS_OK, NKS_EINVAL, NKS_EDOMAIN, NKS_ENOMEM, NKS_EDIVERGED, NKS_ETIMEOUT, NKS_ECUDA, NKS_EPIVOT = range(8)
 NKS_FP64, NKS_MIXED = 0, 1
+# Schwarz preconditioner types (Sec. 4, Table 2)
+RAS_VARIANTS = {"left-ras": 0, "as": 1, "right-ras": 2}
 DT_MODES = {"fixed": 0, "solution": 1, "energy": 2}
 KERNEL_CLASSES = ["residual", "jacobian_action", "schwarz_apply", "assembly_ilu0", "gs_dots", "gs_update",
                   "projection", "energy_mass", "vector_ops", "hessenberg"]
@@ -51,7 +53,8 @@ class nks_opts(ctypes.Structure):
                 ("dt_init", ctypes.c_double), ("dt_min", ctypes.c_double), ("dt_max", ctypes.c_double),
                 ("zeta", ctypes.c_double), ("dt_mode", ctypes.c_int), ("zeta_persist", ctypes.c_int),
                 ("max_retries", ctypes.c_int), ("u0_rtol", ctypes.c_double), ("u0_atol", ctypes.c_double),
-                ("u0_maxit", ctypes.c_int), ("timing", ctypes.c_int), ("graphs", ctypes.c_int)]
+                ("u0_maxit", ctypes.c_int), ("timing", ctypes.c_int), ("graphs", ctypes.c_int),
+                ("ras_variant", ctypes.c_int)]
 
 
 class nks_server_opts(ctypes.Structure):
@@ -246,6 +249,8 @@ def make_opts(op: dict, timing=False):
         o.dt_mode = DT_MODES[op["dt_mode"]] if isinstance(op["dt_mode"], str) else int(op["dt_mode"])
     if "precision" in op:
         o.precision = {"fp64": NKS_FP64, "mixed": NKS_MIXED}.get(op["precision"], op["precision"])
+    if "ras_variant" in op:
+        o.ras_variant = RAS_VARIANTS.get(op["ras_variant"], op["ras_variant"])
     o.timing = 1 if timing else 0
     return o
 

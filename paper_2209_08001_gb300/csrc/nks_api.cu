@@ -657,6 +657,10 @@ static int validate(const nks_grid *grid, const nks_coeffs *coeffs, const nks_op
         g_create_error = "opts: precision must be NKS_FP64 or NKS_MIXED";
         return NKS_EINVAL;
     }
+    if (opts->ras_variant < NKS_LEFT_RAS || opts->ras_variant > NKS_RIGHT_RAS) {
+        g_create_error = "opts: ras_variant must be NKS_LEFT_RAS, NKS_AS or NKS_RIGHT_RAS";
+        return NKS_EINVAL;
+    }
     return NKS_OK;
 }
 

@@ -618,7 +618,7 @@ __global__ void __launch_bounds__(1024) k_ras_apply(DGrid g, Bat bt, const SubIn
                             const T *__restrict__ fac, const TV *__restrict__ r, TV *__restrict__ z,
                             T *__restrict__ scratch, int x_in_smem, int maxnp, long long maxblk, int wpt,
                             int pstride, int *flag, double *__restrict__ cpart, double *__restrict__ csum,
-                            unsigned int *ticket, int withhold)
+                            unsigned int *ticket, int withhold, int variant)
 {
     long long io;
     if (!inst_off(bt, blockIdx.y, io)) return;
@@ -675,14 +675,17 @@ __global__ void __launch_bounds__(1024) k_ras_apply(DGrid g, Bat bt, const SubIn
     __syncthreads();
     if (tid == 0) issue(0);
     for (int i = tid; i < np; i += blockDim.x) lps[i] = lvl_lp[si.pos_off + i];
-    // gather R_i^delta r
+    // gather R_i^delta r (right-RAS: R_i^0 r, the owned points only)
     for (int q = tid; q < np; q += blockDim.x) {
         const int lx = q % si.L[0], ly = (q / si.L[0]) % si.L[1], lz = q / (si.L[0] * si.L[1]);
         const int lp = lx + sy * ly + sz * lz;
         const long long gp = index_of(g, wrapi(si.org[0] + lx, g.n[0]), wrapi(si.org[1] + ly, g.n[1]),
                                       wrapi(si.org[2] + lz, g.n[2]));
+        const bool take = variant != NKS_RIGHT_RAS ||
+                          (lx >= si.own0[0] && lx < si.own1[0] && ly >= si.own0[1] && ly < si.own1[1] &&
+                           lz >= si.own0[2] && lz < si.own1[2]);
 #pragma unroll
-        for (int f = 0; f < NF; f++) x[f * npx + lp] = (T)r[f * N + gp];
+        for (int f = 0; f < NF; f++) x[f * npx + lp] = take ? (T)r[f * N + gp] : (T)0;
     }
     __syncthreads();
     bool failed = false;
@@ -725,6 +728,15 @@ __global__ void __launch_bounds__(1024) k_ras_apply(DGrid g, Bat bt, const SubIn
             mbar_wait_bounded(&bar[0], 0);
             mbar_wait_bounded(&bar[1], 0);
         }
+    }
+    if (variant != NKS_LEFT_RAS) {
+        // overlapped prolongation (classical AS, right-RAS): the whole box solution goes
+        // to the box's slot of the scratch vector; k_as_sum adds the boxes covering a point
+        if (x_in_smem) {
+            T *bo = scratch + si.scr_off;
+            for (int i = failed ? NF * npx : tid; i < NF * npx; i += blockDim.x) bo[i] = x[i];
+        }
+        return;
     }
     // restricted prolongation: owned points only; the sum of the written z_c feeds the
     // projection's mean (FP64 per thread, fixed block tree, last block adds the blocks in order)
@@ -777,7 +789,7 @@ __global__ void __launch_bounds__(256) k_ras_apply_lane(DGrid g, Bat bt, const S
                             const T *__restrict__ fac, const TV *__restrict__ r, TV *__restrict__ z,
                             T *__restrict__ scratch, int x_in_smem, int maxnp, long long maxblk, int *flag,
                             double *__restrict__ cpart, double *__restrict__ csum, unsigned int *ticket,
-                            int withhold)
+                            int withhold, int variant)
 {
     long long io;
     if (!inst_off(bt, blockIdx.y, io)) return;
@@ -828,14 +840,17 @@ __global__ void __launch_bounds__(256) k_ras_apply_lane(DGrid g, Bat bt, const S
     if (tid == 0)
         for (int q = 0; q < NBUF - 1 && q < nuse; q++) issue(q);
     for (int i = tid; i < np; i += blockDim.x) lps[i] = lvl_lp[si.pos_off + i];
-    // gather R_i^delta r
+    // gather R_i^delta r (right-RAS: R_i^0 r, the owned points only)
     for (int q = tid; q < np; q += blockDim.x) {
         const int lx = q % si.L[0], ly = (q / si.L[0]) % si.L[1], lz = q / (si.L[0] * si.L[1]);
         const int lp = lx + sy * ly + sz * lz;
         const long long gp = index_of(g, wrapi(si.org[0] + lx, g.n[0]), wrapi(si.org[1] + ly, g.n[1]),
                                       wrapi(si.org[2] + lz, g.n[2]));
+        const bool take = variant != NKS_RIGHT_RAS ||
+                          (lx >= si.own0[0] && lx < si.own1[0] && ly >= si.own0[1] && ly < si.own1[1] &&
+                           lz >= si.own0[2] && lz < si.own1[2]);
 #pragma unroll
-        for (int f = 0; f < NF; f++) x[f * npx + lp] = (T)r[f * N + gp];
+        for (int f = 0; f < NF; f++) x[f * npx + lp] = take ? (T)r[f * N + gp] : (T)0;
     }
     __syncthreads();
     bool failed = false;
@@ -872,6 +887,15 @@ __global__ void __launch_bounds__(256) k_ras_apply_lane(DGrid g, Bat bt, const S
                 mbar_wait_bounded(&bar[u % NBUF], (uint32_t)((u / NBUF) & 1));
         }
     }
+    if (variant != NKS_LEFT_RAS) {
+        // overlapped prolongation (classical AS, right-RAS): the whole box solution goes
+        // to the box's slot of the scratch vector; k_as_sum adds the boxes covering a point
+        if (x_in_smem) {
+            T *bo = scratch + si.scr_off;
+            for (int i = failed ? NF * npx : tid; i < NF * npx; i += blockDim.x) bo[i] = x[i];
+        }
+        return;
+    }
     // restricted prolongation: owned points only; the sum of the written z_c feeds the
     // projection's mean (FP64 per thread, fixed block tree, last block adds the blocks in order)
     double cs[1] = {0.0};
@@ -892,6 +916,86 @@ __global__ void __launch_bounds__(256) k_ras_apply_lane(DGrid g, Bat bt, const S
         block_reduce_store_n<1>(cs, cpart);
         grid_finalize(cpart, 1, csum, ticket);
     }
+}
+
+// Overlapped prolongation of classical AS and right-RAS: z at a grid point is
+// the sum, over the boxes whose overlapped range covers it, of their solutions
+// there, added in box-index order (a fixed order: deterministic sums).  Per
+// axis the covering boxes are among the owner and its two neighbours; the sum
+// of z_c feeds the projection's mean as in the restricted prolongation.
+template <int NF, typename T, typename TV>
+__global__ void __launch_bounds__(kRedThreads) k_as_sum(DGrid g, Bat bt, const SubInfo *__restrict__ subs, int sub0,
+                                                        int sub1, int sub2, const T *__restrict__ bout,
+                                                        TV *__restrict__ z, double *__restrict__ cpart,
+                                                        double *__restrict__ csum, unsigned int *ticket)
+{
+    long long io;
+    if (!inst_off(bt, blockIdx.y, io)) return;
+    bout = shift(bout, io);
+    z = shift(z, io);
+    cpart = shift(cpart, io);
+    csum = shift(csum, io);
+    ticket = shift(ticket, io);
+    const int sub[3] = {sub0, sub1, sub2};
+    const int astride[3] = {1, sub0, sub0 * sub1};
+    const int N = (int)g.N;
+    double cs[1] = {0.0};
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < N; p += gridDim.x * blockDim.x) {
+        const int c3[3] = {p % g.n[0], (p / g.n[0]) % g.n[1], p / (g.n[0] * g.n[1])};
+        int nb[3], bi[3][3], li[3][3];
+#pragma unroll
+        for (int J = 0; J < 3; J++) {
+            nb[J] = 0;
+            const int n = g.n[J], sb = sub[J], c = c3[J];
+            if (J >= g.dim || sb == 1) {
+                // one box along this axis (every box of a periodic single-box axis spans it)
+                const SubInfo &b0 = subs[0];
+                bi[J][0] = 0;
+                li[J][0] = J >= g.dim ? 0 : ((c - b0.org[J]) % n + n) % n;
+                nb[J] = 1;
+                continue;
+            }
+            int s = (int)((long long)c * sb / n);
+            while ((long long)s * n / sb > c) s--;
+            while ((long long)(s + 1) * n / sb <= c) s++;
+            // candidates in increasing box index
+            int cand[3] = {(s + sb - 1) % sb, s, (s + 1) % sb};
+            for (int a = 1; a < 3; a++)
+                for (int q = a; q > 0 && cand[q - 1] > cand[q]; q--) {
+                    const int t = cand[q];
+                    cand[q] = cand[q - 1];
+                    cand[q - 1] = t;
+                }
+            for (int a = 0; a < 3; a++) {
+                if (a > 0 && cand[a] == cand[a - 1]) continue;
+                const SubInfo &b = subs[cand[a] * astride[J]];
+                const int l = ((c - b.org[J]) % n + n) % n;
+                if (l < b.L[J]) {
+                    bi[J][nb[J]] = cand[a];
+                    li[J][nb[J]] = l;
+                    nb[J]++;
+                }
+            }
+        }
+        T acc[NF];
+#pragma unroll
+        for (int f = 0; f < NF; f++) acc[f] = (T)0;
+        for (int i2 = 0; i2 < nb[2]; i2++)
+            for (int i1 = 0; i1 < nb[1]; i1++)
+                for (int i0 = 0; i0 < nb[0]; i0++) {
+                    const int s = bi[0][i0] + sub0 * (bi[1][i1] + sub1 * bi[2][i2]);
+                    const SubInfo &b = subs[s];
+                    const int lp = li[0][i0] + b.px * (li[1][i1] + b.py * li[2][i2]);
+                    const T *xb = bout + b.scr_off;
+#pragma unroll
+                    for (int f = 0; f < NF; f++) acc[f] += xb[f * b.npx + lp];
+                }
+#pragma unroll
+        for (int f = 0; f < NF; f++) z[(long long)f * N + p] = (TV)acc[f];
+        cs[0] += (double)(TV)acc[0];
+    }
+    block_reduce_store_n<1>(cs, cpart);
+    grid_finalize(cpart, 1, csum, ticket);
 }
 
 // projection P: sums of z_c and of sign_m(p) z_uI for every null mode m.
@@ -1056,11 +1160,18 @@ void launch_apply_t(Problem *P, const TV *r, TV *z, const Bat &bt)
         auto kern = R->lane_bufs == 3 ? k_ras_apply_lane<D, NF, T, TV, 3> : k_ras_apply_lane<D, NF, T, TV, 2>;
         kern<<<dim3(R->nsub, bt.nb), tl, smem, P->stream>>>(P->g, bt, R->sub, R->lvl_ptr, R->lvl_blk, R->lvl_lp, fac, r,
                                                             z, scr, xs ? 1 : 0, R->maxnp, R->maxblk, P->dflag,
-                                                            P->partials, P->zsum, P->tickets + 3, P->withhold_copy);
+                                                            P->partials, P->zsum, P->tickets + 3, P->withhold_copy,
+                                                            P->opts.ras_variant);
     } else {
         k_ras_apply<D, NF, T, TV><<<dim3(R->nsub, bt.nb), threads, smem, P->stream>>>(
             P->g, bt, R->sub, R->lvl_ptr, R->lvl_blk, R->lvl_lp, fac, r, z, scr, xs ? 1 : 0, R->maxnp, R->maxblk, wpt,
-            pstride, P->dflag, P->partials, P->zsum, P->tickets + 3, P->withhold_copy);
+            pstride, P->dflag, P->partials, P->zsum, P->tickets + 3, P->withhold_copy, P->opts.ras_variant);
+    }
+    if (P->opts.ras_variant != NKS_LEFT_RAS) {
+        int sub[3] = {1, 1, 1};
+        for (int J = 0; J < P->g.dim; J++) sub[J] = std::max(1, P->opts.sub[J]);
+        k_as_sum<NF, T, TV><<<dim3(P->rb, bt.nb), kRedThreads, 0, P->stream>>>(
+            P->g, bt, R->sub, sub[0], sub[1], sub[2], scr, z, P->partials, P->zsum, P->tickets + 3);
     }
 }
 
@@ -1139,7 +1250,7 @@ void ras_apply_t(Problem *P, const TV *r, TV *z, const Bat &bt)
     case 32: launch_apply_t<3, 2, TV>(P, r, z, bt); break;
     case 35: launch_apply_t<3, 5, TV>(P, r, z, bt); break;
     }
-    P->count(1);
+    P->count(P->opts.ras_variant != NKS_LEFT_RAS ? 2 : 1);
     P->tock(2);
 }
 template void ras_apply_t<double>(Problem *, const double *, double *, const Bat &);
@@ -1168,10 +1279,14 @@ void ras_slab_items(Problem *P, std::vector<SlabItem> &items)
     const bool mixed = P->opts.precision == NKS_MIXED;
     items.push_back({(void **)&R->fac, sizeof(double) * (size_t)R->fac_elems});
     items.push_back({(void **)&R->proj, sizeof(double) * 64});
-    if (!R->x_smem && !mixed) items.push_back({(void **)&R->scratch, sizeof(double) * (size_t)R->scr_elems});
+    // the scratch vector holds the sub-vectors when they miss shared memory, and the box
+    // solutions of the overlapped prolongation (classical AS, right-RAS)
+    const bool summed = P->opts.ras_variant != NKS_LEFT_RAS;
+    if ((!R->x_smem || summed) && !mixed)
+        items.push_back({(void **)&R->scratch, sizeof(double) * (size_t)R->scr_elems});
     if (mixed) {
         items.push_back({(void **)&R->fac32, sizeof(float) * (size_t)R->fac_elems});
-        if (!R->x_smem32) items.push_back({(void **)&R->scratch32, sizeof(float) * (size_t)R->scr_elems});
+        if (!R->x_smem32 || summed) items.push_back({(void **)&R->scratch32, sizeof(float) * (size_t)R->scr_elems});
     }
 }
 

@@ -358,3 +358,51 @@ def test_sweep_copy_timeout_is_reported_and_the_problem_recovers(nks, prec):
         assert np.array_equal(a, b)
     P.destroy()
     Q.destroy()
+
+
+@pytest.mark.parametrize("variant", ["as", "right-ras"])
+@pytest.mark.parametrize("dim,n,sub,ov", [(2, (37, 29), (3, 2), 1), (2, (40, 36), (2, 3), 2),
+                                          (3, (11, 10, 9), (2, 2, 2), 1)])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_schwarz_types_match_oracle(nks, variant, dim, n, sub, ov, prec):
+    """Classical AS and right-RAS (Sec. 4, Table 2): the preconditioner with the
+    projection against the oracle's, and a GMRES solve; overlaps summed in box order."""
+    cf = S.coefficients()
+    op = S.options(sub=sub, overlap=ov, ras_variant=variant, precision=prec)
+    (c1, e1, u1), (c0, e0, u0) = _pair(dim, n, 300 + dim)
+    P = nks.Problem(dim, n, 0.25, c0, e0, cf, op)
+    O = oracle.Problem(dim, n, 0.25, cf, op)
+    N, nf = P.N, P.nf
+    cb = float(np.sum(c0) / N)
+    X1g, X0g = soa(c1, e1, u1), soa(c0, e0, u0)
+    X1o, X0o = O.interleave(c1, e1, u1), O.interleave(c0, e0, u0)
+    to_soa = lambda Xo: soa(*O.split(Xo))
+    dt = 0.07
+    r = np.random.default_rng(16).standard_normal(nf * N)
+    z = P.apply_preconditioner(X1g, X0g, dt, r)
+    rc, zo = O.precond_apply(X1o, X0o, cb, dt, O.interleave(*split_soa(r, N, nf)))
+    assert rc == 0
+    assert rel(z, to_soa(zo)) <= (1e-9 if prec == "fp64" else 1e-4)
+    assert abs(z[:N].sum()) <= (1e-11 if prec == "fp64" else 1e-5) * np.abs(z[:N]).sum()
+    b = -P.eval_residual(X1g, X0g, dt, 0)
+    tol = 1e-9 * np.linalg.norm(b)
+    x, its, res = P.linear_solve(X1g, X0g, dt, b, tol)
+    assert res <= tol
+    rc, xo, its_o, res_o = O.linear_solve(X1o, X0o, cb, dt, O.interleave(*split_soa(b, N, nf)), tol)
+    assert rel(x, to_soa(xo)) <= 1e-6
+    if prec == "fp64":
+        assert abs(its - its_o) <= max(2, its_o // 5)
+    P.destroy()
+
+
+def test_classical_as_without_overlap_config_2d64(nks):
+    """The paper's choice (Table 2): classical AS, delta = 0, ILU(0)-reuse; ten
+    steps of the 64^2 workload against the oracle."""
+    cfg = S.CONFIGS["2d64"]
+    op = S.options(**dict(cfg["opts"], overlap=0, ras_variant="as"))
+    P, (c, e), (cg, eg, ug), (co, eo, uo), infos, oinf, e0 = _run_both(nks, 2, cfg["n"], cfg["cbar"], cfg["seed"],
+                                                                        cfg["steps"], op)
+    assert rel(cg, co) <= 1e-8 and rel(eg, eo) <= 1e-8 and rel(ug, uo) <= 1e-8
+    m0 = c.sum() * 0.25 ** 2
+    for i in infos:
+        assert abs(i["mass"] - m0) <= 1e-12 * m0
