@@ -234,6 +234,8 @@ def run_ours(args):
         op["ras_variant"] = args.variant
     if args.overlap is not None:
         op["overlap"] = args.overlap
+    if args.u0_maxit is not None:
+        op["u0_maxit"] = args.u0_maxit
     seed = cfg["seed"] + 1000 * rank  # independent replica per rank
     c, e = S.initial_fields(cfg["dim"], cfg["n"], cfg["cbar"], seed)
     N = c.size
@@ -593,6 +595,8 @@ def main():
     ap.add_argument("--variant", default=None, choices=["left-ras", "as", "right-ras"],
                     help="Schwarz preconditioner type (default: the workload's, left-RAS)")
     ap.add_argument("--overlap", type=int, default=None, help="override the workload's Schwarz overlap delta")
+    ap.add_argument("--u0-maxit", type=int, default=None,
+                    help="Newton iterations allowed to the initial mechanical equilibrium (set-up, not timed)")
     ap.add_argument("--autotune", action="store_true",
                     help="pick the Schwarz decomposition with nks_autotune before timing")
     ap.add_argument("--requests", type=int, default=64, help="--serve: requests in the stream")
