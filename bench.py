@@ -41,7 +41,8 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # keyed by (workload, precision, kernel class), from one ncu capture of the 512^2 probe
 # (bench.py --probe gmres512: the same 68x68 boxes, 64 of them) scaled by the 256 boxes of
 # the 1024^2 launch; an entry is removed whenever the kernel changes
-NCU_TRAFFIC = {("2d1024", "fp64", "schwarz_apply"): 4 * (173.719808e6 + 4.763648e6)}
+NCU_TRAFFIC = {("2d1024", "fp64", "schwarz_apply"): 4 * (173.719808e6 + 4.763648e6),
+               ("2d1024", "mixed", "schwarz_apply"): 4 * (86.979328e6 + 2.500608e6)}
 
 
 def kernel_rates(st, cfg, mixed, pk):
