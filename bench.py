@@ -343,7 +343,8 @@ def run_ours(args):
         Q.destroy()
         t_e2e = max_over_ranks(dist, t_e2e, torch.device("cuda", local))
         e2e = {"value": points_all / t_e2e, "unit": METRIC,
-               "h2d_bytes_per_step": int(2 * N * 8 / args.steps), "d2h_bytes_per_step": int(3 * N * 8),
+               "h2d_bytes_per_step": int(2 * N * 8 / args.steps),
+               "d2h_bytes_per_step": int((2 + (cfg["dim"] if S.coefficients().get("Lscale", 1.0) else 0)) * N * 8),
                "includes": "problem creation from host fields (upload + initial mechanical equilibrium solve), "
                            "K steps, fields read back to host after every step"}
 
