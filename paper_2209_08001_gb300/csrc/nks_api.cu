@@ -129,6 +129,7 @@ void Problem::upload_isc()
         double *r = h + (size_t)i * I_NSC;
         for (int q = 0; q < I_NSC; q++) r[q] = 0.0;
         r[I_DT] = is[i].dt > 0.0 ? is[i].dt : 1.0;
+        r[I_IDT] = 1.0 / r[I_DT];
         r[I_CBAR0] = is[i].cbar0;
         r[I_LAM] = is[i].lam;
     }
@@ -709,7 +710,7 @@ int nks_create_batch(const nks_grid *grid, int nb, const double *c, const double
     g.dim = grid->dim;
     for (int J = 0; J < 3; J++) g.n[J] = J < grid->dim ? grid->n[J] : 1;
     g.N = N;
-    g.h = grid->h;
+    set_spacing(g, grid->h);
     P->N = N;
     P->k = derive_coefficients(*coeffs, g.dim, 0.0);  // the mean composition of each instance lives in isc
     P->nf = P->k.nf;
@@ -733,7 +734,7 @@ int nks_create_batch(const nks_grid *grid, int nb, const double *c, const double
     std::vector<SlabItem> items;
     auto add = [&](void *pp, size_t bytes) { items.push_back({(void **)pp, bytes}); };
     double **vecs[] = {&P->Xn, &P->Xprev, &P->X, &P->Xt, &P->F, &P->Ft, &P->S, &P->B, &P->W, &P->Z, &P->R,
-                       &P->T64, &P->Jec, &P->ec};
+                       &P->T64};
     for (double **v : vecs) add(v, vb);
     add(&P->V, vb * (mixed ? 1 : m + 1));
     add(&P->part, 4 * fb);
@@ -756,7 +757,6 @@ int nks_create_batch(const nks_grid *grid, int nb, const double *c, const double
         add(&P->Zf, fvb);
         add(&P->partf, sizeof(float) * 4 * (size_t)g.N);
         add(&P->mobf, sizeof(float) * g.dim * (size_t)g.N);
-        add(&P->Jecf, sizeof(float) * 2 * (size_t)g.N);
     }
     ras_slab_items(P, items);
     std::vector<size_t> off(items.size());
@@ -783,14 +783,7 @@ int nks_create_batch(const nks_grid *grid, int nb, const double *c, const double
     ras_prepare_launch(P);
     cudaMemsetAsync(P->slab, 0, (size_t)P->stride * nb, P->stream);
     cudaMemsetAsync(P->dmask, 0, sizeof(int) * kMasks * nb, P->stream);
-    {
-        // e_c: 1 on the c plane of every instance
-        const std::vector<double> ones((size_t)g.N, 1.0);
-        for (int i = 0; i < nb; i++)
-            cudaMemcpyAsync(shift(P->ec, (long long)i * P->stride), ones.data(), fb, cudaMemcpyHostToDevice,
-                            P->stream);
-        rc = P->sync_check("create");
-    }
+    rc = P->sync_check("create");
     if (!rc && c) {
         for (int i = 0; i < nb; i++) load_fields(P, i, c + (size_t)i * N, eta + (size_t)i * N);
         rc = init_instances(P, std::vector<char>(nb, 1));
@@ -1131,8 +1124,7 @@ int nks_apply_jacobian(nks_problem *H, const double *X1, const double *X0, doubl
             // as the Arnoldi step applies it: FP32 vectors, coefficients and arithmetic
             refresh_f32_coefficients(P, bt);
             P->count(launch_convert(P->nvec, P->B, P->Zf, P->stream, bt));
-            P->count(launch_jv32(P->g, P->k, P->isc, mode, P->partf, P->mobf, P->Zf, P->Wf, P->stream, bt, nullptr,
-                                 nullptr));
+            P->count(launch_jv32(P->g, P->k, P->isc, mode, P->partf, P->mobf, P->Zf, P->Wf, P->stream, bt, nullptr));
             P->count(launch_convert(P->nvec, P->Wf, P->W, P->stream, bt));
         } else {
             P->count(launch_jv64(P->g, P->k, P->isc, mode, P->part, P->mob, P->B, P->Gc, P->sig, P->W, P->stream,

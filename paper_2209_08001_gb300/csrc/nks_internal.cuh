@@ -27,7 +27,16 @@ struct DGrid {
     int n[3];
     long long N;
     double h;
+    double ih, ih2, i2h;  // 1/h, 1/h^2, 1/(2h), formed on the host
 };
+
+inline void set_spacing(DGrid &g, double h)
+{
+    g.h = h;
+    g.ih = 1.0 / h;
+    g.ih2 = 1.0 / (h * h);
+    g.i2h = 0.5 / h;
+}
 
 // Coefficients after the App. B reduction to the polynomial coefficients M_k.
 struct DCoef {
@@ -69,7 +78,8 @@ __device__ __forceinline__ bool inst_off(const Bat &bt, int b, long long &off)
 }
 
 // per-instance device scalars (isc, 8 doubles in each slab)
-enum { I_DT = 0, I_CBAR0 = 1, I_LAM = 2, I_NSC = 8 };
+// I_IDT = 1/dt, formed on the host: a division per thread costs a dozen FP64-pipe operations
+enum { I_DT = 0, I_CBAR0 = 1, I_LAM = 2, I_IDT = 3, I_NSC = 8 };
 
 // ---------------------------------------------------------------------------
 // index helpers
@@ -169,14 +179,14 @@ int launch_trace0(const DGrid &g, const DCoef &k, const double *isc, const doubl
 int launch_residual(const DGrid &g, const DCoef &k, const double *isc, int mode, const double *X1, const double *X0,
                     const double *tr0, const double *mob, double *Gc, double *sig, double *part, double *F, int *flag,
                     double *partials, int rb, cudaStream_t st, const Bat &bt);
-// J v, or J P v with Jec = J e_c and zsum[0] = sum of v_c (P: mean of v_c removed).
+// J v, or J P v with zsum[0] = sum of v_c (P: mean of v_c removed).
 // FP64: two passes through the dG / sig temporaries (N and d(d+1)/2 N doubles).
 int launch_jv64(const DGrid &g, const DCoef &k, const double *isc, int mode, const double *part, const double *mob,
                 const double *v, double *dG, double *sig, double *Jv, cudaStream_t st, const Bat &bt,
-                const double *Jec = nullptr, const double *zsum = nullptr);
-// FP32 arithmetic and storage (FP32 copies of part, mob and the c/eta planes of J e_c)
+                const double *zsum = nullptr);
+// FP32 arithmetic and storage (FP32 copies of part and mob)
 int launch_jv32(const DGrid &g, const DCoef &k, const double *isc, int mode, const float *part, const float *mob,
-                const float *v, float *Jv, cudaStream_t st, const Bat &bt, const float *Jec, const double *zsum);
+                const float *v, float *Jv, cudaStream_t st, const Bat &bt, const double *zsum);
 int launch_energy(const DGrid &g, const DCoef &k, const double *isc, const double *X, double *partials, int rb,
                   cudaStream_t st, const Bat &bt);
 int launch_finalize(const double *partials, int nblocks, int K, double *out, cudaStream_t st, const Bat &bt);
@@ -308,10 +318,7 @@ struct Problem {
     double *dscal = nullptr;                    // small device scalars
     int *dflag = nullptr;
     double *zsum = nullptr;                     // sum of z_c of the last Schwarz sweep (device)
-    double *Jec = nullptr;                      // J e_c at the current iterate (c and eta planes used)
-    double *ec = nullptr;                       // e_c: 1 on the c plane, 0 elsewhere
     float *partf = nullptr, *mobf = nullptr;    // mixed precision: FP32 copies of part and mob for J v
-    float *Jecf = nullptr;                      // mixed precision: c and eta planes of J e_c in FP32
     unsigned int *tickets = nullptr;            // last-block counters of the fused reductions (start at 0)
 
     // Krylov workspace

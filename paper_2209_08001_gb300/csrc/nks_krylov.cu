@@ -565,24 +565,22 @@ static void apply_J(Problem *P, int mode, const TV *v, TV *out, bool project_inp
     P->tick(1);
     if constexpr (sizeof(TV) == sizeof(float))
         P->count(launch_jv32(P->g, P->k, P->isc, mode, P->partf, P->mobf, v, out, P->stream, bt,
-                             project_input ? P->Jecf : nullptr, P->zsum));
+                             project_input ? P->zsum : nullptr));
     else
         P->count(launch_jv64(P->g, P->k, P->isc, mode, P->part, P->mob, v, P->Gc, P->sig, out, P->stream, bt,
-                             project_input ? P->Jec : nullptr, P->zsum));
+                             project_input ? P->zsum : nullptr));
     P->tock(1);
 }
 
-// J e_c at the current iterate: with it the Arnoldi step applies J P z without
-// projecting z (see the Jacobian action).  In mixed precision the FP32 copies
-// of the operator's coefficients are refreshed here as well.
-static void prepare_projection(Problem *P, int mode, const Bat &bt)
+// Start of a solve: in mixed precision the FP32 copies of the operator's
+// coefficients at the current iterate.  (The projection needs no set-up: the
+// Arnoldi step applies J to z with the mean of z_c taken off, see the Jacobian
+// action.)
+static void prepare_operator(Problem *P, const Bat &bt)
 {
+    if (P->opts.precision != NKS_MIXED) return;
     P->tick(1);
-    P->count(launch_jv64(P->g, P->k, P->isc, mode, P->part, P->mob, P->ec, P->Gc, P->sig, P->Jec, P->stream, bt));
-    if (P->opts.precision == NKS_MIXED) {
-        P->count(launch_convert(2 * P->N, P->Jec, P->Jecf, P->stream, bt));
-        refresh_f32_coefficients(P, bt);
-    }
+    refresh_f32_coefficients(P, bt);
     P->tock(1);
 }
 
@@ -665,7 +663,7 @@ static int gmres_t(Problem *P, Basis<TV> K, int mode, const double *b, double *x
     cudaMemset2DAsync(P->dflag + 1, (size_t)P->stride, 0, sizeof(int), (size_t)P->nb, st);
     P->count(launch_zero(n, x, st, bin));
     P->count(launch_copy(n, b, R, st, bin));
-    prepare_projection(P, mode, bin);
+    prepare_operator(P, bin);
     std::vector<double> b2;
     int rc = norm2_batch(P, R, bin, b2);
     if (rc) return rc;

@@ -52,7 +52,7 @@ extern "C" int nks_residual_noalloc(const nks_grid *grid, const nks_coeffs *coef
             return NKS_EINVAL;
         }
     g.N = (long long)g.n[0] * g.n[1] * g.n[2];
-    g.h = grid->h;
+    set_spacing(g, grid->h);
     if (g.N > NKS_NOALLOC_MAX_POINTS) {
         set_thread_error("nks_residual_noalloc: grid larger than NKS_NOALLOC_MAX_POINTS points; use the problem API");
         return NKS_EINVAL;
@@ -83,6 +83,7 @@ extern "C" int nks_residual_noalloc(const nks_grid *grid, const nks_coeffs *coef
     cudaMemsetAsync(flag, 0, sizeof(int), st);
     double hisc[I_NSC] = {0.0};
     hisc[I_DT] = dt;
+    hisc[I_IDT] = 1.0 / dt;
     hisc[I_CBAR0] = cbar0;
     // from pageable memory: the source is staged before the call returns
     cudaMemcpyAsync(isc, hisc, sizeof(hisc), cudaMemcpyHostToDevice, st);

@@ -24,6 +24,7 @@
 // (cp.async.bulk + mbarrier) brings it into shared memory while the previous
 // level is being computed; the dependent path touches shared memory only.
 #include <math.h>
+#include <type_traits>
 
 #include <algorithm>
 #include <set>
@@ -41,6 +42,7 @@ struct SubInfo {
     int own0[3], own1[3];     // owned local range [own0, own1)
     int np, nlev;
     int px, py, npx;          // odd row pitches of the box vector and its padded size (bank-conflict free levels)
+    int qx, qy, nqx;          // the same with kHalo zero cells around the box (FP32 sweep, 1-D and 2-D)
     long long lvl_off;        // into lvl_ptr / lvl_blk (nlev + 1 entries)
     long long pos_off;        // into lvl_lp (np entries): packed coordinates x | y << 10 | z << 20
     long long fac_off;        // into the factor array (elements)
@@ -53,15 +55,26 @@ struct RasPlan {
     int maxnp = 0;
     int maxnpx = 0;                 // largest padded box vector
     int maxcnt = 0;                 // most points in one wavefront level
+    int maxnlev = 0;                // most wavefront levels of one box
     int npart = 0;                  // stage-A partial sums per point (largest of the two sweeps)
     long long maxblk = 0;           // largest forward or backward part of a level (elements)
     long long fac_elems = 0;
+    // FP32 factors, point-major inside each level part: point k's forward values at
+    // k * sf32, its backward values (strict upper, then inverse pivots) at k * sb32
+    int sf32 = 0, sb32 = 0;
+    long long maxblk32 = 0;         // largest FP32 level part (elements)
+    long long fac32_elems = 0;
+    long long nlev_all = 0;         // levels of all boxes
+    long long *lvl_src = nullptr;   // FP64 factor offset of every level's block (nlev_all + 1 entries)
+    int maxnqx = 0;                 // largest box plane with the halo
+    bool halo32 = false;            // FP32 sweep on the halo layout (no neighbour bounds checks)
     long long scr_elems = 0;        // global scratch vector of the sweeps (when x is not in shared memory)
     long long total_np = 0;         // overlapped points of all subdomains
     bool x_smem = true;
     size_t smem_bytes = 0;          // dynamic shared memory of the apply kernel (FP64 factors)
     bool x_smem32 = true;
     int lane_bufs = 2;              // factor buffers of the FP32 sweep
+    int blocks_per_sm32 = 1;        // resident FP32 sweep blocks per SM (plan estimate)
     size_t smem_bytes32 = 0;        // same for the FP32 factors of the mixed-precision mode
     SubInfo *sub = nullptr;
     // runtime copies of the pattern for the assembly kernel
@@ -116,6 +129,24 @@ static Pattern compile_time_pattern(int d, int nf)
 
 __host__ __device__ static inline long long pad4(long long n) { return (n + 3) & ~3LL; }
 
+// Row stride of the FP32 point-major factor layout for n values per point: a
+// multiple of 4 (16-byte loads) whose quotient by 4 is odd, so the 16-byte loads
+// of 8 consecutive points fall in 8 distinct bank groups.
+__host__ __device__ constexpr int pm_stride(int n)
+{
+    const int s = (n + 3) & ~3;
+    return (s / 4) % 2 == 1 ? s : s + 4;
+}
+
+template <int D, int NF>
+struct PM {
+    static constexpr Pattern P = make_pattern<D, NF>();
+    static constexpr int SF = pm_stride(P.nlow), SB = pm_stride(P.nup + NF), PP = P.nlow + P.nup + NF;
+};
+
+// zero cells on each side of the box in the halo layout: the stencil reach
+constexpr int kHalo = 2;
+
 // factor-part buffers of the one-thread-per-point sweep: three (copies two levels
 // ahead) when the sub-vector still fits in shared memory, else two
 constexpr int kLaneBufsMax = 3;
@@ -130,18 +161,19 @@ __host__ __device__ static inline size_t pad16(size_t n) { return (n + 15) & ~(s
 // dynamic shared memory of the apply kernel: barriers, point table, two level
 // buffers, stage-A partial sums and (when it fits) the sub-vector
 // the same for the one-thread-per-point sweep (FP32): no partial sums, kLaneBufs buffers
-static size_t apply_smem_lane(const RasPlan *R, int nf, size_t tsize, bool with_x, int nbuf)
+static size_t apply_smem_lane(const RasPlan *R, int nf, bool halo, bool with_x, int nbuf)
 {
-    size_t b = 32 + pad16((size_t)R->maxnp * sizeof(int)) + nbuf * pad16((size_t)R->maxblk * tsize);
-    if (with_x) b += pad16((size_t)R->maxnpx * nf * tsize);
+    size_t b = 32 + pad16((size_t)R->maxnp * (halo ? sizeof(unsigned short) : sizeof(int))) +
+               pad16(2 * sizeof(int) * (size_t)(R->maxnlev + 1)) + nbuf * pad16((size_t)R->maxblk32 * sizeof(float));
+    if (with_x) b += pad16((size_t)(halo ? R->maxnqx : R->maxnpx) * nf * sizeof(float));
     return b;
 }
 
 static size_t apply_smem(const RasPlan *R, int nf, size_t tsize, bool with_x)
 {
     const int pstride = (R->maxcnt + 31) / 32 * 32;
-    size_t b = 16 + pad16((size_t)R->maxnp * sizeof(int)) + 2 * pad16((size_t)R->maxblk * tsize) +
-               pad16((size_t)R->npart * pstride * tsize);
+    size_t b = 16 + pad16((size_t)R->maxnp * sizeof(int)) + pad16(2 * sizeof(int) * (size_t)(R->maxnlev + 1)) +
+               2 * pad16((size_t)R->maxblk * tsize) + pad16((size_t)R->npart * pstride * tsize);
     if (with_x) b += pad16((size_t)R->maxnpx * nf * tsize);
     return b;
 }
@@ -157,6 +189,97 @@ static int sweep_partials(int d, int nf)
     case 35: return Sched<3, 5>::npart;
     }
     return 0;
+}
+
+static int sweep_tasks(int d, int nf)
+{
+    switch (d * 10 + nf) {
+    case 12: return Sched<1, 2>::ntask;
+    case 13: return Sched<1, 3>::ntask;
+    case 22: return Sched<2, 2>::ntask;
+    case 24: return Sched<2, 4>::ntask;
+    case 32: return Sched<3, 2>::ntask;
+    case 35: return Sched<3, 5>::ntask;
+    }
+    return 1;
+}
+
+static int fp64_sweep_regs(int d, int nf, bool xs);  // registers per thread of the FP64 sweep
+
+static void sm_limits(int &nsm, int &smem_sm)
+{
+    int dev = 0;
+    nsm = 152;
+    smem_sm = 228 * 1024;
+    if (cudaGetDevice(&dev) == cudaSuccess) {
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    }
+}
+
+// Placement of the box vector of the FP64 sweep: in shared memory unless keeping
+// it there costs a wave of blocks (FP64 boxes of 2-D workloads fill an SM's shared
+// memory alone; resident boxes add throughput, the sweep being a latency-bound
+// chain of levels per box, and measured on the 16x16-box 1024^2 workload the
+// global-memory placement with every box resident is the faster one).
+static void choose_x64(const Problem *P, RasPlan *R, int nf)
+{
+    int nsm, smem_sm;
+    sm_limits(nsm, smem_sm);
+    const int d = P->g.dim, ntask = sweep_tasks(d, nf);
+    const int wpt = std::max(1, std::min((R->maxcnt + 31) / 32, 32 / ntask));
+    const int threads = ntask * wpt * 32;
+    const long long blocks = (long long)R->nsub * std::max(1, P->nb);
+    auto waves = [&](bool xs) -> long long {
+        const size_t b = apply_smem(R, nf, sizeof(double), xs);
+        const int regs = std::max(1, fp64_sweep_regs(d, nf, xs));
+        int per_sm = (int)((size_t)smem_sm / (b + 1024));
+        per_sm = std::min(per_sm, 2048 / threads);
+        per_sm = std::min(per_sm, 65536 / (threads * ((regs + 7) & ~7)));
+        per_sm = std::max(1, per_sm);
+        return (blocks + (long long)nsm * per_sm - 1) / ((long long)nsm * per_sm);
+    };
+    R->x_smem = apply_smem(R, nf, sizeof(double), true) <= 227 * 1024;
+    if (R->x_smem && waves(false) < waves(true)) R->x_smem = false;
+    R->smem_bytes = apply_smem(R, nf, sizeof(double), R->x_smem);
+}
+
+// Shared-memory layout of the FP32 sweep.  The box vector stays in shared memory
+// (from global memory its level-to-level reads run several times slower); among
+// the layouts that fit, the one with the fewest waves of blocks wins (each box
+// is a latency-bound chain of levels, so resident boxes add throughput), then
+// the halo layout (no neighbour bounds checks), then the third factor buffer.
+static void choose_lane_config(const Problem *P, RasPlan *R, int nf)
+{
+    int nsm, smem_sm;
+    sm_limits(nsm, smem_sm);
+    const long long blocks = (long long)R->nsub * std::max(1, P->nb);
+    const bool halo_ok = P->g.dim <= 2 && R->maxnqx < 65536;
+    struct Cand {
+        bool halo;
+        int nbuf;
+    };
+    const Cand cands[] = {{true, 3}, {true, 2}, {false, 3}, {false, 2}};
+    long long best_waves = -1;
+    for (const Cand &c : cands) {
+        if (c.halo && !halo_ok) continue;
+        const size_t b = apply_smem_lane(R, nf, c.halo, true, c.nbuf);
+        if (b > 227 * 1024) continue;
+        const int per_sm = std::max(1, std::min(32, (int)((size_t)smem_sm / (b + 1024))));
+        const long long waves = (blocks + (long long)nsm * per_sm - 1) / ((long long)nsm * per_sm);
+        if (best_waves < 0 || waves < best_waves) {
+            best_waves = waves;
+            R->halo32 = c.halo;
+            R->lane_bufs = c.nbuf;
+            R->blocks_per_sm32 = per_sm;
+        }
+    }
+    R->x_smem32 = best_waves >= 0;
+    if (!R->x_smem32) {
+        R->halo32 = false;
+        R->lane_bufs = 2;
+    }
+    R->smem_bytes32 = apply_smem_lane(R, nf, R->halo32, R->x_smem32, R->lane_bufs);
 }
 
 int ras_plan_create(Problem *P, std::string &err)
@@ -229,7 +352,9 @@ int ras_plan_create(Problem *P, std::string &err)
     }
     std::vector<SubInfo> infos(R->nsub);
     std::vector<int> lvl_ptr, lvl_lp;
-    std::vector<long long> lvl_blk;
+    std::vector<long long> lvl_blk, lvl_src;
+    R->sf32 = pm_stride(CP.nlow);
+    R->sb32 = pm_stride(CP.nup + nf);
     long long fac_off = 0, scr_off = 0;
     for (int s2 = 0; s2 < sub[2]; s2++)
         for (int s1 = 0; s1 < sub[1]; s1++)
@@ -266,9 +391,14 @@ int ras_plan_create(Problem *P, std::string &err)
                 si.py = d >= 2 ? (si.L[1] | 1) : 1;
                 si.npx = si.px * si.py * si.L[2];
                 R->maxnpx = std::max(R->maxnpx, si.npx);
+                si.qx = (si.L[0] + 2 * kHalo) | 1;
+                si.qy = d >= 2 ? si.L[1] + 2 * kHalo : 1;
+                si.nqx = si.qx * si.qy * si.L[2];
+                R->maxnqx = std::max(R->maxnqx, si.nqx);
                 R->total_np += si.np;
                 const int nlev = wave(si.L[0] - 1, si.L[1] - 1, si.L[2] - 1) + 1;
                 si.nlev = nlev;
+                R->maxnlev = std::max(R->maxnlev, nlev);
                 si.lvl_off = (long long)lvl_ptr.size();
                 si.pos_off = (long long)lvl_lp.size();
                 si.fac_off = fac_off;
@@ -288,6 +418,8 @@ int ras_plan_create(Problem *P, std::string &err)
                     }
                     const long long cp = pad4((long long)bylev[l].size());
                     R->maxblk = std::max(R->maxblk, std::max<long long>(CP.nlow, CP.nup + nf) * cp);
+                    R->maxblk32 = std::max(R->maxblk32, (long long)std::max(R->sf32, R->sb32) * cp);
+                    lvl_src.push_back(fac_off + blk);
                     R->maxcnt = std::max(R->maxcnt, (int)bylev[l].size());
                     blk += (long long)per_pt * cp;
                 }
@@ -299,11 +431,11 @@ int ras_plan_create(Problem *P, std::string &err)
             }
     R->npart = sweep_partials(d, nf);
     R->fac_elems = fac_off;
-    R->x_smem = apply_smem(R, nf, sizeof(double), true) <= 227 * 1024;
-    R->smem_bytes = apply_smem(R, nf, sizeof(double), R->x_smem);
-    R->lane_bufs = apply_smem_lane(R, nf, sizeof(float), true, kLaneBufsMax) <= 227 * 1024 ? kLaneBufsMax : 2;
-    R->x_smem32 = apply_smem_lane(R, nf, sizeof(float), true, R->lane_bufs) <= 227 * 1024;
-    R->smem_bytes32 = apply_smem_lane(R, nf, sizeof(float), R->x_smem32, R->lane_bufs);
+    R->nlev_all = (long long)lvl_src.size();
+    lvl_src.push_back(fac_off);
+    R->fac32_elems = fac_off / per_pt * (R->sf32 + R->sb32);
+    choose_x64(P, R, nf);
+    choose_lane_config(P, R, nf);
     if (R->smem_bytes > 227 * 1024) {
         err = "decomposition: subdomain boxes too large for the Schwarz kernel (use more subdomains)";
         return NKS_EINVAL;
@@ -328,7 +460,8 @@ int ras_plan_create(Problem *P, std::string &err)
               up((void **)&R->sub, infos.data(), infos.size() * sizeof(SubInfo)) &&
               up((void **)&R->lvl_ptr, lvl_ptr.data(), lvl_ptr.size() * sizeof(int)) &&
               up((void **)&R->lvl_blk, lvl_blk.data(), lvl_blk.size() * sizeof(long long)) &&
-              up((void **)&R->lvl_lp, lvl_lp.data(), lvl_lp.size() * sizeof(int));
+              up((void **)&R->lvl_lp, lvl_lp.data(), lvl_lp.size() * sizeof(int)) &&
+              up((void **)&R->lvl_src, lvl_src.data(), lvl_src.size() * sizeof(long long));
     if (!ok) {
         err = "out of device memory (Schwarz tables)";
         return NKS_ENOMEM;
@@ -612,11 +745,13 @@ __device__ __forceinline__ void stage_b(int kk, int lp, int lx, int ly, int lz, 
 // level by level (factor parts streamed by TMA one level ahead, two-stage
 // schedule inside a level), restricted prolongation.  Threads are grouped in
 // warps per stage-A task: warp w serves task w / wpt, points (w % wpt) * 32 + lane.
-template <int D, int NF, typename T, typename TV>
+// XS: the box vector x lives in shared memory (a compile-time choice, so that its
+// loads are shared-memory loads rather than generic ones), else in global scratch.
+template <int D, int NF, typename T, typename TV, bool XS>
 __global__ void __launch_bounds__(1024) k_ras_apply(DGrid g, Bat bt, const SubInfo *__restrict__ subs, const int *__restrict__ lvl_ptr,
                             const long long *__restrict__ lvl_blk, const int *__restrict__ lvl_lp,
                             const T *__restrict__ fac, const TV *__restrict__ r, TV *__restrict__ z,
-                            T *__restrict__ scratch, int x_in_smem, int maxnp, long long maxblk, int wpt,
+                            T *__restrict__ scratch, int maxnp, int maxnlev, long long maxblk, int wpt,
                             int pstride, int *flag, double *__restrict__ cpart, double *__restrict__ csum,
                             unsigned int *ticket, int withhold, int variant)
 {
@@ -634,13 +769,20 @@ __global__ void __launch_bounds__(1024) k_ras_apply(DGrid g, Bat bt, const SubIn
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
     int *lps = reinterpret_cast<int *>(smem + 16);
-    T *buf0 = reinterpret_cast<T *>(smem + 16 + pad16((size_t)maxnp * sizeof(int)));
+    // level tables: first point of each level, factor offset of each level block
+    int *const slp = reinterpret_cast<int *>(smem + 16 + pad16((size_t)maxnp * sizeof(int)));
+    int *const slo = slp + (maxnlev + 1);
+    T *buf0 = reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(slp) +
+                                    pad16(2 * sizeof(int) * (size_t)(maxnlev + 1)));
     T *buf1 = reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(buf0) + pad16((size_t)maxblk * sizeof(T)));
     T *pt = reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(buf1) + pad16((size_t)maxblk * sizeof(T)));
     const SubInfo si = subs[blockIdx.x];
-    T *x = x_in_smem ? reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(pt) +
-                                             pad16((size_t)Sched<D, NF>::npart * pstride * sizeof(T)))
-                     : scratch + si.scr_off;
+    T *x;
+    if constexpr (XS)
+        x = reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(pt) +
+                                  pad16((size_t)Sched<D, NF>::npart * pstride * sizeof(T)));
+    else
+        x = scratch + si.scr_off;
     const int np = si.np, nlev = si.nlev;  // x holds NF planes of si.npx (padded) entries
     const int *lptr = lvl_ptr + si.lvl_off;
     const long long *lblk = lvl_blk + si.lvl_off;
@@ -652,14 +794,15 @@ __global__ void __launch_bounds__(1024) k_ras_apply(DGrid g, Bat bt, const SubIn
     const int warp = tid >> 5, lane = tid & 31;
     const int task = warp / wpt, kq0 = (warp % wpt) * 32 + lane;
     const int nwb = min(4, (int)(blockDim.x >> 5));
+    const int prod = blockDim.x - 1;  // the copy-issuing thread (its warp has the fewest stage-A points)
     const int nuse = 2 * nlev;  // forward parts of levels 0..nlev-1, then backward parts of nlev-1..0
 
     // the copy of use `it` into buffer it & 1
     auto issue = [&](int it) {
         if (withhold && it == 0) return;  // test hook: this copy never lands, the bounded wait expires
         const int lev = it < nlev ? it : 2 * nlev - 1 - it;
-        const long long cp = pad4((long long)(lptr[lev + 1] - lptr[lev]));
-        const T *src = F + lblk[lev] + (it < nlev ? 0 : (long long)PT.nlow * cp);
+        const int cp = (slp[lev + 1] - slp[lev] + 3) & ~3;
+        const T *src = F + slo[lev] + (it < nlev ? 0 : PT.nlow * cp);
         const uint32_t bytes = (uint32_t)((it < nlev ? PT.nlow : PT.nup + NF) * cp * (long long)sizeof(T));
         uint64_t *b = &bar[it & 1];
         fence_proxy_async();
@@ -667,13 +810,17 @@ __global__ void __launch_bounds__(1024) k_ras_apply(DGrid g, Bat bt, const SubIn
         bulk_g2s((it & 1) ? buf1 : buf0, src, bytes, b);
     };
 
-    if (tid == 0) {
+    if (tid == prod) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         fence_mbar_init();
     }
+    for (int i = tid; i <= nlev; i += blockDim.x) {
+        slp[i] = lptr[i];
+        slo[i] = (int)lblk[i];
+    }
     __syncthreads();
-    if (tid == 0) issue(0);
+    if (tid == prod) issue(0);
     for (int i = tid; i < np; i += blockDim.x) lps[i] = lvl_lp[si.pos_off + i];
     // gather R_i^delta r (right-RAS: R_i^0 r, the owned points only)
     for (int q = tid; q < np; q += blockDim.x) {
@@ -690,10 +837,10 @@ __global__ void __launch_bounds__(1024) k_ras_apply(DGrid g, Bat bt, const SubIn
     __syncthreads();
     bool failed = false;
     for (int it = 0; it < nuse; it++) {
-        if (tid == 0 && it + 1 < nuse) issue(it + 1);
+        if (tid == prod && it + 1 < nuse) issue(it + 1);
         const bool ok = mbar_wait_bounded(&bar[it & 1], (uint32_t)((it >> 1) & 1));
         const int lev = it < nlev ? it : 2 * nlev - 1 - it;
-        const int base = lptr[lev], cnt = lptr[lev + 1] - base;
+        const int base = slp[lev], cnt = slp[lev + 1] - base;
         const long long cp = pad4((long long)cnt);
         const T *B = (it & 1) ? buf1 : buf0;
         const bool fwd = it < nlev;
@@ -723,7 +870,7 @@ __global__ void __launch_bounds__(1024) k_ras_apply(DGrid g, Bat bt, const SubIn
     if (failed) {
         // a copy never completed: report it, let outstanding copies land (bounded), and
         // write nothing (the block still takes its turn in the sum below)
-        if (tid == 0) {
+        if (tid == prod) {
             atomicOr(flag + 1, 4);
             mbar_wait_bounded(&bar[0], 0);
             mbar_wait_bounded(&bar[1], 0);
@@ -732,7 +879,7 @@ __global__ void __launch_bounds__(1024) k_ras_apply(DGrid g, Bat bt, const SubIn
     if (variant != NKS_LEFT_RAS) {
         // overlapped prolongation (classical AS, right-RAS): the whole box solution goes
         // to the box's slot of the scratch vector; k_as_sum adds the boxes covering a point
-        if (x_in_smem) {
+        if (XS) {
             T *bo = scratch + si.scr_off;
             for (int i = failed ? NF * npx : tid; i < NF * npx; i += blockDim.x) bo[i] = x[i];
         }
@@ -760,37 +907,79 @@ __global__ void __launch_bounds__(1024) k_ras_apply(DGrid g, Bat bt, const SubIn
     }
 }
 
-// All rows of one point in sweep order: each row's full lower (forward) or
+// All rows of one point in sweep order, from the point's own factor values Bk
+// (point-major FP32 layout, 16-byte aligned): each row's full lower (forward) or
 // upper (backward) part, including the same-point entries computed just before.
-template <int D, int NF, bool FWD, typename T>
-__device__ __forceinline__ void point_rows(int k, int lp, int lx, int ly, int lz, const T *B, long long cp, T *x,
-                                           int np, const SubInfo &si, int sy, int sz)
+// HALO: x carries kHalo zero cells around the box, so every neighbour is read
+// at a fixed offset from lp (an entry whose column lies outside the box holds 0
+// in the factors and meets 0 in x); otherwise the neighbour is bounds-checked
+// against the box and an outside column reads x at lp itself (times 0).
+template <int D, int NF, bool FWD, bool HALO>
+__device__ __forceinline__ void point_rows_pm(const float *__restrict__ Bk, float *x, int npx, int lp, int lx, int ly,
+                                              int lz, const SubInfo &si, int sy, int sz)
 {
     constexpr Pattern PT = Pat<D, NF>::v;
+    constexpr int NR = FWD ? PT.nlow : PT.nup + NF;
+    constexpr int NV = (NR + 3) / 4;
+    float4 bv[NV];
+    static_for<0, NV>([&](auto jc) {
+        constexpr int j = decltype(jc)::value;
+        bv[j] = reinterpret_cast<const float4 *>(Bk)[j];
+    });
+    auto val = [&](auto rc) -> float {
+        constexpr int r = decltype(rc)::value;
+        if constexpr (r % 4 == 0) return bv[r / 4].x;
+        else if constexpr (r % 4 == 1) return bv[r / 4].y;
+        else if constexpr (r % 4 == 2) return bv[r / 4].z;
+        else return bv[r / 4].w;
+    };
     static_for<0, NF>([&](auto fi) {
         constexpr int f = FWD ? decltype(fi)::value : NF - 1 - decltype(fi)::value;
         constexpr int b = FWD ? PT.rowoff[f] : PT.rowoff[f] + PT.diag[f] + 1;
         constexpr int e = FWD ? PT.rowoff[f] + PT.diag[f] : PT.rowoff[f] + PT.len[f];
-        constexpr int drow = PT.nup + f;  // inverse pivot row in the backward part
-        const T s = slot_sum<D, NF, b, e, T>(B, cp, k, x, np, lp, lx, ly, lz, si, sy, sz);
-        if constexpr (FWD) x[f * np + lp] -= s;
-        else x[f * np + lp] = (x[f * np + lp] - s) * B[(long long)drow * cp + k];
+        float s = 0.f;
+        static_for<b, e>([&](auto ic) {
+            constexpr int a = decltype(ic)::value;
+            constexpr int dx = PT.dx[a], dy = PT.dy[a], dz = PT.dz[a], fc = PT.fc[a];
+            int idx;
+            if constexpr (HALO) {
+                static_assert(dz == 0 && dx >= -kHalo && dx <= kHalo && dy >= -kHalo && dy <= kHalo,
+                              "stencil reach beyond the halo");
+                idx = lp + dx + sy * dy;
+            } else {
+                const bool ok = nb_inbox<dx, dy, dz>(lx, ly, lz, si);
+                idx = ok ? lp + dx + sy * dy + sz * dz : lp;
+            }
+            s += val(std::integral_constant<int, PT.st[a]>{}) * x[fc * npx + idx];
+        });
+        if constexpr (FWD) x[f * npx + lp] -= s;
+        else x[f * npx + lp] = (x[f * npx + lp] - s) * val(std::integral_constant<int, PT.nup + f>{});
     });
 }
 
-// The same sweeps with one thread per point doing all its rows (every lower or
-// upper entry, then the next row): one block barrier per level instead of two
-// and no partial sums.  Used for FP32 factors, where the per-point instruction
-// stream is cheap and the latency of the two-stage schedule dominates; the FP64
-// pipe (1/64 rate) prefers the two-stage schedule's spread over warps.
-template <int D, int NF, typename T, typename TV, int NBUF>
+// The sweeps with one thread per point doing all its rows (every lower or upper
+// entry, then the next row): one block barrier per level and no partial sums.
+// Used for FP32 factors, where the per-point instruction stream is cheap and
+// the latency of the two-stage schedule dominates; the FP64 pipe (1/64 rate)
+// prefers the two-stage schedule's spread over warps.  Factor parts (point-major)
+// are streamed by TMA NBUF - 1 levels ahead, issued by the block's last thread
+// (its warp has the fewest points of a level, warp 0 the most); the level tables
+// are copied to shared memory first (global loads on every level's critical path
+// cost more than the arithmetic).  XS: x in shared memory; HALO: x on the halo
+// layout (1-D and 2-D), the point table then holds 16-bit x indices.
+template <int D, int NF, int NBUF, bool XS, bool HALO>
 __global__ void __launch_bounds__(256) k_ras_apply_lane(DGrid g, Bat bt, const SubInfo *__restrict__ subs, const int *__restrict__ lvl_ptr,
                             const long long *__restrict__ lvl_blk, const int *__restrict__ lvl_lp,
-                            const T *__restrict__ fac, const TV *__restrict__ r, TV *__restrict__ z,
-                            T *__restrict__ scratch, int x_in_smem, int maxnp, long long maxblk, int *flag,
+                            const float *__restrict__ fac, const float *__restrict__ r, float *__restrict__ z,
+                            float *__restrict__ scratch, int maxnp, int maxnlev, long long maxblk, int *flag,
                             double *__restrict__ cpart, double *__restrict__ csum, unsigned int *ticket,
                             int withhold, int variant)
 {
+    static_assert(XS || !HALO, "the halo layout lives in shared memory");
+    static_assert(D <= 2 || !HALO, "the halo layout covers 1-D and 2-D boxes");
+    using T = float;
+    using LT = typename std::conditional<HALO, unsigned short, int>::type;
+    using L = PM<D, NF>;
     long long io;
     if (!inst_off(bt, blockIdx.y, io)) return;
     fac = shift(fac, io);
@@ -801,76 +990,113 @@ __global__ void __launch_bounds__(256) k_ras_apply_lane(DGrid g, Bat bt, const S
     cpart = shift(cpart, io);
     csum = shift(csum, io);
     ticket = shift(ticket, io);
-    constexpr Pattern PT = Pat<D, NF>::v;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
-    int *lps = reinterpret_cast<int *>(smem + 32);
+    LT *lps = reinterpret_cast<LT *>(smem + 32);
     const size_t bstride = pad16((size_t)maxblk * sizeof(T)) / sizeof(T);
-    T *const buf0 = reinterpret_cast<T *>(smem + 32 + pad16((size_t)maxnp * sizeof(int)));
+    // level tables: first point of each level, FP32 factor offset of each level block
+    int *const slp = reinterpret_cast<int *>(smem + 32 + pad16((size_t)maxnp * sizeof(LT)));
+    int *const slo = slp + (maxnlev + 1);
+    T *const buf0 = reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(slp) +
+                                          pad16(2 * sizeof(int) * (size_t)(maxnlev + 1)));
     const SubInfo si = subs[blockIdx.x];
-    T *x = x_in_smem ? buf0 + NBUF * bstride : scratch + si.scr_off;
-    const int np = si.np, nlev = si.nlev;  // x holds NF planes of si.npx (padded) entries
+    T *x;
+    if constexpr (XS) x = buf0 + NBUF * bstride;
+    else x = scratch + si.scr_off;
+    const int np = si.np, nlev = si.nlev;
     const int *lptr = lvl_ptr + si.lvl_off;
     const long long *lblk = lvl_blk + si.lvl_off;
-    const T *F = fac + si.fac_off;
+    const T *F = fac + si.fac_off / L::PP * (L::SF + L::SB);
     const long long N = g.N;
-    const int sy = si.px, sz = si.px * si.py;
-    const int npx = si.npx;
+    // x layout: NF planes of npx entries, local (lx, ly, lz) at l0 + lx + sy ly + sz lz
+    const int sy = HALO ? si.qx : si.px, sz = HALO ? si.qx * si.qy : si.px * si.py;
+    const int npx = HALO ? si.nqx : si.npx;
+    const int l0 = HALO ? kHalo * (1 + (D >= 2 ? si.qx : 0)) : 0;
     const int tid = threadIdx.x;
+    const int prod = blockDim.x - 1;  // the copy-issuing thread
     const int nuse = 2 * nlev;  // forward parts of levels 0..nlev-1, then backward parts of nlev-1..0
 
     // the copy of use `it` into buffer it % NBUF (NBUF - 1 levels ahead)
     auto issue = [&](int it) {
         if (withhold && it == 0) return;  // test hook: this copy never lands, the bounded wait expires
-        const int lev = it < nlev ? it : 2 * nlev - 1 - it;
-        const long long cp = pad4((long long)(lptr[lev + 1] - lptr[lev]));
-        const T *src = F + lblk[lev] + (it < nlev ? 0 : (long long)PT.nlow * cp);
-        const uint32_t bytes = (uint32_t)((it < nlev ? PT.nlow : PT.nup + NF) * cp * (long long)sizeof(T));
+        const bool fw = it < nlev;
+        const int lev = fw ? it : 2 * nlev - 1 - it;
+        const int cp = (slp[lev + 1] - slp[lev] + 3) & ~3;
+        const T *src = F + slo[lev] + (fw ? 0 : cp * L::SF);
+        const uint32_t bytes = (uint32_t)((fw ? L::SF : L::SB) * cp * (long long)sizeof(T));
         uint64_t *b = &bar[it % NBUF];
         fence_proxy_async();
         mbar_expect_tx(b, bytes);
         bulk_g2s(buf0 + (it % NBUF) * bstride, src, bytes, b);
     };
 
-    if (tid == 0) {
+    if (tid == prod) {
         for (int q = 0; q < NBUF; q++) mbar_init(&bar[q], 1);
         fence_mbar_init();
     }
+    for (int i = tid; i <= nlev; i += blockDim.x) {
+        slp[i] = lptr[i];
+        slo[i] = (int)(lblk[i] / L::PP * (L::SF + L::SB));
+    }
     __syncthreads();
-    if (tid == 0)
+    if (tid == prod)
         for (int q = 0; q < NBUF - 1 && q < nuse; q++) issue(q);
-    for (int i = tid; i < np; i += blockDim.x) lps[i] = lvl_lp[si.pos_off + i];
-    // gather R_i^delta r (right-RAS: R_i^0 r, the owned points only)
-    for (int q = tid; q < np; q += blockDim.x) {
-        const int lx = q % si.L[0], ly = (q / si.L[0]) % si.L[1], lz = q / (si.L[0] * si.L[1]);
-        const int lp = lx + sy * ly + sz * lz;
-        const long long gp = index_of(g, wrapi(si.org[0] + lx, g.n[0]), wrapi(si.org[1] + ly, g.n[1]),
-                                      wrapi(si.org[2] + lz, g.n[2]));
-        const bool take = variant != NKS_RIGHT_RAS ||
-                          (lx >= si.own0[0] && lx < si.own1[0] && ly >= si.own0[1] && ly < si.own1[1] &&
-                           lz >= si.own0[2] && lz < si.own1[2]);
+    for (int i = tid; i < np; i += blockDim.x) {
+        const int pk = lvl_lp[si.pos_off + i];
+        if constexpr (HALO) lps[i] = (LT)(l0 + (pk & 1023) + sy * ((pk >> 10) & 1023));
+        else lps[i] = pk;
+    }
+    auto owned = [&](int lx, int ly, int lz) {
+        return lx >= si.own0[0] && lx < si.own1[0] && ly >= si.own0[1] && ly < si.own1[1] && lz >= si.own0[2] &&
+               lz < si.own1[2];
+    };
+    // gather R_i^delta r (right-RAS: R_i^0 r, the owned points only); with the halo
+    // layout every cell of the planes is written (zero outside the box)
+    if constexpr (HALO) {
+        for (int q = tid; q < npx; q += blockDim.x) {
+            const int lx = q % sy - kHalo, ly = D >= 2 ? q / sy - kHalo : 0;
+            const bool in = lx >= 0 && lx < si.L[0] && ly >= 0 && ly < si.L[1];
+            const bool take = in && (variant != NKS_RIGHT_RAS || owned(lx, ly, 0));
+            const long long gp =
+                take ? index_of(g, wrapi(si.org[0] + lx, g.n[0]), wrapi(si.org[1] + ly, g.n[1]), 0) : 0;
 #pragma unroll
-        for (int f = 0; f < NF; f++) x[f * npx + lp] = take ? (T)r[f * N + gp] : (T)0;
+            for (int f = 0; f < NF; f++) x[f * npx + q] = take ? (T)r[f * N + gp] : (T)0;
+        }
+    } else {
+        for (int q = tid; q < np; q += blockDim.x) {
+            const int lx = q % si.L[0], ly = (q / si.L[0]) % si.L[1], lz = q / (si.L[0] * si.L[1]);
+            const int lp = lx + sy * ly + sz * lz;
+            const long long gp = index_of(g, wrapi(si.org[0] + lx, g.n[0]), wrapi(si.org[1] + ly, g.n[1]),
+                                          wrapi(si.org[2] + lz, g.n[2]));
+            const bool take = variant != NKS_RIGHT_RAS || owned(lx, ly, lz);
+#pragma unroll
+            for (int f = 0; f < NF; f++) x[f * npx + lp] = take ? (T)r[f * N + gp] : (T)0;
+        }
     }
     __syncthreads();
     bool failed = false;
     int failed_at = 0;
     for (int it = 0; it < nuse; it++) {
         // buffer (it + NBUF - 1) % NBUF last served use it - 1 (finished at the barrier)
-        if (tid == 0 && it + NBUF - 1 < nuse) issue(it + NBUF - 1);
+        if (tid == prod && it + NBUF - 1 < nuse) issue(it + NBUF - 1);
         const bool ok = mbar_wait_bounded(&bar[it % NBUF], (uint32_t)((it / NBUF) & 1));
         const int lev = it < nlev ? it : 2 * nlev - 1 - it;
-        const int base = lptr[lev], cnt = lptr[lev + 1] - base;
-        const long long cp = pad4((long long)cnt);
+        const int base = slp[lev], cnt = slp[lev + 1] - base;
         const T *B = buf0 + (it % NBUF) * bstride;
         const bool fwd = it < nlev;
         if (ok)
             for (int k = tid; k < cnt; k += blockDim.x) {
-                const int pk = lps[base + k];
-                const int lx = pk & 1023, ly = (pk >> 10) & 1023, lz = pk >> 20;
-                const int lp = lx + sy * ly + sz * lz;
-                if (fwd) point_rows<D, NF, true, T>(k, lp, lx, ly, lz, B, cp, x, npx, si, sy, sz);
-                else point_rows<D, NF, false, T>(k, lp, lx, ly, lz, B, cp, x, npx, si, sy, sz);
+                if constexpr (HALO) {
+                    const int lp = lps[base + k];
+                    if (fwd) point_rows_pm<D, NF, true, true>(B + k * L::SF, x, npx, lp, 0, 0, 0, si, sy, sz);
+                    else point_rows_pm<D, NF, false, true>(B + k * L::SB, x, npx, lp, 0, 0, 0, si, sy, sz);
+                } else {
+                    const int pk = lps[base + k];
+                    const int lx = pk & 1023, ly = (pk >> 10) & 1023, lz = pk >> 20;
+                    const int lp = lx + sy * ly + sz * lz;
+                    if (fwd) point_rows_pm<D, NF, true, false>(B + k * L::SF, x, npx, lp, lx, ly, lz, si, sy, sz);
+                    else point_rows_pm<D, NF, false, false>(B + k * L::SB, x, npx, lp, lx, ly, lz, si, sy, sz);
+                }
             }
         failed = __syncthreads_or(!ok);
         if (failed) {
@@ -881,18 +1107,24 @@ __global__ void __launch_bounds__(256) k_ras_apply_lane(DGrid g, Bat bt, const S
     if (failed) {
         // a copy never completed: report it, let outstanding copies land (bounded), and
         // write nothing (the block still takes its turn in the sum below)
-        if (tid == 0) {
+        if (tid == prod) {
             atomicOr(flag + 1, 4);
             for (int u = failed_at; u < nuse && u < failed_at + NBUF; u++)
                 mbar_wait_bounded(&bar[u % NBUF], (uint32_t)((u / NBUF) & 1));
         }
     }
     if (variant != NKS_LEFT_RAS) {
-        // overlapped prolongation (classical AS, right-RAS): the whole box solution goes
-        // to the box's slot of the scratch vector; k_as_sum adds the boxes covering a point
-        if (x_in_smem) {
+        // overlapped prolongation (classical AS, right-RAS): the box solution goes to the
+        // box's slot of the scratch vector (unpadded box layout); k_as_sum adds the boxes
+        // covering a point
+        if (XS) {
             T *bo = scratch + si.scr_off;
-            for (int i = failed ? NF * npx : tid; i < NF * npx; i += blockDim.x) bo[i] = x[i];
+            for (int q = failed ? np : tid; q < np; q += blockDim.x) {
+                const int lx = q % si.L[0], ly = (q / si.L[0]) % si.L[1], lz = q / (si.L[0] * si.L[1]);
+                const int lo = lx + si.px * ly + si.px * si.py * lz, lq = l0 + lx + sy * ly + sz * lz;
+#pragma unroll
+                for (int f = 0; f < NF; f++) bo[f * si.npx + lo] = x[f * npx + lq];
+            }
         }
         return;
     }
@@ -901,15 +1133,13 @@ __global__ void __launch_bounds__(256) k_ras_apply_lane(DGrid g, Bat bt, const S
     double cs[1] = {0.0};
     for (int q = failed ? np : tid; q < np; q += blockDim.x) {
         const int lx = q % si.L[0], ly = (q / si.L[0]) % si.L[1], lz = q / (si.L[0] * si.L[1]);
-        if (lx < si.own0[0] || lx >= si.own1[0] || ly < si.own0[1] || ly >= si.own1[1] || lz < si.own0[2] ||
-            lz >= si.own1[2])
-            continue;
-        const int lp = lx + sy * ly + sz * lz;
+        if (!owned(lx, ly, lz)) continue;
+        const int lp = l0 + lx + sy * ly + sz * lz;
         const long long gp = index_of(g, wrapi(si.org[0] + lx, g.n[0]), wrapi(si.org[1] + ly, g.n[1]),
                                       wrapi(si.org[2] + lz, g.n[2]));
 #pragma unroll
-        for (int f = 0; f < NF; f++) z[f * N + gp] = (TV)x[f * npx + lp];
-        cs[0] += (double)(TV)x[lp];
+        for (int f = 0; f < NF; f++) z[f * N + gp] = x[f * npx + lp];
+        cs[0] += (double)x[lp];
     }
     if (csum) {
         __syncthreads();
@@ -1081,14 +1311,44 @@ void launch_project_t(Problem *P, TV *z, const Bat &bt)
                                                                                                z);
 }
 
-__global__ void k_to_float(Bat bt, long long n, const double *__restrict__ a, float *__restrict__ b)
+// FP32 copy of the factors in the point-major layout: level block i (FP64 offset
+// lvl_src[i], cp padded points, rows of cp values) becomes cp rows of SF forward
+// values then cp rows of SB backward values; the padding values are zero.
+template <int D, int NF>
+__global__ void __launch_bounds__(256) k_fac_to_f32(Bat bt, long long nlev_all, const long long *__restrict__ lvl_src,
+                                                    const double *__restrict__ a, float *__restrict__ b)
 {
     long long io;
     if (!inst_off(bt, blockIdx.y, io)) return;
     a = shift(a, io);
     b = shift(b, io);
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        b[i] = (float)a[i];
+    using L = PM<D, NF>;
+    constexpr int NL = L::P.nlow, NU = L::P.nup + NF;
+    for (long long i = blockIdx.x; i < nlev_all; i += gridDim.x) {
+        const long long s0 = lvl_src[i];
+        const int cp = (int)((lvl_src[i + 1] - s0) / L::PP);
+        const long long d0 = s0 / L::PP * (L::SF + L::SB);
+        const int nfw = cp * L::SF, tot = cp * (L::SF + L::SB);
+        for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+            float v = 0.f;
+            if (e < nfw) {
+                const int k = e / L::SF, r = e - k * L::SF;
+                if (r < NL) v = (float)a[s0 + (long long)r * cp + k];
+            } else {
+                const int e2 = e - nfw, k = e2 / L::SB, r = e2 - k * L::SB;
+                if (r < NU) v = (float)a[s0 + (long long)(NL + r) * cp + k];
+            }
+            b[d0 + e] = v;
+        }
+    }
+}
+
+template <int D, int NF>
+void launch_fac_to_f32(Problem *P, const Bat &bt)
+{
+    RasPlan *R = P->ras;
+    const unsigned nblk = (unsigned)std::min<long long>(R->nlev_all, 8 * 152);
+    k_fac_to_f32<D, NF><<<dim3(nblk, bt.nb), 256, 0, P->stream>>>(bt, R->nlev_all, R->lvl_src, R->fac, R->fac32);
 }
 
 void launch_factor(Problem *P, int mode, const Bat &bt)
@@ -1110,6 +1370,23 @@ void launch_factor(Problem *P, int mode, const Bat &bt)
                                                 P->mob, R->fac, P->dflag);
 }
 
+using LaneKernel = void (*)(DGrid, Bat, const SubInfo *, const int *, const long long *, const int *, const float *,
+                           const float *, float *, float *, int, int, long long, int *, double *, double *,
+                           unsigned int *, int, int);
+
+// the FP32 sweep instantiation of the plan's layout (halo D <= 2 only; three
+// buffers only with x in shared memory)
+template <int D, int NF>
+LaneKernel lane_kernel(const RasPlan *R)
+{
+    if constexpr (D <= 2) {
+        if (R->halo32) return R->lane_bufs == 3 ? k_ras_apply_lane<D, NF, 3, true, true>
+                                                : k_ras_apply_lane<D, NF, 2, true, true>;
+    }
+    if (!R->x_smem32) return k_ras_apply_lane<D, NF, 2, false, false>;
+    return R->lane_bufs == 3 ? k_ras_apply_lane<D, NF, 3, true, false> : k_ras_apply_lane<D, NF, 2, true, false>;
+}
+
 // the sweep kernel's dynamic shared memory limit (set once, before any graph capture)
 template <int D, int NF, typename TV>
 void apply_attr(Problem *P)
@@ -1120,13 +1397,13 @@ void apply_attr(Problem *P)
     bool &attr = f32 ? R->attr_set32 : R->attr_set;
     if (smem > 48 * 1024 && !attr) {
         if constexpr (f32) {
-            cudaFuncSetAttribute(k_ras_apply_lane<D, NF, TV, TV, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            cudaFuncSetAttribute(lane_kernel<D, NF>(R), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        } else {
+            cudaFuncSetAttribute(k_ras_apply<D, NF, TV, TV, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
-            cudaFuncSetAttribute(k_ras_apply_lane<D, NF, TV, TV, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            cudaFuncSetAttribute(k_ras_apply<D, NF, TV, TV, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         }
-        else
-            cudaFuncSetAttribute(k_ras_apply<D, NF, TV, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = true;
     }
 }
@@ -1157,14 +1434,14 @@ void launch_apply_t(Problem *P, const TV *r, TV *z, const Bat &bt)
     if constexpr (f32) {
         // one thread per point of the widest level
         const int tl = std::min(256, std::max(32, (R->maxcnt + 31) / 32 * 32));
-        auto kern = R->lane_bufs == 3 ? k_ras_apply_lane<D, NF, T, TV, 3> : k_ras_apply_lane<D, NF, T, TV, 2>;
-        kern<<<dim3(R->nsub, bt.nb), tl, smem, P->stream>>>(P->g, bt, R->sub, R->lvl_ptr, R->lvl_blk, R->lvl_lp, fac, r,
-                                                            z, scr, xs ? 1 : 0, R->maxnp, R->maxblk, P->dflag,
-                                                            P->partials, P->zsum, P->tickets + 3, P->withhold_copy,
-                                                            P->opts.ras_variant);
+        lane_kernel<D, NF>(R)<<<dim3(R->nsub, bt.nb), tl, smem, P->stream>>>(
+            P->g, bt, R->sub, R->lvl_ptr, R->lvl_blk, R->lvl_lp, reinterpret_cast<const float *>(fac),
+            reinterpret_cast<const float *>(r), reinterpret_cast<float *>(z), reinterpret_cast<float *>(scr), R->maxnp,
+            R->maxnlev, R->maxblk32, P->dflag, P->partials, P->zsum, P->tickets + 3, P->withhold_copy, P->opts.ras_variant);
     } else {
-        k_ras_apply<D, NF, T, TV><<<dim3(R->nsub, bt.nb), threads, smem, P->stream>>>(
-            P->g, bt, R->sub, R->lvl_ptr, R->lvl_blk, R->lvl_lp, fac, r, z, scr, xs ? 1 : 0, R->maxnp, R->maxblk, wpt,
+        auto kern = xs ? k_ras_apply<D, NF, T, TV, true> : k_ras_apply<D, NF, T, TV, false>;
+        kern<<<dim3(R->nsub, bt.nb), threads, smem, P->stream>>>(
+            P->g, bt, R->sub, R->lvl_ptr, R->lvl_blk, R->lvl_lp, fac, r, z, scr, R->maxnp, R->maxnlev, R->maxblk, wpt,
             pstride, P->dflag, P->partials, P->zsum, P->tickets + 3, P->withhold_copy, P->opts.ras_variant);
     }
     if (P->opts.ras_variant != NKS_LEFT_RAS) {
@@ -1176,6 +1453,27 @@ void launch_apply_t(Problem *P, const TV *r, TV *z, const Bat &bt)
 }
 
 }  // namespace
+
+static int fp64_sweep_regs(int d, int nf, bool xs)
+{
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (d * 10 + nf) {
+#define NKS_REGS_CASE(D, NF)                                                                                  \
+    case D * 10 + NF:                                                                                         \
+        e = xs ? cudaFuncGetAttributes(&fa, k_ras_apply<D, NF, double, double, true>)                         \
+               : cudaFuncGetAttributes(&fa, k_ras_apply<D, NF, double, double, false>);                       \
+        break;
+        NKS_REGS_CASE(1, 2)
+        NKS_REGS_CASE(1, 3)
+        NKS_REGS_CASE(2, 2)
+        NKS_REGS_CASE(2, 4)
+        NKS_REGS_CASE(3, 2)
+        NKS_REGS_CASE(3, 5)
+#undef NKS_REGS_CASE
+    }
+    return e == cudaSuccess ? fa.numRegs : 64;
+}
 
 #define NKS_DISPATCH(FN, ...)              \
     switch (P->g.dim * 10 + P->nf) {       \
@@ -1206,7 +1504,7 @@ int ras_factor(Problem *P, int mode, const Bat &bt, const std::vector<char> &on)
         }
     }
     if (P->opts.precision == NKS_MIXED) {
-        k_to_float<<<dim3(4 * 152, bt.nb), 256, 0, P->stream>>>(bt, P->ras->fac_elems, P->ras->fac, P->ras->fac32);
+        NKS_DISPATCH(launch_fac_to_f32, P, bt);
         P->count(1);
     }
     return NKS_OK;
@@ -1285,7 +1583,7 @@ void ras_slab_items(Problem *P, std::vector<SlabItem> &items)
     if ((!R->x_smem || summed) && !mixed)
         items.push_back({(void **)&R->scratch, sizeof(double) * (size_t)R->scr_elems});
     if (mixed) {
-        items.push_back({(void **)&R->fac32, sizeof(float) * (size_t)R->fac_elems});
+        items.push_back({(void **)&R->fac32, sizeof(float) * (size_t)R->fac32_elems});
         if (!R->x_smem32 || summed) items.push_back({(void **)&R->scratch32, sizeof(float) * (size_t)R->scr_elems});
     }
 }

@@ -133,7 +133,7 @@ template <typename TV>
 __device__ inline void grad_u(const DGrid &g, const TV *U /* field 2 plane */, int x, int y, int z,
                               double (&Du)[3][3])
 {
-    const double i2h = 0.5 / g.h;
+    const double i2h = g.i2h;
     for (int I = 0; I < g.dim; I++)
         for (int J = 0; J < g.dim; J++)
             Du[I][J] = ((double)U[I * g.N + nbrJ(g, x, y, z, J, +1)] - (double)U[I * g.N + nbrJ(g, x, y, z, J, -1)]) * i2h;
@@ -189,7 +189,7 @@ __global__ void k_trace0(DGrid g, DCoef k, Bat bt, const double *__restrict__ is
     const double *U = X0 + 2 * g.N;
     double tr = 0.0;
     for (int K = 0; K < g.dim; K++)
-        tr += (U[K * g.N + nbrJ(g, x, y, z, K, +1)] - U[K * g.N + nbrJ(g, x, y, z, K, -1)]) * (0.5 / g.h);
+        tr += (U[K * g.N + nbrJ(g, x, y, z, K, +1)] - U[K * g.N + nbrJ(g, x, y, z, K, -1)]) * g.i2h;
     tr0[p] = tr - g.dim * k.eps0 * (X0[p] - cbar0);
 }
 
@@ -208,7 +208,7 @@ __global__ void k_res_a(DGrid g, DCoef k, Bat bt, const double *__restrict__ isc
     part = shift(part, io);
     F = shift(F, io);
     flag = shift(flag, io);
-    const double dt = shift(isc, io)[I_DT], cbar0 = shift(isc, io)[I_CBAR0];
+    const double idt = shift(isc, io)[I_IDT], cbar0 = shift(isc, io)[I_CBAR0];
     long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (p >= g.N) return;
     int x, y, z;
@@ -235,7 +235,7 @@ __global__ void k_res_a(DGrid g, DCoef k, Bat bt, const double *__restrict__ isc
         gc += -k.eps0 * k.lam * 0.5 * (tr1 + tr0[p]);
     }
     // G^4 = (-gamma_c D^2 c_h, -3 gamma_eta D^2 eta_h), D^2 = sum_J D+_J D-_J
-    const double ih2 = 1.0 / (g.h * g.h);
+    const double ih2 = g.ih2;
     double lc = 0.0, le = 0.0;
     const double chp = c1 + c0, ehp = e1 + e0;
     for (int J = 0; J < g.dim; J++) {
@@ -246,7 +246,7 @@ __global__ void k_res_a(DGrid g, DCoef k, Bat bt, const double *__restrict__ isc
     gc += -k.gamma_c * 0.5 * lc * ih2;
     ge += -3.0 * k.gamma_eta * 0.5 * le * ih2;
     Gc[p] = gc;
-    F[N + p] = (e1 - e0) / dt + ge;
+    F[N + p] = (e1 - e0) * idt + ge;
     part[p] = G.dcc;
     part[N + p] = G.dce;
     part[2 * N + p] = G.dec;
@@ -268,9 +268,9 @@ __global__ void __launch_bounds__(kRedThreads) k_res_b(DGrid g, DCoef k, Bat bt,
     sig = shift(sig, io);
     F = shift(F, io);
     partials = shift(partials, io);
-    const double dt = shift(isc, io)[I_DT];
+    const double idt = shift(isc, io)[I_IDT];
     const long long N = g.N;
-    const double ih2 = 1.0 / (g.h * g.h), i2h = 0.5 / g.h;
+    const double ih2 = g.ih2, i2h = g.i2h;
     double acc[1] = {0.0};
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
          p += (long long)gridDim.x * blockDim.x) {
@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(kRedThreads) k_res_b(DGrid g, DCoef k, Bat bt,
                 const long long pp = nbrJ(g, x, y, z, J, +1), pm = nbrJ(g, x, y, z, J, -1);
                 flux += mob[J * N + p] * (Gc[pp] - G0) - mob[J * N + pm] * (G0 - Gc[pm]);
             }
-            fc = (X1[p] - X0[p]) / dt - flux * ih2;
+            fc = (X1[p] - X0[p]) * idt - flux * ih2;
         }
         F[p] = fc;
         const double fe = F[N + p];
@@ -314,9 +314,10 @@ __global__ void __launch_bounds__(kRedThreads) k_res_b(DGrid g, DCoef k, Bat bt,
 //   (J v)_u_I = sum_J Dhat_J sigma_IJ,
 // with the pointwise derivatives (dcc, dce, dec, dee) of the last residual
 // evaluation (part).  mode 1 (displacement-only system) keeps the identity on the
-// c and eta rows.  With Jec != nullptr the action is applied to P v instead of v,
-// where P removes the mean of v_c (and the null modes of v_u, which J annihilates):
-// J P v = J v - mean(v_c) J e_c with mean(v_c) = zsum[0] / N.
+// c and eta rows.  With zsum != nullptr the action is applied to P v instead of v,
+// where P removes the mean m = zsum[0] / N of v_c (the null modes of v_u are
+// annihilated by J): every use of v_c reads v_c - m, except the Laplacian, which
+// a constant shift leaves unchanged.
 // Indices are 32-bit (the problem constructor checks nf N < 2^31).
 //
 // GB300 executes FP64 at 1/64 of the FP32 rate, so the FP64 form is organised to
@@ -339,6 +340,7 @@ struct JvConst {
     T ab, b, c4; // (C11 - C12)/(2h), C12/(2h), C44/(2h)
     T ls;        // lam eps0
     T i2h;       // 1/(2h)
+    T invN;      // 1/N: the mean of v_c is zsum / N
     int mode;
 };
 
@@ -357,6 +359,7 @@ static JvConst<T> jv_const(const DGrid &g, const DCoef &k, int mode)
     c.c4 = (T)(k.C44 * i2h);
     c.ls = (T)(k.lam * k.eps0);
     c.i2h = (T)i2h;
+    c.invN = (T)(1.0 / (double)g.N);
     c.mode = mode;
     return c;
 }
@@ -378,9 +381,9 @@ __device__ __forceinline__ void nbr_offsets(const int (&c3)[3], const int (&nn)[
 template <int D, bool EL, typename T, typename TV, typename TC>
 __device__ __forceinline__ void jv_point(const JvConst<T> &c, int mode, int N, int idx, const int (&im)[3],
                                          const int (&ip)[3], const TV *__restrict__ v, const TC *__restrict__ part,
-                                         T &dg, T (&sg)[EL ? D * (D + 1) / 2 : 1])
+                                         T m, T &dg, T (&sg)[EL ? D * (D + 1) / 2 : 1])
 {
-    const T vc = (T)v[idx];
+    const T v0 = (T)v[idx], vc = v0 - m;
     T trd = (T)0;
     if constexpr (EL) {
         T Dd[D][D];
@@ -403,7 +406,7 @@ __device__ __forceinline__ void jv_point(const JvConst<T> &c, int mode, int N, i
         T sn = (T)0;
 #pragma unroll
         for (int J = 0; J < D; J++) sn += (T)v[ip[J]] + (T)v[im[J]];
-        const T lc = sn - (T)(2 * D) * vc;
+        const T lc = sn - (T)(2 * D) * v0;
         dg = (T)part[idx] * vc + (T)part[N + idx] * (T)v[N + idx] - c.gc * lc;
         if constexpr (EL) dg += c.el_c * vc - c.el_t * trd;
     }
@@ -426,7 +429,7 @@ __device__ __forceinline__ bool grid_point(const DGrid &g, int (&c3)[3], int &p)
 template <int D, bool EL>
 __global__ void __launch_bounds__(256) k_jv64_a(DGrid g, JvConst<double> c, Bat bt, const double *__restrict__ part,
                                                 const double *__restrict__ v, double *__restrict__ dG,
-                                                double *__restrict__ sig)
+                                                double *__restrict__ sig, const double *__restrict__ zsum)
 {
     long long io;
     if (!inst_off(bt, blockIdx.z / g.n[2], io)) return;
@@ -434,6 +437,7 @@ __global__ void __launch_bounds__(256) k_jv64_a(DGrid g, JvConst<double> c, Bat 
     v = shift(v, io);
     dG = shift(dG, io);
     sig = shift(sig, io);
+    const double m = zsum ? shift(zsum, io)[0] * c.invN : 0.0;
     int c3[3], p;
     if (!grid_point<D>(g, c3, p)) return;
     const int nn[3] = {g.n[0], g.n[1], g.n[2]};
@@ -441,7 +445,7 @@ __global__ void __launch_bounds__(256) k_jv64_a(DGrid g, JvConst<double> c, Bat 
     int im[3], ip[3];
     nbr_offsets<D>(c3, nn, p, im, ip);
     double dg = 0.0, sg[EL ? D * (D + 1) / 2 : 1];
-    jv_point<D, EL, double, double, double>(c, c.mode, N, p, im, ip, v, part, dg, sg);
+    jv_point<D, EL, double, double, double>(c, c.mode, N, p, im, ip, v, part, m, dg, sg);
     if (c.mode == 0) dG[p] = dg;
     if constexpr (EL) {
 #pragma unroll
@@ -454,7 +458,7 @@ __global__ void __launch_bounds__(256) k_jv64_b(DGrid g, JvConst<double> c, Bat 
                                                 const double *__restrict__ part, const double *__restrict__ mob,
                                                 const double *__restrict__ v, const double *__restrict__ dG,
                                                 const double *__restrict__ sig, double *__restrict__ Jv,
-                                                const double *__restrict__ Jec, const double *__restrict__ zsum)
+                                                const double *__restrict__ zsum)
 {
     long long io;
     if (!inst_off(bt, blockIdx.z / g.n[2], io)) return;
@@ -464,16 +468,15 @@ __global__ void __launch_bounds__(256) k_jv64_b(DGrid g, JvConst<double> c, Bat 
     dG = shift(dG, io);
     sig = shift(sig, io);
     Jv = shift(Jv, io);
-    Jec = shift(Jec, io);
-    zsum = shift(zsum, io);
-    const double idt = 1.0 / shift(isc, io)[I_DT];
+    const double idt = shift(isc, io)[I_IDT];
+    const double m = zsum ? shift(zsum, io)[0] * c.invN : 0.0;
     int c3[3], p;
     if (!grid_point<D>(g, c3, p)) return;
     const int nn[3] = {g.n[0], g.n[1], g.n[2]};
     const int N = (int)g.N;
     int im[3], ip[3];
     nbr_offsets<D>(c3, nn, p, im, ip);
-    const double vc = v[p], ve = v[N + p];
+    const double vc = v[p] - m, ve = v[N + p];
     double jc, je;
     if (c.mode == 0) {
         const double G0 = dG[p];
@@ -488,11 +491,6 @@ __global__ void __launch_bounds__(256) k_jv64_b(DGrid g, JvConst<double> c, Bat 
     } else {
         jc = vc;
         je = ve;
-    }
-    if (Jec) {
-        const double m = zsum[0] / (double)N;
-        jc -= m * Jec[p];
-        je -= m * Jec[N + p];
     }
     Jv[p] = jc;
     Jv[N + p] = je;
@@ -531,7 +529,7 @@ template <int D, bool EL>
 __global__ void __launch_bounds__(256) k_jv32(DGrid g, JvConst<float> c, Bat bt, const double *__restrict__ isc,
                                               const float *__restrict__ part, const float *__restrict__ mob,
                                               const float *__restrict__ v, float *__restrict__ Jv,
-                                              const float *__restrict__ Jec, const double *__restrict__ zsum)
+                                              const double *__restrict__ zsum)
 {
     long long io;
     if (!inst_off(bt, blockIdx.y, io)) return;
@@ -539,8 +537,6 @@ __global__ void __launch_bounds__(256) k_jv32(DGrid g, JvConst<float> c, Bat bt,
     mob = shift(mob, io);
     v = shift(v, io);
     Jv = shift(Jv, io);
-    Jec = shift(Jec, io);
-    zsum = shift(zsum, io);
     constexpr int TX = JvTile<D>::TX, TY = JvTile<D>::TY, TZ = JvTile<D>::TZ;
     constexpr int HX = TX + 2, HY = D >= 2 ? TY + 2 : 1, HZ = D == 3 ? TZ + 2 : 1;
     constexpr int NH = HX * HY * HZ;
@@ -556,6 +552,14 @@ __global__ void __launch_bounds__(256) k_jv32(DGrid g, JvConst<float> c, Bat bt,
     const int y0 = (b % ty_n) * TY;
     const int z0 = (b / ty_n) * TZ;
     const int sh[3] = {1, HX, HX * HY};
+    // per-block scalars (one double-to-float conversion each, not one per thread)
+    __shared__ float sidt, sm;
+    if (threadIdx.x == 0) {
+        sidt = (float)shift(isc, io)[I_IDT];
+        sm = zsum ? (float)(shift(zsum, io)[0] * (double)c.invN) : 0.f;
+    }
+    __syncthreads();
+    const float m = sm, idt = sidt;
 
     // tile + halo: dG_c and sigma
     for (int q = threadIdx.x; q < NH; q += blockDim.x) {
@@ -568,7 +572,7 @@ __global__ void __launch_bounds__(256) k_jv32(DGrid g, JvConst<float> c, Bat bt,
         int im[3], ip[3];
         nbr_offsets<D>(c3, nn, idx, im, ip);
         float dg = 0.f, sg[NS];
-        jv_point<D, EL, float, float, float>(c, c.mode, N, idx, im, ip, v, part, dg, sg);
+        jv_point<D, EL, float, float, float>(c, c.mode, N, idx, im, ip, v, part, m, dg, sg);
         sG[q] = dg;
         if constexpr (EL) {
 #pragma unroll
@@ -577,8 +581,7 @@ __global__ void __launch_bounds__(256) k_jv32(DGrid g, JvConst<float> c, Bat bt,
     }
     __syncthreads();
 
-    const float m = Jec ? (float)zsum[0] * (1.0f / (float)N) : 0.f;
-    const float idt = 1.0f / (float)shift(isc, io)[I_DT], ih2 = c.ih2, ge = c.ge, i2h = c.i2h;
+    const float ih2 = c.ih2, ge = c.ge, i2h = c.i2h;
     for (int t = threadIdx.x; t < TX * TY * TZ; t += blockDim.x) {
         const int tx = t % TX, ty = (t / TX) % TY, tz = t / (TX * TY);
         const int c3[3] = {x0 + tx, y0 + ty, z0 + tz};
@@ -587,7 +590,7 @@ __global__ void __launch_bounds__(256) k_jv32(DGrid g, JvConst<float> c, Bat bt,
         int im[3], ip[3];
         nbr_offsets<D>(c3, nn, p, im, ip);
         const int hq = (tx + 1) + (D >= 2 ? HX * (ty + 1) : 0) + (D == 3 ? HX * HY * (tz + 1) : 0);
-        const float vc = v[p], ve = v[N + p];
+        const float vc = v[p] - m, ve = v[N + p];
         float jc, je;
         if (c.mode == 0) {
             const float G0 = sG[hq];
@@ -602,10 +605,6 @@ __global__ void __launch_bounds__(256) k_jv32(DGrid g, JvConst<float> c, Bat bt,
         } else {
             jc = vc;
             je = ve;
-        }
-        if (Jec) {
-            jc -= m * Jec[p];
-            je -= m * Jec[N + p];
         }
         Jv[p] = jc;
         Jv[N + p] = je;
@@ -636,7 +635,7 @@ __global__ void __launch_bounds__(kRedThreads) k_energy(DGrid g, DCoef k, Bat bt
     partials = shift(partials, io);
     const double cbar0 = shift(isc, io)[I_CBAR0];
     const long long N = g.N;
-    const double ih = 1.0 / g.h;
+    const double ih = g.ih;
     double acc[5] = {0, 0, 0, 0, 0};
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
          p += (long long)gridDim.x * blockDim.x) {
@@ -733,22 +732,21 @@ int launch_residual(const DGrid &g, const DCoef &k, const double *isc, int mode,
 template <int D, bool EL>
 static void launch_jv64_d(const DGrid &g, const JvConst<double> &c, const Bat &bt, const double *isc, const double *part,
                           const double *mob, const double *v, double *dG, double *sig, double *Jv, cudaStream_t st,
-                          const double *Jec, const double *zsum)
+                          const double *zsum)
 {
     const dim3 blk(D == 1 ? 256 : 32, D == 1 ? 1 : 8);
     const dim3 grd((g.n[0] + blk.x - 1) / blk.x, (g.n[1] + blk.y - 1) / blk.y, g.n[2] * bt.nb);
-    k_jv64_a<D, EL><<<grd, blk, 0, st>>>(g, c, bt, part, v, dG, sig);
-    k_jv64_b<D, EL><<<grd, blk, 0, st>>>(g, c, bt, isc, part, mob, v, dG, sig, Jv, Jec, zsum);
+    k_jv64_a<D, EL><<<grd, blk, 0, st>>>(g, c, bt, part, v, dG, sig, zsum);
+    k_jv64_b<D, EL><<<grd, blk, 0, st>>>(g, c, bt, isc, part, mob, v, dG, sig, Jv, zsum);
 }
 
 template <int D, bool EL>
 static void launch_jv32_d(const DGrid &g, const JvConst<float> &c, const Bat &bt, const double *isc, const float *part,
-                          const float *mob, const float *v, float *Jv, cudaStream_t st, const float *Jec,
-                          const double *zsum)
+                          const float *mob, const float *v, float *Jv, cudaStream_t st, const double *zsum)
 {
     constexpr int TX = JvTile<D>::TX, TY = JvTile<D>::TY, TZ = JvTile<D>::TZ;
     const long long tiles = (long long)((g.n[0] + TX - 1) / TX) * ((g.n[1] + TY - 1) / TY) * ((g.n[2] + TZ - 1) / TZ);
-    k_jv32<D, EL><<<dim3((unsigned)tiles, bt.nb), 256, 0, st>>>(g, c, bt, isc, part, mob, v, Jv, Jec, zsum);
+    k_jv32<D, EL><<<dim3((unsigned)tiles, bt.nb), 256, 0, st>>>(g, c, bt, isc, part, mob, v, Jv, zsum);
 }
 
 #define NKS_JV_DISPATCH(FN, ...)                                  \
@@ -763,18 +761,18 @@ static void launch_jv32_d(const DGrid &g, const JvConst<float> &c, const Bat &bt
 
 int launch_jv64(const DGrid &g, const DCoef &k, const double *isc, int mode, const double *part, const double *mob,
                 const double *v, double *dG, double *sig, double *Jv, cudaStream_t st, const Bat &bt,
-                const double *Jec, const double *zsum)
+                const double *zsum)
 {
     const JvConst<double> c = jv_const<double>(g, k, mode);
-    NKS_JV_DISPATCH(launch_jv64_d, g, c, bt, isc, part, mob, v, dG, sig, Jv, st, Jec, zsum);
+    NKS_JV_DISPATCH(launch_jv64_d, g, c, bt, isc, part, mob, v, dG, sig, Jv, st, zsum);
     return 2;
 }
 
 int launch_jv32(const DGrid &g, const DCoef &k, const double *isc, int mode, const float *part, const float *mob,
-                const float *v, float *Jv, cudaStream_t st, const Bat &bt, const float *Jec, const double *zsum)
+                const float *v, float *Jv, cudaStream_t st, const Bat &bt, const double *zsum)
 {
     const JvConst<float> c = jv_const<float>(g, k, mode);
-    NKS_JV_DISPATCH(launch_jv32_d, g, c, bt, isc, part, mob, v, Jv, st, Jec, zsum);
+    NKS_JV_DISPATCH(launch_jv32_d, g, c, bt, isc, part, mob, v, Jv, st, zsum);
     return 1;
 }
 
