@@ -37,12 +37,12 @@ import synthetic as S  # noqa: E402
 METRIC = "point-steps/s"
 # FP64 FMA peak derived from the unit counts: 152 SMs x 2 FP64 FMA/clk x 2 FLOP x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-# DRAM traffic per launch of the dominant kernel (dram__bytes_read.sum + dram__bytes_write.sum),
-# keyed by (workload, precision, kernel class), from one ncu capture of the 512^2 probe
-# (bench.py --probe gmres512: the same 68x68 boxes, 64 of them) scaled by the 256 boxes of
-# the 1024^2 launch; an entry is removed whenever the kernel changes
-NCU_TRAFFIC = {("2d1024", "fp64", "schwarz_apply"): 4 * (173.719808e6 + 4.763648e6),
-               ("2d1024", "mixed", "schwarz_apply"): 4 * (86.979328e6 + 2.500608e6)}
+# DRAM traffic per launch of the dominant kernel (dram__bytes.sum.per_second x duration),
+# keyed by (workload, precision, kernel class), from one ncu capture of the 1024^2 probe
+# (bench.py --probe gmres1024: the bench workload's own 256-box launch); an entry is
+# removed whenever the kernel changes
+NCU_TRAFFIC = {("2d1024", "fp64", "schwarz_apply"): 932.815680e9 * 969.792e-6,
+               ("2d1024", "mixed", "schwarz_apply"): 1435.653e9 * 275.168e-6}
 
 
 def kernel_rates(st, cfg, mixed, pk):
@@ -186,12 +186,12 @@ def oracle_sample(cfg, gmres_per_step, newton_per_step, its=(2, 6)):
     of the same algorithm on the same workload)."""
     import oracle
     op = S.options(**cfg["opts"])
-    c, e = S.initial_fields(cfg["dim"], cfg["n"], cfg["cbar"], cfg["seed"])
+    c, e = S.config_fields(cfg)
     N = c.size
     times = []
     O = None
     for m in its:
-        O = oracle.Problem(cfg["dim"], cfg["n"], cfg["h"], S.coefficients(), dict(op, gmres_maxit=m))
+        O = oracle.Problem(cfg["dim"], cfg["n"], cfg["h"], S.config_coefficients(cfg), dict(op, gmres_maxit=m))
         X = O.interleave(c, e)
         cb = float(np.sum(c) / N)
         F = O.residual(X, X, cb, op["dt_init"])
@@ -205,7 +205,7 @@ def oracle_sample(cfg, gmres_per_step, newton_per_step, its=(2, 6)):
             "sample": ("full-size %s workload, first Newton solve: Jacobian assembly + RAS/ILU(0) set-up + %d and %d "
                        "GMRES iterations timed (%.1f s, %.1f s); step = %.2f set-ups + %.1f iterations (per-step "
                        "counts of the same method); single-threaded FP64 C oracle"
-                       % (cfg["dim"] == 2 and "2-D 1024^2" or "3-D", its[0], its[1], times[0], times[1],
+                       % ("x".join(str(v) for v in cfg["n"]), its[0], its[1], times[0], times[1],
                           newton_per_step, gmres_per_step)),
             "seconds_per_step": step_s, "t_setup_s": t_setup, "t_gmres_iteration_s": t_it}
 
@@ -237,21 +237,20 @@ def run_ours(args):
         op["overlap"] = args.overlap
     if args.u0_maxit is not None:
         op["u0_maxit"] = args.u0_maxit
-    seed = cfg["seed"] + 1000 * rank  # independent replica per rank
-    c, e = S.initial_fields(cfg["dim"], cfg["n"], cfg["cbar"], seed)
+    c, e = S.config_fields(cfg, 1000 * rank)  # independent replica per rank (seeded workloads)
     N = c.size
     tuned = None
     if args.autotune:
         # owned box sides 8..16 (3-D) or 32..128 (2-D), overlap 1 and 2; one timed step each
         sides = (8, 12, 16) if cfg["dim"] == 3 else (32, 64, 128)
         cands = [(tuple(max(2, (nn + b // 2) // b) for nn in cfg["n"]), ov) for b in sides for ov in (1, 2)]
-        op, table, chosen = nks.autotune(cfg["dim"], cfg["n"], cfg["h"], c, e, S.coefficients(), op,
+        op, table, chosen = nks.autotune(cfg["dim"], cfg["n"], cfg["h"], c, e, S.config_coefficients(cfg), op,
                                          candidates=cands, dt_trial=op["dt_init"])
         tuned = {"candidates": [{"sub": list(sb), "overlap": ov, "step_s": t} for sb, ov, t in table],
                  "chosen": {"sub": list(op["sub"]), "overlap": op["overlap"]}}
     stream = torch.cuda.current_stream()
     alloc = nks.torch_allocator()
-    P = nks.Problem(cfg["dim"], cfg["n"], cfg["h"], c, e, S.coefficients(), op, stream=stream.cuda_stream,
+    P = nks.Problem(cfg["dim"], cfg["n"], cfg["h"], c, e, S.config_coefficients(cfg), op, stream=stream.cuda_stream,
                     allocator=alloc, timing=True)
     state0 = P.get_state()
     for _ in range(args.warmup):
@@ -311,7 +310,7 @@ def run_ours(args):
     accuracy = None
     if mixed and not args.no_accuracy and rank == 0:
         cm, em, um = P.get_fields()
-        Q = nks.Problem(cfg["dim"], cfg["n"], cfg["h"], c, e, S.coefficients(), dict(op, precision="fp64"),
+        Q = nks.Problem(cfg["dim"], cfg["n"], cfg["h"], c, e, S.config_coefficients(cfg), dict(op, precision="fp64"),
                         stream=stream.cuda_stream, allocator=alloc)
         for i in infos:
             Q.step(i["dt"])
@@ -332,7 +331,7 @@ def run_ours(args):
         epin = torch.from_numpy(e).pin_memory().numpy()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        Q = nks.Problem(cfg["dim"], cfg["n"], cfg["h"], cpin, epin, S.coefficients(), op, stream=stream.cuda_stream,
+        Q = nks.Problem(cfg["dim"], cfg["n"], cfg["h"], cpin, epin, S.config_coefficients(cfg), op, stream=stream.cuda_stream,
                         allocator=alloc)
         outs = []
         for _ in range(args.steps):
@@ -344,7 +343,7 @@ def run_ours(args):
         t_e2e = max_over_ranks(dist, t_e2e, torch.device("cuda", local))
         e2e = {"value": points_all / t_e2e, "unit": METRIC,
                "h2d_bytes_per_step": int(2 * N * 8 / args.steps),
-               "d2h_bytes_per_step": int((2 + (cfg["dim"] if S.coefficients().get("Lscale", 1.0) else 0)) * N * 8),
+               "d2h_bytes_per_step": int((2 + (cfg["dim"] if S.config_coefficients(cfg).get("Lscale", 1.0) else 0)) * N * 8),
                "includes": "problem creation from host fields (upload + initial mechanical equilibrium solve), "
                            "K steps, fields read back to host after every step"}
 
@@ -426,7 +425,7 @@ def run_batch(args):
     if args.precision:
         op["precision"] = args.precision
     B = args.batch
-    fields = [S.initial_fields(cfg["dim"], cfg["n"], cfg["cbar"], cfg["seed"] + i) for i in range(B)]
+    fields = [S.config_fields(cfg, i) for i in range(B)]
     c = np.stack([f[0] for f in fields])
     e = np.stack([f[1] for f in fields])
     N = c.shape[1]
@@ -446,7 +445,7 @@ def run_batch(args):
         torch.cuda.synchronize()
         return ev0.elapsed_time(ev1), (time.perf_counter() - t0) * 1e3
 
-    Bt = nks.Batch(cfg["dim"], cfg["n"], cfg["h"], B, S.coefficients(), op, c=c, eta=e,
+    Bt = nks.Batch(cfg["dim"], cfg["n"], cfg["h"], B, S.config_coefficients(cfg), op, c=c, eta=e,
                    allocator=nks.torch_allocator())
     st0 = [Bt.get_state(i) for i in range(B)]
     clocks = ClockSampler(0)
@@ -454,7 +453,7 @@ def run_batch(args):
     ms_b, wall_b = timed(lambda: Bt.step(), lambda: [Bt.set_state(i, st0[i]) for i in range(B)])
     clk = clocks.stop()
     stats = Bt.get_stats()
-    P = nks.Problem(cfg["dim"], cfg["n"], cfg["h"], c[0], e[0], S.coefficients(), op,
+    P = nks.Problem(cfg["dim"], cfg["n"], cfg["h"], c[0], e[0], S.config_coefficients(cfg), op,
                     allocator=nks.torch_allocator())
     s1 = P.get_state()
     ms_1, _ = timed(lambda: P.step(), lambda: P.set_state(s1))
@@ -556,14 +555,17 @@ def run_serve(args):
 def run_probe(args):
     """Small fixed cases for profiling single kernels (ncu -k ...): 'gmres512' builds
     the 2-D 512^2 problem with 8x8 subdomains, overlap 2 (the 68x68 boxes of the
-    1024^2 workload) and runs 40 GMRES iterations of the first Newton solve
-    (FP64, or FP32 sweeps and basis with --precision mixed)."""
+    1024^2 workload), 'gmres1024' the 1024^2 problem itself with its 16x16
+    subdomains (the bench's launch configuration, about 2.5 GB on the device);
+    both run 40 GMRES iterations of the first Newton solve (FP64, or FP32 sweeps
+    and basis with --precision mixed) after a one-iteration set-up solve."""
     import torch
     import paper_2209_08001_gb300 as nks
     torch.cuda.set_device(0)
-    if args.probe == "gmres512":
-        n = (512, 512)
-        op = S.options(sub=(8, 8), overlap=2, u0_maxit=1, gmres_maxit=40, u0_rtol=1e-2,
+    if args.probe in ("gmres512", "gmres1024"):
+        side, sub = (512, 8) if args.probe == "gmres512" else (1024, 16)
+        n = (side, side)
+        op = S.options(sub=(sub, sub), overlap=2, u0_maxit=1, gmres_maxit=40, u0_rtol=1e-2,
                        precision=args.precision or "fp64")
         c, e = S.initial_fields(2, n, 0.2, 1)
         P = nks.Problem(2, n, 0.25, c, e, S.coefficients(), op)
@@ -590,7 +592,7 @@ def main():
     # iteration counts used to scale the oracle sample in the reference arm (measured on the GPU arm)
     ap.add_argument("--ref-gmres-per-step", type=float, default=1700.0)
     ap.add_argument("--ref-newton-per-step", type=float, default=5.67)
-    ap.add_argument("--probe", default=None, choices=["gmres512"], help="small profiling case, no JSON bench line")
+    ap.add_argument("--probe", default=None, choices=["gmres512", "gmres1024"], help="small profiling case, no JSON bench line")
     ap.add_argument("--batch", type=int, default=0,
                     help="B > 0: B instances of the workload stepped as one batch (beside one alone)")
     ap.add_argument("--serve", action="store_true", help="the serving workload (p50/p99 latency, throughput)")

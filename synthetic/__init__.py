@@ -13,6 +13,10 @@ Sec. 5.1-5.3; no dataset is involved):
     The order-parameter mean 0.1 is the paper's random initial state (Sec. 5.3);
     a zero-mean eta would put c*eta outside (0, 1) where Psi is undefined;
   * u is not drawn: it is the mechanical equilibrium of the initial c.
+
+The single-particle workload (Sec. 5.1) is deterministic instead: a sphere of
+gamma' (c = 0.238, eta = 0.01) of radius 7.5 at the centre of an 80^3 box of
+gamma matrix (c = 0.1375, eta = 0.99), the Hooke tensor scaled by L = 1.
 """
 from __future__ import annotations
 
@@ -50,6 +54,20 @@ def initial_fields(dim: int, n, cbar: float, seed: int, c_amp: float = 0.005,
     u = uniform01(seed, 2 * N)
     c = cbar + c_amp * (2.0 * u[:N] - 1.0)
     eta = eta_mean + eta_amp * (2.0 * u[N:] - 1.0)
+    return c, eta
+
+
+def sphere_fields(dim: int, n, h: float, radius: float, inside=(0.238, 0.01), outside=(0.1375, 0.99)):
+    """(c, eta) of one spherical particle (Sec. 5.1) as flat float64 arrays in
+    x-fastest order: grid point i of an axis sits at x_i = i h, the centre at
+    (n // 2) h on every axis; points with |x - centre| < radius take `inside`,
+    the rest `outside`."""
+    axes = [(np.arange(n[J]) - n[J] // 2) * h for J in range(dim)]
+    grids = np.meshgrid(*axes[::-1], indexing="ij")  # slowest axis first: ravel is x-fastest
+    r2 = sum(g * g for g in grids).ravel()
+    isin = r2 < radius * radius
+    c = np.where(isin, inside[0], outside[0]).astype(np.float64)
+    eta = np.where(isin, inside[1], outside[1]).astype(np.float64)
     return c, eta
 
 
@@ -123,7 +141,7 @@ def options(**over) -> dict:
 
 
 # ---------------------------------------------------------------------------
-# the five workloads
+# the workloads
 # ---------------------------------------------------------------------------
 
 CONFIGS = {
@@ -146,7 +164,26 @@ CONFIGS = {
         desc="3D 256^3 periodic mixed precision, 100 adaptive DVD steps, RAS 16x16x16 subdomains overlap 1",
         dim=3, n=(256, 256, 256), h=0.25, cbar=0.22, seed=3, steps=100,
         opts=dict(dt_mode="energy", sub=(16, 16, 16), overlap=1, precision="mixed")),
+    "3d80sphere": dict(
+        desc="3D 80^3 single gamma' particle of radius 7.5 at the centre (Sec. 5.1; inside c=0.238, eta=0.01, "
+             "outside c=0.1375, eta=0.99), Hooke tensor x L=1, FP64, adaptive dt (zeta=100, dt in [0.01, 2]), "
+             "RAS 5x5x5 subdomains overlap 1, periodic",
+        dim=3, n=(80, 80, 80), h=0.25, init="sphere", radius=7.5, coeffs=dict(Lscale=1.0), seed=0, steps=100,
+        opts=dict(dt_mode="energy", sub=(5, 5, 5), overlap=1, precision="fp64")),
 }
+
+
+def config_fields(cfg: dict, seed_offset: int = 0):
+    """Initial (c, eta) of a workload: the particle of Sec. 5.1, or the seeded
+    random state (seed + seed_offset)."""
+    if cfg.get("init") == "sphere":
+        return sphere_fields(cfg["dim"], cfg["n"], cfg["h"], cfg["radius"])
+    return initial_fields(cfg["dim"], cfg["n"], cfg["cbar"], cfg["seed"] + seed_offset)
+
+
+def config_coefficients(cfg: dict) -> dict:
+    """Coefficients of a workload (the defaults with its overrides)."""
+    return coefficients(**cfg.get("coeffs", {}))
 
 
 def serving_requests(count: int = 256, seed: int = 4, rate: float = 1.0):

@@ -7,6 +7,8 @@ after whole NKS steps, relative L2 per field <= 1e-8 (the tolerance of the
 FP64 method), mass to 1e-12 and a non-increasing energy.  Full size: one step
 of the 1024^2 workload checked by the oracle's own residual on the GPU result.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -201,6 +203,59 @@ def test_adaptive_steps_replayed_by_oracle(nks):
     rc, X, oinf, _ = O.simulate(c, e, 6, dt_replay=[i["dt"] for i in infos])
     co, eo, uo = O.split(X)
     assert rc == 0 and rel(cg, co) <= 1e-8 and rel(eg, eo) <= 1e-8
+    P.destroy()
+
+
+@pytest.mark.parametrize("L", [0.0, 1.0, 3.0])
+def test_sphere_particle_steps_replayed_by_oracle(nks, L):
+    """The single-particle state of Sec. 5.1 (sharp interface, Hooke tensor x L;
+    L = 0 is the model without elasticity): adaptive steps on the GPU, replayed by
+    the oracle with the same step sizes."""
+    n, h = (16, 16, 16), 0.25
+    cf = S.coefficients(Lscale=L)
+    op = S.options(sub=(2, 2, 2), overlap=1, dt_mode="energy")
+    c, e = S.sphere_fields(3, n, h, 1.6)
+    P = nks.Problem(3, n, h, c, e, cf, op)
+    infos = [P.step() for _ in range(3)]
+    cg, eg, ug = P.get_fields()
+    O = oracle.Problem(3, n, h, cf, dict(op, newton_rtol=1e-12))
+    rc, X, oinf, e0 = O.simulate(c, e, 3, dt_replay=[i["dt"] for i in infos])
+    co, eo, uo = O.split(X)
+    assert rc == 0 and rel(cg, co) <= 1e-8 and rel(eg, eo) <= 1e-8
+    if L:
+        assert rel(ug, uo) <= 1e-8
+    else:
+        assert ug is None and uo is None
+    for gi, oi in zip(infos, oinf):
+        assert gi["energy"] == pytest.approx(oi["energy"], rel=1e-10)
+    P.destroy()
+
+
+def test_full_size_sphere_80_step_checked_by_oracle_residual(nks):
+    """One step of the 80^3 single-particle workload (Sec. 5.1), checked by the
+    oracle's residual of the GPU result."""
+    cfg = S.CONFIGS["3d80sphere"]
+    cf = S.config_coefficients(cfg)
+    op = S.options(**cfg["opts"])
+    n, h = cfg["n"], cfg["h"]
+    c, e = S.config_fields(cfg)
+    P = nks.Problem(3, n, h, c, e, cf, op)
+    _, _, u0 = P.get_fields()
+    info = P.step()
+    assert info["status"] == 0 and info["dt"] == 0.01
+    cg, eg, ug = P.get_fields()
+    O = oracle.Problem(3, n, h, cf, op)
+    cb = float(np.sum(c) / c.size)
+    X0 = O.interleave(c, e, u0)
+    X1 = O.interleave(cg, eg, ug)
+    F = O.residual(X1, X0, cb, info["dt"])
+    F0 = O.residual(X0, X0, cb, info["dt"])
+    assert np.linalg.norm(F) <= 1e-9 * np.linalg.norm(F0)
+    # the mass h^3 sum(c), summed exactly: over 512,000 near-constant values a
+    # plain running sum (the oracle's) drifts by about 1e-11 relative
+    m0 = math.fsum(c) * h ** 3
+    assert abs(info["mass"] - m0) <= 1e-12 * m0
+    assert info["energy"] <= O.energy(X0, cb)
     P.destroy()
 
 

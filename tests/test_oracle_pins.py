@@ -480,6 +480,35 @@ def test_mass_conservation_and_energy_decay(dim, n, sub, mode, steps):
         assert all(i["dt"] >= op["dt_min"] - 1e-15 for i in infos)
 
 
+def test_sphere_particle_state_and_oracle_steps():
+    """The single-particle state of Sec. 5.1: two phases only, the lattice count of
+    the ball within 10% of its volume, symmetric under axis swaps and reflections
+    through the centre; and the oracle's adaptive steps from it, with the Hooke
+    tensor scaled by L = 0 (no elasticity), 1 and 3, conserve mass and do not
+    increase the energy (Theorem 3.2)."""
+    n, h, r = (16, 16, 16), 0.25, 1.6
+    c, e = S.sphere_fields(3, n, h, r)
+    inside = c == 0.238
+    assert np.all(e[inside] == 0.01) and np.all(c[~inside] == 0.1375) and np.all(e[~inside] == 0.99)
+    assert abs(inside.sum() - 4.0 / 3.0 * math.pi * (r / h) ** 3) <= 0.1 * 4.0 / 3.0 * math.pi * (r / h) ** 3
+    c3 = c.reshape(16, 16, 16)
+    assert np.array_equal(c3, c3.transpose(1, 0, 2)) and np.array_equal(c3, c3.transpose(2, 1, 0))
+    core = c3[1:, 1:, 1:]  # points 1..15: the centre is point 8 on every axis
+    assert np.array_equal(core, core[::-1, ::-1, ::-1])
+    for L in (0.0, 1.0, 3.0):
+        n2 = (12, 12, 12)
+        c, e = S.sphere_fields(3, n2, h, 1.0)
+        P = oracle.Problem(3, n2, h, S.coefficients(Lscale=L), S.options(sub=(2, 2, 2), overlap=1, dt_mode="energy"))
+        rc, X, infos, e0 = P.simulate(c, e, 2)
+        assert rc == 0
+        m0 = c.sum() * h ** 3
+        E = [e0] + [i["energy"] for i in infos]
+        for i in infos:
+            assert abs(i["mass"] - m0) <= 1e-12 * m0
+        for a, b in zip(E[:-1], E[1:]):
+            assert b <= a + 1e-12 * abs(a)
+
+
 def test_shift_and_axis_swap_symmetry():
     cf = S.coefficients()
     n = (12, 12)
