@@ -250,8 +250,16 @@ def run_ours(args):
                  "chosen": {"sub": list(op["sub"]), "overlap": op["overlap"]}}
     stream = torch.cuda.current_stream()
     alloc = nks.torch_allocator()
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter()
     P = nks.Problem(cfg["dim"], cfg["n"], cfg["h"], c, e, S.config_coefficients(cfg), op, stream=stream.cuda_stream,
                     allocator=alloc, timing=True)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t_setup
+    sst = P.get_stats()
+    setup = {"seconds": t_setup, "u0_newton_its": sst["newton_its"], "u0_gmres_its": sst["gmres_its"],
+             "includes": "problem creation: plan, factor tables, upload, initial mechanical equilibrium (Newton on "
+                         "the displacement rows, tolerance u0_rtol)"}
     state0 = P.get_state()
     for _ in range(args.warmup):
         P.step()
@@ -364,9 +372,13 @@ def run_ours(args):
                                      "schwarz": op.get("ras_variant", "left-ras")},
                    "steps_in_workload": cfg["steps"],
                    "timed_steps": "steps 1..K of the workload from its initial state",
+                   "initial_equilibrium": ("Newton on the displacement rows, FP64 residual to u0_rtol, inner GMRES in "
+                                           "the mixed form" if op.get("u0_mixed") else
+                                           "Newton on the displacement rows in the solver's precision"),
                    "l2": "working set (state, Krylov basis, ~0.65 GB of Schwarz factors) far above the 129 MB L2",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "gpu_launches": None,
+        "setup": setup,
         "autotune": tuned,
         "roofline": roof,
         "kernels": kernels,

@@ -119,6 +119,13 @@ typedef struct {
  *   graphs             1: each GMRES iteration replays a CUDA graph captured on
  *                      its first use (kernels of all batch slots and the read-back
  *                      of the iteration's scalars); ignored when timing = 1
+ *   u0_mixed           1: the displacement-only solves (the initial mechanical
+ *                      equilibrium, mode 1) run their GMRES in the NKS_MIXED form
+ *                      (FP32 factors, sweeps, basis) even when precision is
+ *                      NKS_FP64; their Newton residual, update and tolerance stay
+ *                      FP64, so the equilibrium meets the same u0_rtol/atol.  The
+ *                      time steps keep `precision`.  0 (default): `precision`.
+ *                      Costs the FP32 buffers of the mixed mode in FP64 mode.
  */
 typedef struct {
     double newton_rtol, newton_atol;
@@ -139,6 +146,7 @@ typedef struct {
     int timing;
     int graphs;
     int ras_variant;
+    int u0_mixed;
 } nks_opts;
 
 /* Optional device allocator (for example a framework's caching allocator).

@@ -54,7 +54,7 @@ class nks_opts(ctypes.Structure):
                 ("zeta", ctypes.c_double), ("dt_mode", ctypes.c_int), ("zeta_persist", ctypes.c_int),
                 ("max_retries", ctypes.c_int), ("u0_rtol", ctypes.c_double), ("u0_atol", ctypes.c_double),
                 ("u0_maxit", ctypes.c_int), ("timing", ctypes.c_int), ("graphs", ctypes.c_int),
-                ("ras_variant", ctypes.c_int)]
+                ("ras_variant", ctypes.c_int), ("u0_mixed", ctypes.c_int)]
 
 
 class nks_server_opts(ctypes.Structure):
@@ -238,7 +238,7 @@ def make_opts(op: dict, timing=False):
         if name in op:
             setattr(o, name, float(op[name]))
     for name in ("newton_maxit", "gmres_restart", "gmres_maxit", "overlap", "ilu_reuse", "zeta_persist",
-                 "max_retries", "u0_maxit", "graphs"):
+                 "max_retries", "u0_maxit", "graphs", "u0_mixed"):
         if name in op:
             setattr(o, name, int(op[name]))
     if "sub" in op:

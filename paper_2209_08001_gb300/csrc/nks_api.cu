@@ -658,6 +658,10 @@ static int validate(const nks_grid *grid, const nks_coeffs *coeffs, const nks_op
         g_create_error = "opts: precision must be NKS_FP64 or NKS_MIXED";
         return NKS_EINVAL;
     }
+    if (opts->u0_mixed != 0 && opts->u0_mixed != 1) {
+        g_create_error = "opts: u0_mixed must be 0 or 1";
+        return NKS_EINVAL;
+    }
     if (opts->ras_variant < NKS_LEFT_RAS || opts->ras_variant > NKS_RIGHT_RAS) {
         g_create_error = "opts: ras_variant must be NKS_LEFT_RAS, NKS_AS or NKS_RIGHT_RAS";
         return NKS_EINVAL;
@@ -731,6 +735,7 @@ int nks_create_batch(const nks_grid *grid, int nb, const double *c, const double
     const size_t vb = sizeof(double) * (size_t)P->ldv, fb = sizeof(double) * (size_t)g.N;
     const int m = opts->gmres_restart;
     const bool mixed = opts->precision == NKS_MIXED;
+    P->f32 = mixed || (opts->u0_mixed && P->k.elastic);
     std::vector<SlabItem> items;
     auto add = [&](void *pp, size_t bytes) { items.push_back({(void **)pp, bytes}); };
     double **vecs[] = {&P->Xn, &P->Xprev, &P->X, &P->Xt, &P->F, &P->Ft, &P->S, &P->B, &P->W, &P->Z, &P->R,
@@ -750,7 +755,7 @@ int nks_create_batch(const nks_grid *grid, int nb, const double *c, const double
     add(&P->zsum, sizeof(double) * 8);
     add(&P->gm, sizeof(double) * gmres_state_doubles(m));
     add(&P->isc, sizeof(double) * I_NSC);
-    if (mixed) {
+    if (P->f32) {
         const size_t fvb = sizeof(float) * (size_t)P->ldvf;
         add(&P->Vf, fvb * (m + 1));
         add(&P->Wf, fvb);

@@ -346,6 +346,9 @@ struct Problem {
     };
     IterGraph graphs[2][kMaxRestart];
     bool graphs_off = false;                    // a capture failed: launch directly
+    bool f32 = false;                           // the FP32 buffers of the mixed form exist
+    // does a linear solve of this mode run in the mixed form (FP32 factors, sweeps, basis)?
+    bool inner_f32(int mode) const { return opts.precision == NKS_MIXED || (mode == 1 && opts.u0_mixed); }
     int withhold_copy = 0;                      // test hook: sweeps withhold their first factor copy
     std::string err;
 

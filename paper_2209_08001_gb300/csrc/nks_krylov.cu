@@ -576,9 +576,9 @@ static void apply_J(Problem *P, int mode, const TV *v, TV *out, bool project_inp
 // coefficients at the current iterate.  (The projection needs no set-up: the
 // Arnoldi step applies J to z with the mean of z_c taken off, see the Jacobian
 // action.)
-static void prepare_operator(Problem *P, const Bat &bt)
+static void prepare_operator(Problem *P, int mode, const Bat &bt)
 {
-    if (P->opts.precision != NKS_MIXED) return;
+    if (!P->inner_f32(mode)) return;
     P->tick(1);
     refresh_f32_coefficients(P, bt);
     P->tock(1);
@@ -663,7 +663,7 @@ static int gmres_t(Problem *P, Basis<TV> K, int mode, const double *b, double *x
     cudaMemset2DAsync(P->dflag + 1, (size_t)P->stride, 0, sizeof(int), (size_t)P->nb, st);
     P->count(launch_zero(n, x, st, bin));
     P->count(launch_copy(n, b, R, st, bin));
-    prepare_operator(P, bin);
+    prepare_operator(P, mode, bin);
     std::vector<double> b2;
     int rc = norm2_batch(P, R, bin, b2);
     if (rc) return rc;
@@ -806,7 +806,7 @@ void destroy_graphs(Problem *P)
 
 int gmres_solve(Problem *P, int mode, const double *b, double *x)
 {
-    if (P->opts.precision == NKS_MIXED) return gmres_t<float>(P, basis32(P), mode, b, x);
+    if (P->inner_f32(mode)) return gmres_t<float>(P, basis32(P), mode, b, x);
     return gmres_t<double>(P, basis64(P), mode, b, x);
 }
 

@@ -1437,7 +1437,7 @@ template <int D, int NF>
 void apply_attrs(Problem *P)
 {
     apply_attr<D, NF, double>(P);
-    if (P->opts.precision == NKS_MIXED) apply_attr<D, NF, float>(P);
+    if (P->f32) apply_attr<D, NF, float>(P);
 }
 
 // FP64 vectors use the FP64 factors; FP32 vectors (mixed precision) the FP32 copy
@@ -1529,7 +1529,7 @@ int ras_factor(Problem *P, int mode, const Bat &bt, const std::vector<char> &on)
             P->is[i].err = "zero pivot in an ILU(0) subdomain factorisation";
         }
     }
-    if (P->opts.precision == NKS_MIXED) {
+    if (P->inner_f32(mode)) {
         NKS_DISPATCH(launch_fac_to_f32, P, bt);
         P->count(1);
     }
@@ -1608,7 +1608,7 @@ void ras_slab_items(Problem *P, std::vector<SlabItem> &items)
     const bool summed = P->opts.ras_variant != NKS_LEFT_RAS;
     if ((!R->x_smem || summed) && !mixed)
         items.push_back({(void **)&R->scratch, sizeof(double) * (size_t)R->scr_elems});
-    if (mixed) {
+    if (P->f32) {
         items.push_back({(void **)&R->fac32, sizeof(float) * (size_t)R->fac32_elems});
         if (!R->x_smem32 || summed) items.push_back({(void **)&R->scratch32, sizeof(float) * (size_t)R->scr_elems});
     }

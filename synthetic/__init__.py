@@ -130,6 +130,9 @@ OPTS = dict(
     dt_init=0.01, dt_min=0.01, dt_max=2.0, zeta=100.0, dt_mode="fixed",
     zeta_persist=0, max_retries=8,
     u0_rtol=1e-12, u0_atol=1e-13, u0_maxit=10,
+    # the initial mechanical equilibrium's inner GMRES in the mixed form (its Newton
+    # residual and tolerance stay FP64); the time steps keep `precision`
+    u0_mixed=1,
     precision="fp64",
 )
 

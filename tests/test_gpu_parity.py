@@ -259,6 +259,33 @@ def test_full_size_sphere_80_step_checked_by_oracle_residual(nks):
     P.destroy()
 
 
+def test_initial_equilibrium_with_mixed_inner_solves(nks):
+    """u0_mixed = 1 in FP64 mode: the equilibrium's GMRES runs in the mixed form but
+    its Newton residual is FP64, so u0 meets the same tolerance as the all-FP64
+    solve (checked with the oracle's residual), and the FP64 steps that follow
+    agree with the all-FP64 run."""
+    n, h = (40, 36), 0.25
+    cf = S.coefficients()
+    c, e = S.initial_fields(2, n, 0.18, 6)
+    O = oracle.Problem(2, n, h, cf, S.options(sub=(2, 3), overlap=2))
+    cb = float(np.sum(c) / c.size)
+    F00 = np.linalg.norm(O.residual(O.interleave(c, e), O.interleave(c, e), cb, 1.0, 1))
+    runs = {}
+    for um in (0, 1):
+        op = S.options(sub=(2, 3), overlap=2, u0_mixed=um, dt_mode="energy")
+        P = nks.Problem(2, n, h, c, e, cf, op)
+        _, _, u0 = P.get_fields()
+        X0 = O.interleave(c, e, u0)
+        assert np.linalg.norm(O.residual(X0, X0, cb, 1.0, mode=1)) <= 1e-11 * F00
+        infos = [P.step() for _ in range(2)]
+        runs[um] = (u0, P.get_fields(), infos)
+        P.destroy()
+    (ua, (ca, ea, wa), ia), (ub, (cb_, eb, wb), ib) = runs[0], runs[1]
+    assert rel(ub, ua) <= 1e-9
+    assert rel(cb_, ca) <= 1e-9 and rel(eb, ea) <= 1e-9 and rel(wb, wa) <= 1e-8
+    assert [i["dt"] for i in ia] == pytest.approx([i["dt"] for i in ib], rel=1e-9)
+
+
 def test_checkpoint_resume_is_bitwise(nks):
     cf = S.coefficients()
     op = S.options(sub=(2, 2), overlap=1, dt_mode="solution")
