@@ -441,7 +441,8 @@ int ras_plan_create(Problem *P, std::string &err)
     R->fac32_elems = fac_off / per_pt * (R->sf32 + R->sb32);
     choose_x64(P, R, nf);
     choose_lane_config(P, R, nf);
-    if (R->smem_bytes > 227 * 1024) {
+    const bool f32_sweeps = P->opts.precision == NKS_MIXED || (P->opts.u0_mixed && P->k.elastic);
+    if (R->smem_bytes > 227 * 1024 || (f32_sweeps && R->smem_bytes32 > 227 * 1024)) {
         err = "decomposition: subdomain boxes too large for the Schwarz kernel (use more subdomains)";
         return NKS_EINVAL;
     }

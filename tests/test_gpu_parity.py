@@ -150,6 +150,30 @@ def test_mixed_operators_match_oracle(nks, dim, n, sub, ov, elastic):
     P.destroy()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("variant", ["left-ras", "as"])
+@pytest.mark.parametrize("dim,n,sub,ov", [(3, (36, 36, 36), (2, 2, 2), 1), (2, (232, 232), (2, 2), 2)])
+def test_preconditioner_with_box_vectors_in_global_memory(nks, dim, n, sub, ov, variant, precision):
+    """Boxes too large for their vector to sit in shared memory (20^3 x 5 fields,
+    120^2 x 4 fields): both sweeps then keep it in global scratch; the Schwarz
+    application still matches the oracle's (restricted and overlapped prolongation)."""
+    cf = S.coefficients()
+    op = S.options(sub=sub, overlap=ov, precision=precision, ras_variant=variant)
+    (c1, e1, u1), (c0, e0, u0) = _pair(dim, n, 300 + dim)
+    P = nks.Problem(dim, n, 0.25, c0, e0, cf, op)
+    O = oracle.Problem(dim, n, 0.25, cf, op)
+    N, nf = P.N, P.nf
+    cb = float(np.sum(c0) / N)
+    X1g, X0g = soa(c1, e1, u1), soa(c0, e0, u0)
+    X1o, X0o = O.interleave(c1, e1, u1), O.interleave(c0, e0, u0)
+    r = np.random.default_rng(9).standard_normal(nf * N)
+    z = P.apply_preconditioner(X1g, X0g, 0.07, r)
+    rc, zo = O.precond_apply(X1o, X0o, cb, 0.07, O.interleave(*split_soa(r, N, nf)))
+    assert rc == 0
+    assert rel(z, soa(*O.split(zo))) <= (1e-10 if precision == "fp64" else 1e-4)
+    P.destroy()
+
+
 def _run_both(nks, dim, n, cbar, seed, steps, op, cf=None, dt=0.01):
     cf = cf or S.coefficients()
     c, e = S.initial_fields(dim, n, cbar, seed)
