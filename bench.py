@@ -258,6 +258,7 @@ def run_ours(args):
     t_setup = time.perf_counter() - t_setup
     sst = P.get_stats()
     setup = {"seconds": t_setup, "u0_newton_its": sst["newton_its"], "u0_gmres_its": sst["gmres_its"],
+             "device_bytes": P.device_bytes(),
              "includes": "problem creation: plan, factor tables, upload, initial mechanical equilibrium (Newton on "
                          "the displacement rows, tolerance u0_rtol)"}
     state0 = P.get_state()

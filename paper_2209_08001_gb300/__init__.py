@@ -339,6 +339,9 @@ class Problem:
     def reset_stats(self):
         _check(load().nks_reset_stats(self._h), self._h)
 
+    def device_bytes(self):
+        return int(load().nks_device_bytes(self._h))
+
     # -- operator-level entry points (state arrays: fields one after another)
     def eval_residual(self, X1, X0, dt, mode=0):
         X1, X0 = _c64(X1), _c64(X0)

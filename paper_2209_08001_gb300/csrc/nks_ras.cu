@@ -152,10 +152,6 @@ constexpr int kHalo = 2;
 // 2-D boxes of the 1024^2 workload the copies land in time without it)
 constexpr int kPrefetch3 = 8;
 
-// factor-part buffers of the one-thread-per-point sweep: three (copies two levels
-// ahead) when the sub-vector still fits in shared memory, else two
-constexpr int kLaneBufsMax = 3;
-
 // Wavefront level of a box point.  Every lower neighbour of the stencil
 // (offsets (1,-1,0), (1,0,-1), (0,1,-1) and the axis offsets) must lie on an
 // earlier level, which the weights 1 < 2 < 3 give with the fewest levels; the
