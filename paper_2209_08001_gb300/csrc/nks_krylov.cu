@@ -105,11 +105,17 @@ __global__ void k_scale_dev(Bat bt, long long n, const TS *__restrict__ src, con
 {
     NKS_INST(src = shift(src, io); s = shift(s, io); dst = shift(dst, io);)
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    if constexpr (sizeof(TS) == sizeof(float) && sizeof(TD) == sizeof(float))
-        dst[i] = src[i] * (float)(*s);  // FP32 basis: FP32 arithmetic
-    else
+    if constexpr (sizeof(TS) == sizeof(float) && sizeof(TD) == sizeof(float)) {
+        // FP32 basis: FP32 arithmetic, the factor converted once per block (a
+        // double-to-float conversion per element would occupy the FP64 pipe)
+        __shared__ float sf;
+        if (threadIdx.x == 0) sf = (float)(*s);
+        __syncthreads();
+        if (i < n) dst[i] = src[i] * sf;
+    } else {
+        if (i >= n) return;
         dst[i] = (TD)((double)src[i] * (*s));
+    }
 }
 
 // y += x (x stored as TV)
@@ -461,8 +467,10 @@ __global__ void k_hsolve(Bat bt, double *gm, GmLayout L)
     }
 }
 
-// out = sum_{i < kdim} y_i v_i (FP64 sums)
-// kdim = the instance's Krylov dimension (gm scalar)
+// out = sum_{i < kdim} y_i v_i, kdim = the instance's Krylov dimension (gm scalar).
+// FP64 basis: FP64 sums.  FP32 basis: FP32 coefficients (converted once per block)
+// and FP32 sums, k ascending: the result is rounded to FP32 and enters the FP32
+// sweep, and FP64 sums of FP32 values would run on the 1/64-rate FP64 pipe.
 template <typename TV>
 __global__ void k_lincomb(Bat bt, long long n, const TV *__restrict__ V, long long ldv, const double *__restrict__ gm,
                           GmLayout L, TV *__restrict__ out)
@@ -470,16 +478,16 @@ __global__ void k_lincomb(Bat bt, long long n, const TV *__restrict__ V, long lo
     NKS_INST(V = shift(V, io); gm = shift(gm, io); out = shift(out, io);)
     const int kdim = (int)gm[L.scal + S_KDIM];
     const double *y = gm + L.y;
-    __shared__ double ys[kMaxDots];
-    if ((int)threadIdx.x < kdim) ys[threadIdx.x] = y[threadIdx.x];
+    __shared__ TV ys[kMaxDots];
+    if ((int)threadIdx.x < kdim) ys[threadIdx.x] = (TV)y[threadIdx.x];
     __syncthreads();
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    double s = 0.0;
+    TV s = (TV)0;
 #pragma unroll
     for (int k = 0; k < kMaxDots; k++)
-        if (k < kdim) s += ys[k] * (double)V[k * ldv + i];
-    out[i] = (TV)s;
+        if (k < kdim) s += ys[k] * V[k * ldv + i];
+    out[i] = s;
 }
 
 }  // namespace
