@@ -227,13 +227,20 @@ namespace nks {
 // points refer to earlier (forward) or later (backward) levels, which are
 // final when the level starts; entries at the same point refer to rows of
 // the same point.  Stage A runs, for every point of the level in parallel,
-// warp-uniform tasks over chunks of the other-point entries (at most kChunk
-// entries each): a row with one chunk and no same-point entry is finished in
+// warp-uniform tasks over chunks of the other-point entries (at most
+// chunk_size(D) entries each): a row with one chunk and no same-point entry is finished in
 // stage A, otherwise the chunk sum goes to a partial.  Stage B, one thread
 // per point, finishes the remaining rows in sweep order from their partials
 // and same-point entries.
 
-constexpr int kChunk = 5;
+// Entries per stage-A chunk: a shorter FP64 chain per task against more tasks,
+// partial sums and FP64 instructions.  Measured per Schwarz application on the
+// bench workloads' boxes: 2-D 68^2 boxes 5: 0.98 ms (4: 1.02, 6: 1.21, 7: 1.22,
+// 10: 1.16); 3-D 18^3 boxes 13: 2.41 ms (16: 2.41, 10: 2.68, 24: 2.76, 7: 3.25,
+// 5: 3.31).
+constexpr int kChunk2 = 5;
+constexpr int kChunk3 = 13;
+__host__ __device__ constexpr int chunk_size(int D) { return D == 3 ? kChunk3 : kChunk2; }
 constexpr int kMaxTasks = 24;
 constexpr int kMaxPartials = 24;
 
@@ -265,7 +272,7 @@ __host__ __device__ constexpr SweepPlan make_sweep_plan()
         S.same_e[f] = se;
         // other-point entries: [b, sb) and [se, e)
         const int n_other = (sb - b) + (e - se);
-        const int nch = (n_other + kChunk - 1) / kChunk;
+        const int nch = (n_other + chunk_size(D) - 1) / chunk_size(D);
         const bool finish_in_a = (nch <= 1) && (se == sb);
         S.row_stage_b[f] = finish_in_a ? 0 : 1;
         S.row_pb[f] = S.npart;
