@@ -23,6 +23,11 @@ Parity status per function (pins live in ``tests/test_oracle_*.py``):
                                         rate, mass, energy law, symmetries)
   physical coefficient values ......... parity unpinned (the CALPHAD and
                                         elastic constants are not printed)
+  three order parameters (n_eta = 3) .. pinned (reduction to the pinned reduced
+                                        model, four-sublattice symmetry of E_G,
+                                        exact discrete chain rule, central
+                                        differences, mass, energy law,
+                                        permutations); no CUDA path yet
 """
 from __future__ import annotations
 
@@ -59,7 +64,7 @@ class _Coeffs(ctypes.Structure):
                 ("theta", ctypes.c_double), ("w_psi", ctypes.c_double), ("dE0", ctypes.c_double),
                 ("L", ctypes.c_double * 4), ("U1", ctypes.c_double), ("U4", ctypes.c_double),
                 ("eps0", ctypes.c_double), ("C11", ctypes.c_double), ("C12", ctypes.c_double),
-                ("C44", ctypes.c_double), ("S", ctypes.c_int)]
+                ("C44", ctypes.c_double), ("S", ctypes.c_int), ("n_eta", ctypes.c_int)]
 
 
 class _Opts(ctypes.Structure):
@@ -160,6 +165,7 @@ def make_coeffs(cf: dict):
     s = cf.get("Lscale", 1.0)
     K.C11, K.C12, K.C44 = cf["C11"] * s, cf["C12"] * s, cf["C44"] * s
     K.S = int(cf["S"])
+    K.n_eta = int(cf.get("n_eta", 1))
     return K
 
 
@@ -197,20 +203,24 @@ class Problem:
         self.O = make_opts(opts) if opts is not None else None
         self.N = int(np.prod(self.n))
         self.nf = lib().orc_nfields(ctypes.byref(self.G), ctypes.byref(self.K))
+        self.ne = 3 if self.K.n_eta == 3 else 1  # order parameters per point
+        self.ku = 1 + self.ne                    # first displacement field
 
-    # SoA (c, eta, u[d, N]) <-> point-interleaved X (Sec. 4)
+    # SoA (c, eta, u[d, N]) <-> point-interleaved X (Sec. 4); with three order
+    # parameters eta is (3, N)
     def interleave(self, c, eta, u=None):
         X = np.zeros((self.N, self.nf))
         X[:, 0] = c
-        X[:, 1] = eta
-        if self.nf > 2 and u is not None:
-            X[:, 2:] = np.asarray(u).reshape(self.dim, self.N).T
+        X[:, 1:self.ku] = np.asarray(eta).reshape(self.ne, self.N).T
+        if self.nf > self.ku and u is not None:
+            X[:, self.ku:] = np.asarray(u).reshape(self.dim, self.N).T
         return np.ascontiguousarray(X.reshape(-1))
 
     def split(self, X):
         Y = np.asarray(X).reshape(self.N, self.nf)
-        u = Y[:, 2:].T.copy() if self.nf > 2 else None
-        return Y[:, 0].copy(), Y[:, 1].copy(), u
+        u = Y[:, self.ku:].T.copy() if self.nf > self.ku else None
+        eta = Y[:, 1].copy() if self.ne == 1 else Y[:, 1:self.ku].T.copy()
+        return Y[:, 0].copy(), eta, u
 
     def _g(self):
         return ctypes.byref(self.G), ctypes.byref(self.K)
@@ -228,9 +238,9 @@ class Problem:
     def dvd_G(self, X1, X0, cbar0, which=15):
         X1 = np.ascontiguousarray(X1, dtype=np.float64)
         X0 = np.ascontiguousarray(X0, dtype=np.float64)
-        gc, ge = np.zeros(self.N), np.zeros(self.N)
+        gc, ge = np.zeros(self.N), np.zeros(self.N * self.ne)
         lib().orc_dvd_G(*self._g(), cbar0, _ptr(X1), _ptr(X0), which, _ptr(gc), _ptr(ge))
-        return gc, ge
+        return gc, (ge if self.ne == 1 else ge.reshape(3, self.N))
 
     def residual(self, X1, X0, cbar0, dt, mode=0):
         X1 = np.ascontiguousarray(X1, dtype=np.float64)

@@ -14,17 +14,20 @@
  *   - unknowns point-interleaved, X = (c_1, eta_1, u_1.., c_2, eta_2, u_2.., ...)
  *     (Sec. 4: "the unknown X is organized by points");
  *   - fields per point: c, eta and, when elasticity is on, the d displacement
- *     components u_1..u_d;
+ *     components u_1..u_d; with three order parameters (App. A, n_eta = 3)
+ *     c, eta_1, eta_2, eta_3, then u_1..u_d;
  *   - every sum is a serial loop in point order; nothing is blocked or fused.
  *
  * The readings of passages the paper leaves open (tolerances, line search,
  * projection of the Krylov corrections, the elastic gauge, ...) are stated at
  * each function.
  */
+#include <complex.h>
 #include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
+#undef I /* complex.h's imaginary unit: _Complex_I is used by name, I stays an axis index */
 
 /* ------------------------------------------------------------------------ */
 /* Public structures (mirrored by ctypes in oracle/__init__.py)              */
@@ -48,6 +51,8 @@ typedef struct {
     double eps0;      /* composition expansion coefficient of the lattice      */
     double C11, C12, C44; /* dimensionless cubic Hooke constants (x Lscale)    */
     int S;            /* Taylor order of Psi_S (Sec. 3); S <= 0: exact quotient */
+    int n_eta;        /* order parameters: 1 (the reduced model of the main text) or
+                         3 (App. A: eta_1..eta_3, eta_4 = 4 - sum); 0 reads as 1      */
 } orc_coeffs;
 
 typedef struct {
@@ -112,8 +117,11 @@ static void coords(const orc_grid *g, long p, long x[3])
 }
 
 static int is_elastic(const orc_coeffs *k) { return k->C11 != 0.0 || k->C12 != 0.0 || k->C44 != 0.0; }
+static int n_eta(const orc_coeffs *k) { return k->n_eta == 3 ? 3 : 1; }
+/* per point: c, the order parameters, then (with elasticity) u_1..u_d from field ufield(k) */
+static int ufield(const orc_coeffs *k) { return 1 + n_eta(k); }
 
-int orc_nfields(const orc_grid *g, const orc_coeffs *k) { return 2 + (is_elastic(k) ? g->dim : 0); }
+int orc_nfields(const orc_grid *g, const orc_coeffs *k) { return ufield(k) + (is_elastic(k) ? g->dim : 0); }
 
 /* ------------------------------------------------------------------------ */
 /* Free energy (Sec. 2, App. A) and its discrete form (Sec. 3, Eq. relations) */
@@ -164,7 +172,7 @@ static void el_strain(const orc_grid *g, const orc_coeffs *k, int nf, double cba
     double Du[3][3] = {{0}};
     for (int I = 0; I < d; I++)
         for (int J = 0; J < d; J++)
-            Du[I][J] = (X[nbr(g, p, J, +1) * nf + 2 + I] - X[nbr(g, p, J, -1) * nf + 2 + I]) / (2.0 * h);
+            Du[I][J] = (X[nbr(g, p, J, +1) * nf + ufield(k) + I] - X[nbr(g, p, J, -1) * nf + ufield(k) + I]) / (2.0 * h);
     double c = X[p * nf + 0];
     for (int I = 0; I < 3; I++)
         for (int J = 0; J < 3; J++) e[I][J] = 0.0;
@@ -204,6 +212,8 @@ static double E3_density(const orc_coeffs *k, int d, double e[3][3])
  * E4 = gamma_c/2 [(D^pm c)^2] + 3 gamma_eta/2 [(D^pm eta)^2] with
  * [(D^pm f)^2] = ((D^+ f)^2 + (D^- f)^2)/2 summed over the d axes.
  * parts (optional) receives the four sums times h^d. */
+static void E12_density3(const orc_coeffs *k, double c, const double e[3], double *e1, double *e2);
+
 double orc_energy(const orc_grid *g, const orc_coeffs *k, double cbar0, const double *X, double *parts)
 {
     int nf = orc_nfields(g, k), d = g->dim;
@@ -211,10 +221,31 @@ double orc_energy(const orc_grid *g, const orc_coeffs *k, double cbar0, const do
     double h = g->h;
     double s1 = 0, s2 = 0, s3 = 0, s4 = 0;
     for (long p = 0; p < N; p++) {
+        if (n_eta(k) == 3) {
+            /* three order parameters: E_1, E_2 of App. A, E_4 with gamma_eta/2 per eta_j */
+            double c = X[p * nf], e[3] = {X[p * nf + 1], X[p * nf + 2], X[p * nf + 3]}, a, b;
+            E12_density3(k, c, e, &a, &b);
+            s1 += a;
+            s2 += b;
+            if (is_elastic(k)) {
+                double ee[3][3];
+                el_strain(g, k, nf, cbar0, X, p, ee);
+                s3 += E3_density(k, d, ee);
+            }
+            for (int f = 0; f < 4; f++) {
+                double gs = 0.0, v0 = X[p * nf + f];
+                for (int J = 0; J < d; J++) {
+                    double dp = (X[nbr(g, p, J, +1) * nf + f] - v0) / h, dm = (v0 - X[nbr(g, p, J, -1) * nf + f]) / h;
+                    gs += 0.5 * (dp * dp + dm * dm);
+                }
+                s4 += 0.5 * (f == 0 ? k->gamma_c : k->gamma_eta) * gs;
+            }
+            continue;
+        }
         double c = X[p * nf], eta = X[p * nf + 1];
         s1 += Phi_poly(k, c, 1.0 - eta);
         s2 += E2_density(k, c, eta);
-        if (nf > 2) {
+        if (is_elastic(k)) {
             double e[3][3];
             el_strain(g, k, nf, cbar0, X, p, e);
             s3 += E3_density(k, d, e);
@@ -354,6 +385,193 @@ static void G2_point(const orc_coeffs *k, double c1, double e1, double c0, doubl
     *ge = k->theta / 4.0 * 3.0 * ch * (Qp - Qq);
 }
 
+/* ------------------------------------------------------------------------ */
+/* Three order parameters (App. A): eta_1, eta_2, eta_3 and eta_4 = 4 - sum  */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Gibbs energy of App. A with the four sublattice site fractions c eta_i
+ * (scaled by 1/(V_m dE) as the reduced model):
+ *   E_1 = dis(c) + a(c) S(eta) + b(c) T(eta),
+ *     dis(c) = dE0 c + c(1-c) sum_i L_i (2c-1)^i,
+ *     a(c)   = 6 U1 c^2 - 2 U1 c^2 + 12 U4 (1-2c) c^2,   b(c) = -48 U4 c^3,
+ *     S = phi_1^2 + phi_2^2 + phi_3^2,  T = phi_1 phi_2 phi_3,
+ *     phi_1 = 1 - (eta_1+eta_2)/2, phi_2 = 1 - (eta_1+eta_3)/2, phi_3 = 1 - (eta_2+eta_3)/2;
+ *   E_2 = theta { w Psi(c) + 1/4 sum_{i=1..4} Psi(c eta_i) };
+ *   E_4 = gamma_c/2 |grad c|^2 + gamma_eta/2 sum_{i=1..3} |grad eta_i|^2.
+ * With eta_1 = eta_2 = eta_3 = eta these are the reduced model's E_1, E_2, E_4.
+ *
+ * Discrete variational derivative (reading: the reduced scheme of Sec. 3 /
+ * App. B extended so that the discrete chain rule holds term by term):
+ *   a product f(c) g(eta) splits symmetrically,
+ *     G_c      += f[c1, c0] (g(eta^0) + g(eta^1))/2,
+ *     G_eta_j  += (f(c0) + f(c1))/2 g_j[eta^0, eta^1],
+ *   with f[c1, c0] = int_0^1 f'(c0 + s (c1 - c0)) ds (the polynomial quotient) and
+ *   g_j the average-vector-field discrete gradient int_0^1 dg/deta_j(eta^0 + s (eta^1 - eta^0)) ds,
+ *   both exact here with 3-point Gauss-Legendre (integrands of degree <= 4);
+ *   the logarithms use the Psi_S quotients of Sec. 3 with p_i = c eta_i:
+ *     G_c     += theta/4 [ 4 w Psi_S[c] + sum_{i=1..4} (eta_i)_h Psi_S[p_i] ],
+ *     G_eta_j += theta/4 c_h ( Psi_S[p_j] - Psi_S[p_4] );
+ *   G^4: G_c = -gamma_c D^2 c_h, G_eta_j = -gamma_eta D^2 (eta_j)_h; G^3 as before.
+ * For eta_1 = eta_2 = eta_3 this gives the reduced G_c and sum_j G_eta_j = G_eta.
+ * The Allen-Cahn rows take the kinetic factor 3, F_eta_j = (eta_j^1 - eta_j^0)/dt
+ * + 3 G_eta_j (reading: the reduced model's eta equation is then the symmetric
+ * solution of this one, whose order parameters stay equal).
+ *
+ * The pointwise functions are written in complex arithmetic so that the
+ * Jacobian's pointwise block is their complex-step derivative (Im f(x + i t)/t,
+ * exact to rounding, no difference quotient); that needs the Taylor form of
+ * Psi_S (S > 0).
+ */
+typedef double complex cplx;
+
+static const double kEtaKinetic3 = 3.0;
+
+static void gauss3(double t[3], double w[3])
+{
+    const double r = sqrt(0.6);
+    t[0] = 0.5 - 0.5 * r;
+    t[1] = 0.5;
+    t[2] = 0.5 + 0.5 * r;
+    w[0] = 5.0 / 18.0;
+    w[1] = 8.0 / 18.0;
+    w[2] = 5.0 / 18.0;
+}
+
+static cplx dis3(const orc_coeffs *k, cplx c)
+{
+    cplx s = 2.0 * c - 1.0;
+    return k->dE0 * c + c * (1.0 - c) * (k->L[0] + k->L[1] * s + k->L[2] * s * s + k->L[3] * s * s * s);
+}
+static cplx dis3_d(const orc_coeffs *k, cplx c)
+{
+    cplx s = 2.0 * c - 1.0;
+    cplx P = k->L[0] + k->L[1] * s + k->L[2] * s * s + k->L[3] * s * s * s;
+    cplx dP = k->L[1] + 2.0 * k->L[2] * s + 3.0 * k->L[3] * s * s;
+    return k->dE0 + (1.0 - 2.0 * c) * P + c * (1.0 - c) * 2.0 * dP;
+}
+static cplx a3(const orc_coeffs *k, cplx c) { return 6.0 * k->U1 * c * c - 2.0 * k->U1 * c * c + 12.0 * k->U4 * (1.0 - 2.0 * c) * c * c; }
+static cplx a3_d(const orc_coeffs *k, cplx c) { return 8.0 * k->U1 * c + 12.0 * k->U4 * (2.0 * c - 6.0 * c * c); }
+static cplx b3(const orc_coeffs *k, cplx c) { return -48.0 * k->U4 * c * c * c; }
+static cplx b3_d(const orc_coeffs *k, cplx c) { return -144.0 * k->U4 * c * c; }
+
+static void phi3(const cplx e[3], cplx f[3])
+{
+    f[0] = 1.0 - 0.5 * (e[0] + e[1]);
+    f[1] = 1.0 - 0.5 * (e[0] + e[2]);
+    f[2] = 1.0 - 0.5 * (e[1] + e[2]);
+}
+static cplx S3(const cplx e[3])
+{
+    cplx f[3];
+    phi3(e, f);
+    return f[0] * f[0] + f[1] * f[1] + f[2] * f[2];
+}
+static cplx T3(const cplx e[3])
+{
+    cplx f[3];
+    phi3(e, f);
+    return f[0] * f[1] * f[2];
+}
+/* dS/deta_j and dT/deta_j */
+static void dST3(const cplx e[3], cplx dS[3], cplx dT[3])
+{
+    cplx f[3];
+    phi3(e, f);
+    dS[0] = -(f[0] + f[1]);
+    dS[1] = -(f[0] + f[2]);
+    dS[2] = -(f[1] + f[2]);
+    dT[0] = -0.5 * f[2] * (f[0] + f[1]);
+    dT[1] = -0.5 * f[1] * (f[0] + f[2]);
+    dT[2] = -0.5 * f[0] * (f[1] + f[2]);
+}
+
+static cplx Psi_cx(cplx z) { return z * clog(z) + (1.0 - z) * clog(1.0 - z); }
+static cplx dPsi_cx(cplx z) { return clog(z) - clog(1.0 - z); }
+
+/* Psi_S[y1, y2] of Sec. 3 (as orc_psi_quot) in complex arithmetic */
+static cplx psi_quot_cx(cplx y1, cplx y2, int S)
+{
+    if (S <= 0) {
+        if (creal(y1) == creal(y2) && cimag(y1) == cimag(y2)) return dPsi_cx(y1);
+        return (Psi_cx(y1) - Psi_cx(y2)) / (y1 - y2);
+    }
+    cplx yb = 0.5 * (y1 + y2), de = 0.5 * (y2 - y1);
+    cplx a2 = (de / (1.0 - yb)) * (de / (1.0 - yb));
+    cplx b2 = (de / yb) * (de / yb);
+    cplx q = dPsi_cx(yb);
+    cplx ak = 1.0, bk = 1.0;
+    for (int kk = 1; kk <= S - 1; kk++) {
+        ak *= a2;
+        bk *= b2;
+        q += (ak - bk) / (2.0 * kk * (2.0 * kk + 1.0));
+    }
+    return q;
+}
+
+/* pointwise G^1 (which & 1) + G^{2,S} (which & 2): out = (G_c, G_eta_1, G_eta_2, G_eta_3) */
+static void G3_point(const orc_coeffs *k, int which, cplx c1, const cplx e1[3], cplx c0, const cplx e0[3], cplx out[4])
+{
+    for (int a = 0; a < 4; a++) out[a] = 0.0;
+    if (which & 1) {
+        double t[3], w[3];
+        gauss3(t, w);
+        cplx qd = 0.0, qa = 0.0, qb = 0.0, Sj[3] = {0, 0, 0}, Tj[3] = {0, 0, 0};
+        for (int i = 0; i < 3; i++) {
+            cplx c = c0 + t[i] * (c1 - c0), e[3], dS[3], dT[3];
+            for (int j = 0; j < 3; j++) e[j] = e0[j] + t[i] * (e1[j] - e0[j]);
+            qd += w[i] * dis3_d(k, c);
+            qa += w[i] * a3_d(k, c);
+            qb += w[i] * b3_d(k, c);
+            dST3(e, dS, dT);
+            for (int j = 0; j < 3; j++) {
+                Sj[j] += w[i] * dS[j];
+                Tj[j] += w[i] * dT[j];
+            }
+        }
+        out[0] += qd + qa * 0.5 * (S3(e0) + S3(e1)) + qb * 0.5 * (T3(e0) + T3(e1));
+        cplx am = 0.5 * (a3(k, c0) + a3(k, c1)), bm = 0.5 * (b3(k, c0) + b3(k, c1));
+        for (int j = 0; j < 3; j++) out[1 + j] += am * Sj[j] + bm * Tj[j];
+    }
+    if (which & 2) {
+        cplx e14 = 4.0 - e1[0] - e1[1] - e1[2], e04 = 4.0 - e0[0] - e0[1] - e0[2];
+        cplx E1[4] = {e1[0], e1[1], e1[2], e14}, E0[4] = {e0[0], e0[1], e0[2], e04};
+        cplx Q[4];
+        for (int i = 0; i < 4; i++) Q[i] = psi_quot_cx(c1 * E1[i], c0 * E0[i], k->S);
+        cplx ch = 0.5 * (c1 + c0), t4 = k->theta / 4.0;
+        cplx gc = 4.0 * k->w_psi * psi_quot_cx(c1, c0, k->S);
+        for (int i = 0; i < 4; i++) gc += 0.5 * (E1[i] + E0[i]) * Q[i];
+        out[0] += t4 * gc;
+        for (int j = 0; j < 3; j++) out[1 + j] += t4 * ch * (Q[j] - Q[3]);
+    }
+}
+
+/* E_1 + E_2 densities of the three-parameter model at one point */
+static void E12_density3(const orc_coeffs *k, double c, const double e[3], double *e1, double *e2)
+{
+    cplx ec[3] = {e[0], e[1], e[2]};
+    *e1 = creal(dis3(k, c) + a3(k, c) * S3(ec) + b3(k, c) * T3(ec));
+    double s = k->w_psi * creal(Psi_cx(c));
+    double e4 = 4.0 - e[0] - e[1] - e[2];
+    for (int i = 0; i < 3; i++) s += 0.25 * creal(Psi_cx(c * e[i]));
+    s += 0.25 * creal(Psi_cx(c * e4));
+    *e2 = k->theta * s;
+}
+
+/* pointwise derivatives d(G_c, G_eta_j)/d(c1, eta_1..3) (row-major 4 x 4) by complex step */
+static void G3_partials(const orc_coeffs *k, double c1, const double e1[3], double c0, const double e0[3], double out[16])
+{
+    const double t = 1e-40;
+    cplx C0 = c0, E0[3] = {e0[0], e0[1], e0[2]};
+    for (int b = 0; b < 4; b++) {
+        cplx C1 = c1, E1[3] = {e1[0], e1[1], e1[2]}, G[4];
+        if (b == 0) C1 += _Complex_I * t;
+        else E1[b - 1] += _Complex_I * t;
+        G3_point(k, 3, C1, E1, C0, E0, G);
+        for (int a = 0; a < 4; a++) out[a * 4 + b] = cimag(G[a]) / t;
+    }
+}
+
 /*
  * Grid functions G_c, G_eta of the DVD derivative, term by term
  * (which: bit 0 = G^1, bit 1 = G^2, bit 2 = G^3, bit 3 = G^4):
@@ -366,6 +584,43 @@ void orc_dvd_G(const orc_grid *g, const orc_coeffs *k, double cbar0, const doubl
     int nf = orc_nfields(g, k), d = g->dim;
     long N = grid_N(g);
     double h = g->h;
+    if (n_eta(k) == 3) {
+        /* Ge holds G_eta_j at Ge[j N + p] */
+        for (long p = 0; p < N; p++) {
+            cplx c1 = X1[p * nf], c0 = X0[p * nf], e1[3], e0[3], G[4];
+            for (int j = 0; j < 3; j++) {
+                e1[j] = X1[p * nf + 1 + j];
+                e0[j] = X0[p * nf + 1 + j];
+            }
+            G3_point(k, which & 3, c1, e1, c0, e0, G);
+            double gc = creal(G[0]), ge[3] = {creal(G[1]), creal(G[2]), creal(G[3])};
+            if ((which & 4) && is_elastic(k)) {
+                double eps1[3][3], eps0m[3][3], s1[3][3], s0[3][3];
+                el_strain(g, k, nf, cbar0, X1, p, eps1);
+                el_strain(g, k, nf, cbar0, X0, p, eps0m);
+                hooke(k, d, eps1, s1);
+                hooke(k, d, eps0m, s0);
+                double tr = 0.0;
+                for (int I = 0; I < d; I++) tr += 0.5 * (s1[I][I] + s0[I][I]);
+                gc += -k->eps0 * tr;
+            }
+            if (which & 8) {
+                for (int f = 0; f < 4; f++) {
+                    double lap = 0.0, mid = 0.5 * (X1[p * nf + f] + X0[p * nf + f]);
+                    for (int J = 0; J < d; J++) {
+                        long pp = nbr(g, p, J, +1), pm = nbr(g, p, J, -1);
+                        lap += (0.5 * (X1[pp * nf + f] + X0[pp * nf + f]) - 2.0 * mid +
+                                0.5 * (X1[pm * nf + f] + X0[pm * nf + f])) / (h * h);
+                    }
+                    if (f == 0) gc += -k->gamma_c * lap;
+                    else ge[f - 1] += -k->gamma_eta * lap;
+                }
+            }
+            Gc[p] = gc;
+            for (int j = 0; j < 3; j++) Ge[j * N + p] = ge[j];
+        }
+        return;
+    }
     for (long p = 0; p < N; p++) {
         double c1 = X1[p * nf], e1 = X1[p * nf + 1], c0 = X0[p * nf], e0 = X0[p * nf + 1];
         double gc = 0.0, ge = 0.0, a, b;
@@ -379,7 +634,7 @@ void orc_dvd_G(const orc_grid *g, const orc_coeffs *k, double cbar0, const doubl
             gc += a;
             ge += b;
         }
-        if ((which & 4) && nf > 2) {
+        if ((which & 4) && is_elastic(k)) {
             double eps1[3][3], eps0m[3][3], s1[3][3], s0[3][3];
             el_strain(g, k, nf, cbar0, X1, p, eps1);
             el_strain(g, k, nf, cbar0, X0, p, eps0m);
@@ -429,10 +684,12 @@ static double edge_mob(const orc_grid *g, const orc_coeffs *k, int nf, const dou
 void orc_residual(const orc_grid *g, const orc_coeffs *k, double cbar0, double dt, const double *X1,
                   const double *X0, int mode, double *F)
 {
-    int nf = orc_nfields(g, k), d = g->dim;
+    int nf = orc_nfields(g, k), d = g->dim, ne = n_eta(k), ku = ufield(k);
     long N = grid_N(g);
     double h = g->h;
-    double *Gc = (double *)malloc(sizeof(double) * N), *Ge = (double *)malloc(sizeof(double) * N);
+    /* kinetic factor of the Allen-Cahn rows: 1 (reduced model), 3 (three order parameters) */
+    double keta = ne == 3 ? kEtaKinetic3 : 1.0;
+    double *Gc = (double *)malloc(sizeof(double) * N), *Ge = (double *)malloc(sizeof(double) * N * ne);
     if (mode == 0) orc_dvd_G(g, k, cbar0, X1, X0, 15, Gc, Ge);
     for (long p = 0; p < N; p++) {
         if (mode == 0) {
@@ -443,12 +700,12 @@ void orc_residual(const orc_grid *g, const orc_coeffs *k, double cbar0, double d
                 flux += (Mp * (Gc[pp] - Gc[p]) - Mm * (Gc[p] - Gc[pm])) / (h * h);
             }
             F[p * nf] = (X1[p * nf] - X0[p * nf]) / dt - flux;
-            F[p * nf + 1] = (X1[p * nf + 1] - X0[p * nf + 1]) / dt + Ge[p];
+            for (int j = 0; j < ne; j++)
+                F[p * nf + 1 + j] = (X1[p * nf + 1 + j] - X0[p * nf + 1 + j]) / dt + keta * Ge[j * N + p];
         } else {
-            F[p * nf] = 0.0;
-            F[p * nf + 1] = 0.0;
+            for (int f = 0; f < ku; f++) F[p * nf + f] = 0.0;
         }
-        if (nf > 2) {
+        if (is_elastic(k)) {
             for (int I = 0; I < d; I++) {
                 double div = 0.0;
                 for (int J = 0; J < d; J++) {
@@ -459,7 +716,7 @@ void orc_residual(const orc_grid *g, const orc_coeffs *k, double cbar0, double d
                     hooke(k, d, em, sm);
                     div += (sp[I][J] - sm[I][J]) / (2.0 * h);
                 }
-                F[p * nf + 2 + I] = div;
+                F[p * nf + ku + I] = div;
             }
         }
     }
@@ -579,10 +836,10 @@ static void G12_partials(const orc_coeffs *k, double c1, double e1, double c0, d
 typedef struct {
     const orc_grid *g;
     const orc_coeffs *k;
-    int nf, d;
+    int nf, d, ne, ku;
     double cbar0, dt;
     const double *X1, *X0;
-    double *part; /* 4 per point */
+    double *part; /* (1 + ne)^2 per point: d(G_c, G_eta_j)/d(c1, eta_j1), row-major */
 } jac_ctx;
 
 /* row of dG_c(q)/dX1 */
@@ -592,9 +849,10 @@ static void Gc_row(const jac_ctx *cx, long q, rowacc *r)
     const orc_coeffs *k = cx->k;
     int nf = cx->nf, d = cx->d;
     double h = g->h;
+    const int P = (1 + cx->ne) * (1 + cx->ne), ku = cx->ku;
     ra_clear(r);
-    double diag = cx->part[q * 4 + 0] + k->gamma_c * d / (h * h);
-    if (nf > 2) {
+    double diag = cx->part[q * P + 0] + k->gamma_c * d / (h * h);
+    if (is_elastic(k)) {
         double lam = k->C11 + (d - 1) * k->C12;
         diag += 0.5 * d * k->eps0 * k->eps0 * lam;
     }
@@ -603,13 +861,13 @@ static void Gc_row(const jac_ctx *cx, long q, rowacc *r)
         ra_add(r, nbr(g, q, J, +1) * nf + 0, -0.5 * k->gamma_c / (h * h));
         ra_add(r, nbr(g, q, J, -1) * nf + 0, -0.5 * k->gamma_c / (h * h));
     }
-    ra_add(r, q * nf + 1, cx->part[q * 4 + 1]);
-    if (nf > 2) {
+    for (int j = 0; j < cx->ne; j++) ra_add(r, q * nf + 1 + j, cx->part[q * P + 1 + j]);
+    if (is_elastic(k)) {
         /* G^3_c = -eps0 (C11 + (d-1) C12) tr eps^el_h, tr eps^el = sum_K Dhat_K u_K - d eps0 (c - cbar0) */
         double lam = k->C11 + (d - 1) * k->C12;
         for (int K = 0; K < d; K++) {
-            ra_add(r, nbr(g, q, K, +1) * nf + 2 + K, -k->eps0 * lam * 0.5 / (2.0 * h));
-            ra_add(r, nbr(g, q, K, -1) * nf + 2 + K, +k->eps0 * lam * 0.5 / (2.0 * h));
+            ra_add(r, nbr(g, q, K, +1) * nf + ku + K, -k->eps0 * lam * 0.5 / (2.0 * h));
+            ra_add(r, nbr(g, q, K, -1) * nf + ku + K, +k->eps0 * lam * 0.5 / (2.0 * h));
         }
     }
 }
@@ -619,21 +877,21 @@ static void sig_row(const jac_ctx *cx, long q, int I, int J, rowacc *r)
 {
     const orc_grid *g = cx->g;
     const orc_coeffs *k = cx->k;
-    int nf = cx->nf, d = cx->d;
+    int nf = cx->nf, d = cx->d, ku = cx->ku;
     double h = g->h;
     ra_clear(r);
     if (I == J) {
         for (int K = 0; K < d; K++) {
             double cf = (K == I) ? k->C11 : k->C12;
-            ra_add(r, nbr(g, q, K, +1) * nf + 2 + K, cf / (2.0 * h));
-            ra_add(r, nbr(g, q, K, -1) * nf + 2 + K, -cf / (2.0 * h));
+            ra_add(r, nbr(g, q, K, +1) * nf + ku + K, cf / (2.0 * h));
+            ra_add(r, nbr(g, q, K, -1) * nf + ku + K, -cf / (2.0 * h));
         }
         ra_add(r, q * nf + 0, -k->eps0 * (k->C11 + (d - 1) * k->C12));
     } else {
-        ra_add(r, nbr(g, q, J, +1) * nf + 2 + I, k->C44 / (2.0 * h));
-        ra_add(r, nbr(g, q, J, -1) * nf + 2 + I, -k->C44 / (2.0 * h));
-        ra_add(r, nbr(g, q, I, +1) * nf + 2 + J, k->C44 / (2.0 * h));
-        ra_add(r, nbr(g, q, I, -1) * nf + 2 + J, -k->C44 / (2.0 * h));
+        ra_add(r, nbr(g, q, J, +1) * nf + ku + I, k->C44 / (2.0 * h));
+        ra_add(r, nbr(g, q, J, -1) * nf + ku + I, -k->C44 / (2.0 * h));
+        ra_add(r, nbr(g, q, I, +1) * nf + ku + J, k->C44 / (2.0 * h));
+        ra_add(r, nbr(g, q, I, -1) * nf + ku + J, -k->C44 / (2.0 * h));
     }
 }
 
@@ -641,13 +899,22 @@ static void sig_row(const jac_ctx *cx, long q, int I, int J, rowacc *r)
 static void assemble_jacobian(const orc_grid *g, const orc_coeffs *k, double cbar0, double dt, const double *X1,
                               const double *X0, int mode, csr *A)
 {
-    int nf = orc_nfields(g, k), d = g->dim;
+    int nf = orc_nfields(g, k), d = g->dim, ne = n_eta(k), ku = ufield(k);
     long N = grid_N(g);
     double h = g->h;
-    jac_ctx cx = {g, k, nf, d, cbar0, dt, X1, X0, NULL};
-    cx.part = (double *)malloc(sizeof(double) * 4 * N);
-    for (long p = 0; p < N; p++)
-        G12_partials(k, X1[p * nf], X1[p * nf + 1], X0[p * nf], X0[p * nf + 1], cx.part + 4 * p);
+    const int P = (1 + ne) * (1 + ne);
+    double keta = ne == 3 ? kEtaKinetic3 : 1.0;
+    jac_ctx cx = {g, k, nf, d, ne, ku, cbar0, dt, X1, X0, NULL};
+    cx.part = (double *)malloc(sizeof(double) * P * N);
+    for (long p = 0; p < N; p++) {
+        if (ne == 3) {
+            double e1[3] = {X1[p * nf + 1], X1[p * nf + 2], X1[p * nf + 3]};
+            double e0[3] = {X0[p * nf + 1], X0[p * nf + 2], X0[p * nf + 3]};
+            G3_partials(k, X1[p * nf], e1, X0[p * nf], e0, cx.part + P * p);
+        } else {
+            G12_partials(k, X1[p * nf], X1[p * nf + 1], X0[p * nf], X0[p * nf + 1], cx.part + P * p);
+        }
+    }
 
     long cap = N * nf * 40 + 16;
     A->n = N * nf;
@@ -677,19 +944,25 @@ static void assemble_jacobian(const orc_grid *g, const orc_coeffs *k, double cba
                 } else {
                     ra_add(row, p * nf + 0, 1.0);
                 }
-            } else if (f == 1) {
+            } else if (f < ku) {
+                /* eta_j row, j = f - 1: (eta_j1 - eta_j0)/dt + keta G_eta_j; the gradient
+                 * part of keta G_eta_j is -3/2 gamma_eta D^2 eta_j1 + ... in both models */
+                const int j = f - 1;
                 if (mode == 0) {
-                    ra_add(row, p * nf + 1, 1.0 / dt + cx.part[p * 4 + 3] + 3.0 * k->gamma_eta * d / (h * h));
-                    ra_add(row, p * nf + 0, cx.part[p * 4 + 2]);
+                    const double *pr = cx.part + (long)P * p + (1 + j) * (1 + ne);
+                    ra_add(row, p * nf + f, 1.0 / dt + keta * pr[1 + j] + 3.0 * k->gamma_eta * d / (h * h));
+                    ra_add(row, p * nf + 0, keta * pr[0]);
+                    for (int jj = 0; jj < ne; jj++)
+                        if (jj != j) ra_add(row, p * nf + 1 + jj, keta * pr[1 + jj]);
                     for (int J = 0; J < d; J++) {
-                        ra_add(row, nbr(g, p, J, +1) * nf + 1, -1.5 * k->gamma_eta / (h * h));
-                        ra_add(row, nbr(g, p, J, -1) * nf + 1, -1.5 * k->gamma_eta / (h * h));
+                        ra_add(row, nbr(g, p, J, +1) * nf + f, -1.5 * k->gamma_eta / (h * h));
+                        ra_add(row, nbr(g, p, J, -1) * nf + f, -1.5 * k->gamma_eta / (h * h));
                     }
                 } else {
-                    ra_add(row, p * nf + 1, 1.0);
+                    ra_add(row, p * nf + f, 1.0);
                 }
             } else {
-                int I = f - 2;
+                int I = f - ku;
                 for (int J = 0; J < d; J++) {
                     sig_row(&cx, nbr(g, p, J, +1), I, J, t);
                     ra_axpy(row, 1.0 / (2.0 * h), t);
@@ -871,6 +1144,7 @@ static void dense_lu_solve(long n, const double *a, const long *piv, const doubl
 
 typedef struct {
     int nsub, nf;
+    int ku;              /* first displacement field (nf: none)            */
     long *next;          /* overlapped (extended) points per subdomain     */
     long **pts;          /* global point of each local point (x-fastest)   */
     unsigned char **own; /* 1 if the local point is owned (restricted)     */
@@ -918,13 +1192,14 @@ static void ras_free(ras_t *R)
 }
 
 /* build the subdomains of the box decomposition and factor J restricted to each overlapped box */
-static int ras_setup(const orc_grid *g, int nf, const orc_opts *o, const csr *J, ras_t *R)
+static int ras_setup(const orc_grid *g, int nf, int ku, const orc_opts *o, const csr *J, ras_t *R)
 {
     int d = g->dim;
     int sub[3] = {1, 1, 1};
     for (int a = 0; a < d; a++) sub[a] = o->sub[a] > 0 ? o->sub[a] : 1;
     R->nsub = sub[0] * sub[1] * sub[2];
     R->nf = nf;
+    R->ku = ku;
     R->subsolver = o->subsolver;
     R->variant = o->variant;
     R->next = (long *)calloc(R->nsub, sizeof(long));
@@ -1030,14 +1305,14 @@ static int ras_setup(const orc_grid *g, int nf, const orc_opts *o, const csr *J,
  *     centred-difference strain: tensor products over the axes of 1 and, on
  *     axes with an even number of cells, (-1)^x.
  */
-static void project(const orc_grid *g, int nf, double *z)
+static void project(const orc_grid *g, int nf, int ku, double *z)
 {
     long N = grid_N(g);
     double s = 0.0;
     for (long p = 0; p < N; p++) s += z[p * nf];
     double mean = s / (double)N;
     for (long p = 0; p < N; p++) z[p * nf] -= mean;
-    if (nf <= 2) return;
+    if (ku >= nf) return;
     int d = g->dim;
     int even_mask = 0;
     for (int J = 0; J < d; J++)
@@ -1053,7 +1328,7 @@ static void project(const orc_grid *g, int nf, double *z)
                 for (int J = 0; J < d; J++)
                     if (m & (1 << J)) par += (int)(x[J] & 1);
                 double sg = (par & 1) ? -1.0 : 1.0;
-                dot += sg * z[p * nf + 2 + I];
+                dot += sg * z[p * nf + ku + I];
             }
             double a = dot / (double)N;
             for (long p = 0; p < N; p++) {
@@ -1063,7 +1338,7 @@ static void project(const orc_grid *g, int nf, double *z)
                 for (int J = 0; J < d; J++)
                     if (m & (1 << J)) par += (int)(x[J] & 1);
                 double sg = (par & 1) ? -1.0 : 1.0;
-                z[p * nf + 2 + I] -= a * sg;
+                z[p * nf + ku + I] -= a * sg;
             }
         }
     }
@@ -1102,7 +1377,7 @@ static void ras_apply(const orc_grid *g, const ras_t *R, int do_project, const d
         free(b);
         free(x);
     }
-    if (do_project) project(g, nf, z);
+    if (do_project) project(g, nf, R->ku, z);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -1217,9 +1492,21 @@ static int gmres(const orc_grid *g, const csr *A, const ras_t *R, int do_project
 /* Newton with line search (Sec. 4)                                          */
 /* ------------------------------------------------------------------------ */
 
-/* c, c eta and c (4 - 3 eta) must lie in (0, 1) for the logarithms */
-static int in_domain(long N, int nf, const double *X)
+/* c, c eta and c (4 - 3 eta) must lie in (0, 1) for the logarithms; with three
+ * order parameters c and the four site fractions c eta_i (eta_4 = 4 - sum) */
+static int in_domain(const orc_coeffs *k, long N, int nf, const double *X)
 {
+    if (n_eta(k) == 3) {
+        for (long p = 0; p < N; p++) {
+            double c = X[p * nf], e4 = 4.0 - X[p * nf + 1] - X[p * nf + 2] - X[p * nf + 3];
+            if (!(c > 0.0 && c < 1.0 && c * e4 > 0.0 && c * e4 < 1.0)) return 0;
+            for (int j = 1; j <= 3; j++) {
+                double q = c * X[p * nf + j];
+                if (!(q > 0.0 && q < 1.0)) return 0;
+            }
+        }
+        return 1;
+    }
     for (long p = 0; p < N; p++) {
         double c = X[p * nf], e = X[p * nf + 1];
         double pp = c * e, q = c * (4.0 - 3.0 * e);
@@ -1266,7 +1553,7 @@ static int newton(const orc_grid *g, const orc_coeffs *k, const orc_opts *o, dou
         assemble_jacobian(g, k, cbar0, dt, X, X0, mode, &J);
         if (!have_R || !o->reuse) {
             if (have_R) ras_free(&R);
-            if (ras_setup(g, nf, o, &J, &R) != 0) {
+            if (ras_setup(g, nf, ufield(k), o, &J, &R) != 0) {
                 have_R = 1;
                 csr_free(&J);
                 rc = ORC_EPIVOT;
@@ -1285,7 +1572,7 @@ static int newton(const orc_grid *g, const orc_coeffs *k, const orc_opts *o, dou
         int ok = 0;
         while (lam >= o->ls_lambda_min) {
             for (long i = 0; i < n; i++) Xt[i] = X[i] + lam * S[i];
-            if (in_domain(N, nf, Xt)) {
+            if (in_domain(k, N, nf, Xt)) {
                 orc_residual(g, k, cbar0, dt, Xt, X0, mode, Ft);
                 ftn = sqrt(dot(n, Ft, Ft));
                 if (isfinite(ftn) && ftn * ftn <= (1.0 - 2.0 * o->ls_alpha * lam) * fn * fn) {
@@ -1326,7 +1613,7 @@ int orc_equilibrate(const orc_grid *g, const orc_coeffs *k, const orc_opts *o, d
                     orc_step_info *info)
 {
     memset(info, 0, sizeof(*info));
-    if (orc_nfields(g, k) <= 2) return ORC_OK;
+    if (!is_elastic(k)) return ORC_OK;
     long n = grid_N(g) * orc_nfields(g, k);
     double *X0 = (double *)malloc(sizeof(double) * n);
     memcpy(X0, X, sizeof(double) * n);
@@ -1357,7 +1644,7 @@ int orc_precond_apply(const orc_grid *g, const orc_coeffs *k, const orc_opts *o,
     assemble_jacobian(g, k, cbar0, dt, X1, X0, 0, &J);
     ras_t R;
     memset(&R, 0, sizeof(R));
-    int rc = ras_setup(g, orc_nfields(g, k), o, &J, &R);
+    int rc = ras_setup(g, orc_nfields(g, k), ufield(k), o, &J, &R);
     if (rc == 0) ras_apply(g, &R, o->project, r, z);
     ras_free(&R);
     csr_free(&J);
@@ -1373,7 +1660,7 @@ int orc_linear_solve(const orc_grid *g, const orc_coeffs *k, const orc_opts *o, 
     assemble_jacobian(g, k, cbar0, dt, X1, X0, mode, &J);
     ras_t R;
     memset(&R, 0, sizeof(R));
-    int rc = ras_setup(g, orc_nfields(g, k), o, &J, &R);
+    int rc = ras_setup(g, orc_nfields(g, k), ufield(k), o, &J, &R);
     if (rc == 0) gmres(g, &J, &R, o->project, b, x, o->gmres_restart, o->gmres_maxit, tol, its, res);
     ras_free(&R);
     csr_free(&J);

@@ -220,6 +220,8 @@ def make_grid(dim, n, h):
 
 
 def make_coeffs(cf: dict):
+    if int(cf.get("n_eta", 1)) != 1:
+        raise NksError(NKS_EINVAL, "the CUDA path solves the model with one order parameter (n_eta = 1)")
     k = nks_coeffs()
     for name in ("kappa", "gamma_c", "gamma_eta", "theta", "w_psi", "dE0", "U1", "U4", "eps0", "C11", "C12", "C44"):
         setattr(k, name, float(cf[name]))

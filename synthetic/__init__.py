@@ -57,6 +57,18 @@ def initial_fields(dim: int, n, cbar: float, seed: int, c_amp: float = 0.005,
     return c, eta
 
 
+def initial_fields3(dim: int, n, cbar: float, seed: int, c_amp: float = 0.005, eta_mean: float = 0.1,
+                    eta_amp: float = 0.01):
+    """(c, eta[3, N]) for the model with three order parameters (App. A): the
+    reduced model's recipe with each eta_j drawn independently (all c draws,
+    then eta_1, eta_2, eta_3, in x-fastest order)."""
+    N = int(np.prod(n[:dim]))
+    u = uniform01(seed, 4 * N)
+    c = cbar + c_amp * (2.0 * u[:N] - 1.0)
+    eta = eta_mean + eta_amp * (2.0 * u[N:].reshape(3, N) - 1.0)
+    return c, eta
+
+
 def sphere_fields(dim: int, n, h: float, radius: float, inside=(0.238, 0.01), outside=(0.1375, 0.99)):
     """(c, eta) of one spherical particle (Sec. 5.1) as flat float64 arrays in
     x-fastest order: grid point i of an axis sits at x_i = i h, the centre at
