@@ -282,15 +282,19 @@ __global__ void __launch_bounds__(kRedThreads, 4) k_cgs_update(Bat bt, long long
 // CGS pass 2 fused with the dot products of the second pass (FP32 basis):
 // w -= sum_i h_i v_i, and with each updated element still in registers,
 // h2_i = v_i . w (i < NV) and w . w, written to out[0..NV].  One read of V
-// and w instead of two.  One element per thread and iteration keeps the NV
-// basis values of that element in registers; the coefficients are read from
-// shared memory.
+// and w instead of two.  Two elements per thread and iteration (8-byte loads:
+// the NV basis pairs of those elements stay in registers; with one element
+// per load the load instructions, not the bytes, bounded the kernel); the
+// coefficients are read from shared memory.  n is even (the basis stride is a
+// multiple of 4 elements).  Above 27 basis vectors the pairs need more than the
+// 128 registers of two blocks per SM: one block per SM, no spills.
 template <int NV, typename TV>
-__global__ void __launch_bounds__(kRedThreads, 2) k_cgs_update_dots(Bat bt, long long n, const TV *__restrict__ V,
+__global__ void __launch_bounds__(kRedThreads, NV > 27 ? 1 : 2) k_cgs_update_dots(Bat bt, long long n, const TV *__restrict__ V,
                                                                     long long ldv, const double *__restrict__ h,
                                                                     TV *__restrict__ w, double *__restrict__ partials,
                                                                     double *out, unsigned int *ticket)
 {
+    static_assert(sizeof(TV) == sizeof(float), "the fused pass serves the FP32 basis");
     NKS_INST(V = shift(V, io); h = shift(h, io); w = shift(w, io); partials = shift(partials, io);
              out = shift(out, io); ticket = shift(ticket, io);)
     __shared__ TV hs[NV];
@@ -299,18 +303,21 @@ __global__ void __launch_bounds__(kRedThreads, 2) k_cgs_update_dots(Bat bt, long
     TV acc[NV + 1];
 #pragma unroll
     for (int k = 0; k <= NV; k++) acc[k] = (TV)0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        TV va[NV];
-        TV sa = w[i];
+    const long long n2 = n / 2;
+    float2 *w2 = reinterpret_cast<float2 *>(w);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
+        float2 va[NV];
+        float2 sa = w2[i];
 #pragma unroll
         for (int k = 0; k < NV; k++) {
-            va[k] = V[k * ldv + i];
-            sa -= hs[k] * va[k];
+            va[k] = reinterpret_cast<const float2 *>(V + k * ldv)[i];
+            sa.x -= hs[k] * va[k].x;
+            sa.y -= hs[k] * va[k].y;
         }
-        w[i] = sa;
+        w2[i] = sa;
 #pragma unroll
-        for (int k = 0; k < NV; k++) acc[k] += va[k] * sa;
-        acc[NV] += sa * sa;
+        for (int k = 0; k < NV; k++) acc[k] += va[k].x * sa.x + va[k].y * sa.y;
+        acc[NV] += sa.x * sa.x + sa.y * sa.y;
     }
     warp_then_block_store<NV + 1, TV>(acc, partials);
     grid_finalize(partials, NV + 1, out, ticket);
