@@ -107,11 +107,23 @@ __global__ void k_scale_dev(Bat bt, long long n, const TS *__restrict__ src, con
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if constexpr (sizeof(TS) == sizeof(float) && sizeof(TD) == sizeof(float)) {
         // FP32 basis: FP32 arithmetic, the factor converted once per block (a
-        // double-to-float conversion per element would occupy the FP64 pipe)
+        // double-to-float conversion per element would occupy the FP64 pipe);
+        // 16-byte accesses (basis vectors start 16-byte aligned), thread i takes
+        // elements 4i..4i+3, the last thread also the n % 4 tail
         __shared__ float sf;
         if (threadIdx.x == 0) sf = (float)(*s);
         __syncthreads();
-        if (i < n) dst[i] = src[i] * sf;
+        const long long n4 = n / 4;
+        if (i < n4) {
+            float4 v = reinterpret_cast<const float4 *>(src)[i];
+            v.x *= sf;
+            v.y *= sf;
+            v.z *= sf;
+            v.w *= sf;
+            reinterpret_cast<float4 *>(dst)[i] = v;
+        }
+        if (i == n4)
+            for (long long t = 4 * n4; t < n; t++) dst[t] = src[t] * sf;
     } else {
         if (i >= n) return;
         dst[i] = (TD)((double)src[i] * (*s));
@@ -737,7 +749,8 @@ static int gmres_t(Problem *P, Basis<TV> K, int mode, const double *b, double *x
                 P->tick(9);
                 k_arnoldi<<<nbt, 1, 0, st>>>(ba, gm, L, j);
                 P->tock(9);
-                k_scale_dev<TV, TV><<<dim3(nb(n), nbt), kT, 0, st>>>(ba, n, W, gm + L.scal + S_INV, vn);
+                k_scale_dev<TV, TV><<<dim3(nb(sizeof(TV) == sizeof(float) ? n / 4 + 1 : n), nbt), kT, 0, st>>>(
+                    ba, n, W, gm + L.scal + S_INV, vn);
                 P->count(7);  // multidot + update (+ dots) + decide + update + accum + arnoldi + scale
                 if (readback) P->enqueue_readback(gm + L.scal, 8);
             };
