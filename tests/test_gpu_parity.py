@@ -348,6 +348,23 @@ def test_steady_state_and_invalid_inputs(nks):
     assert ei.value.code == nks.NKS_EINVAL
 
 
+def test_size_limits_are_refused_before_any_allocation(nks):
+    """The largest sizes: (2 + d) N at or above 2^31 would overflow the kernels'
+    32-bit field offsets, and n_z x slots above 65535 the 3-D launch grid; both
+    are refused by validation, before any device memory is touched."""
+    cf = S.coefficients()
+    op = S.options(sub=(2, 2, 2), overlap=1)
+    with pytest.raises(nks.NksError) as ei:
+        nks.Batch(3, (800, 800, 800), 0.25, 1, cf, op)  # 5 x 512e6 > 2^31
+    assert ei.value.code == nks.NKS_EINVAL
+    with pytest.raises(nks.NksError) as ei:
+        nks.Batch(3, (16, 16, 4096), 0.25, 16, cf, op)  # n_z x slots = 65536
+    assert ei.value.code == nks.NKS_EINVAL
+    with pytest.raises(nks.NksError) as ei:
+        nks.Batch(2, (64, 2), 0.25, 1, cf, S.options(sub=(2, 1), overlap=1))  # fewer than 3 cells
+    assert ei.value.code == nks.NKS_EINVAL
+
+
 def test_full_size_2d1024_step_checked_by_oracle_residual(nks):
     cfg = S.CONFIGS["2d1024"]
     cf = S.coefficients()
