@@ -303,6 +303,19 @@ int nks_batch_set_state(nks_problem *p, int slot, const void *buf, size_t bytes)
  * Schwarz factors, scratch). */
 size_t nks_device_bytes(const nks_problem *p);
 
+/* Pointwise DVD derivative of the model with three order parameters (App. A:
+ * eta_1..eta_3, eta_4 = 4 - sum; the CUDA path of this model is being built and
+ * problems still refuse it).  Host computation, no device needed.
+ *   x1, x0  HOST, 4 doubles each: (c, eta_1, eta_2, eta_3) at levels n+1 and n;
+ *           c and the four site fractions c eta_i must lie in (0, 1)
+ *   G       HOST, 4 doubles out: G^1 + G^{2,S} = (G_c, G_eta_1, G_eta_2, G_eta_3),
+ *           the product terms split symmetrically with exact polynomial quotients
+ *           and average-vector-field gradients, the logarithms by Psi_S (Sec. 3)
+ *   dG      HOST, 16 doubles out: dG[a * 4 + b] = dG_a / dx1_b
+ * coeffs as for nks_create_problem (the Hooke constants are not used).
+ * Returns NKS_EINVAL for a null pointer or S outside 1..16. */
+int nks_model3_point(const nks_coeffs *coeffs, const double *x1, const double *x0, double *G, double *dG);
+
 /* Testing hook for failure detection (no counterpart in the paper): on != 0
  * makes every Schwarz sweep withhold the first bulk copy of factors in each
  * block, so the block's bounded mbarrier wait expires (about a second), the

@@ -169,6 +169,7 @@ def load():
         "nks_batch_set_state": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_size_t]),
         "nks_device_bytes": (ctypes.c_size_t, [_P]),
         "nks_debug_withhold_copy": (ctypes.c_int, [_P, ctypes.c_int]),
+        "nks_model3_point": (ctypes.c_int, [ctypes.POINTER(nks_coeffs), _D, _D, _D, _D]),
         "nks_server_default_opts": (None, [ctypes.POINTER(nks_server_opts)]),
         "nks_server_create": (ctypes.c_int, [ctypes.POINTER(nks_coeffs), ctypes.POINTER(nks_server_opts), pp]),
         "nks_server_submit": (ctypes.c_int, [_P, ctypes.POINTER(nks_grid), _D, _D, ctypes.c_int,
@@ -197,8 +198,9 @@ def exported_symbols():
             "nks_linear_solve", "nks_eval_energy", "nks_residual_noalloc", "nks_create_batch", "nks_batch_size",
             "nks_batch_load", "nks_batch_unload", "nks_batch_loaded", "nks_batch_step", "nks_batch_energy",
             "nks_batch_mass", "nks_batch_get_fields", "nks_batch_get_state", "nks_batch_set_state",
-            "nks_device_bytes", "nks_debug_withhold_copy", "nks_autotune", "nks_server_default_opts", "nks_server_create",
-            "nks_server_submit", "nks_server_wait", "nks_server_status", "nks_server_destroy"]
+            "nks_device_bytes", "nks_debug_withhold_copy", "nks_model3_point", "nks_autotune",
+            "nks_server_default_opts", "nks_server_create", "nks_server_submit", "nks_server_wait",
+            "nks_server_status", "nks_server_destroy"]
 
 
 def _ptr(a):
@@ -486,6 +488,19 @@ class Batch:
 
     def device_bytes(self):
         return int(load().nks_device_bytes(self._h))
+
+
+def model3_point(coeffs: dict, x1, x0):
+    """Pointwise DVD derivative of the model with three order parameters and its
+    derivative block (nks_model3_point): x1, x0 = (c, eta_1, eta_2, eta_3) at
+    levels n+1 and n; returns (G[4], dG[4, 4]) with dG[a, b] = dG_a/dx1_b."""
+    k = make_coeffs({key: v for key, v in coeffs.items() if key != "n_eta"})
+    x1, x0 = _c64(x1).reshape(4), _c64(x0).reshape(4)
+    G, dG = np.empty(4), np.empty(16)
+    rc = load().nks_model3_point(ctypes.byref(k), _ptr(x1), _ptr(x0), _ptr(G), _ptr(dG))
+    if rc != NKS_OK:
+        raise NksError(rc, "nks_model3_point: invalid arguments")
+    return G, dG.reshape(4, 4)
 
 
 def autotune(dim, n, h, c, eta, coeffs: dict, opts: dict, candidates=None, dt_trial=0.01):

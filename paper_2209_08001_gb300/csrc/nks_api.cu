@@ -9,6 +9,7 @@
 #include <string>
 
 #include "nks_internal.cuh"
+#include "nks_model3.cuh"
 
 namespace nks {
 
@@ -939,6 +940,14 @@ int nks_mass(const nks_problem *H, double *out) { return nks_batch_mass(H, 0, ou
 int nks_get_fields(const nks_problem *H, double *c, double *eta, double *u)
 {
     return nks_batch_get_fields(H, 0, c, eta, u);
+}
+
+int nks_model3_point(const nks_coeffs *coeffs, const double *x1, const double *x0, double *G, double *dG)
+{
+    if (!coeffs || !x1 || !x0 || !G || !dG || coeffs->S < 1 || coeffs->S > 16) return NKS_EINVAL;
+    const DCoef k = derive_coefficients(*coeffs, 1, 0.0);
+    model3_block(k, x1, x0, G, dG);
+    return NKS_OK;
 }
 
 int nks_debug_withhold_copy(nks_problem *H, int on)

@@ -348,6 +348,35 @@ def test_steady_state_and_invalid_inputs(nks):
     assert ei.value.code == nks.NKS_EINVAL
 
 
+def test_three_order_parameter_pointwise_derivative_matches_oracle(nks):
+    """The CUDA path's pointwise DVD derivative of the model with three order
+    parameters (closed polynomial quotients, Simpson's rule, dual-number
+    derivatives; a host function of the library) against the oracle's
+    (Gauss-Legendre quotients), and its derivative block against central
+    differences of the oracle's G."""
+    rng = np.random.default_rng(0)
+    cf = S.coefficients(n_eta=3)
+    O = oracle.Problem(1, (1,), 0.25, cf)
+    pack = lambda x: O.interleave(np.array([x[0]]), np.asarray(x[1:]).reshape(3, 1))
+    for _ in range(25):
+        c0, c1 = 0.12 + 0.1 * rng.random(2)
+        e0 = 0.6 + 0.8 * rng.random(3)
+        e1 = e0 + 0.05 * rng.standard_normal(3)
+        x1, x0 = np.array([c1, *e1]), np.array([c0, *e0])
+        G, dG = nks.model3_point(cf, x1, x0)
+        gc, ge = O.dvd_G(pack(x1), pack(x0), 0.0, 3)
+        Go = np.array([gc[0], *ge[:, 0]])
+        assert np.abs(G - Go).max() <= 1e-13 * np.abs(Go).max()
+        fd = np.zeros((4, 4))
+        for b in range(4):
+            xp, xm = x1.copy(), x1.copy()
+            xp[b] += 1e-6
+            xm[b] -= 1e-6
+            gp, gm = O.dvd_G(pack(xp), pack(x0), 0.0, 3), O.dvd_G(pack(xm), pack(x0), 0.0, 3)
+            fd[:, b] = (np.array([gp[0][0], *gp[1][:, 0]]) - np.array([gm[0][0], *gm[1][:, 0]])) / 2e-6
+        assert np.abs(dG - fd).max() <= 1e-7 * np.abs(fd).max()
+
+
 def test_size_limits_are_refused_before_any_allocation(nks):
     """The largest sizes: (2 + d) N at or above 2^31 would overflow the kernels'
     32-bit field offsets, and n_z x slots above 65535 the 3-D launch grid; both
