@@ -23,6 +23,8 @@ Parity status per function (pins live in ``tests/test_oracle_*.py``):
                                         rate, mass, energy law, symmetries)
   physical coefficient values ......... parity unpinned (the CALPHAD and
                                         elastic constants are not printed)
+  Neumann boundaries (no elasticity) .. pinned (mirrored periodic problem, mass,
+                                        energy law, central differences)
   three order parameters (n_eta = 3) .. pinned (reduction to the pinned reduced
                                         model, four-sublattice symmetry of E_G,
                                         exact discrete chain rule, central
@@ -56,7 +58,7 @@ def build(force: bool = False) -> str:
 
 
 class _Grid(ctypes.Structure):
-    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("h", ctypes.c_double)]
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("h", ctypes.c_double), ("neumann", ctypes.c_int)]
 
 
 class _Coeffs(ctypes.Structure):
@@ -143,13 +145,14 @@ def _ptr(a):
     return a.ctypes.data_as(_D)
 
 
-def make_grid(dim, n, h):
+def make_grid(dim, n, h, neumann=False):
     G = _Grid()
     G.dim = dim
     nn = list(n) + [1] * (3 - len(n))
     for J in range(3):
         G.n[J] = int(nn[J]) if J < dim else 1
     G.h = float(h)
+    G.neumann = 1 if neumann else 0
     return G
 
 
@@ -195,10 +198,15 @@ RAS_VARIANTS = {"left-ras": 0, "as": 1, "right-ras": 2}
 class Problem:
     """Grid + coefficients + options bundle; converts SoA fields <-> interleaved X."""
 
-    def __init__(self, dim, n, h, coeffs: dict, opts: dict | None = None):
+    def __init__(self, dim, n, h, coeffs: dict, opts: dict | None = None, neumann=False):
+        """neumann: homogeneous Neumann boundaries (Eq. boundaryequ) instead of
+        periodic ones, for the model without elasticity (Lscale = 0)."""
         self.dim, self.n, self.h = dim, tuple(n[:dim]), h
-        self.G = make_grid(dim, n, h)
+        self.G = make_grid(dim, n, h, neumann)
         self.K = make_coeffs(coeffs)
+        if neumann and (self.K.C11 != 0.0 or self.K.C12 != 0.0 or self.K.C44 != 0.0):
+            raise ValueError("Neumann boundaries: the model without elasticity only (the traction-free "
+                             "boundary of the displacement is not built)")
         self.opts = opts
         self.O = make_opts(opts) if opts is not None else None
         self.N = int(np.prod(self.n))

@@ -10,7 +10,8 @@
  * never calls it.
  *
  * Conventions (Sec. 3 and Sec. 4 of the paper):
- *   - periodic cell-centred grid, points numbered x-fastest, p = x + nx*(y + ny*z);
+ *   - cell-centred grid, periodic (or homogeneous Neumann: mirror ghost cells),
+ *     points numbered x-fastest, p = x + nx*(y + ny*z);
  *   - unknowns point-interleaved, X = (c_1, eta_1, u_1.., c_2, eta_2, u_2.., ...)
  *     (Sec. 4: "the unknown X is organized by points");
  *   - fields per point: c, eta and, when elasticity is on, the d displacement
@@ -37,6 +38,11 @@ typedef struct {
     int dim;      /* d = 1, 2 or 3                                           */
     int n[3];     /* cells per axis; n[J] = 1 for J >= dim                   */
     double h;     /* mesh size, equal on every axis                          */
+    int neumann;  /* 0: periodic; 1: homogeneous Neumann (Eq. boundaryequ) on the
+                     cell-centred grid of Sec. 3: the ghost cell beyond a boundary
+                     cell mirrors it, so D^+ / D^- across the boundary face vanish
+                     and the flux form has no boundary flux (model without
+                     elasticity; the Python wrapper refuses elasticity with it)   */
 } orc_grid;
 
 typedef struct {
@@ -105,6 +111,13 @@ static long nbr(const orc_grid *g, long p, int J, int s)
     x[1] = (p / n0) % n1;
     x[2] = p / (n0 * n1);
     long nJ = g->n[J];
+    if (g->neumann) {
+        /* mirror ghost: beyond the boundary the neighbour is the cell itself */
+        long y = x[J] + s;
+        if (y < 0 || y >= nJ) return p;
+        x[J] = y;
+        return x[0] + n0 * (x[1] + n1 * x[2]);
+    }
     x[J] = ((x[J] + s) % nJ + nJ) % nJ;
     return x[0] + n0 * (x[1] + n1 * x[2]);
 }
@@ -1158,10 +1171,19 @@ typedef struct {
 /* owned cells [o0, o1) of subdomain s along an axis of n cells split in nsub
  * pieces; the extended range adds delta layers per side (periodic), or is the
  * whole axis when that would cover it. */
-static void axis_range(int n, int nsub, int s, int delta, long *start, long *len, long *o0, long *o1)
+static void axis_range(int n, int nsub, int s, int delta, int clip, long *start, long *len, long *o0, long *o1)
 {
     *o0 = (long)s * n / nsub;
     *o1 = (long)(s + 1) * n / nsub;
+    if (clip) {
+        /* Neumann: boxes stop at the boundary (no wrap) */
+        long a = *o0 - delta, b = *o1 + delta;
+        if (a < 0) a = 0;
+        if (b > n) b = n;
+        *start = a;
+        *len = b - a;
+        return;
+    }
     if (*o1 - *o0 + 2 * delta >= n) {
         *start = 0;
         *len = n;
@@ -1219,7 +1241,8 @@ static int ras_setup(const orc_grid *g, int nf, int ku, const orc_opts *o, const
                 int sidx[3] = {s0, s1, s2};
                 long st[3], ln[3], o0[3], o1[3];
                 for (int a = 0; a < 3; a++) {
-                    if (a < d) axis_range(g->n[a], sub[a], sidx[a], o->overlap, &st[a], &ln[a], &o0[a], &o1[a]);
+                    if (a < d)
+                        axis_range(g->n[a], sub[a], sidx[a], o->overlap, g->neumann, &st[a], &ln[a], &o0[a], &o1[a]);
                     else {
                         st[a] = 0;
                         ln[a] = 1;

@@ -1,0 +1,105 @@
+"""Pins of the oracle's homogeneous Neumann boundaries (Eq. boundaryequ; row f3,
+model without elasticity).
+
+On the cell-centred grid of Sec. 3 the Neumann conditions are mirror ghost
+cells, so the fixed standard is the periodic problem on the mirrored domain:
+a state on n cells, reflected across each boundary face into a periodic grid
+of 2n cells, stays mirror-symmetric, and its first n cells are the Neumann
+solution.  Checked for energies (the mirrored energy is 2^d times the Neumann
+one) and for whole NKS steps in 1-D and 2-D, beside mass conservation, the
+energy law and the Jacobian against central differences.  No CUDA path yet.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic as S
+
+
+def _cf():
+    return S.coefficients(Lscale=0.0)
+
+
+def _mirror(f, n):
+    """Reflect a field on n cells (x-fastest) across every boundary face into 2n cells."""
+    a = np.asarray(f).reshape(tuple(reversed(n)))
+    for ax in range(a.ndim):
+        a = np.concatenate([a, np.flip(a, axis=ax)], axis=ax)
+    return a.reshape(-1)
+
+
+def _restrict(f, n):
+    """The first n cells of every axis of a mirrored field on 2n cells."""
+    big = tuple(reversed([2 * m for m in n]))
+    a = np.asarray(f).reshape(big)
+    return a[tuple(slice(0, m) for m in reversed(n))].reshape(-1)
+
+
+@pytest.mark.parametrize("dim,n", [(1, (14,)), (2, (9, 7))])
+def test_energy_of_the_mirrored_state(dim, n):
+    c, e = S.initial_fields(dim, n, 0.18, 3, c_amp=0.02, eta_amp=0.05)
+    On = oracle.Problem(dim, n, 0.25, _cf(), neumann=True)
+    Op = oracle.Problem(dim, tuple(2 * m for m in n), 0.25, _cf())
+    En, pn = On.energy(On.interleave(c, e), 0.0, parts=True)
+    Ep, pp = Op.energy(Op.interleave(_mirror(c, n), _mirror(e, n)), 0.0, parts=True)
+    assert np.allclose(pp, 2 ** dim * pn, rtol=1e-12, atol=1e-12 * abs(En))
+    # the Neumann gradient energy has no boundary-face terms: it differs from the
+    # periodic energy of the same (unmirrored) state
+    Oq = oracle.Problem(dim, n, 0.25, _cf())
+    _, pq = Oq.energy(Oq.interleave(c, e), 0.0, parts=True)
+    assert abs(pq[3] - pn[3]) > 1e-6 * abs(pn[3])
+
+
+@pytest.mark.parametrize("dim,n,sub", [(1, (16,), (2,)), (2, (10, 8), (2, 2))])
+def test_steps_equal_the_mirrored_periodic_steps(dim, n, sub):
+    op = S.options(sub=sub, overlap=1, newton_rtol=1e-12)
+    c, e = S.initial_fields(dim, n, 0.18, 5, c_amp=0.02, eta_amp=0.05)
+    On = oracle.Problem(dim, n, 0.25, _cf(), op, neumann=True)
+    n2 = tuple(2 * m for m in n)
+    Op = oracle.Problem(dim, n2, 0.25, _cf(), dict(op, sub=tuple(2 * s for s in sub)))
+    rcn, Xn, infn, en0 = On.simulate(c, e, 3, dt_replay=[0.01, 0.02, 0.04])
+    rcp, Xp, infp, ep0 = Op.simulate(_mirror(c, n), _mirror(e, n), 3, dt_replay=[0.01, 0.02, 0.04])
+    assert rcn == 0 and rcp == 0
+    cn, en, _ = On.split(Xn)
+    cp, ep, _ = Op.split(Xp)
+    assert np.linalg.norm(_restrict(cp, n) - cn) <= 1e-9 * np.linalg.norm(cn)
+    assert np.linalg.norm(_restrict(ep, n) - en) <= 1e-9 * np.linalg.norm(en)
+    for a, b in zip(infn, infp):
+        assert b["energy"] == pytest.approx(2 ** dim * a["energy"], rel=1e-10)
+
+
+def test_mass_and_energy_law_with_neumann_boundaries():
+    dim, n = 2, (12, 10)
+    op = S.options(sub=(2, 2), overlap=1, dt_mode="energy")
+    O = oracle.Problem(dim, n, 0.25, _cf(), op, neumann=True)
+    c, e = S.initial_fields(dim, n, 0.18, 7, c_amp=0.02, eta_amp=0.05)
+    rc, X, infos, e0 = O.simulate(c, e, 4)
+    assert rc == 0
+    m0 = c.sum() * 0.25 ** dim
+    E = [e0] + [i["energy"] for i in infos]
+    for i in infos:
+        assert abs(i["mass"] - m0) <= 1e-12 * m0
+    for a, b in zip(E[:-1], E[1:]):
+        assert b <= a + 1e-12 * abs(a)
+
+
+def test_jacobian_matches_central_differences_with_neumann_boundaries():
+    dim, n, dt = 2, (5, 4), 0.05
+    O = oracle.Problem(dim, n, 0.25, _cf(), neumann=True)
+    c0, e0 = S.initial_fields(dim, n, 0.18, 8, c_amp=0.03, eta_amp=0.05)
+    c1, e1 = S.initial_fields(dim, n, 0.18, 9, c_amp=0.03, eta_amp=0.05)
+    X0, X1 = O.interleave(c0, e0), O.interleave(c1, e1)
+    cb = float(c0.mean())
+    J = O.jacobian_scipy(X1, X0, cb, dt).toarray()
+    fd = np.zeros_like(J)
+    for i in range(X1.size):
+        xp, xm = X1.copy(), X1.copy()
+        xp[i] += 1e-6
+        xm[i] -= 1e-6
+        fd[:, i] = (O.residual(xp, X0, cb, dt) - O.residual(xm, X0, cb, dt)) / 2e-6
+    assert np.abs(J - fd).max() <= 1e-6 * np.abs(J).max()
+
+
+def test_elasticity_with_neumann_boundaries_is_refused():
+    with pytest.raises(ValueError):
+        oracle.Problem(2, (8, 8), 0.25, S.coefficients(), neumann=True)
