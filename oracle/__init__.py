@@ -23,8 +23,9 @@ Parity status per function (pins live in ``tests/test_oracle_*.py``):
                                         rate, mass, energy law, symmetries)
   physical coefficient values ......... parity unpinned (the CALPHAD and
                                         elastic constants are not printed)
-  Neumann boundaries (no elasticity) .. pinned (mirrored periodic problem, mass,
-                                        energy law, central differences)
+  Neumann boundaries .................. pinned (mirrored periodic problem without
+                                        elasticity; -F_u = dE_3/du; mass, energy
+                                        law, central differences)
   three order parameters (n_eta = 3) .. pinned (reduction to the pinned reduced
                                         model, four-sublattice symmetry of E_G,
                                         exact discrete chain rule, central
@@ -200,13 +201,11 @@ class Problem:
 
     def __init__(self, dim, n, h, coeffs: dict, opts: dict | None = None, neumann=False):
         """neumann: homogeneous Neumann boundaries (Eq. boundaryequ) instead of
-        periodic ones, for the model without elasticity (Lscale = 0)."""
+        periodic ones: mirror ghost cells for c and eta, traction-free displacement
+        rows as the exact variation of the discrete elastic energy."""
         self.dim, self.n, self.h = dim, tuple(n[:dim]), h
         self.G = make_grid(dim, n, h, neumann)
         self.K = make_coeffs(coeffs)
-        if neumann and (self.K.C11 != 0.0 or self.K.C12 != 0.0 or self.K.C44 != 0.0):
-            raise ValueError("Neumann boundaries: the model without elasticity only (the traction-free "
-                             "boundary of the displacement is not built)")
         self.opts = opts
         self.O = make_opts(opts) if opts is not None else None
         self.N = int(np.prod(self.n))

@@ -41,8 +41,9 @@ typedef struct {
     int neumann;  /* 0: periodic; 1: homogeneous Neumann (Eq. boundaryequ) on the
                      cell-centred grid of Sec. 3: the ghost cell beyond a boundary
                      cell mirrors it, so D^+ / D^- across the boundary face vanish
-                     and the flux form has no boundary flux (model without
-                     elasticity; the Python wrapper refuses elasticity with it)   */
+                     and the flux form has no boundary flux; the displacement rows
+                     are the exact variation of the discrete elastic energy (its
+                     natural boundary condition is the traction-free one)        */
 } orc_grid;
 
 typedef struct {
@@ -718,7 +719,34 @@ void orc_residual(const orc_grid *g, const orc_coeffs *k, double cbar0, double d
         } else {
             for (int f = 0; f < ku; f++) F[p * nf + f] = 0.0;
         }
-        if (is_elastic(k)) {
+        if (is_elastic(k) && g->neumann) {
+            /* traction-free boundaries: F_u = -dE_3/du of the discrete elastic energy,
+             * the adjoint of the centred differences with mirror ghosts:
+             *   F_uI(p) = -sum_q sum_J sigma_IJ(q) w_J(q, p),
+             *   w_J(q, p) = ([p == nbr(q, J, +1)] - [p == nbr(q, J, -1)]) / (2h),
+             * over the cells q whose strain reads u(p) (p and its axis neighbours);
+             * on a periodic grid this is the divergence form below */
+            for (int I = 0; I < d; I++) F[p * nf + ku + I] = 0.0;
+            long qs[7];
+            int nq = 0;
+            qs[nq++] = p;
+            for (int J = 0; J < d; J++) {
+                long a = nbr(g, p, J, +1), b = nbr(g, p, J, -1);
+                if (a != p) qs[nq++] = a;
+                if (b != p) qs[nq++] = b;
+            }
+            for (int t = 0; t < nq; t++) {
+                long q = qs[t];
+                double e[3][3], sg[3][3];
+                el_strain(g, k, nf, cbar0, X1, q, e);
+                hooke(k, d, e, sg);
+                for (int J = 0; J < d; J++) {
+                    double w = ((p == nbr(g, q, J, +1)) - (p == nbr(g, q, J, -1))) / (2.0 * h);
+                    if (w == 0.0) continue;
+                    for (int I = 0; I < d; I++) F[p * nf + ku + I] -= sg[I][J] * w;
+                }
+            }
+        } else if (is_elastic(k)) {
             for (int I = 0; I < d; I++) {
                 double div = 0.0;
                 for (int J = 0; J < d; J++) {
@@ -974,6 +1002,24 @@ static void assemble_jacobian(const orc_grid *g, const orc_coeffs *k, double cba
                 } else {
                     ra_add(row, p * nf + f, 1.0);
                 }
+            } else if (g->neumann) {
+                /* traction-free: the adjoint form of orc_residual */
+                int I = f - ku;
+                long qs[7];
+                int nq = 0;
+                qs[nq++] = p;
+                for (int J = 0; J < d; J++) {
+                    long a = nbr(g, p, J, +1), b = nbr(g, p, J, -1);
+                    if (a != p) qs[nq++] = a;
+                    if (b != p) qs[nq++] = b;
+                }
+                for (int q = 0; q < nq; q++)
+                    for (int J = 0; J < d; J++) {
+                        double w = ((p == nbr(g, qs[q], J, +1)) - (p == nbr(g, qs[q], J, -1))) / (2.0 * h);
+                        if (w == 0.0) continue;
+                        sig_row(&cx, qs[q], I, J, t);
+                        ra_axpy(row, -w, t);
+                    }
             } else {
                 int I = f - ku;
                 for (int J = 0; J < d; J++) {
@@ -1337,9 +1383,9 @@ static void project(const orc_grid *g, int nf, int ku, double *z)
     for (long p = 0; p < N; p++) z[p * nf] -= mean;
     if (ku >= nf) return;
     int d = g->dim;
-    int even_mask = 0;
+    int even_mask = 0; /* Neumann (mirror ghosts): translations only */
     for (int J = 0; J < d; J++)
-        if (g->n[J] % 2 == 0) even_mask |= 1 << J;
+        if (g->n[J] % 2 == 0 && !g->neumann) even_mask |= 1 << J;
     for (int I = 0; I < d; I++) {
         for (int m = 0; m < (1 << d); m++) {
             if ((m & ~even_mask) != 0) continue;

@@ -1,13 +1,15 @@
-"""Pins of the oracle's homogeneous Neumann boundaries (Eq. boundaryequ; row f3,
-model without elasticity).
+"""Pins of the oracle's homogeneous Neumann boundaries (Eq. boundaryequ; row f3).
 
 On the cell-centred grid of Sec. 3 the Neumann conditions are mirror ghost
 cells, so the fixed standard is the periodic problem on the mirrored domain:
 a state on n cells, reflected across each boundary face into a periodic grid
 of 2n cells, stays mirror-symmetric, and its first n cells are the Neumann
 solution.  Checked for energies (the mirrored energy is 2^d times the Neumann
-one) and for whole NKS steps in 1-D and 2-D, beside mass conservation, the
-energy law and the Jacobian against central differences.  No CUDA path yet.
+one) and for whole NKS steps in 1-D and 2-D without elasticity.  The traction-
+free displacement rows are the exact variation of the discrete elastic energy:
+-F_u equals its finite differences (on periodic grids too, where it is the
+divergence form).  Mass conservation, the energy law and the Jacobian against
+central differences hold with elasticity.  No CUDA path yet.
 """
 import numpy as np
 import pytest
@@ -100,6 +102,58 @@ def test_jacobian_matches_central_differences_with_neumann_boundaries():
     assert np.abs(J - fd).max() <= 1e-6 * np.abs(J).max()
 
 
-def test_elasticity_with_neumann_boundaries_is_refused():
-    with pytest.raises(ValueError):
-        oracle.Problem(2, (8, 8), 0.25, S.coefficients(), neumann=True)
+@pytest.mark.parametrize("neumann", [True, False])
+def test_displacement_rows_are_the_variation_of_the_elastic_energy(neumann):
+    """F_u = -dE_3/du (per unit volume): the traction-free rows under Neumann, the
+    divergence form on periodic grids."""
+    dim, n, h = 2, (6, 5), 0.25
+    O = oracle.Problem(dim, n, h, S.coefficients(), neumann=neumann)
+    c, e = S.initial_fields(dim, n, 0.18, 12, c_amp=0.03, eta_amp=0.05)
+    u = 0.01 * (2.0 * S.uniform01(13, dim * c.size).reshape(dim, c.size) - 1.0)
+    cb = float(c.mean())
+    X = O.interleave(c, e, u)
+    F = O.residual(X, X, cb, 1.0, mode=1)
+    Fu = O.split(F)[2]
+    grad = np.zeros_like(u)
+    for I in range(dim):
+        for p in range(c.size):
+            up, um = u.copy(), u.copy()
+            up[I, p] += 1e-6
+            um[I, p] -= 1e-6
+            ep = O.energy(O.interleave(c, e, up), cb, parts=True)[1][2]
+            em = O.energy(O.interleave(c, e, um), cb, parts=True)[1][2]
+            grad[I, p] = (ep - em) / 2e-6 / h ** dim
+    assert np.abs(Fu + grad).max() <= 1e-6 * np.abs(grad).max()
+
+
+def test_elastic_steps_with_neumann_boundaries():
+    dim, n = 2, (12, 10)
+    op = S.options(sub=(2, 2), overlap=1, dt_mode="energy")
+    O = oracle.Problem(dim, n, 0.25, S.coefficients(), op, neumann=True)
+    c, e = S.initial_fields(dim, n, 0.18, 14, c_amp=0.02, eta_amp=0.05)
+    rc, X, infos, e0 = O.simulate(c, e, 3)
+    assert rc == 0
+    m0 = c.sum() * 0.25 ** dim
+    E = [e0] + [i["energy"] for i in infos]
+    for i in infos:
+        assert abs(i["mass"] - m0) <= 1e-12 * m0
+    for a, b in zip(E[:-1], E[1:]):
+        assert b <= a + 1e-12 * abs(a)
+    dt = 0.05
+    c0, e0_ = S.initial_fields(dim, (5, 4), 0.18, 15, c_amp=0.03, eta_amp=0.05)
+    Os = oracle.Problem(dim, (5, 4), 0.25, S.coefficients(), neumann=True)
+    u0 = 0.01 * (2.0 * S.uniform01(16, dim * c0.size).reshape(dim, c0.size) - 1.0)
+    X0 = Os.interleave(c0, e0_, u0)
+    X1 = X0 * (1.0 + 0.01 * np.sin(np.arange(X0.size)))
+    cb = float(c0.mean())
+    for mode in (0, 1):
+        J = Os.jacobian_scipy(X1, X0, cb, dt, mode).toarray()
+        fd = np.zeros_like(J)
+        for i in range(X1.size):
+            xp, xm = X1.copy(), X1.copy()
+            xp[i] += 1e-6
+            xm[i] -= 1e-6
+            fd[:, i] = (Os.residual(xp, X0, cb, dt, mode) - Os.residual(xm, X0, cb, dt, mode)) / 2e-6
+        rows = np.arange(X1.size).reshape(-1, Os.nf)
+        check = rows.ravel() if mode == 0 else rows[:, Os.ku:].ravel()
+        assert np.abs(J[check] - fd[check]).max() <= 1e-6 * np.abs(J).max(), mode
