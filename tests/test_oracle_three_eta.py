@@ -208,3 +208,27 @@ def test_permuting_the_order_parameters_permutes_the_step():
     assert np.linalg.norm(cB - cA) <= 1e-9 * np.linalg.norm(cA)
     assert np.linalg.norm(eB - eA[perm]) <= 1e-9 * np.linalg.norm(eA)
     assert np.linalg.norm(uB - uA) <= 1e-8 * np.linalg.norm(uA)
+
+
+def test_three_order_parameters_with_neumann_boundaries():
+    """The two next rows together: three order parameters on a grid with
+    homogeneous Neumann boundaries conserve mass, obey the energy law, and keep
+    the permutation symmetry of the order parameters."""
+    dim, n, h = 2, (10, 9), 0.25
+    op = S.options(sub=(2, 2), overlap=1, dt_mode="energy", newton_rtol=1e-12)
+    O3 = oracle.Problem(dim, n, h, _cf(3), op, neumann=True)
+    c, eta, _ = _state3(dim, n, 61)
+    rc, X, infos, e0 = O3.simulate(c, eta, 3)
+    assert rc == 0
+    m0 = c.sum() * h ** dim
+    E = [e0] + [i["energy"] for i in infos]
+    for i in infos:
+        assert abs(i["mass"] - m0) <= 1e-12 * m0
+    for a, b in zip(E[:-1], E[1:]):
+        assert b <= a + 1e-12 * abs(a)
+    perm = [1, 2, 0]
+    rcp, Xp, _, _ = O3.simulate(c, eta[perm], 3)
+    assert rcp == 0
+    _, eA, _ = O3.split(X)
+    _, eB, _ = O3.split(Xp)
+    assert np.linalg.norm(eB - eA[perm]) <= 1e-8 * np.linalg.norm(eA)
