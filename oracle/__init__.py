@@ -8,7 +8,10 @@ package.  It shares no code with the CUDA path (``paper_2209_08001_gb300``);
 neither imports the other.  The arithmetic lives in ``nks_oracle.c`` (plain
 serial C, compiled with ``-ffp-contract=off``); this module only builds it,
 marshals arrays and converts between the product's field-by-field layout and
-the paper's point-interleaved unknown vector (Sec. 4).
+the paper's point-interleaved unknown vector (Sec. 4).  Loops over independent
+points, rows, subdomains and vector entries run on all host threads (OpenMP,
+``OMP_NUM_THREADS`` to limit them); every sum is taken in a fixed block order,
+so results do not depend on the thread count.
 
 Parity status per function (pins live in ``tests/test_oracle_*.py``):
   energy / mass / G^1 / G^2 / G^4 .... pinned (App. A construction, DVD identity,
@@ -49,10 +52,10 @@ ORC_OK, ORC_EINVAL, ORC_EDOMAIN, ORC_EDIVERGED, ORC_EPIVOT = 0, 1, 2, 4, 7
 
 
 def build(force: bool = False) -> str:
-    """Compile nks_oracle.c into liboracle.so (plain gcc, no FMA contraction)."""
+    """Compile nks_oracle.c into liboracle.so (plain gcc, OpenMP, no FMA contraction)."""
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared",
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
                                _SRC, "-o", tmp, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -109,6 +112,7 @@ def lib():
         si = ctypes.POINTER(StepInfo)
         sig = {
             "orc_nfields": (ctypes.c_int, [g, k]),
+            "orc_num_threads": (ctypes.c_int, []),
             "orc_energy": (ctypes.c_double, [g, k, ctypes.c_double, _D, _D]),
             "orc_mass": (ctypes.c_double, [g, k, _D]),
             "orc_psi_quot": (ctypes.c_double, [ctypes.c_double, ctypes.c_double, ctypes.c_int]),
@@ -319,6 +323,11 @@ class Problem:
         rc = lib().orc_simulate(*self._g(), ctypes.byref(self.O), _ptr(X), nsteps,
                                 _ptr(rp) if rp is not None else None, infos, ctypes.byref(e0))
         return rc, X, [infos[i].as_dict() for i in range(nsteps)], e0.value
+
+
+def num_threads() -> int:
+    """Host threads the oracle's parallel loops use."""
+    return int(lib().orc_num_threads())
 
 
 def psi_quot(y1, y2, S):

@@ -17,7 +17,13 @@
  *   - fields per point: c, eta and, when elasticity is on, the d displacement
  *     components u_1..u_d; with three order parameters (App. A, n_eta = 3)
  *     c, eta_1, eta_2, eta_3, then u_1..u_d;
- *   - every sum is a serial loop in point order; nothing is blocked or fused.
+ *   - loops over independent points, rows, subdomains or vector entries are
+ *     shared among the host's threads (OpenMP); each thread computes whole
+ *     points or rows exactly as the serial loop would;
+ *   - every sum over points or vector entries is taken in fixed blocks of
+ *     ORC_SUM_BLOCK consecutive terms, each block added in index order, then the
+ *     block sums added in block order, so every result is the same for any
+ *     number of threads; nothing else is blocked or fused.
  *
  * The readings of passages the paper leaves open (tolerances, line search,
  * projection of the Krylov corrections, the elastic gauge, ...) are stated at
@@ -28,6 +34,9 @@
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #undef I /* complex.h's imaginary unit: _Complex_I is used by name, I stays an axis index */
 
 /* ------------------------------------------------------------------------ */
@@ -130,6 +139,49 @@ static void coords(const orc_grid *g, long p, long x[3])
     x[2] = p / ((long)g->n[0] * g->n[1]);
 }
 
+/* host threads the parallel loops use (1 without OpenMP) */
+int orc_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sums in a fixed order (independent of the thread count)                   */
+/* ------------------------------------------------------------------------ */
+
+#define ORC_SUM_BLOCK 4096
+
+static long n_blocks(long n) { return (n + ORC_SUM_BLOCK - 1) / ORC_SUM_BLOCK; }
+
+/* sum of the block sums part[0..nb-1], in block order */
+static double sum_parts(const double *part, long nb)
+{
+    double s = 0.0;
+    for (long q = 0; q < nb; q++) s += part[q];
+    return s;
+}
+
+/* sum_i a[i * stride] */
+static double strided_sum(long n, const double *a, long stride)
+{
+    long nb = n_blocks(n);
+    double *part = (double *)malloc(sizeof(double) * (nb > 0 ? nb : 1));
+#pragma omp parallel for schedule(static)
+    for (long q = 0; q < nb; q++) {
+        long i1 = (q + 1) * ORC_SUM_BLOCK < n ? (q + 1) * ORC_SUM_BLOCK : n;
+        double s = 0.0;
+        for (long i = q * ORC_SUM_BLOCK; i < i1; i++) s += a[i * stride];
+        part[q] = s;
+    }
+    double s = sum_parts(part, nb);
+    free(part);
+    return s;
+}
+
 static int is_elastic(const orc_coeffs *k) { return k->C11 != 0.0 || k->C12 != 0.0 || k->C44 != 0.0; }
 static int n_eta(const orc_coeffs *k) { return k->n_eta == 3 ? 3 : 1; }
 /* per point: c, the order parameters, then (with elasticity) u_1..u_d from field ufield(k) */
@@ -228,52 +280,69 @@ static double E3_density(const orc_coeffs *k, int d, double e[3][3])
  * parts (optional) receives the four sums times h^d. */
 static void E12_density3(const orc_coeffs *k, double c, const double e[3], double *e1, double *e2);
 
-double orc_energy(const orc_grid *g, const orc_coeffs *k, double cbar0, const double *X, double *parts)
+/* the four energy densities e1..e4 of point p */
+static void energy_point(const orc_grid *g, const orc_coeffs *k, double cbar0, const double *X, long p, double e4[4])
 {
     int nf = orc_nfields(g, k), d = g->dim;
-    long N = grid_N(g);
     double h = g->h;
-    double s1 = 0, s2 = 0, s3 = 0, s4 = 0;
-    for (long p = 0; p < N; p++) {
-        if (n_eta(k) == 3) {
-            /* three order parameters: E_1, E_2 of App. A, E_4 with gamma_eta/2 per eta_j */
-            double c = X[p * nf], e[3] = {X[p * nf + 1], X[p * nf + 2], X[p * nf + 3]}, a, b;
-            E12_density3(k, c, e, &a, &b);
-            s1 += a;
-            s2 += b;
-            if (is_elastic(k)) {
-                double ee[3][3];
-                el_strain(g, k, nf, cbar0, X, p, ee);
-                s3 += E3_density(k, d, ee);
-            }
-            for (int f = 0; f < 4; f++) {
-                double gs = 0.0, v0 = X[p * nf + f];
-                for (int J = 0; J < d; J++) {
-                    double dp = (X[nbr(g, p, J, +1) * nf + f] - v0) / h, dm = (v0 - X[nbr(g, p, J, -1) * nf + f]) / h;
-                    gs += 0.5 * (dp * dp + dm * dm);
-                }
-                s4 += 0.5 * (f == 0 ? k->gamma_c : k->gamma_eta) * gs;
-            }
-            continue;
-        }
-        double c = X[p * nf], eta = X[p * nf + 1];
-        s1 += Phi_poly(k, c, 1.0 - eta);
-        s2 += E2_density(k, c, eta);
+    e4[0] = e4[1] = e4[2] = e4[3] = 0.0;
+    if (n_eta(k) == 3) {
+        /* three order parameters: E_1, E_2 of App. A, E_4 with gamma_eta/2 per eta_j */
+        double c = X[p * nf], e[3] = {X[p * nf + 1], X[p * nf + 2], X[p * nf + 3]}, a, b;
+        E12_density3(k, c, e, &a, &b);
+        e4[0] = a;
+        e4[1] = b;
         if (is_elastic(k)) {
-            double e[3][3];
-            el_strain(g, k, nf, cbar0, X, p, e);
-            s3 += E3_density(k, d, e);
+            double ee[3][3];
+            el_strain(g, k, nf, cbar0, X, p, ee);
+            e4[2] = E3_density(k, d, ee);
         }
-        double gc = 0.0, ge = 0.0;
-        for (int J = 0; J < d; J++) {
-            long pp = nbr(g, p, J, +1), pm = nbr(g, p, J, -1);
-            double dpc = (X[pp * nf] - c) / h, dmc = (c - X[pm * nf]) / h;
-            double dpe = (X[pp * nf + 1] - eta) / h, dme = (eta - X[pm * nf + 1]) / h;
-            gc += 0.5 * (dpc * dpc + dmc * dmc);
-            ge += 0.5 * (dpe * dpe + dme * dme);
+        for (int f = 0; f < 4; f++) {
+            double gs = 0.0, v0 = X[p * nf + f];
+            for (int J = 0; J < d; J++) {
+                double dp = (X[nbr(g, p, J, +1) * nf + f] - v0) / h, dm = (v0 - X[nbr(g, p, J, -1) * nf + f]) / h;
+                gs += 0.5 * (dp * dp + dm * dm);
+            }
+            e4[3] += 0.5 * (f == 0 ? k->gamma_c : k->gamma_eta) * gs;
         }
-        s4 += 0.5 * k->gamma_c * gc + 1.5 * k->gamma_eta * ge;
+        return;
     }
+    double c = X[p * nf], eta = X[p * nf + 1];
+    e4[0] = Phi_poly(k, c, 1.0 - eta);
+    e4[1] = E2_density(k, c, eta);
+    if (is_elastic(k)) {
+        double e[3][3];
+        el_strain(g, k, nf, cbar0, X, p, e);
+        e4[2] = E3_density(k, d, e);
+    }
+    double gc = 0.0, ge = 0.0;
+    for (int J = 0; J < d; J++) {
+        long pp = nbr(g, p, J, +1), pm = nbr(g, p, J, -1);
+        double dpc = (X[pp * nf] - c) / h, dmc = (c - X[pm * nf]) / h;
+        double dpe = (X[pp * nf + 1] - eta) / h, dme = (eta - X[pm * nf + 1]) / h;
+        gc += 0.5 * (dpc * dpc + dmc * dmc);
+        ge += 0.5 * (dpe * dpe + dme * dme);
+    }
+    e4[3] = 0.5 * k->gamma_c * gc + 1.5 * k->gamma_eta * ge;
+}
+
+double orc_energy(const orc_grid *g, const orc_coeffs *k, double cbar0, const double *X, double *parts)
+{
+    long N = grid_N(g), nb = n_blocks(N);
+    double *part = (double *)malloc(sizeof(double) * 4 * (nb > 0 ? nb : 1));
+#pragma omp parallel for schedule(static)
+    for (long q = 0; q < nb; q++) {
+        long p1 = (q + 1) * ORC_SUM_BLOCK < N ? (q + 1) * ORC_SUM_BLOCK : N;
+        double a[4] = {0.0, 0.0, 0.0, 0.0}, e4[4];
+        for (long p = q * ORC_SUM_BLOCK; p < p1; p++) {
+            energy_point(g, k, cbar0, X, p, e4);
+            for (int t = 0; t < 4; t++) a[t] += e4[t];
+        }
+        for (int t = 0; t < 4; t++) part[t * nb + q] = a[t];
+    }
+    double s1 = sum_parts(part, nb), s2 = sum_parts(part + nb, nb), s3 = sum_parts(part + 2 * nb, nb),
+           s4 = sum_parts(part + 3 * nb, nb);
+    free(part);
     double v = cell_volume(g);
     if (parts) {
         parts[0] = s1 * v;
@@ -288,10 +357,7 @@ double orc_energy(const orc_grid *g, const orc_coeffs *k, double cbar0, const do
 double orc_mass(const orc_grid *g, const orc_coeffs *k, const double *X)
 {
     int nf = orc_nfields(g, k);
-    long N = grid_N(g);
-    double s = 0.0;
-    for (long p = 0; p < N; p++) s += X[p * nf];
-    return s * cell_volume(g);
+    return strided_sum(grid_N(g), X, nf) * cell_volume(g);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -600,6 +666,7 @@ void orc_dvd_G(const orc_grid *g, const orc_coeffs *k, double cbar0, const doubl
     double h = g->h;
     if (n_eta(k) == 3) {
         /* Ge holds G_eta_j at Ge[j N + p] */
+#pragma omp parallel for schedule(static)
         for (long p = 0; p < N; p++) {
             cplx c1 = X1[p * nf], c0 = X0[p * nf], e1[3], e0[3], G[4];
             for (int j = 0; j < 3; j++) {
@@ -635,6 +702,7 @@ void orc_dvd_G(const orc_grid *g, const orc_coeffs *k, double cbar0, const doubl
         }
         return;
     }
+#pragma omp parallel for schedule(static)
     for (long p = 0; p < N; p++) {
         double c1 = X1[p * nf], e1 = X1[p * nf + 1], c0 = X0[p * nf], e0 = X0[p * nf + 1];
         double gc = 0.0, ge = 0.0, a, b;
@@ -705,6 +773,7 @@ void orc_residual(const orc_grid *g, const orc_coeffs *k, double cbar0, double d
     double keta = ne == 3 ? kEtaKinetic3 : 1.0;
     double *Gc = (double *)malloc(sizeof(double) * N), *Ge = (double *)malloc(sizeof(double) * N * ne);
     if (mode == 0) orc_dvd_G(g, k, cbar0, X1, X0, 15, Gc, Ge);
+#pragma omp parallel for schedule(static)
     for (long p = 0; p < N; p++) {
         if (mode == 0) {
             double flux = 0.0;
@@ -947,6 +1016,7 @@ static void assemble_jacobian(const orc_grid *g, const orc_coeffs *k, double cba
     double keta = ne == 3 ? kEtaKinetic3 : 1.0;
     jac_ctx cx = {g, k, nf, d, ne, ku, cbar0, dt, X1, X0, NULL};
     cx.part = (double *)malloc(sizeof(double) * P * N);
+#pragma omp parallel for schedule(static)
     for (long p = 0; p < N; p++) {
         if (ne == 3) {
             double e1[3] = {X1[p * nf + 1], X1[p * nf + 2], X1[p * nf + 3]};
@@ -957,99 +1027,131 @@ static void assemble_jacobian(const orc_grid *g, const orc_coeffs *k, double cba
         }
     }
 
-    long cap = N * nf * 40 + 16;
+    /* rows of consecutive chunks of points are assembled independently (one
+     * thread per chunk) into chunk buffers, then laid out in row order */
+    const long CH = 1024;
+    long nch = (N + CH - 1) / CH;
+    long **cci = (long **)calloc(nch, sizeof(long *));
+    double **cv = (double **)calloc(nch, sizeof(double *));
+    long *cnnz = (long *)calloc(nch, sizeof(long));
     A->n = N * nf;
     A->rp = (long *)malloc(sizeof(long) * (A->n + 1));
-    A->ci = (long *)malloc(sizeof(long) * cap);
-    A->v = (double *)malloc(sizeof(double) * cap);
-    long nnz = 0;
-    rowacc *row = (rowacc *)malloc(sizeof(rowacc)), *t = (rowacc *)malloc(sizeof(rowacc));
-    A->rp[0] = 0;
-    for (long p = 0; p < N; p++) {
-        for (int f = 0; f < nf; f++) {
-            ra_clear(row);
-            if (f == 0) {
-                if (mode == 0) {
-                    ra_add(row, p * nf + 0, 1.0 / dt);
-                    /* - (1/h^2) sum_J [ Mp G(p+J) + Mm G(p-J) - (Mp + Mm) G(p) ] */
-                    for (int J = 0; J < d; J++) {
-                        long pp = nbr(g, p, J, +1), pm = nbr(g, p, J, -1);
-                        double Mp = edge_mob(g, k, nf, X0, p, J), Mm = edge_mob(g, k, nf, X0, pm, J);
-                        Gc_row(&cx, pp, t);
-                        ra_axpy(row, -Mp / (h * h), t);
-                        Gc_row(&cx, pm, t);
-                        ra_axpy(row, -Mm / (h * h), t);
-                        Gc_row(&cx, p, t);
-                        ra_axpy(row, (Mp + Mm) / (h * h), t);
+#pragma omp parallel
+    {
+        rowacc *row = (rowacc *)malloc(sizeof(rowacc)), *t = (rowacc *)malloc(sizeof(rowacc));
+#pragma omp for schedule(dynamic, 1)
+        for (long ch = 0; ch < nch; ch++) {
+            long pa = ch * CH, pb = pa + CH < N ? pa + CH : N;
+            long cap = (pb - pa) * nf * 40 + 16, nnz = 0;
+            long *ci = (long *)malloc(sizeof(long) * cap);
+            double *v = (double *)malloc(sizeof(double) * cap);
+            for (long p = pa; p < pb; p++) {
+                for (int f = 0; f < nf; f++) {
+                    ra_clear(row);
+                    if (f == 0) {
+                        if (mode == 0) {
+                            ra_add(row, p * nf + 0, 1.0 / dt);
+                            /* - (1/h^2) sum_J [ Mp G(p+J) + Mm G(p-J) - (Mp + Mm) G(p) ] */
+                            for (int J = 0; J < d; J++) {
+                                long pp = nbr(g, p, J, +1), pm = nbr(g, p, J, -1);
+                                double Mp = edge_mob(g, k, nf, X0, p, J), Mm = edge_mob(g, k, nf, X0, pm, J);
+                                Gc_row(&cx, pp, t);
+                                ra_axpy(row, -Mp / (h * h), t);
+                                Gc_row(&cx, pm, t);
+                                ra_axpy(row, -Mm / (h * h), t);
+                                Gc_row(&cx, p, t);
+                                ra_axpy(row, (Mp + Mm) / (h * h), t);
+                            }
+                        } else {
+                            ra_add(row, p * nf + 0, 1.0);
+                        }
+                    } else if (f < ku) {
+                        /* eta_j row, j = f - 1: (eta_j1 - eta_j0)/dt + keta G_eta_j; the gradient
+                         * part of keta G_eta_j is -3/2 gamma_eta D^2 eta_j1 + ... in both models */
+                        const int j = f - 1;
+                        if (mode == 0) {
+                            const double *pr = cx.part + (long)P * p + (1 + j) * (1 + ne);
+                            ra_add(row, p * nf + f, 1.0 / dt + keta * pr[1 + j] + 3.0 * k->gamma_eta * d / (h * h));
+                            ra_add(row, p * nf + 0, keta * pr[0]);
+                            for (int jj = 0; jj < ne; jj++)
+                                if (jj != j) ra_add(row, p * nf + 1 + jj, keta * pr[1 + jj]);
+                            for (int J = 0; J < d; J++) {
+                                ra_add(row, nbr(g, p, J, +1) * nf + f, -1.5 * k->gamma_eta / (h * h));
+                                ra_add(row, nbr(g, p, J, -1) * nf + f, -1.5 * k->gamma_eta / (h * h));
+                            }
+                        } else {
+                            ra_add(row, p * nf + f, 1.0);
+                        }
+                    } else if (g->neumann) {
+                        /* traction-free: the adjoint form of orc_residual */
+                        int I = f - ku;
+                        long qs[7];
+                        int nq = 0;
+                        qs[nq++] = p;
+                        for (int J = 0; J < d; J++) {
+                            long a = nbr(g, p, J, +1), b = nbr(g, p, J, -1);
+                            if (a != p) qs[nq++] = a;
+                            if (b != p) qs[nq++] = b;
+                        }
+                        for (int q = 0; q < nq; q++)
+                            for (int J = 0; J < d; J++) {
+                                double w = ((p == nbr(g, qs[q], J, +1)) - (p == nbr(g, qs[q], J, -1))) / (2.0 * h);
+                                if (w == 0.0) continue;
+                                sig_row(&cx, qs[q], I, J, t);
+                                ra_axpy(row, -w, t);
+                            }
+                    } else {
+                        int I = f - ku;
+                        for (int J = 0; J < d; J++) {
+                            sig_row(&cx, nbr(g, p, J, +1), I, J, t);
+                            ra_axpy(row, 1.0 / (2.0 * h), t);
+                            sig_row(&cx, nbr(g, p, J, -1), I, J, t);
+                            ra_axpy(row, -1.0 / (2.0 * h), t);
+                        }
                     }
-                } else {
-                    ra_add(row, p * nf + 0, 1.0);
-                }
-            } else if (f < ku) {
-                /* eta_j row, j = f - 1: (eta_j1 - eta_j0)/dt + keta G_eta_j; the gradient
-                 * part of keta G_eta_j is -3/2 gamma_eta D^2 eta_j1 + ... in both models */
-                const int j = f - 1;
-                if (mode == 0) {
-                    const double *pr = cx.part + (long)P * p + (1 + j) * (1 + ne);
-                    ra_add(row, p * nf + f, 1.0 / dt + keta * pr[1 + j] + 3.0 * k->gamma_eta * d / (h * h));
-                    ra_add(row, p * nf + 0, keta * pr[0]);
-                    for (int jj = 0; jj < ne; jj++)
-                        if (jj != j) ra_add(row, p * nf + 1 + jj, keta * pr[1 + jj]);
-                    for (int J = 0; J < d; J++) {
-                        ra_add(row, nbr(g, p, J, +1) * nf + f, -1.5 * k->gamma_eta / (h * h));
-                        ra_add(row, nbr(g, p, J, -1) * nf + f, -1.5 * k->gamma_eta / (h * h));
+                    ra_sort(row);
+                    if (nnz + row->n > cap) {
+                        cap = cap * 2 + row->n;
+                        ci = (long *)realloc(ci, sizeof(long) * cap);
+                        v = (double *)realloc(v, sizeof(double) * cap);
                     }
-                } else {
-                    ra_add(row, p * nf + f, 1.0);
-                }
-            } else if (g->neumann) {
-                /* traction-free: the adjoint form of orc_residual */
-                int I = f - ku;
-                long qs[7];
-                int nq = 0;
-                qs[nq++] = p;
-                for (int J = 0; J < d; J++) {
-                    long a = nbr(g, p, J, +1), b = nbr(g, p, J, -1);
-                    if (a != p) qs[nq++] = a;
-                    if (b != p) qs[nq++] = b;
-                }
-                for (int q = 0; q < nq; q++)
-                    for (int J = 0; J < d; J++) {
-                        double w = ((p == nbr(g, qs[q], J, +1)) - (p == nbr(g, qs[q], J, -1))) / (2.0 * h);
-                        if (w == 0.0) continue;
-                        sig_row(&cx, qs[q], I, J, t);
-                        ra_axpy(row, -w, t);
+                    for (int i = 0; i < row->n; i++) {
+                        ci[nnz] = row->col[i];
+                        v[nnz] = row->val[i];
+                        nnz++;
                     }
-            } else {
-                int I = f - ku;
-                for (int J = 0; J < d; J++) {
-                    sig_row(&cx, nbr(g, p, J, +1), I, J, t);
-                    ra_axpy(row, 1.0 / (2.0 * h), t);
-                    sig_row(&cx, nbr(g, p, J, -1), I, J, t);
-                    ra_axpy(row, -1.0 / (2.0 * h), t);
+                    A->rp[p * nf + f + 1] = row->n; /* row length; offsets below */
                 }
             }
-            ra_sort(row);
-            if (nnz + row->n > cap) {
-                cap = cap * 2 + row->n;
-                A->ci = (long *)realloc(A->ci, sizeof(long) * cap);
-                A->v = (double *)realloc(A->v, sizeof(double) * cap);
-            }
-            for (int i = 0; i < row->n; i++) {
-                A->ci[nnz] = row->col[i];
-                A->v[nnz] = row->val[i];
-                nnz++;
-            }
-            A->rp[p * nf + f + 1] = nnz;
+            cci[ch] = (long *)realloc(ci, sizeof(long) * (nnz > 0 ? nnz : 1));
+            cv[ch] = (double *)realloc(v, sizeof(double) * (nnz > 0 ? nnz : 1));
+            cnnz[ch] = nnz;
         }
+        free(row);
+        free(t);
     }
-    free(row);
-    free(t);
+    A->rp[0] = 0;
+    for (long r = 0; r < A->n; r++) A->rp[r + 1] += A->rp[r];
+    long total = A->rp[A->n];
+    A->ci = (long *)malloc(sizeof(long) * (total > 0 ? total : 1));
+    A->v = (double *)malloc(sizeof(double) * (total > 0 ? total : 1));
+#pragma omp parallel for schedule(static)
+    for (long ch = 0; ch < nch; ch++) {
+        long off = A->rp[ch * CH * nf];
+        memcpy(A->ci + off, cci[ch], sizeof(long) * cnnz[ch]);
+        memcpy(A->v + off, cv[ch], sizeof(double) * cnnz[ch]);
+        free(cci[ch]);
+        free(cv[ch]);
+    }
+    free(cci);
+    free(cv);
+    free(cnnz);
     free(cx.part);
 }
 
 static void csr_matvec(const csr *A, const double *x, double *y)
 {
+#pragma omp parallel for schedule(static)
     for (long i = 0; i < A->n; i++) {
         double s = 0.0;
         for (long jj = A->rp[i]; jj < A->rp[i + 1]; jj++) s += A->v[jj] * x[A->ci[jj]];
@@ -1276,93 +1378,98 @@ static int ras_setup(const orc_grid *g, int nf, int ku, const orc_opts *o, const
     R->A = (csr *)calloc(R->nsub, sizeof(csr));
     R->dense = (double **)calloc(R->nsub, sizeof(double *));
     R->piv = (long **)calloc(R->nsub, sizeof(long *));
-    long N = grid_N(g);
-    long *gmap = (long *)malloc(sizeof(long) * N);
-    for (long p = 0; p < N; p++) gmap[p] = -1;
     int rc = 0;
-    for (int s2 = 0; s2 < sub[2]; s2++)
-        for (int s1 = 0; s1 < sub[1]; s1++)
-            for (int s0 = 0; s0 < sub[0]; s0++) {
-                int s = s0 + sub[0] * (s1 + sub[1] * s2);
-                int sidx[3] = {s0, s1, s2};
-                long st[3], ln[3], o0[3], o1[3];
-                for (int a = 0; a < 3; a++) {
-                    if (a < d)
-                        axis_range(g->n[a], sub[a], sidx[a], o->overlap, g->neumann, &st[a], &ln[a], &o0[a], &o1[a]);
-                    else {
-                        st[a] = 0;
-                        ln[a] = 1;
-                        o0[a] = 0;
-                        o1[a] = 1;
-                    }
-                }
-                long np = ln[0] * ln[1] * ln[2];
-                R->next[s] = np;
-                R->pts[s] = (long *)malloc(sizeof(long) * np);
-                R->own[s] = (unsigned char *)malloc(np);
-                long lp = 0;
-                for (long z = 0; z < ln[2]; z++)
-                    for (long y = 0; y < ln[1]; y++)
-                        for (long x = 0; x < ln[0]; x++) {
-                            long gx[3] = {x, y, z}, gc[3];
-                            int owned = 1;
-                            for (int a = 0; a < 3; a++) {
-                                long n = g->n[a];
-                                gc[a] = ((st[a] + gx[a]) % n + n) % n;
-                                if (gc[a] < o0[a] || gc[a] >= o1[a]) owned = 0;
-                            }
-                            long gp = gc[0] + (long)g->n[0] * (gc[1] + (long)g->n[1] * gc[2]);
-                            R->pts[s][lp] = gp;
-                            R->own[s][lp] = (unsigned char)owned;
-                            gmap[gp] = lp;
-                            lp++;
-                        }
-                /* local matrix: rows and columns of J restricted to the extended box */
-                csr *L = &R->A[s];
-                L->n = np * nf;
-                L->rp = (long *)malloc(sizeof(long) * (L->n + 1));
-                long cap = 0;
-                for (long q = 0; q < np; q++)
-                    for (int f = 0; f < nf; f++) {
-                        long r = R->pts[s][q] * nf + f;
-                        cap += J->rp[r + 1] - J->rp[r];
-                    }
-                L->ci = (long *)malloc(sizeof(long) * (cap + 1));
-                L->v = (double *)malloc(sizeof(double) * (cap + 1));
-                long nnz = 0;
-                L->rp[0] = 0;
-                rowacc *ra = (rowacc *)malloc(sizeof(rowacc));
-                for (long q = 0; q < np; q++)
-                    for (int f = 0; f < nf; f++) {
-                        long r = R->pts[s][q] * nf + f;
-                        ra_clear(ra);
-                        for (long jj = J->rp[r]; jj < J->rp[r + 1]; jj++) {
-                            long cp = J->ci[jj] / nf, cf = J->ci[jj] % nf;
-                            if (gmap[cp] >= 0) ra_add(ra, gmap[cp] * nf + cf, J->v[jj]);
-                        }
-                        ra_sort(ra);
-                        for (int i = 0; i < ra->n; i++) {
-                            L->ci[nnz] = ra->col[i];
-                            L->v[nnz] = ra->val[i];
-                            nnz++;
-                        }
-                        L->rp[q * nf + f + 1] = nnz;
-                    }
-                free(ra);
-                for (long q = 0; q < np; q++) gmap[R->pts[s][q]] = -1;
-                if (o->subsolver == 0) {
-                    if (orc_ilu0(L->n, L->rp, L->ci, L->v) != 0) rc = ORC_EPIVOT;
-                } else {
-                    long n = L->n;
-                    R->dense[s] = (double *)calloc((size_t)n * n, sizeof(double));
-                    R->piv[s] = (long *)malloc(sizeof(long) * n);
-                    for (long i = 0; i < n; i++)
-                        for (long jj = L->rp[i]; jj < L->rp[i + 1]; jj++) R->dense[s][i * n + L->ci[jj]] = L->v[jj];
-                    if (dense_lu(n, R->dense[s], R->piv[s]) != 0) rc = ORC_EPIVOT;
-                    csr_free(L);
-                }
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : rc)
+    for (int s = 0; s < R->nsub; s++) {
+        int sidx[3] = {s % sub[0], (s / sub[0]) % sub[1], s / (sub[0] * sub[1])};
+        long st[3], ln[3], o0[3], o1[3];
+        for (int a = 0; a < 3; a++) {
+            if (a < d)
+                axis_range(g->n[a], sub[a], sidx[a], o->overlap, g->neumann, &st[a], &ln[a], &o0[a], &o1[a]);
+            else {
+                st[a] = 0;
+                ln[a] = 1;
+                o0[a] = 0;
+                o1[a] = 1;
             }
-    free(gmap);
+        }
+        long np = ln[0] * ln[1] * ln[2];
+        R->next[s] = np;
+        R->pts[s] = (long *)malloc(sizeof(long) * np);
+        R->own[s] = (unsigned char *)malloc(np);
+        long lp = 0;
+        for (long z = 0; z < ln[2]; z++)
+            for (long y = 0; y < ln[1]; y++)
+                for (long x = 0; x < ln[0]; x++) {
+                    long gx[3] = {x, y, z}, gc[3];
+                    int owned = 1;
+                    for (int a = 0; a < 3; a++) {
+                        long n = g->n[a];
+                        gc[a] = ((st[a] + gx[a]) % n + n) % n;
+                        if (gc[a] < o0[a] || gc[a] >= o1[a]) owned = 0;
+                    }
+                    long gp = gc[0] + (long)g->n[0] * (gc[1] + (long)g->n[1] * gc[2]);
+                    R->pts[s][lp] = gp;
+                    R->own[s][lp] = (unsigned char)owned;
+                    lp++;
+                }
+        /* local matrix: rows and columns of J restricted to the extended box; a
+         * global point is in the box when its offset from the box start (modulo
+         * the axis length) is below the box length on every axis, and its local
+         * index is then the x-fastest number of those offsets */
+        csr *L = &R->A[s];
+        L->n = np * nf;
+        L->rp = (long *)malloc(sizeof(long) * (L->n + 1));
+        long cap = 0;
+        for (long q = 0; q < np; q++)
+            for (int f = 0; f < nf; f++) {
+                long r = R->pts[s][q] * nf + f;
+                cap += J->rp[r + 1] - J->rp[r];
+            }
+        L->ci = (long *)malloc(sizeof(long) * (cap + 1));
+        L->v = (double *)malloc(sizeof(double) * (cap + 1));
+        long nnz = 0;
+        L->rp[0] = 0;
+        rowacc *ra = (rowacc *)malloc(sizeof(rowacc));
+        for (long q = 0; q < np; q++)
+            for (int f = 0; f < nf; f++) {
+                long r = R->pts[s][q] * nf + f;
+                ra_clear(ra);
+                for (long jj = J->rp[r]; jj < J->rp[r + 1]; jj++) {
+                    long cp = J->ci[jj] / nf, cf = J->ci[jj] % nf;
+                    long cc[3];
+                    coords(g, cp, cc);
+                    long loc = 0, mul = 1;
+                    int inside = 1;
+                    for (int a = 0; a < 3; a++) {
+                        long n = g->n[a], off = ((cc[a] - st[a]) % n + n) % n;
+                        if (off >= ln[a]) inside = 0;
+                        loc += off * mul;
+                        mul *= ln[a];
+                    }
+                    if (inside) ra_add(ra, loc * nf + cf, J->v[jj]);
+                }
+                ra_sort(ra);
+                for (int i = 0; i < ra->n; i++) {
+                    L->ci[nnz] = ra->col[i];
+                    L->v[nnz] = ra->val[i];
+                    nnz++;
+                }
+                L->rp[q * nf + f + 1] = nnz;
+            }
+        free(ra);
+        if (o->subsolver == 0) {
+            if (orc_ilu0(L->n, L->rp, L->ci, L->v) != 0) rc |= ORC_EPIVOT;
+        } else {
+            long n = L->n;
+            R->dense[s] = (double *)calloc((size_t)n * n, sizeof(double));
+            R->piv[s] = (long *)malloc(sizeof(long) * n);
+            for (long i = 0; i < n; i++)
+                for (long jj = L->rp[i]; jj < L->rp[i + 1]; jj++) R->dense[s][i * n + L->ci[jj]] = L->v[jj];
+            if (dense_lu(n, R->dense[s], R->piv[s]) != 0) rc |= ORC_EPIVOT;
+            csr_free(L);
+        }
+    }
     return rc;
 }
 
@@ -1377,19 +1484,20 @@ static int ras_setup(const orc_grid *g, int nf, int ku, const orc_opts *o, const
 static void project(const orc_grid *g, int nf, int ku, double *z)
 {
     long N = grid_N(g);
-    double s = 0.0;
-    for (long p = 0; p < N; p++) s += z[p * nf];
-    double mean = s / (double)N;
+    double mean = strided_sum(N, z, nf) / (double)N;
+#pragma omp parallel for schedule(static)
     for (long p = 0; p < N; p++) z[p * nf] -= mean;
     if (ku >= nf) return;
     int d = g->dim;
     int even_mask = 0; /* Neumann (mirror ghosts): translations only */
     for (int J = 0; J < d; J++)
         if (g->n[J] % 2 == 0 && !g->neumann) even_mask |= 1 << J;
+    double *sv = (double *)malloc(sizeof(double) * N);
     for (int I = 0; I < d; I++) {
         for (int m = 0; m < (1 << d); m++) {
             if ((m & ~even_mask) != 0) continue;
-            double dot = 0.0;
+            /* sv_p = mode(p) z_uI(p), mode(p) = (-1)^(sum of the coordinates selected by m) */
+#pragma omp parallel for schedule(static)
             for (long p = 0; p < N; p++) {
                 long x[3];
                 coords(g, p, x);
@@ -1397,9 +1505,10 @@ static void project(const orc_grid *g, int nf, int ku, double *z)
                 for (int J = 0; J < d; J++)
                     if (m & (1 << J)) par += (int)(x[J] & 1);
                 double sg = (par & 1) ? -1.0 : 1.0;
-                dot += sg * z[p * nf + ku + I];
+                sv[p] = sg * z[p * nf + ku + I];
             }
-            double a = dot / (double)N;
+            double a = strided_sum(N, sv, 1) / (double)N;
+#pragma omp parallel for schedule(static)
             for (long p = 0; p < N; p++) {
                 long x[3];
                 coords(g, p, x);
@@ -1411,6 +1520,7 @@ static void project(const orc_grid *g, int nf, int ku, double *z)
             }
         }
     }
+    free(sv);
 }
 
 /*
@@ -1426,7 +1536,12 @@ static void ras_apply(const orc_grid *g, const ras_t *R, int do_project, const d
 {
     int nf = R->nf;
     long N = grid_N(g);
+#pragma omp parallel for schedule(static)
     for (long i = 0; i < N * nf; i++) z[i] = 0.0;
+    /* the subdomain solves are independent; left-RAS writes disjoint owned
+     * points, the other types keep each solution and add them in box order */
+    double **xs = (double **)calloc(R->nsub, sizeof(double *));
+#pragma omp parallel for schedule(dynamic, 1)
     for (int s = 0; s < R->nsub; s++) {
         long np = R->next[s], n = np * nf;
         double *b = (double *)malloc(sizeof(double) * n), *x = (double *)malloc(sizeof(double) * n);
@@ -1435,17 +1550,25 @@ static void ras_apply(const orc_grid *g, const ras_t *R, int do_project, const d
                 b[q * nf + f] = (R->variant == 2 && !R->own[s][q]) ? 0.0 : r[R->pts[s][q] * nf + f];
         if (R->subsolver == 0) ilu0_solve(&R->A[s], b, x);
         else dense_lu_solve(n, R->dense[s], R->piv[s], b, x);
-        for (long q = 0; q < np; q++) {
-            if (R->variant == 0) {
+        free(b);
+        if (R->variant == 0) {
+            for (long q = 0; q < np; q++)
                 if (R->own[s][q])
                     for (int f = 0; f < nf; f++) z[R->pts[s][q] * nf + f] = x[q * nf + f];
-            } else {
-                for (int f = 0; f < nf; f++) z[R->pts[s][q] * nf + f] += x[q * nf + f];
-            }
+            free(x);
+        } else {
+            xs[s] = x;
         }
-        free(b);
-        free(x);
     }
+    if (R->variant != 0) {
+        for (int s = 0; s < R->nsub; s++) {
+            long np = R->next[s];
+            for (long q = 0; q < np; q++)
+                for (int f = 0; f < nf; f++) z[R->pts[s][q] * nf + f] += xs[s][q * nf + f];
+            free(xs[s]);
+        }
+    }
+    free(xs);
     if (do_project) project(g, nf, R->ku, z);
 }
 
@@ -1455,8 +1578,17 @@ static void ras_apply(const orc_grid *g, const ras_t *R, int do_project, const d
 
 static double dot(long n, const double *a, const double *b)
 {
-    double s = 0.0;
-    for (long i = 0; i < n; i++) s += a[i] * b[i];
+    long nb = n_blocks(n);
+    double *part = (double *)malloc(sizeof(double) * (nb > 0 ? nb : 1));
+#pragma omp parallel for schedule(static)
+    for (long q = 0; q < nb; q++) {
+        long i1 = (q + 1) * ORC_SUM_BLOCK < n ? (q + 1) * ORC_SUM_BLOCK : n;
+        double s = 0.0;
+        for (long i = q * ORC_SUM_BLOCK; i < i1; i++) s += a[i] * b[i];
+        part[q] = s;
+    }
+    double s = sum_parts(part, nb);
+    free(part);
     return s;
 }
 
@@ -1479,6 +1611,7 @@ static int gmres(const orc_grid *g, const csr *A, const ras_t *R, int do_project
     double *gv = (double *)malloc(sizeof(double) * (m + 1)), *y = (double *)malloc(sizeof(double) * m);
     double *w = (double *)malloc(sizeof(double) * n), *z = (double *)malloc(sizeof(double) * n);
     double *r = (double *)malloc(sizeof(double) * n), *hv = (double *)malloc(sizeof(double) * (m + 1));
+#pragma omp parallel for schedule(static)
     for (long i = 0; i < n; i++) {
         x[i] = 0.0;
         r[i] = b[i];
@@ -1486,6 +1619,7 @@ static int gmres(const orc_grid *g, const csr *A, const ras_t *R, int do_project
     double beta = sqrt(dot(n, r, r));
     int its = 0;
     while (beta > tol && its < maxit) {
+#pragma omp parallel for schedule(static)
         for (long i = 0; i < n; i++) V[0][i] = r[i] / beta;
         for (int i = 0; i <= m; i++) gv[i] = 0.0;
         gv[0] = beta;
@@ -1495,13 +1629,16 @@ static int gmres(const orc_grid *g, const csr *A, const ras_t *R, int do_project
             csr_matvec(A, z, w);
             double wn0 = sqrt(dot(n, w, w));
             for (int i = 0; i <= j; i++) hv[i] = dot(n, V[i], w);
-            for (int i = 0; i <= j; i++)
-                for (long l = 0; l < n; l++) w[l] -= hv[i] * V[i][l];
+            /* per entry, the j + 1 updates in order i = 0..j */
+#pragma omp parallel for schedule(static)
+            for (long l = 0; l < n; l++)
+                for (int i = 0; i <= j; i++) w[l] -= hv[i] * V[i][l];
             double wn = sqrt(dot(n, w, w));
             if (wn < 0.7 * wn0) {
                 for (int i = 0; i <= j; i++) {
                     double h2 = dot(n, V[i], w);
                     hv[i] += h2;
+#pragma omp parallel for schedule(static)
                     for (long l = 0; l < n; l++) w[l] -= h2 * V[i][l];
                 }
                 wn = sqrt(dot(n, w, w));
@@ -1523,8 +1660,10 @@ static int gmres(const orc_grid *g, const csr *A, const ras_t *R, int do_project
             gv[j] = cs[j] * gv[j];
             its++;
             kdim = j + 1;
-            if (wn != 0.0)
+            if (wn != 0.0) {
+#pragma omp parallel for schedule(static)
                 for (long l = 0; l < n; l++) V[j + 1][l] = w[l] / wn;
+            }
             if (fabs(gv[j + 1]) <= tol || its >= maxit || wn == 0.0) break;
         }
         for (int i = kdim - 1; i >= 0; i--) {
@@ -1532,12 +1671,17 @@ static int gmres(const orc_grid *g, const csr *A, const ras_t *R, int do_project
             for (int l = i + 1; l < kdim; l++) s -= H[i * m + l] * y[l];
             y[i] = s / H[i * m + i];
         }
-        for (long l = 0; l < n; l++) w[l] = 0.0;
-        for (int i = 0; i < kdim; i++)
-            for (long l = 0; l < n; l++) w[l] += y[i] * V[i][l];
+        /* per entry, w = sum_i y_i V_i in order i = 0..kdim-1 */
+#pragma omp parallel for schedule(static)
+        for (long l = 0; l < n; l++) {
+            w[l] = 0.0;
+            for (int i = 0; i < kdim; i++) w[l] += y[i] * V[i][l];
+        }
         ras_apply(g, R, do_project, w, z);
+#pragma omp parallel for schedule(static)
         for (long l = 0; l < n; l++) x[l] += z[l];
         csr_matvec(A, x, w);
+#pragma omp parallel for schedule(static)
         for (long l = 0; l < n; l++) r[l] = b[l] - w[l];
         beta = sqrt(dot(n, r, r));
     }
@@ -1565,23 +1709,26 @@ static int gmres(const orc_grid *g, const csr *A, const ras_t *R, int do_project
  * order parameters c and the four site fractions c eta_i (eta_4 = 4 - sum) */
 static int in_domain(const orc_coeffs *k, long N, int nf, const double *X)
 {
+    int ok = 1;
     if (n_eta(k) == 3) {
+#pragma omp parallel for schedule(static) reduction(& : ok)
         for (long p = 0; p < N; p++) {
             double c = X[p * nf], e4 = 4.0 - X[p * nf + 1] - X[p * nf + 2] - X[p * nf + 3];
-            if (!(c > 0.0 && c < 1.0 && c * e4 > 0.0 && c * e4 < 1.0)) return 0;
+            if (!(c > 0.0 && c < 1.0 && c * e4 > 0.0 && c * e4 < 1.0)) ok = 0;
             for (int j = 1; j <= 3; j++) {
                 double q = c * X[p * nf + j];
-                if (!(q > 0.0 && q < 1.0)) return 0;
+                if (!(q > 0.0 && q < 1.0)) ok = 0;
             }
         }
-        return 1;
+        return ok;
     }
+#pragma omp parallel for schedule(static) reduction(& : ok)
     for (long p = 0; p < N; p++) {
         double c = X[p * nf], e = X[p * nf + 1];
         double pp = c * e, q = c * (4.0 - 3.0 * e);
-        if (!(c > 0.0 && c < 1.0 && pp > 0.0 && pp < 1.0 && q > 0.0 && q < 1.0)) return 0;
+        if (!(c > 0.0 && c < 1.0 && pp > 0.0 && pp < 1.0 && q > 0.0 && q < 1.0)) ok = 0;
     }
-    return 1;
+    return ok;
 }
 
 /*
@@ -1630,6 +1777,7 @@ static int newton(const orc_grid *g, const orc_coeffs *k, const orc_opts *o, dou
             }
             have_R = 1;
         }
+#pragma omp parallel for schedule(static)
         for (long i = 0; i < n; i++) b[i] = -F[i];
         int gits;
         double gres;
@@ -1640,6 +1788,7 @@ static int newton(const orc_grid *g, const orc_coeffs *k, const orc_opts *o, dou
         double lam = 1.0, ftn = 0.0;
         int ok = 0;
         while (lam >= o->ls_lambda_min) {
+#pragma omp parallel for schedule(static)
             for (long i = 0; i < n; i++) Xt[i] = X[i] + lam * S[i];
             if (in_domain(k, N, nf, Xt)) {
                 orc_residual(g, k, cbar0, dt, Xt, X0, mode, Ft);
@@ -1757,9 +1906,7 @@ int orc_simulate(const orc_grid *g, const orc_coeffs *k, const orc_opts *o, doub
 {
     int nf = orc_nfields(g, k);
     long N = grid_N(g), n = N * nf;
-    double cbar0 = 0.0;
-    for (long p = 0; p < N; p++) cbar0 += X[p * nf];
-    cbar0 /= (double)N;
+    double cbar0 = strided_sum(N, X, nf) / (double)N;
     orc_step_info ei;
     int rc = orc_equilibrate(g, k, o, cbar0, X, &ei);
     if (rc != ORC_OK) return rc;
@@ -1775,9 +1922,11 @@ int orc_simulate(const orc_grid *g, const orc_coeffs *k, const orc_opts *o, doub
         else {
             double Xd;
             if (o->dt_mode == 1) {
-                double s = 0.0;
-                for (long i = 0; i < n; i++) s += (X[i] - Xprev[i]) * (X[i] - Xprev[i]);
-                Xd = sqrt(s) / dt_prev;
+                double *dx = (double *)malloc(sizeof(double) * n);
+#pragma omp parallel for schedule(static)
+                for (long i = 0; i < n; i++) dx[i] = X[i] - Xprev[i];
+                Xd = sqrt(dot(n, dx, dx)) / dt_prev;
+                free(dx);
             } else {
                 Xd = fabs(E - Eprev) / dt_prev;
             }
