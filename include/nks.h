@@ -410,7 +410,8 @@ int nks_autotune(const nks_grid *grid, const double *c, const double *eta, const
 /* ------------------------------------------------------------------------ */
 
 /* F(X1; X0, dt) of Eq. NSOA-1 (mode 0), or the displacement-only residual
- * (mode 1: F_c = F_eta = 0) used for the initial equilibrium. */
+ * (mode 1: F_c = F_eta = 0) used for the initial equilibrium; without
+ * elasticity mode 1 gives F = 0. */
 int nks_eval_residual(nks_problem *p, const double *X1, const double *X0, double dt, int mode, double *F);
 
 /* Jv = J(X1; X0, dt) v with J = dF/dX1 (Sec. 4, J_m = grad F(X_m)).  In the
@@ -456,23 +457,29 @@ int nks_eval_energy(nks_problem *p, const double *X, double *parts, double *mass
  * synchronise the device.
  *
  *   grid, coeffs   as for nks_create_problem; grid->n[0]*n[1]*n[2] must not
- *                  exceed NKS_NOALLOC_MAX_POINTS (NKS_EINVAL otherwise)
+ *                  exceed NKS_NOALLOC_MAX_POINTS (NKS_EINVAL otherwise); every
+ *                  axis needs at least 3 cells
  *   cbar0          mean composition of the initial state (Sec. 3)
- *   dt, mode       as for nks_eval_residual (mode 1: displacement-only system)
+ *   dt, mode       as for nks_eval_residual (mode 1: displacement-only system;
+ *                  without elasticity that system is empty and F = 0)
  *   X1, X0, F      DEVICE state arrays of nf*N doubles (layout of this header)
  *   fnorm2         DEVICE pointer receiving ||F||^2, or NULL
  *   stream         cudaStream_t to run on (NULL: the legacy default stream)
  * Returns NKS_OK, NKS_EINVAL, NKS_EDOMAIN (X1 outside the domain of the
  * logarithms; F is still written) or NKS_ECUDA; nks_last_error(NULL) gives
- * the message.  The call synchronises the stream before it returns.
+ * the message.  The call synchronises the stream before it returns.  A CUDA
+ * error already pending from the caller's earlier work makes the call return
+ * NKS_ECUDA at once, leaving that error pending for its owner.
  *
  * Scratch: a fixed array of 15 * NKS_NOALLOC_MAX_POINTS doubles (7.5 MiB) plus
  * reduction space, held in device memory by every GPU that loads the library
  * until the process exits.  The first call on a device looks up the array's
  * device address (once per device, with that device current); make that first
- * call before any stream capture.  All calls share the array and it keeps the
- * previous call's contents, so calls that overlap on the GPU (from several
- * threads or streams) race: serialise them.
+ * call before any stream capture.  The address belongs to the device's primary
+ * context: after cudaDeviceReset, or from another context on the same device,
+ * it is no longer valid, so do not call this function there.  All calls share
+ * the array and it keeps the previous call's contents, so calls that overlap
+ * on the GPU (from several threads or streams) race: serialise them.
  */
 int nks_residual_noalloc(const nks_grid *grid, const nks_coeffs *coeffs, double cbar0, double dt, int mode,
                          const double *X1, const double *X0, double *F, double *fnorm2, void *stream);

@@ -11,6 +11,7 @@
 // partials live in the file-scope array below, which every GPU that loads this
 // library keeps for the life of the process.
 #include <mutex>
+#include <string>
 
 #include "nks_internal.cuh"
 
@@ -46,18 +47,32 @@ extern "C" int nks_residual_noalloc(const nks_grid *grid, const nks_coeffs *coef
     DGrid g{};
     g.dim = grid->dim;
     for (int J = 0; J < 3; J++) g.n[J] = J < grid->dim ? grid->n[J] : 1;
-    for (int J = 0; J < g.dim; J++)
+    for (int J = 0; J < g.dim; J++) {
         if (g.n[J] < 3) {
             set_thread_error("nks_residual_noalloc: at least 3 cells per axis");
             return NKS_EINVAL;
         }
+        // each axis on its own first, so that the product below cannot overflow
+        if (g.n[J] > NKS_NOALLOC_MAX_POINTS) {
+            set_thread_error("nks_residual_noalloc: grid larger than NKS_NOALLOC_MAX_POINTS points; use the problem API");
+            return NKS_EINVAL;
+        }
+    }
     g.N = (long long)g.n[0] * g.n[1] * g.n[2];
     set_spacing(g, grid->h);
     if (g.N > NKS_NOALLOC_MAX_POINTS) {
         set_thread_error("nks_residual_noalloc: grid larger than NKS_NOALLOC_MAX_POINTS points; use the problem API");
         return NKS_EINVAL;
     }
+    // an error left pending by the caller's earlier work is theirs: fail without consuming it
+    const cudaError_t pending = cudaPeekAtLastError();
+    if (pending != cudaSuccess) {
+        set_thread_error((std::string("nks_residual_noalloc: a CUDA error of earlier work is pending: ") +
+                          cudaGetErrorString(pending)).c_str());
+        return NKS_ECUDA;
+    }
     // set-up once per device, with that device current: the device address of the scratch array
+    // (an address in the device's primary context, which a cudaDeviceReset invalidates)
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
         set_thread_error("nks_residual_noalloc: no usable CUDA device");
@@ -79,27 +94,33 @@ extern "C" int nks_residual_noalloc(const nks_grid *grid, const nks_coeffs *coef
     double *sums = partials + kRedBlocks * 64;  // 64 doubles after the partials
     int *flag = reinterpret_cast<int *>(sums + 8);
     double *isc = sums + 16;  // the kernels' per-instance scalars (dt, cbar0)
+    auto fail = [](cudaError_t e, const char *what) {
+        set_thread_error((std::string("nks_residual_noalloc: ") + what + ": " + cudaGetErrorString(e)).c_str());
+        return NKS_ECUDA;
+    };
     // the scratch keeps the previous call's contents: only the domain flag must start at zero
-    cudaMemsetAsync(flag, 0, sizeof(int), st);
+    cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), st);
+    if (e != cudaSuccess) return fail(e, "clearing the domain flag");
     double hisc[I_NSC] = {0.0};
     hisc[I_DT] = dt;
     hisc[I_IDT] = 1.0 / dt;
     hisc[I_CBAR0] = cbar0;
     // from pageable memory: the source is staged before the call returns
-    cudaMemcpyAsync(isc, hisc, sizeof(hisc), cudaMemcpyHostToDevice, st);
+    e = cudaMemcpyAsync(isc, hisc, sizeof(hisc), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return fail(e, "uploading dt and cbar0");
     const Bat one{};
     launch_mobility(g, k, X0, mob, st, one);
     if (k.elastic) launch_trace0(g, k, isc, X0, tr0, st, one);
     launch_residual(g, k, isc, mode, X1, X0, tr0, mob, Gc, sig, part, F, flag, partials, kRedBlocks, st, one);
     launch_finalize(partials, kRedBlocks, 1, fnorm2 ? fnorm2 : sums, st, one);
+    // nothing was pending at entry, so a launch error here is this call's
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(e, "kernel launch");
     int hflag = 0;
-    cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
-    cudaError_t e = cudaStreamSynchronize(st);
-    if (e == cudaSuccess) e = cudaGetLastError();
-    if (e != cudaSuccess) {
-        set_thread_error(cudaGetErrorString(e));
-        return NKS_ECUDA;
-    }
+    e = cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return fail(e, "reading the domain flag");
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(e, "synchronising the stream");
     if (hflag & 1) {
         set_thread_error("nks_residual_noalloc: X1 leaves the domain of the logarithms");
         return NKS_EDOMAIN;
