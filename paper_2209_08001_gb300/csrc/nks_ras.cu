@@ -42,7 +42,8 @@ struct SubInfo {
     int own0[3], own1[3];     // owned local range [own0, own1)
     int np, nlev;
     int px, py, npx;          // odd row pitches of the box vector and its padded size (bank-conflict free levels)
-    int qx, qy, nqx;          // the same with kHalo zero cells around the box (FP32 sweep, 1-D and 2-D)
+    int qx, qy, nqx;          // pitches and plane size of the FP32 sweep's branch-free layout: 1-D and 2-D
+                              // boxes with kHalo zero cells around them, 3-D boxes the pitches above
     long long lvl_off;        // into lvl_ptr / lvl_blk (nlev + 1 entries)
     long long pos_off;        // into lvl_lp (np entries): packed coordinates x | y << 10 | z << 20
     long long fac_off;        // into the factor array (elements)
@@ -67,7 +68,8 @@ struct RasPlan {
     long long nlev_all = 0;         // levels of all boxes
     long long *lvl_src = nullptr;   // FP64 factor offset of every level's block (nlev_all + 1 entries)
     int maxnqx = 0;                 // largest box plane with the halo
-    bool halo32 = false;            // FP32 sweep on the halo layout (no neighbour bounds checks)
+    int guard32 = 0;                // zero cells before and after the 3-D box planes (the stencil reach)
+    bool halo32 = false;            // FP32 sweep on the branch-free layout (no neighbour bounds checks)
     long long scr_elems = 0;        // global scratch vector of the sweeps (when x is not in shared memory)
     long long total_np = 0;         // overlapped points of all subdomains
     bool x_smem = true;
@@ -166,7 +168,9 @@ static size_t apply_smem_lane(const RasPlan *R, int nf, bool halo, bool with_x, 
 {
     size_t b = 32 + pad16((size_t)R->maxnp * (halo ? sizeof(unsigned short) : sizeof(int))) +
                pad16(2 * sizeof(int) * (size_t)(R->maxnlev + 1)) + nbuf * pad16((size_t)R->maxblk32 * sizeof(float));
-    if (with_x) b += pad16((size_t)(halo ? R->maxnqx : R->maxnpx) * nf * sizeof(float));
+    if (with_x)
+        b += pad16(((size_t)(halo ? R->maxnqx : R->maxnpx) * nf + (halo ? 2 * (size_t)R->guard32 : 0)) *
+                   sizeof(float));
     return b;
 }
 
@@ -255,7 +259,8 @@ static void choose_lane_config(const Problem *P, RasPlan *R, int nf)
     int nsm, smem_sm;
     sm_limits(nsm, smem_sm);
     const long long blocks = (long long)R->nsub * std::max(1, P->nb);
-    const bool halo_ok = P->g.dim <= 2 && R->maxnqx < 65536;
+    // the branch-free layout needs 16-bit cell indices
+    const bool halo_ok = R->maxnqx < 65536;
     struct Cand {
         bool halo;
         int nbuf;
@@ -392,8 +397,18 @@ int ras_plan_create(Problem *P, std::string &err)
                 si.py = d >= 2 ? (si.L[1] | 1) : 1;
                 si.npx = si.px * si.py * si.L[2];
                 R->maxnpx = std::max(R->maxnpx, si.npx);
-                si.qx = (si.L[0] + 2 * kHalo) | 1;
-                si.qy = d >= 2 ? si.L[1] + 2 * kHalo : 1;
+                if (d <= 2) {
+                    // kHalo zero cells around the box: every neighbour at a fixed offset
+                    si.qx = (si.L[0] + 2 * kHalo) | 1;
+                    si.qy = d >= 2 ? si.L[1] + 2 * kHalo : 1;
+                } else {
+                    // 3-D: the box's own (odd) pitches; a neighbour outside the box lands on
+                    // another cell of the zero-filled planes or on the zero guard cells, and
+                    // its factor entry is an exact zero
+                    si.qx = si.px;
+                    si.qy = si.py;
+                    R->guard32 = std::max(R->guard32, 2 * si.qx * si.qy);  // |dx + qx dy + qx qy dz| <= 2 qx qy
+                }
                 si.nqx = si.qx * si.qy * si.L[2];
                 R->maxnqx = std::max(R->maxnqx, si.nqx);
                 R->total_np += si.np;
@@ -921,10 +936,12 @@ __global__ void __launch_bounds__(1024) k_ras_apply(DGrid g, Bat bt, const SubIn
 // All rows of one point in sweep order, from the point's own factor values Bk
 // (point-major FP32 layout, 16-byte aligned): each row's full lower (forward) or
 // upper (backward) part, including the same-point entries computed just before.
-// HALO: x carries kHalo zero cells around the box, so every neighbour is read
-// at a fixed offset from lp (an entry whose column lies outside the box holds 0
-// in the factors and meets 0 in x); otherwise the neighbour is bounds-checked
-// against the box and an outside column reads x at lp itself (times 0).
+// HALO: every neighbour is read at a fixed offset from lp.  An entry whose
+// column lies outside the box holds an exact 0 in the factors; in 1-D and 2-D
+// it meets one of the kHalo zero cells around the box, in 3-D another finite
+// cell of the zero-filled planes or a zero guard cell (0 times a finite value).
+// Otherwise the neighbour is bounds-checked against the box and an outside
+// column reads x at lp itself (times 0).
 template <int D, int NF, bool FWD, bool HALO>
 __device__ __forceinline__ void point_rows_pm(const float *__restrict__ Bk, float *x, int npx, int lp, int lx, int ly,
                                               int lz, const SubInfo &si, int sy, int sz)
@@ -954,9 +971,11 @@ __device__ __forceinline__ void point_rows_pm(const float *__restrict__ Bk, floa
             constexpr int dx = PT.dx[a], dy = PT.dy[a], dz = PT.dz[a], fc = PT.fc[a];
             int idx;
             if constexpr (HALO) {
-                static_assert(dz == 0 && dx >= -kHalo && dx <= kHalo && dy >= -kHalo && dy <= kHalo,
+                static_assert(D == 3 || (dz == 0 && dx >= -kHalo && dx <= kHalo && dy >= -kHalo && dy <= kHalo),
                               "stencil reach beyond the halo");
-                idx = lp + dx + sy * dy;
+                static_assert((dx < 0 ? -dx : dx) + (dy < 0 ? -dy : dy) + (dz < 0 ? -dz : dz) <= 2,
+                              "stencil reach beyond the guard cells");
+                idx = lp + dx + sy * dy + sz * dz;
             } else {
                 const bool ok = nb_inbox<dx, dy, dz>(lx, ly, lz, si);
                 idx = ok ? lp + dx + sy * dy + sz * dz : lp;
@@ -977,18 +996,19 @@ __device__ __forceinline__ void point_rows_pm(const float *__restrict__ Bk, floa
 // are larger, prefetched into L2 kPrefetch3 levels ahead), issued by the block's last thread
 // (its warp has the fewest points of a level, warp 0 the most); the level tables
 // are copied to shared memory first (global loads on every level's critical path
-// cost more than the arithmetic).  XS: x in shared memory; HALO: x on the halo
-// layout (1-D and 2-D), the point table then holds 16-bit x indices.
+// cost more than the arithmetic).  XS: x in shared memory; HALO: x on the
+// branch-free layout (1-D and 2-D: kHalo zero cells around the box; 3-D: the
+// box planes between `guard` zero cells on each side), the point table then
+// holds 16-bit x indices.
 template <int D, int NF, int NBUF, bool XS, bool HALO>
 __global__ void __launch_bounds__(256) k_ras_apply_lane(DGrid g, Bat bt, const SubInfo *__restrict__ subs, const int *__restrict__ lvl_ptr,
                             const long long *__restrict__ lvl_blk, const int *__restrict__ lvl_lp,
                             const float *__restrict__ fac, const float *__restrict__ r, float *__restrict__ z,
                             float *__restrict__ scratch, int maxnp, int maxnlev, long long maxblk, int *flag,
                             double *__restrict__ cpart, double *__restrict__ csum, unsigned int *ticket,
-                            int withhold, int variant)
+                            int withhold, int variant, int guard)
 {
     static_assert(XS || !HALO, "the halo layout lives in shared memory");
-    static_assert(D <= 2 || !HALO, "the halo layout covers 1-D and 2-D boxes");
     using T = float;
     using LT = typename std::conditional<HALO, unsigned short, int>::type;
     using L = PM<D, NF>;
@@ -1013,7 +1033,7 @@ __global__ void __launch_bounds__(256) k_ras_apply_lane(DGrid g, Bat bt, const S
                                           pad16(2 * sizeof(int) * (size_t)(maxnlev + 1)));
     const SubInfo si = subs[blockIdx.x];
     T *x;
-    if constexpr (XS) x = buf0 + NBUF * bstride;
+    if constexpr (XS) x = buf0 + NBUF * bstride + (HALO && D == 3 ? guard : 0);
     else x = scratch + si.scr_off;
     const int np = si.np, nlev = si.nlev;
     const int *lptr = lvl_ptr + si.lvl_off;
@@ -1023,7 +1043,7 @@ __global__ void __launch_bounds__(256) k_ras_apply_lane(DGrid g, Bat bt, const S
     // x layout: NF planes of npx entries, local (lx, ly, lz) at l0 + lx + sy ly + sz lz
     const int sy = HALO ? si.qx : si.px, sz = HALO ? si.qx * si.qy : si.px * si.py;
     const int npx = HALO ? si.nqx : si.npx;
-    const int l0 = HALO ? kHalo * (1 + (D >= 2 ? si.qx : 0)) : 0;
+    const int l0 = HALO && D <= 2 ? kHalo * (1 + (D >= 2 ? si.qx : 0)) : 0;
     const int tid = threadIdx.x;
     const int prod = blockDim.x - 1;  // the copy-issuing thread
     const int nuse = 2 * nlev;  // forward parts of levels 0..nlev-1, then backward parts of nlev-1..0
@@ -1065,25 +1085,42 @@ __global__ void __launch_bounds__(256) k_ras_apply_lane(DGrid g, Bat bt, const S
         for (int q = 0; q < NBUF - 1 && q < nuse; q++) issue(q);
     for (int i = tid; i < np; i += blockDim.x) {
         const int pk = lvl_lp[si.pos_off + i];
-        if constexpr (HALO) lps[i] = (LT)(l0 + (pk & 1023) + sy * ((pk >> 10) & 1023));
+        if constexpr (HALO) lps[i] = (LT)(l0 + (pk & 1023) + sy * ((pk >> 10) & 1023) + sz * (pk >> 20));
         else lps[i] = pk;
     }
     auto owned = [&](int lx, int ly, int lz) {
         return lx >= si.own0[0] && lx < si.own1[0] && ly >= si.own0[1] && ly < si.own1[1] && lz >= si.own0[2] &&
                lz < si.own1[2];
     };
-    // gather R_i^delta r (right-RAS: R_i^0 r, the owned points only); with the halo
-    // layout every cell of the planes is written (zero outside the box)
+    // gather R_i^delta r (right-RAS: R_i^0 r, the owned points only); with the
+    // branch-free layout every cell of the planes is written (zero outside the box),
+    // and in 3-D the guard cells before and after the planes are zeroed
     if constexpr (HALO) {
+        const int qy = D == 3 ? si.qy : 1;
         for (int q = tid; q < npx; q += blockDim.x) {
-            const int lx = q % sy - kHalo, ly = D >= 2 ? q / sy - kHalo : 0;
-            const bool in = lx >= 0 && lx < si.L[0] && ly >= 0 && ly < si.L[1];
-            const bool take = in && (variant != NKS_RIGHT_RAS || owned(lx, ly, 0));
-            const long long gp =
-                take ? index_of(g, wrapi(si.org[0] + lx, g.n[0]), wrapi(si.org[1] + ly, g.n[1]), 0) : 0;
+            int lx, ly, lz;
+            if constexpr (D == 3) {
+                lx = q % sy;
+                ly = (q / sy) % qy;
+                lz = q / sz;
+            } else {
+                lx = q % sy - kHalo;
+                ly = D >= 2 ? q / sy - kHalo : 0;
+                lz = 0;
+            }
+            const bool in = lx >= 0 && lx < si.L[0] && ly >= 0 && ly < si.L[1] && lz < si.L[2];
+            const bool take = in && (variant != NKS_RIGHT_RAS || owned(lx, ly, lz));
+            const long long gp = take ? index_of(g, wrapi(si.org[0] + lx, g.n[0]), wrapi(si.org[1] + ly, g.n[1]),
+                                                 wrapi(si.org[2] + lz, g.n[2]))
+                                      : 0;
 #pragma unroll
             for (int f = 0; f < NF; f++) x[f * npx + q] = take ? (T)r[f * N + gp] : (T)0;
         }
+        if constexpr (D == 3)
+            for (int q = tid; q < guard; q += blockDim.x) {
+                x[q - guard] = (T)0;
+                x[NF * npx + q] = (T)0;
+            }
     } else {
         for (int q = tid; q < np; q += blockDim.x) {
             const int lx = q % si.L[0], ly = (q / si.L[0]) % si.L[1], lz = q / (si.L[0] * si.L[1]);
@@ -1394,17 +1431,15 @@ void launch_factor(Problem *P, int mode, const Bat &bt)
 
 using LaneKernel = void (*)(DGrid, Bat, const SubInfo *, const int *, const long long *, const int *, const float *,
                            const float *, float *, float *, int, int, long long, int *, double *, double *,
-                           unsigned int *, int, int);
+                           unsigned int *, int, int, int);
 
-// the FP32 sweep instantiation of the plan's layout (halo D <= 2 only; three
-// buffers only with x in shared memory)
+// the FP32 sweep instantiation of the plan's layout (three buffers and the
+// branch-free layout only with x in shared memory)
 template <int D, int NF>
 LaneKernel lane_kernel(const RasPlan *R)
 {
-    if constexpr (D <= 2) {
-        if (R->halo32) return R->lane_bufs == 3 ? k_ras_apply_lane<D, NF, 3, true, true>
-                                                : k_ras_apply_lane<D, NF, 2, true, true>;
-    }
+    if (R->halo32) return R->lane_bufs == 3 ? k_ras_apply_lane<D, NF, 3, true, true>
+                                            : k_ras_apply_lane<D, NF, 2, true, true>;
     if (!R->x_smem32) return k_ras_apply_lane<D, NF, 2, false, false>;
     return R->lane_bufs == 3 ? k_ras_apply_lane<D, NF, 3, true, false> : k_ras_apply_lane<D, NF, 2, true, false>;
 }
@@ -1459,7 +1494,8 @@ void launch_apply_t(Problem *P, const TV *r, TV *z, const Bat &bt)
         lane_kernel<D, NF>(R)<<<dim3(R->nsub, bt.nb), tl, smem, P->stream>>>(
             P->g, bt, R->sub, R->lvl_ptr, R->lvl_blk, R->lvl_lp, reinterpret_cast<const float *>(fac),
             reinterpret_cast<const float *>(r), reinterpret_cast<float *>(z), reinterpret_cast<float *>(scr), R->maxnp,
-            R->maxnlev, R->maxblk32, P->dflag, P->partials, P->zsum, P->tickets + 3, P->withhold_copy, P->opts.ras_variant);
+            R->maxnlev, R->maxblk32, P->dflag, P->partials, P->zsum, P->tickets + 3, P->withhold_copy, P->opts.ras_variant,
+            R->guard32);
     } else {
         auto kern = xs ? k_ras_apply<D, NF, T, TV, true> : k_ras_apply<D, NF, T, TV, false>;
         kern<<<dim3(R->nsub, bt.nb), threads, smem, P->stream>>>(
