@@ -2,23 +2,26 @@
 """Benchmark of the GB300 NKS time step (arXiv 2209.08001, Sec. 4).
 
 Metric: point-steps/s = grid points x accepted time steps / seconds of the
-step loop.  Default workload: the 2-D 1024x1024 periodic FP64 configuration
-(200 adaptive DVD steps with the energy-change dt driver, GMRES(30), RAS on
-16x16 subdomains with overlap 2, ILU(0)-reuse); seeded synthetic initial
-fields.  A bench "step" is one accepted time step (one NKS solve).  Timed
-steps start from the workload's initial state (steps 1..K), after W warm-up
-steps whose state is discarded.
+step loop, with the mixed-precision solver (FP32 Schwarz factors, sweeps and
+Krylov basis; FP64 residual, update, logarithms, energy and mass) beside the
+plain FP64 solver on the same steps.  Default workload: the 3-D 128^3 periodic
+configuration (c = 0.18 + U(-0.005, 0.005), seed 2, 50 adaptive DVD steps with
+the energy-change dt driver, GMRES(30), left-RAS on 8x8x8 subdomains with
+overlap 1, ILU(0)-reuse); seeded synthetic initial fields.  A bench "step" is
+one accepted time step (one NKS solve).  Timed steps start from the workload's
+initial state (steps 1..K), after W warm-up steps whose state is discarded;
+the FP64 solver replays the mixed run's dt sequence.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--config 3d128] [--precision mixed|fp64] [--grid SIDE]
 
 N > 1 runs one independent replica per GPU (launched by torch.distributed.run;
 the method has no data-path exchange on one GPU per problem), weak scaling.
---impl reference times the FP64 CPU oracle on the host cores on a bounded
-sample of the same workload.  One JSON line is printed by rank 0.
+--impl reference times the FP64 CPU oracle on the host cores (real time steps
+of a bounded sample of the workload).  One JSON line is printed by rank 0.
 """
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -37,18 +40,37 @@ import synthetic as S  # noqa: E402
 METRIC = "point-steps/s"
 # FP64 FMA peak derived from the unit counts: 152 SMs x 2 FP64 FMA/clk x 2 FLOP x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-# DRAM traffic per launch of the dominant kernel (dram__bytes.sum.per_second x duration),
-# keyed by (workload, precision, kernel class), from one ncu capture of the 1024^2 probe
-# (bench.py --probe gmres1024: the bench workload's own 256-box launch); an entry is
-# removed whenever the kernel changes
-NCU_TRAFFIC = {("2d1024", "fp64", "schwarz_apply"): 932.815680e9 * 969.792e-6,
-               ("2d1024", "mixed", "schwarz_apply"): 1435.653e9 * 275.168e-6}
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+FIELDS = ("c", "eta", "u1", "u2", "u3")
+
+
+def peaks():
+    try:
+        pk = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        pk.setdefault("source", "measured (MEASURED_PEAKS.json)")
+        return pk
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback (no MEASURED_PEAKS.json)"}
+
+
+def workload(name, side=None):
+    """The workload's description, optionally on a smaller cubic / square grid of
+    `side` cells per axis with the same Schwarz box size (sub = side / box)."""
+    cfg = dict(S.CONFIGS[name])
+    cfg["opts"] = dict(cfg["opts"])
+    if side:
+        d = cfg["dim"]
+        box = [cfg["n"][J] // cfg["opts"]["sub"][J] for J in range(d)]
+        cfg["n"] = tuple([side] * d)
+        cfg["opts"]["sub"] = tuple(max(1, side // b) for b in box)
+        cfg["desc"] = "%s [on a %s grid, sub %s]" % (cfg["desc"], "x".join([str(side)] * d),
+                                                    "x".join(str(v) for v in cfg["opts"]["sub"]))
+    return cfg
 
 
 def kernel_rates(st, cfg, mixed, pk):
     """Achieved rates per kernel class from the CUDA-event times of the timed steps:
-    HBM-bound classes against the measured copy bandwidth, FP64-bound ones against
-    the derived FP64 peak (algorithmic bytes / FLOPs per unit as in the design notes)."""
+    algorithmic bytes per unit (as in the design notes) over the class's device time."""
     d = cfg["dim"]
     N = float(np.prod(cfg["n"]))
     f = 2 + d
@@ -71,25 +93,70 @@ def kernel_rates(st, cfg, mixed, pk):
     # Jacobian action: (2f + 5) words per point per application (v, 4 coefficients + edge
     # mobility, J v), FP32 words in the Arnoldi step of the mixed mode
     rate("jacobian_action", st["launches"]["jacobian_action"] * (2 * f + 5) * b * N,
-         bound="hbm" if mixed else "alu")
+         bound="hbm" if mixed else "fp64")
     # Gram-Schmidt: (2j + 5) basis-vector transfers per pass of Arnoldi step j (counted by the library)
     gs_ms = st["ms"].get("gs_dots", 0.0) + st["ms"].get("gs_update", 0.0)
     if gs_ms > 0 and st.get("cgs_bytes", 0) > 0:
         gbs = st["cgs_bytes"] / (gs_ms / 1e3) / 1e9
         out["gram_schmidt"] = {"algorithmic_bytes": st["cgs_bytes"], "ms": gs_ms, "achieved_gbs": gbs,
-                               "hbm_frac": gbs / hbm if hbm else None, "bound": "hbm" if mixed else "alu",
+                               "hbm_frac": gbs / hbm if hbm else None, "bound": "hbm" if mixed else "fp64",
                                "second_passes": st.get("reorth"), "arnoldi_steps": st["gmres_its"]}
-    # Schwarz sweeps
     rate("schwarz_apply", st["launches"]["schwarz_apply"] * st["schwarz_bytes"],
-         None if mixed else st["launches"]["schwarz_apply"] * st["schwarz_flops"], bound="hbm" if mixed else "alu")
+         None if mixed else st["launches"]["schwarz_apply"] * st["schwarz_flops"],
+         bound="hbm" if mixed else "fp64")
     return out
 
 
-def peaks():
+def traffic_for(workload_name, side, precision, kernel):
+    """DRAM bytes per launch of `kernel` from the ncu summary recorded for this
+    workload, precision and the library's current source hash; None (with the
+    reason) when no capture of the current kernels exists."""
+    from paper_2209_08001_gb300 import build
+    h = build.source_hash()
     try:
-        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        entries = json.load(open(TRAFFIC_FILE))["entries"]
     except Exception:
-        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
+        return None, "no ncu traffic record (profiles/traffic.json)"
+    for e in entries:
+        if (e["workload"], e.get("side"), e["precision"], e["kernel"]) == (workload_name, side, precision, kernel):
+            if e["source_hash"] != h:
+                return None, "ncu capture %s is of other kernel sources (%s, now %s)" % (e["profile"],
+                                                                                       e["source_hash"], h)
+            return e["dram_bytes_per_launch"], "ncu dram__bytes_read.sum + dram__bytes_write.sum, %s" % e["profile"]
+    return None, "no ncu traffic record for this workload, precision and kernel"
+
+
+def roofline(st, kernels, mixed, pk, wl, side, precision):
+    """Roofline of the dominant kernel class of the timed steps."""
+    cls = max(st["ms"], key=lambda k: st["ms"][k])
+    launches = max(st["launches"][cls], 1)
+    avg_s = st["ms"][cls] / launches / 1e3
+    if cls == "schwarz_apply":
+        by, fl = st["schwarz_bytes"], st["schwarz_flops"]
+        if mixed:
+            tr, why = traffic_for(wl, side, precision, "k_ras_apply_lane")
+            roof = {"kernel": "k_ras_apply_lane<FP32> (ILU(0) sweeps, TMA-staged point-major factors)",
+                    "bound": "hbm", "achieved": by / avg_s / 1e9, "peak": pk.get("hbm_gbs"), "unit": "GB/s",
+                    "frac": by / avg_s / 1e9 / pk.get("hbm_gbs"),
+                    "peak_source": "%s, copy bandwidth" % pk.get("source"),
+                    "limiter": "wavefront latency: one block barrier per level of the triangular sweeps",
+                    "algorithmic_bytes_per_launch": by, "algorithmic_flops_per_launch": fl}
+        else:
+            tr, why = traffic_for(wl, side, precision, "k_ras_apply")
+            roof = {"kernel": "k_ras_apply<FP64> (ILU(0) sweeps, TMA-staged factors)", "bound": "alu",
+                    "achieved": fl / avg_s / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": fl / avg_s / 1e12 / FP64_PEAK_TFLOPS,
+                    "peak_source": "derived FP64 FMA peak: 152 SMs x 2 FP64 FMA/clk x 2 FLOP x 2.07 GHz "
+                                   "(a measured FMA loop reached 1.20)",
+                    "limiter": "FP64 pipe and wavefront latency (barriers between levels)",
+                    "algorithmic_flops_per_launch": fl, "algorithmic_bytes_per_launch": by,
+                    "hbm_achieved_gbs": by / avg_s / 1e9, "hbm_peak_gbs": pk.get("hbm_gbs")}
+    else:
+        tr, why = None, "no ncu traffic record for this kernel class"
+        roof = dict(kernels.get(cls, {}), kernel=cls)
+    roof.update({"traffic": tr, "traffic_source": why, "avg_launch_ms": avg_s * 1e3, "launches": launches,
+                 "timing": "CUDA events around every launch of the class on the solver's stream"})
+    return roof
 
 
 class ClockSampler:
@@ -174,45 +241,176 @@ def sum_over_ranks(dist, value, device=None):
     return float(t.item())
 
 
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def field_dict(c, e, u):
+    out = {"c": c, "eta": e}
+    if u is not None:
+        for I in range(len(u)):
+            out["u%d" % (I + 1)] = u[I]
+    return out
+
+
 # ---------------------------------------------------------------------------
-# CPU oracle sample (cpu_baseline and --impl reference)
+# CPU oracle on a bounded sample of the workload (cpu_baseline, --impl reference)
 # ---------------------------------------------------------------------------
 
-def oracle_sample(cfg, gmres_per_step, newton_per_step, its=(2, 6)):
-    """Times the FP64 oracle on the full-size workload: Jacobian assembly, the
-    RAS/ILU(0) set-up and GMRES iterations of the first Newton solve, at two
-    iteration caps.  One time step is then estimated as newton_per_step set-ups
-    (assembly + factorisation) plus gmres_per_step GMRES iterations (the counts
-    of the same algorithm on the same workload)."""
+def cpu_sample_config(name):
+    """The bounded sample of a workload that the CPU oracle runs: the same recipe
+    (initial state, coefficients, solver settings, Schwarz box size and overlap)
+    on a periodic grid of three boxes per axis (3-D 48^3 for 16^3 boxes, 2-D
+    192^2 for 64^2 boxes), or the workload itself when it is no larger."""
+    cfg = S.CONFIGS[name]
+    d = cfg["dim"]
+    box = [cfg["n"][J] // cfg["opts"]["sub"][J] for J in range(d)]
+    side = 3 * max(box)
+    if side >= max(cfg["n"][:d]):
+        return cfg, None
+    return workload(name, side), side
+
+
+def oracle_steps(cfg, warmup, steps, threads=None):
+    """Real oracle time steps: the initial mechanical equilibrium (set-up, not
+    timed), then warmup + steps NKS steps with the workload's dt rule (dt_init,
+    then the oracle's predictor of Eq. sencondt, divergence retries), each timed.
+    Returns (per-step seconds of the timed steps, infos, set-up seconds, threads)."""
     import oracle
+    oracle.set_threads(threads or 0)
     op = S.options(**cfg["opts"])
+    op["precision"] = "fp64"
     c, e = S.config_fields(cfg)
-    N = c.size
-    times = []
-    O = None
-    for m in its:
-        O = oracle.Problem(cfg["dim"], cfg["n"], cfg["h"], S.config_coefficients(cfg), dict(op, gmres_maxit=m))
-        X = O.interleave(c, e)
-        cb = float(np.sum(c) / N)
-        F = O.residual(X, X, cb, op["dt_init"])
+    O = oracle.Problem(cfg["dim"], cfg["n"], cfg["h"], S.config_coefficients(cfg), op)
+    X = O.interleave(c, e)
+    cb = float(np.sum(c) / c.size)
+    t0 = time.perf_counter()
+    rc, X, _ = O.equilibrate(X, cb)
+    t_setup = time.perf_counter() - t0
+    if rc != 0:
+        raise RuntimeError("oracle equilibrium failed (%d)" % rc)
+    E, Eprev, dt_prev, zeta = O.energy(X, cb), None, op["dt_init"], op["zeta"]
+    secs, infos = [], []
+    for st in range(warmup + steps):
+        if st == 0 or op["dt_mode"] == "fixed":
+            dt = op["dt_init"]
+        else:
+            dt = oracle.dt_predict(op["dt_min"], op["dt_max"], zeta, abs(E - Eprev) / dt_prev)
+        zeta = op["zeta"]
         t0 = time.perf_counter()
-        O.linear_solve(X, X, cb, op["dt_init"], -F, 0.0)
-        times.append(time.perf_counter() - t0)
-    t_it = max((times[1] - times[0]) / (its[1] - its[0]), 1e-9)
-    t_setup = max(times[0] - its[0] * t_it, 0.0)
-    step_s = newton_per_step * t_setup + gmres_per_step * t_it
-    return {"value": N / step_s, "unit": METRIC, "cores": 1, "kind": "oracle",
-            "sample": ("full-size %s workload, first Newton solve: Jacobian assembly + RAS/ILU(0) set-up + %d and %d "
-                       "GMRES iterations timed (%.1f s, %.1f s); step = %.2f set-ups + %.1f iterations (per-step "
-                       "counts of the same method); single-threaded FP64 C oracle"
-                       % ("x".join(str(v) for v in cfg["n"]), its[0], its[1], times[0], times[1],
-                          newton_per_step, gmres_per_step)),
-            "seconds_per_step": step_s, "t_setup_s": t_setup, "t_gmres_iteration_s": t_it}
+        for _ in range(op["max_retries"] + 1):
+            rc, Xn, info = O.newton_step(X, cb, dt)
+            if rc == 0:
+                break
+            dt /= 2 ** 0.5
+            zeta *= 2.0
+        if rc != 0:
+            raise RuntimeError("oracle step failed (%d)" % rc)
+        Eprev, E = E, O.energy(Xn, cb)
+        dt_prev, X = dt, Xn
+        el = time.perf_counter() - t0
+        if st >= warmup:
+            secs.append(el)
+            infos.append(info)
+    return secs, infos, t_setup, oracle.num_threads()
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part", "hardware")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def cpu_baseline(name, steps=2):
+    cfg, side = cpu_sample_config(name)
+    N = int(np.prod(cfg["n"]))
+    secs, infos, t_setup, thr = oracle_steps(cfg, 0, steps)
+    v = N * len(secs) / sum(secs)
+    out = {"value": v, "unit": METRIC, "cores": thr, "kind": "oracle",
+           "sample": ("%d real FP64 oracle time steps (all %d host threads, OpenMP) of the workload's recipe on a "
+                      "periodic %s grid (%d points, the workload's Schwarz box size: %s); %.1f s of steps, "
+                      "%.1f s equilibrium set-up untimed; %.1f Newton, %.0f GMRES per step; the full-size grid has "
+                      "more boxes per axis and needs more GMRES iterations per Newton solve"
+                      % (len(secs), thr, "x".join(str(v) for v in cfg["n"]), N, cfg["desc"].split("[")[-1].rstrip("]")
+                         if side else "the workload itself", sum(secs), t_setup,
+                         np.mean([i["newton_its"] for i in infos]), np.mean([i["gmres_its"] for i in infos]))),
+           "nproc": os.cpu_count(), "cpu_model": cpu_model()}
+    # one thread on the small 2-D workload (64^2, 16^2 boxes), for the per-core rate
+    import oracle
+    try:
+        secs1, infos1, _, thr1 = oracle_steps(S.CONFIGS["2d64"], 0, 2, threads=1)
+        out["single_thread_2d64"] = {"value": 4096 * len(secs1) / sum(secs1), "unit": METRIC, "cores": thr1,
+                                     "sample": "2 real oracle steps of the 2-D 64^2 workload on one thread"}
+    finally:
+        oracle.set_threads(0)
+    return out
 
 
 # ---------------------------------------------------------------------------
 # the GPU arm
 # ---------------------------------------------------------------------------
+
+def timed_run(P, steps, warmup, stream, dts=None):
+    """W warm-up steps (state restored afterwards), then K steps between CUDA
+    events on the solver's stream (dts: replay those step sizes)."""
+    import torch
+    state0 = P.get_state()
+    for i in range(warmup):
+        P.step(dts[i] if dts and i < len(dts) else 0.0)
+    P.set_state(state0)
+    P.reset_stats()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    infos = [P.step(dts[i] if dts else 0.0) for i in range(steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1), infos
+
+
+def golden_accuracy(nks, name, cfg, op, stream, alloc):
+    """Per-field error against the full-size FP64 oracle reference of the
+    workload (tests/golden/full_<workload>.json, written by the oracle alone):
+    both GPU solvers replay the oracle's dt sequence for its steps; the relative
+    L2 error per field is estimated from the reference's 256-row sign sketch,
+    and the error at its 1024 sampled points is exact."""
+    path = os.path.join(ROOT, "tests", "golden", "full_%s.json" % name)
+    if not os.path.exists(path):
+        return None
+    G = json.load(open(path))
+    dts = [s["dt"] for s in G["per_step"]]
+    c, e = S.config_fields(cfg)
+    idx = np.array(G["samples"]["index"], dtype=np.int64)
+    out = {"reference": "FP64 oracle, %d steps of the full-size workload (dt replayed), %s" % (len(dts), G["_source"]),
+           "estimator": "relative L2 from a %d-row seeded sign sketch (Johnson-Lindenstrauss; the estimate lies "
+                        "within a factor 0.7..1.3 of the true value with probability > 1 - 1e-6); max relative "
+                        "error over %d sampled points" % (G["sketch"]["k"], idx.size)}
+    for prec in ("mixed", "fp64"):
+        Q = nks.Problem(cfg["dim"], cfg["n"], cfg["h"], c, e, S.config_coefficients(cfg), dict(op, precision=prec),
+                        stream=stream.cuda_stream, allocator=alloc)
+        infos = [Q.step(dt) for dt in dts]
+        fl = field_dict(*Q.get_fields())
+        Q.destroy()
+        sk = S.sign_sketch([fl[f] for f in G["fields"]], G["sketch"]["k"], G["sketch"]["seed"])
+        r = {}
+        for i, f in enumerate(G["fields"]):
+            ref = G["fields"][f]
+            scale = ref["norm"] / np.sqrt(fl[f].size)
+            r[f] = {"rel_l2_est": float(np.linalg.norm(sk[i] - np.array(ref["sketch"])) / ref["norm"]),
+                    "max_rel_at_samples": float(np.max(np.abs(fl[f][idx] - np.array(ref["at_samples"]))) / scale)}
+        r["energy_rel"] = max(abs(i["energy"] - s["energy"]) / abs(s["energy"]) for i, s in zip(infos, G["per_step"]))
+        r["mass_rel"] = max(abs(i["mass"] - s["mass"]) / abs(s["mass"]) for i, s in zip(infos, G["per_step"]))
+        r["max_rel_l2_est"] = max(r[f]["rel_l2_est"] for f in G["fields"])
+        out[prec] = r
+    out["tolerance"] = 1e-8
+    out["within_tolerance"] = all(out[p]["max_rel_l2_est"] <= 1e-8 for p in ("mixed", "fp64"))
+    return out
+
 
 def run_ours(args):
     import torch
@@ -227,16 +425,18 @@ def run_ours(args):
         dist.barrier()
     import paper_2209_08001_gb300 as nks
 
-    cfg = S.CONFIGS[args.config]
+    cfg = workload(args.config, args.grid)
     op = S.options(**cfg["opts"])
-    if args.precision:
-        op["precision"] = args.precision
+    prec = args.precision or "mixed"
+    op["precision"] = prec
     if args.variant:
         op["ras_variant"] = args.variant
     if args.overlap is not None:
         op["overlap"] = args.overlap
     if args.u0_maxit is not None:
         op["u0_maxit"] = args.u0_maxit
+    if args.gmres_maxit is not None:
+        op["gmres_maxit"] = args.gmres_maxit
     c, e = S.config_fields(cfg, 1000 * rank)  # independent replica per rank (seeded workloads)
     N = c.size
     tuned = None
@@ -250,125 +450,107 @@ def run_ours(args):
                  "chosen": {"sub": list(op["sub"]), "overlap": op["overlap"]}}
     stream = torch.cuda.current_stream()
     alloc = nks.torch_allocator()
-    torch.cuda.synchronize()
-    t_setup = time.perf_counter()
-    P = nks.Problem(cfg["dim"], cfg["n"], cfg["h"], c, e, S.config_coefficients(cfg), op, stream=stream.cuda_stream,
-                    allocator=alloc, timing=True)
-    torch.cuda.synchronize()
-    t_setup = time.perf_counter() - t_setup
-    sst = P.get_stats()
-    setup = {"seconds": t_setup, "u0_newton_its": sst["newton_its"], "u0_gmres_its": sst["gmres_its"],
-             "device_bytes": P.device_bytes(),
-             "includes": "problem creation: plan, factor tables, upload, initial mechanical equilibrium (Newton on "
-                         "the displacement rows, tolerance u0_rtol)"}
-    state0 = P.get_state()
-    for _ in range(args.warmup):
-        P.step()
-    P.set_state(state0)
-    P.reset_stats()
+    dev = torch.device("cuda", local)
+    pk = peaks()
+
+    def create(o):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        P = nks.Problem(cfg["dim"], cfg["n"], cfg["h"], c, e, S.config_coefficients(cfg), o,
+                        stream=stream.cuda_stream, allocator=alloc, timing=True)
+        torch.cuda.synchronize()
+        sst = P.get_stats()
+        return P, {"seconds": time.perf_counter() - t0, "u0_newton_its": sst["newton_its"],
+                   "u0_gmres_its": sst["gmres_its"], "device_bytes": P.device_bytes(),
+                   "includes": "problem creation: plan, factor tables, upload, initial mechanical equilibrium "
+                               "(Newton on the displacement rows, tolerance u0_rtol)"}
+
+    def summary(P, ms, infos, mixed):
+        st = P.get_stats()
+        kernels = kernel_rates(st, cfg, mixed, pk)
+        total_ms = sum(st["ms"].values())
+        return st, {
+            "value": sum_over_ranks(dist, float(N * len(infos)), dev) / (max_over_ranks(dist, ms, dev) / 1e3),
+            "ms_per_step": max_over_ranks(dist, ms, dev) / len(infos),
+            "roofline": roofline(st, kernels, mixed, pk, args.config, args.grid, "mixed" if mixed else "fp64"),
+            "kernels": kernels,
+            "kernel_time_share": {k: round(v / max(total_ms, 1e-9), 4) for k, v in st["ms"].items() if v > 0},
+            "iterations": {"newton_per_step": st["newton_its"] / max(st["steps"], 1),
+                           "gmres_per_step": st["gmres_its"] / max(st["steps"], 1),
+                           "dt": [i["dt"] for i in infos]},
+            "gpu_launches": int(st["kernel_launches"])}
+
+    # --- the headline solver: K timed steps from the initial state ---------------
+    P, setup = create(op)
     clocks = ClockSampler(local)
     if dist is not None:
         dist.barrier()
-    torch.cuda.synchronize()
     clocks.start()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    infos = [P.step() for _ in range(args.steps)]
-    ev1.record(stream)
-    torch.cuda.synchronize()
+    ms, infos = timed_run(P, args.steps, args.warmup, stream)
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
     if dist is not None:
         dist.barrier()
-    ms_max = max_over_ranks(dist, ms, torch.device("cuda", local))
-    points_all = sum_over_ranks(dist, float(N * args.steps), torch.device("cuda", local))
-    st = P.get_stats()
-    value = points_all / (ms_max / 1e3)
+    mixed = prec == "mixed"
+    st, head = summary(P, ms, infos, mixed)
+    value = head["value"]
+    dts = [i["dt"] for i in infos]
 
-    # roofline of the dominant kernel class, and achieved rates of the others
-    pk = peaks()
-    mixed = op["precision"] == "mixed"
-    kernels = kernel_rates(st, cfg, mixed, pk)
-    cls = max(st["ms"], key=lambda k: st["ms"][k])
-    launches = max(st["launches"][cls], 1)
-    avg_s = st["ms"][cls] / launches / 1e3
-    if cls == "schwarz_apply" and not mixed:
-        # FP64 sweeps: 2 FLOP per stored factor entry per point; bound by the FP64 pipe on GB300
-        flops = st["schwarz_flops"]
-        roof = {"kernel": "k_ras_apply<FP64> (ILU(0) sweeps, TMA-staged factors)", "bound": "alu",
-                "achieved": flops / avg_s / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": flops / avg_s / 1e12 / FP64_PEAK_TFLOPS,
-                "peak_source": "derived FP64 FMA peak: 152 SMs x 2 FP64 FMA/clk x 2 FLOP x 2.07 GHz "
-                               "(a measured FMA loop reached 1.20)",
-                "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": st["schwarz_bytes"],
-                "hbm_achieved_gbs": st["schwarz_bytes"] / avg_s / 1e9, "hbm_peak_gbs": pk.get("hbm_gbs"),
-                "traffic": NCU_TRAFFIC.get((args.config, op["precision"], cls)), "avg_launch_ms": avg_s * 1e3,
-                "launches": launches}
-    elif cls == "schwarz_apply":
-        # FP32 sweeps (mixed precision): factors and sub-vectors streamed once per sweep
-        by = st["schwarz_bytes"]
-        roof = {"kernel": "k_ras_apply<FP32> (ILU(0) sweeps, TMA-staged factors)", "bound": "hbm",
-                "achieved": by / avg_s / 1e9, "peak": pk.get("hbm_gbs"), "unit": "GB/s",
-                "frac": by / avg_s / 1e9 / pk.get("hbm_gbs"), "peak_source": "measured copy bandwidth (burst)",
-                "algorithmic_bytes_per_launch": by, "algorithmic_flops_per_launch": st["schwarz_flops"],
-                "traffic": NCU_TRAFFIC.get((args.config, op["precision"], cls)), "avg_launch_ms": avg_s * 1e3,
-                "launches": launches}
-    else:
-        roof = dict(kernels.get(cls, {}), kernel=cls, traffic=NCU_TRAFFIC.get((args.config, op["precision"], cls)))
-    # mixed precision: error per field against the FP64 path on the same dt sequence
-    accuracy = None
-    if mixed and not args.no_accuracy and rank == 0:
-        cm, em, um = P.get_fields()
-        Q = nks.Problem(cfg["dim"], cfg["n"], cfg["h"], c, e, S.config_coefficients(cfg), dict(op, precision="fp64"),
-                        stream=stream.cuda_stream, allocator=alloc)
-        for i in infos:
-            Q.step(i["dt"])
-        cd, ed, ud = Q.get_fields()
+    # --- the FP64 solver beside it on the same steps (same K, W, dt sequence) ---
+    fp64 = None
+    accuracy = {}
+    if mixed and not args.no_fp64:
+        Q, qsetup = create(dict(op, precision="fp64"))
+        clocks64 = ClockSampler(local)
+        clocks64.start()
+        ms64, infos64 = timed_run(Q, args.steps, args.warmup, stream, dts=dts)
+        clk64 = clocks64.stop()
+        _, fp64 = summary(Q, ms64, infos64, False)
+        fp64.update({"setup": qsetup, "clocks": clk64, "dt_sequence": "replayed from the mixed-precision run",
+                     "mixed_over_fp64": value / fp64["value"]})
+        fm = field_dict(*P.get_fields())
+        fd = field_dict(*Q.get_fields())
+        accuracy["vs_fp64_gpu"] = {
+            "reference": "FP64 GPU path after the same K steps (same dt sequence)",
+            "rel_l2": {f: rel(fm[f], fd[f]) for f in fm}}
         Q.destroy()
-        rel = lambda a, b: float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
-        accuracy = {"reference": "FP64 GPU path (parity-tested against the FP64 oracle), same dt sequence, "
-                                 "after the K timed steps",
-                    "rel_l2": {"c": rel(cm, cd), "eta": rel(em, ed), "u": rel(um, ud) if um is not None else None},
-                    "tolerance": 1e-8}
-    total_ms = sum(st["ms"].values())
-    breakdown = {k: round(v / max(total_ms, 1e-9), 4) for k, v in st["ms"].items() if v > 0}
+    if not args.no_accuracy and rank == 0:
+        ga = golden_accuracy(nks, args.config if not args.grid else "-", cfg, op, stream, alloc)
+        if ga:
+            accuracy["vs_oracle"] = ga
+    accuracy["tolerance"] = 1e-8
 
-    # end to end through the public API with host buffers
+    # --- end to end through the public API with host buffers ---------------------
     e2e = None
     if not args.no_e2e:
         cpin = torch.from_numpy(c).pin_memory().numpy()
         epin = torch.from_numpy(e).pin_memory().numpy()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        Q = nks.Problem(cfg["dim"], cfg["n"], cfg["h"], cpin, epin, S.config_coefficients(cfg), op, stream=stream.cuda_stream,
-                        allocator=alloc)
-        outs = []
+        R = nks.Problem(cfg["dim"], cfg["n"], cfg["h"], cpin, epin, S.config_coefficients(cfg), op,
+                        stream=stream.cuda_stream, allocator=alloc)
         for _ in range(args.steps):
-            Q.step()
-            outs.append(Q.get_fields()[0])
+            R.step()
+            R.get_fields()
         torch.cuda.synchronize()
         t_e2e = time.perf_counter() - t0
-        Q.destroy()
-        t_e2e = max_over_ranks(dist, t_e2e, torch.device("cuda", local))
-        e2e = {"value": points_all / t_e2e, "unit": METRIC,
-               "h2d_bytes_per_step": int(2 * N * 8 / args.steps),
-               "d2h_bytes_per_step": int((2 + (cfg["dim"] if S.config_coefficients(cfg).get("Lscale", 1.0) else 0)) * N * 8),
+        R.destroy()
+        t_e2e = max_over_ranks(dist, t_e2e, dev)
+        nfr = 2 + (cfg["dim"] if S.config_coefficients(cfg).get("Lscale", 1.0) else 0)
+        e2e = {"value": sum_over_ranks(dist, float(N * args.steps), dev) / t_e2e, "unit": METRIC,
+               "h2d_bytes_per_step": int(2 * N * 8 / args.steps), "d2h_bytes_per_step": int(nfr * N * 8),
                "includes": "problem creation from host fields (upload + initial mechanical equilibrium solve), "
-                           "K steps, fields read back to host after every step"}
+                           "K adaptive steps, all fields read back to host after every step"}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        gm = st["gmres_its"] / max(st["steps"], 1)
-        nw = st["newton_its"] / max(st["steps"], 1)
-        cpu = oracle_sample(cfg, gm, nw)
-        cpu = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        cpu = cpu_baseline(args.config)
 
     out = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if op["precision"] == "fp64" else "f64+f32",
+        "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64+f32" if mixed else "f64",
         "data": "synthetic (seeded SplitMix64 initial fields)",
-        "config": {"workload": cfg["desc"], "precision": op["precision"], "grid": list(cfg["n"]), "points": N,
+        "config": {"workload": cfg["desc"], "precision": prec, "grid": list(cfg["n"]), "points": N,
                    "decomposition": {"sub": list(op["sub"]), "overlap": op["overlap"],
                                      "schwarz": op.get("ras_variant", "left-ras")},
                    "steps_in_workload": cfg["steps"],
@@ -376,24 +558,22 @@ def run_ours(args):
                    "initial_equilibrium": ("Newton on the displacement rows, FP64 residual to u0_rtol, inner GMRES in "
                                            "the mixed form" if op.get("u0_mixed") else
                                            "Newton on the displacement rows in the solver's precision"),
-                   "l2": "working set (state, Krylov basis, ~0.65 GB of Schwarz factors) far above the 129 MB L2",
+                   "l2": "inputs larger than L2: the working set (state, Krylov basis, Schwarz factors; %.1f GB) is "
+                         "far above the 129 MB L2" % (setup["device_bytes"] / 1e9),
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
-        "gpu_launches": None,
+        "gpu_launches": head["gpu_launches"],
         "setup": setup,
         "autotune": tuned,
-        "roofline": roof,
-        "kernels": kernels,
+        "roofline": head["roofline"],
+        "kernels": head["kernels"],
+        "kernel_time_share": head["kernel_time_share"],
+        "iterations": head["iterations"],
+        "fp64": fp64,
         "accuracy": accuracy,
-        "kernel_time_share": breakdown,
-        "iterations": {"newton_per_step": st["newton_its"] / max(st["steps"], 1),
-                       "gmres_per_step": st["gmres_its"] / max(st["steps"], 1),
-                       "dt": [i["dt"] for i in infos]},
         "clocks": clk,
         "e2e": e2e,
         "cpu_baseline": cpu,
     }
-    # kernels this library launched inside the timed region (counted at every launch site)
-    out["gpu_launches"] = int(st["kernel_launches"])
     P.destroy()
     if rank == 0:
         print(json.dumps(out), flush=True)
@@ -402,24 +582,29 @@ def run_ours(args):
 
 
 def run_reference(args):
+    """The oracle (the paper's method in plain FP64 C) on the host cores: W
+    warm-up and K timed real time steps of the bounded sample of the workload."""
     ws, rank, local = dist_env()
     if rank != 0:
         return
-    cfg = S.CONFIGS[args.config]
-    # per-step iteration counts of the method on this workload (same algorithm as the oracle)
-    gm, nw = args.ref_gmres_per_step, args.ref_newton_per_step
-    samples = []
-    for _ in range(args.warmup + args.steps):
-        samples.append(oracle_sample(cfg, gm, nw, its=(1, 3)))
-    timed = samples[args.warmup:]
-    step_s = statistics.mean(s["seconds_per_step"] for s in timed)
+    cfg, side = cpu_sample_config(args.config)
     N = int(np.prod(cfg["n"]))
+    secs, infos, t_setup, thr = oracle_steps(cfg, args.warmup, args.steps)
+    step_s = sum(secs) / len(secs)
     v = N / step_s
+    sample = ("%d real FP64 oracle time steps after %d warm-up steps (all %d host threads, OpenMP) of the workload's "
+              "recipe on a periodic %s grid (%d points) with the workload's Schwarz box size; %.1f Newton, %.0f GMRES "
+              "per step" % (len(secs), args.warmup, thr, "x".join(str(x) for x in cfg["n"]), N,
+                            np.mean([i["newton_its"] for i in infos]), np.mean([i["gmres_its"] for i in infos])))
+    full = workload(args.config)
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded SplitMix64 initial fields)",
-           "config": {"workload": cfg["desc"], "grid": list(cfg["n"]), "points": N},
-           "cpu_baseline": {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": timed[0]["sample"]},
+           "config": {"workload": full["desc"], "grid": list(full["n"]), "points": int(np.prod(full["n"])),
+                      "sample_grid": list(cfg["n"]), "sample_points": N},
+           "cpu_baseline": {"value": v, "unit": METRIC, "cores": thr, "kind": "oracle", "sample": sample,
+                            "nproc": os.cpu_count(), "cpu_model": cpu_model()},
+           "setup_s": t_setup,
            "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -433,7 +618,7 @@ def run_batch(args):
     import __graft_entry__ as g
     g.build()
     torch.cuda.set_device(0)
-    cfg = S.CONFIGS[args.config]
+    cfg = workload(args.config, args.grid)
     op = S.options(**cfg["opts"])
     if args.precision:
         op["precision"] = args.precision
@@ -526,21 +711,20 @@ def run_serve(args):
         th.start()
         th.join()
         res = [srv.wait(ids[r["id"]])[0] for r in reqs]
-        wall = time.perf_counter() - t0
         srv.destroy()
-        return res, wall
+        return res
 
     base = S.serving_requests(count=R, seed=4, rate=1.0)
     # saturated rate: the first requests all at once
     nsat = min(R, max(8, R // 4))
-    sat, wall_sat = stream_run(base[:nsat], 0.0)
+    sat = stream_run(base[:nsat], 0.0)
     span = max(r["t_done"] for r in sat) - min(r["t_submit"] for r in sat)
     rate_sat = nsat / max(span, 1e-9)
     rate = 0.8 * rate_sat
     reqs = S.serving_requests(count=R, seed=4, rate=rate)
     clocks = ClockSampler(0)
     clocks.start()
-    res, wall = stream_run(reqs, rate)
+    res = stream_run(reqs, rate)
     clk = clocks.stop()
     lat = np.array([r["t_done"] - r["t_submit"] for r in res])
     qwait = np.array([r["t_admit"] - r["t_submit"] for r in res])
@@ -565,53 +749,28 @@ def run_serve(args):
     print(json.dumps(out), flush=True)
 
 
-def run_probe(args):
-    """Small fixed cases for profiling single kernels (ncu -k ...): 'gmres512' builds
-    the 2-D 512^2 problem with 8x8 subdomains, overlap 2 (the 68x68 boxes of the
-    1024^2 workload), 'gmres1024' the 1024^2 problem itself with its 16x16
-    subdomains (the bench's launch configuration, about 2.5 GB on the device);
-    both run 40 GMRES iterations of the first Newton solve (FP64, or FP32 sweeps
-    and basis with --precision mixed) after a one-iteration set-up solve."""
-    import torch
-    import paper_2209_08001_gb300 as nks
-    torch.cuda.set_device(0)
-    if args.probe in ("gmres512", "gmres1024"):
-        side, sub = (512, 8) if args.probe == "gmres512" else (1024, 16)
-        n = (side, side)
-        op = S.options(sub=(sub, sub), overlap=2, u0_maxit=1, gmres_maxit=40, u0_rtol=1e-2,
-                       precision=args.precision or "fp64")
-        c, e = S.initial_fields(2, n, 0.2, 1)
-        P = nks.Problem(2, n, 0.25, c, e, S.coefficients(), op)
-        cg, eg, ug = P.get_fields()
-        X = np.concatenate([cg, eg, ug[0], ug[1]])
-        b = -P.eval_residual(X, X, 0.01)
-        x, its, res = P.linear_solve(X, X, 0.01, b, 1e-30)
-        print(json.dumps({"probe": args.probe, "gmres_its": its, "res": res}))
-        P.destroy()
-
-
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="2d1024", choices=sorted(S.CONFIGS))
+    ap.add_argument("--config", default="3d128", choices=sorted(S.CONFIGS))
+    ap.add_argument("--grid", type=int, default=None,
+                    help="run the workload's recipe on a smaller grid of this many cells per axis (same box size)")
     ap.add_argument("--precision", default=None, choices=["fp64", "mixed"],
-                    help="override the workload's precision mode (default: the workload's own)")
+                    help="the headline solver (default mixed, with the FP64 solver beside it)")
+    ap.add_argument("--no-fp64", action="store_true", help="mixed precision without the FP64 solver beside it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-accuracy", action="store_true", help="mixed precision: skip the FP64 comparison")
-    # iteration counts used to scale the oracle sample in the reference arm (measured on the GPU arm)
-    ap.add_argument("--ref-gmres-per-step", type=float, default=1700.0)
-    ap.add_argument("--ref-newton-per-step", type=float, default=5.67)
-    ap.add_argument("--probe", default=None, choices=["gmres512", "gmres1024"], help="small profiling case, no JSON bench line")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the comparison with the oracle reference")
     ap.add_argument("--batch", type=int, default=0,
                     help="B > 0: B instances of the workload stepped as one batch (beside one alone)")
     ap.add_argument("--serve", action="store_true", help="the serving workload (p50/p99 latency, throughput)")
     ap.add_argument("--variant", default=None, choices=["left-ras", "as", "right-ras"],
                     help="Schwarz preconditioner type (default: the workload's, left-RAS)")
     ap.add_argument("--overlap", type=int, default=None, help="override the workload's Schwarz overlap delta")
+    ap.add_argument("--gmres-maxit", type=int, default=None, help="override the GMRES iteration cap per solve")
     ap.add_argument("--u0-maxit", type=int, default=None,
                     help="Newton iterations allowed to the initial mechanical equilibrium (set-up, not timed)")
     ap.add_argument("--autotune", action="store_true",
@@ -621,9 +780,7 @@ def main():
     ap.add_argument("--slots", type=int, default=16, help="--serve: slots per shape group")
     ap.add_argument("--groups", type=int, default=8, help="--serve: shape groups alive at once")
     args = ap.parse_args()
-    if args.probe:
-        run_probe(args)
-    elif args.batch > 0 and args.impl == "ours":
+    if args.batch > 0 and args.impl == "ours":
         run_batch(args)
     elif args.serve and args.impl == "ours":
         run_serve(args)

@@ -113,6 +113,7 @@ def lib():
         sig = {
             "orc_nfields": (ctypes.c_int, [g, k]),
             "orc_num_threads": (ctypes.c_int, []),
+            "orc_set_threads": (None, [ctypes.c_int]),
             "orc_energy": (ctypes.c_double, [g, k, ctypes.c_double, _D, _D]),
             "orc_mass": (ctypes.c_double, [g, k, _D]),
             "orc_psi_quot": (ctypes.c_double, [ctypes.c_double, ctypes.c_double, ctypes.c_int]),
@@ -328,6 +329,11 @@ class Problem:
 def num_threads() -> int:
     """Host threads the oracle's parallel loops use."""
     return int(lib().orc_num_threads())
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's later parallel loops (n <= 0: all processors)."""
+    lib().orc_set_threads(int(n))
 
 
 def psi_quot(y1, y2, S):

@@ -149,6 +149,16 @@ int orc_num_threads(void)
 #endif
 }
 
+/* threads of the following parallel loops: n >= 1, or n <= 0 for all processors */
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    omp_set_num_threads(n >= 1 ? n : omp_get_num_procs());
+#else
+    (void)n;
+#endif
+}
+
 /* ------------------------------------------------------------------------ */
 /* Sums in a fixed order (independent of the thread count)                   */
 /* ------------------------------------------------------------------------ */

@@ -2,8 +2,9 @@
 
 This module is the only code shared by the oracle-side tests and the callers of
 the CUDA path.  It holds no arithmetic of the method: only random draws
-(SplitMix64), grid sizes, coefficient values, solver settings and the five
-workload descriptions.
+(SplitMix64), grid sizes, coefficient values, solver settings, the five
+workload descriptions, and a seeded random projection (``sign_sketch``) and
+point sample (``sample_points``) for comparing full-size fields.
 
 Workload recipe (the paper's own workloads are synthetic initial states,
 Sec. 5.1-5.3; no dataset is involved):
@@ -45,6 +46,32 @@ def splitmix64(seed: int, count: int, start: int = 0) -> np.ndarray:
 def uniform01(seed: int, count: int, start: int = 0) -> np.ndarray:
     """u = (x >> 11) * 2^-53 in [0, 1)."""
     return (splitmix64(seed, count, start) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+
+
+def sign_sketch(fields, k: int = 256, seed: int = 7) -> np.ndarray:
+    """Seeded random projection for comparing large fields without storing them:
+    row i of the k x N matrix S has entries (1 - 2 b_ij)/sqrt(k), b_ij the bits
+    (least significant first) of SplitMix64 outputs with seed (seed << 20) + i.
+    Returns S x for every array x in `fields` (shape (len(fields), k)).  For any
+    vector v, |S v| estimates |v|: |S v|^2 / |v|^2 concentrates like chi^2_k / k
+    (Johnson-Lindenstrauss), so |S a - S b| estimates the L2 distance |a - b|."""
+    X = [np.ascontiguousarray(x, dtype=np.float64).ravel() for x in fields]
+    N = X[0].size
+    words = (N + 63) // 64
+    out = np.zeros((len(X), k))
+    for i in range(k):
+        bits = np.unpackbits(splitmix64((seed << 20) + i, words).view(np.uint8), bitorder="little")[:N]
+        sg = 1.0 - 2.0 * bits.astype(np.float64)
+        for f, x in enumerate(X):
+            out[f, i] = np.dot(sg, x)
+    return out / math.sqrt(k)
+
+
+def sample_points(N: int, count: int = 1024, seed: int = 11) -> np.ndarray:
+    """`count` distinct seeded point indices in [0, N), sorted."""
+    u = uniform01(seed, 4 * count + 64)
+    idx = np.unique((u * N).astype(np.int64))
+    return np.sort(idx[:count]) if idx.size >= count else idx
 
 
 def initial_fields(dim: int, n, cbar: float, seed: int, c_amp: float = 0.005,
