@@ -69,6 +69,7 @@ struct RasPlan {
     long long *lvl_src = nullptr;   // FP64 factor offset of every level's block (nlev_all + 1 entries)
     int maxnqx = 0;                 // largest box plane with the halo
     int guard32 = 0;                // zero cells before and after the 3-D box planes (the stencil reach)
+    int shape32 = 0;                // 1: every box has the compiled-in shape of its dimension
     bool halo32 = false;            // FP32 sweep on the branch-free layout (no neighbour bounds checks)
     long long scr_elems = 0;        // global scratch vector of the sweeps (when x is not in shared memory)
     long long total_np = 0;         // overlapped points of all subdomains
@@ -148,6 +149,18 @@ struct PM {
 
 // zero cells on each side of the box in the halo layout: the stencil reach
 constexpr int kHalo = 2;
+
+// cells a thread gathers per pass in the FP32 sweep
+constexpr int kGatherIlp = 4;
+
+// box plane pitches compiled into the FP32 sweep for the common box shapes (every
+// neighbour offset then an immediate): 3-D 18^3 boxes (16^3 owned, overlap 1) and
+// 2-D 68^2 boxes (64^2 owned, overlap 2) on the branch-free layout
+struct LaneShape {
+    int qx, qy, l2;
+};
+constexpr LaneShape kShape3 = {19, 19, 18};
+constexpr LaneShape kShape2 = {73, 72, 1};
 
 // L2 prefetch distance (levels) of the FP32 sweep on 3-D boxes (measured on the
 // 18^3 boxes of the 128^3 workload: 8 levels ahead 6% faster than none; on the
@@ -446,6 +459,12 @@ int ras_plan_create(Problem *P, std::string &err)
                 scr_off += (long long)nf * si.npx;
             }
     R->npart = sweep_partials(d, nf);
+    {
+        const LaneShape sh = d == 3 ? kShape3 : kShape2;
+        bool uni = d >= 2;
+        for (const SubInfo &si : infos) uni = uni && si.qx == sh.qx && si.qy == sh.qy && si.L[2] == sh.l2;
+        R->shape32 = uni ? 1 : 0;
+    }
     R->fac_elems = fac_off;
     R->nlev_all = (long long)lvl_src.size();
     lvl_src.push_back(fac_off);
@@ -848,17 +867,35 @@ __global__ void __launch_bounds__(1024) k_ras_apply(DGrid g, Bat bt, const SubIn
     __syncthreads();
     if (tid == prod) issue(0);
     for (int i = tid; i < np; i += blockDim.x) lps[i] = lvl_lp[si.pos_off + i];
-    // gather R_i^delta r (right-RAS: R_i^0 r, the owned points only)
-    for (int q = tid; q < np; q += blockDim.x) {
-        const int lx = q % si.L[0], ly = (q / si.L[0]) % si.L[1], lz = q / (si.L[0] * si.L[1]);
-        const int lp = lx + sy * ly + sz * lz;
-        const long long gp = index_of(g, wrapi(si.org[0] + lx, g.n[0]), wrapi(si.org[1] + ly, g.n[1]),
-                                      wrapi(si.org[2] + lz, g.n[2]));
-        const bool take = variant != NKS_RIGHT_RAS ||
-                          (lx >= si.own0[0] && lx < si.own1[0] && ly >= si.own0[1] && ly < si.own1[1] &&
-                           lz >= si.own0[2] && lz < si.own1[2]);
+    // gather R_i^delta r (right-RAS: R_i^0 r, the owned points only), several points
+    // per thread and pass with every load of the pass issued before the first store
+    // (two for FP64 values: the 1024-thread bound leaves 64 registers)
+    constexpr int G = sizeof(T) == 8 ? 2 : kGatherIlp;
+    for (int q0 = tid; q0 < np; q0 += G * blockDim.x) {
+        int lp[G];
+        long long gp[G];
+        bool take[G];
 #pragma unroll
-        for (int f = 0; f < NF; f++) x[f * npx + lp] = take ? (T)r[f * N + gp] : (T)0;
+        for (int j = 0; j < G; j++) {
+            const int q = q0 + j * blockDim.x;
+            const int lx = q % si.L[0], ly = (q / si.L[0]) % si.L[1], lz = q / (si.L[0] * si.L[1]);
+            lp[j] = lx + sy * ly + sz * lz;
+            gp[j] = index_of(g, wrapi(si.org[0] + lx, g.n[0]), wrapi(si.org[1] + ly, g.n[1]),
+                             wrapi(si.org[2] + lz, g.n[2]));
+            take[j] = q < np && (variant != NKS_RIGHT_RAS ||
+                                 (lx >= si.own0[0] && lx < si.own1[0] && ly >= si.own0[1] && ly < si.own1[1] &&
+                                  lz >= si.own0[2] && lz < si.own1[2]));
+        }
+        T v[G][NF];
+#pragma unroll
+        for (int j = 0; j < G; j++)
+#pragma unroll
+            for (int f = 0; f < NF; f++) v[j][f] = take[j] ? (T)r[f * N + gp[j]] : (T)0;
+#pragma unroll
+        for (int j = 0; j < G; j++)
+            if (q0 + j * blockDim.x < np)
+#pragma unroll
+                for (int f = 0; f < NF; f++) x[f * npx + lp[j]] = v[j][f];
     }
     __syncthreads();
     bool failed = false;
@@ -1000,7 +1037,7 @@ __device__ __forceinline__ void point_rows_pm(const float *__restrict__ Bk, floa
 // branch-free layout (1-D and 2-D: kHalo zero cells around the box; 3-D: the
 // box planes between `guard` zero cells on each side), the point table then
 // holds 16-bit x indices.
-template <int D, int NF, int NBUF, bool XS, bool HALO>
+template <int D, int NF, int NBUF, bool XS, bool HALO, bool SHAPE>
 __global__ void __launch_bounds__(256) k_ras_apply_lane(DGrid g, Bat bt, const SubInfo *__restrict__ subs, const int *__restrict__ lvl_ptr,
                             const long long *__restrict__ lvl_blk, const int *__restrict__ lvl_lp,
                             const float *__restrict__ fac, const float *__restrict__ r, float *__restrict__ z,
@@ -1009,6 +1046,8 @@ __global__ void __launch_bounds__(256) k_ras_apply_lane(DGrid g, Bat bt, const S
                             int withhold, int variant, int guard)
 {
     static_assert(XS || !HALO, "the halo layout lives in shared memory");
+    static_assert(HALO || !SHAPE, "compiled-in pitches are those of the branch-free layout");
+    constexpr LaneShape SH = D == 3 ? kShape3 : kShape2;
     using T = float;
     using LT = typename std::conditional<HALO, unsigned short, int>::type;
     using L = PM<D, NF>;
@@ -1041,9 +1080,10 @@ __global__ void __launch_bounds__(256) k_ras_apply_lane(DGrid g, Bat bt, const S
     const T *F = fac + si.fac_off / L::PP * (L::SF + L::SB);
     const long long N = g.N;
     // x layout: NF planes of npx entries, local (lx, ly, lz) at l0 + lx + sy ly + sz lz
-    const int sy = HALO ? si.qx : si.px, sz = HALO ? si.qx * si.qy : si.px * si.py;
-    const int npx = HALO ? si.nqx : si.npx;
-    const int l0 = HALO && D <= 2 ? kHalo * (1 + (D >= 2 ? si.qx : 0)) : 0;
+    const int sy = SHAPE ? SH.qx : (HALO ? si.qx : si.px);
+    const int sz = SHAPE ? SH.qx * SH.qy : (HALO ? si.qx * si.qy : si.px * si.py);
+    const int npx = SHAPE ? SH.qx * SH.qy * SH.l2 : (HALO ? si.nqx : si.npx);
+    const int l0 = HALO && D <= 2 ? kHalo * (1 + (D >= 2 ? sy : 0)) : 0;
     const int tid = threadIdx.x;
     const int prod = blockDim.x - 1;  // the copy-issuing thread
     const int nuse = 2 * nlev;  // forward parts of levels 0..nlev-1, then backward parts of nlev-1..0
@@ -1096,25 +1136,44 @@ __global__ void __launch_bounds__(256) k_ras_apply_lane(DGrid g, Bat bt, const S
     // branch-free layout every cell of the planes is written (zero outside the box),
     // and in 3-D the guard cells before and after the planes are zeroed
     if constexpr (HALO) {
-        const int qy = D == 3 ? si.qy : 1;
-        for (int q = tid; q < npx; q += blockDim.x) {
-            int lx, ly, lz;
-            if constexpr (D == 3) {
-                lx = q % sy;
-                ly = (q / sy) % qy;
-                lz = q / sz;
-            } else {
-                lx = q % sy - kHalo;
-                ly = D >= 2 ? q / sy - kHalo : 0;
-                lz = 0;
-            }
-            const bool in = lx >= 0 && lx < si.L[0] && ly >= 0 && ly < si.L[1] && lz < si.L[2];
-            const bool take = in && (variant != NKS_RIGHT_RAS || owned(lx, ly, lz));
-            const long long gp = take ? index_of(g, wrapi(si.org[0] + lx, g.n[0]), wrapi(si.org[1] + ly, g.n[1]),
-                                                 wrapi(si.org[2] + lz, g.n[2]))
-                                      : 0;
+        const int qy = D == 3 ? (SHAPE ? SH.qy : si.qy) : 1;
+        // kGatherIlp cells per thread and pass: every load of the pass is issued before
+        // the first value is stored (the gather is a latency-bound chain of global loads)
+        constexpr int G = kGatherIlp;
+        for (int q0 = tid; q0 < npx; q0 += G * blockDim.x) {
+            int gp[G];
+            bool take[G];
 #pragma unroll
-            for (int f = 0; f < NF; f++) x[f * npx + q] = take ? (T)r[f * N + gp] : (T)0;
+            for (int j = 0; j < G; j++) {
+                const int q = q0 + j * blockDim.x;
+                int lx, ly, lz;
+                if constexpr (D == 3) {
+                    lx = q % sy;
+                    ly = (q / sy) % qy;
+                    lz = q / sz;
+                } else {
+                    lx = q % sy - kHalo;
+                    ly = D >= 2 ? q / sy - kHalo : 0;
+                    lz = 0;
+                }
+                const bool in = q < npx && lx >= 0 && lx < si.L[0] && ly >= 0 && ly < si.L[1] && lz < si.L[2];
+                take[j] = in && (variant != NKS_RIGHT_RAS || owned(lx, ly, lz));
+                gp[j] = take[j] ? (int)index_of(g, wrapi(si.org[0] + lx, g.n[0]), wrapi(si.org[1] + ly, g.n[1]),
+                                                wrapi(si.org[2] + lz, g.n[2]))
+                                : 0;
+            }
+            T v[G][NF];
+#pragma unroll
+            for (int j = 0; j < G; j++)
+#pragma unroll
+                for (int f = 0; f < NF; f++) v[j][f] = take[j] ? r[f * N + gp[j]] : (T)0;
+#pragma unroll
+            for (int j = 0; j < G; j++) {
+                const int q = q0 + j * blockDim.x;
+                if (q < npx)
+#pragma unroll
+                    for (int f = 0; f < NF; f++) x[f * npx + q] = v[j][f];
+            }
         }
         if constexpr (D == 3)
             for (int q = tid; q < guard; q += blockDim.x) {
@@ -1438,10 +1497,15 @@ using LaneKernel = void (*)(DGrid, Bat, const SubInfo *, const int *, const long
 template <int D, int NF>
 LaneKernel lane_kernel(const RasPlan *R)
 {
-    if (R->halo32) return R->lane_bufs == 3 ? k_ras_apply_lane<D, NF, 3, true, true>
-                                            : k_ras_apply_lane<D, NF, 2, true, true>;
-    if (!R->x_smem32) return k_ras_apply_lane<D, NF, 2, false, false>;
-    return R->lane_bufs == 3 ? k_ras_apply_lane<D, NF, 3, true, false> : k_ras_apply_lane<D, NF, 2, true, false>;
+    if constexpr (D >= 2)
+        if (R->halo32 && R->shape32)
+            return R->lane_bufs == 3 ? k_ras_apply_lane<D, NF, 3, true, true, true>
+                                     : k_ras_apply_lane<D, NF, 2, true, true, true>;
+    if (R->halo32) return R->lane_bufs == 3 ? k_ras_apply_lane<D, NF, 3, true, true, false>
+                                            : k_ras_apply_lane<D, NF, 2, true, true, false>;
+    if (!R->x_smem32) return k_ras_apply_lane<D, NF, 2, false, false, false>;
+    return R->lane_bufs == 3 ? k_ras_apply_lane<D, NF, 3, true, false, false>
+                             : k_ras_apply_lane<D, NF, 2, true, false, false>;
 }
 
 // the sweep kernel's dynamic shared memory limit (set once, before any graph capture)
