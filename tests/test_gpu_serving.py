@@ -169,3 +169,32 @@ def test_autotune_picks_the_fastest_valid_decomposition(nks):
     # the built-in candidate list
     op2, table2, chosen2 = nks.autotune(dim, n, 0.25, c, e, S.coefficients(), S.options())
     assert chosen2 >= 0 and all(o >= 1 for o in op2["sub"])
+
+
+def test_served_results_match_the_oracle(nks):
+    """Requests served in a mix (two shape groups, slots shared) against the FP64
+    oracle run of each request alone: fixed dt so the oracle takes the same step
+    sizes; relative L2 per field <= 1e-8 and energy, mass after the last step."""
+    import oracle
+    base = S.options(precision="mixed", dt_mode="fixed", overlap=1)
+    reqs = [(2, (32, 32), 0.15, 3, 701), (3, (16, 16, 16), 0.2, 2, 702), (2, (40, 36), 0.12, 3, 703),
+            (2, (32, 32), 0.22, 2, 704)]
+    srv = nks.Server(S.coefficients(), base, box_side_2d=SIDE2, box_side_3d=SIDE3, max_slots=2, max_groups=4)
+    init = [S.initial_fields(dim, n, cb, seed) for dim, n, cb, _, seed in reqs]
+    ids = [srv.submit(dim, n, 0.25, c, e, steps) for (dim, n, _, steps, _), (c, e) in zip(reqs, init)]
+    served = [srv.wait(rid) for rid in ids]
+    srv.destroy()
+    rel = lambda a, b: np.linalg.norm(a - b) / np.linalg.norm(b)
+    for (dim, n, _, steps, _), (c0, e0), (r, (c, e, u)) in zip(reqs, init, served):
+        assert r["status"] == 0 and r["steps"] == steps, r
+        op = dict(_req_opts(dim, n, base), precision="fp64", newton_rtol=1e-12)
+        O = oracle.Problem(dim, n, 0.25, S.coefficients(), op)
+        rc, X, infos, _ = O.simulate(c0, e0, steps)
+        assert rc == 0
+        co, eo, uo = O.split(X)
+        assert rel(c, co) <= 1e-8 and rel(e, eo) <= 1e-8, (n, rel(c, co), rel(e, eo))
+        for I in range(dim):
+            assert rel(u[I], uo[I]) <= 1e-8, (n, I, rel(u[I], uo[I]))
+        assert r["energy"] == pytest.approx(infos[-1]["energy"], rel=1e-10)
+        assert r["mass"] == pytest.approx(infos[-1]["mass"], rel=1e-12)
+        assert r["t"] == pytest.approx(sum(i["dt"] for i in infos), rel=1e-14)
