@@ -5,8 +5,10 @@
  * alloys system" (arXiv 2209.08001).
  *
  * The solver advances the coupled Cahn-Hilliard / Allen-Cahn (Ginzburg-Landau)
- * system for the Al composition c, one long-range order parameter eta and the
- * elastic displacement u on a periodic, cell-centred, uniform grid (Sec. 2-3).
+ * system for the Al composition c, the long-range order (one parameter eta, the
+ * reduced model of Sec. 2-5, or the three eta_1..eta_3 of App. A) and the
+ * elastic displacement u on a cell-centred, uniform grid, periodic or with
+ * homogeneous Neumann boundaries (Sec. 2-3).
  * Every time step solves the nonlinear system F(X) = 0 of Eq. NSOA-1 by an
  * inexact Newton method with line search (Sec. 4), whose Jacobian systems are
  * solved by restarted GMRES preconditioned with restricted additive Schwarz
@@ -16,9 +18,11 @@
  * Conventions for every entry point:
  *   - Grids are x-fastest: point p = x + nx*(y + ny*z).  A "field" array holds
  *     N = nx*ny*nz doubles in that order.
- *   - A "state" array (X) holds the fields one after another (SoA): c, eta and,
- *     when elasticity is on (any of C11, C12, C44 non-zero), u_1..u_d.  Its
- *     length is nf*N with nf = 2 + d (elastic) or 2.
+ *   - A "state" array (X) holds the fields one after another (SoA): c, then
+ *     the n_eta order parameters (nks_coeffs.n_eta: 1 or 3) and, when
+ *     elasticity is on (any of C11, C12, C44 non-zero), u_1..u_d.  Its length
+ *     is nf*N with nf = 1 + n_eta + d (elastic) or 1 + n_eta.  An "eta" array
+ *     holds the n_eta order-parameter fields one after another (n_eta*N).
  *   - Pointers marked HOST are read or written with synchronous copies before
  *     the call returns; the caller keeps ownership.  Pointers marked DEVICE
  *     must be device memory on the problem's device.
@@ -39,7 +43,8 @@ extern "C" {
 /* status codes */
 #define NKS_OK 0
 #define NKS_EINVAL 1     /* invalid argument or unsupported configuration        */
-#define NKS_EDOMAIN 2    /* c, c*eta or c*(4-3*eta) outside (0, 1)               */
+#define NKS_EDOMAIN 2    /* c, c*eta or c*(4-3*eta) outside (0, 1); with three order
+                            parameters c, c*eta_i (i = 1..4, eta_4 = 4 - sum) */
 #define NKS_ENOMEM 3     /* device allocation failed                              */
 #define NKS_EDIVERGED 4  /* Newton failed and the retry budget is spent (Sec. 4)  */
 #define NKS_ETIMEOUT 5   /* an iteration cap was reached                          */
@@ -61,11 +66,30 @@ extern "C" {
 #define NKS_DT_SOLUTION 1 /* X'_d = ||X^n - X^{n-1}||_2 / dt_{n-1}                */
 #define NKS_DT_ENERGY 2   /* X'_d = |E^n - E^{n-1}| / dt_{n-1}                    */
 
-/* Periodic cell-centred grid x_i = (i - 1/2) h on each axis (Sec. 3). */
+/* boundary conditions (nks_grid.bc) */
+#define NKS_PERIODIC 0
+#define NKS_NEUMANN 1    /* homogeneous Neumann (Sec. 2, Eq. boundaryequ)              */
+
+/*
+ * Cell-centred grid x_i = (i - 1/2) h on each axis (Sec. 3).
+ *   bc  NKS_PERIODIC: periodic in every axis.
+ *       NKS_NEUMANN: homogeneous Neumann boundaries, n.grad c = n.grad eta =
+ *       n.M grad mu = 0 and n.sigma = 0 (Eq. boundaryequ).  The ghost cell beyond
+ *       a boundary cell mirrors it, so D^+ / D^- across a boundary face vanish and
+ *       the flux form has no boundary flux (Sec. 3's summation by parts holds as
+ *       stated); the displacement rows are the exact variation -dE_3/du of the
+ *       discrete elastic energy (strains by the centred difference with mirrored
+ *       ghosts), whose natural boundary condition is the traction-free one; the
+ *       Schwarz boxes stop at the boundary; the null modes of the strain, which
+ *       the Newton corrections are kept free of, are the d translations and, for
+ *       each pair of axes that both have an even number of cells, a discrete
+ *       rotation (u_I = -S(x_J), u_J = S(x_I), S(x) = floor((x+1)/2) - n/4).
+ */
 typedef struct {
     int dim;     /* 1, 2 or 3                                        */
     int n[3];    /* cells per axis; entries >= dim are ignored        */
     double h;    /* mesh size (the same on every axis)                */
+    int bc;      /* NKS_PERIODIC or NKS_NEUMANN                       */
 } nks_grid;
 
 /*
@@ -81,6 +105,11 @@ typedef struct {
  *   C11, C12, C44  cubic Hooke constants / dE; multiplied by Lscale (Sec. 5.1).
  *               All three zero switches elasticity (and the u fields) off.
  *   S           Taylor order of Psi_S (Sec. 3, S = 10 in Sec. 5); must be >= 1
+ *   n_eta       order parameters: 1 (0 reads as 1) for the reduced model of the
+ *               main text, 3 for the model of App. A (E_1 = dis(c) + a(c) S(eta)
+ *               + b(c) T(eta), E_2 over the four sublattices, gamma_eta/2 per
+ *               |grad eta_j|^2, Allen-Cahn rows with the kinetic factor 3, so
+ *               that eta_1 = eta_2 = eta_3 = eta is the reduced model)
  */
 typedef struct {
     double kappa, gamma_c, gamma_eta, theta, w_psi, dE0;
@@ -88,6 +117,7 @@ typedef struct {
     double U1, U4, eps0;
     double C11, C12, C44, Lscale;
     int S;
+    int n_eta;
 } nks_coeffs;
 
 /*
@@ -205,7 +235,7 @@ void nks_default_opts(nks_opts *o);
  * Create a problem from the initial fields and solve the initial mechanical
  * equilibrium for u (reading: the energy law of Theorem 3.1 assumes u in
  * equilibrium at level n).  The mean composition cbar0 of Sec. 3 is taken from c.
- *   c, eta   HOST, N doubles each (x-fastest)
+ *   c, eta   HOST, N and n_eta*N doubles (x-fastest)
  *   alloc    NULL: cudaMalloc / cudaFree
  *   stream   a cudaStream_t, or NULL for a stream the library creates and owns
  * Fails with NKS_EDOMAIN when an initial value leaves the domain of the
@@ -228,8 +258,8 @@ int nks_energy(const nks_problem *p, double *out);
 /* Mass <c^n> = h^d sum_i c_i (Theorem 3.1). */
 int nks_mass(const nks_problem *p, double *out);
 
-/* Copy the current fields to HOST arrays (N doubles each; u: d*N doubles,
- * component-major, or NULL; ignored without elasticity). */
+/* Copy the current fields to HOST arrays (c: N doubles, eta: n_eta*N; u: d*N
+ * doubles, component-major, or NULL; ignored without elasticity). */
 int nks_get_fields(const nks_problem *p, double *c, double *eta, double *u);
 
 /* Checkpoint: bytes needed, then save / restore X^n, X^{n-1}, t, step count,
@@ -263,7 +293,7 @@ const char *nks_last_error(const nks_problem *p);
 /* ------------------------------------------------------------------------ */
 
 /* Create a batch of nb slots (1 <= nb <= 65535; in 3-D n_z * nb <= 65535).
- *   c, eta   HOST, nb * N doubles each (slot-major), or both NULL: every slot
+ *   c, eta   HOST, nb * N and nb * n_eta * N doubles (slot-major), or both NULL: every slot
  *            starts empty (fill slots with nks_batch_load).
  * Each loaded slot takes its own mean composition cbar0 and initial
  * mechanical equilibrium, as nks_create_problem does.  Errors as there. */
@@ -273,7 +303,7 @@ int nks_create_batch(const nks_grid *grid, int nb, const double *c, const double
 /* Number of slots. */
 int nks_batch_size(const nks_problem *p);
 
-/* Load initial fields (HOST, N doubles each) into a slot: resets its time,
+/* Load initial fields (HOST, N and n_eta*N doubles) into a slot: resets its time,
  * step count and step-size state, solves its initial equilibrium.  Other
  * slots are untouched.  NKS_EINVAL for a bad slot, NKS_EDOMAIN as above. */
 int nks_batch_load(nks_problem *p, int slot, const double *c, const double *eta);
@@ -304,8 +334,8 @@ int nks_batch_set_state(nks_problem *p, int slot, const void *buf, size_t bytes)
 size_t nks_device_bytes(const nks_problem *p);
 
 /* Pointwise DVD derivative of the model with three order parameters (App. A:
- * eta_1..eta_3, eta_4 = 4 - sum; the CUDA path of this model is being built and
- * problems still refuse it).  Host computation, no device needed.
+ * eta_1..eta_3, eta_4 = 4 - sum), the part of the residual the kernels of that
+ * model evaluate per point.  Host computation, no device needed.
  *   x1, x0  HOST, 4 doubles each: (c, eta_1, eta_2, eta_3) at levels n+1 and n;
  *           c and the four site fractions c eta_i must lie in (0, 1)
  *   G       HOST, 4 doubles out: G^1 + G^{2,S} = (G_c, G_eta_1, G_eta_2, G_eta_3),
@@ -369,13 +399,13 @@ typedef struct {
 void nks_server_default_opts(nks_server_opts *o);
 int nks_server_create(const nks_coeffs *coeffs, const nks_server_opts *opts, nks_server **out);
 
-/* Queue a request: grid, initial fields (HOST, N doubles each; copied),
+/* Queue a request: grid, initial fields (HOST, N and n_eta*N doubles; copied),
  * number of time steps (adaptive dt).  Never blocks on the GPU work. */
 int nks_server_submit(nks_server *s, const nks_grid *grid, const double *c, const double *eta, int steps,
                       long long *id);
 
 /* Wait for a request (timeout_s < 0: no limit; NKS_ETIMEOUT on expiry), copy its
- * result and final fields (c, eta: N doubles, u: d N doubles; any may be NULL)
+ * result and final fields (c: N, eta: n_eta N, u: d N doubles; any may be NULL)
  * and release it. */
 int nks_server_wait(nks_server *s, long long id, nks_request_result *res, double *c, double *eta, double *u,
                     double timeout_s);
@@ -465,6 +495,8 @@ int nks_eval_energy(nks_problem *p, const double *X, double *parts, double *mass
  *   X1, X0, F      DEVICE state arrays of nf*N doubles (layout of this header)
  *   fnorm2         DEVICE pointer receiving ||F||^2, or NULL
  *   stream         cudaStream_t to run on (NULL: the legacy default stream)
+ * Serves the model with one order parameter (coeffs->n_eta 0 or 1; NKS_EINVAL
+ * for 3).
  * Returns NKS_OK, NKS_EINVAL, NKS_EDOMAIN (X1 outside the domain of the
  * logarithms; F is still written) or NKS_ECUDA; nks_last_error(NULL) gives
  * the message.  The call synchronises the stream before it returns.  A CUDA

@@ -1483,13 +1483,23 @@ static int ras_setup(const orc_grid *g, int nf, int ku, const orc_opts *o, const
     return rc;
 }
 
+/* centred staircase along an axis of n cells (n even): S(x) = floor((x+1)/2) - n/4.
+ * With mirror ghosts its centred difference is 1/h at every cell, boundary cells
+ * included: (S(1) - S(0))/(2h) = (S(x+1) - S(x-1))/(2h) = (S(n-1) - S(n-2))/(2h). */
+static double staircase(long x, long n) { return (double)((x + 1) / 2) - 0.25 * (double)n; }
+
 /*
  * Projection P applied after the Schwarz sweep (reading of the paper, which
  * only states that mass is conserved):
  *   - subtract the mean of z_c, so every Newton correction has sum s_c = 0;
  *   - remove from each z_uI its components along the null modes of the
  *     centred-difference strain: tensor products over the axes of 1 and, on
- *     axes with an even number of cells, (-1)^x.
+ *     axes with an even number of cells, (-1)^x (periodic grids);
+ *   - with Neumann boundaries (mirror ghosts) the translations, and for every
+ *     pair of axes I < J that both have an even number of cells the discrete
+ *     rotation u_I = -S(x_J), u_J = S(x_I) (S the staircase above): its strain
+ *     sym(Dhat u) vanishes at every cell, so it is an exact null mode of the
+ *     displacement block, and every residual is orthogonal to it.
  */
 static void project(const orc_grid *g, int nf, int ku, double *z)
 {
@@ -1529,6 +1539,30 @@ static void project(const orc_grid *g, int nf, int ku, double *z)
                 z[p * nf + ku + I] -= a * sg;
             }
         }
+    }
+    if (g->neumann) {
+        double *nv = (double *)malloc(sizeof(double) * N);
+        for (int I = 0; I < d; I++)
+            for (int J = I + 1; J < d; J++) {
+                if (g->n[I] % 2 != 0 || g->n[J] % 2 != 0) continue;
+#pragma omp parallel for schedule(static)
+                for (long p = 0; p < N; p++) {
+                    long x[3];
+                    coords(g, p, x);
+                    double mi = -staircase(x[J], g->n[J]), mj = staircase(x[I], g->n[I]);
+                    sv[p] = mi * z[p * nf + ku + I] + mj * z[p * nf + ku + J];
+                    nv[p] = mi * mi + mj * mj;
+                }
+                double a = strided_sum(N, sv, 1) / strided_sum(N, nv, 1);
+#pragma omp parallel for schedule(static)
+                for (long p = 0; p < N; p++) {
+                    long x[3];
+                    coords(g, p, x);
+                    z[p * nf + ku + I] -= a * -staircase(x[J], g->n[J]);
+                    z[p * nf + ku + J] -= a * staircase(x[I], g->n[I]);
+                }
+            }
+        free(nv);
     }
     free(sv);
 }

@@ -32,7 +32,10 @@ class NksError(RuntimeError):
 
 
 class nks_grid(ctypes.Structure):
-    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("h", ctypes.c_double)]
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("h", ctypes.c_double), ("bc", ctypes.c_int)]
+
+
+NKS_PERIODIC, NKS_NEUMANN = 0, 1
 
 
 class nks_coeffs(ctypes.Structure):
@@ -40,7 +43,7 @@ class nks_coeffs(ctypes.Structure):
                 ("theta", ctypes.c_double), ("w_psi", ctypes.c_double), ("dE0", ctypes.c_double),
                 ("L", ctypes.c_double * 4), ("U1", ctypes.c_double), ("U4", ctypes.c_double),
                 ("eps0", ctypes.c_double), ("C11", ctypes.c_double), ("C12", ctypes.c_double),
-                ("C44", ctypes.c_double), ("Lscale", ctypes.c_double), ("S", ctypes.c_int)]
+                ("C44", ctypes.c_double), ("Lscale", ctypes.c_double), ("S", ctypes.c_int), ("n_eta", ctypes.c_int)]
 
 
 class nks_opts(ctypes.Structure):
@@ -211,19 +214,18 @@ def _c64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
-def make_grid(dim, n, h):
+def make_grid(dim, n, h, neumann=False):
     g = nks_grid()
     g.dim = dim
     nn = list(n) + [1] * (3 - len(n))
     for J in range(3):
         g.n[J] = int(nn[J]) if J < dim else 1
     g.h = float(h)
+    g.bc = NKS_NEUMANN if neumann else NKS_PERIODIC
     return g
 
 
 def make_coeffs(cf: dict):
-    if int(cf.get("n_eta", 1)) != 1:
-        raise NksError(NKS_EINVAL, "the CUDA path solves the model with one order parameter (n_eta = 1)")
     k = nks_coeffs()
     for name in ("kappa", "gamma_c", "gamma_eta", "theta", "w_psi", "dE0", "U1", "U4", "eps0", "C11", "C12", "C44"):
         setattr(k, name, float(cf[name]))
@@ -231,7 +233,21 @@ def make_coeffs(cf: dict):
         k.L[i] = float(cf["L"][i])
     k.Lscale = float(cf.get("Lscale", 1.0))
     k.S = int(cf["S"])
+    k.n_eta = int(cf.get("n_eta", 1))
     return k
+
+
+def _layout(dim, coeffs: dict):
+    """(order parameters, fields per point) of a model: c, eta_1..eta_ne and, with
+    elasticity, u_1..u_d."""
+    ne = 3 if int(coeffs.get("n_eta", 1)) == 3 else 1
+    elastic = any(coeffs[k] != 0.0 for k in ("C11", "C12", "C44")) and coeffs.get("Lscale", 1.0) != 0.0
+    return ne, 1 + ne + (dim if elastic else 0)
+
+
+def _eta_out(ne, N):
+    """host array for n_eta order-parameter fields: (N,) for one, (3, N) for three"""
+    return np.empty(N) if ne == 1 else np.empty((ne, N))
 
 
 def make_opts(op: dict, timing=False):
@@ -273,17 +289,20 @@ def _check(rc, p=None):
 class Problem:
     """One simulation resident on the current CUDA device (``nks_problem``)."""
 
-    def __init__(self, dim, n, h, c, eta, coeffs: dict, opts: dict, stream=None, allocator=None, timing=False):
+    def __init__(self, dim, n, h, c, eta, coeffs: dict, opts: dict, stream=None, allocator=None, timing=False,
+                 neumann=False):
+        """neumann: homogeneous Neumann boundaries (mirror ghost cells, traction-free
+        displacement rows) instead of periodic ones."""
         L = load()
         self.dim, self.n = dim, tuple(n[:dim])
         self.N = int(np.prod(self.n))
-        self._grid = make_grid(dim, n, h)
+        self._grid = make_grid(dim, n, h, neumann)
         self._coeffs = make_coeffs(coeffs)
         self._opts = make_opts(opts, timing)
-        elastic = any(coeffs[k] != 0.0 for k in ("C11", "C12", "C44")) and coeffs.get("Lscale", 1.0) != 0.0
-        self.nf = 2 + (dim if elastic else 0)
+        self.ne, self.nf = _layout(dim, coeffs)
+        self.ku = 1 + self.ne  # first displacement field
         c, eta = _c64(c), _c64(eta)
-        assert c.size == self.N and eta.size == self.N
+        assert c.size == self.N and eta.size == self.ne * self.N
         self._alloc = allocator
         handle = ctypes.c_void_p()
         rc = L.nks_create_problem(ctypes.byref(self._grid), _ptr(c), _ptr(eta), ctypes.byref(self._coeffs),
@@ -319,8 +338,10 @@ class Problem:
         return v.value
 
     def get_fields(self):
-        c, eta = np.empty(self.N), np.empty(self.N)
-        u = np.empty((self.nf - 2, self.N)) if self.nf > 2 else None
+        """(c, eta, u): eta is (N,) with one order parameter, (3, N) with three;
+        u is (d, N) or None without elasticity."""
+        c, eta = np.empty(self.N), _eta_out(self.ne, self.N)
+        u = np.empty((self.nf - self.ku, self.N)) if self.nf > self.ku else None
         _check(load().nks_get_fields(self._h, _ptr(c), _ptr(eta), _ptr(u) if u is not None else None), self._h)
         return c, eta, u
 
@@ -392,19 +413,19 @@ class Batch:
     iteration and step size.  c, eta: (nb, N) arrays, or None for empty slots."""
 
     def __init__(self, dim, n, h, nb, coeffs: dict, opts: dict, c=None, eta=None, stream=None, allocator=None,
-                 timing=False):
+                 timing=False, neumann=False):
         L = load()
         self.dim, self.n, self.nb = dim, tuple(n[:dim]), int(nb)
         self.N = int(np.prod(self.n))
-        self._grid = make_grid(dim, n, h)
+        self._grid = make_grid(dim, n, h, neumann)
         self._coeffs = make_coeffs(coeffs)
         self._opts = make_opts(opts, timing)
-        elastic = any(coeffs[k] != 0.0 for k in ("C11", "C12", "C44")) and coeffs.get("Lscale", 1.0) != 0.0
-        self.nf = 2 + (dim if elastic else 0)
+        self.ne, self.nf = _layout(dim, coeffs)
+        self.ku = 1 + self.ne
         cp = ep = None
         if c is not None:
             c, eta = _c64(c).reshape(-1), _c64(eta).reshape(-1)
-            assert c.size == self.N * self.nb and eta.size == self.N * self.nb
+            assert c.size == self.N * self.nb and eta.size == self.ne * self.N * self.nb
             cp, ep = _ptr(c), _ptr(eta)
         self._alloc = allocator
         handle = ctypes.c_void_p()
@@ -425,6 +446,7 @@ class Batch:
 
     def load(self, slot, c, eta):
         c, eta = _c64(c), _c64(eta)
+        assert c.size == self.N and eta.size == self.ne * self.N
         _check(load().nks_batch_load(self._h, int(slot), _ptr(c), _ptr(eta)), self._h)
 
     def unload(self, slot):
@@ -461,8 +483,8 @@ class Batch:
         return v.value
 
     def get_fields(self, slot):
-        c, eta = np.empty(self.N), np.empty(self.N)
-        u = np.empty((self.nf - 2, self.N)) if self.nf > 2 else None
+        c, eta = np.empty(self.N), _eta_out(self.ne, self.N)
+        u = np.empty((self.nf - self.ku, self.N)) if self.nf > self.ku else None
         _check(load().nks_batch_get_fields(self._h, int(slot), _ptr(c), _ptr(eta),
                                            _ptr(u) if u is not None else None), self._h)
         return c, eta, u
@@ -494,7 +516,7 @@ def model3_point(coeffs: dict, x1, x0):
     """Pointwise DVD derivative of the model with three order parameters and its
     derivative block (nks_model3_point): x1, x0 = (c, eta_1, eta_2, eta_3) at
     levels n+1 and n; returns (G[4], dG[4, 4]) with dG[a, b] = dG_a/dx1_b."""
-    k = make_coeffs({key: v for key, v in coeffs.items() if key != "n_eta"})
+    k = make_coeffs(dict(coeffs, n_eta=3))
     x1, x0 = _c64(x1).reshape(4), _c64(x0).reshape(4)
     G, dG = np.empty(4), np.empty(16)
     rc = load().nks_model3_point(ctypes.byref(k), _ptr(x1), _ptr(x0), _ptr(G), _ptr(dG))
@@ -503,12 +525,12 @@ def model3_point(coeffs: dict, x1, x0):
     return G, dG.reshape(4, 4)
 
 
-def autotune(dim, n, h, c, eta, coeffs: dict, opts: dict, candidates=None, dt_trial=0.01):
+def autotune(dim, n, h, c, eta, coeffs: dict, opts: dict, candidates=None, dt_trial=0.01, neumann=False):
     """Pick the Schwarz decomposition (sub, overlap) with the shortest time step
     (nks_autotune).  candidates: list of (sub tuple, overlap) or None for the
     built-in list.  Returns (opts dict with the choice, [(sub, overlap, seconds)])."""
     L = load()
-    g, k, o = make_grid(dim, n, h), make_coeffs(coeffs), make_opts(opts)
+    g, k, o = make_grid(dim, n, h, neumann), make_coeffs(coeffs), make_opts(opts)
     c, eta = _c64(c), _c64(eta)
     if candidates is not None:
         flat = []
@@ -550,14 +572,16 @@ class Server:
         so.max_slots, so.max_groups = int(max_slots), int(max_groups)
         so.box_side_2d, so.box_side_3d = int(box_side_2d), int(box_side_3d)
         self._coeffs = make_coeffs(coeffs)
+        self.ne = 3 if self._coeffs.n_eta == 3 else 1
         h = ctypes.c_void_p()
         _check(L.nks_server_create(ctypes.byref(self._coeffs), ctypes.byref(so), ctypes.byref(h)), None)
         self._h = h
         self._shape = {}
 
-    def submit(self, dim, n, h, c, eta, steps):
-        g = make_grid(dim, n, h)
+    def submit(self, dim, n, h, c, eta, steps, neumann=False):
+        g = make_grid(dim, n, h, neumann)
         c, eta = _c64(c), _c64(eta)
+        assert eta.size == self.ne * c.size
         rid = ctypes.c_longlong()
         _check(load().nks_server_submit(self._h, ctypes.byref(g), _ptr(c), _ptr(eta), int(steps), ctypes.byref(rid)),
                None)
@@ -567,7 +591,7 @@ class Server:
     def wait(self, rid, timeout=-1.0):
         """(result dict, (c, eta, u)) of a finished request."""
         dim, N = self._shape.pop(rid)
-        c, eta, u = np.empty(N), np.empty(N), np.empty((dim, N))
+        c, eta, u = np.empty(N), _eta_out(self.ne, N), np.empty((dim, N))
         r = nks_request_result()
         _check(load().nks_server_wait(self._h, int(rid), ctypes.byref(r), _ptr(c), _ptr(eta), _ptr(u),
                                       float(timeout)), None)
@@ -592,10 +616,10 @@ NOALLOC_MAX_POINTS = 65536
 
 
 def residual_noalloc(dim, n, h, coeffs: dict, cbar0, dt, X1_ptr, X0_ptr, F_ptr, fnorm2_ptr=None, stream=None,
-                     mode=0):
+                     mode=0, neumann=False):
     """F(X1; X0, dt) on caller-owned device arrays (raw pointers) without any
     device allocation (nks_residual_noalloc).  Returns the status code."""
-    g, k = make_grid(dim, n, h), make_coeffs(coeffs)
+    g, k = make_grid(dim, n, h, neumann), make_coeffs(coeffs)
     return load().nks_residual_noalloc(ctypes.byref(g), ctypes.byref(k), float(cbar0), float(dt), int(mode),
                                        X1_ptr, X0_ptr, F_ptr, fnorm2_ptr, stream)
 

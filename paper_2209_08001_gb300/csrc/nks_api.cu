@@ -201,7 +201,9 @@ DCoef derive_coefficients(const nks_coeffs &c, int dim, double cbar0)
     k.C44 = c.C44 * c.Lscale;
     k.lam = k.C11 + (dim - 1) * k.C12;
     k.elastic = (k.C11 != 0.0 || k.C12 != 0.0 || k.C44 != 0.0) ? 1 : 0;
-    k.nf = 2 + (k.elastic ? dim : 0);
+    k.ne = c.n_eta == 3 ? 3 : 1;
+    k.keta = k.ne == 3 ? 3.0 : 1.0;
+    k.nf = 1 + k.ne + (k.elastic ? dim : 0);
     k.S = c.S;
     for (int i = 1; i < 16; i++) {
         k.ser_c[i] = 1.0 / ((2.0 * i) * (2.0 * i + 1.0));
@@ -356,7 +358,7 @@ static int newton(Problem *P, int mode, double rtol, double atol, int maxit, con
             P->tick(8);
             P->count(launch_copy(n, P->Xt, P->X, P->stream, ba));
             P->count(launch_copy(n, P->Ft, P->F, P->stream, ba));
-            P->count(launch_copy(4 * P->N, P->part_t, P->part, P->stream, ba));
+            P->count(launch_copy((1 + P->k.ne) * (1 + P->k.ne) * P->N, P->part_t, P->part, P->stream, ba));
             P->tock(8);
         }
         for (int i = 0; i < nbt; i++) {
@@ -531,23 +533,41 @@ static int step_batch(Problem *P, const std::vector<char> &on, const double *dt_
     return NKS_OK;
 }
 
-static bool host_in_domain(long long N, const double *c, const double *e)
+// c and the site fractions in (0, 1): c eta and c (4 - 3 eta), or with three order
+// parameters (eta: ne planes of N) c eta_i for i = 1..4, eta_4 = 4 - sum
+static bool host_in_domain(long long N, int ne, const double *c, const double *e)
 {
     for (long long p = 0; p < N; p++) {
-        const double pp = c[p] * e[p], q = c[p] * (4.0 - 3.0 * e[p]);
-        if (!(c[p] > 0.0 && c[p] < 1.0 && pp > 0.0 && pp < 1.0 && q > 0.0 && q < 1.0)) return false;
+        bool ok = c[p] > 0.0 && c[p] < 1.0;
+        if (ne == 3) {
+            const double e4 = 4.0 - e[p] - e[N + p] - e[2 * N + p];
+            for (int i = 0; i < 4; i++) {
+                const double q = c[p] * (i < 3 ? e[i * N + p] : e4);
+                ok = ok && q > 0.0 && q < 1.0;
+            }
+        } else {
+            const double pp = c[p] * e[p], q = c[p] * (4.0 - 3.0 * e[p]);
+            ok = ok && pp > 0.0 && pp < 1.0 && q > 0.0 && q < 1.0;
+        }
+        if (!ok) return false;
     }
     return true;
 }
 
-// fields of one instance into its X^n (c, eta; u = 0) and its level-0 scalars
+static const char *domain_message(int ne)
+{
+    return ne == 3 ? "initial state outside the domain: c and c*eta_i (i = 1..4, eta_4 = 4 - sum) must lie in (0, 1)"
+                   : "initial state outside the domain: c, c*eta and c*(4-3*eta) must lie in (0, 1)";
+}
+
+// fields of one instance into its X^n (c, eta_1..eta_ne; u = 0) and its level-0 scalars
 static void load_fields(Problem *P, int i, const double *c, const double *eta)
 {
     const size_t fb = sizeof(double) * (size_t)P->N;
     double *Xn = shift(P->Xn, (long long)i * P->stride);
     cudaMemsetAsync(Xn, 0, sizeof(double) * (size_t)P->ldv, P->stream);
     cudaMemcpyAsync(Xn, c, fb, cudaMemcpyHostToDevice, P->stream);
-    cudaMemcpyAsync(Xn + P->N, eta, fb, cudaMemcpyHostToDevice, P->stream);
+    cudaMemcpyAsync(Xn + P->N, eta, fb * P->k.ne, cudaMemcpyHostToDevice, P->stream);
     double s = 0.0;
     for (long long p = 0; p < P->N; p++) s += c[p];
     IState &st = P->is[i];
@@ -630,6 +650,10 @@ static int validate(const nks_grid *grid, const nks_coeffs *coeffs, const nks_op
         g_create_error = "grid: dim must be 1..3 and h > 0";
         return NKS_EINVAL;
     }
+    if (grid->bc != NKS_PERIODIC && grid->bc != NKS_NEUMANN) {
+        g_create_error = "grid: bc must be NKS_PERIODIC or NKS_NEUMANN";
+        return NKS_EINVAL;
+    }
     long long npts = 1;
     for (int J = 0; J < grid->dim; J++) {
         if (grid->n[J] < 3) {
@@ -638,9 +662,15 @@ static int validate(const nks_grid *grid, const nks_coeffs *coeffs, const nks_op
         }
         npts *= grid->n[J];
     }
-    if (npts * (2 + grid->dim) >= (1LL << 31)) {
+    if (coeffs->n_eta != 0 && coeffs->n_eta != 1 && coeffs->n_eta != 3) {
+        g_create_error = "coeffs: n_eta must be 1 (0 reads as 1) or 3";
+        return NKS_EINVAL;
+    }
+    // the pointwise derivative block: (1 + n_eta)^2 planes
+    const int ne = coeffs->n_eta == 3 ? 3 : 1, planes = std::max(1 + ne + grid->dim, (1 + ne) * (1 + ne));
+    if (npts * planes >= (1LL << 31)) {
         // stencil kernels index the field planes with 32-bit offsets
-        g_create_error = "grid: (2 + dim) * points must be below 2^31";
+        g_create_error = "grid: (1 + n_eta + dim) * points and (1 + n_eta)^2 * points must be below 2^31";
         return NKS_EINVAL;
     }
     if (nb < 1 || nb > 65535 || (grid->dim == 3 && (long long)grid->n[2] * nb > 65535)) {
@@ -687,10 +717,11 @@ int nks_create_batch(const nks_grid *grid, int nb, const double *c, const double
     }
     long long N = 1;
     for (int J = 0; J < grid->dim; J++) N *= grid->n[J];
+    const int ne = coeffs->n_eta == 3 ? 3 : 1;
     if (c)
         for (int i = 0; i < nb; i++)
-            if (!host_in_domain(N, c + (size_t)i * N, eta + (size_t)i * N)) {
-                g_create_error = "initial state outside the domain: c, c*eta and c*(4-3*eta) must lie in (0, 1)";
+            if (!host_in_domain(N, ne, c + (size_t)i * N, eta + (size_t)i * ne * N)) {
+                g_create_error = domain_message(ne);
                 return NKS_EDOMAIN;
             }
     nks_problem *H = new nks_problem();
@@ -715,6 +746,7 @@ int nks_create_batch(const nks_grid *grid, int nb, const double *c, const double
     g.dim = grid->dim;
     for (int J = 0; J < 3; J++) g.n[J] = J < grid->dim ? grid->n[J] : 1;
     g.N = N;
+    g.bc = grid->bc;
     set_spacing(g, grid->h);
     P->N = N;
     P->k = derive_coefficients(*coeffs, g.dim, 0.0);  // the mean composition of each instance lives in isc
@@ -743,8 +775,9 @@ int nks_create_batch(const nks_grid *grid, int nb, const double *c, const double
                        &P->T64};
     for (double **v : vecs) add(v, vb);
     add(&P->V, vb * (mixed ? 1 : m + 1));
-    add(&P->part, 4 * fb);
-    add(&P->part_t, 4 * fb);
+    const int npart = (1 + P->k.ne) * (1 + P->k.ne);  // pointwise derivative block per point
+    add(&P->part, npart * fb);
+    add(&P->part_t, npart * fb);
     add(&P->mob, (size_t)g.dim * fb);
     add(&P->tr0, fb);
     add(&P->Gc, fb);
@@ -761,7 +794,7 @@ int nks_create_batch(const nks_grid *grid, int nb, const double *c, const double
         add(&P->Vf, fvb * (m + 1));
         add(&P->Wf, fvb);
         add(&P->Zf, fvb);
-        add(&P->partf, sizeof(float) * 4 * (size_t)g.N);
+        add(&P->partf, sizeof(float) * npart * (size_t)g.N);
         add(&P->mobf, sizeof(float) * g.dim * (size_t)g.N);
     }
     ras_slab_items(P, items);
@@ -791,7 +824,7 @@ int nks_create_batch(const nks_grid *grid, int nb, const double *c, const double
     cudaMemsetAsync(P->dmask, 0, sizeof(int) * kMasks * nb, P->stream);
     rc = P->sync_check("create");
     if (!rc && c) {
-        for (int i = 0; i < nb; i++) load_fields(P, i, c + (size_t)i * N, eta + (size_t)i * N);
+        for (int i = 0; i < nb; i++) load_fields(P, i, c + (size_t)i * N, eta + (size_t)i * ne * N);
         rc = init_instances(P, std::vector<char>(nb, 1));
     }
     if (rc) {
@@ -840,8 +873,8 @@ int nks_batch_load(nks_problem *H, int slot, const double *c, const double *eta)
         P->err = "null argument";
         return NKS_EINVAL;
     }
-    if (!host_in_domain(P->N, c, eta)) {
-        P->err = "initial state outside the domain: c, c*eta and c*(4-3*eta) must lie in (0, 1)";
+    if (!host_in_domain(P->N, P->k.ne, c, eta)) {
+        P->err = domain_message(P->k.ne);
         return NKS_EDOMAIN;
     }
     load_fields(P, slot, c, eta);
@@ -928,8 +961,9 @@ int nks_batch_get_fields(const nks_problem *H, int slot, double *c, double *eta,
     const size_t fb = sizeof(double) * (size_t)P->N;
     const double *Xn = shift(P->Xn, (long long)slot * P->stride);
     if (c) cudaMemcpyAsync(c, Xn, fb, cudaMemcpyDeviceToHost, P->stream);
-    if (eta) cudaMemcpyAsync(eta, Xn + P->N, fb, cudaMemcpyDeviceToHost, P->stream);
-    if (u && P->k.elastic) cudaMemcpyAsync(u, Xn + 2 * P->N, fb * P->g.dim, cudaMemcpyDeviceToHost, P->stream);
+    if (eta) cudaMemcpyAsync(eta, Xn + P->N, fb * P->k.ne, cudaMemcpyDeviceToHost, P->stream);
+    if (u && P->k.elastic)
+        cudaMemcpyAsync(u, Xn + (1 + P->k.ne) * P->N, fb * P->g.dim, cudaMemcpyDeviceToHost, P->stream);
     return P->sync_check("get_fields");
 }
 

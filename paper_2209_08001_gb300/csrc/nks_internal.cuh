@@ -1,7 +1,8 @@
 // nks_internal.cuh -- shared declarations of the GB300 NKS solver.
 //
 // Layout in HBM: every state vector is structure-of-arrays, field-major:
-//   X[f * N + p],  f = 0 (c), 1 (eta), 2.. (u_1..u_d),  p = x + nx (y + ny z).
+//   X[f * N + p],  f = 0 (c), 1..ne (eta_1..eta_ne), 1 + ne.. (u_1..u_d),
+//   p = x + nx (y + ny z), with ne = 1 (reduced model) or 3 (App. A).
 // One Newton iterate therefore streams nf contiguous, coalesced planes.
 #pragma once
 
@@ -17,8 +18,10 @@ namespace nks {
 
 constexpr int kRedBlocks = 608;    // 4 x 152 SMs: fixed reduction grid (deterministic sums)
 constexpr int kRedThreads = 256;
-constexpr int kMaxNf = 5;          // c, eta, u_1..u_3
-constexpr int kMaxRow = 72;        // longest Jacobian row: 71 entries (3-D c-row)
+constexpr int kMaxNf = 7;          // c, eta_1..eta_3, u_1..u_3
+constexpr int kMaxRow = 128;       // longest Jacobian row (3-D c-row): 71 entries, 83 with Neumann
+                                   // boundaries; 85 / 97 with three order parameters (at most 128:
+                                   // the factor kernel marks present slots in two 64-bit words)
 constexpr int kMaxRestart = 64;
 
 // Grid as seen by the kernels.
@@ -28,6 +31,7 @@ struct DGrid {
     long long N;
     double h;
     double ih, ih2, i2h;  // 1/h, 1/h^2, 1/(2h), formed on the host
+    int bc;               // NKS_PERIODIC or NKS_NEUMANN (mirror ghost cells)
 };
 
 inline void set_spacing(DGrid &g, double h)
@@ -51,6 +55,8 @@ struct DCoef {
     int S;
     int elastic;
     int nf;
+    int ne;                                      // order parameters: 1 or 3 (App. A)
+    double keta;                                 // kinetic factor of the eta rows: 1, or 3 with ne = 3
 };
 
 // Batches.  A problem holds nb instances of the same grid, coefficients and
@@ -87,6 +93,15 @@ enum { I_DT = 0, I_CBAR0 = 1, I_LAM = 2, I_IDT = 3, I_NSC = 8 };
 
 __host__ __device__ inline int wrapi(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
+// coordinate of a one-cell step s (|s| <= 1) from a on an axis of n cells: periodic
+// wrap, or (Neumann) the cell itself when the step leaves the grid (mirror ghost)
+__host__ __device__ inline int stepi(int a, int s, int n, int bc)
+{
+    const int b = a + s;
+    if (bc) return (b < 0 || b >= n) ? a : b;
+    return wrapi(b, n);
+}
+
 __host__ __device__ inline void coords_of(const DGrid &g, long long p, int &x, int &y, int &z)
 {
     x = (int)(p % g.n[0]);
@@ -100,10 +115,11 @@ __host__ __device__ inline long long index_of(const DGrid &g, int x, int y, int 
     return (long long)x + (long long)g.n[0] * ((long long)y + (long long)g.n[1] * z);
 }
 
-// neighbour of (x, y, z) shifted by (dx, dy, dz), periodic (|shift| < n)
+// neighbour of (x, y, z) shifted by (dx, dy, dz), each |d| <= 1: periodic, or the
+// mirror ghost's cell with Neumann boundaries
 __host__ __device__ inline long long nbr_of(const DGrid &g, int x, int y, int z, int dx, int dy, int dz)
 {
-    return index_of(g, wrapi(x + dx, g.n[0]), wrapi(y + dy, g.n[1]), wrapi(z + dz, g.n[2]));
+    return index_of(g, stepi(x, dx, g.n[0], g.bc), stepi(y, dy, g.n[1], g.bc), stepi(z, dz, g.n[2], g.bc));
 }
 
 __device__ inline long long nbrJ(const DGrid &g, int x, int y, int z, int J, int s)

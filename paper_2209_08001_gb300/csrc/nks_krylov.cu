@@ -614,7 +614,7 @@ static void prepare_operator(Problem *P, int mode, const Bat &bt)
 // FP32 copies of the Jacobian action's coefficients at the current iterate
 void refresh_f32_coefficients(Problem *P, const Bat &bt)
 {
-    P->count(launch_convert(4 * P->N, P->part, P->partf, P->stream, bt));
+    P->count(launch_convert((1 + P->k.ne) * (1 + P->k.ne) * P->N, P->part, P->partf, P->stream, bt));
     P->count(launch_convert(P->g.dim * P->N, P->mob, P->mobf, P->stream, bt));
 }
 

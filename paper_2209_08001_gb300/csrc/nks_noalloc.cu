@@ -44,8 +44,18 @@ extern "C" int nks_residual_noalloc(const nks_grid *grid, const nks_coeffs *coef
         set_thread_error("nks_residual_noalloc: invalid argument");
         return NKS_EINVAL;
     }
+    if (grid->bc != NKS_PERIODIC && grid->bc != NKS_NEUMANN) {
+        set_thread_error("nks_residual_noalloc: invalid argument");
+        return NKS_EINVAL;
+    }
+    // the scratch holds the 2 x 2 pointwise block of one order parameter
+    if (coeffs->n_eta != 0 && coeffs->n_eta != 1) {
+        set_thread_error("nks_residual_noalloc: serves the model with one order parameter (n_eta 0 or 1)");
+        return NKS_EINVAL;
+    }
     DGrid g{};
     g.dim = grid->dim;
+    g.bc = grid->bc;
     for (int J = 0; J < 3; J++) g.n[J] = J < grid->dim ? grid->n[J] : 1;
     for (int J = 0; J < g.dim; J++) {
         if (g.n[J] < 3) {

@@ -95,42 +95,66 @@ struct RasPlan {
     double *proj = nullptr;         // projection sums
     int nmodes = 1;                 // null modes per displacement component
     int evenmask = 0;
+    double rot_inorm[3] = {0.0, 0.0, 0.0};  // Neumann: 1/|rotation mode|^2 per plane (0: no mode)
     bool attr_set = false, attr_set32 = false;
 };
 
-template <int D, int NF>
+// V: the pattern variant (bit 0: elasticity under Neumann boundaries, bit 1:
+// three order parameters; see make_pattern)
+template <int D, int NF, int V = 0>
 struct Pat {
-    static constexpr Pattern v = make_pattern<D, NF>();
+    static constexpr Pattern v = make_pattern<D, NF, V>();
 };
 
-template <int D, int NF, bool FWD>
+template <int D, int NF, bool FWD, int V = 0>
 struct SPlan {
-    static constexpr SweepPlan v = make_sweep_plan<D, NF, FWD>();
+    static constexpr SweepPlan v = make_sweep_plan<D, NF, FWD, V>();
 };
 
-template <int D, int NF>
+template <int D, int NF, int V = 0>
 struct Sched {
-    static constexpr SweepPlan fwd = SPlan<D, NF, true>::v;
-    static constexpr SweepPlan bwd = SPlan<D, NF, false>::v;
+    static constexpr SweepPlan fwd = SPlan<D, NF, true, V>::v;
+    static constexpr SweepPlan bwd = SPlan<D, NF, false, V>::v;
     static constexpr int ntask = fwd.ntask > bwd.ntask ? fwd.ntask : bwd.ntask;
     static constexpr int npart = fwd.npart > bwd.npart ? fwd.npart : bwd.npart;
 };
 
 
-static Pattern compile_time_pattern(int d, int nf)
+// every (dimension, fields, pattern variant) the solver instantiates: the reduced
+// model (variants 0, 1) and three order parameters (2, 3), without and with
+// elasticity
+#define NKS_PAT_CASES(X)                                                                                      \
+    X(1, 2, 0) X(1, 3, 0) X(2, 2, 0) X(2, 4, 0) X(3, 2, 0) X(3, 5, 0) X(1, 3, 1) X(2, 4, 1) X(3, 5, 1)       \
+    X(1, 4, 2) X(1, 5, 2) X(2, 4, 2) X(2, 6, 2) X(3, 4, 2) X(3, 7, 2) X(1, 5, 3) X(2, 6, 3) X(3, 7, 3)
+
+static Pattern compile_time_pattern(int d, int nf, int var)
 {
-    switch (d * 10 + nf) {
-    case 12: return Pat<1, 2>::v;
-    case 13: return Pat<1, 3>::v;
-    case 22: return Pat<2, 2>::v;
-    case 24: return Pat<2, 4>::v;
-    case 32: return Pat<3, 2>::v;
-    case 35: return Pat<3, 5>::v;
+    switch (d * 100 + nf * 10 + var) {
+#define NKS_PAT_CASE(D, NF, V) \
+    case D * 100 + NF * 10 + V: return Pat<D, NF, V>::v;
+        NKS_PAT_CASES(NKS_PAT_CASE)
+#undef NKS_PAT_CASE
     }
     return Pattern{};
 }
 
+// the pattern variant of a problem: bit 0 for elasticity under Neumann boundaries,
+// bit 1 for three order parameters
+static int pat_var(const Problem *P)
+{
+    return (P->g.bc == NKS_NEUMANN && P->k.elastic ? 1 : 0) + (P->k.ne == 3 ? 2 : 0);
+}
+
 __host__ __device__ static inline long long pad4(long long n) { return (n + 3) & ~3LL; }
+
+// centred staircase on an axis of n cells (n even) and the axes of rotation plane q
+// (0: (0, 1), 1: (0, 2), 2: (1, 2)); see ModeMasks
+__host__ __device__ inline double staircase(int x, int n) { return (double)((x + 1) / 2) - 0.25 * (double)n; }
+
+__host__ __device__ constexpr int plane_axis(int q, int which)
+{
+    return which == 0 ? (q == 2 ? 1 : 0) : (q == 0 ? 1 : 2);
+}
 
 // Row stride of the FP32 point-major factor layout for n values per point: a
 // multiple of 4 (16-byte loads) whose quotient by 4 is odd, so the 16-byte loads
@@ -141,9 +165,9 @@ __host__ __device__ constexpr int pm_stride(int n)
     return (s / 4) % 2 == 1 ? s : s + 4;
 }
 
-template <int D, int NF>
+template <int D, int NF, int V = 0>
 struct PM {
-    static constexpr Pattern P = make_pattern<D, NF>();
+    static constexpr Pattern P = make_pattern<D, NF, V>();
     static constexpr int SF = pm_stride(P.nlow), SB = pm_stride(P.nup + NF), PP = P.nlow + P.nup + NF;
 };
 
@@ -196,33 +220,29 @@ static size_t apply_smem(const RasPlan *R, int nf, size_t tsize, bool with_x)
     return b;
 }
 
-static int sweep_partials(int d, int nf)
+static int sweep_partials(int d, int nf, int bc)
 {
-    switch (d * 10 + nf) {
-    case 12: return Sched<1, 2>::npart;
-    case 13: return Sched<1, 3>::npart;
-    case 22: return Sched<2, 2>::npart;
-    case 24: return Sched<2, 4>::npart;
-    case 32: return Sched<3, 2>::npart;
-    case 35: return Sched<3, 5>::npart;
+    switch (d * 100 + nf * 10 + bc) {
+#define NKS_NPART(D, NF, V) \
+    case D * 100 + NF * 10 + V: return Sched<D, NF, V>::npart;
+        NKS_PAT_CASES(NKS_NPART)
+#undef NKS_NPART
     }
     return 0;
 }
 
-static int sweep_tasks(int d, int nf)
+static int sweep_tasks(int d, int nf, int bc)
 {
-    switch (d * 10 + nf) {
-    case 12: return Sched<1, 2>::ntask;
-    case 13: return Sched<1, 3>::ntask;
-    case 22: return Sched<2, 2>::ntask;
-    case 24: return Sched<2, 4>::ntask;
-    case 32: return Sched<3, 2>::ntask;
-    case 35: return Sched<3, 5>::ntask;
+    switch (d * 100 + nf * 10 + bc) {
+#define NKS_NTASK(D, NF, V) \
+    case D * 100 + NF * 10 + V: return Sched<D, NF, V>::ntask;
+        NKS_PAT_CASES(NKS_NTASK)
+#undef NKS_NTASK
     }
     return 1;
 }
 
-static int fp64_sweep_regs(int d, int nf, bool xs);  // registers per thread of the FP64 sweep
+static int fp64_sweep_regs(int d, int nf, int bc, bool xs);  // registers per thread of the FP64 sweep
 
 static void sm_limits(int &nsm, int &smem_sm)
 {
@@ -244,13 +264,13 @@ static void choose_x64(const Problem *P, RasPlan *R, int nf)
 {
     int nsm, smem_sm;
     sm_limits(nsm, smem_sm);
-    const int d = P->g.dim, ntask = sweep_tasks(d, nf);
+    const int d = P->g.dim, ntask = sweep_tasks(d, nf, pat_var(P));
     const int wpt = std::max(1, std::min((R->maxcnt + 31) / 32, 32 / ntask));
     const int threads = ntask * wpt * 32;
     const long long blocks = (long long)R->nsub * std::max(1, P->nb);
     auto waves = [&](bool xs) -> long long {
         const size_t b = apply_smem(R, nf, sizeof(double), xs);
-        const int regs = std::max(1, fp64_sweep_regs(d, nf, xs));
+        const int regs = std::max(1, fp64_sweep_regs(d, nf, pat_var(P), xs));
         int per_sm = (int)((size_t)smem_sm / (b + 1024));
         per_sm = std::min(per_sm, 2048 / threads);
         per_sm = std::min(per_sm, 65536 / (threads * ((regs + 7) & ~7)));
@@ -306,7 +326,7 @@ int ras_plan_create(Problem *P, std::string &err)
     RasPlan *R = new RasPlan();
     P->ras = R;
     const int d = P->g.dim, nf = P->nf;
-    const Pattern CP = compile_time_pattern(d, nf);
+    const Pattern CP = compile_time_pattern(d, nf, pat_var(P));
     if (CP.nf != nf) {
         err = "internal: no Jacobian pattern for this dimension";
         return NKS_EINVAL;
@@ -382,7 +402,20 @@ int ras_plan_create(Problem *P, std::string &err)
                 const int sidx[3] = {s0, s1, s2};
                 SubInfo &si = infos[s];
                 for (int J = 0; J < 3; J++) {
-                    if (J < d) {
+                    if (J < d && P->g.bc == NKS_NEUMANN) {
+                        // Neumann: the overlapped box stops at the boundary (no wrap)
+                        const int n = P->g.n[J];
+                        const int o0 = (int)((long long)sidx[J] * n / sub[J]);
+                        const int o1 = (int)((long long)(sidx[J] + 1) * n / sub[J]);
+                        si.org[J] = std::max(0, o0 - delta);
+                        si.L[J] = std::min(n, o1 + delta) - si.org[J];
+                        si.own0[J] = o0 - si.org[J];
+                        si.own1[J] = o1 - si.org[J];
+                        if (o1 - o0 < 1) {
+                            err = "decomposition: more subdomains than cells along an axis";
+                            return NKS_EINVAL;
+                        }
+                    } else if (J < d) {
                         const int n = P->g.n[J];
                         const int o0 = (int)((long long)sidx[J] * n / sub[J]);
                         const int o1 = (int)((long long)(sidx[J] + 1) * n / sub[J]);
@@ -458,7 +491,7 @@ int ras_plan_create(Problem *P, std::string &err)
                 si.scr_off = scr_off;
                 scr_off += (long long)nf * si.npx;
             }
-    R->npart = sweep_partials(d, nf);
+    R->npart = sweep_partials(d, nf, pat_var(P));
     {
         const LaneShape sh = d == 3 ? kShape3 : kShape2;
         bool uni = d >= 2;
@@ -476,11 +509,23 @@ int ras_plan_create(Problem *P, std::string &err)
         err = "decomposition: subdomain boxes too large for the Schwarz kernel (use more subdomains)";
         return NKS_EINVAL;
     }
-    // null modes of the centred-difference strain: sign patterns over the even axes
+    // null modes of the centred-difference strain: sign patterns over the even axes on a
+    // periodic grid; with Neumann boundaries (mirror ghosts) the translations and the
+    // discrete rotations of the planes whose two axes have an even number of cells
     R->evenmask = 0;
     for (int J = 0; J < d; J++)
-        if (P->g.n[J] % 2 == 0) R->evenmask |= 1 << J;
+        if (P->g.n[J] % 2 == 0 && P->g.bc == NKS_PERIODIC) R->evenmask |= 1 << J;
     R->nmodes = 1 << __builtin_popcount(R->evenmask);
+    for (int q = 0; q < 3; q++) {
+        const int A = plane_axis(q, 0), B = plane_axis(q, 1);
+        R->rot_inorm[q] = 0.0;
+        if (P->g.bc != NKS_NEUMANN || B >= d || P->g.n[A] % 2 || P->g.n[B] % 2) continue;
+        // |m|^2 = sum over the grid of S_B(x_B)^2 + S_A(x_A)^2
+        double sa = 0.0, sb = 0.0;
+        for (int x = 0; x < P->g.n[A]; x++) sa += staircase(x, P->g.n[A]) * staircase(x, P->g.n[A]);
+        for (int x = 0; x < P->g.n[B]; x++) sb += staircase(x, P->g.n[B]) * staircase(x, P->g.n[B]);
+        R->rot_inorm[q] = 1.0 / ((double)P->N / P->g.n[B] * sb + (double)P->N / P->g.n[A] * sa);
+    }
 
     auto up = [&](void **dst, const void *src, size_t bytes) -> bool {
         *dst = P->dalloc(bytes);
@@ -544,14 +589,39 @@ struct FacTables {
 // outside the box dropped)
 struct DevAcc {
     double *vals;
+    unsigned long long *pres;  // bit s: a path of the row ends in slot s (the row's own pattern)
     const short *slotmap;  // block of row f
     int nf, lx, ly, lz;
     const SubInfo *si;
-    __host__ __device__ void operator()(int dx, int dy, int dz, int fc, double v)
+    int gx, gy, gz;        // the row's point in the grid
+    int n0, n1, n2, bc;    // grid extents, boundary kind
+    // end of the path o then e from the row's point, as an offset: the sum on a
+    // periodic grid; with Neumann boundaries each step stays on the cell where it
+    // would leave the grid (mirror ghost)
+    __host__ __device__ void end(int o, int e, int g, int n, int &d) const
     {
+        const int a = stepi(g, o, n, bc);
+        d = bc ? stepi(a, e, n, bc) - g : o + e;
+    }
+    __host__ __device__ void operator()(int ox, int oy, int oz, int ex, int ey, int ez, int fc, double v)
+    {
+        int dx, dy, dz;
+        end(ox, ex, gx, n0, dx);
+        end(oy, ey, gy, n1, dy);
+        end(oz, ez, gz, n2, dz);
         if (!inbox(*si, lx + dx, ly + dy, lz + dz)) return;
         const int s = slotmap[((dz + 2) * 25 + (dy + 2) * 5 + (dx + 2)) * nf + fc];
-        if (s >= 0) vals[s] += v;
+        if (s >= 0) {
+            vals[s] += v;
+            pres[s >> 6] |= 1ull << (s & 63);
+        }
+    }
+    // -1 when the one-cell step o stays on the cell (Neumann boundary), else 1
+    __host__ __device__ double flip(int ox, int oy, int oz) const
+    {
+        if (!bc) return 1.0;
+        const bool out = gx + ox < 0 || gx + ox >= n0 || gy + oy < 0 || gy + oy >= n1 || gz + oz < 0 || gz + oz >= n2;
+        return out ? -1.0 : 1.0;
     }
 };
 
@@ -593,16 +663,22 @@ __global__ void k_ras_factor(DGrid g, DCoef k, Bat bt, const double *__restrict_
             const long long gp = index_of(g, gx, gy, gz);
             RowCtx rc{};
             if (mode == 0) {
+                // pointwise block part[(a * (1 + ne) + b) N + p] = dG_a / dx_b, x = (c, eta_1..eta_ne)
+                const int ne = k.ne, w = 1 + ne;
                 rc.a0[0] = part[gp];
-                rc.a1[0] = part[N + gp];
-                rc.a2 = part[2 * N + gp];
-                rc.a3 = part[3 * N + gp];
+                for (int j = 0; j < ne; j++) {
+                    rc.a1[0][j] = part[(1 + j) * N + gp];
+                    rc.a2[j] = part[(long long)(1 + j) * w * N + gp];
+                    for (int i = 0; i < ne; i++) rc.a3[j][i] = part[((long long)(1 + j) * w + 1 + i) * N + gp];
+                }
                 for (int J = 0; J < D; J++) {
                     const long long pp = nbrJ(g, gx, gy, gz, J, +1), pm = nbrJ(g, gx, gy, gz, J, -1);
                     rc.a0[1 + 2 * J] = part[pp];
-                    rc.a1[1 + 2 * J] = part[N + pp];
                     rc.a0[2 + 2 * J] = part[pm];
-                    rc.a1[2 + 2 * J] = part[N + pm];
+                    for (int j = 0; j < ne; j++) {
+                        rc.a1[1 + 2 * J][j] = part[(1 + j) * N + pp];
+                        rc.a1[2 + 2 * J][j] = part[(1 + j) * N + pm];
+                    }
                     rc.Mp[J] = mob[J * N + gp];
                     rc.Mm[J] = mob[J * N + pm];
                 }
@@ -610,7 +686,12 @@ __global__ void k_ras_factor(DGrid g, DCoef k, Bat bt, const double *__restrict_
             for (int f = 0; f < nf; f++) {
                 const int len = T.len[f], r0 = T.rowoff[f];
                 for (int a = 0; a < len; a++) vals[a] = 0.0;
-                DevAcc acc{vals, slotmap + (size_t)f * 125 * nf, nf, lx, ly, lz, &si};
+                // the slots this row's point has: with Neumann boundaries the compile-time
+                // pattern is the union over all places in the grid, and ILU(0) fills only
+                // the point's own pattern (as on a periodic grid, where they coincide)
+                unsigned long long pres[2] = {0ull, 0ull};
+                DevAcc acc{vals, pres, slotmap + (size_t)f * 125 * nf, nf, lx, ly, lz, &si, gx, gy, gz, g.n[0],
+                           g.n[1], g.n[2], g.bc};
                 jac_row(acc, f, k, D, g.h, dt, mode, rc);
                 for (int a = 0; a < T.diag[f]; a++) {
                     const char4 o = tmpl[r0 + a];
@@ -635,7 +716,7 @@ __global__ void k_ras_factor(DGrid g, DCoef k, Bat bt, const double *__restrict_
                     // a_ib -= l * u_kb for every later column b of row i present in row k
                     for (int u = upd_ptr[r0 + a]; u < upd_ptr[r0 + a + 1]; u++) {
                         const short2 bc = upd[u];
-                        vals[bc.x] -= l * U[(long long)st[rk + bc.y] * qcp + qk];
+                        if ((pres[bc.x >> 6] >> (bc.x & 63)) & 1ull) vals[bc.x] -= l * U[(long long)st[rk + bc.y] * qcp + qk];
                     }
                 }
                 const double piv = vals[T.diag[f]];
@@ -719,16 +800,16 @@ __device__ __forceinline__ bool nb_inbox(int lx, int ly, int lz, const SubInfo &
 }
 
 // sum over pattern slots [B, E) of stored entries times x at their columns (see row_dot)
-template <int D, int NF, int B, int E, typename T>
+template <int D, int NF, int B, int E, typename T, int V>
 __device__ __forceinline__ T slot_sum(const T *__restrict__ part, long long cp, int k, const T *x, int np, int lp,
                                       int lx, int ly, int lz, const SubInfo &si, int sy, int sz)
 {
     T s = (T)0;
     static_for<B, E>([&](auto ic) {
         constexpr int a = decltype(ic)::value;
-        constexpr int dx = Pat<D, NF>::v.dx[a], dy = Pat<D, NF>::v.dy[a], dz = Pat<D, NF>::v.dz[a];
-        constexpr int fc = Pat<D, NF>::v.fc[a];
-        constexpr int row = Pat<D, NF>::v.st[a];
+        constexpr int dx = Pat<D, NF, V>::v.dx[a], dy = Pat<D, NF, V>::v.dy[a], dz = Pat<D, NF, V>::v.dz[a];
+        constexpr int fc = Pat<D, NF, V>::v.fc[a];
+        constexpr int row = Pat<D, NF, V>::v.st[a];
         const bool ok = nb_inbox<dx, dy, dz>(lx, ly, lz, si);
         const int idx = ok ? lp + dx + sy * dy + sz * dz : lp;
         s += part[row * cp + k] * x[fc * np + idx];
@@ -737,18 +818,18 @@ __device__ __forceinline__ T slot_sum(const T *__restrict__ part, long long cp, 
 }
 
 // Stage A of one sweep over a level: task t of the compile-time schedule for point k.
-template <int D, int NF, bool FWD, typename T>
+template <int D, int NF, bool FWD, typename T, int V>
 __device__ __forceinline__ void stage_a(int task, int kk, int lp, int lx, int ly, int lz, const T *B, long long cp,
                                         T *x, int np, T *pt, int pstride, const SubInfo &si, int sy, int sz)
 {
-    using SP = SPlan<D, NF, FWD>;
+    using SP = SPlan<D, NF, FWD, V>;
     static_for<0, SP::v.ntask>([&](auto ti) {
         constexpr int t = decltype(ti)::value;
         if (task != t) return;
         constexpr int f = SP::v.t_row[t];
         constexpr int tb = SP::v.t_b[t], te = SP::v.t_e[t], tp = SP::v.t_part[t];
-        constexpr int drow = Pat<D, NF>::v.nup + f;  // inverse pivot row in the backward part
-        const T s = slot_sum<D, NF, tb, te, T>(B, cp, kk, x, np, lp, lx, ly, lz, si, sy, sz);
+        constexpr int drow = Pat<D, NF, V>::v.nup + f;  // inverse pivot row in the backward part
+        const T s = slot_sum<D, NF, tb, te, T, V>(B, cp, kk, x, np, lp, lx, ly, lz, si, sy, sz);
         if constexpr (tp >= 0) {
             pt[tp * pstride + kk] = s;
         } else if constexpr (FWD) {
@@ -760,18 +841,18 @@ __device__ __forceinline__ void stage_a(int task, int kk, int lp, int lx, int ly
 }
 
 // Stage B: rows of one point finished from their partials and same-point entries, in sweep order.
-template <int D, int NF, bool FWD, typename T>
+template <int D, int NF, bool FWD, typename T, int V>
 __device__ __forceinline__ void stage_b(int kk, int lp, int lx, int ly, int lz, const T *B, long long cp, T *x,
                                         int np, const T *pt, int pstride, const SubInfo &si, int sy, int sz)
 {
-    using SP = SPlan<D, NF, FWD>;
+    using SP = SPlan<D, NF, FWD, V>;
     static_for<0, NF>([&](auto fi) {
         constexpr int f = FWD ? decltype(fi)::value : NF - 1 - decltype(fi)::value;
         constexpr int stb = SP::v.row_stage_b[f];
         if constexpr (stb) {
             constexpr int sb = SP::v.same_b[f], se = SP::v.same_e[f], pb = SP::v.row_pb[f], pe = SP::v.row_pe[f];
-            constexpr int drow = Pat<D, NF>::v.nup + f;
-            T s = slot_sum<D, NF, sb, se, T>(B, cp, kk, x, np, lp, lx, ly, lz, si, sy, sz);
+            constexpr int drow = Pat<D, NF, V>::v.nup + f;
+            T s = slot_sum<D, NF, sb, se, T, V>(B, cp, kk, x, np, lp, lx, ly, lz, si, sy, sz);
             static_for<pb, pe>([&](auto pi) {
                 constexpr int q = decltype(pi)::value;
                 s += pt[q * pstride + kk];
@@ -792,7 +873,7 @@ __device__ __forceinline__ void stage_b(int kk, int lp, int lx, int ly, int lz, 
 // occupies the FP64 pipe for less time than a full one, so spreading shortens the
 // row chains but adds pipe time: 2 warps measured fastest on the 2-D 68^2 boxes at
 // two boxes per SM, 4 on the 3-D 18^3 boxes).
-template <int D, int NF, typename T, typename TV, bool XS>
+template <int D, int NF, typename T, typename TV, bool XS, int V>
 __global__ void __launch_bounds__(1024) k_ras_apply(DGrid g, Bat bt, const SubInfo *__restrict__ subs, const int *__restrict__ lvl_ptr,
                             const long long *__restrict__ lvl_blk, const int *__restrict__ lvl_lp,
                             const T *__restrict__ fac, const TV *__restrict__ r, TV *__restrict__ z,
@@ -810,7 +891,7 @@ __global__ void __launch_bounds__(1024) k_ras_apply(DGrid g, Bat bt, const SubIn
     cpart = shift(cpart, io);
     csum = shift(csum, io);
     ticket = shift(ticket, io);
-    constexpr Pattern PT = Pat<D, NF>::v;
+    constexpr Pattern PT = Pat<D, NF, V>::v;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
     int *lps = reinterpret_cast<int *>(smem + 16);
@@ -825,7 +906,7 @@ __global__ void __launch_bounds__(1024) k_ras_apply(DGrid g, Bat bt, const SubIn
     T *x;
     if constexpr (XS)
         x = reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(pt) +
-                                  pad16((size_t)Sched<D, NF>::npart * pstride * sizeof(T)));
+                                  pad16((size_t)Sched<D, NF, V>::npart * pstride * sizeof(T)));
     else
         x = scratch + si.scr_off;
     const int np = si.np, nlev = si.nlev;  // x holds NF planes of si.npx (padded) entries
@@ -913,8 +994,8 @@ __global__ void __launch_bounds__(1024) k_ras_apply(DGrid g, Bat bt, const SubIn
                 const int pk = lps[base + kq];
                 const int lx = pk & 1023, ly = (pk >> 10) & 1023, lz = pk >> 20;
                 const int lp = lx + sy * ly + sz * lz;
-                if (fwd) stage_a<D, NF, true, T>(task, kq, lp, lx, ly, lz, B, cp, x, npx, pt, pstride, si, sy, sz);
-                else stage_a<D, NF, false, T>(task, kq, lp, lx, ly, lz, B, cp, x, npx, pt, pstride, si, sy, sz);
+                if (fwd) stage_a<D, NF, true, T, V>(task, kq, lp, lx, ly, lz, B, cp, x, npx, pt, pstride, si, sy, sz);
+                else stage_a<D, NF, false, T, V>(task, kq, lp, lx, ly, lz, B, cp, x, npx, pt, pstride, si, sy, sz);
             }
         __syncthreads();
         // stage B: one thread per point, the points spread over the first nwb warps
@@ -924,8 +1005,8 @@ __global__ void __launch_bounds__(1024) k_ras_apply(DGrid g, Bat bt, const SubIn
                 const int pk = lps[base + k];
                 const int lx = pk & 1023, ly = (pk >> 10) & 1023, lz = pk >> 20;
                 const int lp = lx + sy * ly + sz * lz;
-                if (fwd) stage_b<D, NF, true, T>(k, lp, lx, ly, lz, B, cp, x, npx, pt, pstride, si, sy, sz);
-                else stage_b<D, NF, false, T>(k, lp, lx, ly, lz, B, cp, x, npx, pt, pstride, si, sy, sz);
+                if (fwd) stage_b<D, NF, true, T, V>(k, lp, lx, ly, lz, B, cp, x, npx, pt, pstride, si, sy, sz);
+                else stage_b<D, NF, false, T, V>(k, lp, lx, ly, lz, B, cp, x, npx, pt, pstride, si, sy, sz);
             }
         failed = __syncthreads_or(!ok);
         if (failed) break;
@@ -979,11 +1060,11 @@ __global__ void __launch_bounds__(1024) k_ras_apply(DGrid g, Bat bt, const SubIn
 // cell of the zero-filled planes or a zero guard cell (0 times a finite value).
 // Otherwise the neighbour is bounds-checked against the box and an outside
 // column reads x at lp itself (times 0).
-template <int D, int NF, bool FWD, bool HALO>
+template <int D, int NF, bool FWD, bool HALO, int V>
 __device__ __forceinline__ void point_rows_pm(const float *__restrict__ Bk, float *x, int npx, int lp, int lx, int ly,
                                               int lz, const SubInfo &si, int sy, int sz)
 {
-    constexpr Pattern PT = Pat<D, NF>::v;
+    constexpr Pattern PT = Pat<D, NF, V>::v;
     constexpr int NR = FWD ? PT.nlow : PT.nup + NF;
     constexpr int NV = (NR + 3) / 4;
     float4 bv[NV];
@@ -1037,7 +1118,7 @@ __device__ __forceinline__ void point_rows_pm(const float *__restrict__ Bk, floa
 // branch-free layout (1-D and 2-D: kHalo zero cells around the box; 3-D: the
 // box planes between `guard` zero cells on each side), the point table then
 // holds 16-bit x indices.
-template <int D, int NF, int NBUF, bool XS, bool HALO, bool SHAPE>
+template <int D, int NF, int NBUF, bool XS, bool HALO, bool SHAPE, int V>
 __global__ void __launch_bounds__(256) k_ras_apply_lane(DGrid g, Bat bt, const SubInfo *__restrict__ subs, const int *__restrict__ lvl_ptr,
                             const long long *__restrict__ lvl_blk, const int *__restrict__ lvl_lp,
                             const float *__restrict__ fac, const float *__restrict__ r, float *__restrict__ z,
@@ -1050,7 +1131,7 @@ __global__ void __launch_bounds__(256) k_ras_apply_lane(DGrid g, Bat bt, const S
     constexpr LaneShape SH = D == 3 ? kShape3 : kShape2;
     using T = float;
     using LT = typename std::conditional<HALO, unsigned short, int>::type;
-    using L = PM<D, NF>;
+    using L = PM<D, NF, V>;
     long long io;
     if (!inst_off(bt, blockIdx.y, io)) return;
     fac = shift(fac, io);
@@ -1206,14 +1287,14 @@ __global__ void __launch_bounds__(256) k_ras_apply_lane(DGrid g, Bat bt, const S
             for (int k = tid; k < cnt; k += blockDim.x) {
                 if constexpr (HALO) {
                     const int lp = lps[base + k];
-                    if (fwd) point_rows_pm<D, NF, true, true>(B + k * L::SF, x, npx, lp, 0, 0, 0, si, sy, sz);
-                    else point_rows_pm<D, NF, false, true>(B + k * L::SB, x, npx, lp, 0, 0, 0, si, sy, sz);
+                    if (fwd) point_rows_pm<D, NF, true, true, V>(B + k * L::SF, x, npx, lp, 0, 0, 0, si, sy, sz);
+                    else point_rows_pm<D, NF, false, true, V>(B + k * L::SB, x, npx, lp, 0, 0, 0, si, sy, sz);
                 } else {
                     const int pk = lps[base + k];
                     const int lx = pk & 1023, ly = (pk >> 10) & 1023, lz = pk >> 20;
                     const int lp = lx + sy * ly + sz * lz;
-                    if (fwd) point_rows_pm<D, NF, true, false>(B + k * L::SF, x, npx, lp, lx, ly, lz, si, sy, sz);
-                    else point_rows_pm<D, NF, false, false>(B + k * L::SB, x, npx, lp, lx, ly, lz, si, sy, sz);
+                    if (fwd) point_rows_pm<D, NF, true, false, V>(B + k * L::SF, x, npx, lp, lx, ly, lz, si, sy, sz);
+                    else point_rows_pm<D, NF, false, false, V>(B + k * L::SB, x, npx, lp, lx, ly, lz, si, sy, sz);
                 }
             }
         failed = __syncthreads_or(!ok);
@@ -1348,14 +1429,24 @@ __global__ void __launch_bounds__(kRedThreads) k_as_sum(DGrid g, Bat bt, const S
 
 // projection P: sums of z_c and of sign_m(p) z_uI for every null mode m.
 // Mode mi is the sign pattern prod over the axes J in mask[mi] of (-1)^x_J.
+// With Neumann boundaries (mirror ghosts) the null modes are the translations and,
+// for every pair of axes I < J that both have an even number of cells, the discrete
+// rotation u_I = -S_J(x_J), u_J = S_I(x_I), S(x) = floor((x + 1) / 2) - n / 4 (the
+// centred staircase whose mirrored centred difference is 1/h at every cell, so the
+// strain of the rotation vanishes).  Planes (0, 1), (0, 2), (1, 2); inorm[q] =
+// 1 / |mode q|^2, or 0 for a plane without the mode.
 struct ModeMasks {
     int m[8];
+    double inorm[3];
 };
 
-template <int NF, int NM, typename TV>
-__global__ void __launch_bounds__(kRedThreads, 4) k_proj_dots(DGrid g, Bat bt, ModeMasks mm, const TV *__restrict__ z,
-                                                              double *__restrict__ partials, double *__restrict__ out,
-                                                              unsigned int *ticket)
+
+// NU displacement components from field ku (NU = 0: the model without elasticity);
+// NR rotation planes (Neumann boundaries: d(d-1)/2, else 0)
+template <int NU, int NM, int NR, typename TV>
+__global__ void __launch_bounds__(kRedThreads, 4) k_proj_dots(DGrid g, Bat bt, ModeMasks mm, int ku,
+                                                              const TV *__restrict__ z, double *__restrict__ partials,
+                                                              double *__restrict__ out, unsigned int *ticket)
 {
     long long io;
     if (!inst_off(bt, blockIdx.y, io)) return;
@@ -1363,14 +1454,14 @@ __global__ void __launch_bounds__(kRedThreads, 4) k_proj_dots(DGrid g, Bat bt, M
     partials = shift(partials, io);
     out = shift(out, io);
     ticket = shift(ticket, io);
-    constexpr int K = 1 + (NF - 2) * NM;
+    constexpr int K = 1 + NU * NM + NR;
     const long long N = g.N;
     double acc[K];
 #pragma unroll
     for (int i = 0; i < K; i++) acc[i] = 0.0;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
         acc[0] += (double)z[p];
-        if constexpr (NF > 2) {
+        if constexpr (NU > 0) {
             int x, y, zz;
             coords_of(g, p, x, y, zz);
             const int par = (x & 1) | ((y & 1) << 1) | ((zz & 1) << 2);
@@ -1378,7 +1469,16 @@ __global__ void __launch_bounds__(kRedThreads, 4) k_proj_dots(DGrid g, Bat bt, M
             for (int mi = 0; mi < NM; mi++) {
                 const double sg = (__popc(mm.m[mi] & par) & 1) ? -1.0 : 1.0;
 #pragma unroll
-                for (int I = 0; I < NF - 2; I++) acc[1 + I * NM + mi] += sg * (double)z[(2 + I) * N + p];
+                for (int I = 0; I < NU; I++) acc[1 + I * NM + mi] += sg * (double)z[(ku + I) * N + p];
+            }
+            if constexpr (NR > 0) {
+                const int c3[3] = {x, y, zz};
+#pragma unroll
+                for (int q = 0; q < NR; q++) {
+                    const int I = plane_axis(q, 0), J = plane_axis(q, 1);
+                    acc[1 + NU * NM + q] += -staircase(c3[J], g.n[J]) * (double)z[(ku + I) * N + p] +
+                                            staircase(c3[I], g.n[I]) * (double)z[(ku + J) * N + p];
+                }
             }
         }
     }
@@ -1386,8 +1486,9 @@ __global__ void __launch_bounds__(kRedThreads, 4) k_proj_dots(DGrid g, Bat bt, M
     grid_finalize(partials, K, out, ticket);
 }
 
-template <int NF, int NM, typename TV>
-__global__ void k_proj_sub(DGrid g, Bat bt, ModeMasks mm, const double *__restrict__ sums, TV *__restrict__ z)
+template <int NU, int NM, int NR, typename TV>
+__global__ void k_proj_sub(DGrid g, Bat bt, ModeMasks mm, int ku, const double *__restrict__ sums,
+                           TV *__restrict__ z)
 {
     long long io;
     if (!inst_off(bt, blockIdx.y, io)) return;
@@ -1398,41 +1499,52 @@ __global__ void k_proj_sub(DGrid g, Bat bt, ModeMasks mm, const double *__restri
     if (p >= N) return;
     const double invN = 1.0 / (double)N;
     z[p] = (TV)((double)z[p] - sums[0] * invN);
-    if constexpr (NF > 2) {
+    if constexpr (NU > 0) {
         int x, y, zz;
         coords_of(g, p, x, y, zz);
         const int par = (x & 1) | ((y & 1) << 1) | ((zz & 1) << 2);
+        const int c3[3] = {x, y, zz};
 #pragma unroll
-        for (int I = 0; I < NF - 2; I++) {
+        for (int I = 0; I < NU; I++) {
             double s = 0.0;
 #pragma unroll
             for (int mi = 0; mi < NM; mi++) {
                 const double sg = (__popc(mm.m[mi] & par) & 1) ? -1.0 : 1.0;
                 s += sums[1 + I * NM + mi] * sg;
             }
-            z[(2 + I) * N + p] = (TV)((double)z[(2 + I) * N + p] - s * invN);
+            double r = 0.0;  // the rotation modes' values at p for component I, times their coefficients
+#pragma unroll
+            for (int q = 0; q < NR; q++) {
+                const int A = plane_axis(q, 0), B = plane_axis(q, 1);
+                const double a = sums[1 + NU * NM + q] * mm.inorm[q];
+                if (I == A) r += a * -staircase(c3[B], g.n[B]);
+                if (I == B) r += a * staircase(c3[A], g.n[A]);
+            }
+            z[(ku + I) * N + p] = (TV)((double)z[(ku + I) * N + p] - s * invN - r);
         }
     }
 }
 
-template <int NF, int NM, typename TV>
+template <int NU, int NM, int NR, typename TV>
 void launch_project_t(Problem *P, TV *z, const Bat &bt)
 {
+    const int ku = 1 + P->k.ne;
     RasPlan *R = P->ras;
     ModeMasks mm{};
     int mi = 0;
     for (int m = 0; m < (1 << P->g.dim); m++)
         if ((m & ~R->evenmask) == 0) mm.m[mi++] = m;
-    k_proj_dots<NF, NM, TV><<<dim3(P->rb, bt.nb), kRedThreads, 0, P->stream>>>(P->g, bt, mm, z, P->partials,
-                                                                                R->proj, P->tickets + 2);
-    k_proj_sub<NF, NM, TV><<<dim3((unsigned)((P->N + 255) / 256), bt.nb), 256, 0, P->stream>>>(P->g, bt, mm, R->proj,
-                                                                                               z);
+    for (int q = 0; q < 3; q++) mm.inorm[q] = R->rot_inorm[q];
+    k_proj_dots<NU, NM, NR, TV><<<dim3(P->rb, bt.nb), kRedThreads, 0, P->stream>>>(P->g, bt, mm, ku, z, P->partials,
+                                                                                    R->proj, P->tickets + 2);
+    k_proj_sub<NU, NM, NR, TV><<<dim3((unsigned)((P->N + 255) / 256), bt.nb), 256, 0, P->stream>>>(
+        P->g, bt, mm, ku, R->proj, z);
 }
 
 // FP32 copy of the factors in the point-major layout: level block i (FP64 offset
 // lvl_src[i], cp padded points, rows of cp values) becomes cp rows of SF forward
 // values then cp rows of SB backward values; the padding values are zero.
-template <int D, int NF>
+template <int D, int NF, int V>
 __global__ void __launch_bounds__(256) k_fac_to_f32(Bat bt, long long nlev_all, const long long *__restrict__ lvl_src,
                                                     const double *__restrict__ a, float *__restrict__ b)
 {
@@ -1440,7 +1552,7 @@ __global__ void __launch_bounds__(256) k_fac_to_f32(Bat bt, long long nlev_all, 
     if (!inst_off(bt, blockIdx.y, io)) return;
     a = shift(a, io);
     b = shift(b, io);
-    using L = PM<D, NF>;
+    using L = PM<D, NF, V>;
     constexpr int NL = L::P.nlow, NU = L::P.nup + NF;
     for (long long i = blockIdx.x; i < nlev_all; i += gridDim.x) {
         const long long s0 = lvl_src[i];
@@ -1461,18 +1573,18 @@ __global__ void __launch_bounds__(256) k_fac_to_f32(Bat bt, long long nlev_all, 
     }
 }
 
-template <int D, int NF>
+template <int D, int NF, int V>
 void launch_fac_to_f32(Problem *P, const Bat &bt)
 {
     RasPlan *R = P->ras;
     const unsigned nblk = (unsigned)std::min<long long>(R->nlev_all, 8 * 152);
-    k_fac_to_f32<D, NF><<<dim3(nblk, bt.nb), 256, 0, P->stream>>>(bt, R->nlev_all, R->lvl_src, R->fac, R->fac32);
+    k_fac_to_f32<D, NF, V><<<dim3(nblk, bt.nb), 256, 0, P->stream>>>(bt, R->nlev_all, R->lvl_src, R->fac, R->fac32);
 }
 
 void launch_factor(Problem *P, int mode, const Bat &bt)
 {
     RasPlan *R = P->ras;
-    const Pattern CP = compile_time_pattern(P->g.dim, P->nf);
+    const Pattern CP = compile_time_pattern(P->g.dim, P->nf, pat_var(P));
     FacTables T{};
     for (int f = 0; f <= P->nf; f++) T.rowoff[f] = CP.rowoff[f];
     for (int f = 0; f < P->nf; f++) {
@@ -1494,22 +1606,24 @@ using LaneKernel = void (*)(DGrid, Bat, const SubInfo *, const int *, const long
 
 // the FP32 sweep instantiation of the plan's layout (three buffers and the
 // branch-free layout only with x in shared memory)
-template <int D, int NF>
+template <int D, int NF, int V>
 LaneKernel lane_kernel(const RasPlan *R)
 {
-    if constexpr (D >= 2)
+    // the compiled-in box shapes are those of the periodic workloads (Neumann boxes
+    // are clipped at the boundary)
+    if constexpr (D >= 2 && V == 0)
         if (R->halo32 && R->shape32)
-            return R->lane_bufs == 3 ? k_ras_apply_lane<D, NF, 3, true, true, true>
-                                     : k_ras_apply_lane<D, NF, 2, true, true, true>;
-    if (R->halo32) return R->lane_bufs == 3 ? k_ras_apply_lane<D, NF, 3, true, true, false>
-                                            : k_ras_apply_lane<D, NF, 2, true, true, false>;
-    if (!R->x_smem32) return k_ras_apply_lane<D, NF, 2, false, false, false>;
-    return R->lane_bufs == 3 ? k_ras_apply_lane<D, NF, 3, true, false, false>
-                             : k_ras_apply_lane<D, NF, 2, true, false, false>;
+            return R->lane_bufs == 3 ? k_ras_apply_lane<D, NF, 3, true, true, true, V>
+                                     : k_ras_apply_lane<D, NF, 2, true, true, true, V>;
+    if (R->halo32) return R->lane_bufs == 3 ? k_ras_apply_lane<D, NF, 3, true, true, false, V>
+                                            : k_ras_apply_lane<D, NF, 2, true, true, false, V>;
+    if (!R->x_smem32) return k_ras_apply_lane<D, NF, 2, false, false, false, V>;
+    return R->lane_bufs == 3 ? k_ras_apply_lane<D, NF, 3, true, false, false, V>
+                             : k_ras_apply_lane<D, NF, 2, true, false, false, V>;
 }
 
 // the sweep kernel's dynamic shared memory limit (set once, before any graph capture)
-template <int D, int NF, typename TV>
+template <int D, int NF, int V, typename TV>
 void apply_attr(Problem *P)
 {
     RasPlan *R = P->ras;
@@ -1518,50 +1632,50 @@ void apply_attr(Problem *P)
     bool &attr = f32 ? R->attr_set32 : R->attr_set;
     if (smem > 48 * 1024 && !attr) {
         if constexpr (f32) {
-            cudaFuncSetAttribute(lane_kernel<D, NF>(R), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(lane_kernel<D, NF, V>(R), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         } else {
-            cudaFuncSetAttribute(k_ras_apply<D, NF, TV, TV, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            cudaFuncSetAttribute(k_ras_apply<D, NF, TV, TV, false, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
-            cudaFuncSetAttribute(k_ras_apply<D, NF, TV, TV, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            cudaFuncSetAttribute(k_ras_apply<D, NF, TV, TV, true, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         }
         attr = true;
     }
 }
 
-template <int D, int NF>
+template <int D, int NF, int V>
 void apply_attrs(Problem *P)
 {
-    apply_attr<D, NF, double>(P);
-    if (P->f32) apply_attr<D, NF, float>(P);
+    apply_attr<D, NF, V, double>(P);
+    if (P->f32) apply_attr<D, NF, V, float>(P);
 }
 
 // FP64 vectors use the FP64 factors; FP32 vectors (mixed precision) the FP32 copy
-template <int D, int NF, typename TV>
+template <int D, int NF, int V, typename TV>
 void launch_apply_t(Problem *P, const TV *r, TV *z, const Bat &bt)
 {
     RasPlan *R = P->ras;
-    const int ntask = Sched<D, NF>::ntask;
+    const int ntask = Sched<D, NF, V>::ntask;
     const int wpt = std::max(1, std::min((R->maxcnt + 31) / 32, 32 / ntask));  // warps per stage-A task
     const int threads = ntask * wpt * 32;
     const int pstride = (R->maxcnt + 31) / 32 * 32;
     constexpr bool f32 = sizeof(TV) == sizeof(float);
     using T = TV;
     const size_t smem = f32 ? R->smem_bytes32 : R->smem_bytes;
-    apply_attr<D, NF, TV>(P);
+    apply_attr<D, NF, V, TV>(P);
     const T *fac = f32 ? reinterpret_cast<const T *>(R->fac32) : reinterpret_cast<const T *>(R->fac);
     T *scr = f32 ? reinterpret_cast<T *>(R->scratch32) : reinterpret_cast<T *>(R->scratch);
     const int xs = f32 ? R->x_smem32 : R->x_smem;
     if constexpr (f32) {
         // one thread per point of the widest level
         const int tl = std::min(256, std::max(32, (R->maxcnt + 31) / 32 * 32));
-        lane_kernel<D, NF>(R)<<<dim3(R->nsub, bt.nb), tl, smem, P->stream>>>(
+        lane_kernel<D, NF, V>(R)<<<dim3(R->nsub, bt.nb), tl, smem, P->stream>>>(
             P->g, bt, R->sub, R->lvl_ptr, R->lvl_blk, R->lvl_lp, reinterpret_cast<const float *>(fac),
             reinterpret_cast<const float *>(r), reinterpret_cast<float *>(z), reinterpret_cast<float *>(scr), R->maxnp,
             R->maxnlev, R->maxblk32, P->dflag, P->partials, P->zsum, P->tickets + 3, P->withhold_copy, P->opts.ras_variant,
             R->guard32);
     } else {
-        auto kern = xs ? k_ras_apply<D, NF, T, TV, true> : k_ras_apply<D, NF, T, TV, false>;
+        auto kern = xs ? k_ras_apply<D, NF, T, TV, true, V> : k_ras_apply<D, NF, T, TV, false, V>;
         kern<<<dim3(R->nsub, bt.nb), threads, smem, P->stream>>>(
             P->g, bt, R->sub, R->lvl_ptr, R->lvl_blk, R->lvl_lp, fac, r, z, scr, R->maxnp, R->maxnlev, R->maxblk, wpt,
             P->g.dim == 3 ? 4 : 2,
@@ -1577,36 +1691,39 @@ void launch_apply_t(Problem *P, const TV *r, TV *z, const Bat &bt)
 
 }  // namespace
 
-static int fp64_sweep_regs(int d, int nf, bool xs)
+static int fp64_sweep_regs(int d, int nf, int bc, bool xs)
 {
     cudaFuncAttributes fa{};
     cudaError_t e = cudaErrorInvalidValue;
-    switch (d * 10 + nf) {
-#define NKS_REGS_CASE(D, NF)                                                                                  \
-    case D * 10 + NF:                                                                                         \
-        e = xs ? cudaFuncGetAttributes(&fa, k_ras_apply<D, NF, double, double, true>)                         \
-               : cudaFuncGetAttributes(&fa, k_ras_apply<D, NF, double, double, false>);                       \
+    switch (d * 100 + nf * 10 + bc) {
+#define NKS_REGS_CASE(D, NF, V)                                                                              \
+    case D * 100 + NF * 10 + V:                                                                              \
+        e = xs ? cudaFuncGetAttributes(&fa, k_ras_apply<D, NF, double, double, true, V>)                     \
+               : cudaFuncGetAttributes(&fa, k_ras_apply<D, NF, double, double, false, V>);                   \
         break;
-        NKS_REGS_CASE(1, 2)
-        NKS_REGS_CASE(1, 3)
-        NKS_REGS_CASE(2, 2)
-        NKS_REGS_CASE(2, 4)
-        NKS_REGS_CASE(3, 2)
-        NKS_REGS_CASE(3, 5)
+        NKS_PAT_CASES(NKS_REGS_CASE)
 #undef NKS_REGS_CASE
     }
     return e == cudaSuccess ? fa.numRegs : 64;
 }
 
-#define NKS_DISPATCH(FN, ...)              \
-    switch (P->g.dim * 10 + P->nf) {       \
-    case 12: FN<1, 2>(__VA_ARGS__); break; \
-    case 13: FN<1, 3>(__VA_ARGS__); break; \
-    case 22: FN<2, 2>(__VA_ARGS__); break; \
-    case 24: FN<2, 4>(__VA_ARGS__); break; \
-    case 32: FN<3, 2>(__VA_ARGS__); break; \
-    case 35: FN<3, 5>(__VA_ARGS__); break; \
+// calls fn(D, NF, V) (integral constants) for the problem's instantiation
+template <class Fn>
+static void dispatch(const Problem *P, Fn &&fn)
+{
+    switch (P->g.dim * 100 + P->nf * 10 + pat_var(P)) {
+#define NKS_DISPATCH_CASE(D, NF, V)                                                                          \
+    case D * 100 + NF * 10 + V:                                                                              \
+        fn(std::integral_constant<int, D>{}, std::integral_constant<int, NF>{}, std::integral_constant<int, V>{}); \
+        break;
+        NKS_PAT_CASES(NKS_DISPATCH_CASE)
+#undef NKS_DISPATCH_CASE
     }
+}
+#define NKS_DISPATCH(FN, ...)                                                                                  \
+    dispatch(P, [&](auto d_, auto nf_, auto v_) {                                                             \
+        FN<decltype(d_)::value, decltype(nf_)::value, decltype(v_)::value>(__VA_ARGS__);                      \
+    })
 
 // factors of the instances of bt; an instance whose factorisation meets a zero
 // pivot is marked failed (is[i].nst = -NKS_EPIVOT); on[i] mirrors bt's mask
@@ -1638,19 +1755,27 @@ void project_t(Problem *P, TV *z, const Bat &bt)
 {
     RasPlan *R = P->ras;
     P->tick(6);
-    if (P->nf == 2) launch_project_t<2, 1, TV>(P, z, bt);
-    else {
-        const int code = P->nf * 10 + R->nmodes;
+    if (!P->k.elastic) launch_project_t<0, 1, 0, TV>(P, z, bt);
+    else if (P->g.bc == NKS_NEUMANN) {
+        // translations and the discrete rotations (planes without the mode weigh 0)
+        switch (P->g.dim) {
+        case 1: launch_project_t<1, 1, 0, TV>(P, z, bt); break;
+        case 2: launch_project_t<2, 1, 1, TV>(P, z, bt); break;
+        default: launch_project_t<3, 1, 3, TV>(P, z, bt); break;
+        }
+    } else {
+        // displacement components (the dimension) and null modes per component
+        const int code = P->g.dim * 10 + R->nmodes;
         switch (code) {
-        case 31: launch_project_t<3, 1, TV>(P, z, bt); break;
-        case 32: launch_project_t<3, 2, TV>(P, z, bt); break;
-        case 41: launch_project_t<4, 1, TV>(P, z, bt); break;
-        case 42: launch_project_t<4, 2, TV>(P, z, bt); break;
-        case 44: launch_project_t<4, 4, TV>(P, z, bt); break;
-        case 51: launch_project_t<5, 1, TV>(P, z, bt); break;
-        case 52: launch_project_t<5, 2, TV>(P, z, bt); break;
-        case 54: launch_project_t<5, 4, TV>(P, z, bt); break;
-        case 58: launch_project_t<5, 8, TV>(P, z, bt); break;
+        case 11: launch_project_t<1, 1, 0, TV>(P, z, bt); break;
+        case 12: launch_project_t<1, 2, 0, TV>(P, z, bt); break;
+        case 21: launch_project_t<2, 1, 0, TV>(P, z, bt); break;
+        case 22: launch_project_t<2, 2, 0, TV>(P, z, bt); break;
+        case 24: launch_project_t<2, 4, 0, TV>(P, z, bt); break;
+        case 31: launch_project_t<3, 1, 0, TV>(P, z, bt); break;
+        case 32: launch_project_t<3, 2, 0, TV>(P, z, bt); break;
+        case 34: launch_project_t<3, 4, 0, TV>(P, z, bt); break;
+        case 38: launch_project_t<3, 8, 0, TV>(P, z, bt); break;
         }
     }
     P->count(2);
@@ -1663,14 +1788,9 @@ template <typename TV>
 void ras_apply_t(Problem *P, const TV *r, TV *z, const Bat &bt)
 {
     P->tick(2);
-    switch (P->g.dim * 10 + P->nf) {
-    case 12: launch_apply_t<1, 2, TV>(P, r, z, bt); break;
-    case 13: launch_apply_t<1, 3, TV>(P, r, z, bt); break;
-    case 22: launch_apply_t<2, 2, TV>(P, r, z, bt); break;
-    case 24: launch_apply_t<2, 4, TV>(P, r, z, bt); break;
-    case 32: launch_apply_t<3, 2, TV>(P, r, z, bt); break;
-    case 35: launch_apply_t<3, 5, TV>(P, r, z, bt); break;
-    }
+    dispatch(P, [&](auto d_, auto nf_, auto v_) {
+        launch_apply_t<decltype(d_)::value, decltype(nf_)::value, decltype(v_)::value, TV>(P, r, z, bt);
+    });
     P->count(P->opts.ras_variant != NKS_LEFT_RAS ? 2 : 1);
     P->tock(2);
 }

@@ -49,10 +49,10 @@ struct Request {
 };
 
 struct ShapeKey {
-    int dim, n0, n1, n2;
+    int dim, n0, n1, n2, bc;
     bool operator<(const ShapeKey &o) const
     {
-        return std::tie(dim, n0, n1, n2) < std::tie(o.dim, o.n0, o.n1, o.n2);
+        return std::tie(dim, n0, n1, n2, bc) < std::tie(o.dim, o.n0, o.n1, o.n2, o.bc);
     }
 };
 
@@ -104,7 +104,7 @@ namespace {
 
 ShapeKey key_of(const nks_grid &g)
 {
-    return ShapeKey{g.dim, g.n[0], g.dim >= 2 ? g.n[1] : 1, g.dim == 3 ? g.n[2] : 1};
+    return ShapeKey{g.dim, g.n[0], g.dim >= 2 ? g.n[1] : 1, g.dim == 3 ? g.n[2] : 1, g.bc};
 }
 
 nks_opts opts_for(const nks_server *S, const nks_grid &g)
@@ -353,8 +353,9 @@ int nks_server_submit(nks_server *S, const nks_grid *grid, const double *c, cons
     for (int J = grid->dim; J < 3; J++) r->grid.n[J] = 1;
     long long N = 1;
     for (int J = 0; J < grid->dim; J++) N *= grid->n[J];
+    const long long ne = S->coeffs.n_eta == 3 ? 3 : 1;  // order-parameter planes
     r->c.assign(c, c + N);
-    r->eta.assign(eta, eta + N);
+    r->eta.assign(eta, eta + ne * N);
     r->steps = steps;
     const ShapeKey k = key_of(r->grid);
     bool need = false;
@@ -386,7 +387,7 @@ int nks_server_submit(nks_server *S, const nks_grid *grid, const double *c, cons
 }
 
 // wait for request id (timeout_s < 0: no limit); copies its result and final
-// fields (c, eta: N doubles, u: d N doubles; any may be NULL) and forgets it
+// fields (c: N, eta: n_eta N, u: d N doubles; any may be NULL) and forgets it
 int nks_server_wait(nks_server *S, long long id, nks_request_result *res, double *c, double *eta, double *u,
                     double timeout_s)
 {
@@ -418,7 +419,7 @@ int nks_server_wait(nks_server *S, long long id, nks_request_result *res, double
     const size_t N = r->c.size();
     if (r->status == NKS_OK) {
         if (c) memcpy(c, r->c.data(), N * sizeof(double));
-        if (eta) memcpy(eta, r->eta.data(), N * sizeof(double));
+        if (eta) memcpy(eta, r->eta.data(), r->eta.size() * sizeof(double));
         if (u && !r->u.empty()) memcpy(u, r->u.data(), r->u.size() * sizeof(double));
     }
     S->all.erase(it);

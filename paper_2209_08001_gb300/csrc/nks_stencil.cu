@@ -4,7 +4,7 @@
 // that the expensive pointwise part (three Psi_S series with logarithms,
 // App. B polynomials, FP64) runs once per point:
 //   pass A: G_c = G^1_c + G^{2,S}_c + G^3_c + G^4_c and G_eta at each point,
-//           F_eta = (eta1 - eta0)/dt + G_eta, the four pointwise derivatives
+//           F_eta = (eta1 - eta0)/dt + G_eta, the pointwise derivatives
 //           of G^1 + G^{2,S} (reused by the Jacobian action), and the stress
 //           sigma(eps^el(u1, c1)) at each point;
 //   pass B: F_c = (c1 - c0)/dt - D M D G_c (flux form with level-n edge
@@ -14,6 +14,7 @@
 #include <math.h>
 
 #include "nks_internal.cuh"
+#include "nks_model3.cuh"
 
 namespace nks {
 
@@ -128,6 +129,18 @@ __device__ inline bool in_domain(double c, double e)
     return c > 0.0 && c < 1.0 && p > 0.0 && p < 1.0 && q > 0.0 && q < 1.0;
 }
 
+// three order parameters: c and the four site fractions c eta_i (eta_4 = 4 - sum)
+__device__ inline bool in_domain3(double c, const double (&e)[3])
+{
+    bool ok = c > 0.0 && c < 1.0;
+    const double e4 = 4.0 - e[0] - e[1] - e[2];
+    for (int i = 0; i < 4; i++) {
+        const double q = c * (i < 3 ? e[i] : e4);
+        ok = ok && q > 0.0 && q < 1.0;
+    }
+    return ok;
+}
+
 // symmetric gradient of the displacement at (x, y, z): Du[I][J] = Dhat_J u_I
 template <typename TV>
 __device__ inline void grad_u(const DGrid &g, const TV *U /* field 2 plane */, int x, int y, int z,
@@ -186,13 +199,16 @@ __global__ void k_trace0(DGrid g, DCoef k, Bat bt, const double *__restrict__ is
     if (p >= g.N) return;
     int x, y, z;
     coords_of(g, p, x, y, z);
-    const double *U = X0 + 2 * g.N;
+    const double *U = X0 + (1 + k.ne) * g.N;
     double tr = 0.0;
     for (int K = 0; K < g.dim; K++)
         tr += (U[K * g.N + nbrJ(g, x, y, z, K, +1)] - U[K * g.N + nbrJ(g, x, y, z, K, -1)]) * g.i2h;
     tr0[p] = tr - g.dim * k.eps0 * (X0[p] - cbar0);
 }
 
+// NE: order parameters (1: the reduced model; 3: App. A, whose pointwise part
+// and its 4 x 4 derivative block come from model3_block)
+template <int NE>
 __global__ void k_res_a(DGrid g, DCoef k, Bat bt, const double *__restrict__ isc, int mode,
                         const double *__restrict__ X1, const double *__restrict__ X0, const double *__restrict__ tr0,
                         double *__restrict__ Gc, double *__restrict__ sig, double *__restrict__ part,
@@ -214,43 +230,73 @@ __global__ void k_res_a(DGrid g, DCoef k, Bat bt, const double *__restrict__ isc
     int x, y, z;
     coords_of(g, p, x, y, z);
     const long long N = g.N;
-    const double c1 = X1[p], e1 = X1[N + p];
-    if (!in_domain(c1, e1)) atomicOr(flag, 1);
+    const double c1 = X1[p];
+    double e1[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int j = 0; j < NE; j++) e1[j] = X1[(1 + j) * N + p];
+    if (!(NE == 3 ? in_domain3(c1, e1) : in_domain(c1, e1[0]))) atomicOr(flag, 1);
     double Du[3][3];
     if (k.elastic) {
-        grad_u(g, X1 + 2 * N, x, y, z, Du);
+        grad_u(g, X1 + (1 + NE) * N, x, y, z, Du);
         hooke_packed(g, k, Du, k.eps0 * (c1 - cbar0), sig, p);
     }
     if (mode != 0) {
-        F[N + p] = 0.0;
+#pragma unroll
+        for (int j = 0; j < NE; j++) F[(1 + j) * N + p] = 0.0;
         return;
     }
-    const double c0 = X0[p], e0 = X0[N + p];
-    PointG G = pointG(k, c1, e1, c0, e0);
-    double gc = G.gc, ge = G.ge;
+    const double c0 = X0[p];
+    double e0[3] = {0.0, 0.0, 0.0}, ge[3] = {0.0, 0.0, 0.0}, gc;
+#pragma unroll
+    for (int j = 0; j < NE; j++) e0[j] = X0[(1 + j) * N + p];
+    if constexpr (NE == 3) {
+        const double x1[4] = {c1, e1[0], e1[1], e1[2]}, x0[4] = {c0, e0[0], e0[1], e0[2]};
+        double G[4], dG[16];
+        model3_block(k, x1, x0, G, dG);
+        gc = G[0];
+#pragma unroll
+        for (int j = 0; j < 3; j++) ge[j] = G[1 + j];
+#pragma unroll
+        for (int a = 0; a < 16; a++) part[a * N + p] = dG[a];
+    } else {
+        const PointG G = pointG(k, c1, e1[0], c0, e0[0]);
+        gc = G.gc;
+        ge[0] = G.ge;
+        part[p] = G.dcc;
+        part[N + p] = G.dce;
+        part[2 * N + p] = G.dec;
+        part[3 * N + p] = G.dee;
+    }
     if (k.elastic) {
         // G^3_c = -eps0 sum_I sigma_II(eps^el_{n+1/2}) = -eps0 lam (tr1 + tr0)/2
         double tr1 = -g.dim * k.eps0 * (c1 - cbar0);
         for (int K = 0; K < g.dim; K++) tr1 += Du[K][K];
         gc += -k.eps0 * k.lam * 0.5 * (tr1 + tr0[p]);
     }
-    // G^4 = (-gamma_c D^2 c_h, -3 gamma_eta D^2 eta_h), D^2 = sum_J D+_J D-_J
+    // G^4 = (-gamma_c D^2 c_h, -3 gamma_eta D^2 eta_h), D^2 = sum_J D+_J D-_J; with three
+    // order parameters -gamma_eta D^2 eta_j,h, the eta_j rows carrying the kinetic factor 3
     const double ih2 = g.ih2;
-    double lc = 0.0, le = 0.0;
-    const double chp = c1 + c0, ehp = e1 + e0;
+    double lc = 0.0, le[3] = {0.0, 0.0, 0.0};
+    const double chp = c1 + c0;
     for (int J = 0; J < g.dim; J++) {
         const long long pp = nbrJ(g, x, y, z, J, +1), pm = nbrJ(g, x, y, z, J, -1);
         lc += (X1[pp] + X0[pp]) + (X1[pm] + X0[pm]) - 2.0 * chp;
-        le += (X1[N + pp] + X0[N + pp]) + (X1[N + pm] + X0[N + pm]) - 2.0 * ehp;
+#pragma unroll
+        for (int j = 0; j < NE; j++) {
+            const long long o = (1 + j) * N;
+            le[j] += (X1[o + pp] + X0[o + pp]) + (X1[o + pm] + X0[o + pm]) - 2.0 * (e1[j] + e0[j]);
+        }
     }
     gc += -k.gamma_c * 0.5 * lc * ih2;
-    ge += -3.0 * k.gamma_eta * 0.5 * le * ih2;
     Gc[p] = gc;
-    F[N + p] = (e1 - e0) * idt + ge;
-    part[p] = G.dcc;
-    part[N + p] = G.dce;
-    part[2 * N + p] = G.dec;
-    part[3 * N + p] = G.dee;
+    if constexpr (NE == 3) {
+#pragma unroll
+        for (int j = 0; j < 3; j++)
+            F[(1 + j) * N + p] = (e1[j] - e0[j]) * idt + k.keta * (ge[j] - k.gamma_eta * 0.5 * le[j] * ih2);
+    } else {
+        ge[0] += -3.0 * k.gamma_eta * 0.5 * le[0] * ih2;
+        F[N + p] = (e1[0] - e0[0]) * idt + ge[0];
+    }
 }
 
 __global__ void __launch_bounds__(kRedThreads) k_res_b(DGrid g, DCoef k, Bat bt, const double *__restrict__ isc,
@@ -287,16 +333,26 @@ __global__ void __launch_bounds__(kRedThreads) k_res_b(DGrid g, DCoef k, Bat bt,
             fc = (X1[p] - X0[p]) * idt - flux * ih2;
         }
         F[p] = fc;
-        const double fe = F[N + p];
-        double s = fc * fc + fe * fe;
+        double s = fc * fc;
+        for (int j = 0; j < k.ne; j++) {
+            const double fe = F[(1 + j) * N + p];
+            s += fe * fe;
+        }
         if (k.elastic) {
+            const long long ou = (long long)(1 + k.ne) * N;
+            // F_uI = sum_J Dhat_J sigma_IJ on a periodic grid; with Neumann boundaries the
+            // exact variation -dE_3/du of the discrete elastic energy, which differs only
+            // where the neighbour is the mirrored cell itself: its sigma enters with the
+            // opposite sign (traction-free rows)
             for (int I = 0; I < g.dim; I++) {
                 double div = 0.0;
                 for (int J = 0; J < g.dim; J++) {
                     const int cmp = scomp(g.dim, I, J);
-                    div += (sig[cmp * N + nbrJ(g, x, y, z, J, +1)] - sig[cmp * N + nbrJ(g, x, y, z, J, -1)]) * i2h;
+                    const long long pp = nbrJ(g, x, y, z, J, +1), pm = nbrJ(g, x, y, z, J, -1);
+                    const double sp = pp == p ? -1.0 : 1.0, sm = pm == p ? -1.0 : 1.0;
+                    div += (sp * sig[cmp * N + pp] - sm * sig[cmp * N + pm]) * i2h;
                 }
-                F[(2 + I) * N + p] = div;
+                F[ou + I * N + p] = div;
                 s += div * div;
             }
         }
@@ -313,7 +369,10 @@ __global__ void __launch_bounds__(kRedThreads) k_res_b(DGrid g, DCoef k, Bat bt,
 //   (J v)_eta = v_eta/dt + dec v_c + dee v_eta - 3/2 gamma_eta Lap_h v_eta
 //   (J v)_u_I = sum_J Dhat_J sigma_IJ,
 // with the pointwise derivatives (dcc, dce, dec, dee) of the last residual
-// evaluation (part).  mode 1 (displacement-only system) keeps the identity on the
+// evaluation (part).  With NE = 3 order parameters the pointwise block is 4 x 4
+// (part[(a * 4 + b) N + p] = dG_a/dx_b, x = (c, eta_1..eta_3)), dG_c sums over the
+// three eta_j, and the eta_j rows carry the kinetic factor keta = 3 on the
+// pointwise block (their Laplacian weight is the same 3/2 gamma_eta).  mode 1 (displacement-only system) keeps the identity on the
 // c and eta rows.  With zsum != nullptr the action is applied to P v instead of v,
 // where P removes the mean m = zsum[0] / N of v_c (the null modes of v_u are
 // annihilated by J): every use of v_c reads v_c - m, except the Laplacian, which
@@ -341,6 +400,7 @@ struct JvConst {
     T ls;        // lam eps0
     T i2h;       // 1/(2h)
     T invN;      // 1/N: the mean of v_c is zsum / N
+    T keta;      // kinetic factor of the eta rows (three order parameters: 3)
     int mode;
 };
 
@@ -360,29 +420,33 @@ static JvConst<T> jv_const(const DGrid &g, const DCoef &k, int mode)
     c.ls = (T)(k.lam * k.eps0);
     c.i2h = (T)i2h;
     c.invN = (T)(1.0 / (double)g.N);
+    c.keta = (T)k.keta;
     c.mode = mode;
     return c;
 }
 
-// neighbour offsets of point (x, y, z) along each axis, periodic, 32-bit
+// neighbour offsets of point (x, y, z) along each axis, 32-bit: periodic, or
+// (bc, Neumann) the point itself beyond a boundary (mirror ghost)
 template <int D>
-__device__ __forceinline__ void nbr_offsets(const int (&c3)[3], const int (&nn)[3], int p, int (&im)[3], int (&ip)[3])
+__device__ __forceinline__ void nbr_offsets(const int (&c3)[3], const int (&nn)[3], int p, int (&im)[3], int (&ip)[3],
+                                            int bc)
 {
     int st = 1;
 #pragma unroll
     for (int J = 0; J < D; J++) {
-        im[J] = p + (c3[J] == 0 ? (nn[J] - 1) * st : -st);
-        ip[J] = p + (c3[J] == nn[J] - 1 ? -(nn[J] - 1) * st : st);
+        im[J] = p + (c3[J] == 0 ? (bc ? 0 : (nn[J] - 1) * st) : -st);
+        ip[J] = p + (c3[J] == nn[J] - 1 ? (bc ? 0 : -(nn[J] - 1) * st) : st);
         st *= nn[J];
     }
 }
 
 // dG_c and sigma at one point; T is the arithmetic type
-template <int D, bool EL, typename T, typename TV, typename TC>
+template <int D, bool EL, int NE, typename T, typename TV, typename TC>
 __device__ __forceinline__ void jv_point(const JvConst<T> &c, int mode, int N, int idx, const int (&im)[3],
                                          const int (&ip)[3], const TV *__restrict__ v, const TC *__restrict__ part,
                                          T m, T &dg, T (&sg)[EL ? D * (D + 1) / 2 : 1])
 {
+    constexpr int KU = 1 + NE;  // first displacement field
     const T v0 = (T)v[idx], vc = v0 - m;
     T trd = (T)0;
     if constexpr (EL) {
@@ -390,7 +454,7 @@ __device__ __forceinline__ void jv_point(const JvConst<T> &c, int mode, int N, i
 #pragma unroll
         for (int I = 0; I < D; I++)
 #pragma unroll
-            for (int J = 0; J < D; J++) Dd[I][J] = (T)v[(2 + I) * N + ip[J]] - (T)v[(2 + I) * N + im[J]];
+            for (int J = 0; J < D; J++) Dd[I][J] = (T)v[(KU + I) * N + ip[J]] - (T)v[(KU + I) * N + im[J]];
 #pragma unroll
         for (int I = 0; I < D; I++) trd += Dd[I][I];
         // sigma_II = (C11 - C12) e_II + C12 tr e - lam eps0 v_c;  sigma_IJ = C44 (D_IJ + D_JI)
@@ -407,7 +471,10 @@ __device__ __forceinline__ void jv_point(const JvConst<T> &c, int mode, int N, i
 #pragma unroll
         for (int J = 0; J < D; J++) sn += (T)v[ip[J]] + (T)v[im[J]];
         const T lc = sn - (T)(2 * D) * v0;
-        dg = (T)part[idx] * vc + (T)part[N + idx] * (T)v[N + idx] - c.gc * lc;
+        dg = (T)part[idx] * vc;
+#pragma unroll
+        for (int j = 1; j <= NE; j++) dg += (T)part[j * N + idx] * (T)v[j * N + idx];
+        dg -= c.gc * lc;
         if constexpr (EL) dg += c.el_c * vc - c.el_t * trd;
     }
 }
@@ -426,7 +493,7 @@ __device__ __forceinline__ bool grid_point(const DGrid &g, int (&c3)[3], int &p)
     return true;
 }
 
-template <int D, bool EL>
+template <int D, bool EL, int NE>
 __global__ void __launch_bounds__(256) k_jv64_a(DGrid g, JvConst<double> c, Bat bt, const double *__restrict__ part,
                                                 const double *__restrict__ v, double *__restrict__ dG,
                                                 double *__restrict__ sig, const double *__restrict__ zsum)
@@ -443,9 +510,9 @@ __global__ void __launch_bounds__(256) k_jv64_a(DGrid g, JvConst<double> c, Bat 
     const int nn[3] = {g.n[0], g.n[1], g.n[2]};
     const int N = (int)g.N;
     int im[3], ip[3];
-    nbr_offsets<D>(c3, nn, p, im, ip);
+    nbr_offsets<D>(c3, nn, p, im, ip, g.bc);
     double dg = 0.0, sg[EL ? D * (D + 1) / 2 : 1];
-    jv_point<D, EL, double, double, double>(c, c.mode, N, p, im, ip, v, part, m, dg, sg);
+    jv_point<D, EL, NE, double, double, double>(c, c.mode, N, p, im, ip, v, part, m, dg, sg);
     if (c.mode == 0) dG[p] = dg;
     if constexpr (EL) {
 #pragma unroll
@@ -453,13 +520,14 @@ __global__ void __launch_bounds__(256) k_jv64_a(DGrid g, JvConst<double> c, Bat 
     }
 }
 
-template <int D, bool EL>
+template <int D, bool EL, int NE>
 __global__ void __launch_bounds__(256) k_jv64_b(DGrid g, JvConst<double> c, Bat bt, const double *__restrict__ isc,
                                                 const double *__restrict__ part, const double *__restrict__ mob,
                                                 const double *__restrict__ v, const double *__restrict__ dG,
                                                 const double *__restrict__ sig, double *__restrict__ Jv,
                                                 const double *__restrict__ zsum)
 {
+    constexpr int KU = 1 + NE;
     long long io;
     if (!inst_off(bt, blockIdx.z / g.n[2], io)) return;
     part = shift(part, io);
@@ -475,35 +543,54 @@ __global__ void __launch_bounds__(256) k_jv64_b(DGrid g, JvConst<double> c, Bat 
     const int nn[3] = {g.n[0], g.n[1], g.n[2]};
     const int N = (int)g.N;
     int im[3], ip[3];
-    nbr_offsets<D>(c3, nn, p, im, ip);
-    const double vc = v[p] - m, ve = v[N + p];
-    double jc, je;
+    nbr_offsets<D>(c3, nn, p, im, ip, g.bc);
+    const double vc = v[p] - m;
+    double ve[NE], je[NE], jc;
+#pragma unroll
+    for (int j = 0; j < NE; j++) ve[j] = v[(1 + j) * N + p];
     if (c.mode == 0) {
         const double G0 = dG[p];
-        double flux = 0.0, sn = 0.0;
+        double flux = 0.0, sn[NE];
+#pragma unroll
+        for (int j = 0; j < NE; j++) sn[j] = 0.0;
 #pragma unroll
         for (int J = 0; J < D; J++) {
             flux += mob[J * N + p] * (dG[ip[J]] - G0) - mob[J * N + im[J]] * (G0 - dG[im[J]]);
-            sn += v[N + ip[J]] + v[N + im[J]];
+#pragma unroll
+            for (int j = 0; j < NE; j++) sn[j] += v[(1 + j) * N + ip[J]] + v[(1 + j) * N + im[J]];
         }
         jc = vc * idt - flux * c.ih2;
-        je = ve * idt + part[2 * N + p] * vc + part[3 * N + p] * ve - c.ge * (sn - (2 * D) * ve);
+#pragma unroll
+        for (int j = 0; j < NE; j++) {
+            const double *pr = part + (size_t)(1 + j) * KU * N + p;  // row 1 + j of the pointwise block
+            if constexpr (NE == 1) {
+                je[j] = ve[j] * idt + pr[0] * vc + pr[N] * ve[j] - c.ge * (sn[j] - (2 * D) * ve[j]);
+            } else {
+                double pw = pr[0] * vc;
+#pragma unroll
+                for (int i = 0; i < NE; i++) pw += pr[(size_t)(1 + i) * N] * ve[i];
+                je[j] = ve[j] * idt + c.keta * pw - c.ge * (sn[j] - (2 * D) * ve[j]);
+            }
+        }
     } else {
         jc = vc;
-        je = ve;
+#pragma unroll
+        for (int j = 0; j < NE; j++) je[j] = ve[j];
     }
     Jv[p] = jc;
-    Jv[N + p] = je;
+#pragma unroll
+    for (int j = 0; j < NE; j++) Jv[(1 + j) * N + p] = je[j];
     if constexpr (EL) {
+        // as the residual: the mirrored neighbour's stress enters with the opposite sign
 #pragma unroll
         for (int I = 0; I < D; I++) {
             double div = 0.0;
 #pragma unroll
             for (int J = 0; J < D; J++) {
                 const int q = scomp(D, I, J) * N;
-                div += sig[q + ip[J]] - sig[q + im[J]];
+                div += (ip[J] == p ? -sig[q + ip[J]] : sig[q + ip[J]]) - (im[J] == p ? -sig[q + im[J]] : sig[q + im[J]]);
             }
-            Jv[(2 + I) * N + p] = div * c.i2h;
+            Jv[(KU + I) * N + p] = div * c.i2h;
         }
     }
 }
@@ -525,7 +612,7 @@ struct JvTile<3> {
     static constexpr int TX = 16, TY = 4, TZ = 4;
 };
 
-template <int D, bool EL>
+template <int D, bool EL, int NE>
 __global__ void __launch_bounds__(256) k_jv32(DGrid g, JvConst<float> c, Bat bt, const double *__restrict__ isc,
                                               const float *__restrict__ part, const float *__restrict__ mob,
                                               const float *__restrict__ v, float *__restrict__ Jv,
@@ -566,13 +653,15 @@ __global__ void __launch_bounds__(256) k_jv32(DGrid g, JvConst<float> c, Bat bt,
         const int hx = q % HX, hy = (q / HX) % HY, hz = q / (HX * HY);
         int c3[3] = {x0 - 1 + hx, D >= 2 ? y0 - 1 + hy : 0, D == 3 ? z0 - 1 + hz : 0};
         if (c3[0] > nn[0] || c3[1] > nn[1] || c3[2] > nn[2]) continue;  // beyond a ragged tile: never read
+        // periodic wrap, or with Neumann boundaries the mirror ghost's cell (a halo cell
+        // beyond the grid holds the boundary cell's values)
 #pragma unroll
-        for (int J = 0; J < 3; J++) c3[J] = wrapi(c3[J], nn[J]);
+        for (int J = 0; J < 3; J++) c3[J] = g.bc ? (c3[J] < 0 ? 0 : (c3[J] >= nn[J] ? nn[J] - 1 : c3[J])) : wrapi(c3[J], nn[J]);
         const int idx = c3[0] + nn[0] * (c3[1] + nn[1] * c3[2]);
         int im[3], ip[3];
-        nbr_offsets<D>(c3, nn, idx, im, ip);
+        nbr_offsets<D>(c3, nn, idx, im, ip, g.bc);
         float dg = 0.f, sg[NS];
-        jv_point<D, EL, float, float, float>(c, c.mode, N, idx, im, ip, v, part, m, dg, sg);
+        jv_point<D, EL, NE, float, float, float>(c, c.mode, N, idx, im, ip, v, part, m, dg, sg);
         sG[q] = dg;
         if constexpr (EL) {
 #pragma unroll
@@ -588,42 +677,80 @@ __global__ void __launch_bounds__(256) k_jv32(DGrid g, JvConst<float> c, Bat bt,
         if (c3[0] >= nn[0] || c3[1] >= nn[1] || c3[2] >= nn[2]) continue;
         const int p = c3[0] + nn[0] * (c3[1] + nn[1] * c3[2]);
         int im[3], ip[3];
-        nbr_offsets<D>(c3, nn, p, im, ip);
+        nbr_offsets<D>(c3, nn, p, im, ip, g.bc);
         const int hq = (tx + 1) + (D >= 2 ? HX * (ty + 1) : 0) + (D == 3 ? HX * HY * (tz + 1) : 0);
-        const float vc = v[p] - m, ve = v[N + p];
-        float jc, je;
+        constexpr int KU = 1 + NE;
+        const float vc = v[p] - m;
+        float ve[NE], je[NE], jc;
+#pragma unroll
+        for (int j = 0; j < NE; j++) ve[j] = v[(1 + j) * N + p];
         if (c.mode == 0) {
             const float G0 = sG[hq];
-            float flux = 0.f, sn = 0.f;
+            float flux = 0.f, sn[NE];
+#pragma unroll
+            for (int j = 0; j < NE; j++) sn[j] = 0.f;
 #pragma unroll
             for (int J = 0; J < D; J++) {
                 flux += mob[J * N + p] * (sG[hq + sh[J]] - G0) - mob[J * N + im[J]] * (G0 - sG[hq - sh[J]]);
-                sn += v[N + ip[J]] + v[N + im[J]];
+#pragma unroll
+                for (int j = 0; j < NE; j++) sn[j] += v[(1 + j) * N + ip[J]] + v[(1 + j) * N + im[J]];
             }
             jc = vc * idt - flux * ih2;
-            je = ve * idt + part[2 * N + p] * vc + part[3 * N + p] * ve - ge * (sn - (float)(2 * D) * ve);
+#pragma unroll
+            for (int j = 0; j < NE; j++) {
+                const float *pr = part + (size_t)(1 + j) * KU * N + p;
+                if constexpr (NE == 1) {
+                    je[j] = ve[j] * idt + pr[0] * vc + pr[N] * ve[j] - ge * (sn[j] - (float)(2 * D) * ve[j]);
+                } else {
+                    float pw = pr[0] * vc;
+#pragma unroll
+                    for (int i = 0; i < NE; i++) pw += pr[(size_t)(1 + i) * N] * ve[i];
+                    je[j] = ve[j] * idt + c.keta * pw - ge * (sn[j] - (float)(2 * D) * ve[j]);
+                }
+            }
         } else {
             jc = vc;
-            je = ve;
+#pragma unroll
+            for (int j = 0; j < NE; j++) je[j] = ve[j];
         }
         Jv[p] = jc;
-        Jv[N + p] = je;
+#pragma unroll
+        for (int j = 0; j < NE; j++) Jv[(1 + j) * N + p] = je[j];
         if constexpr (EL) {
+            // the mirrored neighbour's stress enters with the opposite sign (Neumann)
 #pragma unroll
             for (int I = 0; I < D; I++) {
                 float div = 0.f;
 #pragma unroll
                 for (int J = 0; J < D; J++) {
                     const int s = scomp(D, I, J);
-                    div += sS[s][hq + sh[J]] - sS[s][hq - sh[J]];
+                    const float a = sS[s][hq + sh[J]], b = sS[s][hq - sh[J]];
+                    div += (ip[J] == p ? -a : a) - (im[J] == p ? -b : b);
                 }
-                Jv[(2 + I) * N + p] = div * i2h;
+                Jv[(KU + I) * N + p] = div * i2h;
             }
         }
     }
 }
 
 __device__ inline double Psi(double z) { return z * log(z) + (1.0 - z) * log1p(-z); }
+
+// E_1 and E_2 densities of the model with three order parameters (App. A):
+//   E_1 = dis(c) + a(c) S(eta) + b(c) T(eta), dis(c) = dE0 c + c(1-c) sum_i L_i (2c-1)^i,
+//   a(c) = (4 U1 + 12 U4) c^2 - 24 U4 c^3, b(c) = -48 U4 c^3,
+//   S = phi_1^2 + phi_2^2 + phi_3^2, T = phi_1 phi_2 phi_3 (phi of nks_model3.cuh);
+//   E_2 = theta (w Psi(c) + 1/4 sum_{i=1..4} Psi(c eta_i)), eta_4 = 4 - sum
+__device__ inline void energy12_3(const DCoef &k, double c, const double (&e)[3], double &e1, double &e2)
+{
+    const double s = 2.0 * c - 1.0;
+    const double dis = k.dE0 * c + c * (1.0 - c) * (k.L[0] + s * (k.L[1] + s * (k.L[2] + s * k.L[3])));
+    const double f0 = 1.0 - 0.5 * (e[0] + e[1]), f1 = 1.0 - 0.5 * (e[0] + e[2]), f2 = 1.0 - 0.5 * (e[1] + e[2]);
+    const double c2 = c * c, c3 = c2 * c;
+    const double a = (4.0 * k.U1 + 12.0 * k.U4) * c2 - 24.0 * k.U4 * c3, b = -48.0 * k.U4 * c3;
+    e1 = dis + a * (f0 * f0 + f1 * f1 + f2 * f2) + b * (f0 * f1 * f2);
+    const double e4 = 4.0 - e[0] - e[1] - e[2];
+    e2 = k.theta * (k.w_psi * Psi(c) + 0.25 * (Psi(c * e[0]) + Psi(c * e[1]) + Psi(c * e[2]) + Psi(c * e4)));
+}
 
 // energy parts e1..e4 (Eq. relations) and mass, per-block partial sums
 __global__ void __launch_bounds__(kRedThreads) k_energy(DGrid g, DCoef k, Bat bt, const double *__restrict__ isc,
@@ -641,17 +768,24 @@ __global__ void __launch_bounds__(kRedThreads) k_energy(DGrid g, DCoef k, Bat bt
          p += (long long)gridDim.x * blockDim.x) {
         int x, y, z;
         coords_of(g, p, x, y, z);
-        const double c = X[p], e = X[N + p], f = 1.0 - e;
-        // E1 = Phi(c, phi): App. A with one order parameter
-        const double s = 2.0 * c - 1.0;
-        const double ex = c * (1.0 - c) * (k.L[0] + s * (k.L[1] + s * (k.L[2] + s * k.L[3])));
-        const double e1 = k.dE0 * c + ex + 12.0 * k.U1 * c * c * f * f + 36.0 * k.U4 * (1.0 - 2.0 * c) * c * c * f * f -
-                          48.0 * k.U4 * c * c * c * f * f * f;
-        const double e2 = k.theta * (k.w_psi * Psi(c) + 0.75 * Psi(c * e) + 0.25 * Psi(c * (4.0 - 3.0 * e)));
+        const double c = X[p];
+        double e1, e2;
+        if (k.ne == 3) {
+            const double ee[3] = {X[N + p], X[2 * N + p], X[3 * N + p]};
+            energy12_3(k, c, ee, e1, e2);
+        } else {
+            const double e = X[N + p], f = 1.0 - e;
+            // E1 = Phi(c, phi): App. A with one order parameter
+            const double s = 2.0 * c - 1.0;
+            const double ex = c * (1.0 - c) * (k.L[0] + s * (k.L[1] + s * (k.L[2] + s * k.L[3])));
+            e1 = k.dE0 * c + ex + 12.0 * k.U1 * c * c * f * f + 36.0 * k.U4 * (1.0 - 2.0 * c) * c * c * f * f -
+                 48.0 * k.U4 * c * c * c * f * f * f;
+            e2 = k.theta * (k.w_psi * Psi(c) + 0.75 * Psi(c * e) + 0.25 * Psi(c * (4.0 - 3.0 * e)));
+        }
         double e3 = 0.0;
         if (k.elastic) {
             double Du[3][3];
-            grad_u(g, X + 2 * N, x, y, z, Du);
+            grad_u(g, X + (1 + k.ne) * N, x, y, z, Du);
             const double s0 = k.eps0 * (c - cbar0);
             double tr = 0.0, sq = 0.0, off = 0.0;
             for (int I = 0; I < g.dim; I++) {
@@ -665,18 +799,23 @@ __global__ void __launch_bounds__(kRedThreads) k_energy(DGrid g, DCoef k, Bat bt
             }
             e3 = 0.5 * (k.C12 * tr * tr + (k.C11 - k.C12) * sq + 4.0 * k.C44 * off);
         }
+        // E4: gamma_c/2 |D c|^2 + 3 gamma_eta/2 |D eta|^2, or gamma_eta/2 per eta_j (App. A)
         double gc = 0.0, ge = 0.0;
         for (int J = 0; J < g.dim; J++) {
             const long long pp = nbrJ(g, x, y, z, J, +1), pm = nbrJ(g, x, y, z, J, -1);
             const double dpc = (X[pp] - c) * ih, dmc = (c - X[pm]) * ih;
-            const double dpe = (X[N + pp] - e) * ih, dme = (e - X[N + pm]) * ih;
             gc += 0.5 * (dpc * dpc + dmc * dmc);
-            ge += 0.5 * (dpe * dpe + dme * dme);
+            for (int j = 0; j < k.ne; j++) {
+                const long long o = (1 + j) * N;
+                const double e = X[o + p];
+                const double dpe = (X[o + pp] - e) * ih, dme = (e - X[o + pm]) * ih;
+                ge += 0.5 * (dpe * dpe + dme * dme);
+            }
         }
         acc[0] += e1;
         acc[1] += e2;
         acc[2] += e3;
-        acc[3] += 0.5 * k.gamma_c * gc + 1.5 * k.gamma_eta * ge;
+        acc[3] += 0.5 * k.gamma_c * gc + (k.ne == 3 ? 0.5 : 1.5) * k.gamma_eta * ge;
         acc[4] += c;
     }
     block_reduce_store<5>(acc, partials);
@@ -723,40 +862,51 @@ int launch_residual(const DGrid &g, const DCoef &k, const double *isc, int mode,
                     const double *tr0, const double *mob, double *Gc, double *sig, double *part, double *F, int *flag,
                     double *partials, int rb, cudaStream_t st, const Bat &bt)
 {
-    k_res_a<<<dim3(blocks_for(g.N), bt.nb), kThreads, 0, st>>>(g, k, bt, isc, mode, X1, X0, tr0, Gc, sig, part, F,
-                                                                flag);
+    if (k.ne == 3)
+        k_res_a<3><<<dim3(blocks_for(g.N), bt.nb), kThreads, 0, st>>>(g, k, bt, isc, mode, X1, X0, tr0, Gc, sig, part,
+                                                                       F, flag);
+    else
+        k_res_a<1><<<dim3(blocks_for(g.N), bt.nb), kThreads, 0, st>>>(g, k, bt, isc, mode, X1, X0, tr0, Gc, sig, part,
+                                                                       F, flag);
     k_res_b<<<dim3(rb, bt.nb), kRedThreads, 0, st>>>(g, k, bt, isc, mode, X1, X0, Gc, mob, sig, F, partials);
     return 2;
 }
 
-template <int D, bool EL>
+template <int D, bool EL, int NE>
 static void launch_jv64_d(const DGrid &g, const JvConst<double> &c, const Bat &bt, const double *isc, const double *part,
                           const double *mob, const double *v, double *dG, double *sig, double *Jv, cudaStream_t st,
                           const double *zsum)
 {
     const dim3 blk(D == 1 ? 256 : 32, D == 1 ? 1 : 8);
     const dim3 grd((g.n[0] + blk.x - 1) / blk.x, (g.n[1] + blk.y - 1) / blk.y, g.n[2] * bt.nb);
-    k_jv64_a<D, EL><<<grd, blk, 0, st>>>(g, c, bt, part, v, dG, sig, zsum);
-    k_jv64_b<D, EL><<<grd, blk, 0, st>>>(g, c, bt, isc, part, mob, v, dG, sig, Jv, zsum);
+    k_jv64_a<D, EL, NE><<<grd, blk, 0, st>>>(g, c, bt, part, v, dG, sig, zsum);
+    k_jv64_b<D, EL, NE><<<grd, blk, 0, st>>>(g, c, bt, isc, part, mob, v, dG, sig, Jv, zsum);
 }
 
-template <int D, bool EL>
+template <int D, bool EL, int NE>
 static void launch_jv32_d(const DGrid &g, const JvConst<float> &c, const Bat &bt, const double *isc, const float *part,
                           const float *mob, const float *v, float *Jv, cudaStream_t st, const double *zsum)
 {
     constexpr int TX = JvTile<D>::TX, TY = JvTile<D>::TY, TZ = JvTile<D>::TZ;
     const long long tiles = (long long)((g.n[0] + TX - 1) / TX) * ((g.n[1] + TY - 1) / TY) * ((g.n[2] + TZ - 1) / TZ);
-    k_jv32<D, EL><<<dim3((unsigned)tiles, bt.nb), 256, 0, st>>>(g, c, bt, isc, part, mob, v, Jv, zsum);
+    k_jv32<D, EL, NE><<<dim3((unsigned)tiles, bt.nb), 256, 0, st>>>(g, c, bt, isc, part, mob, v, Jv, zsum);
 }
 
-#define NKS_JV_DISPATCH(FN, ...)                                  \
-    switch (g.dim * 2 + (k.elastic ? 1 : 0)) {                    \
-    case 2: FN<1, false>(__VA_ARGS__); break;                     \
-    case 3: FN<1, true>(__VA_ARGS__); break;                      \
-    case 4: FN<2, false>(__VA_ARGS__); break;                     \
-    case 5: FN<2, true>(__VA_ARGS__); break;                      \
-    case 6: FN<3, false>(__VA_ARGS__); break;                     \
-    default: FN<3, true>(__VA_ARGS__); break;                     \
+// dimension, elasticity and order parameters (1 or 3)
+#define NKS_JV_DISPATCH(FN, ...)                                      \
+    switch ((k.ne == 3 ? 8 : 0) + g.dim * 2 + (k.elastic ? 1 : 0)) { \
+    case 2: FN<1, false, 1>(__VA_ARGS__); break;                      \
+    case 3: FN<1, true, 1>(__VA_ARGS__); break;                       \
+    case 4: FN<2, false, 1>(__VA_ARGS__); break;                      \
+    case 5: FN<2, true, 1>(__VA_ARGS__); break;                       \
+    case 6: FN<3, false, 1>(__VA_ARGS__); break;                      \
+    case 7: FN<3, true, 1>(__VA_ARGS__); break;                       \
+    case 10: FN<1, false, 3>(__VA_ARGS__); break;                     \
+    case 11: FN<1, true, 3>(__VA_ARGS__); break;                      \
+    case 12: FN<2, false, 3>(__VA_ARGS__); break;                     \
+    case 13: FN<2, true, 3>(__VA_ARGS__); break;                      \
+    case 14: FN<3, false, 3>(__VA_ARGS__); break;                     \
+    default: FN<3, true, 3>(__VA_ARGS__); break;                      \
     }
 
 int launch_jv64(const DGrid &g, const DCoef &k, const double *isc, int mode, const double *part, const double *mob,
