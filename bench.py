@@ -41,7 +41,6 @@ METRIC = "point-steps/s"
 # FP64 FMA peak derived from the unit counts: 152 SMs x 2 FP64 FMA/clk x 2 FLOP x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
-FIELDS = ("c", "eta", "u1", "u2", "u3")
 
 
 def peaks():
@@ -73,7 +72,7 @@ def kernel_rates(st, cfg, mixed, pk):
     algorithmic bytes per unit (as in the design notes) over the class's device time."""
     d = cfg["dim"]
     N = float(np.prod(cfg["n"]))
-    f = 2 + d
+    ne, f = layout(cfg)
     b = 4.0 if mixed else 8.0
     out = {}
     hbm = pk.get("hbm_gbs")
@@ -90,9 +89,10 @@ def kernel_rates(st, cfg, mixed, pk):
             e["fp64_frac"] = e["achieved_tflops"] / FP64_PEAK_TFLOPS
         out[cls] = e
 
-    # Jacobian action: (2f + 5) words per point per application (v, 4 coefficients + edge
-    # mobility, J v), FP32 words in the Arnoldi step of the mixed mode
-    rate("jacobian_action", st["launches"]["jacobian_action"] * (2 * f + 5) * b * N,
+    # Jacobian action: 2f + (1 + ne)^2 + d words per point per application (v, the
+    # pointwise derivative block, the d edge mobilities, J v), FP32 words in the
+    # Arnoldi step of the mixed mode
+    rate("jacobian_action", st["launches"]["jacobian_action"] * (2 * f + (1 + ne) ** 2 + d) * b * N,
          bound="hbm" if mixed else "fp64")
     # Gram-Schmidt: (2j + 5) basis-vector transfers per pass of Arnoldi step j (counted by the library)
     gs_ms = st["ms"].get("gs_dots", 0.0) + st["ms"].get("gs_update", 0.0)
@@ -245,8 +245,17 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
+def layout(cfg):
+    """(order parameters, fields per point) of a workload"""
+    cf = S.config_coefficients(cfg)
+    ne = 3 if cf.get("n_eta", 1) == 3 else 1
+    elastic = cf.get("Lscale", 1.0) != 0.0 and any(cf[k] != 0.0 for k in ("C11", "C12", "C44"))
+    return ne, 1 + ne + (cfg["dim"] if elastic else 0)
+
+
 def field_dict(c, e, u):
-    out = {"c": c, "eta": e}
+    e = np.asarray(e)
+    out = {"c": c, "eta": e} if e.ndim == 1 else {"c": c, **{"eta%d" % (j + 1): e[j] for j in range(len(e))}}
     if u is not None:
         for I in range(len(u)):
             out["u%d" % (I + 1)] = u[I]
@@ -433,6 +442,9 @@ def run_ours(args):
         op["ras_variant"] = args.variant
     if args.overlap is not None:
         op["overlap"] = args.overlap
+    if args.sub:
+        op["sub"] = tuple(int(v) for v in args.sub.split(","))
+        args.no_accuracy = True
     if args.u0_maxit is not None:
         op["u0_maxit"] = args.u0_maxit
     if args.gmres_maxit is not None:
@@ -523,7 +535,7 @@ def run_ours(args):
     e2e = None
     if not args.no_e2e:
         cpin = torch.from_numpy(c).pin_memory().numpy()
-        epin = torch.from_numpy(e).pin_memory().numpy()
+        epin = torch.from_numpy(np.ascontiguousarray(e)).pin_memory().numpy()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         R = nks.Problem(cfg["dim"], cfg["n"], cfg["h"], cpin, epin, S.config_coefficients(cfg), op,
@@ -535,9 +547,9 @@ def run_ours(args):
         t_e2e = time.perf_counter() - t0
         R.destroy()
         t_e2e = max_over_ranks(dist, t_e2e, dev)
-        nfr = 2 + (cfg["dim"] if S.config_coefficients(cfg).get("Lscale", 1.0) else 0)
+        ne, nfr = layout(cfg)
         e2e = {"value": sum_over_ranks(dist, float(N * args.steps), dev) / t_e2e, "unit": METRIC,
-               "h2d_bytes_per_step": int(2 * N * 8 / args.steps), "d2h_bytes_per_step": int(nfr * N * 8),
+               "h2d_bytes_per_step": int((1 + ne) * N * 8 / args.steps), "d2h_bytes_per_step": int(nfr * N * 8),
                "includes": "problem creation from host fields (upload + initial mechanical equilibrium solve), "
                            "K adaptive steps, all fields read back to host after every step"}
 
@@ -770,6 +782,8 @@ def main():
     ap.add_argument("--variant", default=None, choices=["left-ras", "as", "right-ras"],
                     help="Schwarz preconditioner type (default: the workload's, left-RAS)")
     ap.add_argument("--overlap", type=int, default=None, help="override the workload's Schwarz overlap delta")
+    ap.add_argument("--sub", default=None,
+                    help="override the workload's subdomains per axis, e.g. 8,8,16 (the oracle comparison is skipped)")
     ap.add_argument("--gmres-maxit", type=int, default=None, help="override the GMRES iteration cap per solve")
     ap.add_argument("--u0-maxit", type=int, default=None,
                     help="Newton iterations allowed to the initial mechanical equilibrium (set-up, not timed)")

@@ -28,12 +28,14 @@ Parity status per function (pins live in ``tests/test_oracle_*.py``):
                                         elastic constants are not printed)
   Neumann boundaries .................. pinned (mirrored periodic problem without
                                         elasticity; -F_u = dE_3/du; mass, energy
-                                        law, central differences)
+                                        law, central differences; projection vs
+                                        the SVD null space of the displacement
+                                        block)
   three order parameters (n_eta = 3) .. pinned (reduction to the pinned reduced
                                         model, four-sublattice symmetry of E_G,
                                         exact discrete chain rule, central
                                         differences, mass, energy law,
-                                        permutations); no CUDA path yet
+                                        permutations)
 """
 from __future__ import annotations
 

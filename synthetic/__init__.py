@@ -202,6 +202,11 @@ CONFIGS = {
              "RAS 8x8x8 subdomains overlap 1",
         dim=3, n=(128, 128, 128), h=0.25, cbar=0.18, seed=2, steps=50,
         opts=dict(dt_mode="energy", sub=(8, 8, 8), overlap=1, precision="fp64")),
+    "3d128eta3": dict(
+        desc="3D 128^3 periodic, three order parameters (App. A, eta_1..eta_3 drawn independently), "
+             "50 adaptive DVD steps, FP64 beside mixed precision, RAS 8x8x8 subdomains overlap 1",
+        dim=3, n=(128, 128, 128), h=0.25, cbar=0.18, seed=2, steps=50, init="three", coeffs=dict(n_eta=3),
+        opts=dict(dt_mode="energy", sub=(8, 8, 8), overlap=1, precision="fp64")),
     "3d256": dict(
         desc="3D 256^3 periodic mixed precision, 100 adaptive DVD steps, RAS 16x16x16 subdomains overlap 1",
         dim=3, n=(256, 256, 256), h=0.25, cbar=0.22, seed=3, steps=100,
@@ -216,10 +221,13 @@ CONFIGS = {
 
 
 def config_fields(cfg: dict, seed_offset: int = 0):
-    """Initial (c, eta) of a workload: the particle of Sec. 5.1, or the seeded
-    random state (seed + seed_offset)."""
+    """Initial (c, eta) of a workload: the particle of Sec. 5.1, the seeded random
+    state (seed + seed_offset), or with three order parameters its App. A form
+    (eta of shape (3, N))."""
     if cfg.get("init") == "sphere":
         return sphere_fields(cfg["dim"], cfg["n"], cfg["h"], cfg["radius"])
+    if cfg.get("init") == "three":
+        return initial_fields3(cfg["dim"], cfg["n"], cfg["cbar"], cfg["seed"] + seed_offset)
     return initial_fields(cfg["dim"], cfg["n"], cfg["cbar"], cfg["seed"] + seed_offset)
 
 

@@ -2,6 +2,7 @@
 
     python tests/golden/make_full_size.py 3d128 5      # -> tests/golden/full_3d128.json
     python tests/golden/make_full_size.py 2d1024 5     # -> tests/golden/full_2d1024.json
+    python tests/golden/make_full_size.py 3d128eta3 3  # -> tests/golden/full_3d128eta3.json
 
 For a workload of ``synthetic.CONFIGS`` this runs the FP64 oracle (``oracle/``,
 nothing else computes) from the workload's initial state for the given number
@@ -10,7 +11,7 @@ of adaptive time steps, with the Newton tolerance of the parity references
 
   * per step: dt, energy, mass, Newton and GMRES iterations (the dt list is
     what the GPU tests replay);
-  * per field of the final state (c, eta, u_1..u_d): its L2 norm, a 256-row
+  * per field of the final state (c, eta or eta_1..eta_3, u_1..u_d): its L2 norm, a 256-row
     seeded sign sketch (``synthetic.sign_sketch``: |S a - S b| estimates the
     L2 distance |a - b|), and its values at 1024 seeded points
     (``synthetic.sample_points``).
@@ -59,7 +60,8 @@ def main(workload, steps):
     if rc != 0:
         raise SystemExit("oracle failed: rc %d" % rc)
     cx, ex, ux = O.split(X)
-    fields = {"c": cx, "eta": ex}
+    # one order parameter: "eta"; three (App. A): "eta1".."eta3"
+    fields = {"c": cx, "eta": ex} if ex.ndim == 1 else {"c": cx, **{"eta%d" % (j + 1): ex[j] for j in range(len(ex))}}
     if ux is not None:
         for I in range(cfg["dim"]):
             fields["u%d" % (I + 1)] = ux[I]

@@ -74,7 +74,7 @@ def test_full_size_steps_match_the_oracle(nks, name, precision):
         prevE = info["energy"]
     cg, eg, ug = P.get_fields()
     P.destroy()
-    fields = {"c": cg, "eta": eg}
+    fields = {"c": cg, "eta": eg} if eg.ndim == 1 else {"c": cg, **{"eta%d" % (j + 1): eg[j] for j in range(len(eg))}}
     if ug is not None:
         for I in range(len(ug)):
             fields["u%d" % (I + 1)] = ug[I]

@@ -61,7 +61,7 @@ def _pair(dim, n, seed, elastic):
 # (dim, grid, subdomains, overlap, elastic, neumann)
 CASES = [(2, (21, 18), (2, 2), 1, True, False), (3, (10, 9, 8), (2, 2, 2), 1, True, False),
          (1, (45,), (3,), 2, True, False), (2, (19, 17), (2, 2), 1, False, False),
-         (3, (9, 8, 7), (2, 2, 2), 1, False, False), (2, (20, 16), (2, 2), 1, True, True),
+         (3, (9, 10, 8), (2, 2, 2), 1, False, False), (2, (20, 16), (2, 2), 1, True, True),
          (3, (8, 8, 6), (2, 2, 2), 1, True, True)]
 
 

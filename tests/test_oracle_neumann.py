@@ -9,7 +9,9 @@ one) and for whole NKS steps in 1-D and 2-D without elasticity.  The traction-
 free displacement rows are the exact variation of the discrete elastic energy:
 -F_u equals its finite differences (on periodic grids too, where it is the
 divergence form).  Mass conservation, the energy law and the Jacobian against
-central differences hold with elasticity.  No CUDA path yet.
+central differences hold with elasticity.  The projection removes the whole null
+space of the traction-free displacement block (its dimension counted by an SVD),
+so the displacement does not depend on the Schwarz decomposition.
 """
 import numpy as np
 import pytest

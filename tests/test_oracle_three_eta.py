@@ -11,7 +11,7 @@ The model is checked against what the mathematics fixes, not against itself:
     residual;
   * on asymmetric states the steps conserve mass and do not increase the
     energy (Theorem 3.2), and permuting eta_1, eta_2, eta_3 permutes the result.
-No CUDA path exists for this model yet; these tests run on the CPU only.
+These tests run on the CPU only; tests/test_gpu_model3.py holds the CUDA path to them.
 """
 import numpy as np
 import pytest
