@@ -3,7 +3,8 @@ oracle's run of the same workload.
 
 The oracle's references (``tests/golden/full_<workload>.json``, written by
 ``tests/golden/make_full_size.py``, which calls only the oracle) hold, for the
-first steps of the 2-D 1024^2 and 3-D 128^3 workloads, the step sizes the
+first steps of the 2-D 1024^2 and 3-D 128^3 workloads and of the 3-D 128^3
+workload with three order parameters (App. A), the step sizes the
 oracle's adaptive controller chose (Sec. 4, Eq. sencondt), the energy and mass
 after every step, and for every field of the final state its L2 norm, a
 256-row seeded sign sketch and its values at 1024 seeded points.  Here the
@@ -29,7 +30,7 @@ import synthetic as S
 pytestmark = pytest.mark.gpu
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-WORKLOADS = ["3d128", "2d1024"]
+WORKLOADS = ["3d128", "2d1024", "3d128eta3"]
 
 
 @pytest.fixture(scope="module")
