@@ -94,6 +94,9 @@ def kernel_rates(st, cfg, mixed, pk):
     # Arnoldi step of the mixed mode
     rate("jacobian_action", st["launches"]["jacobian_action"] * (2 * f + (1 + ne) ** 2 + d) * b * N,
          bound="hbm" if mixed else "fp64")
+    # the FP64 action on the true residual at the end of every GMRES cycle (both precisions)
+    rate("true_residual_jv", st["launches"].get("true_residual_jv", 0) * (2 * f + (1 + ne) ** 2 + d) * 8.0 * N,
+         bound="fp64")
     # Gram-Schmidt: (2j + 5) basis-vector transfers per pass of Arnoldi step j (counted by the library)
     gs_ms = st["ms"].get("gs_dots", 0.0) + st["ms"].get("gs_update", 0.0)
     if gs_ms > 0 and st.get("cgs_bytes", 0) > 0:
@@ -112,7 +115,7 @@ def traffic_for(workload_name, side, precision, kernel):
     workload, precision and the library's current source hash; None (with the
     reason) when no capture of the current kernels exists."""
     from paper_2209_08001_gb300 import build
-    h = build.source_hash()
+    h = build.source_hash(kernel)
     try:
         entries = json.load(open(TRAFFIC_FILE))["entries"]
     except Exception:
@@ -465,11 +468,11 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     pk = peaks()
 
-    def create(o):
+    def create(o, timing=False):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         P = nks.Problem(cfg["dim"], cfg["n"], cfg["h"], c, e, S.config_coefficients(cfg), o,
-                        stream=stream.cuda_stream, allocator=alloc, timing=True)
+                        stream=stream.cuda_stream, allocator=alloc, timing=timing)
         torch.cuda.synchronize()
         sst = P.get_stats()
         return P, {"seconds": time.perf_counter() - t0, "u0_newton_its": sst["newton_its"],
@@ -477,20 +480,35 @@ def run_ours(args):
                    "includes": "problem creation: plan, factor tables, upload, initial mechanical equilibrium "
                                "(Newton on the displacement rows, tolerance u0_rtol)"}
 
-    def summary(P, ms, infos, mixed):
-        st = P.get_stats()
+    def instrumented(o, dts):
+        """the same K steps (dt replayed) on a problem that times every kernel class with
+        CUDA events on its stream (graph replay off): the per-class breakdown"""
+        T, _ = create(o, timing=True)
+        ms_t, infos_t = timed_run(T, args.steps, args.warmup, stream, dts=dts)
+        st = T.get_stats()
+        T.destroy()
+        return st, ms_t, infos_t
+
+    def summary(P, ms, infos, mixed, st, ms_t, infos_t):
         kernels = kernel_rates(st, cfg, mixed, pk)
         total_ms = sum(st["ms"].values())
-        return st, {
+        return {
             "value": sum_over_ranks(dist, float(N * len(infos)), dev) / (max_over_ranks(dist, ms, dev) / 1e3),
             "ms_per_step": max_over_ranks(dist, ms, dev) / len(infos),
             "roofline": roofline(st, kernels, mixed, pk, args.config, args.grid, "mixed" if mixed else "fp64"),
             "kernels": kernels,
             "kernel_time_share": {k: round(v / max(total_ms, 1e-9), 4) for k, v in st["ms"].items() if v > 0},
-            "iterations": {"newton_per_step": st["newton_its"] / max(st["steps"], 1),
-                           "gmres_per_step": st["gmres_its"] / max(st["steps"], 1),
+            "instrumented": {"ms_per_step": ms_t / len(infos_t),
+                             "same_iterations": [(i["newton_its"], i["gmres_its"]) for i in infos] ==
+                                                [(i["newton_its"], i["gmres_its"]) for i in infos_t],
+                             "about": "roofline, kernels and kernel_time_share come from a replay of the same K "
+                                      "steps (dt replayed) with CUDA events around every kernel class on the "
+                                      "solver's stream and graph replay off; value and ms_per_step from the run "
+                                      "as a user runs it (GMRES iterations replayed from CUDA graphs)"},
+            "iterations": {"newton_per_step": sum(i["newton_its"] for i in infos) / max(len(infos), 1),
+                           "gmres_per_step": sum(i["gmres_its"] for i in infos) / max(len(infos), 1),
                            "dt": [i["dt"] for i in infos]},
-            "gpu_launches": int(st["kernel_launches"])}
+            "gpu_launches": int(P.get_stats()["kernel_launches"])}
 
     # --- the headline solver: K timed steps from the initial state ---------------
     P, setup = create(op)
@@ -503,9 +521,9 @@ def run_ours(args):
     if dist is not None:
         dist.barrier()
     mixed = prec == "mixed"
-    st, head = summary(P, ms, infos, mixed)
-    value = head["value"]
     dts = [i["dt"] for i in infos]
+    head = summary(P, ms, infos, mixed, *instrumented(op, dts))
+    value = head["value"]
 
     # --- the FP64 solver beside it on the same steps (same K, W, dt sequence) ---
     fp64 = None
@@ -516,7 +534,7 @@ def run_ours(args):
         clocks64.start()
         ms64, infos64 = timed_run(Q, args.steps, args.warmup, stream, dts=dts)
         clk64 = clocks64.stop()
-        _, fp64 = summary(Q, ms64, infos64, False)
+        fp64 = summary(Q, ms64, infos64, False, *instrumented(dict(op, precision="fp64"), dts))
         fp64.update({"setup": qsetup, "clocks": clk64, "dt_sequence": "replayed from the mixed-precision run",
                      "mixed_over_fp64": value / fp64["value"]})
         fm = field_dict(*P.get_fields())
@@ -579,6 +597,7 @@ def run_ours(args):
         "roofline": head["roofline"],
         "kernels": head["kernels"],
         "kernel_time_share": head["kernel_time_share"],
+        "instrumented": head["instrumented"],
         "iterations": head["iterations"],
         "fp64": fp64,
         "accuracy": accuracy,

@@ -205,7 +205,7 @@ typedef struct {
 } nks_step_info;
 
 /* Per-kernel-class counters (launches and, with opts.timing, device time). */
-#define NKS_NCLASS 10
+#define NKS_NCLASS 11
 typedef struct {
     long long launches[NKS_NCLASS];
     double ms[NKS_NCLASS];          /* summed CUDA-event durations (timing = 1) */
@@ -222,9 +222,11 @@ typedef struct {
                                        passes: (2j + 5) basis-vector reads and
                                        writes for Arnoldi step j, per pass      */
 } nks_stats;
-/* kernel classes: 0 residual, 1 Jacobian action, 2 Schwarz apply,
- * 3 assembly + ILU(0), 4 Gram-Schmidt dots, 5 Gram-Schmidt update,
- * 6 projection, 7 energy/mass, 8 vector ops, 9 small dense (Hessenberg) */
+/* kernel classes: 0 residual, 1 Jacobian action of the Arnoldi steps (FP32 in
+ * mixed precision), 2 Schwarz apply, 3 assembly + ILU(0), 4 Gram-Schmidt dots,
+ * 5 Gram-Schmidt update, 6 projection, 7 energy/mass, 8 vector ops, 9 small
+ * dense (Hessenberg), 10 FP64 Jacobian action of the true residual b - J x at
+ * the end of each GMRES cycle */
 
 /* Fill *o with the default solver settings (Sec. 4-5): eps_r = 1e-10,
  * GMRES(30), 4x4 subdomains with overlap 1, ILU(0)-reuse, dt_1 = dt_min =

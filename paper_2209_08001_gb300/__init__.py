@@ -22,7 +22,7 @@ NKS_FP64, NKS_MIXED = 0, 1
 RAS_VARIANTS = {"left-ras": 0, "as": 1, "right-ras": 2}
 DT_MODES = {"fixed": 0, "solution": 1, "energy": 2}
 KERNEL_CLASSES = ["residual", "jacobian_action", "schwarz_apply", "assembly_ilu0", "gs_dots", "gs_update",
-                  "projection", "energy_mass", "vector_ops", "hessenberg"]
+                  "projection", "energy_mass", "vector_ops", "hessenberg", "true_residual_jv"]
 
 
 class NksError(RuntimeError):
@@ -99,7 +99,7 @@ class nks_step_info(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
-NCLASS = 10
+NCLASS = 11
 
 
 class nks_stats(ctypes.Structure):

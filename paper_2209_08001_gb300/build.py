@@ -35,12 +35,21 @@ def _stale():
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def source_hash() -> str:
-    """sha256 (16 hex digits) of the library's sources, header and build flags:
-    identifies the kernels a profile was taken of."""
+# the sources each profiled kernel is compiled from (its own file, the headers it uses)
+KERNEL_SOURCES = {
+    "k_ras_apply_lane": ["nks_ras.cu", "nks_pattern.cuh", "nks_internal.cuh"],
+    "k_ras_apply": ["nks_ras.cu", "nks_pattern.cuh", "nks_internal.cuh"],
+    "k_jv32": ["nks_stencil.cu", "nks_model3.cuh", "nks_internal.cuh"],
+}
+
+
+def source_hash(kernel: str = None) -> str:
+    """sha256 (16 hex digits) of the sources a kernel is compiled from (all of the
+    library's when kernel is None or unknown), the C header and the build flags:
+    identifies the kernel build a profile was taken of."""
     import hashlib
     h = hashlib.sha256()
-    files = sorted(os.listdir(CSRC))
+    files = sorted(KERNEL_SOURCES.get(kernel) or os.listdir(CSRC))
     for f in files:
         with open(os.path.join(CSRC, f), "rb") as fh:
             h.update(f.encode() + b"\0" + fh.read())

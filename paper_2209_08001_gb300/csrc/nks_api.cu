@@ -820,6 +820,7 @@ int nks_create_batch(const nks_grid *grid, int nb, const double *c, const double
     }
     for (size_t q = 0; q < items.size(); q++) *items[q].ptr = P->slab + off[q];
     ras_prepare_launch(P);
+    if (P->f32) prepare_jv32(P->g, P->k);
     cudaMemsetAsync(P->slab, 0, (size_t)P->stride * nb, P->stream);
     cudaMemsetAsync(P->dmask, 0, sizeof(int) * kMasks * nb, P->stream);
     rc = P->sync_check("create");

@@ -200,7 +200,9 @@ int launch_residual(const DGrid &g, const DCoef &k, const double *isc, int mode,
 int launch_jv64(const DGrid &g, const DCoef &k, const double *isc, int mode, const double *part, const double *mob,
                 const double *v, double *dG, double *sig, double *Jv, cudaStream_t st, const Bat &bt,
                 const double *zsum = nullptr);
-// FP32 arithmetic and storage (FP32 copies of part and mob)
+// FP32 arithmetic and storage (FP32 copies of part and mob); prepare_jv32 sets the
+// kernel attributes it needs (once per problem, before any graph capture)
+void prepare_jv32(const DGrid &g, const DCoef &k);
 int launch_jv32(const DGrid &g, const DCoef &k, const double *isc, int mode, const float *part, const float *mob,
                 const float *v, float *Jv, cudaStream_t st, const Bat &bt, const double *zsum);
 int launch_energy(const DGrid &g, const DCoef &k, const double *isc, const double *X, double *partials, int rb,

@@ -586,17 +586,18 @@ static int norm2_batch(Problem *P, const double *x, const Bat &bt, std::vector<d
     return NKS_OK;
 }
 
+// cls: the timer class (1: the Arnoldi steps' action, 10: the true residual's)
 template <typename TV>
-static void apply_J(Problem *P, int mode, const TV *v, TV *out, bool project_input, const Bat &bt)
+static void apply_J(Problem *P, int mode, const TV *v, TV *out, bool project_input, const Bat &bt, int cls = 1)
 {
-    P->tick(1);
+    P->tick(cls);
     if constexpr (sizeof(TV) == sizeof(float))
         P->count(launch_jv32(P->g, P->k, P->isc, mode, P->partf, P->mobf, v, out, P->stream, bt,
                              project_input ? P->zsum : nullptr));
     else
         P->count(launch_jv64(P->g, P->k, P->isc, mode, P->part, P->mob, v, P->Gc, P->sig, out, P->stream, bt,
                              project_input ? P->zsum : nullptr));
-    P->tock(1);
+    P->tock(cls);
 }
 
 // Start of a solve: in mixed precision the FP32 copies of the operator's
@@ -802,7 +803,7 @@ static int gmres_t(Problem *P, Basis<TV> K, int mode, const double *b, double *x
         // so P is applied once to the FP64 sum; every Newton correction keeps
         // sum s_c = 0 and the gauge of u to FP64 rounding
         project(P, x, bc);
-        apply_J<double>(P, mode, x, Jx, false, bc);
+        apply_J<double>(P, mode, x, Jx, false, bc, 10);
         P->count(launch_waxpy(n, b, -1.0, Jx, R, st, bc));
         rc = norm2_batch(P, R, bc, b2);
         if (rc) return rc;

@@ -13,6 +13,8 @@
 // (mixed-precision Arnoldi vectors).
 #include <math.h>
 
+#include <algorithm>
+
 #include "nks_internal.cuh"
 #include "nks_model3.cuh"
 
@@ -733,6 +735,245 @@ __global__ void __launch_bounds__(256) k_jv32(DGrid g, JvConst<float> c, Bat bt,
     }
 }
 
+// ---- FP32, 3-D: 2.5-D z-marching form ------------------------------------------
+//
+// A block owns a JZ_TX x JZ_TY column of points and marches along z over zc planes.
+// The input v streams through a ring of five planes in shared memory (every field,
+// with a two-cell halo in x and y), each plane loaded once by cp.async while the
+// block works on the planes below it; dG_c and sigma are formed once per halo cell
+// and plane into a ring of three planes, from which the flux and divergence forms
+// of the plane take their neighbours.  Per output point the block reads v once
+// (plus the halo share), the pointwise block and the mobilities once, and writes
+// J v once; dG_c and sigma never leave shared memory.
+//
+// Halo cells beyond the grid hold the wrapped (periodic) or mirrored (Neumann:
+// the boundary cell itself) values; with Neumann boundaries a stage-1 cell or
+// plane beyond the grid takes the values of the boundary cell, as in the tiled form.
+constexpr int JZ_TX = 32, JZ_TY = 8;
+constexpr int JZ_VX = JZ_TX + 4, JZ_VY = JZ_TY + 4, JZ_VP = JZ_VX * JZ_VY;  // v tile, 2-cell halo
+constexpr int JZ_SX = JZ_TX + 2, JZ_SY = JZ_TY + 2, JZ_SP = JZ_SX * JZ_SY;  // dG / sigma tile, 1-cell halo
+constexpr int JZ_NV = 5;                                                   // v ring planes
+// threads per block: every dG / sigma cell of a plane in one pass (340 of 352); the
+// first 256 form J v on the plane
+constexpr int JZ_THREADS = 352;
+static_assert(JZ_THREADS >= JZ_SP && JZ_THREADS >= JZ_TX * JZ_TY && 2 * JZ_THREADS >= JZ_VP, "tile shapes");
+
+__device__ __forceinline__ void cp_async4(float *dst, const float *src)
+{
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// coordinate a of an axis of n cells seen from a halo cell (|overhang| <= 2):
+// periodic wrap, or the mirror ghost's cell (clamp) with Neumann boundaries
+__device__ __forceinline__ int halo_coord(int a, int n, int bc)
+{
+    if (bc) return a < 0 ? 0 : (a >= n ? n - 1 : a);
+    return a < 0 ? a + n : (a >= n ? a - n : a);
+}
+
+// resident blocks of k_jv32_z on the device (set with the kernel's attributes)
+template <bool EL, int NE>
+struct JzOcc {
+    static int resident;
+};
+template <bool EL, int NE>
+int JzOcc<EL, NE>::resident = 0;
+
+template <int NF>
+static size_t jv32z_smem(int ns)
+{
+    return sizeof(float) * ((size_t)JZ_NV * NF * JZ_VP + (size_t)3 * (1 + ns) * JZ_SP);
+}
+
+template <bool EL, int NE>
+__global__ void __launch_bounds__(JZ_THREADS) k_jv32_z(DGrid g, JvConst<float> c, Bat bt, const double *__restrict__ isc,
+                                                const float *__restrict__ part, const float *__restrict__ mob,
+                                                const float *__restrict__ v, float *__restrict__ Jv,
+                                                const double *__restrict__ zsum, int zc)
+{
+    constexpr int KU = 1 + NE, NF = KU + (EL ? 3 : 0), NS = EL ? 6 : 1;
+    long long io;
+    if (!inst_off(bt, blockIdx.y, io)) return;
+    part = shift(part, io);
+    mob = shift(mob, io);
+    v = shift(v, io);
+    Jv = shift(Jv, io);
+    extern __shared__ __align__(16) float jz_smem[];
+    float *sv = jz_smem;                            // [JZ_NV][NF][JZ_VP]
+    float *sg = jz_smem + JZ_NV * NF * JZ_VP;       // [3][1 + NS][JZ_SP]
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2], bc = g.bc;
+    const int N = (int)g.N, nxy = nx * ny;
+    const int tx_n = (nx + JZ_TX - 1) / JZ_TX, ty_n = (ny + JZ_TY - 1) / JZ_TY;
+    int b = blockIdx.x;
+    const int x0 = (b % tx_n) * JZ_TX;
+    b /= tx_n;
+    const int y0 = (b % ty_n) * JZ_TY;
+    const int z0 = (b / ty_n) * zc;
+    const int z1 = min(z0 + zc, nz);
+    const int tid = threadIdx.x;
+    __shared__ float sidt, sm;
+    if (tid == 0) {
+        sidt = (float)shift(isc, io)[I_IDT];
+        sm = zsum ? (float)(shift(zsum, io)[0] * (double)c.invN) : 0.f;
+    }
+    // in-plane source offsets of this thread's v-tile cells (at most two); -1: unused cell
+    int voff[2];
+#pragma unroll
+    for (int r = 0; r < 2; r++) {
+        const int q = tid + r * JZ_THREADS;
+        voff[r] = -1;
+        if (q < JZ_VP) {
+            const int gx = x0 - 2 + q % JZ_VX, gy = y0 - 2 + q / JZ_VX;
+            if (gx <= nx + 1 && gy <= ny + 1) voff[r] = halo_coord(gx, nx, bc) + nx * halo_coord(gy, ny, bc);
+        }
+    }
+    // ring slots: planes are visited in increasing order from z0 - 2, so the slot of a
+    // plane is its distance from z0 - 2 modulo the ring size (no negative operands)
+    auto vplane = [&](int plane) -> float * { return sv + (size_t)((plane - z0 + 2) % JZ_NV) * NF * JZ_VP; };
+    auto splane = [&](int plane) -> float * { return sg + (size_t)((plane - z0 + 3) % 3) * (1 + NS) * JZ_SP; };
+    auto load_plane = [&](int plane) {
+        const float *src = v + (size_t)halo_coord(plane, nz, bc) * nxy;
+        float *dst = vplane(plane);
+#pragma unroll
+        for (int r = 0; r < 2; r++)
+            if (voff[r] >= 0) {
+                const int q = tid + r * JZ_THREADS;
+#pragma unroll
+                for (int f = 0; f < NF; f++) cp_async4(dst + f * JZ_VP + q, src + (size_t)f * N + voff[r]);
+            }
+        cp_async_commit();
+    };
+
+    // stage 1: dG_c and sigma of plane zs on the 1-cell-halo tile
+    auto stage1 = [&](int zs, float m) {
+        const int zsrc = bc ? (zs < 0 ? 0 : (zs >= nz ? nz - 1 : zs)) : zs;  // plane whose values zs holds
+        const int zg = halo_coord(zsrc, nz, 0);                                // its index in the grid
+        const float *__restrict__ Vm = vplane(zsrc - 1), *__restrict__ V0 = vplane(zsrc),
+                    *__restrict__ Vp = vplane(zsrc + 1);
+        float *__restrict__ Sz = splane(zs);
+        for (int q = tid; q < JZ_SP; q += JZ_THREADS) {
+            const int gx = x0 - 1 + q % JZ_SX, gy = y0 - 1 + q / JZ_SX;
+            if (gx > nx || gy > ny) continue;  // beyond a ragged tile: never read
+            const int sx = bc ? (gx < 0 ? 0 : (gx >= nx ? nx - 1 : gx)) : gx;
+            const int sy = bc ? (gy < 0 ? 0 : (gy >= ny ? ny - 1 : gy)) : gy;
+            const int o = (sx - x0 + 2) + JZ_VX * (sy - y0 + 2);  // the source cell in the v tile
+            const float v0 = V0[o], vc = v0 - m;
+            float trd = 0.f;
+            if constexpr (EL) {
+                float Dd[3][3];
+#pragma unroll
+                for (int I = 0; I < 3; I++) {
+                    const int fo = (KU + I) * JZ_VP + o;
+                    Dd[I][0] = V0[fo + 1] - V0[fo - 1];
+                    Dd[I][1] = V0[fo + JZ_VX] - V0[fo - JZ_VX];
+                    Dd[I][2] = Vp[fo] - Vm[fo];
+                }
+                trd = Dd[0][0] + Dd[1][1] + Dd[2][2];
+                const float common = c.b * trd - c.ls * vc;
+#pragma unroll
+                for (int I = 0; I < 3; I++) {
+                    Sz[(1 + I) * JZ_SP + q] = c.ab * Dd[I][I] + common;
+#pragma unroll
+                    for (int J = I + 1; J < 3; J++) Sz[(1 + scomp(3, I, J)) * JZ_SP + q] = c.c4 * (Dd[I][J] + Dd[J][I]);
+                }
+            }
+            if (c.mode == 0) {
+                const int p = halo_coord(sx, nx, 0) + nx * (halo_coord(sy, ny, 0) + ny * zg);
+                const float sn = V0[o + 1] + V0[o - 1] + V0[o + JZ_VX] + V0[o - JZ_VX] + Vp[o] + Vm[o];
+                const float lc = sn - 6.f * v0;
+                float dg = part[p] * vc;
+#pragma unroll
+                for (int j = 1; j <= NE; j++) dg += part[(size_t)j * N + p] * V0[j * JZ_VP + o];
+                dg -= c.gc * lc;
+                if constexpr (EL) dg += c.el_c * vc - c.el_t * trd;
+                Sz[q] = dg;
+            }
+        }
+    };
+
+    // prologue: v planes z0-2 .. z0+2, stage 1 of planes z0-1 and z0
+    for (int pl = z0 - 2; pl <= z0 + 2; pl++) load_plane(pl);
+    cp_async_wait_all();
+    __syncthreads();
+    const float m = sm, idt = sidt;
+    stage1(z0 - 1, m);
+    stage1(z0, m);
+    const float ih2 = c.ih2, ge = c.ge, i2h = c.i2h;
+    const int txl = tid % JZ_TX, tyl = tid / JZ_TX;
+    const int hq = (txl + 1) + JZ_SX * (tyl + 1), o = (txl + 2) + JZ_VX * (tyl + 2);
+    const bool inxy = tid < JZ_TX * JZ_TY && x0 + txl < nx && y0 + tyl < ny;
+    for (int z = z0; z < z1; z++) {
+        cp_async_wait_all();  // v plane z + 2 (issued one iteration ago)
+        __syncthreads();      // ... visible to all; stage 2 of plane z - 1 finished
+        load_plane(z + 3);    // into the slot of plane z - 2, no longer read
+        stage1(z + 1, m);     // into the ring slot of plane z - 2
+        __syncthreads();
+        // stage 2: J v on plane z
+        if (inxy) {
+            const float *__restrict__ Vm = vplane(z - 1), *__restrict__ V0 = vplane(z), *__restrict__ Vp = vplane(z + 1);
+            const float *__restrict__ Sm = splane(z - 1), *__restrict__ S0 = splane(z), *__restrict__ Sp = splane(z + 1);
+            const int c3[3] = {x0 + txl, y0 + tyl, z};
+            const int nn[3] = {nx, ny, nz};
+            const int p = c3[0] + nx * (c3[1] + ny * z);
+            int im[3], ip[3];
+            nbr_offsets<3>(c3, nn, p, im, ip, bc);
+            const float vc = V0[o] - m;
+            float ve[NE], je[NE], jc;
+#pragma unroll
+            for (int j = 0; j < NE; j++) ve[j] = V0[(1 + j) * JZ_VP + o];
+            if (c.mode == 0) {
+                const float G0 = S0[hq];
+                const float gp[3] = {S0[hq + 1], S0[hq + JZ_SX], Sp[hq]};
+                const float gm[3] = {S0[hq - 1], S0[hq - JZ_SX], Sm[hq]};
+                float flux = 0.f;
+#pragma unroll
+                for (int J = 0; J < 3; J++) flux += mob[J * N + p] * (gp[J] - G0) - mob[J * N + im[J]] * (G0 - gm[J]);
+                jc = vc * idt - flux * ih2;
+#pragma unroll
+                for (int j = 0; j < NE; j++) {
+                    const int fo = (1 + j) * JZ_VP + o;
+                    const float sn = V0[fo + 1] + V0[fo - 1] + V0[fo + JZ_VX] + V0[fo - JZ_VX] + Vp[fo] + Vm[fo];
+                    const float *pr = part + (size_t)(1 + j) * KU * N + p;
+                    if constexpr (NE == 1) {
+                        je[j] = ve[j] * idt + pr[0] * vc + pr[N] * ve[j] - ge * (sn - 6.f * ve[j]);
+                    } else {
+                        float pw = pr[0] * vc;
+#pragma unroll
+                        for (int i = 0; i < NE; i++) pw += pr[(size_t)(1 + i) * N] * ve[i];
+                        je[j] = ve[j] * idt + c.keta * pw - ge * (sn - 6.f * ve[j]);
+                    }
+                }
+            } else {
+                jc = vc;
+#pragma unroll
+                for (int j = 0; j < NE; j++) je[j] = ve[j];
+            }
+            Jv[p] = jc;
+#pragma unroll
+            for (int j = 0; j < NE; j++) Jv[(size_t)(1 + j) * N + p] = je[j];
+            if constexpr (EL) {
+                // the mirrored neighbour's stress enters with the opposite sign (Neumann)
+#pragma unroll
+                for (int I = 0; I < 3; I++) {
+                    float div = 0.f;
+#pragma unroll
+                    for (int J = 0; J < 3; J++) {
+                        const int k = (1 + scomp(3, I, J)) * JZ_SP + hq;
+                        const float a = J == 0 ? S0[k + 1] : (J == 1 ? S0[k + JZ_SX] : Sp[k]);
+                        const float bb = J == 0 ? S0[k - 1] : (J == 1 ? S0[k - JZ_SX] : Sm[k]);
+                        div += (ip[J] == p ? -a : a) - (im[J] == p ? -bb : bb);
+                    }
+                    Jv[(size_t)(KU + I) * N + p] = div * i2h;
+                }
+            }
+        }
+    }
+    cp_async_wait_all();  // no copy outlives the block
+}
+
 __device__ inline double Psi(double z) { return z * log(z) + (1.0 - z) * log1p(-z); }
 
 // E_1 and E_2 densities of the model with three order parameters (App. A):
@@ -887,6 +1128,20 @@ template <int D, bool EL, int NE>
 static void launch_jv32_d(const DGrid &g, const JvConst<float> &c, const Bat &bt, const double *isc, const float *part,
                           const float *mob, const float *v, float *Jv, cudaStream_t st, const double *zsum)
 {
+    if constexpr (D == 3) {
+        constexpr int NF = 1 + NE + (EL ? 3 : 0);
+        const size_t smem = jv32z_smem<NF>(EL ? 6 : 1);  // limit set by prepare_jv32
+        // planes per block: split each column into as many chunks as one wave of resident
+        // blocks holds (each chunk forms two extra planes of dG and sigma)
+        const long long cols = (long long)((g.n[0] + JZ_TX - 1) / JZ_TX) * ((g.n[1] + JZ_TY - 1) / JZ_TY) * bt.nb;
+        const long long cap = (long long)std::max(1, JzOcc<EL, NE>::resident);
+        const long long want = std::max(1LL, (cap + cols / 2) / cols);
+        const int zc = std::max(4, (int)((g.n[2] + want - 1) / want));
+        const long long tiles = cols / bt.nb * ((g.n[2] + zc - 1) / zc);
+        k_jv32_z<EL, NE><<<dim3((unsigned)tiles, bt.nb), JZ_THREADS, smem, st>>>(g, c, bt, isc, part, mob, v, Jv, zsum,
+                                                                                zc);
+        return;
+    }
     constexpr int TX = JvTile<D>::TX, TY = JvTile<D>::TY, TZ = JvTile<D>::TZ;
     const long long tiles = (long long)((g.n[0] + TX - 1) / TX) * ((g.n[1] + TY - 1) / TY) * ((g.n[2] + TZ - 1) / TZ);
     k_jv32<D, EL, NE><<<dim3((unsigned)tiles, bt.nb), 256, 0, st>>>(g, c, bt, isc, part, mob, v, Jv, zsum);
@@ -908,6 +1163,23 @@ static void launch_jv32_d(const DGrid &g, const JvConst<float> &c, const Bat &bt
     case 14: FN<3, false, 3>(__VA_ARGS__); break;                     \
     default: FN<3, true, 3>(__VA_ARGS__); break;                      \
     }
+
+template <int D, bool EL, int NE>
+static void prepare_jv32_d()
+{
+    if constexpr (D == 3) {
+        constexpr int NF = 1 + NE + (EL ? 3 : 0);
+        const int smem = (int)jv32z_smem<NF>(EL ? 6 : 1);
+        cudaFuncSetAttribute(k_jv32_z<EL, NE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        int per_sm = 0, nsm = 0, dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jv32_z<EL, NE>, JZ_THREADS, smem) == cudaSuccess)
+            JzOcc<EL, NE>::resident = per_sm * nsm;  // otherwise one block: one chunk per column
+    }
+}
+
+void prepare_jv32(const DGrid &g, const DCoef &k) { NKS_JV_DISPATCH(prepare_jv32_d); }
 
 int launch_jv64(const DGrid &g, const DCoef &k, const double *isc, int mode, const double *part, const double *mob,
                 const double *v, double *dG, double *sig, double *Jv, cudaStream_t st, const Bat &bt,

@@ -204,9 +204,9 @@ CONFIGS = {
         opts=dict(dt_mode="energy", sub=(8, 8, 8), overlap=1, precision="fp64")),
     "3d128eta3": dict(
         desc="3D 128^3 periodic, three order parameters (App. A, eta_1..eta_3 drawn independently), "
-             "50 adaptive DVD steps, FP64 beside mixed precision, RAS 8x8x8 subdomains overlap 1",
+             "50 adaptive DVD steps, FP64 beside mixed precision, RAS 8x16x16 subdomains overlap 1",
         dim=3, n=(128, 128, 128), h=0.25, cbar=0.18, seed=2, steps=50, init="three", coeffs=dict(n_eta=3),
-        opts=dict(dt_mode="energy", sub=(8, 8, 8), overlap=1, precision="fp64")),
+        opts=dict(dt_mode="energy", sub=(8, 16, 16), overlap=1, precision="fp64")),
     "3d256": dict(
         desc="3D 256^3 periodic mixed precision, 100 adaptive DVD steps, RAS 16x16x16 subdomains overlap 1",
         dim=3, n=(256, 256, 256), h=0.25, cbar=0.22, seed=3, steps=100,

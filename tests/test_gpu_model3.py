@@ -123,7 +123,7 @@ def test_model3_operators_match_oracle(nks, dim, n, sub, ov, elastic, neumann):
     P.destroy()
 
 
-@pytest.mark.parametrize("dim,n,sub,ov,elastic,neumann", [CASES[0], CASES[1], CASES[5]])
+@pytest.mark.parametrize("dim,n,sub,ov,elastic,neumann", [CASES[0], CASES[1], CASES[5], CASES[6]])
 def test_model3_mixed_operators_match_oracle(nks, dim, n, sub, ov, elastic, neumann):
     """FP32 Jacobian action within 1e-5 of |J| |v| per row; FP32 Schwarz sweep within 1e-4."""
     cf = S.coefficients(n_eta=3)
