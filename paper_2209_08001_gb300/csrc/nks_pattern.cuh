@@ -21,7 +21,8 @@ namespace nks {
 // ---------------------------------------------------------------------------
 
 // Fields of a point: c (0), the k.ne order parameters (1..k.ne), then the
-// displacement components (from 1 + k.ne).
+// displacement components (from 1 + k.ne).  The row functions take the count as
+// a template argument NE when the caller knows it (NE = 0: k.ne at run time).
 struct RowCtx {
     double a0[7];         // dGc/dc1 at p (0) and p + e_J (1 + 2J), p - e_J (2 + 2J)
     double a1[7][3];      // dGc/deta_j1 at the same points
@@ -32,7 +33,7 @@ struct RowCtx {
 
 // contributions of the linearised G_c at q = the end of step o from p (o = 0 or
 // +-e_J) with weight w
-template <class Acc>
+template <int NE = 0, class Acc>
 __host__ __device__ constexpr void add_grow(Acc &acc, const DCoef &k, int d, double h, int ox, int oy, int oz, double w,
                                          double a0, const double (&a1)[3])
 {
@@ -45,10 +46,11 @@ __host__ __device__ constexpr void add_grow(Acc &acc, const DCoef &k, int d, dou
         acc(ox, oy, oz, ex, ey, ez, 0, -w * 0.5 * k.gamma_c * ih2);
         acc(ox, oy, oz, -ex, -ey, -ez, 0, -w * 0.5 * k.gamma_c * ih2);
     }
-    for (int j = 0; j < k.ne; j++) acc(ox, oy, oz, 0, 0, 0, 1 + j, w * a1[j]);
+    const int ne = NE ? NE : k.ne;
+    for (int j = 0; j < ne; j++) acc(ox, oy, oz, 0, 0, 0, 1 + j, w * a1[j]);
     if (k.elastic) {
         const double t = w * k.eps0 * k.lam * 0.25 / h;  // G^3_c = -eps0 lam (sum_K Dhat_K u_K - d eps0 c ...)/2
-        const int ku = 1 + k.ne;
+        const int ku = 1 + ne;
         for (int K = 0; K < d; K++) {
             const int ex = K == 0, ey = K == 1, ez = K == 2;
             acc(ox, oy, oz, ex, ey, ez, ku + K, -t);
@@ -59,12 +61,12 @@ __host__ __device__ constexpr void add_grow(Acc &acc, const DCoef &k, int d, dou
 
 // sigma_IJ(q) row, q = the end of step o from p, weight w (stress of eps(u) -
 // eps0 (c - cbar) I)
-template <class Acc>
+template <int NE = 0, class Acc>
 __host__ __device__ constexpr void add_sigrow(Acc &acc, const DCoef &k, int d, double h, int ox, int oy, int oz, int I,
                                            int J, double w)
 {
     const double i2h = 0.5 / h;
-    const int ku = 1 + k.ne;
+    const int ku = 1 + (NE ? NE : k.ne);
     if (I == J) {
         for (int K = 0; K < d; K++) {
             const int ex = K == 0, ey = K == 1, ez = K == 2;
@@ -90,7 +92,7 @@ __host__ __device__ constexpr void add_sigrow(Acc &acc, const DCoef &k, int d, d
 // (with Neumann boundaries its traction-free form: a step that stays on the cell
 // enters with the opposite sign, acc.flip).
 // mode 1 (displacement-only system): c and eta rows are identity rows.
-template <class Acc>
+template <int NE = 0, class Acc>
 __host__ __device__ constexpr void jac_row(Acc &acc, int f, const DCoef &k, int d, double h, double dt, int mode,
                                         const RowCtx &r)
 {
@@ -103,13 +105,13 @@ __host__ __device__ constexpr void jac_row(Acc &acc, int f, const DCoef &k, int 
         acc(0, 0, 0, 0, 0, 0, 0, 1.0 / dt);
         double wc = 0.0;
         for (int J = 0; J < d; J++) wc += (r.Mp[J] + r.Mm[J]) * ih2;
-        add_grow(acc, k, d, h, 0, 0, 0, wc, r.a0[0], r.a1[0]);
+        add_grow<NE>(acc, k, d, h, 0, 0, 0, wc, r.a0[0], r.a1[0]);
         for (int J = 0; J < d; J++) {
             const int ex = J == 0, ey = J == 1, ez = J == 2;
-            add_grow(acc, k, d, h, ex, ey, ez, -r.Mp[J] * ih2, r.a0[1 + 2 * J], r.a1[1 + 2 * J]);
-            add_grow(acc, k, d, h, -ex, -ey, -ez, -r.Mm[J] * ih2, r.a0[2 + 2 * J], r.a1[2 + 2 * J]);
+            add_grow<NE>(acc, k, d, h, ex, ey, ez, -r.Mp[J] * ih2, r.a0[1 + 2 * J], r.a1[1 + 2 * J]);
+            add_grow<NE>(acc, k, d, h, -ex, -ey, -ez, -r.Mm[J] * ih2, r.a0[2 + 2 * J], r.a1[2 + 2 * J]);
         }
-    } else if (f <= k.ne) {
+    } else if (f <= (NE ? NE : k.ne)) {
         if (mode != 0) {
             acc(0, 0, 0, 0, 0, 0, f, 1.0);
             return;
@@ -119,7 +121,7 @@ __host__ __device__ constexpr void jac_row(Acc &acc, int f, const DCoef &k, int 
         const int j = f - 1;
         acc(0, 0, 0, 0, 0, 0, f, 1.0 / dt + k.keta * r.a3[j][j] + 3.0 * k.gamma_eta * d * ih2);
         acc(0, 0, 0, 0, 0, 0, 0, k.keta * r.a2[j]);
-        for (int i = 0; i < k.ne; i++)
+        for (int i = 0; i < (NE ? NE : k.ne); i++)
             if (i != j) acc(0, 0, 0, 0, 0, 0, 1 + i, k.keta * r.a3[j][i]);
         for (int J = 0; J < d; J++) {
             const int ex = J == 0, ey = J == 1, ez = J == 2;
@@ -127,12 +129,12 @@ __host__ __device__ constexpr void jac_row(Acc &acc, int f, const DCoef &k, int 
             acc(0, 0, 0, -ex, -ey, -ez, f, -1.5 * k.gamma_eta * ih2);
         }
     } else {
-        const int I = f - 1 - k.ne;
+        const int I = f - 1 - (NE ? NE : k.ne);
         const double i2h = 0.5 / h;
         for (int J = 0; J < d; J++) {
             const int ex = J == 0, ey = J == 1, ez = J == 2;
-            add_sigrow(acc, k, d, h, ex, ey, ez, I, J, i2h * acc.flip(ex, ey, ez));
-            add_sigrow(acc, k, d, h, -ex, -ey, -ez, I, J, -i2h * acc.flip(-ex, -ey, -ez));
+            add_sigrow<NE>(acc, k, d, h, ex, ey, ez, I, J, i2h * acc.flip(ex, ey, ez));
+            add_sigrow<NE>(acc, k, d, h, -ex, -ey, -ez, I, J, -i2h * acc.flip(-ex, -ey, -ez));
         }
     }
 }

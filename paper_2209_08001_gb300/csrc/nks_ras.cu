@@ -331,6 +331,12 @@ int ras_plan_create(Problem *P, std::string &err)
         err = "internal: no Jacobian pattern for this dimension";
         return NKS_EINVAL;
     }
+    // the factor kernel's row capacity (k_ras_factor<CAP, ...>)
+    for (int f = 0; f < nf; f++)
+        if (CP.len[f] > (P->k.ne == 3 ? 100 : 84)) {
+            err = "internal: a Jacobian row exceeds the factor kernel's row capacity";
+            return NKS_EINVAL;
+        }
     // every column left of the diagonal lies on an earlier wavefront level or at the same point
     for (int f = 0; f < nf; f++)
         for (int a = 0; a < CP.diag[f]; a++) {
@@ -586,7 +592,8 @@ struct FacTables {
 };
 
 // adds the contributions of one Jacobian row into a slot-indexed row (columns
-// outside the box dropped)
+// outside the box dropped); MASK: also mark the slots the row's paths reach
+template <bool MASK>
 struct DevAcc {
     double *vals;
     unsigned long long *pres;  // bit s: a path of the row ends in slot s (the row's own pattern)
@@ -613,7 +620,7 @@ struct DevAcc {
         const int s = slotmap[((dz + 2) * 25 + (dy + 2) * 5 + (dx + 2)) * nf + fc];
         if (s >= 0) {
             vals[s] += v;
-            pres[s >> 6] |= 1ull << (s & 63);
+            if constexpr (MASK) pres[s >> 6] |= 1ull << (s & 63);
         }
     }
     // -1 when the one-cell step o stays on the cell (Neumann boundary), else 1
@@ -627,6 +634,11 @@ struct DevAcc {
 
 // Fused assembly + ILU(0) (textbook IKJ order within a row) of J restricted to
 // each overlapped box.  Rows of earlier points are final when a level starts.
+// NE: the order parameters (1 or 3); the row is accumulated in per-thread memory of
+// the pattern's longest row (83 entries with one order parameter, 97 with three).
+// MASK: the pattern is a union over boundary situations (elasticity under Neumann
+// boundaries), so each point's fill is kept to its own slots.
+template <int NE, bool MASK>
 __global__ void k_ras_factor(DGrid g, DCoef k, Bat bt, const double *__restrict__ isc, int mode, FacTables T,
                              const SubInfo *__restrict__ subs,
                              const int *__restrict__ lvl_ptr, const long long *__restrict__ lvl_blk,
@@ -650,7 +662,8 @@ __global__ void k_ras_factor(DGrid g, DCoef k, Bat bt, const double *__restrict_
     const int *lp_of = lvl_lp + si.pos_off;
     double *F = fac + si.fac_off;
     const long long N = g.N;
-    double vals[kMaxRow];
+    constexpr int CAP = NE == 3 ? 100 : 84;
+    double vals[CAP];
     for (int lev = 0; lev < si.nlev; lev++) {
         const long long cp = pad4((long long)(lptr[lev + 1] - lptr[lev]));
         double *blk = F + lblk[lev];
@@ -661,10 +674,10 @@ __global__ void k_ras_factor(DGrid g, DCoef k, Bat bt, const double *__restrict_
             const int gx = wrapi(si.org[0] + lx, g.n[0]), gy = wrapi(si.org[1] + ly, g.n[1]),
                       gz = wrapi(si.org[2] + lz, g.n[2]);
             const long long gp = index_of(g, gx, gy, gz);
-            RowCtx rc{};
+            RowCtx rc;  // mode 0 fills every entry the rows read; mode 1 reads none
             if (mode == 0) {
                 // pointwise block part[(a * (1 + ne) + b) N + p] = dG_a / dx_b, x = (c, eta_1..eta_ne)
-                const int ne = k.ne, w = 1 + ne;
+                constexpr int ne = NE, w = 1 + NE;
                 rc.a0[0] = part[gp];
                 for (int j = 0; j < ne; j++) {
                     rc.a1[0][j] = part[(1 + j) * N + gp];
@@ -690,9 +703,9 @@ __global__ void k_ras_factor(DGrid g, DCoef k, Bat bt, const double *__restrict_
                 // pattern is the union over all places in the grid, and ILU(0) fills only
                 // the point's own pattern (as on a periodic grid, where they coincide)
                 unsigned long long pres[2] = {0ull, 0ull};
-                DevAcc acc{vals, pres, slotmap + (size_t)f * 125 * nf, nf, lx, ly, lz, &si, gx, gy, gz, g.n[0],
-                           g.n[1], g.n[2], g.bc};
-                jac_row(acc, f, k, D, g.h, dt, mode, rc);
+                DevAcc<MASK> acc{vals, pres, slotmap + (size_t)f * 125 * nf, nf, lx, ly, lz, &si, gx, gy, gz, g.n[0],
+                                 g.n[1], g.n[2], g.bc};
+                jac_row<NE>(acc, f, k, D, g.h, dt, mode, rc);
                 for (int a = 0; a < T.diag[f]; a++) {
                     const char4 o = tmpl[r0 + a];
                     const int nx = lx + o.x, ny = ly + o.y, nz = lz + o.z;
@@ -716,7 +729,8 @@ __global__ void k_ras_factor(DGrid g, DCoef k, Bat bt, const double *__restrict_
                     // a_ib -= l * u_kb for every later column b of row i present in row k
                     for (int u = upd_ptr[r0 + a]; u < upd_ptr[r0 + a + 1]; u++) {
                         const short2 bc = upd[u];
-                        if ((pres[bc.x >> 6] >> (bc.x & 63)) & 1ull) vals[bc.x] -= l * U[(long long)st[rk + bc.y] * qcp + qk];
+                        if (!MASK || ((pres[bc.x >> 6] >> (bc.x & 63)) & 1ull))
+                            vals[bc.x] -= l * U[(long long)st[rk + bc.y] * qcp + qk];
                     }
                 }
                 const double piv = vals[T.diag[f]];
@@ -1594,10 +1608,11 @@ void launch_factor(Problem *P, int mode, const Bat &bt)
     T.nlow = CP.nlow;
     T.nup = CP.nup;
     T.nf = P->nf;
-    k_ras_factor<<<dim3(R->nsub, bt.nb), 64, 0, P->stream>>>(P->g, P->k, bt, P->isc, mode, T, R->sub, R->lvl_ptr,
-                                                             R->lvl_blk,
-                                                R->lvl_lp, R->tmpl, R->st, R->slotmap, R->upd_ptr, R->upd, P->part,
-                                                P->mob, R->fac, P->dflag);
+    auto kern = P->k.ne == 3 ? (pat_var(P) & 1 ? k_ras_factor<3, true> : k_ras_factor<3, false>)
+                             : (pat_var(P) & 1 ? k_ras_factor<1, true> : k_ras_factor<1, false>);
+    kern<<<dim3(R->nsub, bt.nb), 64, 0, P->stream>>>(P->g, P->k, bt, P->isc, mode, T, R->sub, R->lvl_ptr, R->lvl_blk,
+                                                     R->lvl_lp, R->tmpl, R->st, R->slotmap, R->upd_ptr, R->upd, P->part,
+                                                     P->mob, R->fac, P->dflag);
 }
 
 using LaneKernel = void (*)(DGrid, Bat, const SubInfo *, const int *, const long long *, const int *, const float *,
