@@ -1610,7 +1610,10 @@ void launch_factor(Problem *P, int mode, const Bat &bt)
     T.nf = P->nf;
     auto kern = P->k.ne == 3 ? (pat_var(P) & 1 ? k_ras_factor<3, true> : k_ras_factor<3, false>)
                              : (pat_var(P) & 1 ? k_ras_factor<1, true> : k_ras_factor<1, false>);
-    kern<<<dim3(R->nsub, bt.nb), 64, 0, P->stream>>>(P->g, P->k, bt, P->isc, mode, T, R->sub, R->lvl_ptr, R->lvl_blk,
+    // one thread per point of the largest level (a level's points are independent),
+    // so every level is one round of row eliminations
+    const int threads = std::min(256, std::max(64, (R->maxcnt + 31) / 32 * 32));
+    kern<<<dim3(R->nsub, bt.nb), threads, 0, P->stream>>>(P->g, P->k, bt, P->isc, mode, T, R->sub, R->lvl_ptr, R->lvl_blk,
                                                      R->lvl_lp, R->tmpl, R->st, R->slotmap, R->upd_ptr, R->upd, P->part,
                                                      P->mob, R->fac, P->dflag);
 }
