@@ -138,6 +138,15 @@ void Problem::upload_isc()
                       cudaMemcpyHostToDevice, stream);
 }
 
+void Problem::upload_rows(double *dev0, const double *rows, int count)
+{
+    double *h = hsc_ring + (size_t)(ring_pos++ % kRing) * nb * I_NSC;
+    for (int i = 0; i < nb; i++)
+        for (int q = 0; q < count; q++) h[(size_t)i * count + q] = rows[(size_t)i * count + q];
+    cudaMemcpy2DAsync(dev0, (size_t)stride, h, sizeof(double) * count, sizeof(double) * count, (size_t)nb,
+                      cudaMemcpyHostToDevice, stream);
+}
+
 // count doubles at dev0 (instance 0's address) of every instance -> hread[i * 64 + q],
 // and both flag words of every instance -> hflags[2 i + q]; synchronises
 void Problem::enqueue_readback(const double *dev0, int count)

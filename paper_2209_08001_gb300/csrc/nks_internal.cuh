@@ -377,6 +377,9 @@ struct Problem {
     Bat masked(int m) const { return Bat{stride, dmask + (size_t)m * nb, nb}; }
     Bat set_mask(int m, const std::vector<char> &on);   // upload mask m, return its Bat
     void upload_isc();                                  // isc of every instance from is[]
+    // count (<= I_NSC) doubles per instance, host rows[i * count + q], to dev0 (instance 0's
+    // address) + the slab stride; staged through the pinned ring, no synchronisation
+    void upload_rows(double *dev0, const double *rows, int count);
     int read_scalars(const double *dev0, int count, const char *where);  // -> hread[b * 64 + i], hflags
     int read_flags(const char *where);                                   // -> hflags[2 b + q]
     void enqueue_readback(const double *dev0, int count);                // the copies of read_scalars

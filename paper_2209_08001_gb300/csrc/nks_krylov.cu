@@ -51,8 +51,12 @@ struct GmLayout {
         total = scal + 16;
     }
 };
-// scal slots
-enum { S_WN0 = 0, S_WN = 1, S_RES = 2, S_INV = 3, S_FLAG = 4, S_BETA = 5, S_KDIM = 6 };
+// scal slots; S_GTOL .. S_CGSV: the device-side control of a cycle (its tolerance,
+// iterations left in the solve, 1 while iterating, iterations, second passes and
+// Gram-Schmidt vector transfers so far in the cycle)
+enum { S_WN0 = 0, S_WN = 1, S_RES = 2, S_INV = 3, S_FLAG = 4, S_BETA = 5, S_KDIM = 6, S_GTOL = 7, S_LEFT = 8,
+       S_ACTV = 9, S_NIT = 10, S_NREO = 11, S_CGSV = 12 };
+constexpr int kCycleRow = 6;  // S_GTOL .. S_CGSV, written by the host at the start of a cycle
 
 // Element-wise kernels run instance blockIdx.y of the batch.
 #define NKS_INST(...)                         \
@@ -461,6 +465,30 @@ __global__ void k_arnoldi(Bat bt, double *gm, GmLayout L, int j)
     sc[S_KDIM] = j + 1;
 }
 
+// End of Arnoldi step j of every instance still iterating: count the step, its
+// second pass and its Gram-Schmidt vector transfers (pass 1 reads j + 2 vectors, the
+// update reads j + 2 and writes 1; a second pass repeats both, or with the FP32 basis,
+// whose second-pass products ride on the first update, adds only its update, j + 3),
+// and take the instance out of the cycle (act[i] = 0) when its residual estimate met
+// the tolerance, its iterations are spent, the Krylov space broke down, or the estimate
+// is not a number (the true residual decides then).  The host reads the counters once
+// per few steps instead of after every step.
+__global__ void k_gm_continue(Bat bt, double *gm, GmLayout L, int j, int *act, int fp32_basis)
+{
+    NKS_GM_INST()
+    double *sc = gm + L.scal;
+    const bool second = sc[S_FLAG] != 0.0;
+    sc[S_NIT] = j + 1;
+    sc[S_NREO] += second ? 1.0 : 0.0;
+    const double extra = fp32_basis ? (j + 3.0) : (2.0 * j + 5.0);
+    sc[S_CGSV] += (2.0 * j + 5.0) + (second ? extra : 0.0);
+    const double res = sc[S_RES], wn = sqrt(sc[S_WN]);
+    if (!(res == res) || res <= sc[S_GTOL] || (double)(j + 1) >= sc[S_LEFT] || wn == 0.0) {
+        act[blockIdx.x] = 0;
+        sc[S_ACTV] = 0.0;
+    }
+}
+
 // beta = sqrt(beta2[0]): the norm of the starting residual
 __global__ void k_gm_start(Bat bt, double *gm, GmLayout L, const double *beta2)
 {
@@ -707,14 +735,27 @@ static int gmres_t(Problem *P, Basis<TV> K, int mode, const double *b, double *x
         if (!any) break;
         const Bat bc = P->set_mask(M_CYC, cyc);
         act = cyc;
-        Bat ba = P->set_mask(M_ACT, act);
+        const Bat ba = P->set_mask(M_ACT, act);
+        {
+            // the cycle's control rows: tolerance, iterations left, active, counters
+            std::vector<double> rows((size_t)nbt * kCycleRow, 0.0);
+            for (int i = 0; i < nbt; i++) {
+                rows[(size_t)i * kCycleRow + 0] = P->is[i].gtol;
+                rows[(size_t)i * kCycleRow + 1] = (double)(maxit - P->is[i].gits);
+                rows[(size_t)i * kCycleRow + 2] = cyc[i] ? 1.0 : 0.0;
+            }
+            P->upload_rows(gm + L.scal + S_GTOL, rows.data(), kCycleRow);
+        }
         k_gm_start<<<nbt, 1, 0, st>>>(bc, gm, L, P->dscal + 1);
         k_scale_dev<double, TV><<<dim3(nb(n), nbt), kT, 0, st>>>(bc, n, R, gm + L.scal + S_INV, V);
         P->count(2);
+        // Arnoldi steps in groups of kGroup between host read-backs: each step ends with
+        // the device-side test of every instance (k_gm_continue), which masks finished
+        // instances out of the steps that follow; the host learns of them at the group's end
+        constexpr int kGroup = 4;
         for (int j = 0; j < m; j++) {
-            // one Arnoldi step of every instance still iterating, then the read-back
-            // of its scalars (captured together when graphs are on)
-            auto iteration = [&](bool readback) {
+            // one Arnoldi step of every instance still iterating (one graph when graphs are on)
+            auto iteration = [&]() {
                 TV *vj = V + (size_t)j * ldv, *vn = V + (size_t)(j + 1) * ldv;
                 ras_apply_t<TV>(P, vj, Z, ba);         // z = RAS^-1 v_j (sum of z_c to zsum)
                 apply_J<TV>(P, mode, Z, W, true, ba);  // w = J P z
@@ -753,44 +794,30 @@ static int gmres_t(Problem *P, Basis<TV> K, int mode, const double *b, double *x
                 k_scale_dev<TV, TV><<<dim3(nb(sizeof(TV) == sizeof(float) ? n / 4 + 1 : n), nbt), kT, 0, st>>>(
                     ba, n, W, gm + L.scal + S_INV, vn);
                 P->count(7);  // multidot + update (+ dots) + decide + update + accum + arnoldi + scale
-                if (readback) P->enqueue_readback(gm + L.scal, 8);
+                k_gm_continue<<<nbt, 1, 0, st>>>(ba, gm, L, j, P->dmask + (size_t)M_ACT * nbt,
+                                                   sizeof(TV) == sizeof(float) ? 1 : 0);
+                P->count(1);
             };
-            if (use_graphs && run_graph(P, mode, j, [&] { iteration(true); })) {
-                rc = P->sync_check("gmres");
-            } else {
-                iteration(false);
-                rc = P->read_scalars(gm + L.scal, 8, "gmres");
-            }
+            if (!(use_graphs && run_graph(P, mode, j, iteration))) iteration();
+            if ((j + 1) % kGroup != 0 && j + 1 < m) continue;
+            rc = P->read_scalars(gm + L.scal, S_CGSV + 1, "gmres");
             if (rc) return rc;
             for (int i = 0; i < nbt; i++)
-                if (act[i] && (P->hflags[2 * i + 1] & 4)) {
+                if (cyc[i] && (P->hflags[2 * i + 1] & 4)) {
                     P->err = "Schwarz sweep: a bulk copy of the factors did not complete";
                     return NKS_ETIMEOUT;
                 }
-            bool changed = false, left = false;
-            for (int i = 0; i < nbt; i++) {
-                if (!act[i]) continue;
-                IState &s = P->is[i];
-                s.gits++;
-                // algorithmic traffic of this step's Gram-Schmidt passes: pass 1 reads j + 2
-                // vectors, the update reads j + 2 and writes 1; the second pass repeats both
-                // (FP32 basis: the second pass's dot products ride on the first update, so a
-                // second pass adds only its update, j + 3 transfers)
-                const bool second = P->hread[(size_t)i * 64 + S_FLAG] != 0.0;
-                P->stats.reorth += second ? 1 : 0;
-                const double extra = sizeof(TV) == sizeof(float) ? (j + 3.0) : (2.0 * j + 5.0);
-                P->stats.cgs_bytes += ((2.0 * j + 5.0) + (second ? extra : 0.0)) * (double)n * sizeof(TV);
-                const double res = P->hread[(size_t)i * 64 + S_RES], wn = sqrt(P->hread[(size_t)i * 64 + S_WN]);
-                // NaN leaves the cycle (the true residual decides)
-                if (!(res == res) || res <= s.gtol || s.gits >= maxit || wn == 0.0) {
-                    act[i] = 0;
-                    changed = true;
-                } else {
-                    left = true;
-                }
-            }
+            bool left = false;
+            for (int i = 0; i < nbt; i++) left = left || (cyc[i] && P->hread[(size_t)i * 64 + S_ACTV] != 0.0);
             if (!left) break;
-            if (changed) ba = P->set_mask(M_ACT, act);
+        }
+        // the cycle's iterations and Gram-Schmidt work of every instance (read back above)
+        for (int i = 0; i < nbt; i++) {
+            if (!cyc[i]) continue;
+            const double *h = P->hread + (size_t)i * 64;
+            P->is[i].gits += (int)h[S_NIT];
+            P->stats.reorth += (long long)h[S_NREO];
+            P->stats.cgs_bytes += h[S_CGSV] * (double)n * sizeof(TV);
         }
         // x += M^-1 (V y), then the true residual in FP64
         k_hsolve<<<nbt, 1, 0, st>>>(bc, gm, L);
