@@ -48,7 +48,7 @@ KEYS = ("dt", "t", "energy", "mass", "newton_its", "gmres_its", "retries", "stat
 
 
 @pytest.mark.parametrize("dim,n,sub,prec", [(2, (24, 20), (2, 2), "fp64"), (2, (24, 20), (2, 2), "mixed"),
-                                            (3, (9, 10, 8), (2, 2, 2), "fp64")])
+                                            (3, (9, 10, 8), (2, 2, 2), "fp64"), (3, (9, 10, 8), (2, 2, 2), "mixed")])
 def test_batch_slots_equal_their_runs_alone(nks, dim, n, sub, prec):
     op = S.options(sub=sub, overlap=1, precision=prec, dt_mode="energy")
     cbars, seeds = [0.14, 0.2, 0.17, 0.23], [11, 12, 13, 14]
