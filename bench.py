@@ -142,7 +142,8 @@ def roofline(st, kernels, mixed, pk, wl, side, precision):
                     "bound": "hbm", "achieved": by / avg_s / 1e9, "peak": pk.get("hbm_gbs"), "unit": "GB/s",
                     "frac": by / avg_s / 1e9 / pk.get("hbm_gbs"),
                     "peak_source": "%s, copy bandwidth" % pk.get("source"),
-                    "limiter": "wavefront latency: one block barrier per level of the triangular sweeps",
+                    "limiter": "wavefront latency: each box is a chain of dependent level steps (one "
+                               "point's rows per thread, then a block barrier) at one warp per scheduler",
                     "algorithmic_bytes_per_launch": by, "algorithmic_flops_per_launch": fl}
         else:
             tr, why = traffic_for(wl, side, precision, "k_ras_apply")
