@@ -115,7 +115,10 @@ def test_neumann_operators_match_oracle(nks, dim, n, sub, ov, elastic):
 @pytest.mark.parametrize("dim,n,sub,ov,elastic", CASES[:3])
 def test_neumann_mixed_operators_match_oracle(nks, dim, n, sub, ov, elastic):
     cf = S.coefficients()
-    op = S.options(sub=sub, overlap=ov, precision="mixed")
+    # the set-up equilibrium's GMRES runs into its 300-iteration cap on these ragged grids,
+    # so its Newton loop needs close to the default 10 steps and their count follows the
+    # FP32 rounding; the operators compared below take their fields as arguments
+    op = S.options(sub=sub, overlap=ov, precision="mixed", u0_maxit=40)
     (c1, e1, u1), (c0, e0, u0) = _pair(dim, n, 500 + dim)
     P = nks.Problem(dim, n, 0.25, c0, e0, cf, op, neumann=True)
     O = oracle.Problem(dim, n, 0.25, cf, op, neumann=True)
