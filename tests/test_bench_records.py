@@ -72,3 +72,21 @@ def test_bench_reports_traffic_only_for_the_captured_sources(tmp_path, monkeypat
     monkeypatch.setattr(bench, "TRAFFIC_FILE", str(tmp_path / "missing.json"))
     tr, why = bench.traffic_for("w1", None, "mixed", "k_ras_apply_lane")
     assert tr is None
+
+
+def test_roofline_of_the_sweep_is_algorithmic_bytes_over_the_mean_launch_time():
+    import bench
+    st = {"ms": {"schwarz_apply": 20.0, "jacobian_action": 5.0}, "launches": {"schwarz_apply": 40,
+                                                                             "jacobian_action": 40},
+          "schwarz_bytes": 2.0e9, "schwarz_flops": 1.0e9}
+    pk = {"hbm_gbs": 5000.0, "source": "test peaks"}
+    r = bench.roofline(st, {}, True, pk, "no-such-workload", None, "mixed")
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert r["avg_launch_ms"] == pytest.approx(0.5)
+    assert r["achieved"] == pytest.approx(2.0e9 / 0.5e-3 / 1e9)  # 4000 GB/s
+    assert r["frac"] == pytest.approx(0.8)
+    assert r["traffic"] is None and r["launches"] == 40
+    r64 = bench.roofline(st, {}, False, pk, "no-such-workload", None, "fp64")
+    assert r64["unit"] == "TFLOP/s"
+    assert r64["achieved"] == pytest.approx(1.0e9 / 0.5e-3 / 1e12)
+    assert r64["frac"] == pytest.approx(r64["achieved"] / bench.FP64_PEAK_TFLOPS)
